@@ -1,0 +1,150 @@
+"""FP64 physics of the equilibrium-dust path (test infrastructure only).
+
+Plain NumPy/SciPy definitions, one function per quantity, in the order the
+method uses them (Juvela 2019, arXiv:1812.06632, Sect. 2.1.1: the frequency
+integral of absorbed energy is gathered on the device; a separate kernel
+solves the equilibrium temperature of each cell; with a reference/constant
+field the constant sources are simulated once, Sect. 2.1.2).
+
+Units: cgs.  Densities rho are in arbitrary "density units"; opacities kappa
+are cross sections per density unit (rho * kappa is an inverse length in cm);
+a cell of hierarchy level L (0-based) has side ell * 2^-L for root-cell side
+ell (cm).
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.optimize import brentq
+
+# CODATA 2018 exact SI-defined constants, in cgs
+H_PLANCK = 6.62607015e-27      # erg s
+K_BOLTZ = 1.380649e-16         # erg / K
+C_LIGHT = 2.99792458e10        # cm / s
+W_UNIT = 2.0 ** 32             # fixed-point units of one package's initial weight
+
+T_MIN = 2.7                    # K: temperature of cells that absorb nothing
+T_MAX = 3000.0                 # K: upper end of the solver's range
+
+
+def planck_nu(nu, T):
+    """B_nu(T) = (2 h nu^3 / c^2) / (exp(h nu / k T) - 1)  [erg/s/cm^2/Hz/sr]."""
+    nu = np.asarray(nu, dtype=np.float64)
+    T = np.asarray(T, dtype=np.float64)
+    x = H_PLANCK * nu / (K_BOLTZ * T)
+    with np.errstate(over="ignore"):
+        return (2.0 * H_PLANCK * nu ** 3 / C_LIGHT ** 2) / np.expm1(x)
+
+
+def dplanck_dT(nu, T):
+    """dB_nu/dT."""
+    nu = np.asarray(nu, dtype=np.float64)
+    T = np.asarray(T, dtype=np.float64)
+    x = H_PLANCK * nu / (K_BOLTZ * T)
+    with np.errstate(over="ignore", invalid="ignore"):
+        em1 = np.expm1(x)
+        val = (2.0 * H_PLANCK * nu ** 3 / C_LIGHT ** 2) * (x / T) * (em1 + 1.0) / (em1 * em1)
+    return np.nan_to_num(val, nan=0.0, posinf=0.0)
+
+
+def trapezoid_weights(nu):
+    """Trapezoid-rule weights w_nu on the frequency nodes (sum_nu w f(nu) ~ int f dnu)."""
+    nu = np.asarray(nu, dtype=np.float64)
+    w = np.zeros_like(nu)
+    if nu.size == 1:
+        w[0] = 1.0
+        return w
+    d = np.diff(nu)
+    w[:-1] += 0.5 * d
+    w[1:] += 0.5 * d
+    return w
+
+
+def emission_integral(T, nu, kabs):
+    """E(T) = 4 pi sum_nu w_nu kabs(nu) B_nu(T): power emitted per unit of rho*V."""
+    w = trapezoid_weights(nu)
+    return 4.0 * np.pi * float(np.sum(w * np.asarray(kabs, np.float64) * planck_nu(nu, T)))
+
+
+def temperature(A, nu, kabs, t_min=T_MIN, t_max=T_MAX, rtol=1e-13):
+    """Equilibrium temperature: root of E(T) = A (Brent's method).  A at or
+    below E(t_min) (in particular no absorption) gives t_min; above E(t_max)
+    gives t_max."""
+    A = float(A)
+    e_lo = emission_integral(t_min, nu, kabs)
+    e_hi = emission_integral(t_max, nu, kabs)
+    if not A > e_lo:
+        return t_min
+    if A >= e_hi:
+        return t_max
+    return brentq(lambda T: emission_integral(T, nu, kabs) - A, t_min, t_max,
+                  xtol=1e-14, rtol=rtol, maxiter=500)
+
+
+def temperatures(A, nu, kabs, **kw):
+    return np.array([temperature(a, nu, kabs, **kw) for a in np.asarray(A).ravel()])
+
+
+def cell_volumes(grid, ell):
+    """Volume (cm^3) of every cell of an oracle.Grid with root-cell side ell."""
+    lv = grid.level_of()
+    return (ell * np.ldexp(1.0, -lv)) ** 3
+
+
+def absorbed_power(tally, e_unit, nu, rho, volume, A_in=None):
+    """Absorbed power per unit rho*V (Sect. 2.1.1's frequency integral):
+    A_c = A_in + sum_nu w_nu e_unit(nu) tally[nu, c] / (rho_c V_c).
+    ``tally`` is int64 [n_freq, n_cells]; ``e_unit[nu]`` the energy (erg/s/Hz)
+    of one fixed-point unit.  Cells with rho = 0 (and parents) get A_in."""
+    tally = np.asarray(tally)
+    w = trapezoid_weights(nu)
+    acc = np.zeros(tally.shape[1], np.float64)
+    for k in range(tally.shape[0]):
+        acc += (w[k] * float(e_unit[k])) * tally[k].astype(np.float64)
+    rv = np.asarray(rho, np.float64) * np.asarray(volume, np.float64)
+    out = np.zeros_like(acc) if A_in is None else np.array(A_in, np.float64, copy=True)
+    ok = rv > 0
+    out[ok] += acc[ok] / rv[ok]
+    return out
+
+
+def background_package_energy(I_nu, nx, ny, nz, ell, n_packages):
+    """Energy per unit of weight of a background package.  An isotropic
+    intensity I_nu outside the box sends pi I_nu per unit area through every
+    face, so the packages share pi I_nu S (S the box surface); one package
+    starts with 2^32 units."""
+    S = 2.0 * (nx * ny + ny * nz + nz * nx) * ell * ell
+    return np.pi * np.asarray(I_nu, np.float64) * S / n_packages / W_UNIT
+
+
+def point_package_energy(L_nu_total, n_packages):
+    """Energy per unit of weight of a point-source package: the sources'
+    total luminosity L_nu (erg/s/Hz) shared by n_packages."""
+    return np.asarray(L_nu_total, np.float64) / n_packages / W_UNIT
+
+
+def point_source_cdf(L_nu):
+    """Cumulative luminosity fractions per frequency, [n_freq, n_ps], FP32,
+    used to pick the source of a package (last entry forced to 1)."""
+    L = np.asarray(L_nu, np.float64)          # [n_ps, n_freq]
+    tot = L.sum(axis=0)
+    cdf = np.cumsum(L, axis=0) / np.where(tot > 0, tot, 1.0)
+    cdf[-1, :] = 1.0
+    return cdf.T.astype(np.float32)
+
+
+def dust_luminosity(T, rho, volume, kabs_nu, nu):
+    """L_c(nu) = 4 pi rho_c V_c kabs(nu) B_nu(T_c) of the given cells (erg/s/Hz)."""
+    return 4.0 * np.pi * np.asarray(rho, np.float64) * np.asarray(volume, np.float64) \
+        * float(kabs_nu) * planck_nu(nu, np.asarray(T, np.float64))
+
+
+def dust_weights(L, n_per_cell):
+    """Fixed-point initial weights of dust packages at one frequency: every
+    cell sends n_per_cell packages; W_c = rint(2^32 L_c / max L), and one unit
+    then carries e_unit = (max L / n_per_cell) / 2^32.  Returns (W uint64, e_unit)."""
+    L = np.asarray(L, np.float64)
+    Lmax = float(L.max()) if L.size else 0.0
+    if not Lmax > 0:
+        return np.zeros(L.shape, np.uint64), 0.0
+    W = np.rint((L / Lmax) * W_UNIT).astype(np.uint64)
+    return W, Lmax / n_per_cell / W_UNIT

@@ -1,0 +1,429 @@
+"""Pins of the CPU oracle against what the mathematics and the physics fix
+(no GPU).  Each test is chosen so that a plausible slip in the oracle (a
+dropped term, a wrong sign, a transposed operand, a wrong constant) fails it.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import physics as P
+from paper_1812_06632_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _grid(cl):
+    return oracle.Grid(cl.nx, cl.ny, cl.nz, cl.level_start, cl.rho, cl.child, cl.parent)
+
+
+def _ulp_err(approx, exact):
+    approx = np.asarray(approx, np.float64)
+    exact = np.asarray(exact, np.float64)
+    ulp = np.spacing(np.abs(exact).astype(np.float32)).astype(np.float64)
+    return np.abs(approx - exact) / ulp
+
+
+# ----------------------------------------------------------------------------
+# random numbers
+# ----------------------------------------------------------------------------
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = oracle.philox4x32_10(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_u01_open_interval_and_grid():
+    xs = [0, 1, 255, 256, 0x7FFFFFFF, 0x80000000, 0xFFFFFF00, 0xFFFFFFFF]
+    us = [oracle.u01(x) for x in xs]
+    assert min(us) == 2.0 ** -24 and max(us) == 1.0 - 2.0 ** -24
+    for x, u in zip(xs, us):
+        assert 0.0 < u < 1.0
+        k = u * 2.0 ** 24
+        assert k == int(k) and int(k) % 2 == 1 and int(k) == ((x >> 8) | 1)
+
+
+# ----------------------------------------------------------------------------
+# elementary functions of the FP32 contract
+# ----------------------------------------------------------------------------
+def test_exp_neg_within_2ulp_of_fp64():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([-rng.uniform(0, 87, 400_000), -np.geomspace(1e-30, 1, 20_000),
+                        [0.0, -0.5 * math.log(2), -math.log(2), -10 * math.log(2), -87.0]])
+    x = x.astype(np.float32)
+    y = oracle.exp_neg(x)
+    err = _ulp_err(y, np.exp(x.astype(np.float64)))
+    assert err.max() <= 2.0, err.max()
+    assert oracle.exp_neg(np.float32([-87.5, -1000.0])).tolist() == [0.0, 0.0]
+    assert oracle.exp_neg(np.float32([0.0]))[0] == 1.0
+
+
+def test_one_minus_exp_within_2ulp_of_fp64():
+    rng = np.random.default_rng(1)
+    tau = np.concatenate([np.geomspace(1e-30, 0.5, 100_000), rng.uniform(0.4, 0.6, 50_000),
+                          rng.uniform(0, 80, 100_000)]).astype(np.float32)
+    q = oracle.one_minus_exp(tau)
+    err = _ulp_err(q, -np.expm1(-tau.astype(np.float64)))
+    assert err.max() <= 2.0, err.max()
+    assert oracle.one_minus_exp(np.float32([0.0, -1.0])).tolist() == [0.0, 0.0]
+
+
+def test_log_within_2ulp_of_fp64():
+    rng = np.random.default_rng(2)
+    k = rng.integers(0, 1 << 24, 400_000)
+    u = (((k >> 0) | 1) * 2.0 ** -24).astype(np.float32)
+    u = np.concatenate([u, np.float32([2.0 ** -24, 0.5, 1 - 2.0 ** -24, 0.70710677, 0.7071068])])
+    y = oracle.log(u)
+    err = _ulp_err(y, np.log(u.astype(np.float64)))
+    assert err.max() <= 2.0, err.max()
+
+
+# ----------------------------------------------------------------------------
+# pencil beams: exp(-tau) attenuation and geometry
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("refined", [False, True])
+def test_pencil_beam_column_exp_minus_tau(refined):
+    n, kabs = 24, 0.37
+    cl = I.regular(np.ones((n, 1, 1), np.float32))
+    if refined:                       # refine every 3rd cell: same medium, deeper tree
+        cl = I.refine_cells(cl, np.arange(0, n, 3))
+    G = _grid(cl)
+    tally, st, steps = oracle.trace_pencil(G, [0.5, 0.5, 0.0], [0.0, 0.0, 1.0], kabs=kabs)
+    assert tally.sum() + st["escaped"] == st["emitted"] == oracle.W_UNIT
+    T = st["escaped"] / oracle.W_UNIT
+    assert abs(T / math.exp(-kabs * n) - 1.0) < n * 4e-7
+    # every root cell (with its children) absorbs W_in (1 - e^-kabs)
+    per_root = np.zeros(n)
+    owner = np.arange(cl.n_cells)
+    for k, p in enumerate(cl.parent):
+        owner[cl.n_root + 8 * k: cl.n_root + 8 * k + 8] = p
+    np.add.at(per_root, owner, tally)
+    expect = np.exp(-kabs * np.arange(n)) * (1 - math.exp(-kabs)) * oracle.W_UNIT
+    np.testing.assert_allclose(per_root, expect, rtol=5e-6 * n)
+    assert steps == (n if not refined else n + (n // 3) * 1)
+
+
+def test_pencil_beam_oblique_path_length():
+    n, kabs = 16, 0.05
+    cl = I.regular(np.ones((n, n, n), np.float32))
+    d = np.array([0.3, 0.5, 0.81], np.float64)
+    d /= np.linalg.norm(d)
+    d32 = d.astype(np.float32)
+    tally, st, _ = oracle.trace_pencil(_grid(cl), [0.0, 0.0, 0.0], d32, kabs=kabs)
+    L = n / np.abs(d32.astype(np.float64)).max()       # first face of the box hit
+    assert abs(st["escaped"] / oracle.W_UNIT / math.exp(-kabs * L) - 1) < 2e-5
+
+
+def test_zero_density_cells_are_transparent():
+    n = 10
+    rho = np.zeros((n, 1, 1), np.float32)
+    rho[4, 0, 0] = 1.0
+    G = _grid(I.regular(rho))
+    tally, st, _ = oracle.trace_pencil(G, [0.5, 0.5, 0.0], [0.0, 0.0, 1.0], kabs=0.5, ksca=2.0)
+    # only cell 4 can absorb or scatter; cells below it never get a deposit
+    assert np.all(tally[:4] == 0)
+    assert tally.sum() + st["escaped"] == oracle.W_UNIT
+
+
+# ----------------------------------------------------------------------------
+# conservation (exact, integer) for every source class and grid kind
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("source", [oracle.SRC_BACKGROUND, oracle.SRC_POINT, oracle.SRC_DUST])
+@pytest.mark.parametrize("octree", [False, True])
+def test_conservation_exact(source, octree):
+    if octree:
+        w = I.config_c3(root_n=8, max_refine=2, sigma=2.0, threshold=3.0)
+    else:
+        w = I.config_c2(n=12, n_freq=8)
+    cl = w.clouds[0]
+    G = _grid(cl)
+    f = len(w.dust.nu) - 2
+    kw = dict(kabs=w.dust.kabs[f] * cl.ell, ksca=w.dust.ksca[f] * cl.ell, g=0.5, seed=7, freq=f)
+    if source == oracle.SRC_POINT:
+        pos = np.array([[cl.nx / 2 + 0.3, cl.ny / 3, cl.nz * 0.7]])
+        kw.update(ps_pos=pos, ps_cdf=np.float32([1.0]))
+    n = 3000
+    if source == oracle.SRC_DUST:
+        leaf = cl.leaves()
+        rng = np.random.default_rng(3)
+        dw = rng.integers(0, 2 ** 32, leaf.size).astype(np.uint64)
+        dw[::7] = 0
+        kw.update(leaf=leaf, dust_w=dw, n_per_cell=2)
+        n = 2 * leaf.size
+    tally, st, steps = oracle.trace(G, source=source, n_packages=n, want_steps=True, **kw)
+    assert int(tally.sum()) + st["escaped"] == st["emitted"]
+    assert st["steps"] == int(steps.sum()) and st["capped"] == 0
+    assert np.all(tally >= 0)
+    if source == oracle.SRC_DUST:
+        assert st["emitted"] == 2 * int(dw.sum())
+        assert np.all(steps[0::2][dw == 0] == 0)
+
+
+def test_step_cap_ends_packages_and_conserves():
+    cl = I.regular(np.ones((8, 8, 8), np.float32))
+    tally, st, steps = oracle.trace(_grid(cl), source=oracle.SRC_BACKGROUND, kabs=0.01, ksca=3.0,
+                                    n_packages=500, max_steps=5, want_steps=True)
+    assert st["capped"] > 0 and steps.max() == 5
+    assert int(tally.sum()) + st["escaped"] == st["emitted"]
+
+
+def test_same_seed_same_result_other_seed_differs():
+    cl = I.regular(np.ones((8, 8, 8), np.float32))
+    G = _grid(cl)
+    a = oracle.trace(G, source=0, kabs=0.1, ksca=0.2, g=0.3, seed=5, n_packages=2000)[0]
+    b = oracle.trace(G, source=0, kabs=0.1, ksca=0.2, g=0.3, seed=5, n_packages=2000)[0]
+    c = oracle.trace(G, source=0, kabs=0.1, ksca=0.2, g=0.3, seed=6, n_packages=2000)[0]
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    # packages are independent: two halves add up to the whole
+    h1 = oracle.trace(G, source=0, kabs=0.1, ksca=0.2, g=0.3, seed=5, n_packages=1000)[0]
+    h2 = oracle.trace(G, source=0, kabs=0.1, ksca=0.2, g=0.3, seed=5, pid_lo=1000, n_packages=1000)[0]
+    assert np.array_equal(h1 + h2, a)
+
+
+# ----------------------------------------------------------------------------
+# radiation-field normalisation
+# ----------------------------------------------------------------------------
+def test_background_thin_cube_absorbs_4pi_kappa_I():
+    """Inside an optically thin box in an isotropic field I, every cell absorbs
+    4 pi kabs I per unit rho V (J = I).  Pins the cosine-weighted entry, the
+    face choice and the energy per package (pi I S / N)."""
+    n, ell, kabs, I_nu = 8, 2.0, 1e-4, 3.0
+    cl = I.regular(np.ones((n, n, n), np.float32), ell=ell)
+    N = 200_000
+    tally, st, _ = oracle.trace(_grid(cl), source=0, kabs=kabs * ell, ksca=0.0, seed=11, n_packages=N)
+    e = P.background_package_energy([I_nu], n, n, n, ell, N)
+    A = P.absorbed_power(tally[None, :], e, [1.0], cl.rho, cl.volumes())
+    ratio = A / (4 * np.pi * kabs * I_nu)
+    assert abs(ratio.mean() - 1) < 4e-3
+    assert np.all(np.abs(ratio - 1) < 0.12)
+    # mean chord of cosine-weighted entry is 4V/S (Cauchy): steps ~ N * n * 2/3 * ...
+    assert abs(st["emitted"] - N * oracle.W_UNIT) == 0
+
+
+def test_point_source_inverse_square():
+    """Optically thin cube with a central point source: absorbed power per
+    cell = kabs rho L <1/(4 pi r^2)>_cell, i.e. J = L / (16 pi^2 r^2)."""
+    n, kabs, L = 24, 1e-4, 5.0
+    cl = I.regular(np.ones((n, n, n), np.float32))
+    N = 400_000
+    c = n / 2
+    tally, st, _ = oracle.trace(_grid(cl), source=1, kabs=kabs, ksca=0.0, seed=3, n_packages=N,
+                                ps_pos=np.array([[c, c, c]]), ps_cdf=np.float32([1.0]))
+    absorbed = tally * (L / N / oracle.W_UNIT)
+    # exact cell average of 1/(4 pi r^2) by a 6^3 midpoint rule
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    sub = (np.arange(6) + 0.5) / 6
+    inv = np.zeros((n, n, n))
+    for a in sub:
+        for b in sub:
+            for cc in sub:
+                r2 = (i + a - c) ** 2 + (j + b - c) ** 2 + (k + cc - c) ** 2
+                inv += 1.0 / (4 * np.pi * r2)
+    inv /= 216
+    expect = (kabs * L * inv).ravel()
+    r = np.sqrt((i + 0.5 - c) ** 2 + (j + 0.5 - c) ** 2 + (k + 0.5 - c) ** 2).ravel()
+    far = r >= 4
+    ratio = absorbed[far].sum() / expect[far].sum()
+    assert abs(ratio - 1) < 5e-3
+    # slope of the shell averages in log J vs log r is -2
+    bins = np.arange(4, 11)
+    mids, vals = [], []
+    for lo, hi in zip(bins[:-1], bins[1:]):
+        m = (r >= lo) & (r < hi)
+        mids.append(np.mean(r[m]))
+        vals.append(absorbed[m].mean())
+    slope = np.polyfit(np.log(mids), np.log(vals), 1)[0]
+    assert abs(slope + 2) < 0.05
+
+
+def _cube_transmission_quadrature(tau_side, n=96):
+    """Escape probability of cosine-weighted rays entering a unit cube through
+    one face with absorption coefficient tau_side (deterministic midpoint
+    quadrature over entry point (x, y), mu^2 and azimuth)."""
+    g = (np.arange(n) + 0.5) / n
+    x, y = np.meshgrid(g, g, indexing="ij")
+    tot = 0.0
+    for m2 in g:
+        mu = math.sqrt(m2)
+        st = math.sqrt(1 - m2)
+        for ph in 2 * np.pi * g:
+            dx, dy = st * math.cos(ph), st * math.sin(ph)
+            tz = 1.0 / mu
+            tx = np.where(dx > 0, (1 - x) / dx, np.where(dx < 0, -x / dx, np.inf)) if dx != 0 else np.inf
+            ty = np.where(dy > 0, (1 - y) / dy, np.where(dy < 0, -y / dy, np.inf)) if dy != 0 else np.inf
+            Lp = np.minimum(np.minimum(tx, ty), tz)
+            tot += np.exp(-tau_side * Lp).mean()
+    return tot / (n * n)
+
+
+@pytest.mark.parametrize("layout", ["1cube", "2cube", "2cube_refined"])
+def test_brute_force_escape_probability_small_grids(layout):
+    """Albedo 0: the escaped fraction of background packages equals the
+    quadrature of exp(-tau(path)) over cosine-weighted entry (same for every
+    face by symmetry)."""
+    tau_side = 1.3
+    if layout == "1cube":
+        cl = I.regular(np.ones((1, 1, 1), np.float32)); k = tau_side
+    else:
+        cl = I.regular(np.ones((2, 2, 2), np.float32)); k = tau_side / 2
+        if layout == "2cube_refined":
+            cl = I.refine_cells(cl, [0, 3, 6])
+            cl = I.refine_cells(cl, [cl.level_start[1] + 1, cl.level_start[1] + 9])
+    N = 400_000
+    tally, st, _ = oracle.trace(_grid(cl), source=0, kabs=k, ksca=0.0, seed=21, n_packages=N)
+    p_mc = st["escaped"] / (N * oracle.W_UNIT)
+    p_q = _cube_transmission_quadrature(tau_side)
+    assert abs(p_mc - p_q) < 2.5e-3, (p_mc, p_q)
+
+
+def test_octree_refinement_does_not_change_root_absorption():
+    """A uniform cloud refined arbitrarily is the same medium: with the same
+    random numbers the absorption summed per root cell matches the unrefined
+    run up to rounding-level path differences."""
+    n = 6
+    base = I.regular(np.ones((n, n, n), np.float32) * 2.0)
+    rng = np.random.default_rng(4)
+    ref = I.refine_cells(base, rng.choice(base.n_cells, 60, replace=False))
+    lv2 = np.arange(ref.level_start[1], ref.level_start[2])
+    ref = I.refine_cells(ref, rng.choice(lv2, 100, replace=False))
+    kw = dict(source=0, kabs=0.08, ksca=0.15, g=0.4, seed=9, n_packages=30_000)
+    t0, s0, _ = oracle.trace(_grid(base), **kw)
+    t1, s1, _ = oracle.trace(_grid(ref), **kw)
+    # map every cell to its root ancestor
+    owner = np.arange(ref.n_cells)
+    par_of_cell = np.full(ref.n_cells, -1)
+    for k, p in enumerate(ref.parent):
+        par_of_cell[ref.n_root + 8 * k: ref.n_root + 8 * k + 8] = p
+    for _ in range(ref.n_levels):
+        owner = np.where(owner >= ref.n_root, par_of_cell[owner], owner)
+    per_root = np.bincount(owner, weights=t1.astype(np.float64), minlength=ref.n_root)
+    rel = np.abs(per_root - t0.astype(np.float64)) / t0.sum()
+    assert rel.max() < 2e-3
+    assert abs(s1["escaped"] - s0["escaped"]) / s0["emitted"] < 2e-3
+    assert s1["steps"] > s0["steps"]
+
+
+# ----------------------------------------------------------------------------
+# scattering
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("g", [0.0, 0.5, -0.3, 0.9])
+def test_hg_moments(g):
+    n = 200_000
+    d0 = np.array([0.3, -0.4, np.sqrt(1 - 0.25)], np.float32)
+    cosv, dout = oracle.hg_samples(g, d0, 123, n)
+    se = 1.0 / math.sqrt(n)
+    assert abs(cosv.mean() - g) < 4 * se
+    assert abs((cosv.astype(np.float64) ** 2).mean() - (1 + 2 * g * g) / 3) < 4 * se
+    np.testing.assert_allclose(np.linalg.norm(dout.astype(np.float64), axis=1), 1.0, atol=3e-7)
+    # azimuthal symmetry about d0: the perpendicular part averages to zero
+    perp = dout - cosv[:, None] * d0[None, :]
+    assert np.abs(perp.mean(axis=0)).max() < 4 * se
+
+
+def test_hg_along_z_branch():
+    d0 = np.array([0.0, 0.0, -1.0], np.float32)
+    cosv, _ = oracle.hg_samples(0.6, d0, 5, 100_000)
+    assert abs(cosv.mean() - 0.6) < 4 / math.sqrt(100_000)
+
+
+# ----------------------------------------------------------------------------
+# noise law (paper Sect. 3.1: noise ~ N^-1/2)
+# ----------------------------------------------------------------------------
+def test_noise_scales_as_inverse_sqrt_n():
+    cl = I.regular(np.ones((6, 6, 6), np.float32))
+    G = _grid(cl)
+
+    def rms(N):
+        a = oracle.trace(G, source=0, kabs=0.1, ksca=0.1, seed=100, n_packages=N)[0] / N
+        b = oracle.trace(G, source=0, kabs=0.1, ksca=0.1, seed=200, n_packages=N)[0] / N
+        return np.sqrt(np.mean((a - b) ** 2))
+
+    r = rms(4000) / rms(64000)
+    assert 3.3 < r < 4.8       # sqrt(16) = 4
+
+
+# ----------------------------------------------------------------------------
+# FP64 physics
+# ----------------------------------------------------------------------------
+def test_planck_integrates_to_stefan_boltzmann():
+    sigma = 5.670374419e-5          # CODATA 2018
+    for T in (10.0, 300.0, 6000.0):
+        nu = np.geomspace(1e8, 1e17, 200_001)
+        I_ = np.sum(P.trapezoid_weights(nu) * P.planck_nu(nu, T))
+        assert abs(I_ / (sigma * T ** 4 / np.pi) - 1) < 1e-6
+
+
+def test_planck_derivative():
+    nu = np.geomspace(1e11, 1e15, 50)
+    for T in (5.0, 50.0, 900.0):
+        h = T * 1e-6
+        fd = (P.planck_nu(nu, T + h) - P.planck_nu(nu, T - h)) / (2 * h)
+        ok = P.H_PLANCK * nu / (P.K_BOLTZ * T) < 300.0
+        np.testing.assert_allclose(P.dplanck_dT(nu, T)[ok], fd[ok], rtol=1e-6)
+
+
+def test_trapezoid_weights_exact_for_linear():
+    nu = np.geomspace(3e11, 3e15, 64)
+    w = P.trapezoid_weights(nu)
+    assert abs(w.sum() / (nu[-1] - nu[0]) - 1) < 1e-14
+    assert abs(np.sum(w * nu) / (0.5 * (nu[-1] ** 2 - nu[0] ** 2)) - 1) < 1e-13
+
+
+@pytest.mark.parametrize("beta", [1.0, 2.0])
+@pytest.mark.parametrize("W", [1.0, 1e-3, 1e-8])
+def test_temperature_closed_form_diluted_blackbody(beta, W):
+    """Optically thin dust in a field W B(T*) with kappa ~ nu^beta is at
+    T = W^(1/(4+beta)) T* (infinite frequency range)."""
+    Tstar = 200.0
+    nu = np.geomspace(1e9, 1e16, 6000)
+    kabs = (nu / 1e12) ** beta
+    A = 4 * np.pi * np.sum(P.trapezoid_weights(nu) * kabs * W * P.planck_nu(nu, Tstar))
+    T = P.temperature(A, nu, kabs)
+    assert abs(T / (W ** (1 / (4 + beta)) * Tstar) - 1) < 1e-4
+
+
+def test_temperature_blackbody_field_on_coarse_grid_and_limits():
+    nu = I.frequency_grid(64)
+    kabs = (nu / 1e14) ** 2
+    for Tstar in (15.0, 120.0, 1500.0):
+        A = P.emission_integral(Tstar, nu, kabs)      # W = 1: T = T* for any quadrature
+        assert abs(P.temperature(A, nu, kabs) / Tstar - 1) < 1e-10
+    assert P.temperature(0.0, nu, kabs) == P.T_MIN
+    assert P.temperature(1e300, nu, kabs) == P.T_MAX
+
+
+def test_thin_cube_mc_temperature_matches_closed_form():
+    """End to end in FP64 after the FP32 tracer: a thin cube in W B(T*) reaches
+    the temperature of the same quadrature's equilibrium."""
+    nu = I.frequency_grid(16)
+    kabs = 1e-6 * (nu / 1e14) ** 2
+    W, Tstar = 1e-6, 3000.0
+    I_nu = W * P.planck_nu(nu, Tstar)
+    n, ell, N = 6, 1.0, 60_000
+    cl = I.regular(np.ones((n, n, n), np.float32), ell=ell)
+    G = _grid(cl)
+    tal = np.zeros((len(nu), cl.n_cells), np.int64)
+    for f in range(len(nu)):
+        tal[f] = oracle.trace(G, source=0, kabs=kabs[f] * ell, ksca=0.0, seed=1, freq=f,
+                              n_packages=N)[0]
+    e = P.background_package_energy(I_nu, n, n, n, ell, N)
+    A = P.absorbed_power(tal, e, nu, cl.rho, cl.volumes())
+    T = P.temperatures(A, nu, kabs)
+    A_exact = 4 * np.pi * np.sum(P.trapezoid_weights(nu) * kabs * I_nu)
+    T_exact = P.temperature(A_exact, nu, kabs)
+    assert abs(T.mean() / T_exact - 1) < 2e-3
+    assert np.all(np.abs(T / T_exact - 1) < 0.02)
+
+
+def test_dust_weights():
+    L = np.array([0.0, 1.0, 2.5, 5.0, 5.0 * (1 - 2 ** -40)])
+    W, e = P.dust_weights(L, 3)
+    assert W[3] == 2 ** 32 and W[0] == 0 and W[1] == round(2 ** 32 / 5)
+    assert W[4] == 2 ** 32
+    assert abs(e * 2 ** 32 * 3 - 5.0) < 1e-12
