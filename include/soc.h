@@ -1,0 +1,274 @@
+/*
+ * soc.h -- C-ABI of libsoc, a GB300 (sm_103a) implementation of the Monte Carlo
+ * photon-package transport and equilibrium dust-temperature update of SOC
+ * (M. Juvela, "SOC program for dust continuum radiative transfer",
+ * A&A 2019, arXiv:1812.06632).
+ *
+ * Conventions
+ *  - Every function returns soc_status (SOC_OK == 0, errors < 0) and never
+ *    throws.  soc_last_error() gives a message for the last failing call on
+ *    a context.
+ *  - "host" pointers are read during the call only; the caller keeps
+ *    ownership.  "device" pointers are caller-owned device memory on the
+ *    context's device (e.g. torch tensors); the library never frees them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls taking a stream are asynchronous on it unless stated.
+ *  - Fixed point: one photon package starts with SOC_W_UNIT = 2^32 weight
+ *    units; absorption counters ("tallies") are int64 sums of weight units.
+ *  - Lengths: the kernels work in root-cell units; physical sizes (cm)
+ *    enter only through the root-cell side of each grid.
+ *  - A context is not thread-safe; use one per host thread.
+ */
+#ifndef SOC_H
+#define SOC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int soc_status;
+#define SOC_OK              0
+#define SOC_ERR_ARG        -1   /* bad argument (null pointer, size, index)          */
+#define SOC_ERR_GRID       -2   /* malformed grid (link out of range, NaN, rho < 0)  */
+#define SOC_ERR_CUDA       -3   /* a CUDA runtime call failed                        */
+#define SOC_ERR_STEP_LIMIT -4   /* packages were ended by the step cap               */
+#define SOC_ERR_STATE      -5   /* call order: e.g. simulation before soc_dust_upload */
+#define SOC_ERR_NOMEM      -6   /* device allocation failed                          */
+
+#define SOC_SRC_BACKGROUND 0
+#define SOC_SRC_POINT      1
+#define SOC_SRC_DUST       2
+
+#define SOC_W_UNIT   4294967296ull      /* 2^32 */
+#define SOC_MAX_LEVELS 16
+
+typedef struct soc_ctx soc_ctx;
+
+/* Create a context on CUDA device `device` with the Monte Carlo seed `seed`
+ * (the Philox key of every package stream).  *out receives the context. */
+soc_status soc_create(soc_ctx **out, int device, uint64_t seed);
+/* Free every device buffer the context owns.  NULL is accepted. */
+void soc_destroy(soc_ctx *ctx);
+/* Message of the last failing call on ctx (never NULL). */
+const char *soc_last_error(const soc_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * soc_grid_upload -- hierarchical density grid (paper Sect. 2.1.1).
+ * The root grid is nx*ny*nz cubic cells (x fastest: c = i + nx*(j + ny*k)).
+ * Octree refinement splits a cell into an octet of 8 equal cells.  The cell
+ * vector is level ordered: root cells, then every cell of level 2, then of
+ * level 3, ...; each octet is contiguous, its cells ordered by octant
+ * ox + 2*oy + 4*oz, so cell c >= n_root belongs to octet (c - n_root)/8.
+ *   rho[n_cells]      host, FP32: density of every leaf (>= 0, finite).  With
+ *                     first_child == NULL, refined cells carry the paper's
+ *                     encoding: minus the index of their first child (exact
+ *                     only below 2^24 cells).
+ *   first_child       host [n_cells] int32 or NULL: first child index of a
+ *                     refined cell, -1 for a leaf (overrides rho's encoding).
+ *   parent            host [(n_cells - n_root)/8] int32 or NULL: parent cell of
+ *                     each octet (reverse links); derived when NULL, checked
+ *                     when given.
+ *   cells_per_level   host [n_levels].
+ *   root_cell_size    root-cell side in cm (> 0).
+ * The grid is validated on the host (SOC_ERR_GRID on any inconsistency),
+ * converted to tagged 32-bit cell words (bit 31 set: first-child index in
+ * bits 0..30; else the FP32 density) and copied to the device.  Returns the
+ * new cloud id in *cloud_id (0, 1, 2, ... in call order).  Synchronous.
+ * ------------------------------------------------------------------------ */
+typedef struct soc_grid_desc {
+    int32_t nx, ny, nz;
+    int32_t n_levels;
+    const int64_t *cells_per_level;
+    const float *rho;
+    const int32_t *first_child;
+    const int32_t *parent;
+    double root_cell_size;
+} soc_grid_desc;
+
+soc_status soc_grid_upload(soc_ctx *ctx, const soc_grid_desc *desc, int *cloud_id);
+
+/* ------------------------------------------------------------------------
+ * soc_dust_upload -- dust properties on the fixed frequency grid (paper
+ * Sect. 2.1.1: cross sections for absorption and scattering and the
+ * scattering function against frequency; Sect. 2.2: fixed frequency grid).
+ *   nu[n_freq]        host, Hz, strictly increasing.
+ *   kabs, ksca        host [n_freq]: cross sections per density unit (cm^2):
+ *                     rho*kappa is an inverse length in 1/cm.
+ *   g                 host [n_freq]: Henyey-Greenstein asymmetry, |g| < 1.
+ * Also builds the FP64 emission table E(T) = 4 pi sum_nu w_nu kabs B_nu(T)
+ * on 4096 log-spaced T in [2.7, 3000] K (w_nu = trapezoid weights).  Must be
+ * called once, before any simulation.  Synchronous.
+ * ------------------------------------------------------------------------ */
+soc_status soc_dust_upload(soc_ctx *ctx, int n_freq, const double *nu, const double *kabs,
+                           const double *ksca, const double *g);
+
+/* ------------------------------------------------------------------------
+ * soc_sources_upload -- radiation sources of one cloud (paper Sect. 2.2:
+ * isotropic external background and blackbody point sources).
+ *   bg_I_nu           host [n_freq] or NULL: background intensity
+ *                     (erg/s/cm^2/Hz/sr) outside the box.
+ *   n_ps              number of point sources (0 allowed).
+ *   ps_pos            host [3*n_ps]: positions in root-cell units, strictly
+ *                     inside the root grid.
+ *   ps_L_nu           host [n_ps*n_freq] (source-major): luminosity erg/s/Hz.
+ * A point-source package picks its source with probability proportional to
+ * L_nu, so all packages of a frequency carry the same energy.  Synchronous.
+ * ------------------------------------------------------------------------ */
+soc_status soc_sources_upload(soc_ctx *ctx, int cloud_id, const double *bg_I_nu, int n_ps,
+                              const double *ps_pos, const double *ps_L_nu);
+
+/* ------------------------------------------------------------------------
+ * soc_simulate_frequency_batch -- trace photon packages (paper Sect. 2.1.1:
+ * package creation, cell-to-cell stepping with partial traversal of the
+ * hierarchy, absorption counters per cell and frequency).  Every item is one
+ * (cloud, frequency, source class) with its own package-id range; all items
+ * run in ONE persistent kernel launch.
+ *   items[n_items]    host array (copied during the call):
+ *     cloud, freq     indices of an uploaded grid and of the frequency grid;
+ *     source          SOC_SRC_BACKGROUND / SOC_SRC_POINT / SOC_SRC_DUST;
+ *     iteration       RNG stream selector (key word 1 gets iteration << 16);
+ *     pid_offset      first package id (packages pid_offset .. +n_packages-1);
+ *     n_packages      number of packages (< 2^32 - pid_offset);
+ *     w0              initial weight of background / point packages (1..2^32);
+ *     tally_offset    element offset in d_tally of this item's cell 0: the
+ *                     item adds its deposits to d_tally[tally_offset + cell];
+ *     d_dust_w        device [n_leaf] uint64: initial weight of the packages
+ *                     of each leaf (leaves in cell order), SOC_SRC_DUST only;
+ *     n_per_cell      dust packages per leaf (n_packages = n_leaf*n_per_cell).
+ *   d_tally           device int64, accumulated into (caller zeroes it).
+ *   d_stats           device int64 [n_items][4], accumulated into:
+ *                     {escaped weight, capped packages, photon-cell steps,
+ *                      emitted weight}.  Energy is conserved exactly:
+ *                     sum(tally of the item) + escaped == emitted.
+ *   d_pkg_steps       device uint32 [sum of n_packages] or NULL: steps of each
+ *                     package, in item order then package order.
+ * Deterministic: results depend only on inputs and the seed, not on launch
+ * shape.  Asynchronous on `stream`.
+ * ------------------------------------------------------------------------ */
+typedef struct soc_batch_item {
+    int32_t cloud;
+    int32_t freq;
+    int32_t source;
+    int32_t iteration;
+    uint64_t pid_offset;
+    uint64_t n_packages;
+    uint64_t w0;
+    int64_t tally_offset;
+    const uint64_t *d_dust_w;
+    uint32_t n_per_cell;
+    uint32_t reserved;
+} soc_batch_item;
+
+soc_status soc_simulate_frequency_batch(soc_ctx *ctx, const soc_batch_item *items, int n_items,
+                                        int64_t *d_tally, int64_t *d_stats,
+                                        uint32_t *d_pkg_steps, void *stream);
+
+/* Per-package energy of background / point-source packages (paper Sect. 2.2
+ * sources): the energy in erg/s/Hz carried by one weight unit when
+ * n_packages packages of weight 2^32 are launched at every frequency.
+ *   background: pi I_nu S / n_packages / 2^32 (S = box surface, cm^2);
+ *   point:      sum_k L_nu,k / n_packages / 2^32.
+ * e_unit: host [n_freq].  Synchronous (host only). */
+soc_status soc_package_energy(soc_ctx *ctx, int cloud_id, int source, uint64_t n_packages,
+                              double *e_unit);
+
+/* ------------------------------------------------------------------------
+ * soc_dust_emission -- weights of dust re-emission packages (paper Sect. 3.2:
+ * the same number of packages from every cell, random position and direction
+ * inside the cell).  For every leaf c and frequency index f in
+ * [freq_lo, freq_lo + n_freq):
+ *   L_c = 4 pi rho_c V_c kabs(nu) B_nu(T_c)   (FP64),
+ *   d_w[(f - freq_lo)*n_leaf + leaf(c)] = rint(2^32 L_c / max_c L_c),
+ *   d_e_unit[f - freq_lo] = max_c L_c / n_per_cell / 2^32.
+ *   d_T               device float [n_cells] (leaf temperatures; parents ignored).
+ *   d_w               device uint64 [n_freq][n_leaf].
+ *   d_e_unit          device double [n_freq].
+ * Asynchronous on `stream`.
+ * ------------------------------------------------------------------------ */
+soc_status soc_dust_emission(soc_ctx *ctx, int cloud_id, const float *d_T, int freq_lo, int n_freq,
+                             uint32_t n_per_cell, uint64_t *d_w, double *d_e_unit, void *stream);
+
+/* ------------------------------------------------------------------------
+ * soc_absorbed_power -- frequency integral of the absorption counters (paper
+ * Sect. 2.1.1: for equilibrium dust the integral of absorbed energy over
+ * frequency is gathered on the device):
+ *   d_A_out[c] = d_A_in[c] + sum_f w_f e_unit_f d_tally[f*tally_stride + c] / (rho_c V_c)
+ * for every leaf with rho > 0 (others: d_A_in[c], or 0), in FP64, summed in
+ * frequency order.  w_f = trapezoid weights of the uploaded frequency grid.
+ *   d_tally           device int64 [n_freq][tally_stride] (cell 0 at offset 0).
+ *   d_e_unit          device double [n_freq].
+ *   d_A_in            device double [n_cells] or NULL; may equal d_A_out.
+ *   d_A_out           device double [n_cells].
+ * Asynchronous on `stream`.
+ * ------------------------------------------------------------------------ */
+soc_status soc_absorbed_power(soc_ctx *ctx, int cloud_id, const int64_t *d_tally, int64_t tally_stride,
+                              const double *d_e_unit, const double *d_A_in, double *d_A_out,
+                              void *stream);
+
+/* ------------------------------------------------------------------------
+ * soc_update_temperature -- equilibrium dust temperature (paper Sect. 2.1.1:
+ * a separate kernel solves the temperatures from the absorbed energy).  For
+ * every leaf: T solves 4 pi sum_nu w_nu kabs B_nu(T) = A (FP64 table
+ * inversion with log-log interpolation, then one Newton step on the
+ * quadrature).  A <= E(2.7 K) gives 2.7 K (cells that absorbed nothing);
+ * A >= E(3000 K) gives 3000 K.
+ *   d_A               device double [n_cells].
+ *   d_T               device float [n_cells], in/out: holds T_prev on entry.
+ *   d_max_dT          device double [1] or NULL: receives max |T - T_prev|
+ *                     over leaves (overwritten, not accumulated).
+ * Asynchronous on `stream`.
+ * ------------------------------------------------------------------------ */
+soc_status soc_update_temperature(soc_ctx *ctx, int cloud_id, const double *d_A, float *d_T,
+                                  double *d_max_dT, void *stream);
+
+/* ------------------------------------------------------------------------
+ * soc_iterate -- the iteration of paper Sect. 2.1.2 / 3.3: iteration 0
+ * simulates the constant sources (background, point sources) once and keeps
+ * their absorbed power; iterations k >= 1 re-simulate only dust re-emission
+ * from T_{k-1} (with the same random numbers every iteration), add the
+ * constant part and update T, until max |T_k - T_{k-1}| < dT_tol or
+ * max_iter iterations.  Synchronises once per iteration (reads max |dT|).
+ *   d_T_seed          device float [n_cells] or NULL: initial temperatures
+ *                     (e.g. a learned prediction); NULL uses T from the
+ *                     constant sources alone.
+ *   d_T_out           device float [n_cells]: final temperatures.
+ *   res               host, out (may be NULL).
+ *   dT_history        host double [max_iter] or NULL: max |dT| per iteration.
+ * ------------------------------------------------------------------------ */
+typedef struct soc_iterate_params {
+    uint64_t n_background;     /* background packages per frequency (0: none)  */
+    uint64_t n_point;          /* point-source packages per frequency (0: none) */
+    uint32_t n_per_cell;       /* dust packages per leaf and frequency          */
+    int32_t max_iter;          /* dust iterations after iteration 0 (>= 0)      */
+    double dT_tol;             /* stop when max |dT| < dT_tol (K)               */
+} soc_iterate_params;
+
+typedef struct soc_iterate_result {
+    int32_t iterations;        /* dust iterations done                          */
+    int32_t converged;         /* 1 if max |dT| < dT_tol was reached            */
+    double final_max_dT;
+    int64_t steps;             /* photon-cell steps over all iterations          */
+    int64_t capped;            /* packages ended by the step cap                */
+} soc_iterate_result;
+
+soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *params,
+                       const float *d_T_seed, float *d_T_out, soc_iterate_result *res,
+                       double *dT_history, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Launch configuration of the tracer (autotuner hook).  threads_per_block in
+ * {32, 64, ..., 1024}; blocks_per_sm >= 1 (0 = occupancy maximum); chunk =
+ * packages a warp takes per lane from the global work counter (>= 1).
+ * Results do not depend on these settings.
+ * ------------------------------------------------------------------------ */
+soc_status soc_set_launch(soc_ctx *ctx, int threads_per_block, int blocks_per_sm, int chunk);
+/* Step cap per package (default 10^7); packages beyond it are ended with
+ * their weight deposited and counted in stats[1]. */
+soc_status soc_set_max_steps(soc_ctx *ctx, uint32_t max_steps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SOC_H */

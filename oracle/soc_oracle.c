@@ -242,15 +242,16 @@ static void descend(const oracle_grid *G, pkg_t *p)
     }
 }
 
-/* Unit-disk rejection sample -> (cos phi, sin phi), no trigonometry. */
+/* Unit-disk rejection sample -> (cos phi, sin phi), no trigonometry.  At
+ * most 64 tries (all rejected with probability < 1e-42); then azimuth 0. */
 static void disk_azimuth(rng_t *r, float *c, float *s)
 {
-    float a, b, r2;
-    for (;;) {
-        a = 2.0f * rng_u(r) - 1.0f;
-        b = 2.0f * rng_u(r) - 1.0f;
-        r2 = a * a + b * b;
-        if (r2 <= 1.0f && r2 > 0.0f) break;
+    float a = 1.0f, b = 0.0f, r2 = 1.0f;
+    for (int tries = 0; tries < 64; ++tries) {
+        float ta = 2.0f * rng_u(r) - 1.0f;
+        float tb = 2.0f * rng_u(r) - 1.0f;
+        float t2 = ta * ta + tb * tb;
+        if (t2 <= 1.0f && t2 > 0.0f) { a = ta; b = tb; r2 = t2; break; }
     }
     float rr = sqrtf(r2);
     *c = a / rr;
@@ -453,6 +454,10 @@ static uint32_t propagate(const oracle_grid *G, const oracle_item *it, rng_t *r,
                 float si = (face - p.x[i]) * p.inv[i];
                 if (si < s) { s = si; axis = i; }
             }
+        }
+        if (axis < 0) {                        /* no finite exit face: end here */
+            pend += p.W; p.W = 0; st->capped++;
+            break;
         }
         const float ksh = (rho * it->ksca) * p.h;
         const float dtau = ksh * s;

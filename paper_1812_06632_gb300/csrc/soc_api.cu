@@ -1,0 +1,670 @@
+// soc_api.cu -- host side of libsoc: context, validated uploads, batch
+// preparation and the iteration driver (the C-ABI of include/soc.h).
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+#include "soc_internal.h"
+
+using namespace soc;
+
+namespace {
+
+constexpr double kPi = 3.141592653589793;
+constexpr double kHc = 6.62607015e-27, kKc = 1.380649e-16, kCc = 2.99792458e10;
+
+template <class T>
+struct DevBuf {                     // owning device buffer
+    T *p = nullptr;
+    size_t n = 0;
+    cudaError_t alloc(size_t count)
+    {
+        if (count <= n && p) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+        if (e != cudaSuccess) { p = nullptr; n = 0; return e; }
+        n = count;
+        return cudaSuccess;
+    }
+    void release() { if (p) cudaFree(p); p = nullptr; n = 0; }
+};
+
+struct CloudHost {
+    int nx = 0, ny = 0, nz = 0, n_levels = 0;
+    int64_t n_cells = 0, n_root = 0, n_leaf = 0;
+    std::vector<int64_t> level_start;
+    double ell = 1.0;
+    DevBuf<uint32_t> cell;
+    DevBuf<int32_t> parent, leaf;
+    DevBuf<float> rho;
+    DevBuf<double> volume;
+    DevBuf<float2> kappa;
+    DevBuf<float> ps_pos, ps_cdf;
+    int n_ps = 0;
+    std::vector<double> bg_I;                  // [n_freq] or empty
+    std::vector<double> ps_L_total;            // [n_freq]
+    // iteration scratch (library owned)
+    DevBuf<int64_t> tally;
+    DevBuf<double> A_const, A;
+    DevBuf<uint64_t> dust_w;
+    DevBuf<double> e_unit;
+    DevBuf<int64_t> stats;
+};
+
+}  // namespace
+
+struct soc_ctx {
+    int device = 0;
+    uint64_t seed = 1;
+    std::string err = "no error";
+    std::vector<CloudHost *> clouds;
+    DevBuf<DevCloud> d_clouds;
+    bool clouds_dirty = true;
+    // dust
+    int n_freq = 0;
+    std::vector<double> nu, kabs, ksca, g, w;
+    DevBuf<float> d_g;
+    DevBuf<double> d_w, d_w_kabs, d_nu, d_kabs, d_lnE, d_lnT;
+    // batch scratch
+    DevBuf<DevItem> d_items;
+    DevBuf<uint64_t> d_prefix;
+    DevBuf<unsigned long long> d_counter;
+    DevBuf<unsigned long long> d_lmax;
+    DevBuf<double> d_maxdT;
+    // launch
+    int tpb = 256, bps = 0, chunk = 1;
+    uint32_t max_steps = 10000000u;
+    int sms = 0;
+};
+
+namespace {
+
+soc_status fail(soc_ctx *c, soc_status code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+soc_status cuda_fail(soc_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, e == cudaErrorMemoryAllocation ? SOC_ERR_NOMEM : SOC_ERR_CUDA, "%s: %s", where,
+                cudaGetErrorString(e));
+}
+
+#define CK(expr, where)                                          \
+    do {                                                         \
+        cudaError_t e_ = (expr);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+    } while (0)
+
+double planck_host(double nu, double T)
+{
+    const double x = kHc * nu / (kKc * T);
+    return (2.0 * kHc * nu * nu * nu / (kCc * kCc)) / std::expm1(x);
+}
+
+std::vector<double> trapezoid(const std::vector<double> &nu)
+{
+    std::vector<double> w(nu.size(), 0.0);
+    if (nu.size() == 1) { w[0] = 1.0; return w; }
+    for (size_t i = 0; i + 1 < nu.size(); ++i) {
+        const double d = 0.5 * (nu[i + 1] - nu[i]);
+        w[i] += d;
+        w[i + 1] += d;
+    }
+    return w;
+}
+
+// Per-cloud kappa table (kabs * ell, ksca * ell as FP32) and per-frequency
+// point-source CDF need both the grid and the dust.
+soc_status build_cloud_tables(soc_ctx *ctx, CloudHost &cl)
+{
+    if (ctx->n_freq == 0) return SOC_OK;
+    std::vector<float2> k(ctx->n_freq);
+    for (int f = 0; f < ctx->n_freq; ++f)
+        k[f] = make_float2((float)(ctx->kabs[f] * cl.ell), (float)(ctx->ksca[f] * cl.ell));
+    CK(cl.kappa.alloc(ctx->n_freq), "alloc kappa");
+    CK(cudaMemcpy(cl.kappa.p, k.data(), sizeof(float2) * ctx->n_freq, cudaMemcpyHostToDevice), "copy kappa");
+    ctx->clouds_dirty = true;
+    return SOC_OK;
+}
+
+soc_status sync_clouds(soc_ctx *ctx)
+{
+    if (!ctx->clouds_dirty) return SOC_OK;
+    std::vector<DevCloud> v(ctx->clouds.size());
+    for (size_t i = 0; i < ctx->clouds.size(); ++i) {
+        const CloudHost &c = *ctx->clouds[i];
+        DevCloud &d = v[i];
+        memset(&d, 0, sizeof d);
+        d.cell = c.cell.p; d.parent = c.parent.p; d.leaf = c.leaf.p; d.rho = c.rho.p;
+        d.volume = c.volume.p; d.kappa = c.kappa.p; d.ps_pos = c.ps_pos.p; d.ps_cdf = c.ps_cdf.p;
+        d.nx = c.nx; d.ny = c.ny; d.nz = c.nz; d.n_levels = c.n_levels; d.n_ps = c.n_ps;
+        d.n_cells = c.n_cells; d.n_root = c.n_root; d.n_leaf = c.n_leaf;
+        for (int L = 0; L <= c.n_levels; ++L) d.level_start[L] = c.level_start[L];
+        for (int L = c.n_levels + 1; L <= SOC_MAX_LEVELS; ++L) d.level_start[L] = c.n_cells;
+    }
+    CK(ctx->d_clouds.alloc(v.size()), "alloc cloud table");
+    CK(cudaMemcpy(ctx->d_clouds.p, v.data(), sizeof(DevCloud) * v.size(), cudaMemcpyHostToDevice),
+       "copy cloud table");
+    ctx->clouds_dirty = false;
+    return SOC_OK;
+}
+
+soc_status check_cloud(soc_ctx *ctx, int id)
+{
+    if (!ctx) return SOC_ERR_ARG;
+    if (id < 0 || id >= (int)ctx->clouds.size()) return fail(ctx, SOC_ERR_ARG, "cloud id %d out of range", id);
+    return SOC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+soc_status soc_create(soc_ctx **out, int device, uint64_t seed)
+{
+    if (!out) return SOC_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return SOC_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return SOC_ERR_CUDA;
+    soc_ctx *ctx = new (std::nothrow) soc_ctx();
+    if (!ctx) return SOC_ERR_NOMEM;
+    ctx->device = device;
+    ctx->seed = seed;
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+    if (ctx->d_counter.alloc(1) != cudaSuccess || ctx->d_maxdT.alloc(1) != cudaSuccess) {
+        delete ctx;
+        return SOC_ERR_NOMEM;
+    }
+    *out = ctx;
+    return SOC_OK;
+}
+
+void soc_destroy(soc_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    for (CloudHost *c : ctx->clouds) {
+        c->cell.release(); c->parent.release(); c->leaf.release(); c->rho.release();
+        c->volume.release(); c->kappa.release(); c->ps_pos.release(); c->ps_cdf.release();
+        c->tally.release(); c->A_const.release(); c->A.release(); c->dust_w.release();
+        c->e_unit.release(); c->stats.release();
+        delete c;
+    }
+    ctx->d_clouds.release(); ctx->d_g.release(); ctx->d_w.release(); ctx->d_w_kabs.release();
+    ctx->d_nu.release(); ctx->d_kabs.release(); ctx->d_lnE.release(); ctx->d_lnT.release();
+    ctx->d_items.release(); ctx->d_prefix.release(); ctx->d_counter.release(); ctx->d_lmax.release();
+    ctx->d_maxdT.release();
+    delete ctx;
+}
+
+const char *soc_last_error(const soc_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+soc_status soc_set_launch(soc_ctx *ctx, int threads_per_block, int blocks_per_sm, int chunk)
+{
+    if (!ctx) return SOC_ERR_ARG;
+    if (threads_per_block < 32 || threads_per_block > 256 || threads_per_block % 32)
+        return fail(ctx, SOC_ERR_ARG, "threads_per_block must be a multiple of 32 in [32, 256]");
+    if (blocks_per_sm < 0 || chunk < 1 || chunk > 1024) return fail(ctx, SOC_ERR_ARG, "bad blocks_per_sm/chunk");
+    ctx->tpb = threads_per_block;
+    ctx->bps = blocks_per_sm;
+    ctx->chunk = chunk;
+    return SOC_OK;
+}
+
+soc_status soc_set_max_steps(soc_ctx *ctx, uint32_t max_steps)
+{
+    if (!ctx || max_steps == 0) return SOC_ERR_ARG;
+    ctx->max_steps = max_steps;
+    return SOC_OK;
+}
+
+soc_status soc_grid_upload(soc_ctx *ctx, const soc_grid_desc *d, int *cloud_id)
+{
+    if (!ctx || !d || !cloud_id || !d->rho || !d->cells_per_level) return fail(ctx, SOC_ERR_ARG, "null argument");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(ctx, SOC_ERR_ARG, "root grid must be >= 1 cell per axis");
+    if (d->n_levels < 1 || d->n_levels > SOC_MAX_LEVELS) return fail(ctx, SOC_ERR_ARG, "n_levels out of [1, 16]");
+    if (!(d->root_cell_size > 0.0) || !std::isfinite(d->root_cell_size))
+        return fail(ctx, SOC_ERR_ARG, "root_cell_size must be positive");
+    const int64_t n_root = (int64_t)d->nx * d->ny * d->nz;
+    std::vector<int64_t> start(d->n_levels + 1, 0);
+    for (int L = 0; L < d->n_levels; ++L) {
+        const int64_t c = d->cells_per_level[L];
+        if (c < 0 || (L == 0 && c != n_root) || (L > 0 && c % 8 != 0))
+            return fail(ctx, SOC_ERR_GRID, "cells_per_level[%d] = %lld is inconsistent", L, (long long)c);
+        start[L + 1] = start[L] + c;
+    }
+    const int64_t n = start[d->n_levels];
+    if (n >= (int64_t)1 << 31) return fail(ctx, SOC_ERR_GRID, "more than 2^31 - 1 cells");
+    const int64_t n_oct = (n - n_root) / 8;
+    std::vector<int32_t> child(n, -1);
+    for (int64_t c = 0; c < n; ++c) {
+        if (d->first_child) {
+            child[c] = d->first_child[c] < 0 ? -1 : d->first_child[c];
+        } else if (d->rho[c] < 0.0f) {
+            const float v = -d->rho[c];
+            if (!(v < 16777216.0f) || v != std::floor(v))
+                return fail(ctx, SOC_ERR_GRID, "cell %lld: negative-density link %g not an exact index",
+                            (long long)c, (double)d->rho[c]);
+            child[c] = (int32_t)v;
+        }
+    }
+    std::vector<int32_t> parent(n_oct, -1);
+    int lv = 0;
+    for (int64_t c = 0; c < n; ++c) {
+        while (c >= start[lv + 1]) ++lv;
+        const int32_t fc = child[c];
+        if (fc < 0) {
+            const float r = d->rho[c];
+            if (!std::isfinite(r) || r < 0.0f)
+                return fail(ctx, SOC_ERR_GRID, "leaf %lld has invalid density %g", (long long)c, (double)r);
+            continue;
+        }
+        if (lv + 1 >= d->n_levels || fc < start[lv + 1] || fc + 8 > start[lv + 2] || (fc - n_root) % 8 != 0)
+            return fail(ctx, SOC_ERR_GRID, "cell %lld (level %d): child link %d out of range", (long long)c,
+                        lv + 1, fc);
+        const int64_t k = (fc - n_root) / 8;
+        if (parent[k] != -1) return fail(ctx, SOC_ERR_GRID, "octet %lld has two parents", (long long)k);
+        parent[k] = (int32_t)c;
+    }
+    for (int64_t k = 0; k < n_oct; ++k) {
+        if (parent[k] < 0) return fail(ctx, SOC_ERR_GRID, "octet %lld has no parent", (long long)k);
+        if (d->parent && d->parent[k] != parent[k])
+            return fail(ctx, SOC_ERR_GRID, "parent[%lld] = %d, links say %d", (long long)k, d->parent[k], parent[k]);
+    }
+    // device images
+    std::vector<uint32_t> word(n);
+    std::vector<float> rho(n);
+    std::vector<double> vol(n);
+    std::vector<int32_t> leaf;
+    leaf.reserve(n);
+    const double ell3 = (d->root_cell_size * d->root_cell_size) * d->root_cell_size;
+    lv = 0;
+    for (int64_t c = 0; c < n; ++c) {
+        while (c >= start[lv + 1]) ++lv;
+        vol[c] = std::ldexp(ell3, -3 * lv);
+        if (child[c] >= 0) {
+            word[c] = kLinkBit | (uint32_t)child[c];
+            rho[c] = 0.0f;
+        } else {
+            const float r = d->rho[c] == 0.0f ? 0.0f : d->rho[c];      // no -0
+            memcpy(&word[c], &r, 4);
+            rho[c] = r;
+            leaf.push_back((int32_t)c);
+        }
+    }
+    CloudHost *cl = new (std::nothrow) CloudHost();
+    if (!cl) return fail(ctx, SOC_ERR_NOMEM, "host allocation");
+    cl->nx = d->nx; cl->ny = d->ny; cl->nz = d->nz; cl->n_levels = d->n_levels;
+    cl->n_cells = n; cl->n_root = n_root; cl->n_leaf = (int64_t)leaf.size(); cl->level_start = start;
+    cl->ell = d->root_cell_size;
+    cudaError_t e = cudaSuccess;
+    if ((e = cl->cell.alloc(n)) == cudaSuccess && (e = cl->parent.alloc(n_oct)) == cudaSuccess &&
+        (e = cl->leaf.alloc(leaf.size())) == cudaSuccess && (e = cl->rho.alloc(n)) == cudaSuccess &&
+        (e = cl->volume.alloc(n)) == cudaSuccess &&
+        (e = cudaMemcpy(cl->cell.p, word.data(), 4 * n, cudaMemcpyHostToDevice)) == cudaSuccess &&
+        (e = cudaMemcpy(cl->parent.p, parent.data(), 4 * n_oct, cudaMemcpyHostToDevice)) == cudaSuccess &&
+        (e = cudaMemcpy(cl->leaf.p, leaf.data(), 4 * leaf.size(), cudaMemcpyHostToDevice)) == cudaSuccess &&
+        (e = cudaMemcpy(cl->rho.p, rho.data(), 4 * n, cudaMemcpyHostToDevice)) == cudaSuccess &&
+        (e = cudaMemcpy(cl->volume.p, vol.data(), 8 * n, cudaMemcpyHostToDevice)) == cudaSuccess) {
+    }
+    if (e != cudaSuccess) {
+        cl->cell.release(); cl->parent.release(); cl->leaf.release(); cl->rho.release(); cl->volume.release();
+        delete cl;
+        return cuda_fail(ctx, e, "grid upload");
+    }
+    ctx->clouds.push_back(cl);
+    ctx->clouds_dirty = true;
+    soc_status st = build_cloud_tables(ctx, *cl);
+    if (st != SOC_OK) return st;
+    *cloud_id = (int)ctx->clouds.size() - 1;
+    return SOC_OK;
+}
+
+soc_status soc_dust_upload(soc_ctx *ctx, int n_freq, const double *nu, const double *kabs, const double *ksca,
+                           const double *g)
+{
+    if (!ctx || n_freq < 1 || n_freq > 65535 || !nu || !kabs || !ksca || !g)
+        return fail(ctx, SOC_ERR_ARG, "bad dust arguments");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    for (int f = 0; f < n_freq; ++f) {
+        if (!(nu[f] > 0) || (f && !(nu[f] > nu[f - 1])) || !(kabs[f] >= 0) || !(ksca[f] >= 0) ||
+            !std::isfinite(kabs[f]) || !std::isfinite(ksca[f]) || !(std::fabs(g[f]) < 1.0))
+            return fail(ctx, SOC_ERR_ARG, "dust table entry %d invalid", f);
+    }
+    ctx->n_freq = n_freq;
+    ctx->nu.assign(nu, nu + n_freq);
+    ctx->kabs.assign(kabs, kabs + n_freq);
+    ctx->ksca.assign(ksca, ksca + n_freq);
+    ctx->g.assign(g, g + n_freq);
+    ctx->w = trapezoid(ctx->nu);
+    std::vector<float> gf(n_freq);
+    std::vector<double> wk(n_freq);
+    for (int f = 0; f < n_freq; ++f) {
+        gf[f] = (float)g[f];
+        wk[f] = 4.0 * kPi * ctx->w[f] * kabs[f];
+    }
+    // emission table E(T_k), T_k log-spaced in [kTMin, kTMax]
+    std::vector<double> lnE(kTableN), lnT(kTableN);
+    const double l0 = std::log(kTMin), l1 = std::log(kTMax);
+    for (int k = 0; k < kTableN; ++k) {
+        lnT[k] = l0 + (l1 - l0) * k / (kTableN - 1);
+        const double T = std::exp(lnT[k]);
+        double E = 0.0;
+        for (int f = 0; f < n_freq; ++f) E += wk[f] * planck_host(ctx->nu[f], T);
+        lnE[k] = std::log(std::max(E, 1e-300));
+    }
+    CK(ctx->d_g.alloc(n_freq), "alloc");
+    CK(ctx->d_w.alloc(n_freq), "alloc");
+    CK(ctx->d_w_kabs.alloc(n_freq), "alloc");
+    CK(ctx->d_nu.alloc(n_freq), "alloc");
+    CK(ctx->d_kabs.alloc(n_freq), "alloc");
+    CK(ctx->d_lnE.alloc(kTableN), "alloc");
+    CK(ctx->d_lnT.alloc(kTableN), "alloc");
+    CK(ctx->d_lmax.alloc(n_freq), "alloc");
+    CK(cudaMemcpy(ctx->d_g.p, gf.data(), 4 * n_freq, cudaMemcpyHostToDevice), "copy");
+    CK(cudaMemcpy(ctx->d_w.p, ctx->w.data(), 8 * n_freq, cudaMemcpyHostToDevice), "copy");
+    CK(cudaMemcpy(ctx->d_w_kabs.p, wk.data(), 8 * n_freq, cudaMemcpyHostToDevice), "copy");
+    CK(cudaMemcpy(ctx->d_nu.p, nu, 8 * n_freq, cudaMemcpyHostToDevice), "copy");
+    CK(cudaMemcpy(ctx->d_kabs.p, kabs, 8 * n_freq, cudaMemcpyHostToDevice), "copy");
+    CK(cudaMemcpy(ctx->d_lnE.p, lnE.data(), 8 * kTableN, cudaMemcpyHostToDevice), "copy");
+    CK(cudaMemcpy(ctx->d_lnT.p, lnT.data(), 8 * kTableN, cudaMemcpyHostToDevice), "copy");
+    for (CloudHost *c : ctx->clouds) {
+        soc_status st = build_cloud_tables(ctx, *c);
+        if (st != SOC_OK) return st;
+        if (c->n_ps && c->ps_cdf.n != (size_t)c->n_ps * n_freq)
+            return fail(ctx, SOC_ERR_STATE, "sources were uploaded for another frequency grid");
+    }
+    return SOC_OK;
+}
+
+soc_status soc_sources_upload(soc_ctx *ctx, int cloud_id, const double *bg_I_nu, int n_ps, const double *ps_pos,
+                              const double *ps_L_nu)
+{
+    soc_status st = check_cloud(ctx, cloud_id);
+    if (st) return st;
+    if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
+    if (n_ps < 0 || (n_ps > 0 && (!ps_pos || !ps_L_nu))) return fail(ctx, SOC_ERR_ARG, "bad point sources");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CloudHost &cl = *ctx->clouds[cloud_id];
+    const int nf = ctx->n_freq;
+    cl.bg_I.clear();
+    if (bg_I_nu) {
+        for (int f = 0; f < nf; ++f)
+            if (!(bg_I_nu[f] >= 0) || !std::isfinite(bg_I_nu[f])) return fail(ctx, SOC_ERR_ARG, "bad bg_I_nu[%d]", f);
+        cl.bg_I.assign(bg_I_nu, bg_I_nu + nf);
+    }
+    cl.n_ps = n_ps;
+    cl.ps_L_total.assign(nf, 0.0);
+    if (n_ps > 0) {
+        const int nr[3] = {cl.nx, cl.ny, cl.nz};
+        std::vector<float> pos(3 * n_ps);
+        for (int k = 0; k < n_ps; ++k)
+            for (int a = 0; a < 3; ++a) {
+                const double v = ps_pos[3 * k + a];
+                if (!(v > 0.0 && v < nr[a])) return fail(ctx, SOC_ERR_ARG, "point source %d outside the grid", k);
+                pos[3 * k + a] = (float)v;
+            }
+        std::vector<float> cdf((size_t)nf * n_ps);
+        for (int f = 0; f < nf; ++f) {
+            double tot = 0.0;
+            for (int k = 0; k < n_ps; ++k) {
+                const double L = ps_L_nu[(size_t)k * nf + f];
+                if (!(L >= 0) || !std::isfinite(L)) return fail(ctx, SOC_ERR_ARG, "bad ps_L_nu");
+                tot += L;
+            }
+            cl.ps_L_total[f] = tot;
+            double run = 0.0;
+            for (int k = 0; k < n_ps; ++k) {
+                run += ps_L_nu[(size_t)k * nf + f];
+                cdf[(size_t)f * n_ps + k] = (float)(run / (tot > 0 ? tot : 1.0));
+            }
+            cdf[(size_t)f * n_ps + n_ps - 1] = 1.0f;
+        }
+        CK(cl.ps_pos.alloc(pos.size()), "alloc");
+        CK(cl.ps_cdf.alloc(cdf.size()), "alloc");
+        CK(cudaMemcpy(cl.ps_pos.p, pos.data(), 4 * pos.size(), cudaMemcpyHostToDevice), "copy");
+        CK(cudaMemcpy(cl.ps_cdf.p, cdf.data(), 4 * cdf.size(), cudaMemcpyHostToDevice), "copy");
+    }
+    ctx->clouds_dirty = true;
+    return SOC_OK;
+}
+
+soc_status soc_package_energy(soc_ctx *ctx, int cloud_id, int source, uint64_t n_packages, double *e_unit)
+{
+    soc_status st = check_cloud(ctx, cloud_id);
+    if (st) return st;
+    if (!e_unit || n_packages == 0) return fail(ctx, SOC_ERR_ARG, "bad arguments");
+    const CloudHost &cl = *ctx->clouds[cloud_id];
+    const int nf = ctx->n_freq;
+    if (source == SOC_SRC_BACKGROUND) {
+        if (cl.bg_I.empty()) return fail(ctx, SOC_ERR_STATE, "no background uploaded");
+        const double S = 2.0 * ((double)cl.nx * cl.ny + (double)cl.ny * cl.nz + (double)cl.nz * cl.nx) * cl.ell * cl.ell;
+        for (int f = 0; f < nf; ++f) e_unit[f] = kPi * cl.bg_I[f] * S / (double)n_packages / 4294967296.0;
+        return SOC_OK;
+    }
+    if (source == SOC_SRC_POINT) {
+        if (cl.n_ps == 0) return fail(ctx, SOC_ERR_STATE, "no point sources uploaded");
+        for (int f = 0; f < nf; ++f) e_unit[f] = cl.ps_L_total[f] / (double)n_packages / 4294967296.0;
+        return SOC_OK;
+    }
+    return fail(ctx, SOC_ERR_ARG, "source must be background or point");
+}
+
+soc_status soc_simulate_frequency_batch(soc_ctx *ctx, const soc_batch_item *items, int n_items, int64_t *d_tally,
+                                        int64_t *d_stats, uint32_t *d_pkg_steps, void *stream)
+{
+    if (!ctx || !items || n_items < 1 || !d_tally || !d_stats) return fail(ctx, SOC_ERR_ARG, "null argument");
+    if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<DevItem> dv(n_items);
+    std::vector<uint64_t> prefix(n_items + 1, 0);
+    for (int i = 0; i < n_items; ++i) {
+        const soc_batch_item &it = items[i];
+        if (it.cloud < 0 || it.cloud >= (int)ctx->clouds.size()) return fail(ctx, SOC_ERR_ARG, "item %d: bad cloud", i);
+        const CloudHost &cl = *ctx->clouds[it.cloud];
+        if (it.freq < 0 || it.freq >= ctx->n_freq) return fail(ctx, SOC_ERR_ARG, "item %d: bad freq", i);
+        if (it.iteration < 0 || it.iteration > 65535) return fail(ctx, SOC_ERR_ARG, "item %d: bad iteration", i);
+        if (it.pid_offset + it.n_packages > 0xFFFFFFFFull || it.pid_offset > 0xFFFFFFFFull)
+            return fail(ctx, SOC_ERR_ARG, "item %d: package ids exceed 2^32", i);
+        if (it.tally_offset < 0) return fail(ctx, SOC_ERR_ARG, "item %d: negative tally offset", i);
+        if (it.source == SOC_SRC_BACKGROUND || it.source == SOC_SRC_POINT) {
+            if (it.w0 == 0 || it.w0 > SOC_W_UNIT) return fail(ctx, SOC_ERR_ARG, "item %d: w0 out of [1, 2^32]", i);
+            if (it.source == SOC_SRC_POINT && cl.n_ps == 0)
+                return fail(ctx, SOC_ERR_STATE, "item %d: cloud has no point sources", i);
+        } else if (it.source == SOC_SRC_DUST) {
+            if (!it.d_dust_w || it.n_per_cell == 0) return fail(ctx, SOC_ERR_ARG, "item %d: dust weights missing", i);
+            if (it.pid_offset + it.n_packages > (uint64_t)cl.n_leaf * it.n_per_cell)
+                return fail(ctx, SOC_ERR_ARG, "item %d: more dust packages than n_leaf*n_per_cell", i);
+        } else {
+            return fail(ctx, SOC_ERR_ARG, "item %d: unknown source %d", i, it.source);
+        }
+        DevItem &d = dv[i];
+        d.cloud = it.cloud; d.freq = it.freq; d.source = it.source; d.iteration = it.iteration;
+        d.pid_offset = (uint32_t)it.pid_offset; d.n_per_cell = it.n_per_cell ? it.n_per_cell : 1;
+        d.w0 = it.w0; d.tally_offset = it.tally_offset; d.dust_w = it.d_dust_w;
+        prefix[i + 1] = prefix[i] + it.n_packages;
+    }
+    const uint64_t total = prefix[n_items];
+    soc_status st = sync_clouds(ctx);
+    if (st) return st;
+    if (total == 0) return SOC_OK;
+    CK(ctx->d_items.alloc(n_items), "alloc items");
+    CK(ctx->d_prefix.alloc(n_items + 1), "alloc prefix");
+    CK(cudaMemcpyAsync(ctx->d_items.p, dv.data(), sizeof(DevItem) * n_items, cudaMemcpyHostToDevice, s), "copy items");
+    CK(cudaMemcpyAsync(ctx->d_prefix.p, prefix.data(), 8 * (n_items + 1), cudaMemcpyHostToDevice, s), "copy prefix");
+    CK(cudaMemsetAsync(ctx->d_counter.p, 0, sizeof(unsigned long long), s), "zero counter");
+    TraceParams P;
+    P.clouds = ctx->d_clouds.p;
+    P.items = ctx->d_items.p;
+    P.prefix = ctx->d_prefix.p;
+    P.g_hg = ctx->d_g.p;
+    P.tally = reinterpret_cast<unsigned long long *>(d_tally);
+    P.stats = reinterpret_cast<unsigned long long *>(d_stats);
+    P.pkg_steps = d_pkg_steps;
+    P.counter = ctx->d_counter.p;
+    P.total = total;
+    P.seed = ctx->seed;
+    P.n_items = n_items;
+    P.max_steps = ctx->max_steps;
+    P.chunk = ctx->chunk;
+    const int per_sm = ctx->bps > 0 ? std::min(ctx->bps, trace_block_limit(ctx->tpb)) : trace_block_limit(ctx->tpb);
+    const uint64_t warps_needed = (total + 31) / 32;
+    int64_t grid = (int64_t)ctx->sms * per_sm;
+    const int64_t grid_need = (int64_t)((warps_needed * 32 + ctx->tpb - 1) / ctx->tpb);
+    if (grid_need < grid) grid = grid_need < 1 ? 1 : grid_need;
+    CK(launch_trace(P, (int)grid, ctx->tpb, s), "trace launch");
+    // the host copies above used pageable buffers: they are staged before return
+    return SOC_OK;
+}
+
+soc_status soc_dust_emission(soc_ctx *ctx, int cloud_id, const float *d_T, int freq_lo, int n_freq,
+                             uint32_t n_per_cell, uint64_t *d_w, double *d_e_unit, void *stream)
+{
+    soc_status st = check_cloud(ctx, cloud_id);
+    if (st) return st;
+    if (!d_T || !d_w || !d_e_unit || n_per_cell == 0 || freq_lo < 0 || n_freq < 1 || freq_lo + n_freq > ctx->n_freq)
+        return fail(ctx, SOC_ERR_ARG, "bad dust-emission arguments");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if ((st = sync_clouds(ctx))) return st;
+    const CloudHost &cl = *ctx->clouds[cloud_id];
+    TempTables tt{ctx->n_freq, ctx->d_w_kabs.p, ctx->d_w.p, ctx->d_nu.p, ctx->d_kabs.p, ctx->d_lnE.p, ctx->d_lnT.p};
+    CK(launch_dust_emission(ctx->d_clouds.p + cloud_id, cl.n_leaf, tt, d_T, freq_lo, n_freq, n_per_cell, d_w,
+                            d_e_unit, ctx->d_lmax.p, (cudaStream_t)stream),
+       "dust emission");
+    return SOC_OK;
+}
+
+soc_status soc_absorbed_power(soc_ctx *ctx, int cloud_id, const int64_t *d_tally, int64_t tally_stride,
+                              const double *d_e_unit, const double *d_A_in, double *d_A_out, void *stream)
+{
+    soc_status st = check_cloud(ctx, cloud_id);
+    if (st) return st;
+    const CloudHost &cl = *ctx->clouds[cloud_id];
+    if (!d_tally || !d_e_unit || !d_A_out || tally_stride < cl.n_cells)
+        return fail(ctx, SOC_ERR_ARG, "bad absorbed-power arguments");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if ((st = sync_clouds(ctx))) return st;
+    CK(launch_absorbed_power(ctx->d_clouds.p + cloud_id, cl.n_cells, d_tally, tally_stride, d_e_unit, ctx->d_w.p,
+                             ctx->n_freq, d_A_in, d_A_out, (cudaStream_t)stream),
+       "absorbed power");
+    return SOC_OK;
+}
+
+soc_status soc_update_temperature(soc_ctx *ctx, int cloud_id, const double *d_A, float *d_T, double *d_max_dT,
+                                  void *stream)
+{
+    soc_status st = check_cloud(ctx, cloud_id);
+    if (st) return st;
+    if (!d_A || !d_T) return fail(ctx, SOC_ERR_ARG, "null argument");
+    if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if ((st = sync_clouds(ctx))) return st;
+    const CloudHost &cl = *ctx->clouds[cloud_id];
+    TempTables tt{ctx->n_freq, ctx->d_w_kabs.p, ctx->d_w.p, ctx->d_nu.p, ctx->d_kabs.p, ctx->d_lnE.p, ctx->d_lnT.p};
+    CK(launch_update_temperature(ctx->d_clouds.p + cloud_id, cl.n_cells, tt, d_A, d_T, d_max_dT,
+                                 (cudaStream_t)stream),
+       "temperature");
+    return SOC_OK;
+}
+
+soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm, const float *d_T_seed,
+                       float *d_T_out, soc_iterate_result *res, double *dT_history, void *stream)
+{
+    soc_status st = check_cloud(ctx, cloud_id);
+    if (st) return st;
+    if (!prm || !d_T_out || prm->max_iter < 0) return fail(ctx, SOC_ERR_ARG, "bad iterate arguments");
+    if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CloudHost &cl = *ctx->clouds[cloud_id];
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nf = ctx->n_freq;
+    const int64_t n = cl.n_cells;
+    if (prm->n_background && cl.bg_I.empty()) return fail(ctx, SOC_ERR_STATE, "no background uploaded");
+    if (prm->n_point && cl.n_ps == 0) return fail(ctx, SOC_ERR_STATE, "no point sources uploaded");
+    CK(cl.tally.alloc((size_t)nf * n), "alloc tally");
+    CK(cl.A_const.alloc(n), "alloc A");
+    CK(cl.A.alloc(n), "alloc A");
+    CK(cl.e_unit.alloc(nf), "alloc e_unit");
+    CK(cl.stats.alloc((size_t)4 * nf), "alloc stats");
+    if (prm->max_iter > 0) CK(cl.dust_w.alloc((size_t)nf * cl.n_leaf), "alloc dust weights");
+    int64_t steps = 0, capped = 0;
+    std::vector<int64_t> hstats(4 * nf);
+    std::vector<soc_batch_item> items(nf);
+    std::vector<double> e(nf);
+    auto run_items = [&](int source, uint64_t npk, int iteration, const uint64_t *dw, uint32_t npc) -> soc_status {
+        for (int f = 0; f < nf; ++f) {
+            soc_batch_item &it = items[f];
+            memset(&it, 0, sizeof it);
+            it.cloud = cloud_id; it.freq = f; it.source = source; it.iteration = iteration;
+            it.pid_offset = 0; it.n_packages = npk; it.w0 = SOC_W_UNIT; it.tally_offset = (int64_t)f * n;
+            it.d_dust_w = dw ? dw + (size_t)f * cl.n_leaf : nullptr; it.n_per_cell = npc;
+        }
+        CK(cudaMemsetAsync(cl.tally.p, 0, sizeof(int64_t) * nf * n, s), "zero tally");
+        CK(cudaMemsetAsync(cl.stats.p, 0, sizeof(int64_t) * 4 * nf, s), "zero stats");
+        soc_status r = soc_simulate_frequency_batch(ctx, items.data(), nf, cl.tally.p, cl.stats.p, nullptr, stream);
+        if (r) return r;
+        CK(cudaMemcpyAsync(hstats.data(), cl.stats.p, sizeof(int64_t) * 4 * nf, cudaMemcpyDeviceToHost, s), "stats");
+        CK(cudaStreamSynchronize(s), "sync");
+        for (int f = 0; f < nf; ++f) { capped += hstats[4 * f + 1]; steps += hstats[4 * f + 2]; }
+        return SOC_OK;
+    };
+    // iteration 0: constant sources, kept as A_const
+    CK(cudaMemsetAsync(cl.A_const.p, 0, sizeof(double) * n, s), "zero A");
+    const uint64_t nsrc[2] = {prm->n_background, prm->n_point};
+    for (int k = 0; k < 2; ++k) {
+        if (!nsrc[k]) continue;
+        const int source = k == 0 ? SOC_SRC_BACKGROUND : SOC_SRC_POINT;
+        if ((st = run_items(source, nsrc[k], 0, nullptr, 1))) return st;
+        if ((st = soc_package_energy(ctx, cloud_id, source, nsrc[k], e.data()))) return st;
+        CK(cudaMemcpyAsync(cl.e_unit.p, e.data(), 8 * nf, cudaMemcpyHostToDevice, s), "copy e_unit");
+        if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit.p, cl.A_const.p, cl.A_const.p, stream)))
+            return st;
+    }
+    if (d_T_seed) {
+        CK(cudaMemcpyAsync(d_T_out, d_T_seed, sizeof(float) * n, cudaMemcpyDeviceToDevice, s), "copy seed");
+    } else {
+        if ((st = soc_update_temperature(ctx, cloud_id, cl.A_const.p, d_T_out, nullptr, stream))) return st;
+    }
+    int it_done = 0, conv = 0;
+    double dT = 0.0;
+    for (int k = 1; k <= prm->max_iter; ++k) {
+        if ((st = soc_dust_emission(ctx, cloud_id, d_T_out, 0, nf, prm->n_per_cell, cl.dust_w.p, cl.e_unit.p, stream)))
+            return st;
+        // frozen dust random numbers: the same RNG stream (iteration 1) every time
+        if ((st = run_items(SOC_SRC_DUST, (uint64_t)cl.n_leaf * prm->n_per_cell, 1, cl.dust_w.p, prm->n_per_cell)))
+            return st;
+        if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit.p, cl.A_const.p, cl.A.p, stream)))
+            return st;
+        if ((st = soc_update_temperature(ctx, cloud_id, cl.A.p, d_T_out, ctx->d_maxdT.p, stream))) return st;
+        CK(cudaMemcpyAsync(&dT, ctx->d_maxdT.p, sizeof(double), cudaMemcpyDeviceToHost, s), "read max dT");
+        CK(cudaStreamSynchronize(s), "sync");
+        if (dT_history) dT_history[k - 1] = dT;
+        it_done = k;
+        if (dT < prm->dT_tol) { conv = 1; break; }
+    }
+    if (res) {
+        res->iterations = it_done;
+        res->converged = conv;
+        res->final_max_dT = dT;
+        res->steps = steps;
+        res->capped = capped;
+    }
+    return capped ? fail(ctx, SOC_ERR_STEP_LIMIT, "%lld packages hit the step cap", (long long)capped) : SOC_OK;
+}
+
+}  // extern "C"

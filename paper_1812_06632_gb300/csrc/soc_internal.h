@@ -1,0 +1,80 @@
+// soc_internal.h -- device-side data layout shared by the libsoc translation
+// units (not part of the public C-ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "../../include/soc.h"
+
+namespace soc {
+
+constexpr uint32_t kLinkBit = 0x80000000u;   // cell word: bit 31 = refined
+constexpr uint64_t kWMin = 1ull << 12;       // packages below this weight end
+constexpr int kTableN = 4096;                // T grid of the emission table
+constexpr double kTMin = 2.7, kTMax = 3000.0;
+
+// One uploaded grid as the kernels see it (lives in device memory, in an
+// array indexed by cloud id).  Cell words: FP32 density, or kLinkBit | first
+// child.  Octet k (cells n_root + 8k .. +7) has parent parent[k].
+struct DevCloud {
+    const uint32_t *cell;        // [n_cells]
+    const int32_t *parent;       // [n_octets]
+    const int32_t *leaf;         // [n_leaf] leaf cells in increasing order
+    const float *rho;            // [n_cells] FP32 density (0 for refined cells)
+    const double *volume;        // [n_cells] cm^3
+    const float2 *kappa;         // [n_freq] (kabs * ell, ksca * ell) per root-cell length
+    const float *ps_pos;         // [3 n_ps] root-cell units
+    const float *ps_cdf;         // [n_freq][n_ps] cumulative luminosity fraction
+    int32_t nx, ny, nz, n_levels;
+    int32_t n_ps, pad_;
+    int64_t n_cells, n_root, n_leaf;
+    int64_t level_start[SOC_MAX_LEVELS + 1];
+};
+
+// Batch item after preparation on the host.
+struct DevItem {
+    int32_t cloud, freq, source, iteration;
+    uint32_t pid_offset, n_per_cell;
+    uint64_t w0;
+    int64_t tally_offset;
+    const uint64_t *dust_w;
+};
+
+struct TraceParams {
+    const DevCloud *clouds;
+    const DevItem *items;
+    const uint64_t *prefix;      // [n_items + 1] exclusive prefix of n_packages
+    const float *g_hg;           // [n_freq]
+    unsigned long long *tally;
+    unsigned long long *stats;   // [n_items][4]
+    uint32_t *pkg_steps;         // nullable
+    unsigned long long *counter; // global work counter
+    uint64_t total;
+    uint64_t seed;
+    int32_t n_items;
+    uint32_t max_steps;
+    int32_t chunk;
+};
+
+cudaError_t launch_trace(const TraceParams &p, int grid, int block, cudaStream_t s);
+int trace_block_limit(int block);   // max resident blocks/SM for this block size
+
+struct TempTables {
+    int n_freq;
+    const double *w_kabs;        // [n_freq] 4 pi w_nu kabs(nu)
+    const double *w;             // [n_freq] trapezoid weights
+    const double *nu;            // [n_freq]
+    const double *kabs;          // [n_freq] physical cross sections
+    const double *lnE;           // [kTableN]
+    const double *lnT;           // [kTableN]
+};
+
+cudaError_t launch_absorbed_power(const DevCloud *dcl, int64_t n_cells, const int64_t *tally,
+                                  int64_t stride, const double *e_unit, const double *w, int n_freq,
+                                  const double *A_in, double *A_out, cudaStream_t s);
+cudaError_t launch_update_temperature(const DevCloud *dcl, int64_t n_cells, const TempTables &tt,
+                                      const double *A, float *T, double *max_dT, cudaStream_t s);
+cudaError_t launch_dust_emission(const DevCloud *dcl, int64_t n_leaf, const TempTables &tt, const float *T,
+                                 int freq_lo, int n_freq, uint32_t n_per_cell, uint64_t *w,
+                                 double *e_unit, unsigned long long *scratch_max, cudaStream_t s);
+
+}  // namespace soc

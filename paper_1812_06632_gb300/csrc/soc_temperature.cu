@@ -1,0 +1,240 @@
+// soc_temperature.cu -- FP64 kernels of the equilibrium-dust step (paper
+// Sect. 2.1.1: the frequency integral of absorbed energy is gathered on the
+// device and a separate kernel solves each cell's temperature from it;
+// Sect. 3.2: uniform dust re-emission from every cell).
+//
+// All three kernels stream cell-indexed arrays with one thread per leaf
+// (coalesced; the counter array [n_freq][n_cells] is read column by column,
+// adjacent threads reading adjacent cells).  Sums and products are written
+// with the _rn intrinsics in a fixed order so that the absorbed power equals
+// a plain sequential FP64 evaluation bit for bit.
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "soc_internal.h"
+
+namespace soc {
+namespace {
+
+constexpr double kH = 6.62607015e-27;      // erg s   (CODATA 2018, exact)
+constexpr double kK = 1.380649e-16;        // erg / K (exact)
+constexpr double kC = 2.99792458e10;       // cm / s  (exact)
+constexpr double kPi = 3.141592653589793;
+
+// B_nu(T) = (2 h nu^3 / c^2) / (exp(h nu / k T) - 1).
+__device__ __forceinline__ double planck(double nu, double T)
+{
+    const double x = __ddiv_rn(__dmul_rn(kH, nu), __dmul_rn(kK, T));
+    const double pre = __ddiv_rn(__dmul_rn(__dmul_rn(2.0, kH), __dmul_rn(__dmul_rn(nu, nu), nu)),
+                                 __dmul_rn(kC, kC));
+    return __ddiv_rn(pre, expm1(x));
+}
+
+// E(T) = sum_f wk_f B_f(T) and dE/dT, wk_f = 4 pi w_f kabs_f.
+__device__ __forceinline__ void emission_and_slope(const TempTables &tt, double T, double &E, double &dE)
+{
+    E = 0.0;
+    dE = 0.0;
+    for (int f = 0; f < tt.n_freq; ++f) {
+        const double nu = __ldg(tt.nu + f);
+        const double x = __ddiv_rn(__dmul_rn(kH, nu), __dmul_rn(kK, T));
+        if (x > 700.0) continue;
+        const double em1 = expm1(x);
+        const double pre = __ddiv_rn(__dmul_rn(__dmul_rn(2.0, kH), __dmul_rn(__dmul_rn(nu, nu), nu)),
+                                     __dmul_rn(kC, kC));
+        const double B = __ddiv_rn(pre, em1);
+        const double wk = __ldg(tt.w_kabs + f);
+        E = __dadd_rn(E, __dmul_rn(wk, B));
+        // dB/dT = B (x / T) (em1 + 1) / em1
+        dE = __dadd_rn(dE, __dmul_rn(wk, __dmul_rn(B, __ddiv_rn(__dmul_rn(x, __dadd_rn(em1, 1.0)),
+                                                                __dmul_rn(T, em1)))));
+    }
+}
+
+__global__ void absorbed_power_kernel(const DevCloud *__restrict__ dcl, int64_t n_cells,
+                                      const long long *__restrict__ tally, int64_t stride,
+                                      const double *__restrict__ e_unit, const double *__restrict__ w,
+                                      int n_freq, const double *A_in, double *A_out)
+{
+    const DevCloud &C = *dcl;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n_cells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const double a0 = A_in ? A_in[c] : 0.0;
+        const double rv = __dmul_rn((double)__ldg(C.rho + c), __ldg(C.volume + c));
+        if (!(rv > 0.0)) { A_out[c] = a0; continue; }
+        double acc = 0.0;
+        for (int f = 0; f < n_freq; ++f) {
+            const double wf = __dmul_rn(__ldg(w + f), __ldg(e_unit + f));
+            acc = __dadd_rn(acc, __dmul_rn(wf, (double)__ldg(tally + (int64_t)f * stride + c)));
+        }
+        A_out[c] = __dadd_rn(a0, __ddiv_rn(acc, rv));
+    }
+}
+
+// Block-wide max of a non-negative double into *out via its bit pattern
+// (non-negative IEEE doubles order like their unsigned integer images).
+__device__ __forceinline__ void block_max_to(double v, unsigned long long *out)
+{
+    __shared__ unsigned long long smax[32];
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, b, o);
+        b = t > b ? t : b;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) smax[warp] = b;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        b = lane < nw ? smax[lane] : 0ull;
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, b, o);
+            b = t > b ? t : b;
+        }
+        if (lane == 0 && b) atomicMax(out, b);
+    }
+}
+
+// Equilibrium temperature: table bracket + log-log interpolation, then one
+// Newton step on the FP64 quadrature.
+__global__ void temperature_kernel(const DevCloud *__restrict__ dcl, int64_t n_cells, const TempTables tt,
+                                   const double *__restrict__ A, float *T, unsigned long long *max_dT)
+{
+    const DevCloud &C = *dcl;
+    double dmax = 0.0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n_cells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (__ldg(C.cell + c) & kLinkBit) continue;                // refined cells carry no T
+        const double a = A[c];
+        double Tn;
+        if (!(a > 0.0)) {
+            Tn = kTMin;
+        } else {
+            const double la = log(a);
+            if (la <= __ldg(tt.lnE)) {
+                Tn = kTMin;
+            } else if (la >= __ldg(tt.lnE + kTableN - 1)) {
+                Tn = kTMax;
+            } else {
+                int lo = 0, hi = kTableN - 1;                         // lnE[lo] < la <= lnE[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (__ldg(tt.lnE + mid) < la) lo = mid; else hi = mid;
+                }
+                const double e0 = __ldg(tt.lnE + lo), e1 = __ldg(tt.lnE + hi);
+                const double t0 = __ldg(tt.lnT + lo), t1 = __ldg(tt.lnT + hi);
+                const double T0 = exp(t0 + (la - e0) * (t1 - t0) / (e1 - e0));
+                double E, dE;
+                emission_and_slope(tt, T0, E, dE);
+                Tn = (dE > 0.0) ? T0 - (E - a) / dE : T0;
+                Tn = fmin(fmax(Tn, kTMin), kTMax);
+            }
+        }
+        const float Tf = (float)Tn;
+        if (max_dT) dmax = fmax(dmax, fabs((double)Tf - (double)T[c]));
+        T[c] = Tf;
+    }
+    if (max_dT) block_max_to(dmax, max_dT);
+}
+
+// Dust luminosity of leaf li at frequency f: 4 pi rho V kabs B_nu(T), in the
+// order (((4 pi rho) V) kabs) B.
+__device__ __forceinline__ double dust_L(const DevCloud &C, const TempTables &tt, const float *T,
+                                         int32_t cell, int f)
+{
+    const double rho = (double)__ldg(C.rho + cell);
+    const double V = __ldg(C.volume + cell);
+    const double B = planck(__ldg(tt.nu + f), (double)__ldg(T + cell));
+    return __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(4.0 * kPi, rho), V), __ldg(tt.kabs + f)), B);
+}
+
+__global__ void dust_max_kernel(const DevCloud *__restrict__ dcl, int64_t n_leaf, const TempTables tt,
+                                const float *__restrict__ T, int freq_lo, int n_freq,
+                                unsigned long long *Lmax)
+{
+    const DevCloud &C = *dcl;
+    for (int fi = 0; fi < n_freq; ++fi) {
+        double m = 0.0;
+        for (int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; li < n_leaf;
+             li += (int64_t)gridDim.x * blockDim.x) {
+            const double L = dust_L(C, tt, T, __ldg(C.leaf + li), freq_lo + fi);
+            m = L > m ? L : m;
+        }
+        block_max_to(m, Lmax + fi);
+        __syncthreads();
+    }
+}
+
+__global__ void dust_weight_kernel(const DevCloud *__restrict__ dcl, int64_t n_leaf, const TempTables tt,
+                                   const float *__restrict__ T, int freq_lo, int n_freq, uint32_t n_per_cell,
+                                   const unsigned long long *__restrict__ Lmax, unsigned long long *w,
+                                   double *e_unit)
+{
+    const DevCloud &C = *dcl;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tid < n_freq) {
+        const double m = __longlong_as_double((long long)Lmax[tid]);
+        e_unit[tid] = __ddiv_rn(__ddiv_rn(m, (double)n_per_cell), 4294967296.0);
+    }
+    for (int64_t li = tid; li < n_leaf; li += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t cell = __ldg(C.leaf + li);
+        for (int fi = 0; fi < n_freq; ++fi) {
+            const double m = __longlong_as_double((long long)__ldg(Lmax + fi));
+            unsigned long long W = 0;
+            if (m > 0.0) {
+                const double L = dust_L(C, tt, T, cell, freq_lo + fi);
+                W = (unsigned long long)rint(__dmul_rn(__ddiv_rn(L, m), 4294967296.0));
+            }
+            w[(int64_t)fi * n_leaf + li] = W;
+        }
+    }
+}
+
+int grid_for(int64_t n, int block)
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t need = (n + block - 1) / block;
+    const int64_t cap = (int64_t)sms * 8;
+    return (int)(need < 1 ? 1 : (need < cap ? need : cap));
+}
+
+}  // namespace
+
+cudaError_t launch_absorbed_power(const DevCloud *dcl, int64_t n_cells, const int64_t *tally, int64_t stride,
+                                  const double *e_unit, const double *w, int n_freq, const double *A_in,
+                                  double *A_out, cudaStream_t s)
+{
+    absorbed_power_kernel<<<grid_for(n_cells, 256), 256, 0, s>>>(
+        dcl, n_cells, reinterpret_cast<const long long *>(tally), stride, e_unit, w, n_freq, A_in, A_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_temperature(const DevCloud *dcl, int64_t n_cells, const TempTables &tt,
+                                      const double *A, float *T, double *max_dT, cudaStream_t s)
+{
+    if (max_dT) {
+        cudaError_t e = cudaMemsetAsync(max_dT, 0, sizeof(double), s);
+        if (e != cudaSuccess) return e;
+    }
+    temperature_kernel<<<grid_for(n_cells, 256), 256, 0, s>>>(
+        dcl, n_cells, tt, A, T, reinterpret_cast<unsigned long long *>(max_dT));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dust_emission(const DevCloud *dcl, int64_t n_leaf, const TempTables &tt, const float *T,
+                                 int freq_lo, int n_freq, uint32_t n_per_cell, uint64_t *w, double *e_unit,
+                                 unsigned long long *scratch_max, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(scratch_max, 0, sizeof(unsigned long long) * n_freq, s);
+    if (e != cudaSuccess) return e;
+    dust_max_kernel<<<grid_for(n_leaf, 256), 256, 0, s>>>(dcl, n_leaf, tt, T, freq_lo, n_freq, scratch_max);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int64_t n = n_leaf > n_freq ? n_leaf : n_freq;
+    dust_weight_kernel<<<grid_for(n, 256), 256, 0, s>>>(dcl, n_leaf, tt, T, freq_lo, n_freq, n_per_cell,
+                                                         scratch_max, reinterpret_cast<unsigned long long *>(w),
+                                                         e_unit);
+    return cudaGetLastError();
+}
+
+}  // namespace soc

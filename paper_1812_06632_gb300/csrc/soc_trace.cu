@@ -1,0 +1,481 @@
+// soc_trace.cu -- persistent photon-package tracer (paper Sect. 2.1.1: package
+// creation, cell-to-cell stepping through the hierarchical grid with partial
+// traversal up to the common ancestor and down to the new leaf, per-cell
+// absorption counters; Sect. 2.2 sources; Sect. 3.2 uniform dust emission).
+//
+// Scheduling: one package per lane.  A warp takes chunk*32 consecutive work
+// indices at a time from a global counter; whenever a lane's package ends
+// the lane takes the next index of the warp's chunk (per-lane refill, the
+// interleaving of creation and tracking suggested in Sect. 4.2).  One launch
+// covers every (cloud, frequency, source) item of a batch.
+//
+// Arithmetic: the FP32 sequence of soc_fp32.cuh; deposits are uint64 fixed
+// point (2^32 units per package) and are merged per cell before one 64-bit
+// atomic add, so the counters are exact and independent of scheduling.
+// Compiled with -fmad=false.
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "soc_internal.h"
+#include "soc_fp32.cuh"
+
+namespace soc {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// One package's random stream: key (seed, iteration, frequency), counter
+// (package id, block, cloud, source class); draw n = word n%4 of block n/4.
+struct Rng {
+    uint32_t k0, k1, pid, cloud, cls, n;
+    uint32_t b0, b1, b2, b3;
+
+    __device__ __forceinline__ void init(uint64_t seed, uint32_t iteration, uint32_t freq,
+                                         uint32_t pid_, uint32_t cloud_, uint32_t cls_)
+    {
+        k0 = (uint32_t)seed;
+        k1 = (uint32_t)(seed >> 32) ^ (iteration << 16) ^ freq;
+        pid = pid_; cloud = cloud_; cls = cls_; n = 0;
+    }
+    __device__ __forceinline__ uint32_t next()
+    {
+        const uint32_t j = n & 3u;
+        if (j == 0) {
+            const U4 v = philox10(pid, n >> 2, cloud, cls, k0, k1);
+            b0 = v.a; b1 = v.b; b2 = v.c; b3 = v.d;
+        }
+        ++n;
+        return j == 0 ? b0 : (j == 1 ? b1 : (j == 2 ? b2 : b3));
+    }
+    __device__ __forceinline__ float u() { return u01(next()); }
+};
+
+struct Pkg {
+    int32_t cell;                 // current leaf
+    int32_t ri, rj, rk;           // root-grid coordinates of its root ancestor
+    float h;                      // cell side in root-cell units
+    float x, y, z;                // position in [0,1]^3 of the cell
+    float dx, dy, dz;             // direction
+    float ix, iy, iz;             // 1/d (unused where d == 0)
+    float rho;                    // density of the current leaf
+    float tauf;                   // remaining scattering optical depth
+    uint64_t W;                   // weight (fixed point)
+    uint64_t pend;                // deposits in the current cell not yet added
+    uint32_t steps;
+};
+
+__device__ __forceinline__ void set_inverse(Pkg &p)
+{
+    p.ix = (p.dx != 0.0f) ? __fdiv_rn(1.0f, p.dx) : 0.0f;
+    p.iy = (p.dy != 0.0f) ? __fdiv_rn(1.0f, p.dy) : 0.0f;
+    p.iz = (p.dz != 0.0f) ? __fdiv_rn(1.0f, p.dz) : 0.0f;
+}
+
+// Follow child links to the leaf that contains the position; the upper child
+// is taken on an axis when 2x >= 1.
+__device__ __forceinline__ void descend(const uint32_t *__restrict__ cells, Pkg &p)
+{
+    uint32_t w = __ldg(cells + p.cell);
+    while (w & kLinkBit) {
+        const float x2 = __fmul_rn(2.0f, p.x), y2 = __fmul_rn(2.0f, p.y), z2 = __fmul_rn(2.0f, p.z);
+        const int bx = x2 >= 1.0f, by = y2 >= 1.0f, bz = z2 >= 1.0f;
+        p.x = __fsub_rn(x2, (float)bx);
+        p.y = __fsub_rn(y2, (float)by);
+        p.z = __fsub_rn(z2, (float)bz);
+        p.h = __fmul_rn(p.h, 0.5f);
+        p.cell = (int32_t)(w & ~kLinkBit) + (bx | (by << 1) | (bz << 2));
+        w = __ldg(cells + p.cell);
+    }
+    p.rho = __uint_as_float(w);
+}
+
+// (cos phi, sin phi) from a point drawn uniformly in the unit disk.  After 64
+// rejections (probability < 1e-42) the azimuth 0 is used, so the loop is bounded.
+__device__ __forceinline__ void disk(Rng &r, float &c, float &s)
+{
+    float a = 1.0f, b = 0.0f, r2 = 1.0f;
+    for (int tries = 0; tries < 64; ++tries) {
+        const float ta = __fsub_rn(__fmul_rn(2.0f, r.u()), 1.0f);
+        const float tb = __fsub_rn(__fmul_rn(2.0f, r.u()), 1.0f);
+        const float t2 = __fadd_rn(__fmul_rn(ta, ta), __fmul_rn(tb, tb));
+        if (t2 <= 1.0f && t2 > 0.0f) { a = ta; b = tb; r2 = t2; break; }
+    }
+    const float rr = __fsqrt_rn(r2);
+    c = __fdiv_rn(a, rr);
+    s = __fdiv_rn(b, rr);
+}
+
+__device__ __forceinline__ void isotropic(Rng &r, Pkg &p)
+{
+    const float mu = __fsub_rn(__fmul_rn(2.0f, r.u()), 1.0f);
+    float c, s;
+    disk(r, c, s);
+    const float st = __fsqrt_rn(fmaxf(0.0f, __fsub_rn(1.0f, __fmul_rn(mu, mu))));
+    p.dx = __fmul_rn(st, c);
+    p.dy = __fmul_rn(st, s);
+    p.dz = mu;
+}
+
+// Henyey-Greenstein deflection of the direction by the angle with
+// cos = (1 + g^2 - ((1 - g^2)/(1 - g + 2 g u))^2) / (2 g); rotation about the
+// old direction by the azimuth from the disk sampler; renormalised.
+__device__ __forceinline__ void hg_scatter(Rng &r, float g, Pkg &p)
+{
+    const float u = r.u();
+    float mu;
+    if (fabsf(g) < 1e-4f) {
+        mu = __fsub_rn(__fmul_rn(2.0f, u), 1.0f);
+    } else {
+        const float g2 = __fmul_rn(g, g);
+        const float den = __fadd_rn(__fsub_rn(1.0f, g), __fmul_rn(__fadd_rn(g, g), u));
+        const float tmp = __fdiv_rn(__fsub_rn(1.0f, g2), den);
+        mu = __fdiv_rn(__fsub_rn(__fadd_rn(1.0f, g2), __fmul_rn(tmp, tmp)), __fadd_rn(g, g));
+        mu = fminf(fmaxf(mu, -1.0f), 1.0f);
+    }
+    float c, s;
+    disk(r, c, s);
+    const float st = __fsqrt_rn(fmaxf(0.0f, __fsub_rn(1.0f, __fmul_rn(mu, mu))));
+    const float dx = p.dx, dy = p.dy, dz = p.dz;
+    float nx, ny, nz;
+    if (fabsf(dz) > 0.99999f) {
+        nx = __fmul_rn(st, c);
+        ny = __fmul_rn(st, s);
+        nz = (dz > 0.0f) ? mu : -mu;
+    } else {
+        const float t = __fsqrt_rn(__fsub_rn(1.0f, __fmul_rn(dz, dz)));
+        const float ax = __fsub_rn(__fmul_rn(__fmul_rn(dx, dz), c), __fmul_rn(dy, s));
+        const float ay = __fadd_rn(__fmul_rn(__fmul_rn(dy, dz), c), __fmul_rn(dx, s));
+        nx = __fadd_rn(__fdiv_rn(__fmul_rn(st, ax), t), __fmul_rn(dx, mu));
+        ny = __fadd_rn(__fdiv_rn(__fmul_rn(st, ay), t), __fmul_rn(dy, mu));
+        nz = __fsub_rn(__fmul_rn(dz, mu), __fmul_rn(__fmul_rn(st, c), t));
+    }
+    const float nrm = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(nx, nx), __fmul_rn(ny, ny)),
+                                           __fmul_rn(nz, nz)));
+    p.dx = __fdiv_rn(nx, nrm);
+    p.dy = __fdiv_rn(ny, nrm);
+    p.dz = __fdiv_rn(nz, nrm);
+}
+
+// Root cell index along an axis of n cells for root-unit coordinate v, and
+// the local coordinate v - i.
+__device__ __forceinline__ int root_axis(float v, int n, float &local)
+{
+    int i = __float2int_rz(v);
+    i = max(0, min(i, n - 1));
+    local = clamp01(__fsub_rn(v, __int2float_rn(i)));
+    return i;
+}
+
+__device__ __forceinline__ int32_t root_cell(const DevCloud &C, int i, int j, int k)
+{
+    return i + C.nx * (j + C.ny * k);
+}
+
+// Emission (Sect. 2.2 background and point sources, Sect. 3.2 dust).  Returns
+// false for a dust package of zero weight (nothing to trace).
+__device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r, Pkg &p)
+{
+    p.h = 1.0f;
+    if (it.source == SOC_SRC_BACKGROUND) {
+        const float fx = __int2float_rn(C.nx), fy = __int2float_rn(C.ny), fz = __int2float_rn(C.nz);
+        const float ax = __fmul_rn(fy, fz), ay = __fmul_rn(fx, fz), az = __fmul_rn(fx, fy);
+        const float c0 = ax, c1 = __fadd_rn(c0, ax), c2 = __fadd_rn(c1, ay);
+        const float c3 = __fadd_rn(c2, ay), c4 = __fadd_rn(c3, az), c5 = __fadd_rn(c4, az);
+        const float t = __fmul_rn(r.u(), c5);
+        const int f = (t < c0) ? 0 : (t < c1) ? 1 : (t < c2) ? 2 : (t < c3) ? 3 : (t < c4) ? 4 : 5;
+        const int a = f >> 1;
+        const bool low = (f & 1) == 0;
+        // tangential axes t1 < t2
+        const int n1 = (a == 0) ? C.ny : C.nx;
+        const int n2 = (a == 2) ? C.ny : C.nz;
+        const int na = (a == 0) ? C.nx : (a == 1) ? C.ny : C.nz;
+        float l1, l2;
+        const int i1 = root_axis(__fmul_rn(r.u(), __int2float_rn(n1)), n1, l1);
+        const int i2 = root_axis(__fmul_rn(r.u(), __int2float_rn(n2)), n2, l2);
+        const int ia = low ? 0 : na - 1;
+        const float la = low ? 0.0f : 1.0f;
+        const float u = r.u();
+        const float mu = __fsqrt_rn(u);                 // cosine-weighted inward
+        const float st = __fsqrt_rn(__fsub_rn(1.0f, u));
+        float c, s;
+        disk(r, c, s);
+        const float da = low ? mu : -mu, d1 = __fmul_rn(st, c), d2 = __fmul_rn(st, s);
+        p.x = (a == 0) ? la : l1;
+        p.y = (a == 0) ? l1 : (a == 1) ? la : l2;
+        p.z = (a == 2) ? la : l2;
+        p.ri = (a == 0) ? ia : i1;
+        p.rj = (a == 0) ? i1 : (a == 1) ? ia : i2;
+        p.rk = (a == 2) ? ia : i2;
+        p.dx = (a == 0) ? da : d1;
+        p.dy = (a == 0) ? d1 : (a == 1) ? da : d2;
+        p.dz = (a == 2) ? da : d2;
+        p.W = it.w0;
+        p.cell = root_cell(C, p.ri, p.rj, p.rk);
+        descend(C.cell, p);
+        return true;
+    }
+    if (it.source == SOC_SRC_POINT) {
+        const float t = r.u();
+        const float *cdf = C.ps_cdf + (int64_t)it.freq * C.n_ps;
+        int k = 0;
+        while (k < C.n_ps - 1 && !(t < __ldg(cdf + k))) ++k;
+        p.ri = root_axis(__ldg(C.ps_pos + 3 * k + 0), C.nx, p.x);
+        p.rj = root_axis(__ldg(C.ps_pos + 3 * k + 1), C.ny, p.y);
+        p.rk = root_axis(__ldg(C.ps_pos + 3 * k + 2), C.nz, p.z);
+        isotropic(r, p);
+        p.W = it.w0;
+        p.cell = root_cell(C, p.ri, p.rj, p.rk);
+        descend(C.cell, p);
+        return true;
+    }
+    // dust: n_per_cell packages from every leaf, uniform inside the cell
+    const int64_t li = (int64_t)(pid / it.n_per_cell);
+    p.cell = __ldg(C.leaf + li);
+    p.W = __ldg(reinterpret_cast<const unsigned long long *>(it.dust_w) + li);
+    if (p.W == 0) return false;
+    int L = 0;
+    while (L + 1 < C.n_levels && (int64_t)p.cell >= C.level_start[L + 1]) ++L;
+    p.h = __uint_as_float((uint32_t)(127 - L) << 23);        // 2^-L
+    int32_t anc = p.cell;
+    while ((int64_t)anc >= C.n_root) anc = __ldg(C.parent + ((anc - C.n_root) >> 3));
+    p.ri = anc % C.nx;
+    p.rj = (anc / C.nx) % C.ny;
+    p.rk = anc / (C.nx * C.ny);
+    p.rho = __uint_as_float(__ldg(C.cell + p.cell));
+    p.x = r.u();
+    p.y = r.u();
+    p.z = r.u();
+    isotropic(r, p);
+    return true;
+}
+
+// Cross the face on axis `ax`: the package sits on it in the current frame.
+// Returns false when it leaves the root grid.
+__device__ bool cross_face(const DevCloud &C, Pkg &p, int ax, bool up)
+{
+    const int32_t n_root = (int32_t)C.n_root;
+    while (p.cell >= n_root) {
+        const int o = (p.cell - n_root) & 7;
+        const int b = (o >> ax) & 1;
+        if (up ? (b == 0) : (b == 1)) {
+            p.cell += up ? (1 << ax) : -(1 << ax);
+            const float v = up ? 0.0f : 1.0f;
+            if (ax == 0) p.x = v; else if (ax == 1) p.y = v; else p.z = v;
+            descend(C.cell, p);
+            return true;
+        }
+        p.x = __fmul_rn(__fadd_rn(p.x, (float)(o & 1)), 0.5f);
+        p.y = __fmul_rn(__fadd_rn(p.y, (float)((o >> 1) & 1)), 0.5f);
+        p.z = __fmul_rn(__fadd_rn(p.z, (float)((o >> 2) & 1)), 0.5f);
+        p.h = __fmul_rn(p.h, 2.0f);
+        p.cell = __ldg(C.parent + ((p.cell - n_root) >> 3));
+    }
+    const int step = up ? 1 : -1;
+    if (ax == 0) { p.ri += step; if (p.ri < 0 || p.ri >= C.nx) return false; }
+    else if (ax == 1) { p.rj += step; if (p.rj < 0 || p.rj >= C.ny) return false; }
+    else { p.rk += step; if (p.rk < 0 || p.rk >= C.nz) return false; }
+    p.cell = root_cell(C, p.ri, p.rj, p.rk);
+    const float v = up ? 0.0f : 1.0f;
+    if (ax == 0) p.x = v; else if (ax == 1) p.y = v; else p.z = v;
+    descend(C.cell, p);
+    return true;
+}
+
+enum StepResult { kContinue = 0, kAbsorbed = 1, kEscaped = 2, kCapped = 3 };
+
+// One photon-cell step (one segment inside one leaf).
+__device__ __forceinline__ int step(const DevCloud &C, Pkg &p, Rng &r, float kabs, float ksca,
+                                    float g, unsigned long long *tally, uint32_t max_steps)
+{
+    if (p.steps >= max_steps) { p.pend += p.W; p.W = 0; return kCapped; }
+    ++p.steps;
+    float s = __int_as_float(0x7f800000);     // +inf
+    int ax = -1;
+    if (p.dx != 0.0f) {
+        const float si = __fmul_rn(__fsub_rn(p.dx > 0.0f ? 1.0f : 0.0f, p.x), p.ix);
+        if (si < s) { s = si; ax = 0; }
+    }
+    if (p.dy != 0.0f) {
+        const float si = __fmul_rn(__fsub_rn(p.dy > 0.0f ? 1.0f : 0.0f, p.y), p.iy);
+        if (si < s) { s = si; ax = 1; }
+    }
+    if (p.dz != 0.0f) {
+        const float si = __fmul_rn(__fsub_rn(p.dz > 0.0f ? 1.0f : 0.0f, p.z), p.iz);
+        if (si < s) { s = si; ax = 2; }
+    }
+    if (ax < 0) { p.pend += p.W; p.W = 0; return kCapped; }     // no exit face: end safely
+    const float ksh = __fmul_rn(__fmul_rn(p.rho, ksca), p.h);
+    const float dtau = __fmul_rn(ksh, s);
+    float sp = s;
+    bool scatter = false;
+    if (ksh > 0.0f && dtau >= p.tauf) {
+        sp = fminf(__fdiv_rn(p.tauf, ksh), s);
+        scatter = true;
+    }
+    const float tau_abs = __fmul_rn(__fmul_rn(__fmul_rn(p.rho, kabs), p.h), sp);
+    if (tau_abs > 0.0f) {
+        const float q = one_minus_exp(tau_abs);
+        uint64_t dep = __float2ull_rn(__fmul_rn(__ull2float_rn(p.W), q));
+        dep = dep > p.W ? p.W : dep;
+        p.W -= dep;
+        p.pend += dep;
+    }
+    if (p.W < kWMin) { p.pend += p.W; p.W = 0; return kAbsorbed; }
+    if (scatter) {
+        p.x = clamp01(__fadd_rn(p.x, __fmul_rn(p.dx, sp)));
+        p.y = clamp01(__fadd_rn(p.y, __fmul_rn(p.dy, sp)));
+        p.z = clamp01(__fadd_rn(p.z, __fmul_rn(p.dz, sp)));
+        hg_scatter(r, g, p);
+        set_inverse(p);
+        p.tauf = -log_pos(r.u());
+        return kContinue;
+    }
+    p.tauf = __fsub_rn(p.tauf, dtau);
+    if (p.pend) { atomicAdd(tally + p.cell, (unsigned long long)p.pend); p.pend = 0; }
+    bool up;
+    if (ax == 0) {
+        up = p.dx > 0.0f;
+        p.x = up ? 1.0f : 0.0f;
+        p.y = clamp01(__fadd_rn(p.y, __fmul_rn(p.dy, s)));
+        p.z = clamp01(__fadd_rn(p.z, __fmul_rn(p.dz, s)));
+    } else if (ax == 1) {
+        up = p.dy > 0.0f;
+        p.x = clamp01(__fadd_rn(p.x, __fmul_rn(p.dx, s)));
+        p.y = up ? 1.0f : 0.0f;
+        p.z = clamp01(__fadd_rn(p.z, __fmul_rn(p.dz, s)));
+    } else {
+        up = p.dz > 0.0f;
+        p.x = clamp01(__fadd_rn(p.x, __fmul_rn(p.dx, s)));
+        p.y = clamp01(__fadd_rn(p.y, __fmul_rn(p.dy, s)));
+        p.z = up ? 1.0f : 0.0f;
+    }
+    if (!cross_face(C, p, ax, up)) return kEscaped;
+    return kContinue;
+}
+
+__device__ __forceinline__ int find_item(const uint64_t *__restrict__ prefix, int n_items, uint64_t g)
+{
+    int lo = 0, hi = n_items;              // prefix[lo] <= g < prefix[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(reinterpret_cast<const unsigned long long *>(prefix) + mid) <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) trace_kernel(const TraceParams P)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint64_t span = (uint64_t)P.chunk * 32u;
+    uint64_t q_next = 0, q_end = 0;          // warp-uniform chunk of work indices
+    bool exhausted = false;
+
+    Pkg p;
+    Rng r;
+    p.steps = 0; p.W = 0; p.pend = 0;
+    bool active = false;
+    int item = -1;
+    const DevCloud *C = nullptr;
+    float kabs = 0.f, ksca = 0.f, g = 0.f;
+    unsigned long long *tally = nullptr;
+    uint64_t gidx = 0;
+    // per-lane statistics, flushed when the lane moves to another item
+    int acc_item = -1;
+    unsigned long long acc_esc = 0, acc_cap = 0, acc_steps = 0, acc_emit = 0;
+
+    for (;;) {
+        unsigned idle = __ballot_sync(kFull, !active);
+        while (idle && !exhausted) {
+            if (q_next >= q_end) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(P.counter, (unsigned long long)span);
+                base = __shfl_sync(kFull, base, 0);
+                if (base >= P.total) { exhausted = true; break; }
+                q_next = base;
+                q_end = min((uint64_t)base + span, P.total);
+            }
+            const int n_idle = __popc(idle);
+            const uint64_t avail = q_end - q_next;
+            const int take = avail < (uint64_t)n_idle ? (int)avail : n_idle;
+            const int rank = __popc(idle & lt_mask);
+            if (!active && rank < take) {
+                gidx = q_next + rank;
+                const int it_idx = find_item(P.prefix, P.n_items, gidx);
+                if (it_idx != item) {
+                    item = it_idx;
+                    const DevItem &IT = P.items[item];
+                    C = P.clouds + IT.cloud;
+                    const float2 kap = __ldg(C->kappa + IT.freq);
+                    kabs = kap.x; ksca = kap.y;
+                    g = __ldg(P.g_hg + IT.freq);
+                    tally = P.tally + IT.tally_offset;
+                }
+                const DevItem &IT = P.items[item];
+                const uint32_t pid = IT.pid_offset + (uint32_t)(gidx - P.prefix[item]);
+                r.init(P.seed, (uint32_t)IT.iteration, (uint32_t)IT.freq, pid, (uint32_t)IT.cloud,
+                       (uint32_t)IT.source);
+                p.steps = 0; p.pend = 0;
+                if (emit(*C, IT, pid, r, p)) {
+                    set_inverse(p);
+                    p.tauf = -log_pos(r.u());
+                    if (acc_item != item) {
+                        if (acc_item >= 0) {
+                            unsigned long long *st = P.stats + 4 * acc_item;
+                            if (acc_esc) atomicAdd(st + 0, acc_esc);
+                            if (acc_cap) atomicAdd(st + 1, acc_cap);
+                            if (acc_steps) atomicAdd(st + 2, acc_steps);
+                            if (acc_emit) atomicAdd(st + 3, acc_emit);
+                        }
+                        acc_item = item; acc_esc = acc_cap = acc_steps = acc_emit = 0;
+                    }
+                    acc_emit += p.W;
+                    active = true;
+                } else if (P.pkg_steps) {
+                    P.pkg_steps[gidx] = 0;
+                }
+            }
+            q_next += (uint64_t)take;
+            idle = __ballot_sync(kFull, !active);
+        }
+        if (!__any_sync(kFull, active)) {
+            if (exhausted) break;
+            continue;
+        }
+        if (active) {
+            const int res = step(*C, p, r, kabs, ksca, g, tally, P.max_steps);
+            if (res != kContinue) {
+                if (p.pend) atomicAdd(tally + p.cell, (unsigned long long)p.pend);
+                p.pend = 0;
+                if (res == kEscaped) acc_esc += p.W;
+                if (res == kCapped) acc_cap += 1;
+                acc_steps += p.steps;
+                if (P.pkg_steps) P.pkg_steps[gidx] = p.steps;
+                active = false;
+            }
+        }
+    }
+    if (acc_item >= 0) {
+        unsigned long long *st = P.stats + 4 * acc_item;
+        if (acc_esc) atomicAdd(st + 0, acc_esc);
+        if (acc_cap) atomicAdd(st + 1, acc_cap);
+        if (acc_steps) atomicAdd(st + 2, acc_steps);
+        if (acc_emit) atomicAdd(st + 3, acc_emit);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_trace(const TraceParams &p, int grid, int block, cudaStream_t s)
+{
+    trace_kernel<<<grid, block, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+int trace_block_limit(int block)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel, block, 0) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+}  // namespace soc

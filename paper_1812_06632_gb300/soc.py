@@ -1,0 +1,234 @@
+"""ctypes binding of libsoc (include/soc.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts NumPy
+arrays / torch tensors to pointers and raises on error statuses.  It raises
+at import time if libsoc.so has not been built (there is no fallback).
+Device buffers are torch CUDA tensors owned by the caller.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsoc.so")
+
+SOC_OK = 0
+SOC_ERR_STEP_LIMIT = -4
+SRC_BACKGROUND, SRC_POINT, SRC_DUST = 0, 1, 2
+W_UNIT = 1 << 32
+
+EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "soc_dust_upload",
+           "soc_sources_upload", "soc_simulate_frequency_batch", "soc_package_energy",
+           "soc_dust_emission", "soc_absorbed_power", "soc_update_temperature", "soc_iterate",
+           "soc_set_launch", "soc_set_max_steps"]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("n_levels", C.c_int32),
+                ("cells_per_level", C.c_void_p), ("rho", C.c_void_p), ("first_child", C.c_void_p),
+                ("parent", C.c_void_p), ("root_cell_size", C.c_double)]
+
+
+class BatchItem(C.Structure):
+    _fields_ = [("cloud", C.c_int32), ("freq", C.c_int32), ("source", C.c_int32),
+                ("iteration", C.c_int32), ("pid_offset", C.c_uint64), ("n_packages", C.c_uint64),
+                ("w0", C.c_uint64), ("tally_offset", C.c_int64), ("d_dust_w", C.c_void_p),
+                ("n_per_cell", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class IterateParams(C.Structure):
+    _fields_ = [("n_background", C.c_uint64), ("n_point", C.c_uint64), ("n_per_cell", C.c_uint32),
+                ("max_iter", C.c_int32), ("dT_tol", C.c_double)]
+
+
+class IterateResult(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("final_max_dT", C.c_double),
+                ("steps", C.c_int64), ("capped", C.c_int64)]
+
+
+class SocError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libsoc status {status}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1812_06632_gb300.build`")
+    lib = C.CDLL(LIB_PATH)
+    P, I, U64, D = C.c_void_p, C.c_int, C.c_uint64, C.c_double
+    sig = {
+        "soc_create": ([C.POINTER(P), I, U64], I),
+        "soc_destroy": ([P], None),
+        "soc_last_error": ([P], C.c_char_p),
+        "soc_grid_upload": ([P, C.POINTER(GridDesc), C.POINTER(I)], I),
+        "soc_dust_upload": ([P, I, P, P, P, P], I),
+        "soc_sources_upload": ([P, I, P, I, P, P], I),
+        "soc_simulate_frequency_batch": ([P, P, I, P, P, P, P], I),
+        "soc_package_energy": ([P, I, I, U64, P], I),
+        "soc_dust_emission": ([P, I, P, I, I, C.c_uint32, P, P, P], I),
+        "soc_absorbed_power": ([P, I, P, C.c_int64, P, P, P, P], I),
+        "soc_update_temperature": ([P, I, P, P, P, P], I),
+        "soc_iterate": ([P, I, C.POINTER(IterateParams), P, P, C.POINTER(IterateResult), P, P], I),
+        "soc_set_launch": ([P, I, I, I], I),
+        "soc_set_max_steps": ([P, C.c_uint32], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _t_ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One libsoc context (device + seed).  Methods mirror the C-ABI."""
+
+    def __init__(self, device: int = 0, seed: int = 1):
+        h = C.c_void_p()
+        st = lib.soc_create(C.byref(h), device, seed & (2 ** 64 - 1))
+        if st != SOC_OK:
+            raise SocError(st, "soc_create failed (no CUDA device?)")
+        self.h = h
+        self.device = device
+        self.n_freq = 0
+        self.clouds = []
+
+    def close(self):
+        if self.h:
+            lib.soc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, ok=(SOC_OK,)):
+        if st not in ok:
+            raise SocError(st, lib.soc_last_error(self.h).decode())
+        return st
+
+    # -- uploads ------------------------------------------------------------
+    def grid_upload(self, cloud, *, paper_encoding: bool = False) -> int:
+        """Upload an inputs.Cloud.  With paper_encoding the links travel as
+        negative densities (the paper's format) instead of a child array."""
+        cpl = np.ascontiguousarray(cloud.cells_per_level(), np.int64)
+        if paper_encoding:
+            rho = np.ascontiguousarray(cloud.paper_encoding(), np.float32)
+            child = None
+        else:
+            rho = np.ascontiguousarray(cloud.rho, np.float32)
+            child = np.ascontiguousarray(cloud.child, np.int32)
+        parent = np.ascontiguousarray(cloud.parent, np.int32) if cloud.parent.size else None
+        d = GridDesc(cloud.nx, cloud.ny, cloud.nz, cloud.n_levels, _np_ptr(cpl), _np_ptr(rho),
+                     _np_ptr(child), _np_ptr(parent), float(cloud.ell))
+        cid = C.c_int(-1)
+        self._check(lib.soc_grid_upload(self.h, C.byref(d), C.byref(cid)))
+        self.clouds.append(cloud)
+        return cid.value
+
+    def grid_upload_raw(self, nx, ny, nz, cells_per_level, rho, first_child=None, parent=None, ell=1.0) -> int:
+        cpl = np.ascontiguousarray(cells_per_level, np.int64)
+        rho = np.ascontiguousarray(rho, np.float32)
+        fc = None if first_child is None else np.ascontiguousarray(first_child, np.int32)
+        pa = None if parent is None else np.ascontiguousarray(parent, np.int32)
+        d = GridDesc(nx, ny, nz, cpl.size, _np_ptr(cpl), _np_ptr(rho), _np_ptr(fc), _np_ptr(pa), float(ell))
+        cid = C.c_int(-1)
+        self._check(lib.soc_grid_upload(self.h, C.byref(d), C.byref(cid)))
+        return cid.value
+
+    def dust_upload(self, nu, kabs, ksca, g):
+        nu, kabs, ksca, g = (np.ascontiguousarray(a, np.float64) for a in (nu, kabs, ksca, g))
+        self._check(lib.soc_dust_upload(self.h, nu.size, _np_ptr(nu), _np_ptr(kabs), _np_ptr(ksca), _np_ptr(g)))
+        self.n_freq = nu.size
+
+    def sources_upload(self, cloud_id, bg_I=None, ps_pos=None, ps_L=None):
+        bg = None if bg_I is None else np.ascontiguousarray(bg_I, np.float64)
+        n_ps = 0 if ps_pos is None else int(np.asarray(ps_pos).shape[0])
+        pos = None if ps_pos is None else np.ascontiguousarray(ps_pos, np.float64).ravel()
+        L = None if ps_L is None else np.ascontiguousarray(ps_L, np.float64).ravel()
+        self._check(lib.soc_sources_upload(self.h, cloud_id, _np_ptr(bg), n_ps, _np_ptr(pos), _np_ptr(L)))
+
+    def set_launch(self, threads_per_block=256, blocks_per_sm=0, chunk=1):
+        self._check(lib.soc_set_launch(self.h, threads_per_block, blocks_per_sm, chunk))
+
+    def set_max_steps(self, n):
+        self._check(lib.soc_set_max_steps(self.h, n))
+
+    # -- compute ------------------------------------------------------------
+    @staticmethod
+    def items(specs):
+        """Array of BatchItem from dicts (keys as in soc_batch_item)."""
+        arr = (BatchItem * len(specs))()
+        for i, s in enumerate(specs):
+            it = arr[i]
+            it.cloud = s.get("cloud", 0)
+            it.freq = s.get("freq", 0)
+            it.source = s["source"]
+            it.iteration = s.get("iteration", 0)
+            it.pid_offset = s.get("pid_offset", 0)
+            it.n_packages = s["n_packages"]
+            it.w0 = s.get("w0", W_UNIT)
+            it.tally_offset = s.get("tally_offset", 0)
+            dw = s.get("dust_w")
+            it.d_dust_w = None if dw is None else dw.data_ptr()
+            it.n_per_cell = s.get("n_per_cell", 1)
+        return arr
+
+    def simulate(self, items, tally, stats, pkg_steps=None, stream=None):
+        """soc_simulate_frequency_batch; items from Context.items()."""
+        return self._check(lib.soc_simulate_frequency_batch(
+            self.h, C.cast(items, C.c_void_p), len(items), _t_ptr(tally), _t_ptr(stats),
+            _t_ptr(pkg_steps), _stream(stream)))
+
+    def package_energy(self, cloud_id, source, n_packages):
+        e = np.zeros(self.n_freq, np.float64)
+        self._check(lib.soc_package_energy(self.h, cloud_id, source, n_packages, _np_ptr(e)))
+        return e
+
+    def dust_emission(self, cloud_id, T, w, e_unit, n_per_cell=1, freq_lo=0, n_freq=None, stream=None):
+        n_freq = self.n_freq - freq_lo if n_freq is None else n_freq
+        self._check(lib.soc_dust_emission(self.h, cloud_id, _t_ptr(T), freq_lo, n_freq, n_per_cell,
+                                          _t_ptr(w), _t_ptr(e_unit), _stream(stream)))
+
+    def absorbed_power(self, cloud_id, tally, stride, e_unit, A_out, A_in=None, stream=None):
+        self._check(lib.soc_absorbed_power(self.h, cloud_id, _t_ptr(tally), stride, _t_ptr(e_unit),
+                                           _t_ptr(A_in), _t_ptr(A_out), _stream(stream)))
+
+    def update_temperature(self, cloud_id, A, T, max_dT=None, stream=None):
+        self._check(lib.soc_update_temperature(self.h, cloud_id, _t_ptr(A), _t_ptr(T), _t_ptr(max_dT),
+                                               _stream(stream)))
+
+    def iterate(self, cloud_id, T_out, *, n_background=0, n_point=0, n_per_cell=1, max_iter=0,
+                dT_tol=0.1, T_seed=None, stream=None):
+        p = IterateParams(n_background, n_point, n_per_cell, max_iter, dT_tol)
+        r = IterateResult()
+        hist = np.zeros(max(max_iter, 1), np.float64)
+        self._check(lib.soc_iterate(self.h, cloud_id, C.byref(p), _t_ptr(T_seed), _t_ptr(T_out), C.byref(r),
+                                    _np_ptr(hist), _stream(stream)), ok=(SOC_OK, SOC_ERR_STEP_LIMIT))
+        return dict(iterations=r.iterations, converged=bool(r.converged), final_max_dT=r.final_max_dT,
+                    steps=r.steps, capped=r.capped, history=hist[:r.iterations].copy())
