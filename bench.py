@@ -1,0 +1,348 @@
+"""Throughput of the SOC hot path on GB300: photon-cell steps per second.
+
+One step = one pass of the whole path over the 128^3 lognormal cloud
+(sigma_lnrho 1.5, P(k) ~ k^-3.5), 64 log-spaced frequencies 3e11-3e15 Hz,
+1e6 background packages per frequency (HG g = 0.5, kappa ~ nu^2 with a smooth
+albedo, 3-blackbody background): counter reset, the persistent tracer over
+all 64 frequencies in one launch, the FP64 absorbed-power integral and the
+temperature update.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  --impl reference times the CPU oracle (the reference
+arm of this project) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_STEP = 12          # 4 B cell word read + 8 B int64 counter update per photon-cell step
+N_PACKAGES = 1_000_000
+WORKLOAD = "lognormal 128^3, 64 nu (3e11-3e15 Hz), 1e6 background packages/nu, HG g=0.5, FP64 T update"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (worker processes are spawned)
+# ---------------------------------------------------------------------------
+def _oracle_worker(args):
+    sys.path.insert(0, ROOT)
+    freqs, pid_lo, n = args
+    from paper_1812_06632_gb300 import inputs as I
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity_helpers import oracle_item
+    w = _workload_cache(I)
+    steps = 0
+    t0 = time.perf_counter()
+    for f in freqs:
+        _, st, _ = oracle_item(w, 0, dict(source=0, freq=f, pid_offset=pid_lo, n_packages=n))
+        steps += st["steps"]
+    return steps, time.perf_counter() - t0
+
+
+_W = None
+
+
+def _workload_cache(I):
+    global _W
+    if _W is None:
+        _W = I.config_c2()
+    return _W
+
+
+def cpu_baseline(per_freq: int = 300, cores: int | None = None):
+    """Oracle steps/s on all 64 frequencies x per_freq packages each, split
+    over `cores` spawned processes (package ranges)."""
+    import oracle
+    oracle.build()
+    cores = cores or os.cpu_count() or 1
+    freqs = list(range(64))
+    chunks = [(freqs, k * (per_freq // cores), per_freq // cores) for k in range(cores)]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        # warm the workers (cloud generation) outside the timed part
+        pool.map(_warm, range(cores))
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, chunks)
+    wall = time.perf_counter() - t0
+    steps = sum(r[0] for r in res)
+    return dict(value=steps / wall, unit="photon-cell steps/s", cores=cores, kind="oracle",
+                sample=f"64 frequencies x {per_freq} background packages of the same 128^3 workload "
+                       f"({steps} steps, {wall:.1f} s wall on {cores} processes)")
+
+
+def _warm(_):
+    sys.path.insert(0, ROOT)
+    from paper_1812_06632_gb300 import inputs as I
+    _workload_cache(I)
+    import oracle
+    oracle.lib()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_base = cpu_baseline(args.cpu_sample)          # before the first GPU call
+
+    from paper_1812_06632_gb300 import build as B
+    B.build()
+    from paper_1812_06632_gb300 import inputs as I
+    from paper_1812_06632_gb300 import soc
+
+    w = I.config_c2(n_packages=N_PACKAGES)
+    cl = w.clouds[0]
+    nf = len(w.dust.nu)
+    ctx = soc.Context(local, w.seed)
+    ctx.dust_upload(w.dust.nu, w.dust.kabs, w.dust.ksca, w.dust.g)
+    cid = ctx.grid_upload(cl)
+    ctx.sources_upload(cid, w.bg_I[0])
+    # rank r traces package ids [r N, (r+1) N) of every frequency (weak scaling)
+    specs = [dict(source=0, freq=f, pid_offset=rank * N_PACKAGES, n_packages=N_PACKAGES,
+                  tally_offset=f * cl.n_cells) for f in range(nf)]
+    items = ctx.items(specs)
+    stream = torch.cuda.Stream()
+    tally = torch.zeros(nf * cl.n_cells, dtype=torch.int64, device="cuda")
+    stats = torch.zeros((nf, 4), dtype=torch.int64, device="cuda")
+    e_host = ctx.package_energy(cid, 0, N_PACKAGES * world)
+    e_unit = torch.from_numpy(e_host).cuda()
+    A = torch.zeros(cl.n_cells, dtype=torch.float64, device="cuda")
+    T = torch.full((cl.n_cells,), 2.7, dtype=torch.float32, device="cuda")
+    dT = torch.zeros(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step(ev=None):
+        with torch.cuda.stream(stream):
+            tally.zero_()
+            stats.zero_()
+            if ev:
+                ev[0].record(stream)
+            ctx.simulate(items, tally, stats, stream=stream)
+            if ev:
+                ev[1].record(stream)
+            if world > 1:
+                dist.all_reduce(tally)
+            ctx.absorbed_power(cid, tally, cl.n_cells, e_unit, A, stream=stream)
+            ctx.update_temperature(cid, A, T, dT, stream=stream)
+            if ev:
+                ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    step_steps = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))                      # L2 flush between steps, outside the events
+            step(evs[k])
+            step_steps.append(stats[:, 2].sum())
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_step = [evs[k][0].elapsed_time(evs[k][2]) for k in range(args.steps)]      # ms
+    t_trace = [evs[k][0].elapsed_time(evs[k][1]) for k in range(args.steps)]
+    steps_per_step = float(torch.stack(step_steps).double().mean().item())
+    ms = sum(t_step) / args.steps
+    ms_trace = sum(t_trace) / args.steps
+    if world > 1:
+        t = torch.tensor([ms, steps_per_step], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_all, total_steps = mx[0].item(), sm[1].item()
+    else:
+        ms_all, total_steps = ms, steps_per_step
+    value = total_steps / (ms_all / 1e3)
+
+    # end to end through the public API with host buffers: upload the grid and
+    # sources from host memory, run iteration 0 (tracer + absorbed power + T),
+    # read T back into pinned host memory
+    e2e = None
+    if world == 1 and args.e2e_steps > 0:
+        T_host = torch.empty(cl.n_cells, dtype=torch.float32).pin_memory()
+        rho = np.ascontiguousarray(cl.rho, np.float32)
+        child = np.ascontiguousarray(cl.child, np.int32)
+        h2d = rho.nbytes + child.nbytes + cl.cells_per_level().nbytes + w.bg_I[0].nbytes
+        times = []
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c2 = ctx.grid_upload(cl)
+            ctx.sources_upload(c2, w.bg_I[0])
+            T2 = torch.empty(cl.n_cells, dtype=torch.float32, device="cuda")
+            r = ctx.iterate(c2, T2, n_background=N_PACKAGES, max_iter=0, stream=stream)
+            with torch.cuda.stream(stream):
+                T_host.copy_(T2, non_blocking=True)
+            stream.synchronize()
+            dt = time.perf_counter() - t0
+            ctx.grid_free(c2)
+            if k > 0:
+                times.append((dt, r["steps"]))
+        tot = sum(t for t, _ in times)
+        e2e = {"value": sum(s for _, s in times) / tot, "unit": "photon-cell steps/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(T_host.numel() * 4),
+               "ms_per_step": 1e3 * tot / len(times)}
+
+    peaks, peak_kind = _peaks()
+    bytes_trace = steps_per_step * BYTES_PER_STEP
+    achieved = bytes_trace / (ms_trace / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "trace_kernel", "peak_source": f"{peak_kind} hbm_gbs (copy)",
+                "bytes_per_unit": BYTES_PER_STEP, "units_per_launch": steps_per_step,
+                "ms_per_launch": ms_trace}
+    out = {
+        "metric": "photon-cell steps/s", "value": value, "unit": "photon-cell steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": int(cl.n_cells), "frequencies": nf,
+                   "packages_per_frequency": N_PACKAGES * world, "steps_per_pass": total_steps,
+                   "l2": "512 MiB buffer written between steps, outside the step events",
+                   "parallelism": f"package shards x{world}" if world > 1 else "single GPU"},
+        "roofline": roofline, "gpu_launches": 3 * args.steps, "e2e": e2e,
+        "cpu_baseline": cpu_base,
+    }
+    if rank == 0:
+        out["clocks"] = clk.summary()
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = []
+    cb = None
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(args.cpu_sample)
+        if k >= args.warmup:
+            per_step.append(cb)
+    v = statistics.mean(c["value"] for c in per_step)
+    steps_per_pass = None
+    out = {"impl": "reference", "metric": "photon-cell steps/s", "value": v, "unit": "photon-cell steps/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "steps_per_pass": steps_per_pass},
+           "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": v,
+                            "unit": "photon-cell steps/s"},
+           "e2e": {"value": v, "unit": "photon-cell steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=4096, help="oracle packages per frequency")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

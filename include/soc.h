@@ -89,6 +89,16 @@ typedef struct soc_grid_desc {
 
 soc_status soc_grid_upload(soc_ctx *ctx, const soc_grid_desc *desc, int *cloud_id);
 
+/* Release the device memory of an uploaded grid (and of its sources and
+ * iteration buffers).  The id is not reused; later calls naming it fail with
+ * SOC_ERR_ARG.  Synchronous: waits for the device to finish using it. */
+soc_status soc_grid_free(soc_ctx *ctx, int cloud_id);
+
+/* Host-only check of a grid description with the rules of soc_grid_upload
+ * (needs no device and no context).  SOC_OK or SOC_ERR_ARG / SOC_ERR_GRID;
+ * msg (host, msg_len bytes, may be NULL) receives the reason. */
+soc_status soc_grid_validate(const soc_grid_desc *desc, char *msg, int msg_len);
+
 /* ------------------------------------------------------------------------
  * soc_dust_upload -- dust properties on the fixed frequency grid (paper
  * Sect. 2.1.1: cross sections for absorption and scattering and the
@@ -259,8 +269,9 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *par
 
 /* ------------------------------------------------------------------------
  * Launch configuration of the tracer (autotuner hook).  threads_per_block in
- * {32, 64, ..., 1024}; blocks_per_sm >= 1 (0 = occupancy maximum); chunk =
- * packages a warp takes per lane from the global work counter (>= 1).
+ * {32, 64, ..., 256}; blocks_per_sm >= 1 (0 = occupancy maximum); chunk in
+ * [1, 1024] = packages per lane that a warp takes from the global work
+ * counter at a time.
  * Results do not depend on these settings.
  * ------------------------------------------------------------------------ */
 soc_status soc_set_launch(soc_ctx *ctx, int threads_per_block, int blocks_per_sm, int chunk);

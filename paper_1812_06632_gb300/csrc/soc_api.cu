@@ -46,6 +46,7 @@ struct CloudHost {
     DevBuf<float2> kappa;
     DevBuf<float> ps_pos, ps_cdf;
     int n_ps = 0;
+    bool freed = false;
     std::vector<double> bg_I;                  // [n_freq] or empty
     std::vector<double> ps_L_total;            // [n_freq]
     // iteration scratch (library owned)
@@ -165,6 +166,7 @@ soc_status check_cloud(soc_ctx *ctx, int id)
 {
     if (!ctx) return SOC_ERR_ARG;
     if (id < 0 || id >= (int)ctx->clouds.size()) return fail(ctx, SOC_ERR_ARG, "cloud id %d out of range", id);
+    if (ctx->clouds[id]->freed) return fail(ctx, SOC_ERR_ARG, "cloud id %d was freed", id);
     return SOC_OK;
 }
 
@@ -192,15 +194,32 @@ soc_status soc_create(soc_ctx **out, int device, uint64_t seed)
     return SOC_OK;
 }
 
+static void release_cloud(CloudHost *c)
+{
+    c->cell.release(); c->parent.release(); c->leaf.release(); c->rho.release();
+    c->volume.release(); c->kappa.release(); c->ps_pos.release(); c->ps_cdf.release();
+    c->tally.release(); c->A_const.release(); c->A.release(); c->dust_w.release();
+    c->e_unit.release(); c->stats.release();
+    c->freed = true;
+}
+
+soc_status soc_grid_free(soc_ctx *ctx, int cloud_id)
+{
+    soc_status st = check_cloud(ctx, cloud_id);
+    if (st) return st;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaDeviceSynchronize(), "synchronize before free");
+    release_cloud(ctx->clouds[cloud_id]);
+    ctx->clouds_dirty = true;
+    return SOC_OK;
+}
+
 void soc_destroy(soc_ctx *ctx)
 {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     for (CloudHost *c : ctx->clouds) {
-        c->cell.release(); c->parent.release(); c->leaf.release(); c->rho.release();
-        c->volume.release(); c->kappa.release(); c->ps_pos.release(); c->ps_cdf.release();
-        c->tally.release(); c->A_const.release(); c->A.release(); c->dust_w.release();
-        c->e_unit.release(); c->stats.release();
+        release_cloud(c);
         delete c;
     }
     ctx->d_clouds.release(); ctx->d_g.release(); ctx->d_w.release(); ctx->d_w_kabs.release();
@@ -231,24 +250,33 @@ soc_status soc_set_max_steps(soc_ctx *ctx, uint32_t max_steps)
     return SOC_OK;
 }
 
-soc_status soc_grid_upload(soc_ctx *ctx, const soc_grid_desc *d, int *cloud_id)
+namespace {
+
+struct GridCheck {
+    std::vector<int64_t> start;
+    std::vector<int32_t> child, parent;
+    int64_t n = 0, n_root = 0;
+};
+
+// Host validation of a grid description (paper Sect. 2.1.1 layout).
+soc_status validate_grid(soc_ctx *ctx, const soc_grid_desc *d, GridCheck &g)
 {
-    if (!ctx || !d || !cloud_id || !d->rho || !d->cells_per_level) return fail(ctx, SOC_ERR_ARG, "null argument");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (!d || !d->rho || !d->cells_per_level) return fail(ctx, SOC_ERR_ARG, "null argument");
     if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(ctx, SOC_ERR_ARG, "root grid must be >= 1 cell per axis");
     if (d->n_levels < 1 || d->n_levels > SOC_MAX_LEVELS) return fail(ctx, SOC_ERR_ARG, "n_levels out of [1, 16]");
     if (!(d->root_cell_size > 0.0) || !std::isfinite(d->root_cell_size))
         return fail(ctx, SOC_ERR_ARG, "root_cell_size must be positive");
     const int64_t n_root = (int64_t)d->nx * d->ny * d->nz;
+    if (n_root >= (int64_t)1 << 31) return fail(ctx, SOC_ERR_GRID, "more than 2^31 - 1 root cells");
     std::vector<int64_t> start(d->n_levels + 1, 0);
     for (int L = 0; L < d->n_levels; ++L) {
         const int64_t c = d->cells_per_level[L];
         if (c < 0 || (L == 0 && c != n_root) || (L > 0 && c % 8 != 0))
             return fail(ctx, SOC_ERR_GRID, "cells_per_level[%d] = %lld is inconsistent", L, (long long)c);
         start[L + 1] = start[L] + c;
+        if (start[L + 1] >= (int64_t)1 << 31) return fail(ctx, SOC_ERR_GRID, "more than 2^31 - 1 cells");
     }
     const int64_t n = start[d->n_levels];
-    if (n >= (int64_t)1 << 31) return fail(ctx, SOC_ERR_GRID, "more than 2^31 - 1 cells");
     const int64_t n_oct = (n - n_root) / 8;
     std::vector<int32_t> child(n, -1);
     for (int64_t c = 0; c < n; ++c) {
@@ -285,6 +313,42 @@ soc_status soc_grid_upload(soc_ctx *ctx, const soc_grid_desc *d, int *cloud_id)
         if (d->parent && d->parent[k] != parent[k])
             return fail(ctx, SOC_ERR_GRID, "parent[%lld] = %d, links say %d", (long long)k, d->parent[k], parent[k]);
     }
+    g.start.swap(start);
+    g.child.swap(child);
+    g.parent.swap(parent);
+    g.n = n;
+    g.n_root = n_root;
+    return SOC_OK;
+}
+
+thread_local std::string g_validate_msg;
+
+}  // namespace
+
+extern "C" soc_status soc_grid_validate(const soc_grid_desc *desc, char *msg, int msg_len)
+{
+    soc_ctx tmp;
+    GridCheck g;
+    soc_status st = validate_grid(&tmp, desc, g);
+    if (msg && msg_len > 0) {
+        strncpy(msg, st == SOC_OK ? "ok" : tmp.err.c_str(), (size_t)msg_len - 1);
+        msg[msg_len - 1] = '\0';
+    }
+    return st;
+}
+
+extern "C" soc_status soc_grid_upload(soc_ctx *ctx, const soc_grid_desc *d, int *cloud_id)
+{
+    if (!ctx || !cloud_id) return fail(ctx, SOC_ERR_ARG, "null argument");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    GridCheck g;
+    soc_status vs = validate_grid(ctx, d, g);
+    if (vs != SOC_OK) return vs;
+    const int64_t n = g.n, n_root = g.n_root, n_oct = (int64_t)g.parent.size();
+    std::vector<int64_t> &start = g.start;
+    std::vector<int32_t> &child = g.child;
+    std::vector<int32_t> &parent = g.parent;
+    int lv = 0;
     // device images
     std::vector<uint32_t> word(n);
     std::vector<float> rho(n);
@@ -292,7 +356,6 @@ soc_status soc_grid_upload(soc_ctx *ctx, const soc_grid_desc *d, int *cloud_id)
     std::vector<int32_t> leaf;
     leaf.reserve(n);
     const double ell3 = (d->root_cell_size * d->root_cell_size) * d->root_cell_size;
-    lv = 0;
     for (int64_t c = 0; c < n; ++c) {
         while (c >= start[lv + 1]) ++lv;
         vol[c] = std::ldexp(ell3, -3 * lv);
@@ -475,7 +538,8 @@ soc_status soc_simulate_frequency_batch(soc_ctx *ctx, const soc_batch_item *item
     std::vector<uint64_t> prefix(n_items + 1, 0);
     for (int i = 0; i < n_items; ++i) {
         const soc_batch_item &it = items[i];
-        if (it.cloud < 0 || it.cloud >= (int)ctx->clouds.size()) return fail(ctx, SOC_ERR_ARG, "item %d: bad cloud", i);
+        if (it.cloud < 0 || it.cloud >= (int)ctx->clouds.size() || ctx->clouds[it.cloud]->freed)
+            return fail(ctx, SOC_ERR_ARG, "item %d: bad or freed cloud", i);
         const CloudHost &cl = *ctx->clouds[it.cloud];
         if (it.freq < 0 || it.freq >= ctx->n_freq) return fail(ctx, SOC_ERR_ARG, "item %d: bad freq", i);
         if (it.iteration < 0 || it.iteration > 65535) return fail(ctx, SOC_ERR_ARG, "item %d: bad iteration", i);

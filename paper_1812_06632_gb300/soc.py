@@ -20,7 +20,8 @@ SOC_ERR_STEP_LIMIT = -4
 SRC_BACKGROUND, SRC_POINT, SRC_DUST = 0, 1, 2
 W_UNIT = 1 << 32
 
-EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "soc_dust_upload",
+EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "soc_grid_validate", "soc_grid_free",
+           "soc_dust_upload",
            "soc_sources_upload", "soc_simulate_frequency_batch", "soc_package_energy",
            "soc_dust_emission", "soc_absorbed_power", "soc_update_temperature", "soc_iterate",
            "soc_set_launch", "soc_set_max_steps"]
@@ -65,6 +66,8 @@ def _load():
         "soc_destroy": ([P], None),
         "soc_last_error": ([P], C.c_char_p),
         "soc_grid_upload": ([P, C.POINTER(GridDesc), C.POINTER(I)], I),
+        "soc_grid_validate": ([C.POINTER(GridDesc), C.c_char_p, I], I),
+        "soc_grid_free": ([P, I], I),
         "soc_dust_upload": ([P, I, P, P, P, P], I),
         "soc_sources_upload": ([P, I, P, I, P, P], I),
         "soc_simulate_frequency_batch": ([P, P, I, P, P, P, P], I),
@@ -101,6 +104,24 @@ def _stream(stream):
     if isinstance(stream, int):
         return C.c_void_p(stream)
     return C.c_void_p(stream.cuda_stream)
+
+
+def grid_desc(nx, ny, nz, cells_per_level, rho, first_child=None, parent=None, ell=1.0):
+    """GridDesc plus the arrays it points into (keep them alive together)."""
+    keep = [np.ascontiguousarray(cells_per_level, np.int64), np.ascontiguousarray(rho, np.float32),
+            None if first_child is None else np.ascontiguousarray(first_child, np.int32),
+            None if parent is None else np.ascontiguousarray(parent, np.int32)]
+    d = GridDesc(nx, ny, nz, keep[0].size, _np_ptr(keep[0]), _np_ptr(keep[1]), _np_ptr(keep[2]),
+                 _np_ptr(keep[3]), float(ell))
+    return d, keep
+
+
+def validate_grid(nx, ny, nz, cells_per_level, rho, first_child=None, parent=None, ell=1.0):
+    """soc_grid_validate: (status, message); host only, no GPU needed."""
+    d, keep = grid_desc(nx, ny, nz, cells_per_level, rho, first_child, parent, ell)
+    buf = C.create_string_buffer(512)
+    st = lib.soc_grid_validate(C.byref(d), buf, 512)
+    return st, buf.value.decode()
 
 
 class Context:
@@ -160,6 +181,9 @@ class Context:
         cid = C.c_int(-1)
         self._check(lib.soc_grid_upload(self.h, C.byref(d), C.byref(cid)))
         return cid.value
+
+    def grid_free(self, cloud_id):
+        self._check(lib.soc_grid_free(self.h, cloud_id))
 
     def dust_upload(self, nu, kabs, ksca, g):
         nu, kabs, ksca, g = (np.ascontiguousarray(a, np.float64) for a in (nu, kabs, ksca, g))

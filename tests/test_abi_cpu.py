@@ -1,0 +1,80 @@
+"""C-ABI checks that need no GPU: every symbol declared in include/soc.h is
+exported by libsoc.so, and the host-side grid validation accepts the paper's
+layout and rejects malformed grids."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1812_06632_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "soc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(soc_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(libsoc):
+    names = _declared()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(libsoc.lib, n), n
+    assert set(libsoc.EXPORTS) == set(names)
+
+
+def _v(libsoc, cl, **over):
+    args = dict(nx=cl.nx, ny=cl.ny, nz=cl.nz, cells_per_level=cl.cells_per_level(), rho=cl.rho,
+                first_child=cl.child, parent=cl.parent if cl.parent.size else None, ell=cl.ell)
+    args.update(over)
+    return libsoc.validate_grid(**args)
+
+
+def test_valid_grids(libsoc):
+    reg = I.regular(np.ones((3, 4, 5), np.float32))
+    assert _v(libsoc, reg)[0] == 0
+    oc = I.config_c3(root_n=8, max_refine=2, threshold=3.0).clouds[0]
+    assert oc.n_levels == 3
+    assert _v(libsoc, oc)[0] == 0
+    # the paper's encoding: links as negative densities, no child array
+    assert _v(libsoc, oc, rho=oc.paper_encoding(), first_child=None)[0] == 0
+    # parent array may be omitted
+    assert _v(libsoc, oc, parent=None)[0] == 0
+
+
+@pytest.mark.parametrize("case", ["link_range", "link_level", "two_parents", "orphan", "nan", "neg",
+                                  "parent_mismatch", "cpl", "bad_paper_link", "ell"])
+def test_malformed_grids_rejected(libsoc, case):
+    oc = I.config_c3(root_n=8, max_refine=2, threshold=3.0).clouds[0]
+    child, rho, parent = oc.child.copy(), oc.rho.copy(), oc.parent.copy()
+    over = {}
+    refined = np.nonzero(child >= 0)[0]
+    leaves = np.nonzero(child < 0)[0]
+    if case == "link_range":
+        child[refined[0]] = oc.n_cells + 8
+    elif case == "link_level":                      # points into its own level
+        child[refined[0]] = 0
+    elif case == "two_parents":
+        child[refined[1]] = child[refined[0]]
+    elif case == "orphan":
+        child[refined[-1]] = -1
+    elif case == "nan":
+        rho[leaves[3]] = np.nan
+    elif case == "neg":
+        rho[leaves[5]] = -1.0
+    elif case == "parent_mismatch":
+        parent[0] = parent[1]
+    elif case == "cpl":
+        over["cells_per_level"] = oc.cells_per_level() + np.array([0, 1, 0])
+    elif case == "bad_paper_link":
+        rho = oc.paper_encoding()
+        rho[refined[0]] = -float(child[refined[0]]) - 0.5
+        child = None
+    elif case == "ell":
+        over["ell"] = 0.0
+    st, msg = _v(libsoc, oc, rho=rho, first_child=child, parent=parent, **over)
+    assert st in (-1, -2), (case, st, msg)
+    assert msg and msg != "ok"
