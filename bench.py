@@ -159,6 +159,10 @@ class Clocks:
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_gpu(args):
+    global N_PACKAGES, WORKLOAD
+    if args.packages != N_PACKAGES:
+        N_PACKAGES = args.packages
+        WORKLOAD = WORKLOAD.replace("1e6 background", f"{N_PACKAGES:.0e} background")
     import torch
     import torch.distributed as dist
 
@@ -337,6 +341,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=4096, help="oracle packages per frequency")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--packages", type=int, default=N_PACKAGES,
+                    help="packages per frequency (smaller only for profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -74,7 +74,8 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            _lib = C.CDLL(build())
+            # SOC_ORACLE_LIB: a deliberately broken copy, for the mutation tests
+            _lib = C.CDLL(os.environ.get("SOC_ORACLE_LIB") or build())
             P = C.c_void_p
             _lib.oracle_philox4x32_10.argtypes = [P, P, P]
             _lib.oracle_u01.argtypes = [C.c_uint32]

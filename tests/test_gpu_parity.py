@@ -276,7 +276,10 @@ def test_dust_emission_weights_match_oracle():
         Wo, eo = P.dust_weights(L, 3)
         d = np.abs(Wg[f].astype(np.int64) - Wo.astype(np.int64))
         assert d.max() <= 1, (f, d.max())
-        assert abs(eg[f] / eo - 1) < 1e-13
+        if eo == 0.0:                          # B_nu(T) underflows for every cell
+            assert eg[f] == 0.0 and np.all(Wg[f] == 0)
+        else:
+            assert abs(eg[f] / eo - 1) < 1e-13
 
 
 def test_iterate_matches_oracle_driven_iteration():

@@ -1,0 +1,50 @@
+"""The pins catch plausible mistakes: each case plants one slip in a copy of
+the oracle's C source (on the CPU), builds it, and runs the pins against it
+in a subprocess; the pins must fail.  The oracle itself is never modified."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "soc_oracle.c")
+
+MUTANTS = {
+    "uniform_not_cosine_entry": ("float mu = sqrtf(u);                 /* cosine-weighted inward angle */",
+                                 "float mu = u;"),
+    "exp_drops_ln2_lo": ("float r = (x - t * LN2_HI) - t * LN2_LO;", "float r = (x - t * LN2_HI);"),
+    "log_drops_ln2_lo": ("return (t * LN2_LO + lm) + t * LN2_HI;", "return lm + t * LN2_HI;"),
+    "series_one_term_short": ("for (int k = 8; k >= 2; --k)", "for (int k = 8; k >= 3; --k)"),
+    "hg_sign": ("mu = ((1.0f + g2) - tmp * tmp) / (g + g);", "mu = ((1.0f + g2) - tmp) / (g + g);"),
+    "rotation_sign": ("ny = (sint * ((dy * dz) * c + dx * s)) / t + dy * mu;",
+                      "ny = (sint * ((dy * dz) * c - dx * s)) / t + dy * mu;"),
+    "sibling_entry_side": ("if (up && b == 0) { p->cell += 1 << a; p->x[a] = 0.0f;",
+                           "if (up && b == 0) { p->cell += 1 << a; p->x[a] = 1.0f;"),
+    "climb_drops_octant": ("p->x[i] = (p->x[i] + (float)((oct >> i) & 1)) * 0.5f;", "p->x[i] = p->x[i] * 0.5f;"),
+    "level_scale_kept": ("        p->h = p->h * 0.5f;\n        p->cell = G->child", "        p->cell = G->child"),
+    "face_area_swap": ("cum[1] = cum[0] + ax; cum[2] = cum[1] + ay;", "cum[1] = cum[0] + ay; cum[2] = cum[1] + ax;"),
+    "free_path_halved": ("tauf = -oracle_log(rng_u(r));\n            continue;",
+                         "tauf = -0.5f * oracle_log(rng_u(r));\n            continue;"),
+    "point_source_hemisphere": ("float mu = 2.0f * rng_u(r) - 1.0f;\n    float c, s;\n    disk_azimuth(r, &c, &s);\n    float sint",
+                                "float mu = rng_u(r);\n    float c, s;\n    disk_azimuth(r, &c, &s);\n    float sint"),
+    "escape_not_counted": ("            st->escaped += (int64_t)p.W;\n", ""),
+    "philox_key_bump": ("k0 += PHILOX_W0; k1 += PHILOX_W1;", "k0 += PHILOX_W1; k1 += PHILOX_W0;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    mut = tmp_path / "mut.c"
+    mut.write_text(src.replace(old, new, 1))
+    so = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                    "-o", str(so), str(mut), "-lm"], check=True)
+    env = dict(os.environ, SOC_ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"

@@ -120,6 +120,25 @@ def test_pencil_beam_oblique_path_length():
     assert abs(st["escaped"] / oracle.W_UNIT / math.exp(-kabs * L) - 1) < 2e-5
 
 
+def test_unscattered_fraction_is_exp_minus_tau_sca():
+    """Pencil beams up a column with albedo 0.5: a package that never scatters
+    leaves through the top with one exact weight; the fraction of such
+    packages is exp(-tau_sca) (free paths drawn in scattering optical depth)."""
+    n, ksca, kabs = 8, 0.125, 0.125                       # tau_sca = tau_abs = 1
+    cl = I.regular(np.ones((n, 9, 9), np.float32))
+    G = _grid(cl)
+    straight, _, _ = oracle.trace_pencil(G, [4.5, 4.5, 0.0], [0.0, 0.0, 1.0], kabs=kabs)
+    w_straight = oracle.W_UNIT - int(straight.sum())
+    M = 6000
+    hits = 0
+    for pid in range(M):
+        t, st, _ = oracle.trace_pencil(G, [4.5, 4.5, 0.0], [0.0, 0.0, 1.0], kabs=kabs, ksca=ksca, g=0.3,
+                                       seed=77, pid=pid)
+        hits += st["escaped"] == w_straight
+    p = math.exp(-ksca * n)
+    assert abs(hits / M - p) < 4 * math.sqrt(p * (1 - p) / M)
+
+
 def test_zero_density_cells_are_transparent():
     n = 10
     rho = np.zeros((n, 1, 1), np.float32)
@@ -189,16 +208,18 @@ def test_same_seed_same_result_other_seed_differs():
 # ----------------------------------------------------------------------------
 # radiation-field normalisation
 # ----------------------------------------------------------------------------
-def test_background_thin_cube_absorbs_4pi_kappa_I():
+@pytest.mark.parametrize("shape", [(8, 8, 8), (4, 6, 10)])
+def test_background_thin_box_absorbs_4pi_kappa_I(shape):
     """Inside an optically thin box in an isotropic field I, every cell absorbs
     4 pi kabs I per unit rho V (J = I).  Pins the cosine-weighted entry, the
-    face choice and the energy per package (pi I S / N)."""
-    n, ell, kabs, I_nu = 8, 2.0, 1e-4, 3.0
-    cl = I.regular(np.ones((n, n, n), np.float32), ell=ell)
+    face choice by area (non-cubic box) and the energy per package (pi I S / N)."""
+    nz, ny, nx = shape
+    ell, kabs, I_nu = 2.0, 1e-4, 3.0
+    cl = I.regular(np.ones(shape, np.float32), ell=ell)
     N = 200_000
     tally, st, _ = oracle.trace(_grid(cl), source=0, kabs=kabs * ell, ksca=0.0, seed=11, n_packages=N)
-    e = P.background_package_energy([I_nu], n, n, n, ell, N)
-    A = P.absorbed_power(tally[None, :], e, [1.0], cl.rho, cl.volumes())
+    e = P.background_package_energy([I_nu], nx, ny, nz, ell, N)
+    A = P.absorbed_power(tally[None, :], e, [1.0], cl.rho, P.cell_volumes(_grid(cl), ell))
     ratio = A / (4 * np.pi * kabs * I_nu)
     assert abs(ratio.mean() - 1) < 4e-3
     assert np.all(np.abs(ratio - 1) < 0.12)
@@ -240,6 +261,12 @@ def test_point_source_inverse_square():
         vals.append(absorbed[m].mean())
     slope = np.polyfit(np.log(mids), np.log(vals), 1)[0]
     assert abs(slope + 2) < 0.05
+    # isotropy: the six half-spaces around the source absorb equal shares
+    a3 = absorbed.reshape(n, n, n)
+    h = n // 2
+    halves = [a3[:h].sum(), a3[h:].sum(), a3[:, :h].sum(), a3[:, h:].sum(), a3[:, :, :h].sum(), a3[:, :, h:].sum()]
+    tot = a3.sum()
+    assert max(abs(x / tot - 0.5) for x in halves) < 0.01
 
 
 def _cube_transmission_quadrature(tau_side, n=96):
@@ -312,6 +339,28 @@ def test_octree_refinement_does_not_change_root_absorption():
 # ----------------------------------------------------------------------------
 # scattering
 # ----------------------------------------------------------------------------
+@pytest.mark.parametrize("g", [0.0, 0.5])
+def test_mean_square_absorption_distance_point_source(g):
+    """Point source in a (practically) infinite uniform medium, absorption as
+    continuous attenuation, Poisson scattering with mean cosine g: the
+    direction autocorrelation along the path is exp(-ks (1-g) l), so the
+    energy-weighted mean square distance of absorption from the source is
+    exactly 2 / (ka (ka + ks (1 - g))).  Pins the free-path draws after every
+    scattering and the transport effect of the phase function."""
+    n, ka, ks = 96, 0.1, 0.3
+    cl = I.regular(np.ones((n, n, n), np.float32))
+    c = n / 2
+    N = 20_000
+    tally, st, _ = oracle.trace(_grid(cl), source=1, kabs=ka, ksca=ks, g=g, seed=13, n_packages=N,
+                                ps_pos=np.array([[c, c, c]]), ps_cdf=np.float32([1.0]))
+    assert st["escaped"] < 1e-3 * st["emitted"]
+    idx = np.nonzero(tally)[0]
+    i, j, k = idx % n, (idx // n) % n, idx // (n * n)
+    r2 = (i + 0.5 - c) ** 2 + (j + 0.5 - c) ** 2 + (k + 0.5 - c) ** 2 + 0.25   # cell average of r^2
+    m = np.sum(tally[idx] * r2) / tally[idx].sum()
+    expect = 2.0 / (ka * (ka + ks * (1 - g)))
+    assert abs(m / expect - 1) < 0.04, (m, expect)
+
 @pytest.mark.parametrize("g", [0.0, 0.5, -0.3, 0.9])
 def test_hg_moments(g):
     n = 200_000
