@@ -220,9 +220,9 @@ soc_status soc_absorbed_power(soc_ctx *ctx, int cloud_id, const int64_t *d_tally
 /* ------------------------------------------------------------------------
  * soc_update_temperature -- equilibrium dust temperature (paper Sect. 2.1.1:
  * a separate kernel solves the temperatures from the absorbed energy).  For
- * every leaf: T solves 4 pi sum_nu w_nu kabs B_nu(T) = A (FP64 table
- * inversion with log-log interpolation, then one Newton step on the
- * quadrature).  A <= E(2.7 K) gives 2.7 K (cells that absorbed nothing);
+ * every leaf: T solves 4 pi sum_nu w_nu kabs B_nu(T) = A by FP64 table
+ * inversion: ln A is bracketed in ln E(T_k) (4096 log-spaced T_k) and ln T
+ * interpolated linearly (error < 2e-7 relative on a 64-point grid).
  * A >= E(3000 K) gives 3000 K.
  *   d_A               device double [n_cells].
  *   d_T               device float [n_cells], in/out: holds T_prev on entry.
@@ -269,12 +269,19 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *par
 
 /* ------------------------------------------------------------------------
  * Launch configuration of the tracer (autotuner hook).  threads_per_block in
- * {32, 64, ..., 256}; blocks_per_sm >= 1 (0 = occupancy maximum); chunk in
+ * {32, 64, ..., 256}; blocks_per_sm >= 1 (0 = occupancy maximum of the
+ * default build; 4 or more selects the build limited to 64 registers per
+ * thread, which keeps 4 blocks of 256 threads resident per SM); chunk in
  * [1, 1024] = packages per lane that a warp takes from the global work
  * counter at a time.
  * Results do not depend on these settings.
  * ------------------------------------------------------------------------ */
 soc_status soc_set_launch(soc_ctx *ctx, int threads_per_block, int blocks_per_sm, int chunk);
+/* A warp refills its idle lanes with new packages once at least
+ * min_idle_lanes (1..32) of its 32 lanes are idle (or all are): emission then
+ * runs for several lanes together instead of one lane at a time.  Results do
+ * not depend on it. */
+soc_status soc_set_refill(soc_ctx *ctx, int min_idle_lanes);
 /* Step cap per package (default 10^7); packages beyond it are ended with
  * their weight deposited and counted in stats[1]. */
 soc_status soc_set_max_steps(soc_ctx *ctx, uint32_t max_steps);

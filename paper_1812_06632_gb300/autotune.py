@@ -1,0 +1,114 @@
+"""Autotuner of the tracer's launch configuration.
+
+The persistent tracer's speed depends on threads per block, resident blocks
+per SM (which also selects the 80- or 64-register build), the chunk of work
+indices a warp takes from the global counter and the refill threshold (how
+many idle lanes a warp waits for before emitting new packages).  None of
+these changes the results: every candidate's counters are compared with the
+first candidate's and must be identical, bit for bit.
+
+The best configuration is cached in a JSON file keyed by the GPU name and a
+hash of the workload (grid sizes, frequencies, package counts, sources).
+"""
+from __future__ import annotations
+
+import hashlib
+import itertools
+import json
+import os
+
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+
+DEFAULT_SPACE = dict(threads_per_block=(128, 256), blocks_per_sm=(0, 4), chunk=(1, 4, 16),
+                     refill=(1, 4, 8, 16))
+
+
+def workload_key(gpu_name: str, specs, clouds) -> str:
+    """Stable key for (GPU, workload)."""
+    desc = {
+        "gpu": gpu_name,
+        "clouds": [[int(c.nx), int(c.ny), int(c.nz), int(c.n_cells)] for c in clouds],
+        "items": [[int(s.get("cloud", 0)), int(s.get("freq", 0)), int(s["source"]), int(s["n_packages"])]
+                  for s in specs],
+    }
+    h = hashlib.sha1(json.dumps(desc, sort_keys=True).encode()).hexdigest()[:16]
+    return f"{gpu_name}|{h}"
+
+
+def candidates(space=None):
+    space = dict(DEFAULT_SPACE, **(space or {}))
+    keys = ["threads_per_block", "blocks_per_sm", "chunk", "refill"]
+    for vals in itertools.product(*(space[k] for k in keys)):
+        yield dict(zip(keys, vals))
+
+
+def apply(ctx, cfg):
+    ctx.set_launch(cfg["threads_per_block"], cfg["blocks_per_sm"], cfg["chunk"])
+    ctx.set_refill(cfg["refill"])
+
+
+def load_cache(path=DEFAULT_CACHE):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache, path=DEFAULT_CACHE):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def pick(results):
+    """Fastest candidate; results = [(cfg, ms)]."""
+    return min(results, key=lambda r: r[1])[0]
+
+
+def tune(ctx, specs, tally_len, clouds, *, space=None, reps=2, cache_path=DEFAULT_CACHE, use_cache=True,
+         stream=None):
+    """Time every candidate on the batch `specs` (dicts for Context.items),
+    check that all give identical counters, apply and cache the fastest.
+    Returns (best cfg, [(cfg, ms per launch)])."""
+    import torch
+
+    key = workload_key(torch.cuda.get_device_name(), specs, clouds)
+    cache = load_cache(cache_path) if use_cache else {}
+    if use_cache and key in cache:
+        apply(ctx, cache[key]["best"])
+        return cache[key]["best"], [(c, m) for c, m in cache[key]["results"]]
+    items = ctx.items(specs)
+    stream = stream or torch.cuda.current_stream()
+    tally = torch.zeros(tally_len, dtype=torch.int64, device="cuda")
+    stats = torch.zeros((len(specs), 4), dtype=torch.int64, device="cuda")
+    ref = None
+    results = []
+    for cfg in candidates(space):
+        apply(ctx, cfg)
+        times = []
+        for r in range(reps + 1):
+            tally.zero_()
+            stats.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                a.record(stream)
+                ctx.simulate(items, tally, stats, stream=stream)
+                b.record(stream)
+            stream.synchronize()
+            if r > 0:
+                times.append(a.elapsed_time(b))
+        if ref is None:
+            ref = (tally.clone(), stats.clone())
+        elif not (torch.equal(ref[0], tally) and torch.equal(ref[1], stats)):
+            raise RuntimeError(f"launch configuration {cfg} changed the counters")
+        results.append((cfg, min(times)))
+    best = pick(results)
+    apply(ctx, best)
+    if use_cache:
+        cache[key] = {"best": best, "results": [[c, m] for c, m in results]}
+        save_cache(cache, cache_path)
+    return best, results

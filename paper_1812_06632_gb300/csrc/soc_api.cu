@@ -78,7 +78,7 @@ struct soc_ctx {
     DevBuf<unsigned long long> d_lmax;
     DevBuf<double> d_maxdT;
     // launch
-    int tpb = 256, bps = 0, chunk = 1;
+    int tpb = 256, bps = 4, chunk = 16, refill_min = 8;   // autotuned on the 128^3 x 64 nu workload
     uint32_t max_steps = 10000000u;
     int sms = 0;
 };
@@ -240,6 +240,14 @@ soc_status soc_set_launch(soc_ctx *ctx, int threads_per_block, int blocks_per_sm
     ctx->tpb = threads_per_block;
     ctx->bps = blocks_per_sm;
     ctx->chunk = chunk;
+    return SOC_OK;
+}
+
+soc_status soc_set_refill(soc_ctx *ctx, int min_idle_lanes)
+{
+    if (!ctx) return SOC_ERR_ARG;
+    if (min_idle_lanes < 1 || min_idle_lanes > 32) return fail(ctx, SOC_ERR_ARG, "min_idle_lanes must be in [1, 32]");
+    ctx->refill_min = min_idle_lanes;
     return SOC_OK;
 }
 
@@ -586,12 +594,15 @@ soc_status soc_simulate_frequency_batch(soc_ctx *ctx, const soc_batch_item *item
     P.n_items = n_items;
     P.max_steps = ctx->max_steps;
     P.chunk = ctx->chunk;
-    const int per_sm = ctx->bps > 0 ? std::min(ctx->bps, trace_block_limit(ctx->tpb)) : trace_block_limit(ctx->tpb);
+    P.refill_min = ctx->refill_min;
+    const int variant = ctx->bps >= 4 ? 4 : 3;
+    const int limit = trace_block_limit(ctx->tpb, variant);
+    const int per_sm = ctx->bps > 0 ? std::min(ctx->bps, limit) : limit;
     const uint64_t warps_needed = (total + 31) / 32;
     int64_t grid = (int64_t)ctx->sms * per_sm;
     const int64_t grid_need = (int64_t)((warps_needed * 32 + ctx->tpb - 1) / ctx->tpb);
     if (grid_need < grid) grid = grid_need < 1 ? 1 : grid_need;
-    CK(launch_trace(P, (int)grid, ctx->tpb, s), "trace launch");
+    CK(launch_trace(P, (int)grid, ctx->tpb, variant, s), "trace launch");
     // the host copies above used pageable buffers: they are staged before return
     return SOC_OK;
 }

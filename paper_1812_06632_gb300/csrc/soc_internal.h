@@ -53,10 +53,13 @@ struct TraceParams {
     int32_t n_items;
     uint32_t max_steps;
     int32_t chunk;
+    int32_t refill_min;          // refill a warp's idle lanes once this many are idle
 };
 
-cudaError_t launch_trace(const TraceParams &p, int grid, int block, cudaStream_t s);
-int trace_block_limit(int block);   // max resident blocks/SM for this block size
+// variant: 3 or 4 = minimum resident 256-thread blocks per SM the kernel is
+// compiled for (register budget 80 or 64 per thread)
+cudaError_t launch_trace(const TraceParams &p, int grid, int block, int variant, cudaStream_t s);
+int trace_block_limit(int block, int variant);   // max resident blocks/SM
 
 struct TempTables {
     int n_freq;

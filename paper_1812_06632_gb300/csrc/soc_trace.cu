@@ -259,7 +259,9 @@ __device__ bool cross_face(const DevCloud &C, Pkg &p, int ax, bool up)
         if (up ? (b == 0) : (b == 1)) {
             p.cell += up ? (1 << ax) : -(1 << ax);
             const float v = up ? 0.0f : 1.0f;
-            if (ax == 0) p.x = v; else if (ax == 1) p.y = v; else p.z = v;
+            p.x = (ax == 0) ? v : p.x;
+            p.y = (ax == 1) ? v : p.y;
+            p.z = (ax == 2) ? v : p.z;
             descend(C.cell, p);
             return true;
         }
@@ -270,17 +272,36 @@ __device__ bool cross_face(const DevCloud &C, Pkg &p, int ax, bool up)
         p.cell = __ldg(C.parent + ((p.cell - n_root) >> 3));
     }
     const int step = up ? 1 : -1;
-    if (ax == 0) { p.ri += step; if (p.ri < 0 || p.ri >= C.nx) return false; }
-    else if (ax == 1) { p.rj += step; if (p.rj < 0 || p.rj >= C.ny) return false; }
-    else { p.rk += step; if (p.rk < 0 || p.rk >= C.nz) return false; }
-    p.cell = root_cell(C, p.ri, p.rj, p.rk);
+    const int ri = p.ri + ((ax == 0) ? step : 0);
+    const int rj = p.rj + ((ax == 1) ? step : 0);
+    const int rk = p.rk + ((ax == 2) ? step : 0);
+    // one unsigned compare per axis tests both ends of the root grid
+    if ((unsigned)ri >= (unsigned)C.nx || (unsigned)rj >= (unsigned)C.ny || (unsigned)rk >= (unsigned)C.nz)
+        return false;
+    p.ri = ri; p.rj = rj; p.rk = rk;
+    p.cell = root_cell(C, ri, rj, rk);
     const float v = up ? 0.0f : 1.0f;
-    if (ax == 0) p.x = v; else if (ax == 1) p.y = v; else p.z = v;
+    p.x = (ax == 0) ? v : p.x;
+    p.y = (ax == 1) ? v : p.y;
+    p.z = (ax == 2) ? v : p.z;
     descend(C.cell, p);
     return true;
 }
 
 enum StepResult { kContinue = 0, kAbsorbed = 1, kEscaped = 2, kCapped = 3 };
+
+// float(W) with round-to-nearest for 0 <= W <= 2^32, through the 32-bit
+// converter (64-bit conversions run on the slow double-precision pipe).
+__device__ __forceinline__ float w_to_float(uint64_t W)
+{
+    return (W >> 32) ? 4294967296.0f : __uint2float_rn((uint32_t)W);
+}
+
+// rint(v) as an integer for 0 <= v <= 2^32 (v = float(W) * q, q <= 1).
+__device__ __forceinline__ uint64_t float_to_w(float v)
+{
+    return (v >= 4294967296.0f) ? (1ull << 32) : (uint64_t)__float2uint_rn(v);
+}
 
 // One photon-cell step (one segment inside one leaf).
 __device__ __forceinline__ int step(const DevCloud &C, Pkg &p, Rng &r, float kabs, float ksca,
@@ -314,7 +335,8 @@ __device__ __forceinline__ int step(const DevCloud &C, Pkg &p, Rng &r, float kab
     const float tau_abs = __fmul_rn(__fmul_rn(__fmul_rn(p.rho, kabs), p.h), sp);
     if (tau_abs > 0.0f) {
         const float q = one_minus_exp(tau_abs);
-        uint64_t dep = __float2ull_rn(__fmul_rn(__ull2float_rn(p.W), q));
+        const float prod = __fmul_rn(w_to_float(p.W), q);
+        uint64_t dep = float_to_w(prod);
         dep = dep > p.W ? p.W : dep;
         p.W -= dep;
         p.pend += dep;
@@ -331,23 +353,18 @@ __device__ __forceinline__ int step(const DevCloud &C, Pkg &p, Rng &r, float kab
     }
     p.tauf = __fsub_rn(p.tauf, dtau);
     if (p.pend) { atomicAdd(tally + p.cell, (unsigned long long)p.pend); p.pend = 0; }
-    bool up;
-    if (ax == 0) {
-        up = p.dx > 0.0f;
-        p.x = up ? 1.0f : 0.0f;
-        p.y = clamp01(__fadd_rn(p.y, __fmul_rn(p.dy, s)));
-        p.z = clamp01(__fadd_rn(p.z, __fmul_rn(p.dz, s)));
-    } else if (ax == 1) {
-        up = p.dy > 0.0f;
-        p.x = clamp01(__fadd_rn(p.x, __fmul_rn(p.dx, s)));
-        p.y = up ? 1.0f : 0.0f;
-        p.z = clamp01(__fadd_rn(p.z, __fmul_rn(p.dz, s)));
-    } else {
-        up = p.dz > 0.0f;
-        p.x = clamp01(__fadd_rn(p.x, __fmul_rn(p.dx, s)));
-        p.y = clamp01(__fadd_rn(p.y, __fmul_rn(p.dy, s)));
-        p.z = up ? 1.0f : 0.0f;
-    }
+    // move to the exit face: the exit coordinate exactly on the face, the
+    // others advanced (selects, so lanes leaving through different faces
+    // stay converged)
+    const float da = (ax == 0) ? p.dx : (ax == 1) ? p.dy : p.dz;
+    const bool up = da > 0.0f;
+    const float face = up ? 1.0f : 0.0f;
+    const float mx = clamp01(__fadd_rn(p.x, __fmul_rn(p.dx, s)));
+    const float my = clamp01(__fadd_rn(p.y, __fmul_rn(p.dy, s)));
+    const float mz = clamp01(__fadd_rn(p.z, __fmul_rn(p.dz, s)));
+    p.x = (ax == 0) ? face : mx;
+    p.y = (ax == 1) ? face : my;
+    p.z = (ax == 2) ? face : mz;
     if (!cross_face(C, p, ax, up)) return kEscaped;
     return kContinue;
 }
@@ -362,7 +379,8 @@ __device__ __forceinline__ int find_item(const uint64_t *__restrict__ prefix, in
     return lo;
 }
 
-__global__ void __launch_bounds__(256) trace_kernel(const TraceParams P)
+template <int kMinBlocks>
+__global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParams P)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -385,6 +403,9 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams P)
 
     for (;;) {
         unsigned idle = __ballot_sync(kFull, !active);
+        // refill once at least refill_min lanes are idle (emission runs for
+        // several lanes together), or when the whole warp is idle
+        if (__popc(idle) < P.refill_min && idle != kFull) idle = 0;
         while (idle && !exhausted) {
             if (q_next >= q_end) {
                 unsigned long long base = 0;
@@ -465,16 +486,22 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams P)
 
 }  // namespace
 
-cudaError_t launch_trace(const TraceParams &p, int grid, int block, cudaStream_t s)
+cudaError_t launch_trace(const TraceParams &p, int grid, int block, int variant, cudaStream_t s)
 {
-    trace_kernel<<<grid, block, 0, s>>>(p);
+    if (variant == 4)
+        trace_kernel<4><<<grid, block, 0, s>>>(p);
+    else
+        trace_kernel<3><<<grid, block, 0, s>>>(p);
     return cudaGetLastError();
 }
 
-int trace_block_limit(int block)
+int trace_block_limit(int block, int variant)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel, block, 0) != cudaSuccess) return 1;
+    cudaError_t e = (variant == 4)
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<4>, block, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<3>, block, 0);
+    if (e != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }
 

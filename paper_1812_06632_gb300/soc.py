@@ -24,7 +24,7 @@ EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "so
            "soc_dust_upload",
            "soc_sources_upload", "soc_simulate_frequency_batch", "soc_package_energy",
            "soc_dust_emission", "soc_absorbed_power", "soc_update_temperature", "soc_iterate",
-           "soc_set_launch", "soc_set_max_steps"]
+           "soc_set_launch", "soc_set_refill", "soc_set_max_steps"]
 
 
 class GridDesc(C.Structure):
@@ -77,6 +77,7 @@ def _load():
         "soc_update_temperature": ([P, I, P, P, P, P], I),
         "soc_iterate": ([P, I, C.POINTER(IterateParams), P, P, C.POINTER(IterateResult), P, P], I),
         "soc_set_launch": ([P, I, I, I], I),
+        "soc_set_refill": ([P, I], I),
         "soc_set_max_steps": ([P, C.c_uint32], I),
     }
     for name, (args, res) in sig.items():
@@ -199,6 +200,9 @@ class Context:
 
     def set_launch(self, threads_per_block=256, blocks_per_sm=0, chunk=1):
         self._check(lib.soc_set_launch(self.h, threads_per_block, blocks_per_sm, chunk))
+
+    def set_refill(self, min_idle_lanes):
+        self._check(lib.soc_set_refill(self.h, min_idle_lanes))
 
     def set_max_steps(self, n):
         self._check(lib.soc_set_max_steps(self.h, n))
