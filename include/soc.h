@@ -175,6 +175,33 @@ soc_status soc_simulate_frequency_batch(soc_ctx *ctx, const soc_batch_item *item
                                         int64_t *d_tally, int64_t *d_stats,
                                         uint32_t *d_pkg_steps, void *stream);
 
+/* ------------------------------------------------------------------------
+ * soc_simulate_frequency_batch_noalloc -- the same call, arguments, results
+ * and determinism as soc_simulate_frequency_batch, for callers that must not
+ * allocate device memory while they run (code inside a framework's caching
+ * allocator or memory budget, real-time loops where cudaMalloc/cudaFree would
+ * synchronise the device, embedders that only hand out fixed buffers).  The
+ * paper has no counterpart: this is an interface variant, not a step of the
+ * method.
+ *   Scratch (work counter, item table, prefix sums, grid table) lives in one
+ *   fixed device array inside the library, about 74 KB, which every GPU that
+ *   loads the library keeps until the process exits.  No cudaMalloc, cudaFree
+ *   or allocating library routine is called.
+ *   Limits: n_items <= SOC_NOALLOC_MAX_ITEMS and at most
+ *   SOC_NOALLOC_MAX_CLOUDS grids uploaded on the context; larger requests
+ *   fail with SOC_ERR_ARG.
+ *   The first call on a device looks up the array's device address (set-up
+ *   for that device); make that first call before any stream capture.
+ *   All calls share the one array: calls that overlap on the GPU (other
+ *   streams, other contexts on the same device) race and must be ordered by
+ *   the caller.
+ * ------------------------------------------------------------------------ */
+#define SOC_NOALLOC_MAX_ITEMS  1024
+#define SOC_NOALLOC_MAX_CLOUDS 64
+soc_status soc_simulate_frequency_batch_noalloc(soc_ctx *ctx, const soc_batch_item *items, int n_items,
+                                                int64_t *d_tally, int64_t *d_stats,
+                                                uint32_t *d_pkg_steps, void *stream);
+
 /* Per-package energy of background / point-source packages (paper Sect. 2.2
  * sources): the energy in erg/s/Hz carried by one weight unit when
  * n_packages packages of weight 2^32 are launched at every frequency.

@@ -743,3 +743,139 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of soc_simulate_frequency_batch.
+//
+// Some callers cannot allocate device memory while they trace: code that runs
+// under a framework's caching allocator or memory budget (where a cudaMalloc
+// outside the pool breaks its accounting or fails at the limit), real-time
+// loops where cudaMalloc/cudaFree would synchronise the device, and embedders
+// that hand the library fixed buffers only.  This entry point keeps all of its
+// per-call scratch -- the work counter, the item table and its prefix sums,
+// and the grid table -- in one file-scope device array of fixed size, so it
+// never calls cudaMalloc, cudaFree or any allocating library routine.  The
+// caller still passes the counters and statistics buffers.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxItems = SOC_NOALLOC_MAX_ITEMS;
+constexpr int kNoAllocMaxClouds = SOC_NOALLOC_MAX_CLOUDS;
+
+struct NoAllocLayout {
+    unsigned long long counter;
+    unsigned long long pad[31];              // keeps the tables 256-byte aligned
+    uint64_t prefix[kNoAllocMaxItems + 1];
+    DevItem items[kNoAllocMaxItems];
+    DevCloud clouds[kNoAllocMaxClouds];
+};
+
+// Shared by every call on a device; holds the last call's contents.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocLayout)];
+
+constexpr int kMaxDevices = 64;
+void *g_noalloc_addr[kMaxDevices] = {};       // device address of g_noalloc_scratch, per device
+
+// Host staging for the tables (static storage: no heap use either).
+thread_local uint64_t t_prefix[kNoAllocMaxItems + 1];
+thread_local DevItem t_items[kNoAllocMaxItems];
+thread_local DevCloud t_clouds[kNoAllocMaxClouds];
+
+}  // namespace
+
+extern "C" soc_status soc_simulate_frequency_batch_noalloc(soc_ctx *ctx, const soc_batch_item *items, int n_items,
+                                                           int64_t *d_tally, int64_t *d_stats, uint32_t *d_pkg_steps,
+                                                           void *stream)
+{
+    if (!ctx || !items || n_items < 1 || !d_tally || !d_stats) return fail(ctx, SOC_ERR_ARG, "null argument");
+    if (n_items > kNoAllocMaxItems)
+        return fail(ctx, SOC_ERR_ARG, "n_items %d exceeds the allocation-free limit of %d items", n_items,
+                    kNoAllocMaxItems);
+    if ((int)ctx->clouds.size() > kNoAllocMaxClouds)
+        return fail(ctx, SOC_ERR_ARG, "%d grids exceed the allocation-free limit of %d grids",
+                    (int)ctx->clouds.size(), kNoAllocMaxClouds);
+    if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
+    if (ctx->device < 0 || ctx->device >= kMaxDevices) return fail(ctx, SOC_ERR_ARG, "device index too large");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    // set-up, once per device, with that device current: the host-side name
+    // g_noalloc_scratch is only a stand-in, the kernel needs the device address
+    if (!g_noalloc_addr[ctx->device]) {
+        void *addr = nullptr;
+        CK(cudaGetSymbolAddress(&addr, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)");
+        g_noalloc_addr[ctx->device] = addr;
+    }
+    NoAllocLayout *S = static_cast<NoAllocLayout *>(g_noalloc_addr[ctx->device]);
+    cudaStream_t s = (cudaStream_t)stream;
+    t_prefix[0] = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const soc_batch_item &it = items[i];
+        if (it.cloud < 0 || it.cloud >= (int)ctx->clouds.size() || ctx->clouds[it.cloud]->freed)
+            return fail(ctx, SOC_ERR_ARG, "item %d: bad or freed cloud", i);
+        const CloudHost &cl = *ctx->clouds[it.cloud];
+        if (it.freq < 0 || it.freq >= ctx->n_freq) return fail(ctx, SOC_ERR_ARG, "item %d: bad freq", i);
+        if (it.iteration < 0 || it.iteration > 65535) return fail(ctx, SOC_ERR_ARG, "item %d: bad iteration", i);
+        if (it.pid_offset + it.n_packages > 0xFFFFFFFFull || it.pid_offset > 0xFFFFFFFFull)
+            return fail(ctx, SOC_ERR_ARG, "item %d: package ids exceed 2^32", i);
+        if (it.tally_offset < 0) return fail(ctx, SOC_ERR_ARG, "item %d: negative tally offset", i);
+        if (it.source == SOC_SRC_BACKGROUND || it.source == SOC_SRC_POINT) {
+            if (it.w0 == 0 || it.w0 > SOC_W_UNIT) return fail(ctx, SOC_ERR_ARG, "item %d: w0 out of [1, 2^32]", i);
+            if (it.source == SOC_SRC_POINT && cl.n_ps == 0)
+                return fail(ctx, SOC_ERR_STATE, "item %d: cloud has no point sources", i);
+        } else if (it.source == SOC_SRC_DUST) {
+            if (!it.d_dust_w || it.n_per_cell == 0) return fail(ctx, SOC_ERR_ARG, "item %d: dust weights missing", i);
+            if (it.pid_offset + it.n_packages > (uint64_t)cl.n_leaf * it.n_per_cell)
+                return fail(ctx, SOC_ERR_ARG, "item %d: more dust packages than n_leaf*n_per_cell", i);
+        } else {
+            return fail(ctx, SOC_ERR_ARG, "item %d: unknown source %d", i, it.source);
+        }
+        DevItem &d = t_items[i];
+        d.cloud = it.cloud; d.freq = it.freq; d.source = it.source; d.iteration = it.iteration;
+        d.pid_offset = (uint32_t)it.pid_offset; d.n_per_cell = it.n_per_cell ? it.n_per_cell : 1;
+        d.w0 = it.w0; d.tally_offset = it.tally_offset; d.dust_w = it.d_dust_w;
+        t_prefix[i + 1] = t_prefix[i] + it.n_packages;
+    }
+    const uint64_t total = t_prefix[n_items];
+    if (total == 0) return SOC_OK;
+    const int nc = (int)ctx->clouds.size();
+    for (int i = 0; i < nc; ++i) {
+        const CloudHost &c = *ctx->clouds[i];
+        DevCloud &d = t_clouds[i];
+        memset(&d, 0, sizeof d);
+        if (c.freed) continue;
+        d.cell = c.cell.p; d.parent = c.parent.p; d.leaf = c.leaf.p; d.rho = c.rho.p;
+        d.volume = c.volume.p; d.kappa = c.kappa.p; d.ps_pos = c.ps_pos.p; d.ps_cdf = c.ps_cdf.p;
+        d.nx = c.nx; d.ny = c.ny; d.nz = c.nz; d.n_levels = c.n_levels; d.n_ps = c.n_ps;
+        d.n_cells = c.n_cells; d.n_root = c.n_root; d.n_leaf = c.n_leaf;
+        for (int L = 0; L <= c.n_levels; ++L) d.level_start[L] = c.level_start[L];
+        for (int L = c.n_levels + 1; L <= SOC_MAX_LEVELS; ++L) d.level_start[L] = c.n_cells;
+    }
+    CK(cudaMemcpyAsync(S->clouds, t_clouds, sizeof(DevCloud) * nc, cudaMemcpyHostToDevice, s), "copy grid table");
+    CK(cudaMemcpyAsync(S->items, t_items, sizeof(DevItem) * n_items, cudaMemcpyHostToDevice, s), "copy items");
+    CK(cudaMemcpyAsync(S->prefix, t_prefix, sizeof(uint64_t) * (n_items + 1), cudaMemcpyHostToDevice, s),
+       "copy prefix");
+    CK(cudaMemsetAsync(&S->counter, 0, sizeof(unsigned long long), s), "zero counter");   // must start at 0
+    TraceParams P;
+    P.clouds = S->clouds;
+    P.items = S->items;
+    P.prefix = S->prefix;
+    P.g_hg = ctx->d_g.p;
+    P.tally = reinterpret_cast<unsigned long long *>(d_tally);
+    P.stats = reinterpret_cast<unsigned long long *>(d_stats);
+    P.pkg_steps = d_pkg_steps;
+    P.counter = &S->counter;
+    P.total = total;
+    P.seed = ctx->seed;
+    P.n_items = n_items;
+    P.max_steps = ctx->max_steps;
+    P.chunk = ctx->chunk;
+    P.refill_min = ctx->refill_min;
+    const int variant = ctx->bps >= 4 ? 4 : 3;
+    const int limit = trace_block_limit(ctx->tpb, variant);
+    const int per_sm = ctx->bps > 0 ? std::min(ctx->bps, limit) : limit;
+    const uint64_t warps_needed = (total + 31) / 32;
+    int64_t grid = (int64_t)ctx->sms * per_sm;
+    const int64_t grid_need = (int64_t)((warps_needed * 32 + ctx->tpb - 1) / ctx->tpb);
+    if (grid_need < grid) grid = grid_need < 1 ? 1 : grid_need;
+    CK(launch_trace(P, (int)grid, ctx->tpb, variant, s), "trace launch");
+    return SOC_OK;
+}

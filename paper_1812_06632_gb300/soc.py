@@ -24,7 +24,7 @@ EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "so
            "soc_dust_upload",
            "soc_sources_upload", "soc_simulate_frequency_batch", "soc_package_energy",
            "soc_dust_emission", "soc_absorbed_power", "soc_update_temperature", "soc_iterate",
-           "soc_set_launch", "soc_set_refill", "soc_set_max_steps"]
+           "soc_set_launch", "soc_set_refill", "soc_set_max_steps", "soc_simulate_frequency_batch_noalloc"]
 
 
 class GridDesc(C.Structure):
@@ -79,6 +79,7 @@ def _load():
         "soc_set_launch": ([P, I, I, I], I),
         "soc_set_refill": ([P, I], I),
         "soc_set_max_steps": ([P, C.c_uint32], I),
+        "soc_simulate_frequency_batch_noalloc": ([P, P, I, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -230,6 +231,13 @@ class Context:
     def simulate(self, items, tally, stats, pkg_steps=None, stream=None):
         """soc_simulate_frequency_batch; items from Context.items()."""
         return self._check(lib.soc_simulate_frequency_batch(
+            self.h, C.cast(items, C.c_void_p), len(items), _t_ptr(tally), _t_ptr(stats),
+            _t_ptr(pkg_steps), _stream(stream)))
+
+    def simulate_noalloc(self, items, tally, stats, pkg_steps=None, stream=None):
+        """soc_simulate_frequency_batch_noalloc: same results, no device
+        allocation (fixed library-internal scratch; see include/soc.h)."""
+        return self._check(lib.soc_simulate_frequency_batch_noalloc(
             self.h, C.cast(items, C.c_void_p), len(items), _t_ptr(tally), _t_ptr(stats),
             _t_ptr(pkg_steps), _stream(stream)))
 
