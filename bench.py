@@ -33,6 +33,27 @@ N_PACKAGES = 1_000_000
 WORKLOAD = "lognormal 128^3, 64 nu (3e11-3e15 Hz), 1e6 background packages/nu, HG g=0.5, FP64 T update"
 
 
+# DRAM bytes (read + write) per photon-cell step of trace_kernel from one ncu
+# capture (small case of the same workload, scaled by steps), valid only for
+# the kernel source it was taken on.
+TRACE_DRAM = {"source_sha1": None, "bytes_per_step": None, "profile": None}
+
+
+def _trace_source_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("soc_trace.cu", "soc_fp32.cuh", "soc_internal.h"):
+        with open(os.path.join(ROOT, "paper_1812_06632_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _traffic_per_launch(steps):
+    if TRACE_DRAM["source_sha1"] and TRACE_DRAM["source_sha1"] == _trace_source_sha1():
+        return TRACE_DRAM["bytes_per_step"] * steps
+    return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -192,7 +213,6 @@ def run_gpu(args):
     # rank r traces package ids [r N, (r+1) N) of every frequency (weak scaling)
     specs = [dict(source=0, freq=f, pid_offset=rank * N_PACKAGES, n_packages=N_PACKAGES,
                   tally_offset=f * cl.n_cells) for f in range(nf)]
-    items = ctx.items(specs)
     stream = torch.cuda.Stream()
     tally = torch.zeros(nf * cl.n_cells, dtype=torch.int64, device="cuda")
     stats = torch.zeros((nf, 4), dtype=torch.int64, device="cuda")
@@ -202,20 +222,28 @@ def run_gpu(args):
     T = torch.full((cl.n_cells,), 2.7, dtype=torch.float32, device="cuda")
     dT = torch.zeros(1, dtype=torch.float64, device="cuda")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    # the tracer pass as one prepared batch in a CUDA graph (counter reset +
+    # persistent launch), the FP64 integral and temperature in a second graph
+    batch = ctx.batch_create(ctx.items(specs))
+    torch.cuda.synchronize()
+    ctx.capture_begin(stream)
+    ctx.batch_launch(batch, tally, stats, stream=stream)
+    g_trace = ctx.capture_end(stream)
+    ctx.capture_begin(stream)
+    ctx.absorbed_power(cid, tally, cl.n_cells, e_unit, A, stream=stream)
+    ctx.update_temperature(cid, A, T, dT, stream=stream)
+    g_temp = ctx.capture_end(stream)
 
     def step(ev=None):
         with torch.cuda.stream(stream):
-            tally.zero_()
-            stats.zero_()
             if ev:
                 ev[0].record(stream)
-            ctx.simulate(items, tally, stats, stream=stream)
+            ctx.graph_launch(g_trace, stream=stream)
             if ev:
                 ev[1].record(stream)
             if world > 1:
                 dist.all_reduce(tally)
-            ctx.absorbed_power(cid, tally, cl.n_cells, e_unit, A, stream=stream)
-            ctx.update_temperature(cid, A, T, dT, stream=stream)
+            ctx.graph_launch(g_temp, stream=stream)
             if ev:
                 ev[2].record(stream)
 
@@ -285,11 +313,12 @@ def run_gpu(args):
     peaks, peak_kind = _peaks()
     bytes_trace = steps_per_step * BYTES_PER_STEP
     achieved = bytes_trace / (ms_trace / 1e3) / 1e9
+    traffic = _traffic_per_launch(steps_per_step)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "kernel": "trace_kernel", "peak_source": f"{peak_kind} hbm_gbs (copy)",
                 "bytes_per_unit": BYTES_PER_STEP, "units_per_launch": steps_per_step,
-                "ms_per_launch": ms_trace}
+                "ms_per_launch": ms_trace, "launch_includes": "counter reset (1.07 GB memset) + tracer"}
     out = {
         "metric": "photon-cell steps/s", "value": value, "unit": "photon-cell steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all,
@@ -300,11 +329,15 @@ def run_gpu(args):
                    "l2": "512 MiB buffer written between steps, outside the step events",
                    "parallelism": f"package shards x{world}" if world > 1 else "single GPU"},
         "roofline": roofline, "gpu_launches": 3 * args.steps, "e2e": e2e,
+        "trace_source_sha1": _trace_source_sha1(),
         "cpu_baseline": cpu_base,
     }
     if rank == 0:
         out["clocks"] = clk.summary()
         print(json.dumps(out), flush=True)
+    ctx.graph_destroy(g_trace)
+    ctx.graph_destroy(g_temp)
+    ctx.batch_destroy(batch)
     ctx.close()
     if world > 1:
         dist.destroy_process_group()

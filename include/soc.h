@@ -202,6 +202,31 @@ soc_status soc_simulate_frequency_batch_noalloc(soc_ctx *ctx, const soc_batch_it
                                                 int64_t *d_tally, int64_t *d_stats,
                                                 uint32_t *d_pkg_steps, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Prepared batches and CUDA graphs: many frequencies and clouds in one
+ * persistent launch, replayed without host work.
+ * soc_batch_create checks the items as soc_simulate_frequency_batch does and
+ * copies them once into library-owned device memory (synchronous); returns
+ * *batch_id.  soc_batch_launch zeroes d_tally[0, tally_len) (tally_len 0:
+ * no zeroing) and the batch's d_stats rows, resets the batch's work counter
+ * and launches the tracer on `stream`: no host-to-device copy, so it can be
+ * captured.  soc_capture_begin / soc_capture_end capture every library call
+ * issued on `stream` in between (soc_batch_launch, soc_absorbed_power,
+ * soc_update_temperature, soc_dust_emission; NOT soc_simulate_frequency_batch,
+ * which copies from host memory) into an executable CUDA graph *graph_id;
+ * soc_graph_launch replays it.  `stream` must not be the legacy default
+ * stream.  Grids, dust and sources must not be re-uploaded or freed while a
+ * batch or graph that uses them is alive.
+ * ------------------------------------------------------------------------ */
+soc_status soc_batch_create(soc_ctx *ctx, const soc_batch_item *items, int n_items, int *batch_id);
+soc_status soc_batch_launch(soc_ctx *ctx, int batch_id, int64_t *d_tally, int64_t tally_len,
+                            int64_t *d_stats, uint32_t *d_pkg_steps, void *stream);
+soc_status soc_batch_destroy(soc_ctx *ctx, int batch_id);
+soc_status soc_capture_begin(soc_ctx *ctx, void *stream);
+soc_status soc_capture_end(soc_ctx *ctx, void *stream, int *graph_id);
+soc_status soc_graph_launch(soc_ctx *ctx, int graph_id, void *stream);
+soc_status soc_graph_destroy(soc_ctx *ctx, int graph_id);
+
 /* Per-package energy of background / point-source packages (paper Sect. 2.2
  * sources): the energy in erg/s/Hz carried by one weight unit when
  * n_packages packages of weight 2^32 are launched at every frequency.

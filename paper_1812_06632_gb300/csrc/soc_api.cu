@@ -59,6 +59,14 @@ struct CloudHost {
 
 }  // namespace
 
+struct BatchHost {
+    int n_items = 0;
+    uint64_t total = 0;
+    DevBuf<DevItem> items;
+    DevBuf<uint64_t> prefix;
+    DevBuf<unsigned long long> counter;
+};
+
 struct soc_ctx {
     int device = 0;
     uint64_t seed = 1;
@@ -77,10 +85,14 @@ struct soc_ctx {
     DevBuf<unsigned long long> d_counter;
     DevBuf<unsigned long long> d_lmax;
     DevBuf<double> d_maxdT;
+    // prepared batches and graphs
+    std::vector<struct BatchHost *> batches;
+    std::vector<cudaGraphExec_t> graphs;
     // launch
     int tpb = 256, bps = 4, chunk = 16, refill_min = 8;   // autotuned on the 128^3 x 64 nu workload
     uint32_t max_steps = 10000000u;
     int sms = 0;
+    int occ[2][8] = {};           // resident blocks/SM per (build, threads/32), from soc_create
 };
 
 namespace {
@@ -186,6 +198,8 @@ soc_status soc_create(soc_ctx **out, int device, uint64_t seed)
     ctx->device = device;
     ctx->seed = seed;
     cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+    for (int v = 3; v <= 4; ++v)
+        for (int t = 32; t <= 256; t += 32) ctx->occ[v - 3][t / 32 - 1] = trace_block_limit(t, v);
     if (ctx->d_counter.alloc(1) != cudaSuccess || ctx->d_maxdT.alloc(1) != cudaSuccess) {
         delete ctx;
         return SOC_ERR_NOMEM;
@@ -226,6 +240,10 @@ void soc_destroy(soc_ctx *ctx)
     ctx->d_nu.release(); ctx->d_kabs.release(); ctx->d_lnE.release(); ctx->d_lnT.release();
     ctx->d_items.release(); ctx->d_prefix.release(); ctx->d_counter.release(); ctx->d_lmax.release();
     ctx->d_maxdT.release();
+    for (BatchHost *b : ctx->batches)
+        if (b) { b->items.release(); b->prefix.release(); b->counter.release(); delete b; }
+    for (cudaGraphExec_t g : ctx->graphs)
+        if (g) cudaGraphExecDestroy(g);
     delete ctx;
 }
 
@@ -535,15 +553,12 @@ soc_status soc_package_energy(soc_ctx *ctx, int cloud_id, int source, uint64_t n
     return fail(ctx, SOC_ERR_ARG, "source must be background or point");
 }
 
-soc_status soc_simulate_frequency_batch(soc_ctx *ctx, const soc_batch_item *items, int n_items, int64_t *d_tally,
-                                        int64_t *d_stats, uint32_t *d_pkg_steps, void *stream)
+// Check the batch items and convert them to the device form (host vectors).
+static soc_status prepare_items(soc_ctx *ctx, const soc_batch_item *items, int n_items, std::vector<DevItem> &dv,
+                                std::vector<uint64_t> &prefix)
 {
-    if (!ctx || !items || n_items < 1 || !d_tally || !d_stats) return fail(ctx, SOC_ERR_ARG, "null argument");
-    if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    cudaStream_t s = (cudaStream_t)stream;
-    std::vector<DevItem> dv(n_items);
-    std::vector<uint64_t> prefix(n_items + 1, 0);
+    dv.assign(n_items, DevItem{});
+    prefix.assign(n_items + 1, 0);
     for (int i = 0; i < n_items; ++i) {
         const soc_batch_item &it = items[i];
         if (it.cloud < 0 || it.cloud >= (int)ctx->clouds.size() || ctx->clouds[it.cloud]->freed)
@@ -571,6 +586,33 @@ soc_status soc_simulate_frequency_batch(soc_ctx *ctx, const soc_batch_item *item
         d.w0 = it.w0; d.tally_offset = it.tally_offset; d.dust_w = it.d_dust_w;
         prefix[i + 1] = prefix[i] + it.n_packages;
     }
+    return SOC_OK;
+}
+
+// Launch shape of the tracer for `total` work indices.
+static void launch_geometry(soc_ctx *ctx, uint64_t total, int &grid_out, int &variant)
+{
+    variant = ctx->bps >= 4 ? 4 : 3;
+    const int limit = std::max(1, ctx->occ[variant - 3][ctx->tpb / 32 - 1]);
+    const int per_sm = ctx->bps > 0 ? std::min(ctx->bps, limit) : limit;
+    const uint64_t warps_needed = (total + 31) / 32;
+    int64_t grid = (int64_t)ctx->sms * per_sm;
+    const int64_t grid_need = (int64_t)((warps_needed * 32 + ctx->tpb - 1) / ctx->tpb);
+    if (grid_need < grid) grid = grid_need < 1 ? 1 : grid_need;
+    grid_out = (int)grid;
+}
+
+soc_status soc_simulate_frequency_batch(soc_ctx *ctx, const soc_batch_item *items, int n_items, int64_t *d_tally,
+                                        int64_t *d_stats, uint32_t *d_pkg_steps, void *stream)
+{
+    if (!ctx || !items || n_items < 1 || !d_tally || !d_stats) return fail(ctx, SOC_ERR_ARG, "null argument");
+    if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<DevItem> dv;
+    std::vector<uint64_t> prefix;
+    soc_status pst = prepare_items(ctx, items, n_items, dv, prefix);
+    if (pst != SOC_OK) return pst;
     const uint64_t total = prefix[n_items];
     soc_status st = sync_clouds(ctx);
     if (st) return st;
@@ -595,15 +637,127 @@ soc_status soc_simulate_frequency_batch(soc_ctx *ctx, const soc_batch_item *item
     P.max_steps = ctx->max_steps;
     P.chunk = ctx->chunk;
     P.refill_min = ctx->refill_min;
-    const int variant = ctx->bps >= 4 ? 4 : 3;
-    const int limit = trace_block_limit(ctx->tpb, variant);
-    const int per_sm = ctx->bps > 0 ? std::min(ctx->bps, limit) : limit;
-    const uint64_t warps_needed = (total + 31) / 32;
-    int64_t grid = (int64_t)ctx->sms * per_sm;
-    const int64_t grid_need = (int64_t)((warps_needed * 32 + ctx->tpb - 1) / ctx->tpb);
-    if (grid_need < grid) grid = grid_need < 1 ? 1 : grid_need;
-    CK(launch_trace(P, (int)grid, ctx->tpb, variant, s), "trace launch");
+    int grid = 1, variant = 3;
+    launch_geometry(ctx, total, grid, variant);
+    CK(launch_trace(P, grid, ctx->tpb, variant, s), "trace launch");
     // the host copies above used pageable buffers: they are staged before return
+    return SOC_OK;
+}
+
+soc_status soc_batch_create(soc_ctx *ctx, const soc_batch_item *items, int n_items, int *batch_id)
+{
+    if (!ctx || !items || n_items < 1 || !batch_id) return fail(ctx, SOC_ERR_ARG, "null argument");
+    if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    std::vector<DevItem> dv;
+    std::vector<uint64_t> prefix;
+    soc_status st = prepare_items(ctx, items, n_items, dv, prefix);
+    if (st != SOC_OK) return st;
+    BatchHost *b = new (std::nothrow) BatchHost();
+    if (!b) return fail(ctx, SOC_ERR_NOMEM, "host allocation");
+    b->n_items = n_items;
+    b->total = prefix[n_items];
+    cudaError_t e = cudaSuccess;
+    if ((e = b->items.alloc(n_items)) != cudaSuccess || (e = b->prefix.alloc(n_items + 1)) != cudaSuccess ||
+        (e = b->counter.alloc(1)) != cudaSuccess ||
+        (e = cudaMemcpy(b->items.p, dv.data(), sizeof(DevItem) * n_items, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->prefix.p, prefix.data(), 8 * (n_items + 1), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        b->items.release(); b->prefix.release(); b->counter.release();
+        delete b;
+        return cuda_fail(ctx, e, "batch upload");
+    }
+    ctx->batches.push_back(b);
+    *batch_id = (int)ctx->batches.size() - 1;
+    return sync_clouds(ctx);                 // the launch must not need to upload the grid table
+}
+
+soc_status soc_batch_launch(soc_ctx *ctx, int batch_id, int64_t *d_tally, int64_t tally_len, int64_t *d_stats,
+                            uint32_t *d_pkg_steps, void *stream)
+{
+    if (!ctx || batch_id < 0 || batch_id >= (int)ctx->batches.size() || !ctx->batches[batch_id])
+        return fail(ctx, SOC_ERR_ARG, "bad batch id");
+    if (!d_tally || !d_stats || tally_len < 0) return fail(ctx, SOC_ERR_ARG, "null argument");
+    if (ctx->clouds_dirty) return fail(ctx, SOC_ERR_STATE, "grids changed after soc_batch_create");
+    const BatchHost &b = *ctx->batches[batch_id];
+    cudaStream_t s = (cudaStream_t)stream;
+    if (tally_len) CK(cudaMemsetAsync(d_tally, 0, sizeof(int64_t) * tally_len, s), "zero tally");
+    CK(cudaMemsetAsync(d_stats, 0, sizeof(int64_t) * 4 * b.n_items, s), "zero stats");
+    if (b.total == 0) return SOC_OK;
+    CK(cudaMemsetAsync(b.counter.p, 0, sizeof(unsigned long long), s), "zero counter");
+    TraceParams P;
+    P.clouds = ctx->d_clouds.p;
+    P.items = b.items.p;
+    P.prefix = b.prefix.p;
+    P.g_hg = ctx->d_g.p;
+    P.tally = reinterpret_cast<unsigned long long *>(d_tally);
+    P.stats = reinterpret_cast<unsigned long long *>(d_stats);
+    P.pkg_steps = d_pkg_steps;
+    P.counter = b.counter.p;
+    P.total = b.total;
+    P.seed = ctx->seed;
+    P.n_items = b.n_items;
+    P.max_steps = ctx->max_steps;
+    P.chunk = ctx->chunk;
+    P.refill_min = ctx->refill_min;
+    int grid = 1, variant = 3;
+    launch_geometry(ctx, b.total, grid, variant);
+    CK(launch_trace(P, grid, ctx->tpb, variant, s), "trace launch");
+    return SOC_OK;
+}
+
+soc_status soc_batch_destroy(soc_ctx *ctx, int batch_id)
+{
+    if (!ctx || batch_id < 0 || batch_id >= (int)ctx->batches.size() || !ctx->batches[batch_id])
+        return fail(ctx, SOC_ERR_ARG, "bad batch id");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaDeviceSynchronize(), "synchronize before free");
+    BatchHost *b = ctx->batches[batch_id];
+    b->items.release(); b->prefix.release(); b->counter.release();
+    delete b;
+    ctx->batches[batch_id] = nullptr;
+    return SOC_OK;
+}
+
+soc_status soc_capture_begin(soc_ctx *ctx, void *stream)
+{
+    if (!ctx || !stream) return fail(ctx, SOC_ERR_ARG, "capture needs a non-default stream");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    soc_status st = sync_clouds(ctx);
+    if (st) return st;
+    CK(cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    return SOC_OK;
+}
+
+soc_status soc_capture_end(soc_ctx *ctx, void *stream, int *graph_id)
+{
+    if (!ctx || !stream || !graph_id) return fail(ctx, SOC_ERR_ARG, "null argument");
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamEndCapture((cudaStream_t)stream, &g), "end capture");
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+    ctx->graphs.push_back(ex);
+    *graph_id = (int)ctx->graphs.size() - 1;
+    return SOC_OK;
+}
+
+soc_status soc_graph_launch(soc_ctx *ctx, int graph_id, void *stream)
+{
+    if (!ctx || graph_id < 0 || graph_id >= (int)ctx->graphs.size() || !ctx->graphs[graph_id])
+        return fail(ctx, SOC_ERR_ARG, "bad graph id");
+    CK(cudaGraphLaunch(ctx->graphs[graph_id], (cudaStream_t)stream), "graph launch");
+    return SOC_OK;
+}
+
+soc_status soc_graph_destroy(soc_ctx *ctx, int graph_id)
+{
+    if (!ctx || graph_id < 0 || graph_id >= (int)ctx->graphs.size() || !ctx->graphs[graph_id])
+        return fail(ctx, SOC_ERR_ARG, "bad graph id");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(cudaDeviceSynchronize(), "synchronize before free");
+    cudaGraphExecDestroy(ctx->graphs[graph_id]);
+    ctx->graphs[graph_id] = nullptr;
     return SOC_OK;
 }
 

@@ -24,7 +24,9 @@ EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "so
            "soc_dust_upload",
            "soc_sources_upload", "soc_simulate_frequency_batch", "soc_package_energy",
            "soc_dust_emission", "soc_absorbed_power", "soc_update_temperature", "soc_iterate",
-           "soc_set_launch", "soc_set_refill", "soc_set_max_steps", "soc_simulate_frequency_batch_noalloc"]
+           "soc_set_launch", "soc_set_refill", "soc_set_max_steps",
+           "soc_batch_create", "soc_batch_launch", "soc_batch_destroy", "soc_capture_begin",
+           "soc_capture_end", "soc_graph_launch", "soc_graph_destroy", "soc_simulate_frequency_batch_noalloc"]
 
 
 class GridDesc(C.Structure):
@@ -78,6 +80,13 @@ def _load():
         "soc_iterate": ([P, I, C.POINTER(IterateParams), P, P, C.POINTER(IterateResult), P, P], I),
         "soc_set_launch": ([P, I, I, I], I),
         "soc_set_refill": ([P, I], I),
+        "soc_batch_create": ([P, P, I, C.POINTER(I)], I),
+        "soc_batch_launch": ([P, I, P, C.c_int64, P, P, P], I),
+        "soc_batch_destroy": ([P, I], I),
+        "soc_capture_begin": ([P, P], I),
+        "soc_capture_end": ([P, P, C.POINTER(I)], I),
+        "soc_graph_launch": ([P, I, P], I),
+        "soc_graph_destroy": ([P, I], I),
         "soc_set_max_steps": ([P, C.c_uint32], I),
         "soc_simulate_frequency_batch_noalloc": ([P, P, I, P, P, P, P], I),
     }
@@ -240,6 +249,33 @@ class Context:
         return self._check(lib.soc_simulate_frequency_batch_noalloc(
             self.h, C.cast(items, C.c_void_p), len(items), _t_ptr(tally), _t_ptr(stats),
             _t_ptr(pkg_steps), _stream(stream)))
+
+    # -- prepared batches and CUDA graphs ----------------------------------
+    def batch_create(self, items) -> int:
+        bid = C.c_int(-1)
+        self._check(lib.soc_batch_create(self.h, C.cast(items, C.c_void_p), len(items), C.byref(bid)))
+        return bid.value
+
+    def batch_launch(self, batch_id, tally, stats, pkg_steps=None, zero_tally=True, stream=None):
+        self._check(lib.soc_batch_launch(self.h, batch_id, _t_ptr(tally), tally.numel() if zero_tally else 0,
+                                         _t_ptr(stats), _t_ptr(pkg_steps), _stream(stream)))
+
+    def batch_destroy(self, batch_id):
+        self._check(lib.soc_batch_destroy(self.h, batch_id))
+
+    def capture_begin(self, stream):
+        self._check(lib.soc_capture_begin(self.h, _stream(stream)))
+
+    def capture_end(self, stream) -> int:
+        gid = C.c_int(-1)
+        self._check(lib.soc_capture_end(self.h, _stream(stream), C.byref(gid)))
+        return gid.value
+
+    def graph_launch(self, graph_id, stream=None):
+        self._check(lib.soc_graph_launch(self.h, graph_id, _stream(stream)))
+
+    def graph_destroy(self, graph_id):
+        self._check(lib.soc_graph_destroy(self.h, graph_id))
 
     def package_energy(self, cloud_id, source, n_packages):
         e = np.zeros(self.n_freq, np.float64)
