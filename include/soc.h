@@ -320,6 +320,51 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *par
                        double *dT_history, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Learned temperature seed (not a step of the paper's method: a 3D U-Net that
+ * maps the first, noisy temperature field and the log density to the
+ * converged temperature and seeds soc_iterate; the Monte Carlo iterations
+ * remain its judge).  Channels-last (N, side, side, side, C) tensors; BF16
+ * activations and weights on tensor cores with FP32 accumulation; FP32
+ * master weights, gradients and Adam moments.  Architecture: 4 levels with
+ * 16-32-64-128 channels, two 3x3x3 convolutions (ReLU) per level, 2x2x2 max
+ * pooling, nearest 2x upsampling, skip concatenation [upsampled, skip], a
+ * 3x3x3 output convolution (channel 0 = prediction).  side % 8 == 0.
+ * Parameters are packed layer by layer (15 layers in forward order), each as
+ * w[Cout][27][Cin] then b[Cout], FP32; soc_unet_param_count() floats.
+ *   soc_unet_create     device buffers for a batch size and cube side.
+ *   soc_unet_forward    d_input (N,S,S,S,2) FP32 device -> d_pred (N,S,S,S).
+ *   soc_unet_backward   forward, MSE loss against d_target (N,S,S,S), and
+ *                       the gradients of every parameter (kept in the net);
+ *                       d_pred / d_loss (device double) optional.
+ *   soc_unet_adam       one Adam step (beta 0.9, 0.999, eps 1e-8) with lr.
+ *   soc_unet_get_params host copy of the parameters (grads = 0) or of their
+ *                       gradients (grads = 1).  Synchronous.
+ * ------------------------------------------------------------------------ */
+soc_status soc_unet_create(int device, int batch, int side, int *net_id);
+soc_status soc_unet_destroy(int net_id);
+int64_t soc_unet_param_count(void);
+soc_status soc_unet_set_params(int net_id, const float *host_params);
+soc_status soc_unet_get_params(int net_id, float *host_params, int grads);
+soc_status soc_unet_forward(int net_id, const float *d_input, float *d_pred, void *stream);
+soc_status soc_unet_backward(int net_id, const float *d_input, const float *d_target, float *d_pred,
+                             double *d_loss, void *stream);
+soc_status soc_unet_adam(int net_id, float lr, void *stream);
+
+/* Single network operations (channels-last BF16, Cin and Cout multiples of
+ * 16), the building blocks of the U-Net:
+ *   soc_nn_conv3d        y = relu?(conv3x3x3(x, w) + bias) into y_bf16 or y_f32;
+ *   soc_nn_conv3d_dgrad  gx (FP32) = transposed convolution of gy with w
+ *                        (w_scratch: device BF16 [Cout*27*Cin]);
+ *   soc_nn_conv3d_wgrad  gw[Cout][27][Cin] += sum_v gy[v] x[v + tap] and
+ *                        gb[Cout] += sum_v gy[v] (FP32, accumulated). */
+soc_status soc_nn_conv3d(const void *x, int N, int D, int H, int W, int Cin, const void *w, const float *bias,
+                         int Cout, int relu, void *y_bf16, float *y_f32, void *stream);
+soc_status soc_nn_conv3d_dgrad(const void *gy, int N, int D, int H, int W, int Cout, const void *w, int Cin,
+                               void *w_scratch, float *gx, void *stream);
+soc_status soc_nn_conv3d_wgrad(const void *gy, const void *x, int N, int D, int H, int W, int Cin, int Cout,
+                               float *gw, float *gb, void *stream);
+
+/* ------------------------------------------------------------------------
  * Launch configuration of the tracer (autotuner hook).  threads_per_block in
  * {32, 64, ..., 256}; blocks_per_sm >= 1 (0 = occupancy maximum of the
  * default build; 4 or more selects the build limited to 64 registers per

@@ -28,6 +28,7 @@ SOURCES = {
     "soc_trace.cu": ["-fmad=false", "-prec-div=true", "-prec-sqrt=true", "-ftz=false"],
     "soc_temperature.cu": ["-fmad=false"],
     "soc_api.cu": [],
+    "soc_nn.cu": [],
 }
 
 

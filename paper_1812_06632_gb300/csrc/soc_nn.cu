@@ -1,0 +1,844 @@
+// soc_nn.cu -- the learned temperature seed: a 3D U-Net trained and run by
+// this library's own kernels (tensor cores in BF16 with FP32 accumulation).
+//
+// The method itself has no network; the seed replaces the first, most
+// expensive iterations of the temperature solution (paper Sect. 3.3-3.4
+// discuss cutting the cost of the early iterations).  Layout: channels-last
+// (N, D, H, W, C), BF16 activations, FP32 master weights, gradients and Adam
+// moments.
+//
+// Convolutions (3x3x3, stride 1, zero padding 1) are implicit GEMMs:
+//   forward:  M = voxels, N = C_out, K = 27 C_in (tap-major, channel-minor);
+//   dgrad:    the forward kernel with the weights flipped in space and
+//             transposed in channels;
+//   wgrad:    M = C_out, N = C_in per tap, K = voxels (split over blocks,
+//             FP32 atomics).
+// Tiles are staged in shared memory and multiplied with
+// mma.sync.m16n8k16 (BF16 inputs, FP32 accumulators).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+#include "soc_internal.h"
+
+namespace soc {
+namespace nn {
+
+using bf16 = __nv_bfloat16;
+
+__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+struct ConvArgs {
+    const bf16 *in;
+    int in_stride, in_off;          // elements per voxel, first channel
+    const bf16 *w;                  // [Cout][27][Cin]
+    const float *bias;              // [Cout] or null
+    bf16 *out;                      // BF16 output (when out_f32 is null)
+    float *out_f32;                 // FP32 output (optional)
+    int out_stride, out_off;
+    int N, D, H, W, Cin, Cout;
+    int relu, accumulate;           // accumulate: FP32 output += result
+};
+
+// Forward implicit-GEMM convolution.  Block: 128 threads (4 warps), 64 output
+// voxels x BN output channels; every warp owns 16 voxels.
+template <int BN>
+__global__ void __launch_bounds__(128) conv3d_kernel(const ConvArgs a)
+{
+    __shared__ __align__(16) bf16 As[64][24];
+    __shared__ __align__(16) bf16 Bs[BN][24];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, t2 = (lane & 3) * 2;
+    const long long V = (long long)a.N * a.D * a.H * a.W;
+    const long long v0 = (long long)blockIdx.x * 64;
+    const int n0 = blockIdx.y * BN;
+    float acc[BN / 8][4];
+#pragma unroll
+    for (int i = 0; i < BN / 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+    const int r = tid >> 1, hh = tid & 1;
+    const long long v = v0 + r;
+    const bool vin = v < V;
+    int n = 0, z = 0, y = 0, x = 0;
+    if (vin) {
+        long long q = v;
+        x = (int)(q % a.W); q /= a.W;
+        y = (int)(q % a.H); q /= a.H;
+        z = (int)(q % a.D); n = (int)(q / a.D);
+    }
+    for (int tap = 0; tap < 27; ++tap) {
+        const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
+        const bool ok = vin && zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+        const long long src = ok ? ((((long long)n * a.D + zz) * a.H + yy) * a.W + xx) * a.in_stride + a.in_off : 0;
+        for (int c0 = 0; c0 < a.Cin; c0 += 16) {
+            uint4 av = make_uint4(0u, 0u, 0u, 0u);
+            if (ok) av = *reinterpret_cast<const uint4 *>(a.in + src + c0 + hh * 8);
+            *reinterpret_cast<uint4 *>(&As[r][hh * 8]) = av;
+            if (tid < BN * 2) {
+                const int br = tid >> 1, bh = tid & 1;
+                *reinterpret_cast<uint4 *>(&Bs[br][bh * 8]) = *reinterpret_cast<const uint4 *>(
+                    a.w + ((long long)(n0 + br) * 27 + tap) * a.Cin + c0 + bh * 8);
+            }
+            __syncthreads();
+            uint32_t af[4];
+            const int ar = warp * 16 + g;
+            af[0] = *reinterpret_cast<const uint32_t *>(&As[ar][t2]);
+            af[1] = *reinterpret_cast<const uint32_t *>(&As[ar + 8][t2]);
+            af[2] = *reinterpret_cast<const uint32_t *>(&As[ar][t2 + 8]);
+            af[3] = *reinterpret_cast<const uint32_t *>(&As[ar + 8][t2 + 8]);
+#pragma unroll
+            for (int nt = 0; nt < BN / 8; ++nt) {
+                uint32_t bfr[2];
+                bfr[0] = *reinterpret_cast<const uint32_t *>(&Bs[nt * 8 + g][t2]);
+                bfr[1] = *reinterpret_cast<const uint32_t *>(&Bs[nt * 8 + g][t2 + 8]);
+                mma16816(acc[nt], af, bfr);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int nt = 0; nt < BN / 8; ++nt) {
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+            const long long vo = v0 + warp * 16 + g + hf * 8;
+            if (vo >= V) continue;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int co = n0 + nt * 8 + t2 + j;
+                float val = acc[nt][hf * 2 + j];
+                if (a.bias) val += a.bias[co];
+                if (a.relu) val = fmaxf(val, 0.f);
+                const long long o = vo * a.out_stride + a.out_off + co;
+                if (a.out_f32) {
+                    a.out_f32[o] = a.accumulate ? a.out_f32[o] + val : val;
+                } else {
+                    a.out[o] = __float2bfloat16_rn(val);
+                }
+            }
+        }
+    }
+}
+
+// Wt[ci][t][co] = W[co][26 - t][ci]: weights of the transposed convolution.
+__global__ void flip_weights_kernel(const bf16 *W, int Cout, int Cin, bf16 *Wt)
+{
+    const long long n = (long long)Cout * 27 * Cin;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int co = (int)(i % Cout);
+        const int t = (int)((i / Cout) % 27);
+        const int ci = (int)(i / (27LL * Cout));
+        Wt[i] = W[((long long)co * 27 + (26 - t)) * Cin + ci];
+    }
+}
+
+struct WgradArgs {
+    const bf16 *gy;
+    int gy_stride, gy_off;
+    const bf16 *x;
+    int x_stride, x_off;
+    float *gw;                       // [Cout][27][Cin], accumulated
+    int N, D, H, W, Cin, Cout;
+    long long vox_per_block;
+};
+
+// gw[co][tap][ci] += sum_v gy[v][co] x[v + off(tap)][ci].  Block: 128 threads,
+// COT output channels (16 per warp) x 16 input channels of one tap, over a
+// range of voxels (K), 16 voxels per MMA step.
+template <int COT>
+__global__ void __launch_bounds__(128) conv3d_wgrad_kernel(const WgradArgs a)
+{
+    __shared__ __align__(16) bf16 Ast[COT][24];   // [co][voxel]
+    __shared__ __align__(16) bf16 Bst[16][24];    // [ci][voxel]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, t2 = (lane & 3) * 2;
+    const long long V = (long long)a.N * a.D * a.H * a.W;
+    const int co0 = blockIdx.y * COT;
+    const int tap = blockIdx.z % 27;
+    const int ci0 = (blockIdx.z / 27) * 16;
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const long long vb = (long long)blockIdx.x * a.vox_per_block;
+    const long long ve = vb + a.vox_per_block < V ? vb + a.vox_per_block : V;
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    const bool warp_on = warp * 16 < COT;
+    for (long long k0 = vb; k0 < ve; k0 += 16) {
+        // gy tile: 16 voxels x COT channels, 8 channels per thread
+        for (int e = tid; e < 16 * (COT / 8); e += 128) {
+            const int kv = e / (COT / 8), cg = e % (COT / 8);
+            const long long vv = k0 + kv;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (vv < ve) val = *reinterpret_cast<const uint4 *>(a.gy + vv * a.gy_stride + a.gy_off + co0 + cg * 8);
+            const bf16 *pv = reinterpret_cast<const bf16 *>(&val);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) Ast[cg * 8 + j][kv] = pv[j];
+        }
+        // x tile: 16 voxels shifted by the tap x 16 channels
+        if (tid < 32) {
+            const int kv = tid >> 1, hh = tid & 1;
+            const long long vv = k0 + kv;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (vv < ve) {
+                long long q = vv;
+                const int xx = (int)(q % a.W) + dx; q /= a.W;
+                const int yy = (int)(q % a.H) + dy; q /= a.H;
+                const int zz = (int)(q % a.D) + dz;
+                const long long nn = q / a.D;
+                if (zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
+                    val = *reinterpret_cast<const uint4 *>(
+                        a.x + (((nn * a.D + zz) * a.H + yy) * a.W + xx) * a.x_stride + a.x_off + ci0 + hh * 8);
+            }
+            const bf16 *pv = reinterpret_cast<const bf16 *>(&val);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) Bst[hh * 8 + j][kv] = pv[j];
+        }
+        __syncthreads();
+        if (warp_on) {
+            uint32_t af[4];
+            const int ar = warp * 16 + g;
+            af[0] = *reinterpret_cast<const uint32_t *>(&Ast[ar][t2]);
+            af[1] = *reinterpret_cast<const uint32_t *>(&Ast[ar + 8][t2]);
+            af[2] = *reinterpret_cast<const uint32_t *>(&Ast[ar][t2 + 8]);
+            af[3] = *reinterpret_cast<const uint32_t *>(&Ast[ar + 8][t2 + 8]);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                uint32_t bfr[2];
+                bfr[0] = *reinterpret_cast<const uint32_t *>(&Bst[nt * 8 + g][t2]);
+                bfr[1] = *reinterpret_cast<const uint32_t *>(&Bst[nt * 8 + g][t2 + 8]);
+                mma16816(acc[nt], af, bfr);
+            }
+        }
+        __syncthreads();
+    }
+    if (!warp_on) return;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int co = co0 + warp * 16 + g + hf * 8;
+                const int ci = ci0 + nt * 8 + t2 + j;
+                atomicAdd(a.gw + ((long long)co * 27 + tap) * a.Cin + ci, acc[nt][hf * 2 + j]);
+            }
+}
+
+// Bias gradient: gb[c] += sum_v gy[v][c] (BF16 gradient, dense C channels).
+__global__ void bias_grad_kernel(const bf16 *gy, int C, long long V, long long vox_per_block, float *gb)
+{
+    __shared__ float part[256];
+    const long long vb = (long long)blockIdx.x * vox_per_block;
+    const long long ve = vb + vox_per_block < V ? vb + vox_per_block : V;
+    const int c = threadIdx.x % C, lane_v = threadIdx.x / C, nv = blockDim.x / C;
+    float s = 0.f;
+    if (lane_v < nv)
+        for (long long v = vb + lane_v; v < ve; v += nv) s += __bfloat162float(gy[v * C + c]);
+    part[threadIdx.x] = (lane_v < nv) ? s : 0.f;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float t = 0.f;
+        for (int k = 0; k < nv; ++k) t += part[k * C + threadIdx.x];
+        atomicAdd(gb + threadIdx.x, t);
+    }
+}
+
+// out_bf16[v][c] = (mask == null || mask[v][c] > 0) ? bf16(g[v][c]) : 0.
+__global__ void mask_to_bf16_kernel(const float *g, int g_stride, int g_off, const bf16 *mask, int m_stride, int m_off,
+                                    int C, long long V, bf16 *out)
+{
+    const long long n = V * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long v = i / C;
+        const int c = (int)(i % C);
+        float val = g[v * g_stride + g_off + c];
+        if (mask && !(__bfloat162float(mask[v * m_stride + m_off + c]) > 0.f)) val = 0.f;
+        out[i] = __float2bfloat16_rn(val);
+    }
+}
+
+// 2x2x2 max pooling of a strided BF16 view into a dense output; arg = index
+// of the first maximum in octant order ox + 2 oy + 4 oz.
+__global__ void maxpool_kernel(const bf16 *in, int in_stride, int in_off, int N, int D, int H, int W, int C, bf16 *out,
+                               uint8_t *arg)
+{
+    const int d2 = D / 2, h2 = H / 2, w2 = W / 2;
+    const long long n_out = (long long)N * d2 * h2 * w2 * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_out; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        long long q = i / C;
+        const int x = (int)(q % w2); q /= w2;
+        const int y = (int)(q % h2); q /= h2;
+        const int z = (int)(q % d2);
+        const long long n = q / d2;
+        float best = 0.f;
+        int bi = 0;
+        for (int o = 0; o < 8; ++o) {
+            const int zz = 2 * z + (o >> 2), yy = 2 * y + ((o >> 1) & 1), xx = 2 * x + (o & 1);
+            const float val = __bfloat162float(in[(((n * D + zz) * H + yy) * W + xx) * in_stride + in_off + c]);
+            if (o == 0 || val > best) { best = val; bi = o; }
+        }
+        out[i] = __float2bfloat16_rn(best);
+        arg[i] = (uint8_t)bi;
+    }
+}
+
+// g_in[argmax] += g_out (FP32; g_in strided view of the fine grid).
+__global__ void maxpool_bwd_kernel(const float *g_out, const uint8_t *arg, int N, int D, int H, int W, int C, float *g_in,
+                                   int in_stride, int in_off)
+{
+    const int d2 = D / 2, h2 = H / 2, w2 = W / 2;
+    const long long n_out = (long long)N * d2 * h2 * w2 * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_out; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        long long q = i / C;
+        const int x = (int)(q % w2); q /= w2;
+        const int y = (int)(q % h2); q /= h2;
+        const int z = (int)(q % d2);
+        const long long n = q / d2;
+        const int o = arg[i];
+        const int zz = 2 * z + (o >> 2), yy = 2 * y + ((o >> 1) & 1), xx = 2 * x + (o & 1);
+        g_in[(((n * D + zz) * H + yy) * W + xx) * in_stride + in_off + c] += g_out[i];
+    }
+}
+
+// Nearest 2x upsampling of a dense coarse BF16 tensor into a strided fine view.
+__global__ void upsample_kernel(const bf16 *in, int N, int d2, int h2, int w2, int C, bf16 *out, int out_stride, int out_off)
+{
+    const int D = 2 * d2, H = 2 * h2, W = 2 * w2;
+    const long long n = (long long)N * D * H * W * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        long long q = i / C;
+        const int x = (int)(q % W); q /= W;
+        const int y = (int)(q % H); q /= H;
+        const int z = (int)(q % D);
+        const long long nn = q / D;
+        out[(q * H * W + (long long)y * W + x) * out_stride + out_off + c] =
+            in[(((nn * d2 + z / 2) * h2 + y / 2) * w2 + x / 2) * C + c];
+    }
+}
+
+// g_in[coarse] = sum over the 8 fine voxels of g_out (strided FP32 view).
+__global__ void upsample_bwd_kernel(const float *g_out, int out_stride, int out_off, int N, int d2, int h2, int w2, int C,
+                                    float *g_in)
+{
+    const int D = 2 * d2, H = 2 * h2, W = 2 * w2;
+    const long long n = (long long)N * d2 * h2 * w2 * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        long long q = i / C;
+        const int x = (int)(q % w2); q /= w2;
+        const int y = (int)(q % h2); q /= h2;
+        const int z = (int)(q % d2);
+        const long long nn = q / d2;
+        float s = 0.f;
+        for (int o = 0; o < 8; ++o) {
+            const int zz = 2 * z + (o >> 2), yy = 2 * y + ((o >> 1) & 1), xx = 2 * x + (o & 1);
+            s += g_out[(((nn * D + zz) * H + yy) * W + xx) * out_stride + out_off + c];
+        }
+        g_in[i] = s;
+    }
+}
+
+// Network input: x16[v][0..1] = bf16(in[v][0..1]), channels 2..15 zero.
+__global__ void input_kernel(const float *in, long long V, bf16 *x16)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V * 16; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % 16);
+        x16[i] = __float2bfloat16_rn(c < 2 ? in[(i / 16) * 2 + c] : 0.f);
+    }
+}
+
+// Prediction = head channel 0; MSE loss and its gradient into head channel 0.
+__global__ void mse_kernel(const float *head, const float *target, long long V, float *pred, float *ghead, double *loss)
+{
+    __shared__ double part[256];
+    double s = 0.0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        const float p = head[v * 16];
+        if (pred) pred[v] = p;
+        if (target) {
+            const float d = p - target[v];
+            s += (double)d * d;
+            if (ghead) ghead[v * 16] = 2.0f * d / (float)V;
+        }
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && loss && target) atomicAdd(loss, part[0] / (double)V);
+}
+
+// Adam on FP32 master weights; writes the BF16 copy used by the kernels.
+__global__ void adam_kernel(float *w, float *m, float *v, const float *g, long long n, float lr, float b1, float b2,
+                            float eps, float c1, float c2, bf16 *w16)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        w[i] = wi;
+        if (w16) w16[i] = __float2bfloat16_rn(wi);
+    }
+}
+
+__global__ void to_bf16_kernel(const float *src, long long n, bf16 *dst)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+inline int grid_1d(long long n, int block = 256)
+{
+    long long g = (n + block - 1) / block;
+    return (int)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
+}
+
+inline int pick_bn(int C) { return (C % 64 == 0) ? 64 : (C % 32 == 0) ? 32 : 16; }
+
+cudaError_t conv_launch(const ConvArgs &a, cudaStream_t s)
+{
+    const long long V = (long long)a.N * a.D * a.H * a.W;
+    const int bn = pick_bn(a.Cout);
+    dim3 grid((unsigned)((V + 63) / 64), (unsigned)(a.Cout / bn));
+    if (bn == 64) conv3d_kernel<64><<<grid, 128, 0, s>>>(a);
+    else if (bn == 32) conv3d_kernel<32><<<grid, 128, 0, s>>>(a);
+    else conv3d_kernel<16><<<grid, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t wgrad_launch(const WgradArgs &a0, cudaStream_t s)
+{
+    WgradArgs a = a0;
+    const long long V = (long long)a.N * a.D * a.H * a.W;
+    a.vox_per_block = 4096;
+    const int cot = pick_bn(a.Cout);
+    dim3 grid((unsigned)((V + a.vox_per_block - 1) / a.vox_per_block), (unsigned)(a.Cout / cot),
+              (unsigned)(27 * (a.Cin / 16)));
+    if (cot == 64) conv3d_wgrad_kernel<64><<<grid, 128, 0, s>>>(a);
+    else if (cot == 32) conv3d_wgrad_kernel<32><<<grid, 128, 0, s>>>(a);
+    else conv3d_wgrad_kernel<16><<<grid, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t bias_grad_launch(const bf16 *gy, int C, long long V, float *gb, cudaStream_t s)
+{
+    const long long per = 4096;
+    bias_grad_kernel<<<(unsigned)((V + per - 1) / per), 256, 0, s>>>(gy, C, V, per, gb);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The U-Net
+// ---------------------------------------------------------------------------
+constexpr int kLayers = 15;
+struct LayerSpec { int cin, cout, relu; };
+constexpr LayerSpec kSpec[kLayers] = {
+    {16, 16, 1}, {16, 16, 1}, {16, 32, 1}, {32, 32, 1}, {32, 64, 1}, {64, 64, 1}, {64, 128, 1}, {128, 128, 1},
+    {192, 64, 1}, {64, 64, 1}, {96, 32, 1}, {32, 32, 1}, {48, 16, 1}, {16, 16, 1}, {16, 16, 0}};
+
+template <class T>
+struct Buf {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaError_t alloc(size_t count)
+    {
+        n = count;
+        return cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    }
+    void release() { if (p) cudaFree(p); p = nullptr; n = 0; }
+};
+
+struct Net {
+    int device = 0;
+    int batch = 0, S = 0;
+    long long V0 = 0, V1 = 0, V2 = 0, V3 = 0;     // voxels per level (all samples)
+    // parameters
+    Buf<float> w32[kLayers], b32[kLayers], gw[kLayers], gb[kLayers], mw[kLayers], vw[kLayers], mb[kLayers], vb[kLayers];
+    Buf<bf16> w16[kLayers], wt[kLayers];
+    long long adam_t = 0;
+    // activations (BF16)
+    Buf<bf16> x16, e0a, cat0, p0, e1a, cat1, p1, e2a, cat2, p2, b_a, b_b, d2a, d2b, d1a, d1b, d0a, d0b;
+    Buf<uint8_t> arg0, arg1, arg2;
+    Buf<float> head;
+    // gradients (FP32) and a BF16 staging buffer
+    Buf<float> g_head, g_d0b, g_d0a, g_cat0, g_d1b, g_d1a, g_cat1, g_d2b, g_d2a, g_cat2, g_bb, g_ba, g_p2, g_e2a, g_p1,
+        g_e1a, g_p0, g_e0a;
+    Buf<bf16> gstage;
+    Buf<double> loss;
+
+    template <class F>
+    void each(F f)
+    {
+        for (int l = 0; l < kLayers; ++l) {
+            f(w32[l]); f(b32[l]); f(gw[l]); f(gb[l]); f(mw[l]); f(vw[l]); f(mb[l]); f(vb[l]);
+        }
+        f(head); f(g_head); f(g_d0b); f(g_d0a); f(g_cat0); f(g_d1b); f(g_d1a); f(g_cat1); f(g_d2b); f(g_d2a);
+        f(g_cat2); f(g_bb); f(g_ba); f(g_p2); f(g_e2a); f(g_p1); f(g_e1a); f(g_p0); f(g_e0a);
+    }
+    template <class F>
+    void each16(F f)
+    {
+        for (int l = 0; l < kLayers; ++l) { f(w16[l]); f(wt[l]); }
+        f(x16); f(e0a); f(cat0); f(p0); f(e1a); f(cat1); f(p1); f(e2a); f(cat2); f(p2); f(b_a); f(b_b); f(d2a);
+        f(d2b); f(d1a); f(d1b); f(d0a); f(d0b); f(gstage);
+    }
+    void release()
+    {
+        each([](Buf<float> &b) { b.release(); });
+        each16([](Buf<bf16> &b) { b.release(); });
+        arg0.release(); arg1.release(); arg2.release(); loss.release();
+    }
+};
+
+}  // namespace nn
+}  // namespace soc
+
+using namespace soc::nn;
+
+namespace {
+
+struct NetRegistry {
+    std::vector<Net *> nets;
+};
+NetRegistry g_nets;
+
+Net *net_of(int id)
+{
+    if (id < 0 || id >= (int)g_nets.nets.size() || !g_nets.nets[id]) return nullptr;
+    Net *n = g_nets.nets[id];
+    if (cudaSetDevice(n->device) != cudaSuccess) return nullptr;
+    return n;
+}
+
+#define NNCK(expr)                                        \
+    do {                                                  \
+        cudaError_t e_ = (expr);                          \
+        if (e_ != cudaSuccess) return SOC_ERR_CUDA;       \
+    } while (0)
+
+ConvArgs conv_args(const bf16 *in, int in_stride, int in_off, const bf16 *w, const float *bias, int N, int S, int Cin,
+                   int Cout, int relu)
+{
+    ConvArgs a;
+    memset(&a, 0, sizeof a);
+    a.in = in; a.in_stride = in_stride; a.in_off = in_off; a.w = w; a.bias = bias;
+    a.N = N; a.D = S; a.H = S; a.W = S; a.Cin = Cin; a.Cout = Cout; a.relu = relu;
+    return a;
+}
+
+// forward of one layer into a BF16 view
+soc_status fwd(Net &n, int l, const bf16 *in, int in_stride, int in_off, int S, bf16 *out, int out_stride, int out_off,
+               cudaStream_t s)
+{
+    ConvArgs a = conv_args(in, in_stride, in_off, n.w16[l].p, n.b32[l].p, n.batch, S, kSpec[l].cin, kSpec[l].cout,
+                           kSpec[l].relu);
+    a.out = out; a.out_stride = out_stride; a.out_off = out_off;
+    NNCK(conv_launch(a, s));
+    return SOC_OK;
+}
+
+// backward of one layer: gy (FP32 view, masked by the layer's output y when it
+// has a ReLU) -> gw, gb, and (if gx) gx (FP32 view, accumulate or overwrite)
+soc_status bwd(Net &n, int l, const float *gy, int gy_stride, int gy_off, const bf16 *y, int y_stride, int y_off,
+               const bf16 *x, int x_stride, int x_off, int S, float *gx, int gx_stride, int gx_off, int accumulate,
+               cudaStream_t s)
+{
+    const int Cin = kSpec[l].cin, Cout = kSpec[l].cout;
+    const long long V = (long long)n.batch * S * S * S;
+    mask_to_bf16_kernel<<<grid_1d(V * Cout), 256, 0, s>>>(gy, gy_stride, gy_off, kSpec[l].relu ? y : nullptr, y_stride,
+                                                         y_off, Cout, V, n.gstage.p);
+    NNCK(cudaGetLastError());
+    WgradArgs wa;
+    memset(&wa, 0, sizeof wa);
+    wa.gy = n.gstage.p; wa.gy_stride = Cout; wa.gy_off = 0; wa.x = x; wa.x_stride = x_stride; wa.x_off = x_off;
+    wa.gw = n.gw[l].p; wa.N = n.batch; wa.D = S; wa.H = S; wa.W = S; wa.Cin = Cin; wa.Cout = Cout;
+    NNCK(wgrad_launch(wa, s));
+    NNCK(bias_grad_launch(n.gstage.p, Cout, V, n.gb[l].p, s));
+    if (gx) {
+        ConvArgs a = conv_args(n.gstage.p, Cout, 0, n.wt[l].p, nullptr, n.batch, S, Cout, Cin, 0);
+        a.out_f32 = gx; a.out_stride = gx_stride; a.out_off = gx_off; a.accumulate = accumulate;
+        NNCK(conv_launch(a, s));
+    }
+    return SOC_OK;
+}
+
+soc_status forward(Net &n, const float *d_in, cudaStream_t s)
+{
+    const int S0 = n.S, S1 = S0 / 2, S2 = S0 / 4, S3 = S0 / 8;
+    soc_status st;
+    input_kernel<<<grid_1d(n.V0 * 16), 256, 0, s>>>(d_in, n.V0, n.x16.p);
+    NNCK(cudaGetLastError());
+    if ((st = fwd(n, 0, n.x16.p, 16, 0, S0, n.e0a.p, 16, 0, s))) return st;
+    if ((st = fwd(n, 1, n.e0a.p, 16, 0, S0, n.cat0.p, 48, 32, s))) return st;
+    maxpool_kernel<<<grid_1d(n.V1 * 16), 256, 0, s>>>(n.cat0.p, 48, 32, n.batch, S0, S0, S0, 16, n.p0.p, n.arg0.p);
+    if ((st = fwd(n, 2, n.p0.p, 16, 0, S1, n.e1a.p, 32, 0, s))) return st;
+    if ((st = fwd(n, 3, n.e1a.p, 32, 0, S1, n.cat1.p, 96, 64, s))) return st;
+    maxpool_kernel<<<grid_1d(n.V2 * 32), 256, 0, s>>>(n.cat1.p, 96, 64, n.batch, S1, S1, S1, 32, n.p1.p, n.arg1.p);
+    if ((st = fwd(n, 4, n.p1.p, 32, 0, S2, n.e2a.p, 64, 0, s))) return st;
+    if ((st = fwd(n, 5, n.e2a.p, 64, 0, S2, n.cat2.p, 192, 128, s))) return st;
+    maxpool_kernel<<<grid_1d(n.V3 * 64), 256, 0, s>>>(n.cat2.p, 192, 128, n.batch, S2, S2, S2, 64, n.p2.p, n.arg2.p);
+    if ((st = fwd(n, 6, n.p2.p, 64, 0, S3, n.b_a.p, 128, 0, s))) return st;
+    if ((st = fwd(n, 7, n.b_a.p, 128, 0, S3, n.b_b.p, 128, 0, s))) return st;
+    upsample_kernel<<<grid_1d(n.V2 * 128), 256, 0, s>>>(n.b_b.p, n.batch, S3, S3, S3, 128, n.cat2.p, 192, 0);
+    if ((st = fwd(n, 8, n.cat2.p, 192, 0, S2, n.d2a.p, 64, 0, s))) return st;
+    if ((st = fwd(n, 9, n.d2a.p, 64, 0, S2, n.d2b.p, 64, 0, s))) return st;
+    upsample_kernel<<<grid_1d(n.V1 * 64), 256, 0, s>>>(n.d2b.p, n.batch, S2, S2, S2, 64, n.cat1.p, 96, 0);
+    if ((st = fwd(n, 10, n.cat1.p, 96, 0, S1, n.d1a.p, 32, 0, s))) return st;
+    if ((st = fwd(n, 11, n.d1a.p, 32, 0, S1, n.d1b.p, 32, 0, s))) return st;
+    upsample_kernel<<<grid_1d(n.V0 * 32), 256, 0, s>>>(n.d1b.p, n.batch, S1, S1, S1, 32, n.cat0.p, 48, 0);
+    if ((st = fwd(n, 12, n.cat0.p, 48, 0, S0, n.d0a.p, 16, 0, s))) return st;
+    if ((st = fwd(n, 13, n.d0a.p, 16, 0, S0, n.d0b.p, 16, 0, s))) return st;
+    ConvArgs a = conv_args(n.d0b.p, 16, 0, n.w16[14].p, n.b32[14].p, n.batch, S0, 16, 16, 0);
+    a.out_f32 = n.head.p; a.out_stride = 16; a.out_off = 0;
+    NNCK(conv_launch(a, s));
+    return SOC_OK;
+}
+
+soc_status backward(Net &n, const float *d_target, cudaStream_t s)
+{
+    const int S0 = n.S, S1 = S0 / 2, S2 = S0 / 4, S3 = S0 / 8;
+    soc_status st;
+    for (int l = 0; l < kLayers; ++l) {
+        NNCK(cudaMemsetAsync(n.gw[l].p, 0, n.gw[l].n * 4, s));
+        NNCK(cudaMemsetAsync(n.gb[l].p, 0, n.gb[l].n * 4, s));
+        flip_weights_kernel<<<grid_1d((long long)kSpec[l].cout * 27 * kSpec[l].cin), 256, 0, s>>>(
+            n.w16[l].p, kSpec[l].cout, kSpec[l].cin, n.wt[l].p);
+    }
+    NNCK(cudaMemsetAsync(n.g_head.p, 0, n.g_head.n * 4, s));
+    NNCK(cudaMemsetAsync(n.loss.p, 0, 8, s));
+    mse_kernel<<<grid_1d(n.V0), 256, 0, s>>>(n.head.p, d_target, n.V0, nullptr, n.g_head.p, n.loss.p);
+    NNCK(cudaGetLastError());
+    // decoder level 0
+    if ((st = bwd(n, 14, n.g_head.p, 16, 0, nullptr, 0, 0, n.d0b.p, 16, 0, S0, n.g_d0b.p, 16, 0, 0, s))) return st;
+    if ((st = bwd(n, 13, n.g_d0b.p, 16, 0, n.d0b.p, 16, 0, n.d0a.p, 16, 0, S0, n.g_d0a.p, 16, 0, 0, s))) return st;
+    if ((st = bwd(n, 12, n.g_d0a.p, 16, 0, n.d0a.p, 16, 0, n.cat0.p, 48, 0, S0, n.g_cat0.p, 48, 0, 0, s))) return st;
+    upsample_bwd_kernel<<<grid_1d(n.V1 * 32), 256, 0, s>>>(n.g_cat0.p, 48, 0, n.batch, S1, S1, S1, 32, n.g_d1b.p);
+    // decoder level 1
+    if ((st = bwd(n, 11, n.g_d1b.p, 32, 0, n.d1b.p, 32, 0, n.d1a.p, 32, 0, S1, n.g_d1a.p, 32, 0, 0, s))) return st;
+    if ((st = bwd(n, 10, n.g_d1a.p, 32, 0, n.d1a.p, 32, 0, n.cat1.p, 96, 0, S1, n.g_cat1.p, 96, 0, 0, s))) return st;
+    upsample_bwd_kernel<<<grid_1d(n.V2 * 64), 256, 0, s>>>(n.g_cat1.p, 96, 0, n.batch, S2, S2, S2, 64, n.g_d2b.p);
+    // decoder level 2
+    if ((st = bwd(n, 9, n.g_d2b.p, 64, 0, n.d2b.p, 64, 0, n.d2a.p, 64, 0, S2, n.g_d2a.p, 64, 0, 0, s))) return st;
+    if ((st = bwd(n, 8, n.g_d2a.p, 64, 0, n.d2a.p, 64, 0, n.cat2.p, 192, 0, S2, n.g_cat2.p, 192, 0, 0, s))) return st;
+    upsample_bwd_kernel<<<grid_1d(n.V3 * 128), 256, 0, s>>>(n.g_cat2.p, 192, 0, n.batch, S3, S3, S3, 128, n.g_bb.p);
+    // bottleneck
+    if ((st = bwd(n, 7, n.g_bb.p, 128, 0, n.b_b.p, 128, 0, n.b_a.p, 128, 0, S3, n.g_ba.p, 128, 0, 0, s))) return st;
+    if ((st = bwd(n, 6, n.g_ba.p, 128, 0, n.b_a.p, 128, 0, n.p2.p, 64, 0, S3, n.g_p2.p, 64, 0, 0, s))) return st;
+    maxpool_bwd_kernel<<<grid_1d(n.V3 * 64), 256, 0, s>>>(n.g_p2.p, n.arg2.p, n.batch, S2, S2, S2, 64, n.g_cat2.p, 192,
+                                                          128);
+    // encoder level 2 (its output is the skip slice of cat2)
+    if ((st = bwd(n, 5, n.g_cat2.p, 192, 128, n.cat2.p, 192, 128, n.e2a.p, 64, 0, S2, n.g_e2a.p, 64, 0, 0, s))) return st;
+    if ((st = bwd(n, 4, n.g_e2a.p, 64, 0, n.e2a.p, 64, 0, n.p1.p, 32, 0, S2, n.g_p1.p, 32, 0, 0, s))) return st;
+    maxpool_bwd_kernel<<<grid_1d(n.V2 * 32), 256, 0, s>>>(n.g_p1.p, n.arg1.p, n.batch, S1, S1, S1, 32, n.g_cat1.p, 96, 64);
+    if ((st = bwd(n, 3, n.g_cat1.p, 96, 64, n.cat1.p, 96, 64, n.e1a.p, 32, 0, S1, n.g_e1a.p, 32, 0, 0, s))) return st;
+    if ((st = bwd(n, 2, n.g_e1a.p, 32, 0, n.e1a.p, 32, 0, n.p0.p, 16, 0, S1, n.g_p0.p, 16, 0, 0, s))) return st;
+    maxpool_bwd_kernel<<<grid_1d(n.V1 * 16), 256, 0, s>>>(n.g_p0.p, n.arg0.p, n.batch, S0, S0, S0, 16, n.g_cat0.p, 48, 32);
+    if ((st = bwd(n, 1, n.g_cat0.p, 48, 32, n.cat0.p, 48, 32, n.e0a.p, 16, 0, S0, n.g_e0a.p, 16, 0, 0, s))) return st;
+    if ((st = bwd(n, 0, n.g_e0a.p, 16, 0, n.e0a.p, 16, 0, n.x16.p, 16, 0, S0, nullptr, 0, 0, 0, s))) return st;
+    NNCK(cudaGetLastError());
+    return SOC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+soc_status soc_unet_create(int device, int batch, int side, int *net_id)
+{
+    if (!net_id || batch < 1 || side < 8 || side % 8 != 0) return SOC_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return SOC_ERR_CUDA;
+    Net *n = new (std::nothrow) Net();
+    if (!n) return SOC_ERR_NOMEM;
+    n->device = device;
+    n->batch = batch;
+    n->S = side;
+    n->V0 = (long long)batch * side * side * side;
+    n->V1 = n->V0 / 8; n->V2 = n->V1 / 8; n->V3 = n->V2 / 8;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto &b, size_t cnt) { if (e == cudaSuccess) e = b.alloc(cnt); };
+    for (int l = 0; l < kLayers; ++l) {
+        const size_t nw = (size_t)kSpec[l].cout * 27 * kSpec[l].cin, nb = kSpec[l].cout;
+        A(n->w32[l], nw); A(n->gw[l], nw); A(n->mw[l], nw); A(n->vw[l], nw); A(n->w16[l], nw); A(n->wt[l], nw);
+        A(n->b32[l], nb); A(n->gb[l], nb); A(n->mb[l], nb); A(n->vb[l], nb);
+    }
+    A(n->x16, n->V0 * 16); A(n->e0a, n->V0 * 16); A(n->cat0, n->V0 * 48); A(n->p0, n->V1 * 16);
+    A(n->e1a, n->V1 * 32); A(n->cat1, n->V1 * 96); A(n->p1, n->V2 * 32); A(n->e2a, n->V2 * 64);
+    A(n->cat2, n->V2 * 192); A(n->p2, n->V3 * 64); A(n->b_a, n->V3 * 128); A(n->b_b, n->V3 * 128);
+    A(n->d2a, n->V2 * 64); A(n->d2b, n->V2 * 64); A(n->d1a, n->V1 * 32); A(n->d1b, n->V1 * 32);
+    A(n->d0a, n->V0 * 16); A(n->d0b, n->V0 * 16); A(n->head, n->V0 * 16);
+    A(n->arg0, n->V1 * 16); A(n->arg1, n->V2 * 32); A(n->arg2, n->V3 * 64);
+    A(n->g_head, n->V0 * 16); A(n->g_d0b, n->V0 * 16); A(n->g_d0a, n->V0 * 16); A(n->g_cat0, n->V0 * 48);
+    A(n->g_d1b, n->V1 * 32); A(n->g_d1a, n->V1 * 32); A(n->g_cat1, n->V1 * 96); A(n->g_d2b, n->V2 * 64);
+    A(n->g_d2a, n->V2 * 64); A(n->g_cat2, n->V2 * 192); A(n->g_bb, n->V3 * 128); A(n->g_ba, n->V3 * 128);
+    A(n->g_p2, n->V3 * 64); A(n->g_e2a, n->V2 * 64); A(n->g_p1, n->V2 * 32); A(n->g_e1a, n->V1 * 32);
+    A(n->g_p0, n->V1 * 16); A(n->g_e0a, n->V0 * 16); A(n->gstage, n->V0 * 48); A(n->loss, 1);
+    if (e != cudaSuccess) { n->release(); delete n; return SOC_ERR_NOMEM; }
+    for (int l = 0; l < kLayers; ++l) {
+        cudaMemset(n->mw[l].p, 0, n->mw[l].n * 4); cudaMemset(n->vw[l].p, 0, n->vw[l].n * 4);
+        cudaMemset(n->mb[l].p, 0, n->mb[l].n * 4); cudaMemset(n->vb[l].p, 0, n->vb[l].n * 4);
+        cudaMemset(n->w32[l].p, 0, n->w32[l].n * 4); cudaMemset(n->b32[l].p, 0, n->b32[l].n * 4);
+        cudaMemset(n->w16[l].p, 0, n->w16[l].n * 2);
+    }
+    g_nets.nets.push_back(n);
+    *net_id = (int)g_nets.nets.size() - 1;
+    return SOC_OK;
+}
+
+soc_status soc_unet_destroy(int net_id)
+{
+    Net *n = net_of(net_id);
+    if (!n) return SOC_ERR_ARG;
+    cudaDeviceSynchronize();
+    n->release();
+    delete n;
+    g_nets.nets[net_id] = nullptr;
+    return SOC_OK;
+}
+
+int64_t soc_unet_param_count(void)
+{
+    int64_t c = 0;
+    for (int l = 0; l < kLayers; ++l) c += (int64_t)kSpec[l].cout * 27 * kSpec[l].cin + kSpec[l].cout;
+    return c;
+}
+
+soc_status soc_unet_set_params(int net_id, const float *host)
+{
+    Net *n = net_of(net_id);
+    if (!n || !host) return SOC_ERR_ARG;
+    const float *p = host;
+    for (int l = 0; l < kLayers; ++l) {
+        NNCK(cudaMemcpy(n->w32[l].p, p, n->w32[l].n * 4, cudaMemcpyHostToDevice));
+        p += n->w32[l].n;
+        NNCK(cudaMemcpy(n->b32[l].p, p, n->b32[l].n * 4, cudaMemcpyHostToDevice));
+        p += n->b32[l].n;
+        to_bf16_kernel<<<grid_1d((long long)n->w32[l].n), 256>>>(n->w32[l].p, (long long)n->w32[l].n, n->w16[l].p);
+        NNCK(cudaGetLastError());
+    }
+    NNCK(cudaDeviceSynchronize());
+    n->adam_t = 0;
+    return SOC_OK;
+}
+
+soc_status soc_unet_get_params(int net_id, float *host, int grads)
+{
+    Net *n = net_of(net_id);
+    if (!n || !host) return SOC_ERR_ARG;
+    NNCK(cudaDeviceSynchronize());
+    float *p = host;
+    for (int l = 0; l < kLayers; ++l) {
+        NNCK(cudaMemcpy(p, grads ? n->gw[l].p : n->w32[l].p, n->w32[l].n * 4, cudaMemcpyDeviceToHost));
+        p += n->w32[l].n;
+        NNCK(cudaMemcpy(p, grads ? n->gb[l].p : n->b32[l].p, n->b32[l].n * 4, cudaMemcpyDeviceToHost));
+        p += n->b32[l].n;
+    }
+    return SOC_OK;
+}
+
+soc_status soc_unet_forward(int net_id, const float *d_input, float *d_pred, void *stream)
+{
+    Net *n = net_of(net_id);
+    if (!n || !d_input || !d_pred) return SOC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    soc_status st = forward(*n, d_input, s);
+    if (st) return st;
+    mse_kernel<<<grid_1d(n->V0), 256, 0, s>>>(n->head.p, nullptr, n->V0, d_pred, nullptr, nullptr);
+    NNCK(cudaGetLastError());
+    return SOC_OK;
+}
+
+soc_status soc_unet_backward(int net_id, const float *d_input, const float *d_target, float *d_pred, double *d_loss,
+                             void *stream)
+{
+    Net *n = net_of(net_id);
+    if (!n || !d_input || !d_target) return SOC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    soc_status st = forward(*n, d_input, s);
+    if (st) return st;
+    if (d_pred) {
+        mse_kernel<<<grid_1d(n->V0), 256, 0, s>>>(n->head.p, nullptr, n->V0, d_pred, nullptr, nullptr);
+        NNCK(cudaGetLastError());
+    }
+    if ((st = backward(*n, d_target, s))) return st;
+    if (d_loss) NNCK(cudaMemcpyAsync(d_loss, n->loss.p, 8, cudaMemcpyDeviceToDevice, s));
+    return SOC_OK;
+}
+
+soc_status soc_unet_adam(int net_id, float lr, void *stream)
+{
+    Net *n = net_of(net_id);
+    if (!n || !(lr >= 0.f)) return SOC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    n->adam_t += 1;
+    const float c1 = 1.f - powf(b1, (float)n->adam_t), c2 = 1.f - powf(b2, (float)n->adam_t);
+    for (int l = 0; l < kLayers; ++l) {
+        adam_kernel<<<grid_1d((long long)n->w32[l].n), 256, 0, s>>>(n->w32[l].p, n->mw[l].p, n->vw[l].p, n->gw[l].p,
+                                                                   (long long)n->w32[l].n, lr, b1, b2, eps, c1, c2,
+                                                                   n->w16[l].p);
+        adam_kernel<<<grid_1d((long long)n->b32[l].n), 256, 0, s>>>(n->b32[l].p, n->mb[l].p, n->vb[l].p, n->gb[l].p,
+                                                                   (long long)n->b32[l].n, lr, b1, b2, eps, c1, c2,
+                                                                   nullptr);
+    }
+    NNCK(cudaGetLastError());
+    return SOC_OK;
+}
+
+// --- single-operation entry points (for parity tests and reuse) -----------
+soc_status soc_nn_conv3d(const void *x, int N, int D, int H, int W, int Cin, const void *w, const float *bias, int Cout,
+                         int relu, void *y_bf16, float *y_f32, void *stream)
+{
+    if (!x || !w || (!y_bf16 && !y_f32) || Cin % 16 || Cout % 16 || N < 1 || D < 1 || H < 1 || W < 1) return SOC_ERR_ARG;
+    ConvArgs a;
+    memset(&a, 0, sizeof a);
+    a.in = (const bf16 *)x; a.in_stride = Cin; a.w = (const bf16 *)w; a.bias = bias;
+    a.out = (bf16 *)y_bf16; a.out_f32 = y_f32; a.out_stride = Cout;
+    a.N = N; a.D = D; a.H = H; a.W = W; a.Cin = Cin; a.Cout = Cout; a.relu = relu;
+    NNCK(conv_launch(a, (cudaStream_t)stream));
+    return SOC_OK;
+}
+
+soc_status soc_nn_conv3d_dgrad(const void *gy, int N, int D, int H, int W, int Cout, const void *w, int Cin, void *w_scratch,
+                               float *gx, void *stream)
+{
+    if (!gy || !w || !w_scratch || !gx || Cin % 16 || Cout % 16) return SOC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    flip_weights_kernel<<<grid_1d((long long)Cout * 27 * Cin), 256, 0, s>>>((const bf16 *)w, Cout, Cin, (bf16 *)w_scratch);
+    NNCK(cudaGetLastError());
+    ConvArgs a;
+    memset(&a, 0, sizeof a);
+    a.in = (const bf16 *)gy; a.in_stride = Cout; a.w = (const bf16 *)w_scratch;
+    a.out_f32 = gx; a.out_stride = Cin; a.N = N; a.D = D; a.H = H; a.W = W; a.Cin = Cout; a.Cout = Cin;
+    NNCK(conv_launch(a, s));
+    return SOC_OK;
+}
+
+soc_status soc_nn_conv3d_wgrad(const void *gy, const void *x, int N, int D, int H, int W, int Cin, int Cout, float *gw,
+                               float *gb, void *stream)
+{
+    if (!gy || !x || !gw || Cin % 16 || Cout % 16) return SOC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    WgradArgs wa;
+    memset(&wa, 0, sizeof wa);
+    wa.gy = (const bf16 *)gy; wa.gy_stride = Cout; wa.x = (const bf16 *)x; wa.x_stride = Cin; wa.gw = gw;
+    wa.N = N; wa.D = D; wa.H = H; wa.W = W; wa.Cin = Cin; wa.Cout = Cout;
+    NNCK(wgrad_launch(wa, s));
+    if (gb) NNCK(bias_grad_launch((const bf16 *)gy, Cout, (long long)N * D * H * W, gb, s));
+    return SOC_OK;
+}
+
+}  // extern "C"

@@ -26,7 +26,10 @@ EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "so
            "soc_dust_emission", "soc_absorbed_power", "soc_update_temperature", "soc_iterate",
            "soc_set_launch", "soc_set_refill", "soc_set_max_steps",
            "soc_batch_create", "soc_batch_launch", "soc_batch_destroy", "soc_capture_begin",
-           "soc_capture_end", "soc_graph_launch", "soc_graph_destroy", "soc_simulate_frequency_batch_noalloc"]
+           "soc_capture_end", "soc_graph_launch", "soc_graph_destroy",
+           "soc_unet_create", "soc_unet_destroy", "soc_unet_param_count", "soc_unet_set_params",
+           "soc_unet_get_params", "soc_unet_forward", "soc_unet_backward", "soc_unet_adam",
+           "soc_nn_conv3d", "soc_nn_conv3d_dgrad", "soc_nn_conv3d_wgrad", "soc_simulate_frequency_batch_noalloc"]
 
 
 class GridDesc(C.Structure):
@@ -87,6 +90,17 @@ def _load():
         "soc_capture_end": ([P, P, C.POINTER(I)], I),
         "soc_graph_launch": ([P, I, P], I),
         "soc_graph_destroy": ([P, I], I),
+        "soc_unet_create": ([I, I, I, C.POINTER(I)], I),
+        "soc_unet_destroy": ([I], I),
+        "soc_unet_param_count": ([], C.c_int64),
+        "soc_unet_set_params": ([I, P], I),
+        "soc_unet_get_params": ([I, P, I], I),
+        "soc_unet_forward": ([I, P, P, P], I),
+        "soc_unet_backward": ([I, P, P, P, P, P], I),
+        "soc_unet_adam": ([I, C.c_float, P], I),
+        "soc_nn_conv3d": ([P, I, I, I, I, I, P, P, I, I, P, P, P], I),
+        "soc_nn_conv3d_dgrad": ([P, I, I, I, I, I, P, I, P, P, P], I),
+        "soc_nn_conv3d_wgrad": ([P, P, I, I, I, I, I, I, P, P, P], I),
         "soc_set_max_steps": ([P, C.c_uint32], I),
         "soc_simulate_frequency_batch_noalloc": ([P, P, I, P, P, P, P], I),
     }
@@ -304,3 +318,74 @@ class Context:
                                     _np_ptr(hist), _stream(stream)), ok=(SOC_OK, SOC_ERR_STEP_LIMIT))
         return dict(iterations=r.iterations, converged=bool(r.converged), final_max_dT=r.final_max_dT,
                     steps=r.steps, capped=r.capped, history=hist[:r.iterations].copy())
+
+
+def _nn_check(st, what):
+    if st != SOC_OK:
+        raise SocError(st, what)
+
+
+class UNet:
+    """The learned temperature seed (soc_unet_*): 3D U-Net on cubes of side
+    `side` (multiple of 8), batch `batch`; input (N,S,S,S,2) FP32, output
+    (N,S,S,S) FP32, all torch CUDA tensors."""
+
+    def __init__(self, batch: int, side: int, device: int = 0):
+        nid = C.c_int(-1)
+        _nn_check(lib.soc_unet_create(device, batch, side, C.byref(nid)), "soc_unet_create")
+        self.id = nid.value
+        self.batch, self.side = batch, side
+        self.n_params = int(lib.soc_unet_param_count())
+
+    def close(self):
+        if self.id is not None:
+            lib.soc_unet_destroy(self.id)
+            self.id = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, np.float32)
+        assert flat.size == self.n_params
+        _nn_check(lib.soc_unet_set_params(self.id, _np_ptr(flat)), "soc_unet_set_params")
+
+    def get_params(self, grads: bool = False):
+        out = np.empty(self.n_params, np.float32)
+        _nn_check(lib.soc_unet_get_params(self.id, _np_ptr(out), int(grads)), "soc_unet_get_params")
+        return out
+
+    def forward(self, x, pred, stream=None):
+        _nn_check(lib.soc_unet_forward(self.id, _t_ptr(x), _t_ptr(pred), _stream(stream)), "soc_unet_forward")
+
+    def backward(self, x, target, pred=None, loss=None, stream=None):
+        _nn_check(lib.soc_unet_backward(self.id, _t_ptr(x), _t_ptr(target), _t_ptr(pred), _t_ptr(loss),
+                                        _stream(stream)), "soc_unet_backward")
+
+    def adam(self, lr, stream=None):
+        _nn_check(lib.soc_unet_adam(self.id, C.c_float(lr), _stream(stream)), "soc_unet_adam")
+
+
+def conv3d(x, w, bias=None, relu=False, out=None, out_f32=None, stream=None):
+    """soc_nn_conv3d on channels-last BF16 tensors (N, D, H, W, C)."""
+    N, D, H, W, Cin = x.shape
+    Cout = w.shape[0]
+    _nn_check(lib.soc_nn_conv3d(_t_ptr(x), N, D, H, W, Cin, _t_ptr(w), _t_ptr(bias), Cout, int(relu),
+                                _t_ptr(out), _t_ptr(out_f32), _stream(stream)), "soc_nn_conv3d")
+
+
+def conv3d_dgrad(gy, w, w_scratch, gx, stream=None):
+    N, D, H, W, Cout = gy.shape
+    Cin = w.shape[2]
+    _nn_check(lib.soc_nn_conv3d_dgrad(_t_ptr(gy), N, D, H, W, Cout, _t_ptr(w), Cin, _t_ptr(w_scratch),
+                                      _t_ptr(gx), _stream(stream)), "soc_nn_conv3d_dgrad")
+
+
+def conv3d_wgrad(gy, x, gw, gb=None, stream=None):
+    N, D, H, W, Cout = gy.shape
+    Cin = x.shape[4]
+    _nn_check(lib.soc_nn_conv3d_wgrad(_t_ptr(gy), _t_ptr(x), N, D, H, W, Cin, Cout, _t_ptr(gw), _t_ptr(gb),
+                                      _stream(stream)), "soc_nn_conv3d_wgrad")

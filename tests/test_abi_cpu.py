@@ -15,7 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "soc.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(soc_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(soc_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_every_declared_symbol_is_exported(libsoc):
