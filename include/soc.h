@@ -305,6 +305,10 @@ typedef struct soc_iterate_params {
     uint32_t n_per_cell;       /* dust packages per leaf and frequency          */
     int32_t max_iter;          /* dust iterations after iteration 0 (>= 0)      */
     double dT_tol;             /* stop when max |dT| < dT_tol (K)               */
+    int32_t reuse_constant;    /* 1: skip iteration 0 and reuse the constant-
+                                  source absorption kept by the previous
+                                  soc_iterate call on this cloud               */
+    int32_t reserved;
 } soc_iterate_params;
 
 typedef struct soc_iterate_result {

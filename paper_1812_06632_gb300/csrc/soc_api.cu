@@ -47,6 +47,7 @@ struct CloudHost {
     DevBuf<float> ps_pos, ps_cdf;
     int n_ps = 0;
     bool freed = false;
+    bool has_const = false;            // A_const holds an iteration-0 result
     std::vector<double> bg_I;                  // [n_freq] or empty
     std::vector<double> ps_L_total;            // [n_freq]
     // iteration scratch (library owned)
@@ -853,8 +854,10 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
         return SOC_OK;
     };
     // iteration 0: constant sources, kept as A_const
-    CK(cudaMemsetAsync(cl.A_const.p, 0, sizeof(double) * n, s), "zero A");
-    const uint64_t nsrc[2] = {prm->n_background, prm->n_point};
+    if (prm->reuse_constant && !cl.has_const)
+        return fail(ctx, SOC_ERR_STATE, "reuse_constant: no earlier iteration 0 on this cloud");
+    if (!prm->reuse_constant) CK(cudaMemsetAsync(cl.A_const.p, 0, sizeof(double) * n, s), "zero A");
+    const uint64_t nsrc[2] = {prm->reuse_constant ? 0 : prm->n_background, prm->reuse_constant ? 0 : prm->n_point};
     for (int k = 0; k < 2; ++k) {
         if (!nsrc[k]) continue;
         const int source = k == 0 ? SOC_SRC_BACKGROUND : SOC_SRC_POINT;
@@ -864,6 +867,7 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
         if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit.p, cl.A_const.p, cl.A_const.p, stream)))
             return st;
     }
+    cl.has_const = true;
     if (d_T_seed) {
         CK(cudaMemcpyAsync(d_T_out, d_T_seed, sizeof(float) * n, cudaMemcpyDeviceToDevice, s), "copy seed");
     } else {

@@ -325,3 +325,26 @@ def config_c5(n_clouds: int = 64, n_freq: int = 32, seed: int = 5, sizes=None,
         cl.rho = (cl.rho * scale).astype(np.float32)
     return Workload(f"c5_batch{len(sizes)}_{n_freq}nu", clouds, dust, bg, pos, Ls, nbg, nps,
                     seed=1, extra=dict(sizes=np.asarray(sizes), taus=taus))
+
+
+def config_c4(seed: int, side: int = 64, n_freq: int = 64, side_pc: float = 0.2, n_bg: int = 200_000,
+              n_ps: int = 200_000) -> Workload:
+    """One cloud of the learned-seed training set: side^3 lognormal GRF
+    (field seed = seed, sigma_lnrho ~ U(1, 2)), mean-density centre-to-face
+    tau(1 um) ~ logU(1, 50), 1-3 blackbody point sources (1e4 K,
+    L ~ logU(1e36, 1e37) erg/s) at random positions in the inner half, plus the
+    3-blackbody background.  All draws from numpy.random.default_rng(seed)."""
+    rng = np.random.default_rng(10_000 + seed)
+    sigma = float(rng.uniform(1.0, 2.0))
+    tau = float(np.exp(rng.uniform(np.log(1.0), np.log(50.0))))
+    k = int(rng.integers(1, 4))
+    pos = rng.uniform(0.25, 0.75, size=(k, 3)) * side
+    Lb = np.exp(rng.uniform(np.log(1e36), np.log(1e37), size=k))
+    rho = lognormal_density(side, seed, sigma, -3.5).astype(np.float32)
+    ell = side_pc * PC_CM / side
+    cl = regular(rho, ell=ell)
+    nu = frequency_grid(n_freq)
+    dust = power_law_dust(nu, tau / ((side / 2) * ell))
+    L = np.stack([stellar_luminosity(nu, 1e4, l) for l in Lb])
+    return Workload(f"c4_lognormal{side}_seed{seed}", [cl], dust, [diluted_blackbodies(nu)], [pos], [L],
+                    [n_bg], [n_ps], seed=1, extra=dict(sigma=sigma, tau=tau, n_sources=k))
