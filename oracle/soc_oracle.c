@@ -413,8 +413,6 @@ static int cross_face(const oracle_grid *G, pkg_t *p, int a)
     return 1;
 }
 
-#define W_MIN ((uint64_t)1 << 12)
-
 /* Follow one emitted package to its end.  Per photon-cell step (one segment
  * inside one leaf cell):
  *   s      = min over axes with d_i != 0 of (face_i - x_i) * (1/d_i), ties to
@@ -424,7 +422,8 @@ static int cross_face(const oracle_grid *G, pkg_t *p, int a)
  *            s' = min(tau_f / ksh, s), else s' = s;
  *   q      = 1 - exp(-((rho * kabs) * h) * s'),
  *            dep = min(W, rint(float(W) * q)), W -= dep (exact in integers);
- *   W < 2^12 ends the package with W deposited in the cell;
+ *   W < max(W0 / 2^20, 1) (W0 = initial weight; 2^12 for a full package)
+ *            ends the package with W deposited in the cell;
  *   a scattering moves x by d s', draws a new HG direction and a new tau_f;
  *   a face crossing subtracts dtau from tau_f, flushes the cell's merged
  *            deposits, places x exactly on the face and finds the neighbour.
@@ -435,6 +434,8 @@ static uint32_t propagate(const oracle_grid *G, const oracle_item *it, rng_t *r,
 {
     pkg_t p = *pp;
     st->emitted += (int64_t)p.W;
+    /* packages end once attenuated below 2^-20 of their initial weight */
+    const uint64_t w_min = (p.W >> 20) > 0 ? (p.W >> 20) : 1;
     set_inverse(&p);
     float tauf = -oracle_log(rng_u(r));
     uint64_t pend = 0;
@@ -476,7 +477,7 @@ static uint32_t propagate(const oracle_grid *G, const oracle_item *it, rng_t *r,
             p.W -= dep;
             pend += dep;
         }
-        if (p.W < W_MIN) { pend += p.W; p.W = 0; break; }
+        if (p.W < w_min) { pend += p.W; p.W = 0; break; }
         if (scatter) {
             for (int i = 0; i < 3; ++i) p.x[i] = clamp01(p.x[i] + p.d[i] * sp);
             hg_scatter(r, it->g, p.d);

@@ -8,7 +8,6 @@
 namespace soc {
 
 constexpr uint32_t kLinkBit = 0x80000000u;   // cell word: bit 31 = refined
-constexpr uint64_t kWMin = 1ull << 12;       // packages below this weight end
 constexpr int kTableN = 4096;                // T grid of the emission table
 constexpr double kTMin = 2.7, kTMax = 3000.0;
 

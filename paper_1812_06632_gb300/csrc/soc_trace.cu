@@ -60,6 +60,7 @@ struct Pkg {
     float tauf;                   // remaining scattering optical depth
     uint64_t W;                   // weight (fixed point)
     uint64_t pend;                // deposits in the current cell not yet added
+    uint64_t wmin;                // end below this weight: max(W0 / 2^20, 1)
     uint32_t steps;
 };
 
@@ -341,7 +342,7 @@ __device__ __forceinline__ int step(const DevCloud &C, Pkg &p, Rng &r, float kab
         p.W -= dep;
         p.pend += dep;
     }
-    if (p.W < kWMin) { p.pend += p.W; p.W = 0; return kAbsorbed; }
+    if (p.W < p.wmin) { p.pend += p.W; p.W = 0; return kAbsorbed; }
     if (scatter) {
         p.x = clamp01(__fadd_rn(p.x, __fmul_rn(p.dx, sp)));
         p.y = clamp01(__fadd_rn(p.y, __fmul_rn(p.dy, sp)));
@@ -437,6 +438,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
                        (uint32_t)IT.source);
                 p.steps = 0; p.pend = 0;
                 if (emit(*C, IT, pid, r, p)) {
+                    p.wmin = (p.W >> 20) ? (p.W >> 20) : 1ull;
                     set_inverse(p);
                     p.tauf = -log_pos(r.u());
                     if (acc_item != item) {

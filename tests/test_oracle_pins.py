@@ -476,3 +476,18 @@ def test_dust_weights():
     assert W[3] == 2 ** 32 and W[0] == 0 and W[1] == round(2 ** 32 / 5)
     assert W[4] == 2 ** 32
     assert abs(e * 2 ** 32 * 3 - 5.0) < 1e-12
+
+
+def test_faint_dust_package_is_not_dumped_into_its_own_cell():
+    """A dust package carries W0 = 2^32 L_c / max L; a faint one (small W0)
+    must deposit its energy along the same path as a bright one, scaled by
+    W0, instead of ending at once in the emitting cell (which would make the
+    cell re-absorb its own emission)."""
+    cl = I.regular(np.ones((6, 6, 6), np.float32))
+    leaf = cl.leaves()
+    G = _grid(cl)
+    kw = dict(source=oracle.SRC_DUST, kabs=0.05, ksca=0.0, seed=4, leaf=leaf, n_per_cell=1, n_packages=leaf.size)
+    big = oracle.trace(G, dust_w=np.full(leaf.size, 2 ** 32, np.uint64), **kw)[0].astype(np.float64)
+    small = oracle.trace(G, dust_w=np.full(leaf.size, 2 ** 11, np.uint64), **kw)[0].astype(np.float64)
+    assert small.sum() > 0
+    np.testing.assert_allclose(small / small.sum(), big / big.sum(), atol=2e-3)
