@@ -211,8 +211,9 @@ def run_gpu(args):
     cid = ctx.grid_upload(cl)
     ctx.sources_upload(cid, w.bg_I[0])
     # rank r traces package ids [r N, (r+1) N) of every frequency (weak scaling)
-    specs = [dict(source=0, freq=f, pid_offset=rank * N_PACKAGES, n_packages=N_PACKAGES,
-                  tally_offset=f * cl.n_cells) for f in range(nf)]
+    from paper_1812_06632_gb300 import shard
+    specs = shard.shard_items([dict(source=0, freq=f, n_packages=N_PACKAGES, tally_offset=f * cl.n_cells)
+                               for f in range(nf)], rank, world)
     stream = torch.cuda.Stream()
     tally = torch.zeros(nf * cl.n_cells, dtype=torch.int64, device="cuda")
     stats = torch.zeros((nf, 4), dtype=torch.int64, device="cuda")
@@ -242,7 +243,7 @@ def run_gpu(args):
             if ev:
                 ev[1].record(stream)
             if world > 1:
-                dist.all_reduce(tally)
+                shard.allreduce_counters(tally)
             ctx.graph_launch(g_temp, stream=stream)
             if ev:
                 ev[2].record(stream)
