@@ -100,7 +100,9 @@ def init_params(seed=0):
 
 
 def train(X, Y, side, epochs=30, batch=4, lr=1e-3, seed=0, log=print):
-    """Adam on MSE of the residual; returns the trained net and loss history."""
+    """Adam on MSE of the normalised residual (Y is already normalised, so a
+    constant predictor scores 1); the learning rate decays linearly to 10 %.
+    Returns the trained net and the loss history."""
     import torch
     from . import soc
     net = soc.UNet(batch, side)
@@ -119,7 +121,7 @@ def train(X, Y, side, epochs=30, batch=4, lr=1e-3, seed=0, log=print):
             xb = Xd.index_select(0, idx).contiguous()
             yb = Yd.index_select(0, idx).contiguous()
             net.backward(xb, yb, loss=loss)
-            net.adam(lr * (0.5 if ep >= epochs * 2 // 3 else 1.0))
+            net.adam(lr * (1.0 - 0.9 * ep / max(1, epochs - 1)))
             tot += loss.item()
         hist.append(tot / max(1, n // batch))
         log(f"epoch {ep}: loss {hist[-1]:.5f}")
@@ -132,7 +134,7 @@ def predict_seed(net, T1, rho, side, stats):
     x = torch.from_numpy(np.repeat(features(T1, rho, side, stats)[None], net.batch, axis=0)).cuda()
     pred = torch.empty((net.batch, side, side, side), dtype=torch.float32, device="cuda")
     net.forward(x, pred)
-    p = pred[0].reshape(-1)
+    p = pred[0].reshape(-1) * stats["y_std"] + stats["y_mean"]
     return torch.clamp(torch.from_numpy(T1).cuda() * torch.exp(p), T_MIN, T_MAX).contiguous()
 
 
@@ -142,6 +144,10 @@ def compare(net, seeds, side, stats, max_iter=60, tol=0.1, log=print):
     import torch
     from . import soc
     rows = []
+    # one untimed forward: loads the network's kernels before the timed runs
+    w0 = I.config_c4(int(seeds[0]), side=side)
+    predict_seed(net, np.full(w0.clouds[0].n_cells, 10.0, np.float32), w0.clouds[0].rho, side, stats)
+    torch.cuda.synchronize()
     for s in seeds:
         w = I.config_c4(int(s), side=side)
         res = {}
@@ -176,9 +182,10 @@ def main():
     ap.add_argument("--side", type=int, default=64)
     ap.add_argument("--train", type=int, default=160)
     ap.add_argument("--test", type=int, default=20)
-    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--max-iter", type=int, default=60)
     ap.add_argument("--tol", type=float, default=0.1)
+    ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--out", default=os.path.join("gpurun_out", "learned_seed.json"))
     a = ap.parse_args()
     t0 = time.perf_counter()
@@ -189,9 +196,11 @@ def main():
     stats = norm_stats(T1, rho)
     X = np.stack([features(T1[i], rho[i], a.side, stats) for i in range(len(train_seeds))])
     Y = (np.log(np.clip(T, T_MIN, T_MAX)) - np.log(np.clip(T1, T_MIN, T_MAX))).reshape(-1, a.side, a.side, a.side)
-    Y = Y.astype(np.float32)
+    stats["y_mean"] = float(Y.mean())
+    stats["y_std"] = float(Y.std() + 1e-12)
+    Y = ((Y - stats["y_mean"]) / stats["y_std"]).astype(np.float32)
     t1 = time.perf_counter()
-    net, hist = train(X, Y, a.side, epochs=a.epochs)
+    net, hist = train(X, Y, a.side, epochs=a.epochs, lr=a.lr)
     t_train = time.perf_counter() - t1
     rows = compare(net, test_seeds, a.side, stats, a.max_iter, a.tol)
     summary = dict(side=a.side, n_train=a.train, n_test=a.test, epochs=a.epochs, tol_K=a.tol,
