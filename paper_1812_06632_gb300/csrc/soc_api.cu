@@ -39,9 +39,8 @@ struct CloudHost {
     int64_t n_cells = 0, n_root = 0, n_leaf = 0;
     std::vector<int64_t> level_start;
     double ell = 1.0;
-    DevBuf<uint32_t> cell, tcell;
-    DevBuf<int32_t> parent, leaf, tparent;
-    int nbx = 0, nby = 0, n_root_pad = 0, delta = 0;
+    DevBuf<uint32_t> cell;
+    DevBuf<int32_t> parent, leaf;
     DevBuf<float> rho;
     DevBuf<double> volume;
     DevBuf<float2> kappa;
@@ -163,8 +162,6 @@ soc_status sync_clouds(soc_ctx *ctx)
         DevCloud &d = v[i];
         memset(&d, 0, sizeof d);
         d.cell = c.cell.p; d.parent = c.parent.p; d.leaf = c.leaf.p; d.rho = c.rho.p;
-        d.tcell = c.tcell.p; d.tparent = c.tparent.p;
-        d.nbx = c.nbx; d.nby = c.nby; d.n_root_pad = c.n_root_pad; d.delta = c.delta;
         d.volume = c.volume.p; d.kappa = c.kappa.p; d.ps_pos = c.ps_pos.p; d.ps_cdf = c.ps_cdf.p;
         d.nx = c.nx; d.ny = c.ny; d.nz = c.nz; d.n_levels = c.n_levels; d.n_ps = c.n_ps;
         d.n_cells = c.n_cells; d.n_root = c.n_root; d.n_leaf = c.n_leaf;
@@ -215,7 +212,6 @@ soc_status soc_create(soc_ctx **out, int device, uint64_t seed)
 static void release_cloud(CloudHost *c)
 {
     c->cell.release(); c->parent.release(); c->leaf.release(); c->rho.release();
-    c->tcell.release(); c->tparent.release();
     c->volume.release(); c->kappa.release(); c->ps_pos.release(); c->ps_cdf.release();
     c->tally.release(); c->A_const.release(); c->A.release(); c->dust_w.release();
     c->e_unit.release(); c->stats.release();
@@ -400,24 +396,8 @@ extern "C" soc_status soc_grid_upload(soc_ctx *ctx, const soc_grid_desc *d, int 
             leaf.push_back((int32_t)c);
         }
     }
-    // traversal copy: root grid in 4x4x4 bricks, refined levels shifted by delta
-    const int nbx = (d->nx + 3) / 4, nby = (d->ny + 3) / 4, nbz = (d->nz + 3) / 4;
-    const int64_t n_root_pad = (int64_t)nbx * nby * nbz * 64;
-    if (n_root_pad + (n - n_root) >= ((int64_t)1 << 31)) return fail(ctx, SOC_ERR_GRID, "grid too large");
-    const int64_t delta = n_root_pad - n_root;
-    auto tindex = [&](int64_t c) -> int64_t {
-        if (c >= n_root) return c + delta;
-        const int i = (int)(c % d->nx), j = (int)((c / d->nx) % d->ny), k = (int)(c / ((int64_t)d->nx * d->ny));
-        return ((((int64_t)(k >> 2) * nby + (j >> 2)) * nbx + (i >> 2)) << 6) | ((k & 3) << 4) | ((j & 3) << 2) | (i & 3);
-    };
-    std::vector<uint32_t> tword(n_root_pad + (n - n_root), 0u);
-    for (int64_t c = 0; c < n; ++c)
-        tword[tindex(c)] = (child[c] >= 0) ? (kLinkBit | (uint32_t)(child[c] + delta)) : word[c];
-    std::vector<int32_t> tpar(n_oct);
-    for (int64_t k = 0; k < n_oct; ++k) tpar[k] = (int32_t)tindex(parent[k]);
     CloudHost *cl = new (std::nothrow) CloudHost();
     if (!cl) return fail(ctx, SOC_ERR_NOMEM, "host allocation");
-    cl->nbx = nbx; cl->nby = nby; cl->n_root_pad = (int)n_root_pad; cl->delta = (int)delta;
     cl->nx = d->nx; cl->ny = d->ny; cl->nz = d->nz; cl->n_levels = d->n_levels;
     cl->n_cells = n; cl->n_root = n_root; cl->n_leaf = (int64_t)leaf.size(); cl->level_start = start;
     cl->ell = d->root_cell_size;
@@ -429,14 +409,10 @@ extern "C" soc_status soc_grid_upload(soc_ctx *ctx, const soc_grid_desc *d, int 
         (e = cudaMemcpy(cl->parent.p, parent.data(), 4 * n_oct, cudaMemcpyHostToDevice)) == cudaSuccess &&
         (e = cudaMemcpy(cl->leaf.p, leaf.data(), 4 * leaf.size(), cudaMemcpyHostToDevice)) == cudaSuccess &&
         (e = cudaMemcpy(cl->rho.p, rho.data(), 4 * n, cudaMemcpyHostToDevice)) == cudaSuccess &&
-        (e = cudaMemcpy(cl->volume.p, vol.data(), 8 * n, cudaMemcpyHostToDevice)) == cudaSuccess &&
-        (e = cl->tcell.alloc(tword.size())) == cudaSuccess && (e = cl->tparent.alloc(n_oct)) == cudaSuccess &&
-        (e = cudaMemcpy(cl->tcell.p, tword.data(), 4 * tword.size(), cudaMemcpyHostToDevice)) == cudaSuccess &&
-        (e = cudaMemcpy(cl->tparent.p, tpar.data(), 4 * n_oct, cudaMemcpyHostToDevice)) == cudaSuccess) {
+        (e = cudaMemcpy(cl->volume.p, vol.data(), 8 * n, cudaMemcpyHostToDevice)) == cudaSuccess) {
     }
     if (e != cudaSuccess) {
         cl->cell.release(); cl->parent.release(); cl->leaf.release(); cl->rho.release(); cl->volume.release();
-        cl->tcell.release(); cl->tparent.release();
         delete cl;
         return cuda_fail(ctx, e, "grid upload");
     }
@@ -1025,8 +1001,6 @@ extern "C" soc_status soc_simulate_frequency_batch_noalloc(soc_ctx *ctx, const s
         memset(&d, 0, sizeof d);
         if (c.freed) continue;
         d.cell = c.cell.p; d.parent = c.parent.p; d.leaf = c.leaf.p; d.rho = c.rho.p;
-        d.tcell = c.tcell.p; d.tparent = c.tparent.p;
-        d.nbx = c.nbx; d.nby = c.nby; d.n_root_pad = c.n_root_pad; d.delta = c.delta;
         d.volume = c.volume.p; d.kappa = c.kappa.p; d.ps_pos = c.ps_pos.p; d.ps_cdf = c.ps_cdf.p;
         d.nx = c.nx; d.ny = c.ny; d.nz = c.nz; d.n_levels = c.n_levels; d.n_ps = c.n_ps;
         d.n_cells = c.n_cells; d.n_root = c.n_root; d.n_leaf = c.n_leaf;

@@ -14,20 +14,9 @@ constexpr double kTMin = 2.7, kTMax = 3000.0;
 // One uploaded grid as the kernels see it (lives in device memory, in an
 // array indexed by cloud id).  Cell words: FP32 density, or kLinkBit | first
 // child.  Octet k (cells n_root + 8k .. +7) has parent parent[k].
-//
-// The tracer walks a second copy of the cell words, `tcell`, in which the
-// root grid is stored in 4x4x4 bricks (brick-major, x fastest inside a
-// brick) so that one 128-byte line holds a 4x4x2 block of neighbours instead
-// of 32 cells along x; root cell (i,j,k) sits at
-//   ((((k>>2) nby + (j>>2)) nbx + (i>>2)) << 6) | (k&3)<<4 | (j&3)<<2 | (i&3)
-// in [0, n_root_pad), and every refined-level cell c at c + delta
-// (delta = n_root_pad - n_root).  Links in tcell and tparent use these
-// indices; counters stay in the external (caller's) order.
 struct DevCloud {
     const uint32_t *cell;        // [n_cells]
     const int32_t *parent;       // [n_octets]
-    const uint32_t *tcell;       // [n_root_pad + n_cells - n_root] traversal order
-    const int32_t *tparent;      // [n_octets] parents in traversal order
     const int32_t *leaf;         // [n_leaf] leaf cells in increasing order
     const float *rho;            // [n_cells] FP32 density (0 for refined cells)
     const double *volume;        // [n_cells] cm^3
@@ -36,7 +25,6 @@ struct DevCloud {
     const float *ps_cdf;         // [n_freq][n_ps] cumulative luminosity fraction
     int32_t nx, ny, nz, n_levels;
     int32_t n_ps, pad_;
-    int32_t nbx, nby, n_root_pad, delta;
     int64_t n_cells, n_root, n_leaf;
     int64_t level_start[SOC_MAX_LEVELS + 1];
 };

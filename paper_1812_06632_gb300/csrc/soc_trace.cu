@@ -166,17 +166,9 @@ __device__ __forceinline__ int root_axis(float v, int n, float &local)
     return i;
 }
 
-// Traversal index of root cell (i, j, k) (4x4x4 bricks).
 __device__ __forceinline__ int32_t root_cell(const DevCloud &C, int i, int j, int k)
 {
-    return ((((k >> 2) * C.nby + (j >> 2)) * C.nbx + (i >> 2)) << 6) | ((k & 3) << 4) | ((j & 3) << 2) | (i & 3);
-}
-
-// Counter index (caller's order) of the package's current leaf.
-__device__ __forceinline__ int64_t ext_index(const DevCloud &C, const Pkg &p)
-{
-    return (p.cell < C.n_root_pad) ? (int64_t)p.ri + (int64_t)C.nx * (p.rj + (int64_t)C.ny * p.rk)
-                                   : (int64_t)p.cell - C.delta;
+    return i + C.nx * (j + C.ny * k);
 }
 
 // Emission (Sect. 2.2 background and point sources, Sect. 3.2 dust).  Returns
@@ -219,7 +211,7 @@ __device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r,
         p.dz = (a == 2) ? da : d2;
         p.W = it.w0;
         p.cell = root_cell(C, p.ri, p.rj, p.rk);
-        descend(C.tcell, p);
+        descend(C.cell, p);
         return true;
     }
     if (it.source == SOC_SRC_POINT) {
@@ -233,24 +225,23 @@ __device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r,
         isotropic(r, p);
         p.W = it.w0;
         p.cell = root_cell(C, p.ri, p.rj, p.rk);
-        descend(C.tcell, p);
+        descend(C.cell, p);
         return true;
     }
     // dust: n_per_cell packages from every leaf, uniform inside the cell
     const int64_t li = (int64_t)(pid / it.n_per_cell);
-    const int32_t ext = __ldg(C.leaf + li);
+    p.cell = __ldg(C.leaf + li);
     p.W = __ldg(reinterpret_cast<const unsigned long long *>(it.dust_w) + li);
     if (p.W == 0) return false;
     int L = 0;
-    while (L + 1 < C.n_levels && (int64_t)ext >= C.level_start[L + 1]) ++L;
+    while (L + 1 < C.n_levels && (int64_t)p.cell >= C.level_start[L + 1]) ++L;
     p.h = __uint_as_float((uint32_t)(127 - L) << 23);        // 2^-L
-    int32_t anc = ext;
+    int32_t anc = p.cell;
     while ((int64_t)anc >= C.n_root) anc = __ldg(C.parent + ((anc - C.n_root) >> 3));
     p.ri = anc % C.nx;
     p.rj = (anc / C.nx) % C.ny;
     p.rk = anc / (C.nx * C.ny);
-    p.cell = ((int64_t)ext < C.n_root) ? root_cell(C, p.ri, p.rj, p.rk) : ext + C.delta;
-    p.rho = __uint_as_float(__ldg(C.tcell + p.cell));
+    p.rho = __uint_as_float(__ldg(C.cell + p.cell));
     p.x = r.u();
     p.y = r.u();
     p.z = r.u();
@@ -262,7 +253,7 @@ __device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r,
 // Returns false when it leaves the root grid.
 __device__ bool cross_face(const DevCloud &C, Pkg &p, int ax, bool up)
 {
-    const int32_t n_root = C.n_root_pad;
+    const int32_t n_root = (int32_t)C.n_root;
     while (p.cell >= n_root) {
         const int o = (p.cell - n_root) & 7;
         const int b = (o >> ax) & 1;
@@ -272,14 +263,14 @@ __device__ bool cross_face(const DevCloud &C, Pkg &p, int ax, bool up)
             p.x = (ax == 0) ? v : p.x;
             p.y = (ax == 1) ? v : p.y;
             p.z = (ax == 2) ? v : p.z;
-            descend(C.tcell, p);
+            descend(C.cell, p);
             return true;
         }
         p.x = __fmul_rn(__fadd_rn(p.x, (float)(o & 1)), 0.5f);
         p.y = __fmul_rn(__fadd_rn(p.y, (float)((o >> 1) & 1)), 0.5f);
         p.z = __fmul_rn(__fadd_rn(p.z, (float)((o >> 2) & 1)), 0.5f);
         p.h = __fmul_rn(p.h, 2.0f);
-        p.cell = __ldg(C.tparent + ((p.cell - n_root) >> 3));
+        p.cell = __ldg(C.parent + ((p.cell - n_root) >> 3));
     }
     const int step = up ? 1 : -1;
     const int ri = p.ri + ((ax == 0) ? step : 0);
@@ -294,7 +285,7 @@ __device__ bool cross_face(const DevCloud &C, Pkg &p, int ax, bool up)
     p.x = (ax == 0) ? v : p.x;
     p.y = (ax == 1) ? v : p.y;
     p.z = (ax == 2) ? v : p.z;
-    descend(C.tcell, p);
+    descend(C.cell, p);
     return true;
 }
 
@@ -362,7 +353,7 @@ __device__ __forceinline__ int step(const DevCloud &C, Pkg &p, Rng &r, float kab
         return kContinue;
     }
     p.tauf = __fsub_rn(p.tauf, dtau);
-    if (p.pend) { atomicAdd(tally + ext_index(C, p), (unsigned long long)p.pend); p.pend = 0; }
+    if (p.pend) { atomicAdd(tally + p.cell, (unsigned long long)p.pend); p.pend = 0; }
     // move to the exit face: the exit coordinate exactly on the face, the
     // others advanced (selects, so lanes leaving through different faces
     // stay converged)
@@ -476,7 +467,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
         if (active) {
             const int res = step(*C, p, r, kabs, ksca, g, tally, P.max_steps);
             if (res != kContinue) {
-                if (p.pend) atomicAdd(tally + ext_index(*C, p), (unsigned long long)p.pend);
+                if (p.pend) atomicAdd(tally + p.cell, (unsigned long long)p.pend);
                 p.pend = 0;
                 if (res == kEscaped) acc_esc += p.W;
                 if (res == kCapped) acc_cap += 1;
