@@ -213,10 +213,10 @@ def run_gpu(args):
     # rank r traces package ids [r N, (r+1) N) of every frequency (weak scaling)
     from paper_1812_06632_gb300 import shard
     specs = shard.shard_items([dict(source=0, freq=f, n_packages=N_PACKAGES, tally_offset=f * cl.n_cells)
-                               for f in range(nf)], rank, world)
+                               for f in range(0, nf, args.freq_stride)], rank, world)
     stream = torch.cuda.Stream()
     tally = torch.zeros(nf * cl.n_cells, dtype=torch.int64, device="cuda")
-    stats = torch.zeros((nf, 4), dtype=torch.int64, device="cuda")
+    stats = torch.zeros((len(specs), 4), dtype=torch.int64, device="cuda")
     e_host = ctx.package_energy(cid, 0, N_PACKAGES * world)
     e_unit = torch.from_numpy(e_host).cuda()
     A = torch.zeros(cl.n_cells, dtype=torch.float64, device="cuda")
@@ -344,6 +344,82 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_extra(args):
+    """Secondary workloads (one JSON line each; not the headline):
+    c3: octree cloud (64^3 root + 3 levels, 4.4e6 cells), background + 3 point
+        sources, 64 nu x 1e6 packages each, one graph-replayed launch per
+        pass; plus plain time to converged T (max |dT| < 0.1 K);
+    c5: 64 clouds of side 32-128, 32 nu, background + point sources,
+        1e5-1e6 packages per cloud, all in one persistent launch."""
+    import torch
+    from paper_1812_06632_gb300 import build as B
+    B.build()
+    from paper_1812_06632_gb300 import inputs as I
+    from paper_1812_06632_gb300 import soc
+    torch.cuda.set_device(0)
+    t_gen = time.perf_counter()
+    if args.workload == "c3":
+        w = I.config_c3()
+    else:
+        w = I.config_c5()
+    t_gen = time.perf_counter() - t_gen
+    nf = len(w.dust.nu)
+    ctx = soc.Context(0, w.seed)
+    ctx.dust_upload(w.dust.nu, w.dust.kabs, w.dust.ksca, w.dust.g)
+    ids, offs, specs, off = [], [], [], 0
+    for ci, cl in enumerate(w.clouds):
+        cid = ctx.grid_upload(cl)
+        ctx.sources_upload(cid, w.bg_I[ci], w.ps_pos[ci], w.ps_L[ci])
+        ids.append(cid)
+    for ci, cl in enumerate(w.clouds):
+        for src, npk in ((0, w.n_bg[ci]), (1, w.n_ps[ci])):
+            for f in range(nf):
+                specs.append(dict(cloud=ids[ci], source=src, freq=f, n_packages=npk, tally_offset=off))
+                off += cl.n_cells
+    stream = torch.cuda.Stream()
+    tally = torch.zeros(off, dtype=torch.int64, device="cuda")
+    stats = torch.zeros((len(specs), 4), dtype=torch.int64, device="cuda")
+    batch = ctx.batch_create(ctx.items(specs))
+    torch.cuda.synchronize()
+    ctx.capture_begin(stream)
+    ctx.batch_launch(batch, tally, stats, stream=stream)
+    g = ctx.capture_end(stream)
+    for _ in range(args.warmup):
+        ctx.graph_launch(g, stream=stream)
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        ctx.graph_launch(g, stream=stream)
+        ev[k][1].record(stream)
+    stream.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    st = stats.cpu().numpy()
+    steps = float(st[:, 2].sum())
+    assert np.all(st[:, 1] == 0)
+    t_ok = int(tally.sum().item()) + int(st[:, 0].sum()) == int(st[:, 3].sum())
+    out = {"metric": "photon-cell steps/s", "value": steps / (ms / 1e3), "unit": "photon-cell steps/s",
+           "workload": args.workload, "ms_per_launch": ms, "steps_per_launch": steps, "items": len(specs),
+           "clouds": len(w.clouds), "cells": int(sum(c.n_cells for c in w.clouds)), "frequencies": nf,
+           "packages": int(sum(s["n_packages"] for s in specs)), "energy_conserved": bool(t_ok),
+           "roofline_hbm_frac_12B": steps * BYTES_PER_STEP / (ms / 1e3) / 1e9 / _peaks()[0]["hbm_gbs"],
+           "input_generation_s": t_gen}
+    if args.workload == "c3":
+        cl = w.clouds[0]
+        T = torch.empty(cl.n_cells, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = ctx.iterate(ids[0], T, n_background=w.n_bg[0], n_point=w.n_ps[0], n_per_cell=1, max_iter=40, dT_tol=0.1)
+        torch.cuda.synchronize()
+        out["convergence"] = {"wall_s": time.perf_counter() - t0, "dust_iterations": r["iterations"],
+                              "converged": r["converged"], "max_dT_history_K": [round(x, 4) for x in r["history"]],
+                              "photon_cell_steps": r["steps"], "T_max_K": float(T.max().item())}
+    ctx.graph_destroy(g)
+    ctx.batch_destroy(batch)
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -375,11 +451,17 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=4096, help="oracle packages per frequency")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
+                    help="c2 (default, the headline 128^3 x 64 nu pass), c3 octree, c5 uneven 64-cloud batch")
+    ap.add_argument("--freq-stride", type=int, default=1,
+                    help="trace every k-th frequency only (profiling captures of a smaller case)")
     ap.add_argument("--packages", type=int, default=N_PACKAGES,
                     help="packages per frequency (smaller only for profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "c2":
+        run_extra(args)
     else:
         run_gpu(args)
 
