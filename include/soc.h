@@ -383,6 +383,12 @@ soc_status soc_set_launch(soc_ctx *ctx, int threads_per_block, int blocks_per_sm
  * runs for several lanes together instead of one lane at a time.  Results do
  * not depend on it. */
 soc_status soc_set_refill(soc_ctx *ctx, int min_idle_lanes);
+/* A lane whose package has to scatter waits until min_lanes (1..32) lanes of
+ * its warp wait too (or every active lane does); the warp then draws their
+ * new directions together instead of diverging on every scattering.  Each
+ * package's draws and operations keep their order: results do not depend
+ * on it. */
+soc_status soc_set_scatter_batch(soc_ctx *ctx, int min_lanes);
 /* Step cap per package (default 10^7); packages beyond it are ended with
  * their weight deposited and counted in stats[1]. */
 soc_status soc_set_max_steps(soc_ctx *ctx, uint32_t max_steps);

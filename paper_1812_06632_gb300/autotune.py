@@ -3,7 +3,8 @@
 The persistent tracer's speed depends on threads per block, resident blocks
 per SM (which also selects the 80- or 64-register build), the chunk of work
 indices a warp takes from the global counter and the refill threshold (how
-many idle lanes a warp waits for before emitting new packages).  None of
+many idle lanes a warp waits for before emitting new packages) and the
+scattering batch (how many lanes wait to scatter together).  None of
 these changes the results: every candidate's counters are compared with the
 first candidate's and must be identical, bit for bit.
 
@@ -19,8 +20,8 @@ import os
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
-DEFAULT_SPACE = dict(threads_per_block=(128, 256), blocks_per_sm=(0, 4), chunk=(1, 4, 16),
-                     refill=(1, 4, 8, 16))
+DEFAULT_SPACE = dict(threads_per_block=(128, 256), blocks_per_sm=(0, 4), chunk=(4, 16),
+                     refill=(4, 8, 16), scatter=(1, 4, 8, 16))
 
 
 def workload_key(gpu_name: str, specs, clouds) -> str:
@@ -37,7 +38,7 @@ def workload_key(gpu_name: str, specs, clouds) -> str:
 
 def candidates(space=None):
     space = dict(DEFAULT_SPACE, **(space or {}))
-    keys = ["threads_per_block", "blocks_per_sm", "chunk", "refill"]
+    keys = ["threads_per_block", "blocks_per_sm", "chunk", "refill", "scatter"]
     for vals in itertools.product(*(space[k] for k in keys)):
         yield dict(zip(keys, vals))
 
@@ -45,6 +46,7 @@ def candidates(space=None):
 def apply(ctx, cfg):
     ctx.set_launch(cfg["threads_per_block"], cfg["blocks_per_sm"], cfg["chunk"])
     ctx.set_refill(cfg["refill"])
+    ctx.set_scatter_batch(cfg.get("scatter", 1))
 
 
 def load_cache(path=DEFAULT_CACHE):

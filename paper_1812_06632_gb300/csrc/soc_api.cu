@@ -90,7 +90,7 @@ struct soc_ctx {
     std::vector<struct BatchHost *> batches;
     std::vector<cudaGraphExec_t> graphs;
     // launch
-    int tpb = 256, bps = 4, chunk = 16, refill_min = 8;   // autotuned on the 128^3 x 64 nu workload
+    int tpb = 256, bps = 4, chunk = 16, refill_min = 8, scatter_min = 1;   // autotuned on the 128^3 x 64 nu workload
     uint32_t max_steps = 10000000u;
     int sms = 0;
     int occ[2][8] = {};           // resident blocks/SM per (build, threads/32), from soc_create
@@ -267,6 +267,14 @@ soc_status soc_set_refill(soc_ctx *ctx, int min_idle_lanes)
     if (!ctx) return SOC_ERR_ARG;
     if (min_idle_lanes < 1 || min_idle_lanes > 32) return fail(ctx, SOC_ERR_ARG, "min_idle_lanes must be in [1, 32]");
     ctx->refill_min = min_idle_lanes;
+    return SOC_OK;
+}
+
+soc_status soc_set_scatter_batch(soc_ctx *ctx, int min_lanes)
+{
+    if (!ctx) return SOC_ERR_ARG;
+    if (min_lanes < 1 || min_lanes > 32) return fail(ctx, SOC_ERR_ARG, "min_lanes must be in [1, 32]");
+    ctx->scatter_min = min_lanes;
     return SOC_OK;
 }
 
@@ -638,6 +646,7 @@ soc_status soc_simulate_frequency_batch(soc_ctx *ctx, const soc_batch_item *item
     P.max_steps = ctx->max_steps;
     P.chunk = ctx->chunk;
     P.refill_min = ctx->refill_min;
+    P.scatter_min = ctx->scatter_min;
     int grid = 1, variant = 3;
     launch_geometry(ctx, total, grid, variant);
     CK(launch_trace(P, grid, ctx->tpb, variant, s), "trace launch");
@@ -700,6 +709,7 @@ soc_status soc_batch_launch(soc_ctx *ctx, int batch_id, int64_t *d_tally, int64_
     P.max_steps = ctx->max_steps;
     P.chunk = ctx->chunk;
     P.refill_min = ctx->refill_min;
+    P.scatter_min = ctx->scatter_min;
     int grid = 1, variant = 3;
     launch_geometry(ctx, b.total, grid, variant);
     CK(launch_trace(P, grid, ctx->tpb, variant, s), "trace launch");
@@ -1027,6 +1037,7 @@ extern "C" soc_status soc_simulate_frequency_batch_noalloc(soc_ctx *ctx, const s
     P.max_steps = ctx->max_steps;
     P.chunk = ctx->chunk;
     P.refill_min = ctx->refill_min;
+    P.scatter_min = ctx->scatter_min;
     const int variant = ctx->bps >= 4 ? 4 : 3;
     const int limit = trace_block_limit(ctx->tpb, variant);
     const int per_sm = ctx->bps > 0 ? std::min(ctx->bps, limit) : limit;

@@ -53,6 +53,7 @@ struct TraceParams {
     uint32_t max_steps;
     int32_t chunk;
     int32_t refill_min;          // refill a warp's idle lanes once this many are idle
+    int32_t scatter_min;         // scatter a warp's waiting lanes once this many wait
 };
 
 // variant: 3 or 4 = minimum resident 256-thread blocks per SM the kernel is

@@ -62,6 +62,7 @@ struct Pkg {
     uint64_t pend;                // deposits in the current cell not yet added
     uint64_t wmin;                // end below this weight: max(W0 / 2^20, 1)
     uint32_t steps;
+    bool scat;                    // waiting for its scattering (new direction, new free path)
 };
 
 __device__ __forceinline__ void set_inverse(Pkg &p)
@@ -347,9 +348,7 @@ __device__ __forceinline__ int step(const DevCloud &C, Pkg &p, Rng &r, float kab
         p.x = clamp01(__fadd_rn(p.x, __fmul_rn(p.dx, sp)));
         p.y = clamp01(__fadd_rn(p.y, __fmul_rn(p.dy, sp)));
         p.z = clamp01(__fadd_rn(p.z, __fmul_rn(p.dz, sp)));
-        hg_scatter(r, g, p);
-        set_inverse(p);
-        p.tauf = -log_pos(r.u());
+        p.scat = true;            // the new direction is drawn in the warp's scattering phase
         return kContinue;
     }
     p.tauf = __fsub_rn(p.tauf, dtau);
@@ -391,7 +390,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
 
     Pkg p;
     Rng r;
-    p.steps = 0; p.W = 0; p.pend = 0;
+    p.steps = 0; p.W = 0; p.pend = 0; p.scat = false;
     bool active = false;
     int item = -1;
     const DevCloud *C = nullptr;
@@ -436,7 +435,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
                 const uint32_t pid = IT.pid_offset + (uint32_t)(gidx - P.prefix[item]);
                 r.init(P.seed, (uint32_t)IT.iteration, (uint32_t)IT.freq, pid, (uint32_t)IT.cloud,
                        (uint32_t)IT.source);
-                p.steps = 0; p.pend = 0;
+                p.steps = 0; p.pend = 0; p.scat = false;
                 if (emit(*C, IT, pid, r, p)) {
                     p.wmin = (p.W >> 20) ? (p.W >> 20) : 1ull;
                     set_inverse(p);
@@ -464,7 +463,20 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
             if (exhausted) break;
             continue;
         }
-        if (active) {
+        // scattering phase: run the Henyey-Greenstein draw for the waiting
+        // lanes together once scatter_min of them wait (or every active lane
+        // does); a package's draws and operations keep their order
+        {
+            const unsigned act = __ballot_sync(kFull, active);
+            const unsigned sc = __ballot_sync(kFull, active && p.scat);
+            if (sc && (__popc(sc) >= P.scatter_min || sc == act) && active && p.scat) {
+                hg_scatter(r, g, p);
+                set_inverse(p);
+                p.tauf = -log_pos(r.u());
+                p.scat = false;
+            }
+        }
+        if (active && !p.scat) {
             const int res = step(*C, p, r, kabs, ksca, g, tally, P.max_steps);
             if (res != kContinue) {
                 if (p.pend) atomicAdd(tally + p.cell, (unsigned long long)p.pend);

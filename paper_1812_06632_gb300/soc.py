@@ -24,7 +24,7 @@ EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "so
            "soc_dust_upload",
            "soc_sources_upload", "soc_simulate_frequency_batch", "soc_package_energy",
            "soc_dust_emission", "soc_absorbed_power", "soc_update_temperature", "soc_iterate",
-           "soc_set_launch", "soc_set_refill", "soc_set_max_steps",
+           "soc_set_launch", "soc_set_refill", "soc_set_scatter_batch", "soc_set_max_steps",
            "soc_batch_create", "soc_batch_launch", "soc_batch_destroy", "soc_capture_begin",
            "soc_capture_end", "soc_graph_launch", "soc_graph_destroy",
            "soc_unet_create", "soc_unet_destroy", "soc_unet_param_count", "soc_unet_set_params",
@@ -84,6 +84,7 @@ def _load():
         "soc_iterate": ([P, I, C.POINTER(IterateParams), P, P, C.POINTER(IterateResult), P, P], I),
         "soc_set_launch": ([P, I, I, I], I),
         "soc_set_refill": ([P, I], I),
+        "soc_set_scatter_batch": ([P, I], I),
         "soc_batch_create": ([P, P, I, C.POINTER(I)], I),
         "soc_batch_launch": ([P, I, P, C.c_int64, P, P, P], I),
         "soc_batch_destroy": ([P, I], I),
@@ -228,6 +229,9 @@ class Context:
 
     def set_refill(self, min_idle_lanes):
         self._check(lib.soc_set_refill(self.h, min_idle_lanes))
+
+    def set_scatter_batch(self, min_lanes):
+        self._check(lib.soc_set_scatter_batch(self.h, min_lanes))
 
     def set_max_steps(self, n):
         self._check(lib.soc_set_max_steps(self.h, n))

@@ -22,9 +22,9 @@ def test_tuner_candidates_agree_bit_for_bit(tmp_path):
     ctx, ids = gpu_context(w)
     specs = [dict(source=0, freq=f, n_packages=4000, tally_offset=k * cl.n_cells)
              for k, f in enumerate((5, 30, 55))]
-    space = dict(threads_per_block=(64, 256), blocks_per_sm=(0, 4), chunk=(1, 16), refill=(1, 8))
+    space = dict(threads_per_block=(64, 256), blocks_per_sm=(0, 4), chunk=(1, 16), refill=(1, 8), scatter=(1, 8))
     best, res = A.tune(ctx, specs, 3 * cl.n_cells, w.clouds, space=space, reps=1,
                        cache_path=str(tmp_path / "t.json"))
-    assert len(res) == 16 and best in [c for c, _ in res]
+    assert len(res) == 32 and best in [c for c, _ in res]
     best2, res2 = A.tune(ctx, specs, 3 * cl.n_cells, w.clouds, space=space, cache_path=str(tmp_path / "t.json"))
     assert best2 == best

@@ -118,16 +118,19 @@ def test_two_clouds_uneven_batch_bit_exact():
         p += n
 
 
-@pytest.mark.parametrize("tpb,bps,chunk", [(32, 0, 1), (128, 2, 7), (256, 0, 64), (64, 1, 3)])
-def test_launch_shape_does_not_change_results(tpb, bps, chunk):
+@pytest.mark.parametrize("tpb,bps,chunk,refill,scatter", [(32, 0, 1, 1, 1), (128, 2, 7, 4, 8), (256, 0, 64, 16, 32),
+                                                            (64, 1, 3, 32, 3), (256, 4, 16, 8, 16)])
+def test_launch_shape_does_not_change_results(tpb, bps, chunk, refill, scatter):
     w = I.config_c2(n=20, n_freq=64, n_packages=0)
     ctx, ids = gpu_context(w)
     cl = w.clouds[0]
     specs = [dict(source=0, freq=f, n_packages=2500, tally_offset=k * cl.n_cells)
-             for k, f in enumerate((10, 50))]
-    ref = run_gpu(ctx, specs, 2 * cl.n_cells)
+             for k, f in enumerate((10, 50, 63))]
+    ref = run_gpu(ctx, specs, 3 * cl.n_cells)
     ctx.set_launch(tpb, bps, chunk)
-    got = run_gpu(ctx, specs, 2 * cl.n_cells)
+    ctx.set_refill(refill)
+    ctx.set_scatter_batch(scatter)
+    got = run_gpu(ctx, specs, 3 * cl.n_cells)
     for a, b in zip(ref, got):
         np.testing.assert_array_equal(a, b)
 
