@@ -90,7 +90,7 @@ struct soc_ctx {
     std::vector<struct BatchHost *> batches;
     std::vector<cudaGraphExec_t> graphs;
     // launch
-    int tpb = 256, bps = 4, chunk = 16, refill_min = 8, scatter_min = 1;   // autotuned on the 128^3 x 64 nu workload
+    int tpb = 256, bps = 4, chunk = 16, refill_min = 8, scatter_min = 8;   // autotuned on the 128^3 x 64 nu workload
     uint32_t max_steps = 10000000u;
     int sms = 0;
     int occ[2][8] = {};           // resident blocks/SM per (build, threads/32), from soc_create

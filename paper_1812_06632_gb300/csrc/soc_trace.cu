@@ -60,7 +60,7 @@ struct Pkg {
     float tauf;                   // remaining scattering optical depth
     uint64_t W;                   // weight (fixed point)
     uint64_t pend;                // deposits in the current cell not yet added
-    uint64_t wmin;                // end below this weight: max(W0 / 2^20, 1)
+    uint32_t wmin;                // end below this weight: max(W0 / 2^20, 1) <= 2^12
     uint32_t steps;
     bool scat;                    // waiting for its scattering (new direction, new free path)
 };
@@ -343,7 +343,7 @@ __device__ __forceinline__ int step(const DevCloud &C, Pkg &p, Rng &r, float kab
         p.W -= dep;
         p.pend += dep;
     }
-    if (p.W < p.wmin) { p.pend += p.W; p.W = 0; return kAbsorbed; }
+    if (p.W < (uint64_t)p.wmin) { p.pend += p.W; p.W = 0; return kAbsorbed; }
     if (scatter) {
         p.x = clamp01(__fadd_rn(p.x, __fmul_rn(p.dx, sp)));
         p.y = clamp01(__fadd_rn(p.y, __fmul_rn(p.dy, sp)));
@@ -385,7 +385,12 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint64_t span = (uint64_t)P.chunk * 32u;
-    uint64_t q_next = 0, q_end = 0;          // warp-uniform chunk of work indices
+    // the warp's current chunk of work indices [q_next, q_end), kept in shared
+    // memory (read only when lanes refill) to spare registers
+    __shared__ unsigned long long s_q[8][2];
+    unsigned long long *const q = s_q[threadIdx.x >> 5];
+    if (lane == 0) { q[0] = 0; q[1] = 0; }
+    __syncwarp();
     bool exhausted = false;
 
     Pkg p;
@@ -397,9 +402,13 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
     float kabs = 0.f, ksca = 0.f, g = 0.f;
     unsigned long long *tally = nullptr;
     uint64_t gidx = 0;
-    // per-lane statistics, flushed when the lane moves to another item
+    // per-lane statistics, flushed when the lane moves to another item; the
+    // sums live in shared memory (touched once per package) to spare registers
+    __shared__ unsigned long long s_acc[256][3];     // escaped, steps, emitted
+    unsigned long long *const acc = s_acc[threadIdx.x];
+    acc[0] = acc[1] = acc[2] = 0;
     int acc_item = -1;
-    unsigned long long acc_esc = 0, acc_cap = 0, acc_steps = 0, acc_emit = 0;
+    unsigned acc_cap = 0;
 
     for (;;) {
         unsigned idle = __ballot_sync(kFull, !active);
@@ -407,6 +416,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
         // several lanes together), or when the whole warp is idle
         if (__popc(idle) < P.refill_min && idle != kFull) idle = 0;
         while (idle && !exhausted) {
+            uint64_t q_next = q[0], q_end = q[1];
             if (q_next >= q_end) {
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(P.counter, (unsigned long long)span);
@@ -437,26 +447,29 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
                        (uint32_t)IT.source);
                 p.steps = 0; p.pend = 0; p.scat = false;
                 if (emit(*C, IT, pid, r, p)) {
-                    p.wmin = (p.W >> 20) ? (p.W >> 20) : 1ull;
+                    p.wmin = (p.W >> 20) ? (uint32_t)(p.W >> 20) : 1u;
                     set_inverse(p);
                     p.tauf = -log_pos(r.u());
                     if (acc_item != item) {
                         if (acc_item >= 0) {
                             unsigned long long *st = P.stats + 4 * acc_item;
-                            if (acc_esc) atomicAdd(st + 0, acc_esc);
-                            if (acc_cap) atomicAdd(st + 1, acc_cap);
-                            if (acc_steps) atomicAdd(st + 2, acc_steps);
-                            if (acc_emit) atomicAdd(st + 3, acc_emit);
+                            if (acc[0]) atomicAdd(st + 0, acc[0]);
+                            if (acc_cap) atomicAdd(st + 1, (unsigned long long)acc_cap);
+                            if (acc[1]) atomicAdd(st + 2, acc[1]);
+                            if (acc[2]) atomicAdd(st + 3, acc[2]);
                         }
-                        acc_item = item; acc_esc = acc_cap = acc_steps = acc_emit = 0;
+                        acc_item = item; acc_cap = 0;
+                        acc[0] = acc[1] = acc[2] = 0;
                     }
-                    acc_emit += p.W;
+                    acc[2] += p.W;
                     active = true;
                 } else if (P.pkg_steps) {
                     P.pkg_steps[gidx] = 0;
                 }
             }
-            q_next += (uint64_t)take;
+            __syncwarp();
+            if (lane == 0) { q[0] = q_next + (uint64_t)take; q[1] = q_end; }
+            __syncwarp();
             idle = __ballot_sync(kFull, !active);
         }
         if (!__any_sync(kFull, active)) {
@@ -481,9 +494,9 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
             if (res != kContinue) {
                 if (p.pend) atomicAdd(tally + p.cell, (unsigned long long)p.pend);
                 p.pend = 0;
-                if (res == kEscaped) acc_esc += p.W;
+                if (res == kEscaped) acc[0] += p.W;
                 if (res == kCapped) acc_cap += 1;
-                acc_steps += p.steps;
+                acc[1] += p.steps;
                 if (P.pkg_steps) P.pkg_steps[gidx] = p.steps;
                 active = false;
             }
@@ -491,10 +504,10 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
     }
     if (acc_item >= 0) {
         unsigned long long *st = P.stats + 4 * acc_item;
-        if (acc_esc) atomicAdd(st + 0, acc_esc);
-        if (acc_cap) atomicAdd(st + 1, acc_cap);
-        if (acc_steps) atomicAdd(st + 2, acc_steps);
-        if (acc_emit) atomicAdd(st + 3, acc_emit);
+        if (acc[0]) atomicAdd(st + 0, acc[0]);
+        if (acc_cap) atomicAdd(st + 1, (unsigned long long)acc_cap);
+        if (acc[1]) atomicAdd(st + 2, acc[1]);
+        if (acc[2]) atomicAdd(st + 3, acc[2]);
     }
 }
 
