@@ -175,6 +175,15 @@ soc_status soc_simulate_frequency_batch(soc_ctx *ctx, const soc_batch_item *item
                                         int64_t *d_tally, int64_t *d_stats,
                                         uint32_t *d_pkg_steps, void *stream);
 
+/* The same, with a second counter array d_self (device int64, same layout
+ * and offsets as d_tally, accumulated; NULL = none): for dust items it
+ * receives the deposits a package makes in its emission cell before it
+ * first leaves that cell -- the local re-absorption used by the accelerated
+ * (ALI, paper Sect. 2.1.2 / 3.3) temperature update. */
+soc_status soc_simulate_frequency_batch_ex(soc_ctx *ctx, const soc_batch_item *items, int n_items,
+                                           int64_t *d_tally, int64_t *d_self, int64_t *d_stats,
+                                           uint32_t *d_pkg_steps, void *stream);
+
 /* ------------------------------------------------------------------------
  * soc_simulate_frequency_batch_noalloc -- the same call, arguments, results
  * and determinism as soc_simulate_frequency_batch, for callers that must not
@@ -285,6 +294,17 @@ soc_status soc_absorbed_power(soc_ctx *ctx, int cloud_id, const int64_t *d_tally
 soc_status soc_update_temperature(soc_ctx *ctx, int cloud_id, const double *d_A, float *d_T,
                                   double *d_max_dT, void *stream);
 
+/* Accelerated lambda iteration with the diagonal operator (paper Sect. 2.1.2:
+ * ALI solves explicitly for the photons absorbed within the emitting cell;
+ * Sect. 3.3 tests it): with A_self the absorbed power per unit rho V that a
+ * leaf re-absorbed from its own emission in this iteration (from the d_self
+ * counters of soc_simulate_frequency_batch_ex through soc_absorbed_power),
+ * beta = A_self / E(T_prev) (clamped to [0, 0.99], E from the table) and T
+ * solves E(T) (1 - beta) = A - A_self.  Same arguments otherwise as
+ * soc_update_temperature.  Asynchronous on `stream`. */
+soc_status soc_update_temperature_ali(soc_ctx *ctx, int cloud_id, const double *d_A, const double *d_A_self,
+                                      float *d_T, double *d_max_dT, void *stream);
+
 /* ------------------------------------------------------------------------
  * soc_iterate -- the iteration of paper Sect. 2.1.2 / 3.3: iteration 0
  * simulates the constant sources (background, point sources) once and keeps
@@ -308,7 +328,8 @@ typedef struct soc_iterate_params {
     int32_t reuse_constant;    /* 1: skip iteration 0 and reuse the constant-
                                   source absorption kept by the previous
                                   soc_iterate call on this cloud               */
-    int32_t reserved;
+    int32_t ali;               /* 1: accelerated update (diagonal operator,
+                                  soc_update_temperature_ali)                  */
 } soc_iterate_params;
 
 typedef struct soc_iterate_result {

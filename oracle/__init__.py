@@ -83,7 +83,7 @@ def lib():
             for n in ("oracle_exp_neg_v", "oracle_one_minus_exp_v", "oracle_log_v"):
                 getattr(_lib, n).argtypes = [P, P, C.c_int64]
             _lib.oracle_trace.argtypes = [C.POINTER(_Grid), C.POINTER(_Item), C.c_uint32,
-                                          C.c_uint32, P, C.POINTER(_Stats), P]
+                                          C.c_uint32, P, C.POINTER(_Stats), P, P]
             _lib.oracle_hg_samples.argtypes = [C.c_float, P, C.c_uint64, C.c_int64, P, P]
             _lib.oracle_trace_pencil.argtypes = [C.POINTER(_Grid), C.POINTER(_Item), P, P,
                                                  C.c_uint32, P, C.POINTER(_Stats)]
@@ -182,9 +182,11 @@ def trace(grid: Grid, *, source: int, kabs: float, ksca: float, g: float = 0.0,
           seed: int = 1, freq: int = 0, iteration: int = 0, cloud: int = 0,
           pid_lo: int = 0, n_packages: int, w0: int = W_UNIT, max_steps: int = 10_000_000,
           ps_pos=None, ps_cdf=None, n_per_cell: int = 1, leaf=None, dust_w=None,
-          tally=None, want_steps: bool = False):
+          tally=None, want_steps: bool = False, self_tally=None):
     """Trace packages pid_lo .. pid_lo + n_packages - 1 of one (source, freq)
     item.  ``kabs``/``ksca`` are per unit density and per root-cell length.
+    ``self_tally`` (int64[n_cells], accumulated) receives the deposits dust
+    packages make in their emission cell before they first leave it.
     Returns (tally int64[n_cells], stats dict, per-package steps or None)."""
     if tally is None:
         tally = np.zeros(grid.n_cells, np.int64)
@@ -200,7 +202,7 @@ def trace(grid: Grid, *, source: int, kabs: float, ksca: float, g: float = 0.0,
     steps = np.zeros(n_packages, np.uint32) if want_steps else None
     gc = grid._c()
     lib().oracle_trace(C.byref(gc), C.byref(it), pid_lo, pid_lo + n_packages,
-                       _ptr(tally), C.byref(st), _ptr(steps))
+                       _ptr(tally), C.byref(st), _ptr(steps), _ptr(self_tally))
     stats = dict(escaped=st.escaped, capped=st.capped, steps=st.steps, emitted=st.emitted)
     return tally, stats, steps
 

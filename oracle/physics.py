@@ -148,3 +148,14 @@ def dust_weights(L, n_per_cell):
         return np.zeros(L.shape, np.uint64), 0.0
     W = np.rint((L / Lmax) * W_UNIT).astype(np.uint64)
     return W, Lmax / n_per_cell / W_UNIT
+
+
+def temperature_ali(A, A_self, T_old, nu, kabs, beta_max=0.99, **kw):
+    """Accelerated update with the diagonal (one-cell) operator: the part of
+    A that the cell absorbed from its own emission, A_self, is assumed to
+    scale with its emission, A_self(T) = beta E(T) with beta = A_self /
+    E(T_old) (at most beta_max); T solves E(T) (1 - beta) = A - A_self."""
+    E_old = emission_integral(T_old, nu, kabs)
+    beta = min(beta_max, A_self / E_old) if E_old > 0 else 0.0
+    beta = max(beta, 0.0)
+    return temperature((A - A_self) / (1.0 - beta), nu, kabs, **kw)

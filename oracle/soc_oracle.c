@@ -430,9 +430,13 @@ static int cross_face(const oracle_grid *G, pkg_t *p, int a)
  * Deposits made in one cell between two crossings are merged before they are
  * added to tally[cell]. */
 static uint32_t propagate(const oracle_grid *G, const oracle_item *it, rng_t *r, pkg_t *pp,
-                          int64_t *tally, oracle_stats *st)
+                          int64_t *tally, int64_t *self_tally, oracle_stats *st)
 {
     pkg_t p = *pp;
+    /* a dust package is "at home" until it first leaves its emission cell;
+       deposits made at home are also added to self_tally (the local
+       re-absorption used by the accelerated temperature update) */
+    int home = (it->source == SRC_DUST) && self_tally != 0;
     st->emitted += (int64_t)p.W;
     /* packages end once attenuated below 2^-20 of their initial weight */
     const uint64_t w_min = (p.W >> 20) > 0 ? (p.W >> 20) : 1;
@@ -486,7 +490,12 @@ static uint32_t propagate(const oracle_grid *G, const oracle_item *it, rng_t *r,
             continue;
         }
         tauf = tauf - dtau;
-        if (pend) { tally[p.cell] += (int64_t)pend; pend = 0; }
+        if (pend) {
+            tally[p.cell] += (int64_t)pend;
+            if (home) self_tally[p.cell] += (int64_t)pend;
+            pend = 0;
+        }
+        home = 0;
         for (int i = 0; i < 3; ++i)
             p.x[i] = (i == axis) ? ((p.d[i] > 0.0f) ? 1.0f : 0.0f) : clamp01(p.x[i] + p.d[i] * s);
         if (!cross_face(G, &p, axis)) {
@@ -495,7 +504,10 @@ static uint32_t propagate(const oracle_grid *G, const oracle_item *it, rng_t *r,
             break;
         }
     }
-    if (pend) tally[p.cell] += (int64_t)pend;
+    if (pend) {
+        tally[p.cell] += (int64_t)pend;
+        if (home) self_tally[p.cell] += (int64_t)pend;
+    }
     st->steps += steps;
     *pp = p;
     return steps;
@@ -503,24 +515,26 @@ static uint32_t propagate(const oracle_grid *G, const oracle_item *it, rng_t *r,
 
 /* Emit and trace package pid of an item; returns its step count. */
 static uint32_t trace_one(const oracle_grid *G, const oracle_item *it, uint32_t pid,
-                          int64_t *tally, oracle_stats *st)
+                          int64_t *tally, int64_t *self_tally, oracle_stats *st)
 {
     rng_t r;
     rng_init(&r, it->seed, (uint32_t)it->iteration, (uint32_t)it->freq, pid,
              (uint32_t)it->cloud, (uint32_t)it->source);
     pkg_t p;
     if (!emit(G, it, &r, pid, &p)) return 0;
-    return propagate(G, it, &r, &p, tally, st);
+    return propagate(G, it, &r, &p, tally, self_tally, st);
 }
 
 /* Trace packages pid_lo .. pid_hi-1 of one item.  tally[] (n_cells, int64)
  * and *st are accumulated into; pkg_steps (nullable) receives each package's
- * step count at index pid - pid_lo. */
+ * step count at index pid - pid_lo; self_tally (nullable, n_cells) receives
+ * the deposits dust packages make in their emission cell before they first
+ * leave it. */
 void oracle_trace(const oracle_grid *G, const oracle_item *it, uint32_t pid_lo, uint32_t pid_hi,
-                  int64_t *tally, oracle_stats *st, uint32_t *pkg_steps)
+                  int64_t *tally, oracle_stats *st, uint32_t *pkg_steps, int64_t *self_tally)
 {
     for (uint32_t pid = pid_lo; pid < pid_hi; ++pid) {
-        uint32_t n = trace_one(G, it, pid, tally, st);
+        uint32_t n = trace_one(G, it, pid, tally, self_tally, st);
         if (pkg_steps) pkg_steps[pid - pid_lo] = n;
     }
 }
@@ -565,5 +579,5 @@ uint32_t oracle_trace_pencil(const oracle_grid *G, const oracle_item *it, const 
     rng_t r;
     rng_init(&r, it->seed, (uint32_t)it->iteration, (uint32_t)it->freq, pid,
              (uint32_t)it->cloud, (uint32_t)it->source);
-    return propagate(G, it, &r, &p, tally, st);
+    return propagate(G, it, &r, &p, tally, 0, st);
 }

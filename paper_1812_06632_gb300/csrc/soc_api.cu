@@ -51,8 +51,8 @@ struct CloudHost {
     std::vector<double> bg_I;                  // [n_freq] or empty
     std::vector<double> ps_L_total;            // [n_freq]
     // iteration scratch (library owned)
-    DevBuf<int64_t> tally;
-    DevBuf<double> A_const, A;
+    DevBuf<int64_t> tally, self_tally;
+    DevBuf<double> A_const, A, A_self;
     DevBuf<uint64_t> dust_w;
     DevBuf<double> e_unit;
     DevBuf<int64_t> stats;
@@ -214,6 +214,7 @@ static void release_cloud(CloudHost *c)
     c->cell.release(); c->parent.release(); c->leaf.release(); c->rho.release();
     c->volume.release(); c->kappa.release(); c->ps_pos.release(); c->ps_cdf.release();
     c->tally.release(); c->A_const.release(); c->A.release(); c->dust_w.release();
+    c->self_tally.release(); c->A_self.release();
     c->e_unit.release(); c->stats.release();
     c->freed = true;
 }
@@ -614,6 +615,12 @@ static void launch_geometry(soc_ctx *ctx, uint64_t total, int &grid_out, int &va
 soc_status soc_simulate_frequency_batch(soc_ctx *ctx, const soc_batch_item *items, int n_items, int64_t *d_tally,
                                         int64_t *d_stats, uint32_t *d_pkg_steps, void *stream)
 {
+    return soc_simulate_frequency_batch_ex(ctx, items, n_items, d_tally, nullptr, d_stats, d_pkg_steps, stream);
+}
+
+soc_status soc_simulate_frequency_batch_ex(soc_ctx *ctx, const soc_batch_item *items, int n_items, int64_t *d_tally,
+                                           int64_t *d_self, int64_t *d_stats, uint32_t *d_pkg_steps, void *stream)
+{
     if (!ctx || !items || n_items < 1 || !d_tally || !d_stats) return fail(ctx, SOC_ERR_ARG, "null argument");
     if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
@@ -637,6 +644,7 @@ soc_status soc_simulate_frequency_batch(soc_ctx *ctx, const soc_batch_item *item
     P.prefix = ctx->d_prefix.p;
     P.g_hg = ctx->d_g.p;
     P.tally = reinterpret_cast<unsigned long long *>(d_tally);
+    P.self = reinterpret_cast<unsigned long long *>(d_self);
     P.stats = reinterpret_cast<unsigned long long *>(d_stats);
     P.pkg_steps = d_pkg_steps;
     P.counter = ctx->d_counter.p;
@@ -700,6 +708,7 @@ soc_status soc_batch_launch(soc_ctx *ctx, int batch_id, int64_t *d_tally, int64_
     P.prefix = b.prefix.p;
     P.g_hg = ctx->d_g.p;
     P.tally = reinterpret_cast<unsigned long long *>(d_tally);
+    P.self = nullptr;
     P.stats = reinterpret_cast<unsigned long long *>(d_stats);
     P.pkg_steps = d_pkg_steps;
     P.counter = b.counter.p;
@@ -822,6 +831,23 @@ soc_status soc_update_temperature(soc_ctx *ctx, int cloud_id, const double *d_A,
     return SOC_OK;
 }
 
+soc_status soc_update_temperature_ali(soc_ctx *ctx, int cloud_id, const double *d_A, const double *d_A_self, float *d_T,
+                                      double *d_max_dT, void *stream)
+{
+    soc_status st = check_cloud(ctx, cloud_id);
+    if (st) return st;
+    if (!d_A || !d_A_self || !d_T) return fail(ctx, SOC_ERR_ARG, "null argument");
+    if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if ((st = sync_clouds(ctx))) return st;
+    const CloudHost &cl = *ctx->clouds[cloud_id];
+    TempTables tt{ctx->n_freq, ctx->d_w_kabs.p, ctx->d_w.p, ctx->d_nu.p, ctx->d_kabs.p, ctx->d_lnE.p, ctx->d_lnT.p};
+    CK(launch_update_temperature_ali(ctx->d_clouds.p + cloud_id, cl.n_cells, tt, d_A, d_A_self, d_T, d_max_dT,
+                                     (cudaStream_t)stream),
+       "temperature (ALI)");
+    return SOC_OK;
+}
+
 soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm, const float *d_T_seed,
                        float *d_T_out, soc_iterate_result *res, double *dT_history, void *stream)
 {
@@ -842,11 +868,17 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
     CK(cl.e_unit.alloc(nf), "alloc e_unit");
     CK(cl.stats.alloc((size_t)4 * nf), "alloc stats");
     if (prm->max_iter > 0) CK(cl.dust_w.alloc((size_t)nf * cl.n_leaf), "alloc dust weights");
+    const bool ali = prm->ali != 0;
+    if (ali && prm->max_iter > 0) {
+        CK(cl.self_tally.alloc((size_t)nf * n), "alloc self counters");
+        CK(cl.A_self.alloc(n), "alloc A_self");
+    }
     int64_t steps = 0, capped = 0;
     std::vector<int64_t> hstats(4 * nf);
     std::vector<soc_batch_item> items(nf);
     std::vector<double> e(nf);
-    auto run_items = [&](int source, uint64_t npk, int iteration, const uint64_t *dw, uint32_t npc) -> soc_status {
+    auto run_items = [&](int source, uint64_t npk, int iteration, const uint64_t *dw, uint32_t npc,
+                         int64_t *self) -> soc_status {
         for (int f = 0; f < nf; ++f) {
             soc_batch_item &it = items[f];
             memset(&it, 0, sizeof it);
@@ -856,7 +888,9 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
         }
         CK(cudaMemsetAsync(cl.tally.p, 0, sizeof(int64_t) * nf * n, s), "zero tally");
         CK(cudaMemsetAsync(cl.stats.p, 0, sizeof(int64_t) * 4 * nf, s), "zero stats");
-        soc_status r = soc_simulate_frequency_batch(ctx, items.data(), nf, cl.tally.p, cl.stats.p, nullptr, stream);
+        if (self) CK(cudaMemsetAsync(self, 0, sizeof(int64_t) * nf * n, s), "zero self counters");
+        soc_status r = soc_simulate_frequency_batch_ex(ctx, items.data(), nf, cl.tally.p, self, cl.stats.p, nullptr,
+                                                       stream);
         if (r) return r;
         CK(cudaMemcpyAsync(hstats.data(), cl.stats.p, sizeof(int64_t) * 4 * nf, cudaMemcpyDeviceToHost, s), "stats");
         CK(cudaStreamSynchronize(s), "sync");
@@ -871,7 +905,7 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
     for (int k = 0; k < 2; ++k) {
         if (!nsrc[k]) continue;
         const int source = k == 0 ? SOC_SRC_BACKGROUND : SOC_SRC_POINT;
-        if ((st = run_items(source, nsrc[k], 0, nullptr, 1))) return st;
+        if ((st = run_items(source, nsrc[k], 0, nullptr, 1, nullptr))) return st;
         if ((st = soc_package_energy(ctx, cloud_id, source, nsrc[k], e.data()))) return st;
         CK(cudaMemcpyAsync(cl.e_unit.p, e.data(), 8 * nf, cudaMemcpyHostToDevice, s), "copy e_unit");
         if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit.p, cl.A_const.p, cl.A_const.p, stream)))
@@ -889,11 +923,19 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
         if ((st = soc_dust_emission(ctx, cloud_id, d_T_out, 0, nf, prm->n_per_cell, cl.dust_w.p, cl.e_unit.p, stream)))
             return st;
         // frozen dust random numbers: the same RNG stream (iteration 1) every time
-        if ((st = run_items(SOC_SRC_DUST, (uint64_t)cl.n_leaf * prm->n_per_cell, 1, cl.dust_w.p, prm->n_per_cell)))
+        if ((st = run_items(SOC_SRC_DUST, (uint64_t)cl.n_leaf * prm->n_per_cell, 1, cl.dust_w.p, prm->n_per_cell,
+                            ali ? cl.self_tally.p : nullptr)))
             return st;
         if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit.p, cl.A_const.p, cl.A.p, stream)))
             return st;
-        if ((st = soc_update_temperature(ctx, cloud_id, cl.A.p, d_T_out, ctx->d_maxdT.p, stream))) return st;
+        if (ali) {
+            if ((st = soc_absorbed_power(ctx, cloud_id, cl.self_tally.p, n, cl.e_unit.p, nullptr, cl.A_self.p, stream)))
+                return st;
+            if ((st = soc_update_temperature_ali(ctx, cloud_id, cl.A.p, cl.A_self.p, d_T_out, ctx->d_maxdT.p, stream)))
+                return st;
+        } else if ((st = soc_update_temperature(ctx, cloud_id, cl.A.p, d_T_out, ctx->d_maxdT.p, stream))) {
+            return st;
+        }
         CK(cudaMemcpyAsync(&dT, ctx->d_maxdT.p, sizeof(double), cudaMemcpyDeviceToHost, s), "read max dT");
         CK(cudaStreamSynchronize(s), "sync");
         if (dT_history) dT_history[k - 1] = dT;
@@ -1028,6 +1070,7 @@ extern "C" soc_status soc_simulate_frequency_batch_noalloc(soc_ctx *ctx, const s
     P.prefix = S->prefix;
     P.g_hg = ctx->d_g.p;
     P.tally = reinterpret_cast<unsigned long long *>(d_tally);
+    P.self = nullptr;
     P.stats = reinterpret_cast<unsigned long long *>(d_stats);
     P.pkg_steps = d_pkg_steps;
     P.counter = &S->counter;

@@ -44,6 +44,8 @@ struct TraceParams {
     const uint64_t *prefix;      // [n_items + 1] exclusive prefix of n_packages
     const float *g_hg;           // [n_freq]
     unsigned long long *tally;
+    unsigned long long *self;    // nullable: same layout as tally; deposits of dust
+                                 // packages in their emission cell before they leave it
     unsigned long long *stats;   // [n_items][4]
     uint32_t *pkg_steps;         // nullable
     unsigned long long *counter; // global work counter
@@ -76,6 +78,9 @@ cudaError_t launch_absorbed_power(const DevCloud *dcl, int64_t n_cells, const in
                                   const double *A_in, double *A_out, cudaStream_t s);
 cudaError_t launch_update_temperature(const DevCloud *dcl, int64_t n_cells, const TempTables &tt,
                                       const double *A, float *T, double *max_dT, cudaStream_t s);
+cudaError_t launch_update_temperature_ali(const DevCloud *dcl, int64_t n_cells, const TempTables &tt,
+                                          const double *A, const double *A_self, float *T, double *max_dT,
+                                          cudaStream_t s);
 cudaError_t launch_dust_emission(const DevCloud *dcl, int64_t n_leaf, const TempTables &tt, const float *T,
                                  int freq_lo, int n_freq, uint32_t n_per_cell, uint64_t *w,
                                  double *e_unit, unsigned long long *scratch_max, cudaStream_t s);

@@ -116,6 +116,59 @@ __global__ void temperature_kernel(const DevCloud *__restrict__ dcl, int64_t n_c
     if (max_dT) block_max_to(dmax, max_dT);
 }
 
+// T from A by the table (shared by both temperature kernels).
+__device__ __forceinline__ double invert_table(const TempTables &tt, double a)
+{
+    if (!(a > 0.0)) return kTMin;
+    const double la = log(a);
+    if (la <= __ldg(tt.lnE)) return kTMin;
+    if (la >= __ldg(tt.lnE + kTableN - 1)) return kTMax;
+    int lo = 0, hi = kTableN - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(tt.lnE + mid) < la) lo = mid; else hi = mid;
+    }
+    const double e0 = __ldg(tt.lnE + lo), e1 = __ldg(tt.lnE + hi);
+    const double t0 = __ldg(tt.lnT + lo), t1 = __ldg(tt.lnT + hi);
+    return fmin(fmax(exp(t0 + (la - e0) * (t1 - t0) / (e1 - e0)), kTMin), kTMax);
+}
+
+// E(T) from the table (ln E linear in ln T between the log-spaced nodes).
+__device__ __forceinline__ double emission_table(const TempTables &tt, double T)
+{
+    const double l0 = __ldg(tt.lnT), l1 = __ldg(tt.lnT + kTableN - 1);
+    double u = (log(fmin(fmax(T, kTMin), kTMax)) - l0) / (l1 - l0) * (kTableN - 1);
+    int k = (int)u;
+    k = k < 0 ? 0 : (k > kTableN - 2 ? kTableN - 2 : k);
+    const double f = u - k;
+    return exp(__ldg(tt.lnE + k) * (1.0 - f) + __ldg(tt.lnE + k + 1) * f);
+}
+
+// Accelerated update with the diagonal operator: the cell's re-absorption of
+// its own emission, A_self, scales with its emission (beta = A_self / E(T_old),
+// at most 0.99), so T solves E(T) (1 - beta) = A - A_self.
+__global__ void temperature_ali_kernel(const DevCloud *__restrict__ dcl, int64_t n_cells, const TempTables tt,
+                                       const double *__restrict__ A, const double *__restrict__ A_self, float *T,
+                                       unsigned long long *max_dT)
+{
+    const DevCloud &C = *dcl;
+    double dmax = 0.0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n_cells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (__ldg(C.cell + c) & kLinkBit) continue;
+        const double told = (double)T[c];
+        const double as = A_self[c];
+        const double eo = emission_table(tt, told);
+        double beta = eo > 0.0 ? as / eo : 0.0;
+        beta = fmin(fmax(beta, 0.0), 0.99);
+        const double Tn = invert_table(tt, (A[c] - as) / (1.0 - beta));
+        const float Tf = (float)Tn;
+        if (max_dT) dmax = fmax(dmax, fabs((double)Tf - told));
+        T[c] = Tf;
+    }
+    if (max_dT) block_max_to(dmax, max_dT);
+}
+
 // Dust luminosity of leaf li at frequency f: 4 pi rho V kabs B_nu(T), in the
 // order (((4 pi rho) V) kabs) B.
 __device__ __forceinline__ double dust_L(const DevCloud &C, const TempTables &tt, const float *T,
@@ -199,6 +252,19 @@ cudaError_t launch_update_temperature(const DevCloud *dcl, int64_t n_cells, cons
     }
     temperature_kernel<<<grid_for(n_cells, 256), 256, 0, s>>>(
         dcl, n_cells, tt, A, T, reinterpret_cast<unsigned long long *>(max_dT));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_temperature_ali(const DevCloud *dcl, int64_t n_cells, const TempTables &tt,
+                                          const double *A, const double *A_self, float *T, double *max_dT,
+                                          cudaStream_t s)
+{
+    if (max_dT) {
+        cudaError_t e = cudaMemsetAsync(max_dT, 0, sizeof(double), s);
+        if (e != cudaSuccess) return e;
+    }
+    temperature_ali_kernel<<<grid_for(n_cells, 256), 256, 0, s>>>(
+        dcl, n_cells, tt, A, A_self, T, reinterpret_cast<unsigned long long *>(max_dT));
     return cudaGetLastError();
 }
 

@@ -60,10 +60,15 @@ struct Pkg {
     float tauf;                   // remaining scattering optical depth
     uint64_t W;                   // weight (fixed point)
     uint64_t pend;                // deposits in the current cell not yet added
-    uint32_t wmin;                // end below this weight: max(W0 / 2^20, 1) <= 2^12
+    uint32_t wf;                  // bits 0..12: weight floor max(W0 / 2^20, 1) (<= 2^12);
+                                  // kScatBit: waiting for its scattering;
+                                  // kHomeBit: dust package still in its emission cell
     uint32_t steps;
-    bool scat;                    // waiting for its scattering (new direction, new free path)
 };
+
+constexpr uint32_t kFloorMask = 0x1fffu;
+constexpr uint32_t kScatBit = 1u << 30;
+constexpr uint32_t kHomeBit = 1u << 31;
 
 __device__ __forceinline__ void set_inverse(Pkg &p)
 {
@@ -307,7 +312,8 @@ __device__ __forceinline__ uint64_t float_to_w(float v)
 
 // One photon-cell step (one segment inside one leaf).
 __device__ __forceinline__ int step(const DevCloud &C, Pkg &p, Rng &r, float kabs, float ksca,
-                                    float g, unsigned long long *tally, uint32_t max_steps)
+                                    float g, unsigned long long *tally, unsigned long long *self,
+                                    uint32_t max_steps)
 {
     if (p.steps >= max_steps) { p.pend += p.W; p.W = 0; return kCapped; }
     ++p.steps;
@@ -343,16 +349,21 @@ __device__ __forceinline__ int step(const DevCloud &C, Pkg &p, Rng &r, float kab
         p.W -= dep;
         p.pend += dep;
     }
-    if (p.W < (uint64_t)p.wmin) { p.pend += p.W; p.W = 0; return kAbsorbed; }
+    if (p.W < (uint64_t)(p.wf & kFloorMask)) { p.pend += p.W; p.W = 0; return kAbsorbed; }
     if (scatter) {
         p.x = clamp01(__fadd_rn(p.x, __fmul_rn(p.dx, sp)));
         p.y = clamp01(__fadd_rn(p.y, __fmul_rn(p.dy, sp)));
         p.z = clamp01(__fadd_rn(p.z, __fmul_rn(p.dz, sp)));
-        p.scat = true;            // the new direction is drawn in the warp's scattering phase
+        p.wf |= kScatBit;         // the new direction is drawn in the warp's scattering phase
         return kContinue;
     }
     p.tauf = __fsub_rn(p.tauf, dtau);
-    if (p.pend) { atomicAdd(tally + p.cell, (unsigned long long)p.pend); p.pend = 0; }
+    if (p.pend) {
+        atomicAdd(tally + p.cell, (unsigned long long)p.pend);
+        if (p.wf & kHomeBit) atomicAdd(self + p.cell, (unsigned long long)p.pend);
+        p.pend = 0;
+    }
+    p.wf &= ~kHomeBit;            // it leaves the cell it was emitted in
     // move to the exit face: the exit coordinate exactly on the face, the
     // others advanced (selects, so lanes leaving through different faces
     // stay converged)
@@ -395,7 +406,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
 
     Pkg p;
     Rng r;
-    p.steps = 0; p.W = 0; p.pend = 0; p.scat = false;
+    p.steps = 0; p.W = 0; p.pend = 0; p.wf = 0;
     bool active = false;
     int item = -1;
     const DevCloud *C = nullptr;
@@ -445,9 +456,10 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
                 const uint32_t pid = IT.pid_offset + (uint32_t)(gidx - P.prefix[item]);
                 r.init(P.seed, (uint32_t)IT.iteration, (uint32_t)IT.freq, pid, (uint32_t)IT.cloud,
                        (uint32_t)IT.source);
-                p.steps = 0; p.pend = 0; p.scat = false;
+                p.steps = 0; p.pend = 0;
                 if (emit(*C, IT, pid, r, p)) {
-                    p.wmin = (p.W >> 20) ? (uint32_t)(p.W >> 20) : 1u;
+                    p.wf = ((p.W >> 20) ? (uint32_t)(p.W >> 20) : 1u) |
+                           ((IT.source == SOC_SRC_DUST && P.self) ? kHomeBit : 0u);
                     set_inverse(p);
                     p.tauf = -log_pos(r.u());
                     if (acc_item != item) {
@@ -481,18 +493,22 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
         // does); a package's draws and operations keep their order
         {
             const unsigned act = __ballot_sync(kFull, active);
-            const unsigned sc = __ballot_sync(kFull, active && p.scat);
-            if (sc && (__popc(sc) >= P.scatter_min || sc == act) && active && p.scat) {
+            const unsigned sc = __ballot_sync(kFull, active && (p.wf & kScatBit));
+            if (sc && (__popc(sc) >= P.scatter_min || sc == act) && active && (p.wf & kScatBit)) {
                 hg_scatter(r, g, p);
                 set_inverse(p);
                 p.tauf = -log_pos(r.u());
-                p.scat = false;
+                p.wf &= ~kScatBit;
             }
         }
-        if (active && !p.scat) {
-            const int res = step(*C, p, r, kabs, ksca, g, tally, P.max_steps);
+        if (active && !(p.wf & kScatBit)) {
+            unsigned long long *self = P.self ? P.self + (tally - P.tally) : nullptr;
+            const int res = step(*C, p, r, kabs, ksca, g, tally, self, P.max_steps);
             if (res != kContinue) {
-                if (p.pend) atomicAdd(tally + p.cell, (unsigned long long)p.pend);
+                if (p.pend) {
+                    atomicAdd(tally + p.cell, (unsigned long long)p.pend);
+                    if (p.wf & kHomeBit) atomicAdd(self + p.cell, (unsigned long long)p.pend);
+                }
                 p.pend = 0;
                 if (res == kEscaped) acc[0] += p.W;
                 if (res == kCapped) acc_cap += 1;

@@ -21,7 +21,7 @@ SRC_BACKGROUND, SRC_POINT, SRC_DUST = 0, 1, 2
 W_UNIT = 1 << 32
 
 EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "soc_grid_validate", "soc_grid_free",
-           "soc_dust_upload",
+           "soc_dust_upload", "soc_simulate_frequency_batch_ex", "soc_update_temperature_ali",
            "soc_sources_upload", "soc_simulate_frequency_batch", "soc_package_energy",
            "soc_dust_emission", "soc_absorbed_power", "soc_update_temperature", "soc_iterate",
            "soc_set_launch", "soc_set_refill", "soc_set_scatter_batch", "soc_set_max_steps",
@@ -48,7 +48,7 @@ class BatchItem(C.Structure):
 class IterateParams(C.Structure):
     _fields_ = [("n_background", C.c_uint64), ("n_point", C.c_uint64), ("n_per_cell", C.c_uint32),
                 ("max_iter", C.c_int32), ("dT_tol", C.c_double), ("reuse_constant", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("ali", C.c_int32)]
 
 
 class IterateResult(C.Structure):
@@ -77,6 +77,8 @@ def _load():
         "soc_dust_upload": ([P, I, P, P, P, P], I),
         "soc_sources_upload": ([P, I, P, I, P, P], I),
         "soc_simulate_frequency_batch": ([P, P, I, P, P, P, P], I),
+        "soc_simulate_frequency_batch_ex": ([P, P, I, P, P, P, P, P], I),
+        "soc_update_temperature_ali": ([P, I, P, P, P, P, P], I),
         "soc_package_energy": ([P, I, I, U64, P], I),
         "soc_dust_emission": ([P, I, P, I, I, C.c_uint32, P, P, P], I),
         "soc_absorbed_power": ([P, I, P, C.c_int64, P, P, P, P], I),
@@ -256,8 +258,12 @@ class Context:
             it.n_per_cell = s.get("n_per_cell", 1)
         return arr
 
-    def simulate(self, items, tally, stats, pkg_steps=None, stream=None):
-        """soc_simulate_frequency_batch; items from Context.items()."""
+    def simulate(self, items, tally, stats, pkg_steps=None, stream=None, self_tally=None):
+        """soc_simulate_frequency_batch(_ex); items from Context.items()."""
+        if self_tally is not None:
+            return self._check(lib.soc_simulate_frequency_batch_ex(
+                self.h, C.cast(items, C.c_void_p), len(items), _t_ptr(tally), _t_ptr(self_tally), _t_ptr(stats),
+                _t_ptr(pkg_steps), _stream(stream)))
         return self._check(lib.soc_simulate_frequency_batch(
             self.h, C.cast(items, C.c_void_p), len(items), _t_ptr(tally), _t_ptr(stats),
             _t_ptr(pkg_steps), _stream(stream)))
@@ -310,13 +316,17 @@ class Context:
         self._check(lib.soc_absorbed_power(self.h, cloud_id, _t_ptr(tally), stride, _t_ptr(e_unit),
                                            _t_ptr(A_in), _t_ptr(A_out), _stream(stream)))
 
+    def update_temperature_ali(self, cloud_id, A, A_self, T, max_dT=None, stream=None):
+        self._check(lib.soc_update_temperature_ali(self.h, cloud_id, _t_ptr(A), _t_ptr(A_self), _t_ptr(T),
+                                                   _t_ptr(max_dT), _stream(stream)))
+
     def update_temperature(self, cloud_id, A, T, max_dT=None, stream=None):
         self._check(lib.soc_update_temperature(self.h, cloud_id, _t_ptr(A), _t_ptr(T), _t_ptr(max_dT),
                                                _stream(stream)))
 
     def iterate(self, cloud_id, T_out, *, n_background=0, n_point=0, n_per_cell=1, max_iter=0,
-                dT_tol=0.1, T_seed=None, reuse_constant=False, stream=None):
-        p = IterateParams(n_background, n_point, n_per_cell, max_iter, dT_tol, int(reuse_constant), 0)
+                dT_tol=0.1, T_seed=None, reuse_constant=False, ali=False, stream=None):
+        p = IterateParams(n_background, n_point, n_per_cell, max_iter, dT_tol, int(reuse_constant), int(ali))
         r = IterateResult()
         hist = np.zeros(max(max_iter, 1), np.float64)
         self._check(lib.soc_iterate(self.h, cloud_id, C.byref(p), _t_ptr(T_seed), _t_ptr(T_out), C.byref(r),

@@ -491,3 +491,43 @@ def test_faint_dust_package_is_not_dumped_into_its_own_cell():
     small = oracle.trace(G, dust_w=np.full(leaf.size, 2 ** 11, np.uint64), **kw)[0].astype(np.float64)
     assert small.sum() > 0
     np.testing.assert_allclose(small / small.sum(), big / big.sum(), atol=2e-3)
+
+
+def test_self_absorption_counter():
+    """Deposits a dust package makes before it first leaves its emission cell:
+    never more than the cell's total, equal to it in a one-cell grid, and the
+    local absorption of an optically thick cell is most of its emission."""
+    cl = I.regular(np.ones((6, 6, 6), np.float32))
+    leaf = cl.leaves()
+    kw = dict(source=oracle.SRC_DUST, ksca=0.3, g=0.2, seed=8, leaf=leaf, n_per_cell=2, n_packages=2 * leaf.size,
+              dust_w=np.full(leaf.size, 2 ** 32, np.uint64))
+    self_t = np.zeros(cl.n_cells, np.int64)
+    tally, st, _ = oracle.trace(_grid(cl), kabs=0.2, self_tally=self_t, **kw)
+    assert np.all(self_t <= tally) and self_t.sum() > 0
+    one = I.regular(np.ones((1, 1, 1), np.float32))
+    s1 = np.zeros(1, np.int64)
+    t1, _, _ = oracle.trace(_grid(one), kabs=0.7, self_tally=s1, leaf=one.leaves(), dust_w=np.full(1, 2 ** 32, np.uint64),
+                            source=oracle.SRC_DUST, ksca=0.4, g=0.0, seed=3, n_per_cell=500, n_packages=500)
+    assert s1[0] == t1[0] > 0
+    s2 = np.zeros(cl.n_cells, np.int64)
+    t2, st2, _ = oracle.trace(_grid(cl), kabs=20.0, self_tally=s2, **kw)
+    assert s2.sum() > 0.85 * st2["emitted"]
+
+
+def test_ali_update_reaches_the_same_fixed_point():
+    """The diagonal-operator update has the plain update's fixed point: with
+    A = A_ext + A_self and A_self = beta E(T) at T = T*, both return T*."""
+    nu = I.frequency_grid(16)
+    kabs = (nu / 1e14) ** 2
+    Tstar = 85.0
+    E = P.emission_integral(Tstar, nu, kabs)
+    for beta in (0.0, 0.3, 0.9):
+        A = E
+        A_self = beta * E
+        assert abs(P.temperature_ali(A, A_self, Tstar, nu, kabs) / Tstar - 1) < 1e-9
+    # away from the fixed point ALI moves further toward it than the plain update
+    T_old, beta, A_ext = 40.0, 0.8, 0.2 * E
+    A_self = beta * P.emission_integral(T_old, nu, kabs)
+    plain = P.temperature(A_ext + A_self, nu, kabs)
+    ali = P.temperature_ali(A_ext + A_self, A_self, T_old, nu, kabs)
+    assert plain < ali <= Tstar * 1.0001
