@@ -406,14 +406,23 @@ def run_extra(args):
            "input_generation_s": t_gen}
     if args.workload == "c3":
         cl = w.clouds[0]
-        T = torch.empty(cl.n_cells, dtype=torch.float32, device="cuda")
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r = ctx.iterate(ids[0], T, n_background=w.n_bg[0], n_point=w.n_ps[0], n_per_cell=1, max_iter=40, dT_tol=0.1)
-        torch.cuda.synchronize()
-        out["convergence"] = {"wall_s": time.perf_counter() - t0, "dust_iterations": r["iterations"],
-                              "converged": r["converged"], "max_dT_history_K": [round(x, 4) for x in r["history"]],
-                              "photon_cell_steps": r["steps"], "T_max_K": float(T.max().item())}
+        out["convergence"] = {}
+        Ts = {}
+        for mode in ("plain", "ali"):
+            T = torch.empty(cl.n_cells, dtype=torch.float32, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = ctx.iterate(ids[0], T, n_background=w.n_bg[0], n_point=w.n_ps[0], n_per_cell=1, max_iter=40,
+                            dT_tol=0.1, ali=(mode == "ali"))
+            torch.cuda.synchronize()
+            Ts[mode] = T
+            out["convergence"][mode] = {"wall_s": time.perf_counter() - t0, "dust_iterations": r["iterations"],
+                                        "converged": r["converged"],
+                                        "max_dT_history_K": [round(x, 4) for x in r["history"]],
+                                        "photon_cell_steps": r["steps"], "T_max_K": float(T.max().item())}
+        leaf = torch.from_numpy(cl.leaves().astype(np.int64)).cuda()
+        out["convergence"]["max_abs_T_difference_K"] = float(
+            (Ts["plain"].index_select(0, leaf) - Ts["ali"].index_select(0, leaf)).abs().max().item())
     ctx.graph_destroy(g)
     ctx.batch_destroy(batch)
     ctx.close()
