@@ -36,7 +36,11 @@ WORKLOAD = "lognormal 128^3, 64 nu (3e11-3e15 Hz), 1e6 background packages/nu, H
 # DRAM bytes (read + write) per photon-cell step of trace_kernel from one ncu
 # capture (small case of the same workload, scaled by steps), valid only for
 # the kernel source it was taken on.
-TRACE_DRAM = {"source_sha1": None, "bytes_per_step": None, "profile": None}
+TRACE_DRAM = {"source_sha1": "3888c8006fdfb31f66c0e21032771cf8476207d8", "bytes_per_step": 1.9153,
+              "warp_instructions_per_step": 11.378,
+              "profile": "profiles/trace_kernel_lognormal128_8nu_1e6pkg_full.md"}
+# issue-rate peak: 4 warp-instructions per cycle per SM (4 schedulers)
+ISSUE_PER_SM_CYCLE = 4
 
 
 def _trace_source_sha1():
@@ -52,6 +56,18 @@ def _traffic_per_launch(steps):
     if TRACE_DRAM["source_sha1"] and TRACE_DRAM["source_sha1"] == _trace_source_sha1():
         return TRACE_DRAM["bytes_per_step"] * steps
     return None
+
+
+def _issue_roofline(steps, ms, sms, clock_mhz):
+    """Instruction-issue roofline of the tracer: warp instructions per step
+    (ncu, same kernel source) x steps / time, against 4 per cycle per SM."""
+    if not (TRACE_DRAM["source_sha1"] == _trace_source_sha1() and clock_mhz):
+        return None
+    achieved = TRACE_DRAM["warp_instructions_per_step"] * steps / (ms / 1e3)
+    peak = ISSUE_PER_SM_CYCLE * sms * clock_mhz * 1e6
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "warp-instructions/s",
+            "frac": achieved / peak, "instructions_per_unit": TRACE_DRAM["warp_instructions_per_step"],
+            "peak_source": f"4 issue slots/cycle/SM x {sms} SMs x {clock_mhz:.0f} MHz (median SM clock in the run)"}
 
 
 def _peaks():
@@ -262,7 +278,8 @@ def run_gpu(args):
             with torch.cuda.stream(stream):
                 flush.fill_(float(k))                      # L2 flush between steps, outside the events
             step(evs[k])
-            step_steps.append(stats[:, 2].sum())
+            with torch.cuda.stream(stream):              # ordered after this pass's tracer
+                step_steps.append(stats[:, 2].sum())
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -335,6 +352,9 @@ def run_gpu(args):
     }
     if rank == 0:
         out["clocks"] = clk.summary()
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = (out["clocks"] or {}).get("sm_mhz")
+        out["roofline_alu"] = _issue_roofline(steps_per_step, ms_trace, sms, mhz)
         print(json.dumps(out), flush=True)
     ctx.graph_destroy(g_trace)
     ctx.graph_destroy(g_temp)
