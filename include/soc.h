@@ -306,6 +306,24 @@ soc_status soc_update_temperature_ali(soc_ctx *ctx, int cloud_id, const double *
                                       float *d_T, double *d_max_dT, void *stream);
 
 /* ------------------------------------------------------------------------
+ * soc_map -- surface-brightness map (paper Sect. 2.1.1: after the
+ * temperatures are solved, a mapping kernel makes maps for chosen
+ * frequencies and directions).  Rays travel along `dir` (the observer looks
+ * back along it); the map plane has axes e1 = up x dir and e2 = dir x e1
+ * (normalised); pixel (px, py) is centred at
+ *   center + ((px + 0.5) - npx/2) pix_size e1 + ((py + 0.5) - npy/2) pix_size e2
+ * (root-cell units).  Along each leaf segment of extinction optical depth
+ * dtau (kext = kabs + ksca of frequency `freq`) the intensity gains
+ * (kabs/kext) B_nu(T) (1 - e^-dtau) e^-tau_front; I_bg (erg/s/cm^2/Hz/sr)
+ * enters from behind attenuated by the total optical depth.
+ *   d_T     device float [n_cells];  d_map  device float [npy][npx].
+ * FP32 cell-local traversal as the tracer, FP64 accumulation.  Asynchronous.
+ * ------------------------------------------------------------------------ */
+soc_status soc_map(soc_ctx *ctx, int cloud_id, const float *d_T, int freq, const double *dir, const double *up,
+                   int npx, int npy, double pix_size, const double *center, double I_bg, float *d_map,
+                   void *stream);
+
+/* ------------------------------------------------------------------------
  * soc_iterate -- the iteration of paper Sect. 2.1.2 / 3.3: iteration 0
  * simulates the constant sources (background, point sources) once and keeps
  * their absorbed power; iterations k >= 1 re-simulate only dust re-emission

@@ -848,6 +848,47 @@ soc_status soc_update_temperature_ali(soc_ctx *ctx, int cloud_id, const double *
     return SOC_OK;
 }
 
+soc_status soc_map(soc_ctx *ctx, int cloud_id, const float *d_T, int freq, const double *dir, const double *up, int npx,
+                   int npy, double pix_size, const double *center, double I_bg, float *d_map, void *stream)
+{
+    soc_status st = check_cloud(ctx, cloud_id);
+    if (st) return st;
+    if (!d_T || !dir || !up || !center || !d_map || npx < 1 || npy < 1 || !(pix_size > 0.0))
+        return fail(ctx, SOC_ERR_ARG, "bad map arguments");
+    if (freq < 0 || freq >= ctx->n_freq) return fail(ctx, SOC_ERR_ARG, "bad frequency index");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if ((st = sync_clouds(ctx))) return st;
+    const CloudHost &cl = *ctx->clouds[cloud_id];
+    MapParams M;
+    memset(&M, 0, sizeof M);
+    const double dn = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+    if (!(dn > 0.0)) return fail(ctx, SOC_ERR_ARG, "zero view direction");
+    for (int a = 0; a < 3; ++a) M.d[a] = dir[a] / dn;
+    // e1 = up x d (normalised), e2 = d x e1
+    double e1[3] = {up[1] * M.d[2] - up[2] * M.d[1], up[2] * M.d[0] - up[0] * M.d[2], up[0] * M.d[1] - up[1] * M.d[0]};
+    const double n1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    if (!(n1 > 1e-12)) return fail(ctx, SOC_ERR_ARG, "up vector parallel to the view direction");
+    for (int a = 0; a < 3; ++a) M.e1[a] = e1[a] / n1;
+    M.e2[0] = M.d[1] * M.e1[2] - M.d[2] * M.e1[1];
+    M.e2[1] = M.d[2] * M.e1[0] - M.d[0] * M.e1[2];
+    M.e2[2] = M.d[0] * M.e1[1] - M.d[1] * M.e1[0];
+    for (int a = 0; a < 3; ++a) M.c[a] = center[a];
+    M.cloud = ctx->d_clouds.p + cloud_id;
+    M.T = d_T;
+    M.map = d_map;
+    M.pix = pix_size;
+    M.nu = ctx->nu[freq];
+    const double kext = ctx->kabs[freq] + ctx->ksca[freq];
+    M.kext_root = kext * cl.ell;
+    M.kabs_over_kext = kext > 0.0 ? ctx->kabs[freq] / kext : 0.0;
+    M.I_bg = I_bg;
+    M.npx = npx;
+    M.npy = npy;
+    M.max_cells = 100000000u;
+    CK(launch_map(M, (cudaStream_t)stream), "map");
+    return SOC_OK;
+}
+
 soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm, const float *d_T_seed,
                        float *d_T_out, soc_iterate_result *res, double *dT_history, void *stream)
 {

@@ -63,6 +63,21 @@ struct TraceParams {
 cudaError_t launch_trace(const TraceParams &p, int grid, int block, int variant, cudaStream_t s);
 int trace_block_limit(int block, int variant);   // max resident blocks/SM
 
+// Surface-brightness map of one frequency seen along direction d (rays
+// travel along d); pixel (px, py) centre = c + ((px+0.5) - npx/2) pix e1 +
+// ((py+0.5) - npy/2) pix e2, all in root-cell units.
+struct MapParams {
+    const DevCloud *cloud;
+    const float *T;               // [n_cells]
+    float *map;                   // [npy][npx]
+    double d[3], e1[3], e2[3], c[3];
+    double pix, nu, kext_root, kabs_over_kext, I_bg;
+    int32_t npx, npy;
+    uint32_t max_cells;
+};
+
+cudaError_t launch_map(const MapParams &m, cudaStream_t s);
+
 struct TempTables {
     int n_freq;
     const double *w_kabs;        // [n_freq] 4 pi w_nu kabs(nu)

@@ -527,7 +527,101 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
     }
 }
 
+// ---------------------------------------------------------------------------
+// Surface-brightness maps (paper Sect. 2.1.1: a separate kernel makes maps at
+// chosen frequencies and directions from the solved temperatures).  One
+// thread per pixel: the ray enters the root box (FP64 slab test), then walks
+// the leaves with the tracer's FP32 cell-local traversal; along each segment
+// of optical depth dtau = rho kext_root h s the intensity gains
+// S (1 - e^-dtau) e^-tau_front with S = (kabs / kext) B_nu(T_cell), in FP64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double planck_d(double nu, double T)
+{
+    const double h = 6.62607015e-27, k = 1.380649e-16, c = 2.99792458e10;
+    return (2.0 * h * nu * nu * nu / (c * c)) / expm1(h * nu / (k * T));
+}
+
+__global__ void map_kernel(const MapParams M)
+{
+    const int px = blockIdx.x * blockDim.x + threadIdx.x;
+    const int py = blockIdx.y * blockDim.y + threadIdx.y;
+    if (px >= M.npx || py >= M.npy) return;
+    const DevCloud &C = *M.cloud;
+    const double ox = M.c[0] + ((px + 0.5) - 0.5 * M.npx) * M.pix * M.e1[0] + ((py + 0.5) - 0.5 * M.npy) * M.pix * M.e2[0];
+    const double oy = M.c[1] + ((px + 0.5) - 0.5 * M.npx) * M.pix * M.e1[1] + ((py + 0.5) - 0.5 * M.npy) * M.pix * M.e2[1];
+    const double oz = M.c[2] + ((px + 0.5) - 0.5 * M.npx) * M.pix * M.e1[2] + ((py + 0.5) - 0.5 * M.npy) * M.pix * M.e2[2];
+    const double o[3] = {ox, oy, oz};
+    const double n[3] = {(double)C.nx, (double)C.ny, (double)C.nz};
+    double t0 = -1e300, t1 = 1e300;
+    int ea = -1;
+    for (int a = 0; a < 3; ++a) {
+        const double da = M.d[a];
+        if (da == 0.0) {
+            if (o[a] < 0.0 || o[a] > n[a]) { t0 = 1.0; t1 = 0.0; }
+            continue;
+        }
+        double ta = (0.0 - o[a]) / da, tb = (n[a] - o[a]) / da;
+        if (ta > tb) { const double tt = ta; ta = tb; tb = tt; }
+        if (ta > t0) { t0 = ta; ea = a; }
+        if (tb < t1) t1 = tb;
+    }
+    double I = 0.0, tau = 0.0;
+    if (ea >= 0 && t0 < t1) {
+        Pkg p;
+        p.h = 1.0f;
+        p.dx = (float)M.d[0]; p.dy = (float)M.d[1]; p.dz = (float)M.d[2];
+        set_inverse(p);
+        const double q[3] = {o[0] + t0 * M.d[0], o[1] + t0 * M.d[1], o[2] + t0 * M.d[2]};
+        float lx, ly, lz;
+        p.ri = root_axis((float)q[0], C.nx, lx);
+        p.rj = root_axis((float)q[1], C.ny, ly);
+        p.rk = root_axis((float)q[2], C.nz, lz);
+        // the entry coordinate exactly on the face the ray enters through
+        const bool up = M.d[ea] > 0.0;
+        if (ea == 0) { p.ri = up ? 0 : C.nx - 1; lx = up ? 0.f : 1.f; }
+        if (ea == 1) { p.rj = up ? 0 : C.ny - 1; ly = up ? 0.f : 1.f; }
+        if (ea == 2) { p.rk = up ? 0 : C.nz - 1; lz = up ? 0.f : 1.f; }
+        p.x = lx; p.y = ly; p.z = lz;
+        p.cell = root_cell(C, p.ri, p.rj, p.rk);
+        descend(C.cell, p);
+        const double kext = M.kext_root, ratio = M.kabs_over_kext;
+        for (uint32_t it = 0; it < M.max_cells; ++it) {
+            float s = __int_as_float(0x7f800000);
+            int ax = -1;
+            if (p.dx != 0.0f) { const float si = __fmul_rn(__fsub_rn(p.dx > 0.0f ? 1.0f : 0.0f, p.x), p.ix); if (si < s) { s = si; ax = 0; } }
+            if (p.dy != 0.0f) { const float si = __fmul_rn(__fsub_rn(p.dy > 0.0f ? 1.0f : 0.0f, p.y), p.iy); if (si < s) { s = si; ax = 1; } }
+            if (p.dz != 0.0f) { const float si = __fmul_rn(__fsub_rn(p.dz > 0.0f ? 1.0f : 0.0f, p.z), p.iz); if (si < s) { s = si; ax = 2; } }
+            if (ax < 0) break;
+            const double dtau = (double)p.rho * kext * (double)p.h * (double)s;
+            if (dtau > 0.0) {
+                const double Tc = (double)__ldg(M.T + p.cell);
+                I += ratio * planck_d(M.nu, Tc) * (-expm1(-dtau)) * exp(-tau);
+                tau += dtau;
+            }
+            const float da = (ax == 0) ? p.dx : (ax == 1) ? p.dy : p.dz;
+            const bool upx = da > 0.0f;
+            const float face = upx ? 1.0f : 0.0f;
+            const float mx = clamp01(__fadd_rn(p.x, __fmul_rn(p.dx, s)));
+            const float my = clamp01(__fadd_rn(p.y, __fmul_rn(p.dy, s)));
+            const float mz = clamp01(__fadd_rn(p.z, __fmul_rn(p.dz, s)));
+            p.x = (ax == 0) ? face : mx;
+            p.y = (ax == 1) ? face : my;
+            p.z = (ax == 2) ? face : mz;
+            if (!cross_face(C, p, ax, upx)) break;
+        }
+    }
+    M.map[(int64_t)py * M.npx + px] = (float)(I + M.I_bg * exp(-tau));
+}
+
 }  // namespace
+
+cudaError_t launch_map(const MapParams &m, cudaStream_t s)
+{
+    dim3 block(16, 16);
+    dim3 grid((m.npx + 15) / 16, (m.npy + 15) / 16);
+    map_kernel<<<grid, block, 0, s>>>(m);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_trace(const TraceParams &p, int grid, int block, int variant, cudaStream_t s)
 {

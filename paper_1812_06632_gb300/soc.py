@@ -21,7 +21,7 @@ SRC_BACKGROUND, SRC_POINT, SRC_DUST = 0, 1, 2
 W_UNIT = 1 << 32
 
 EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "soc_grid_validate", "soc_grid_free",
-           "soc_dust_upload", "soc_simulate_frequency_batch_ex", "soc_update_temperature_ali",
+           "soc_dust_upload", "soc_simulate_frequency_batch_ex", "soc_update_temperature_ali", "soc_map",
            "soc_sources_upload", "soc_simulate_frequency_batch", "soc_package_energy",
            "soc_dust_emission", "soc_absorbed_power", "soc_update_temperature", "soc_iterate",
            "soc_set_launch", "soc_set_refill", "soc_set_scatter_batch", "soc_set_max_steps",
@@ -79,6 +79,7 @@ def _load():
         "soc_simulate_frequency_batch": ([P, P, I, P, P, P, P], I),
         "soc_simulate_frequency_batch_ex": ([P, P, I, P, P, P, P, P], I),
         "soc_update_temperature_ali": ([P, I, P, P, P, P, P], I),
+        "soc_map": ([P, I, P, I, P, P, I, I, C.c_double, P, C.c_double, P, P], I),
         "soc_package_energy": ([P, I, I, U64, P], I),
         "soc_dust_emission": ([P, I, P, I, I, C.c_uint32, P, P, P], I),
         "soc_absorbed_power": ([P, I, P, C.c_int64, P, P, P, P], I),
@@ -315,6 +316,14 @@ class Context:
     def absorbed_power(self, cloud_id, tally, stride, e_unit, A_out, A_in=None, stream=None):
         self._check(lib.soc_absorbed_power(self.h, cloud_id, _t_ptr(tally), stride, _t_ptr(e_unit),
                                            _t_ptr(A_in), _t_ptr(A_out), _stream(stream)))
+
+    def map(self, cloud_id, T, freq, direction, up, npx, npy, pix_size, center, out, I_bg=0.0, stream=None):
+        """soc_map: surface-brightness map into out (torch float32 [npy, npx])."""
+        d = np.ascontiguousarray(direction, np.float64)
+        u = np.ascontiguousarray(up, np.float64)
+        c = np.ascontiguousarray(center, np.float64)
+        self._check(lib.soc_map(self.h, cloud_id, _t_ptr(T), freq, _np_ptr(d), _np_ptr(u), npx, npy,
+                                float(pix_size), _np_ptr(c), float(I_bg), _t_ptr(out), _stream(stream)))
 
     def update_temperature_ali(self, cloud_id, A, A_self, T, max_dT=None, stream=None):
         self._check(lib.soc_update_temperature_ali(self.h, cloud_id, _t_ptr(A), _t_ptr(A_self), _t_ptr(T),
