@@ -147,6 +147,12 @@ soc_status soc_sources_upload(soc_ctx *ctx, int cloud_id, const double *bg_I_nu,
  *     d_dust_w        device [n_leaf] uint64: initial weight of the packages
  *                     of each leaf (leaves in cell order), SOC_SRC_DUST only;
  *     n_per_cell      dust packages per leaf (n_packages = n_leaf*n_per_cell).
+ *     reserved        flags: SOC_ITEM_WEIGHTED (dust) = emission-weighted
+ *                     sampling: d_dust_w holds [n_leaf] weights followed by
+ *                     the [n_leaf + 1] uint64 prefix of packages per leaf
+ *                     (as written by soc_dust_weighted); package pid comes
+ *                     from the leaf li with prefix[li] <= pid < prefix[li+1];
+ *                     n_packages = prefix[n_leaf].
  *   d_tally           device int64, accumulated into (caller zeroes it).
  *   d_stats           device int64 [n_items][4], accumulated into:
  *                     {escaped weight, capped packages, photon-cell steps,
@@ -157,6 +163,8 @@ soc_status soc_sources_upload(soc_ctx *ctx, int cloud_id, const double *bg_I_nu,
  * Deterministic: results depend only on inputs and the seed, not on launch
  * shape.  Asynchronous on `stream`.
  * ------------------------------------------------------------------------ */
+#define SOC_ITEM_WEIGHTED 1u   /* soc_batch_item.reserved flag: weighted dust sampling */
+
 typedef struct soc_batch_item {
     int32_t cloud;
     int32_t freq;
@@ -260,6 +268,24 @@ soc_status soc_package_energy(soc_ctx *ctx, int cloud_id, int source, uint64_t n
  * ------------------------------------------------------------------------ */
 soc_status soc_dust_emission(soc_ctx *ctx, int cloud_id, const float *d_T, int freq_lo, int n_freq,
                              uint32_t n_per_cell, uint64_t *d_w, double *d_e_unit, void *stream);
+
+/* ------------------------------------------------------------------------
+ * soc_dust_weighted -- emission-weighted dust sampling (paper Sect. 3.2:
+ * packages per cell in proportion to the cell's luminosity, with a cap on
+ * any single cell).  From the uniform weights u = rint(2^32 L / max L) of
+ * soc_dust_emission (n_per_cell = 1) and its d_e_unit, per frequency:
+ *   S = sum u;  n_c = u_c ? min(cap, ceil(N u_c / S)) : 0;
+ *   E_ref = max(S / N, 2^32 / cap);  W_c = rint((u_c / n_c) / E_ref 2^32);
+ *   e_unit = e_unit_uniform E_ref / 2^32  (energy of one weight unit).
+ *   d_u               device uint64 [n_freq][n_leaf].
+ *   d_out             device uint64 [n_freq][2 n_leaf + 1]: W then the
+ *                     exclusive prefix of n (last entry = packages to trace).
+ *   d_e_unit          device double [n_freq].
+ * Integer sums and a fixed operation order: deterministic.  Asynchronous.
+ * ------------------------------------------------------------------------ */
+soc_status soc_dust_weighted(soc_ctx *ctx, int cloud_id, const uint64_t *d_u, const double *d_e_unit_uniform,
+                             int n_freq, uint64_t n_total, uint32_t cap, uint64_t *d_out, double *d_e_unit,
+                             void *stream);
 
 /* ------------------------------------------------------------------------
  * soc_absorbed_power -- frequency integral of the absorption counters (paper

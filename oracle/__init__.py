@@ -62,7 +62,7 @@ class _Item(C.Structure):
                 ("w0", C.c_uint64), ("max_steps", C.c_uint32),
                 ("n_ps", C.c_int32), ("ps_pos", C.c_void_p), ("ps_cdf", C.c_void_p),
                 ("n_per_cell", C.c_uint32), ("n_leaf", C.c_int64),
-                ("leaf", C.c_void_p), ("dust_w", C.c_void_p)]
+                ("leaf", C.c_void_p), ("dust_w", C.c_void_p), ("dust_prefix", C.c_void_p)]
 
 
 class _Stats(C.Structure):
@@ -182,7 +182,7 @@ def trace(grid: Grid, *, source: int, kabs: float, ksca: float, g: float = 0.0,
           seed: int = 1, freq: int = 0, iteration: int = 0, cloud: int = 0,
           pid_lo: int = 0, n_packages: int, w0: int = W_UNIT, max_steps: int = 10_000_000,
           ps_pos=None, ps_cdf=None, n_per_cell: int = 1, leaf=None, dust_w=None,
-          tally=None, want_steps: bool = False, self_tally=None):
+          tally=None, want_steps: bool = False, self_tally=None, dust_prefix=None):
     """Trace packages pid_lo .. pid_lo + n_packages - 1 of one (source, freq)
     item.  ``kabs``/``ksca`` are per unit density and per root-cell length.
     ``self_tally`` (int64[n_cells], accumulated) receives the deposits dust
@@ -194,10 +194,11 @@ def trace(grid: Grid, *, source: int, kabs: float, ksca: float, g: float = 0.0,
     ps_cdf_a = None if ps_cdf is None else np.ascontiguousarray(ps_cdf, np.float32)
     leaf_a = None if leaf is None else np.ascontiguousarray(leaf, np.int32)
     dust_a = None if dust_w is None else np.ascontiguousarray(dust_w, np.uint64)
+    pref_a = None if dust_prefix is None else np.ascontiguousarray(dust_prefix, np.uint64)
     it = _Item(source, freq, iteration, cloud, seed & (2**64 - 1),
                np.float32(kabs), np.float32(ksca), np.float32(g), w0, max_steps,
                0 if ps_cdf_a is None else ps_cdf_a.size, _ptr(ps_pos_a), _ptr(ps_cdf_a),
-               n_per_cell, 0 if leaf_a is None else leaf_a.size, _ptr(leaf_a), _ptr(dust_a))
+               n_per_cell, 0 if leaf_a is None else leaf_a.size, _ptr(leaf_a), _ptr(dust_a), _ptr(pref_a))
     st = _Stats()
     steps = np.zeros(n_packages, np.uint32) if want_steps else None
     gc = grid._c()
@@ -213,7 +214,7 @@ def trace_pencil(grid: Grid, pos, direction, *, kabs: float, ksca: float = 0.0, 
     beam).  Returns (tally, stats, steps)."""
     tally = np.zeros(grid.n_cells, np.int64)
     it = _Item(SRC_POINT, 0, 0, 0, seed, np.float32(kabs), np.float32(ksca), np.float32(g),
-               w0, max_steps, 0, None, None, 1, 0, None, None)
+               w0, max_steps, 0, None, None, 1, 0, None, None, None)
     st = _Stats()
     pos_a = np.ascontiguousarray(pos, np.float32)
     dir_a = np.ascontiguousarray(direction, np.float32)

@@ -159,3 +159,29 @@ def temperature_ali(A, A_self, T_old, nu, kabs, beta_max=0.99, **kw):
     beta = min(beta_max, A_self / E_old) if E_old > 0 else 0.0
     beta = max(beta, 0.0)
     return temperature((A - A_self) / (1.0 - beta), nu, kabs, **kw)
+
+
+def weighted_dust_sampling(u, e_unit_uniform, n_total, cap):
+    """Emission-weighted dust sampling (paper Sect. 3.2: packages per cell in
+    proportion to the cell's luminosity, at most `cap` from any cell), built
+    from the uniform weights u_c = rint(2^32 L_c / max L) of one frequency:
+      S = sum u_c (integer),
+      n_c = 0 if u_c = 0 else min(cap, ceil(N u_c / S)),
+      E_ref = max(S / N, 2^32 / cap)  (in units of max L / 2^32),
+      W_c = rint((u_c / n_c) / E_ref * 2^32)  (<= 2^32),
+      one fixed-point unit carries e_unit_uniform * E_ref / 2^32.
+    Returns (n uint64, exclusive prefix uint64 [n_leaf + 1], W uint64, e_unit)."""
+    u = np.asarray(u, np.uint64)
+    S = int(u.sum(dtype=np.uint64))
+    n = np.zeros(u.shape, np.uint64)
+    W = np.zeros(u.shape, np.uint64)
+    if S == 0:
+        return n, np.zeros(u.size + 1, np.uint64), W, 0.0
+    uf = u.astype(np.float64)
+    nz = u > 0
+    n[nz] = np.minimum(float(cap), np.ceil(float(n_total) * uf[nz] / float(S))).astype(np.uint64)
+    E_ref = max(float(S) / float(n_total), W_UNIT / float(cap))
+    W[nz] = np.rint((uf[nz] / n[nz].astype(np.float64)) / E_ref * W_UNIT).astype(np.uint64)
+    prefix = np.zeros(u.size + 1, np.uint64)
+    prefix[1:] = np.cumsum(n, dtype=np.uint64)
+    return n, prefix, W, float(e_unit_uniform) * E_ref / W_UNIT

@@ -197,6 +197,8 @@ typedef struct {
     int64_t n_leaf;
     const int32_t *leaf;         /* [n_leaf] leaf cell indices, increasing          */
     const uint64_t *dust_w;      /* [n_leaf] initial weight of each cell's packages */
+    const uint64_t *dust_prefix; /* [n_leaf+1] or NULL: package ids of leaf li are
+                                    prefix[li] .. prefix[li+1]-1 (weighted sampling) */
 } oracle_item;
 
 typedef struct {
@@ -370,8 +372,19 @@ static int emit(const oracle_grid *G, const oracle_item *it, rng_t *r, uint32_t 
         descend(G, p);
         return 1;
     }
-    /* Dust: n_per_cell packages from every leaf, uniform in the cell. */
-    int64_t li = (int64_t)(pid / it->n_per_cell);
+    /* Dust: n_per_cell packages from every leaf, or (weighted sampling) the
+     * leaf whose range of package ids holds pid; uniform in the cell. */
+    int64_t li;
+    if (it->dust_prefix) {
+        int64_t lo = 0, hi = it->n_leaf;          /* prefix[lo] <= pid < prefix[hi] */
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) / 2;
+            if (it->dust_prefix[mid] <= (uint64_t)pid) lo = mid; else hi = mid;
+        }
+        li = lo;
+    } else {
+        li = (int64_t)(pid / it->n_per_cell);
+    }
     p->cell = it->leaf[li];
     p->W = it->dust_w[li];
     if (p->W == 0) return 0;

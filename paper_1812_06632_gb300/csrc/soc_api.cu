@@ -85,6 +85,7 @@ struct soc_ctx {
     DevBuf<uint64_t> d_prefix;
     DevBuf<unsigned long long> d_counter;
     DevBuf<unsigned long long> d_lmax;
+    DevBuf<unsigned long long> d_wscratch;
     DevBuf<double> d_maxdT;
     // prepared batches and graphs
     std::vector<struct BatchHost *> batches;
@@ -242,6 +243,7 @@ void soc_destroy(soc_ctx *ctx)
     ctx->d_nu.release(); ctx->d_kabs.release(); ctx->d_lnE.release(); ctx->d_lnT.release();
     ctx->d_items.release(); ctx->d_prefix.release(); ctx->d_counter.release(); ctx->d_lmax.release();
     ctx->d_maxdT.release();
+    ctx->d_wscratch.release();
     for (BatchHost *b : ctx->batches)
         if (b) { b->items.release(); b->prefix.release(); b->counter.release(); delete b; }
     for (cudaGraphExec_t g : ctx->graphs)
@@ -585,7 +587,7 @@ static soc_status prepare_items(soc_ctx *ctx, const soc_batch_item *items, int n
                 return fail(ctx, SOC_ERR_STATE, "item %d: cloud has no point sources", i);
         } else if (it.source == SOC_SRC_DUST) {
             if (!it.d_dust_w || it.n_per_cell == 0) return fail(ctx, SOC_ERR_ARG, "item %d: dust weights missing", i);
-            if (it.pid_offset + it.n_packages > (uint64_t)cl.n_leaf * it.n_per_cell)
+            if (!(it.reserved & SOC_ITEM_WEIGHTED) && it.pid_offset + it.n_packages > (uint64_t)cl.n_leaf * it.n_per_cell)
                 return fail(ctx, SOC_ERR_ARG, "item %d: more dust packages than n_leaf*n_per_cell", i);
         } else {
             return fail(ctx, SOC_ERR_ARG, "item %d: unknown source %d", i, it.source);
@@ -593,6 +595,7 @@ static soc_status prepare_items(soc_ctx *ctx, const soc_batch_item *items, int n
         DevItem &d = dv[i];
         d.cloud = it.cloud; d.freq = it.freq; d.source = it.source; d.iteration = it.iteration;
         d.pid_offset = (uint32_t)it.pid_offset; d.n_per_cell = it.n_per_cell ? it.n_per_cell : 1;
+        d.flags = (it.source == SOC_SRC_DUST && (it.reserved & SOC_ITEM_WEIGHTED)) ? kItemWeighted : 0u;
         d.w0 = it.w0; d.tally_offset = it.tally_offset; d.dust_w = it.d_dust_w;
         prefix[i + 1] = prefix[i] + it.n_packages;
     }
@@ -795,6 +798,23 @@ soc_status soc_dust_emission(soc_ctx *ctx, int cloud_id, const float *d_T, int f
     CK(launch_dust_emission(ctx->d_clouds.p + cloud_id, cl.n_leaf, tt, d_T, freq_lo, n_freq, n_per_cell, d_w,
                             d_e_unit, ctx->d_lmax.p, (cudaStream_t)stream),
        "dust emission");
+    return SOC_OK;
+}
+
+soc_status soc_dust_weighted(soc_ctx *ctx, int cloud_id, const uint64_t *d_u, const double *d_e_unit_uniform,
+                             int n_freq, uint64_t n_total, uint32_t cap, uint64_t *d_out, double *d_e_unit, void *stream)
+{
+    soc_status st = check_cloud(ctx, cloud_id);
+    if (st) return st;
+    if (!d_u || !d_e_unit_uniform || !d_out || !d_e_unit || n_freq < 1 || n_total < 1 || cap < 1)
+        return fail(ctx, SOC_ERR_ARG, "bad weighted-sampling arguments");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const CloudHost &cl = *ctx->clouds[cloud_id];
+    const int64_t n_chunks = (cl.n_leaf + 1023) / 1024;
+    CK(ctx->d_wscratch.alloc((size_t)n_freq * (1 + n_chunks)), "alloc weighted-sampling scratch");
+    CK(launch_dust_weighted(cl.n_leaf, n_freq, d_u, d_e_unit_uniform, n_total, cap, d_out, d_e_unit,
+                            ctx->d_wscratch.p, (cudaStream_t)stream),
+       "weighted sampling");
     return SOC_OK;
 }
 
@@ -1082,6 +1102,7 @@ extern "C" soc_status soc_simulate_frequency_batch_noalloc(soc_ctx *ctx, const s
         DevItem &d = t_items[i];
         d.cloud = it.cloud; d.freq = it.freq; d.source = it.source; d.iteration = it.iteration;
         d.pid_offset = (uint32_t)it.pid_offset; d.n_per_cell = it.n_per_cell ? it.n_per_cell : 1;
+        d.flags = (it.source == SOC_SRC_DUST && (it.reserved & SOC_ITEM_WEIGHTED)) ? kItemWeighted : 0u;
         d.w0 = it.w0; d.tally_offset = it.tally_offset; d.dust_w = it.d_dust_w;
         t_prefix[i + 1] = t_prefix[i] + it.n_packages;
     }

@@ -30,9 +30,12 @@ struct DevCloud {
 };
 
 // Batch item after preparation on the host.
+constexpr uint32_t kItemWeighted = 1u;   // dust weights followed by the package prefix
+
 struct DevItem {
     int32_t cloud, freq, source, iteration;
     uint32_t pid_offset, n_per_cell;
+    uint32_t flags, pad_;
     uint64_t w0;
     int64_t tally_offset;
     const uint64_t *dust_w;
@@ -93,6 +96,9 @@ cudaError_t launch_absorbed_power(const DevCloud *dcl, int64_t n_cells, const in
                                   const double *A_in, double *A_out, cudaStream_t s);
 cudaError_t launch_update_temperature(const DevCloud *dcl, int64_t n_cells, const TempTables &tt,
                                       const double *A, float *T, double *max_dT, cudaStream_t s);
+cudaError_t launch_dust_weighted(int64_t n_leaf, int n_freq, const uint64_t *u, const double *e_uni, uint64_t n_total,
+                                 uint32_t cap, uint64_t *out, double *e_unit, unsigned long long *scratch,
+                                 cudaStream_t s);
 cudaError_t launch_update_temperature_ali(const DevCloud *dcl, int64_t n_cells, const TempTables &tt,
                                           const double *A, const double *A_self, float *T, double *max_dT,
                                           cudaStream_t s);

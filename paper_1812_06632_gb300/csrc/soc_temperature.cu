@@ -10,6 +10,7 @@
 // a plain sequential FP64 evaluation bit for bit.
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <algorithm>
 #include "soc_internal.h"
 
 namespace soc {
@@ -222,6 +223,117 @@ __global__ void dust_weight_kernel(const DevCloud *__restrict__ dcl, int64_t n_l
     }
 }
 
+// ---------------------------------------------------------------------------
+// Emission-weighted dust sampling (paper Sect. 3.2: packages per cell in
+// proportion to its luminosity, at most `cap` per cell), from the uniform
+// weights u = rint(2^32 L / max L) of each frequency.  Integer sums and a
+// fixed operation order keep the allocation deterministic.
+// out layout per frequency: [W: n_leaf][prefix: n_leaf + 1] (uint64).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v)
+{
+    __shared__ unsigned long long ssum[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) ssum[warp] = v;
+    __syncthreads();
+    unsigned long long t = 0;
+    if (warp == 0) {
+        t = lane < (int)((blockDim.x + 31) >> 5) ? ssum[lane] : 0ull;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    __syncthreads();
+    return t;                                   // valid in thread 0
+}
+
+constexpr int kScanChunk = 1024;
+
+// S[f] = sum over leaves of u[f][li]
+__global__ void wsum_kernel(const unsigned long long *u, int64_t n_leaf, int n_freq, unsigned long long *S)
+{
+    const int f = blockIdx.y;
+    unsigned long long v = 0;
+    for (int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; li < n_leaf; li += (int64_t)gridDim.x * blockDim.x)
+        v += u[(int64_t)f * n_leaf + li];
+    const unsigned long long t = block_sum_u64(v);
+    if (threadIdx.x == 0 && t) atomicAdd(S + f, t);
+}
+
+// n = min(cap, ceil(N u / S)) (0 for u = 0) into the prefix slot (shifted by
+// one), W = rint((u / n) / E_ref 2^32), E_ref = max(S / N, 2^32 / cap); and
+// the per-chunk sums of n.
+__global__ void walloc_kernel(const unsigned long long *u, int64_t n_leaf, int n_freq, const unsigned long long *S,
+                              double n_total, double cap, const double *e_uni, unsigned long long *out, double *e_unit,
+                              unsigned long long *chunk_sum, int64_t n_chunks)
+{
+    const int f = blockIdx.y;
+    const double Sf = (double)S[f];
+    const double E_ref = fmax(__ddiv_rn(Sf, n_total), __ddiv_rn(4294967296.0, cap));
+    unsigned long long *W = out + (int64_t)f * (2 * n_leaf + 1);
+    unsigned long long *pre = W + n_leaf;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        e_unit[f] = Sf > 0.0 ? __ddiv_rn(__dmul_rn(e_uni[f], E_ref), 4294967296.0) : 0.0;
+        pre[0] = 0;
+    }
+    for (int64_t k = blockIdx.x; k < n_chunks; k += gridDim.x) {
+        unsigned long long v = 0;
+        for (int64_t li = k * kScanChunk + threadIdx.x; li < (k + 1) * kScanChunk && li < n_leaf; li += blockDim.x) {
+            const unsigned long long uc = u[(int64_t)f * n_leaf + li];
+            unsigned long long n = 0, w = 0;
+            if (uc && Sf > 0.0) {
+                n = (unsigned long long)fmin(cap, ceil(__ddiv_rn(__dmul_rn(n_total, (double)uc), Sf)));
+                w = (unsigned long long)rint(__dmul_rn(__ddiv_rn(__ddiv_rn((double)uc, (double)n), E_ref), 4294967296.0));
+            }
+            W[li] = w;
+            pre[li + 1] = n;
+            v += n;
+        }
+        const unsigned long long t = block_sum_u64(v);
+        if (threadIdx.x == 0) chunk_sum[(int64_t)f * n_chunks + k] = t;
+    }
+}
+
+// exclusive scan of the chunk sums of each frequency (one thread per frequency)
+__global__ void wchunk_scan_kernel(unsigned long long *chunk_sum, int64_t n_chunks, int n_freq)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n_freq) return;
+    unsigned long long run = 0;
+    for (int64_t k = 0; k < n_chunks; ++k) {
+        const unsigned long long v = chunk_sum[(int64_t)f * n_chunks + k];
+        chunk_sum[(int64_t)f * n_chunks + k] = run;
+        run += v;
+    }
+}
+
+// inclusive scan inside each chunk plus its offset: pre[li + 1] = sum of n[0..li]
+__global__ void wprefix_kernel(int64_t n_leaf, int n_freq, unsigned long long *out, const unsigned long long *chunk_off,
+                               int64_t n_chunks)
+{
+    __shared__ unsigned long long sh[kScanChunk];
+    const int f = blockIdx.y;
+    unsigned long long *pre = out + (int64_t)f * (2 * n_leaf + 1) + n_leaf;
+    for (int64_t k = blockIdx.x; k < n_chunks; k += gridDim.x) {
+        const int64_t base = k * kScanChunk;
+        for (int i = threadIdx.x; i < kScanChunk; i += blockDim.x)
+            sh[i] = (base + i < n_leaf) ? pre[base + i + 1] : 0ull;
+        __syncthreads();
+        for (int off = 1; off < kScanChunk; off <<= 1) {           // Hillis-Steele, in place
+            unsigned long long add[kScanChunk / 256];
+            int c = 0;
+            for (int i = threadIdx.x; i < kScanChunk; i += blockDim.x, ++c) add[c] = (i >= off) ? sh[i - off] : 0ull;
+            __syncthreads();
+            c = 0;
+            for (int i = threadIdx.x; i < kScanChunk; i += blockDim.x, ++c) sh[i] += add[c];
+            __syncthreads();
+        }
+        const unsigned long long o = chunk_off[(int64_t)f * n_chunks + k];
+        for (int i = threadIdx.x; i < kScanChunk; i += blockDim.x)
+            if (base + i < n_leaf) pre[base + i + 1] = sh[i] + o;
+        __syncthreads();
+    }
+}
+
 int grid_for(int64_t n, int block)
 {
     int dev = 0, sms = 148;
@@ -252,6 +364,30 @@ cudaError_t launch_update_temperature(const DevCloud *dcl, int64_t n_cells, cons
     }
     temperature_kernel<<<grid_for(n_cells, 256), 256, 0, s>>>(
         dcl, n_cells, tt, A, T, reinterpret_cast<unsigned long long *>(max_dT));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dust_weighted(int64_t n_leaf, int n_freq, const uint64_t *u, const double *e_uni, uint64_t n_total,
+                                 uint32_t cap, uint64_t *out, double *e_unit, unsigned long long *scratch,
+                                 cudaStream_t s)
+{
+    // scratch: [n_freq] sums, then [n_freq][n_chunks] chunk sums
+    const int64_t n_chunks = (n_leaf + kScanChunk - 1) / kScanChunk;
+    unsigned long long *S = scratch, *chunk = scratch + n_freq;
+    cudaError_t e = cudaMemsetAsync(S, 0, sizeof(unsigned long long) * n_freq, s);
+    if (e != cudaSuccess) return e;
+    const auto *uu = reinterpret_cast<const unsigned long long *>(u);
+    auto *oo = reinterpret_cast<unsigned long long *>(out);
+    dim3 g1((unsigned)std::min<int64_t>((n_leaf + 255) / 256, 1024), (unsigned)n_freq);
+    wsum_kernel<<<g1, 256, 0, s>>>(uu, n_leaf, n_freq, S);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dim3 g2((unsigned)std::min<int64_t>(n_chunks, 1024), (unsigned)n_freq);
+    walloc_kernel<<<g2, 256, 0, s>>>(uu, n_leaf, n_freq, S, (double)n_total, (double)cap, e_uni, oo, e_unit, chunk,
+                                     n_chunks);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    wchunk_scan_kernel<<<(n_freq + 63) / 64, 64, 0, s>>>(chunk, n_chunks, n_freq);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    wprefix_kernel<<<g2, 256, 0, s>>>(n_leaf, n_freq, oo, chunk, n_chunks);
     return cudaGetLastError();
 }
 

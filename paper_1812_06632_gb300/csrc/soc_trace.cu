@@ -234,8 +234,21 @@ __device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r,
         descend(C.cell, p);
         return true;
     }
-    // dust: n_per_cell packages from every leaf, uniform inside the cell
-    const int64_t li = (int64_t)(pid / it.n_per_cell);
+    // dust: n_per_cell packages from every leaf, or (weighted sampling) the
+    // leaf whose package-id range [prefix[li], prefix[li+1]) holds pid;
+    // uniform inside the cell
+    int64_t li;
+    if (it.flags & kItemWeighted) {
+        const unsigned long long *pre = reinterpret_cast<const unsigned long long *>(it.dust_w) + C.n_leaf;
+        int64_t lo = 0, hi = C.n_leaf;
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (__ldg(pre + mid) <= (unsigned long long)pid) lo = mid; else hi = mid;
+        }
+        li = lo;
+    } else {
+        li = (int64_t)(pid / it.n_per_cell);
+    }
     p.cell = __ldg(C.leaf + li);
     p.W = __ldg(reinterpret_cast<const unsigned long long *>(it.dust_w) + li);
     if (p.W == 0) return false;

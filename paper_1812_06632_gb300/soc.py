@@ -22,6 +22,7 @@ W_UNIT = 1 << 32
 
 EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "soc_grid_validate", "soc_grid_free",
            "soc_dust_upload", "soc_simulate_frequency_batch_ex", "soc_update_temperature_ali", "soc_map",
+           "soc_dust_weighted",
            "soc_sources_upload", "soc_simulate_frequency_batch", "soc_package_energy",
            "soc_dust_emission", "soc_absorbed_power", "soc_update_temperature", "soc_iterate",
            "soc_set_launch", "soc_set_refill", "soc_set_scatter_batch", "soc_set_max_steps",
@@ -80,6 +81,7 @@ def _load():
         "soc_simulate_frequency_batch_ex": ([P, P, I, P, P, P, P, P], I),
         "soc_update_temperature_ali": ([P, I, P, P, P, P, P], I),
         "soc_map": ([P, I, P, I, P, P, I, I, C.c_double, P, C.c_double, P, P], I),
+        "soc_dust_weighted": ([P, I, P, P, I, C.c_uint64, C.c_uint32, P, P, P], I),
         "soc_package_energy": ([P, I, I, U64, P], I),
         "soc_dust_emission": ([P, I, P, I, I, C.c_uint32, P, P, P], I),
         "soc_absorbed_power": ([P, I, P, C.c_int64, P, P, P, P], I),
@@ -257,6 +259,7 @@ class Context:
             dw = s.get("dust_w")
             it.d_dust_w = None if dw is None else dw.data_ptr()
             it.n_per_cell = s.get("n_per_cell", 1)
+            it.reserved = 1 if s.get("weighted") else 0
         return arr
 
     def simulate(self, items, tally, stats, pkg_steps=None, stream=None, self_tally=None):
@@ -312,6 +315,12 @@ class Context:
         n_freq = self.n_freq - freq_lo if n_freq is None else n_freq
         self._check(lib.soc_dust_emission(self.h, cloud_id, _t_ptr(T), freq_lo, n_freq, n_per_cell,
                                           _t_ptr(w), _t_ptr(e_unit), _stream(stream)))
+
+    def dust_weighted(self, cloud_id, u, e_unit_uniform, n_total, cap, out, e_unit, stream=None):
+        """soc_dust_weighted: out = [n_freq][2 n_leaf + 1] (weights, prefix)."""
+        n_freq = u.shape[0]
+        self._check(lib.soc_dust_weighted(self.h, cloud_id, _t_ptr(u), _t_ptr(e_unit_uniform), n_freq, n_total, cap,
+                                          _t_ptr(out), _t_ptr(e_unit), _stream(stream)))
 
     def absorbed_power(self, cloud_id, tally, stride, e_unit, A_out, A_in=None, stream=None):
         self._check(lib.soc_absorbed_power(self.h, cloud_id, _t_ptr(tally), stride, _t_ptr(e_unit),

@@ -531,3 +531,37 @@ def test_ali_update_reaches_the_same_fixed_point():
     plain = P.temperature(A_ext + A_self, nu, kabs)
     ali = P.temperature_ali(A_ext + A_self, A_self, T_old, nu, kabs)
     assert plain < ali <= Tstar * 1.0001
+
+
+def test_weighted_dust_sampling_allocation():
+    """Packages follow the luminosity, the cap holds, every emitting cell
+    gets a package, and packages x weight x unit energy return each cell's
+    luminosity (to rounding)."""
+    rng = np.random.default_rng(5)
+    L = np.exp(rng.normal(0, 3, 2000))
+    L[7] = L.max() * 50                       # one very bright cell
+    L[::13] = 0.0
+    u, e_uni = P.dust_weights(L, 1)
+    N, cap = 20000, 300
+    n, pref, W, e = P.weighted_dust_sampling(u, e_uni, N, cap)
+    assert n.max() <= cap and n[7] == cap
+    assert np.all((n > 0) == (u > 0)) and pref[-1] == n.sum()
+    assert np.all(W <= 2 ** 32) and W.max() == 2 ** 32
+    emitted = n.astype(np.float64) * W.astype(np.float64) * e
+    ok = u > 2 ** 12
+    np.testing.assert_allclose(emitted[ok], L[ok], rtol=2e-3)
+    # away from the cap and from the one-package floor, n follows L
+    mid = (n > 5) & (n < cap)
+    ratio = n[mid] / (N * L[mid] / L.sum())
+    assert np.all((ratio > 0.8) & (ratio < 1.3))
+
+
+def test_weighted_dust_tracing_conserves_and_uses_prefix():
+    cl = I.regular(np.ones((5, 5, 5), np.float32))
+    leaf = cl.leaves()
+    rng = np.random.default_rng(6)
+    u = rng.integers(0, 2 ** 32, leaf.size).astype(np.uint64)
+    n, pref, W, e = P.weighted_dust_sampling(u, 1.0, 3 * leaf.size, 40)
+    tally, st, steps = oracle.trace(_grid(cl), source=oracle.SRC_DUST, kabs=0.3, ksca=0.2, g=0.1, seed=2, leaf=leaf,
+                                    dust_w=W, dust_prefix=pref, n_packages=int(pref[-1]), want_steps=True)
+    assert int(tally.sum()) + st["escaped"] == st["emitted"] == int((n * W).sum())
