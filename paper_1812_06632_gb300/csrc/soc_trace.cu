@@ -237,17 +237,17 @@ __device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r,
     // dust: n_per_cell packages from every leaf, or (weighted sampling) the
     // leaf whose package-id range [prefix[li], prefix[li+1]) holds pid;
     // uniform inside the cell
-    int64_t li;
+    int32_t li;
     if (it.flags & kItemWeighted) {
         const unsigned long long *pre = reinterpret_cast<const unsigned long long *>(it.dust_w) + C.n_leaf;
-        int64_t lo = 0, hi = C.n_leaf;
+        int32_t lo = 0, hi = (int32_t)C.n_leaf;
         while (hi - lo > 1) {
-            const int64_t mid = (lo + hi) >> 1;
+            const int32_t mid = (lo + hi) >> 1;
             if (__ldg(pre + mid) <= (unsigned long long)pid) lo = mid; else hi = mid;
         }
         li = lo;
     } else {
-        li = (int64_t)(pid / it.n_per_cell);
+        li = (int32_t)(pid / it.n_per_cell);
     }
     p.cell = __ldg(C.leaf + li);
     p.W = __ldg(reinterpret_cast<const unsigned long long *>(it.dust_w) + li);
@@ -325,10 +325,9 @@ __device__ __forceinline__ uint64_t float_to_w(float v)
 
 // One photon-cell step (one segment inside one leaf).
 __device__ __forceinline__ int step(const DevCloud &C, Pkg &p, Rng &r, float kabs, float ksca,
-                                    float g, unsigned long long *tally, unsigned long long *self,
-                                    uint32_t max_steps)
+                                    float g, unsigned long long *tally, const TraceParams &P)
 {
-    if (p.steps >= max_steps) { p.pend += p.W; p.W = 0; return kCapped; }
+    if (p.steps >= P.max_steps) { p.pend += p.W; p.W = 0; return kCapped; }
     ++p.steps;
     float s = __int_as_float(0x7f800000);     // +inf
     int ax = -1;
@@ -373,7 +372,8 @@ __device__ __forceinline__ int step(const DevCloud &C, Pkg &p, Rng &r, float kab
     p.tauf = __fsub_rn(p.tauf, dtau);
     if (p.pend) {
         atomicAdd(tally + p.cell, (unsigned long long)p.pend);
-        if (p.wf & kHomeBit) atomicAdd(self + p.cell, (unsigned long long)p.pend);
+        if (p.wf & kHomeBit)      // self counters: same offset as the item's counters
+            atomicAdd(P.self + (tally - P.tally) + p.cell, (unsigned long long)p.pend);
         p.pend = 0;
     }
     p.wf &= ~kHomeBit;            // it leaves the cell it was emitted in
@@ -515,12 +515,11 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
             }
         }
         if (active && !(p.wf & kScatBit)) {
-            unsigned long long *self = P.self ? P.self + (tally - P.tally) : nullptr;
-            const int res = step(*C, p, r, kabs, ksca, g, tally, self, P.max_steps);
+            const int res = step(*C, p, r, kabs, ksca, g, tally, P);
             if (res != kContinue) {
                 if (p.pend) {
                     atomicAdd(tally + p.cell, (unsigned long long)p.pend);
-                    if (p.wf & kHomeBit) atomicAdd(self + p.cell, (unsigned long long)p.pend);
+                    if (p.wf & kHomeBit) atomicAdd(P.self + (tally - P.tally) + p.cell, (unsigned long long)p.pend);
                 }
                 p.pend = 0;
                 if (res == kEscaped) acc[0] += p.W;
