@@ -324,6 +324,7 @@ __device__ __forceinline__ uint64_t float_to_w(float v)
 }
 
 // One photon-cell step (one segment inside one leaf).
+template <bool kSelf>
 __device__ __forceinline__ int step(const DevCloud &C, Pkg &p, Rng &r, float kabs, float ksca,
                                     float g, unsigned long long *tally, const TraceParams &P)
 {
@@ -372,11 +373,11 @@ __device__ __forceinline__ int step(const DevCloud &C, Pkg &p, Rng &r, float kab
     p.tauf = __fsub_rn(p.tauf, dtau);
     if (p.pend) {
         atomicAdd(tally + p.cell, (unsigned long long)p.pend);
-        if (p.wf & kHomeBit)      // self counters: same offset as the item's counters
+        if (kSelf && (p.wf & kHomeBit))      // self counters: same offset as the item's counters
             atomicAdd(P.self + (tally - P.tally) + p.cell, (unsigned long long)p.pend);
         p.pend = 0;
     }
-    p.wf &= ~kHomeBit;            // it leaves the cell it was emitted in
+    if (kSelf) p.wf &= ~kHomeBit;            // it leaves the cell it was emitted in
     // move to the exit face: the exit coordinate exactly on the face, the
     // others advanced (selects, so lanes leaving through different faces
     // stay converged)
@@ -403,7 +404,7 @@ __device__ __forceinline__ int find_item(const uint64_t *__restrict__ prefix, in
     return lo;
 }
 
-template <int kMinBlocks>
+template <int kMinBlocks, bool kSelf>
 __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParams P)
 {
     const int lane = threadIdx.x & 31;
@@ -472,7 +473,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
                 p.steps = 0; p.pend = 0;
                 if (emit(*C, IT, pid, r, p)) {
                     p.wf = ((p.W >> 20) ? (uint32_t)(p.W >> 20) : 1u) |
-                           ((IT.source == SOC_SRC_DUST && P.self) ? kHomeBit : 0u);
+                           ((kSelf && IT.source == SOC_SRC_DUST) ? kHomeBit : 0u);
                     set_inverse(p);
                     p.tauf = -log_pos(r.u());
                     if (acc_item != item) {
@@ -515,11 +516,12 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
             }
         }
         if (active && !(p.wf & kScatBit)) {
-            const int res = step(*C, p, r, kabs, ksca, g, tally, P);
+            const int res = step<kSelf>(*C, p, r, kabs, ksca, g, tally, P);
             if (res != kContinue) {
                 if (p.pend) {
                     atomicAdd(tally + p.cell, (unsigned long long)p.pend);
-                    if (p.wf & kHomeBit) atomicAdd(P.self + (tally - P.tally) + p.cell, (unsigned long long)p.pend);
+                    if (kSelf && (p.wf & kHomeBit))
+                        atomicAdd(P.self + (tally - P.tally) + p.cell, (unsigned long long)p.pend);
                 }
                 p.pend = 0;
                 if (res == kEscaped) acc[0] += p.W;
@@ -637,10 +639,14 @@ cudaError_t launch_map(const MapParams &m, cudaStream_t s)
 
 cudaError_t launch_trace(const TraceParams &p, int grid, int block, int variant, cudaStream_t s)
 {
-    if (variant == 4)
-        trace_kernel<4><<<grid, block, 0, s>>>(p);
-    else
-        trace_kernel<3><<<grid, block, 0, s>>>(p);
+    // the self-counter logic (ALI) is compiled only into the variants that need it
+    if (p.self) {
+        if (variant == 4) trace_kernel<4, true><<<grid, block, 0, s>>>(p);
+        else trace_kernel<3, true><<<grid, block, 0, s>>>(p);
+    } else {
+        if (variant == 4) trace_kernel<4, false><<<grid, block, 0, s>>>(p);
+        else trace_kernel<3, false><<<grid, block, 0, s>>>(p);
+    }
     return cudaGetLastError();
 }
 
@@ -648,8 +654,8 @@ int trace_block_limit(int block, int variant)
 {
     int n = 0;
     cudaError_t e = (variant == 4)
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<4>, block, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<3>, block, 0);
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<4, false>, block, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<3, false>, block, 0);
     if (e != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }
