@@ -61,13 +61,12 @@ struct Pkg {
     uint64_t W;                   // weight (fixed point)
     uint64_t pend;                // deposits in the current cell not yet added
     uint32_t wf;                  // bits 0..12: weight floor max(W0 / 2^20, 1) (<= 2^12);
-                                  // kScatBit: waiting for its scattering;
                                   // kHomeBit: dust package still in its emission cell
     uint32_t steps;
+    bool scat;                    // waiting for its scattering (new direction, new free path)
 };
 
 constexpr uint32_t kFloorMask = 0x1fffu;
-constexpr uint32_t kScatBit = 1u << 30;
 constexpr uint32_t kHomeBit = 1u << 31;
 
 __device__ __forceinline__ void set_inverse(Pkg &p)
@@ -362,12 +361,12 @@ __device__ __forceinline__ int step(const DevCloud &C, Pkg &p, Rng &r, float kab
         p.W -= dep;
         p.pend += dep;
     }
-    if (p.W < (uint64_t)(p.wf & kFloorMask)) { p.pend += p.W; p.W = 0; return kAbsorbed; }
+    if (p.W < (uint64_t)(kSelf ? (p.wf & kFloorMask) : p.wf)) { p.pend += p.W; p.W = 0; return kAbsorbed; }
     if (scatter) {
         p.x = clamp01(__fadd_rn(p.x, __fmul_rn(p.dx, sp)));
         p.y = clamp01(__fadd_rn(p.y, __fmul_rn(p.dy, sp)));
         p.z = clamp01(__fadd_rn(p.z, __fmul_rn(p.dz, sp)));
-        p.wf |= kScatBit;         // the new direction is drawn in the warp's scattering phase
+        p.scat = true;            // the new direction is drawn in the warp's scattering phase
         return kContinue;
     }
     p.tauf = __fsub_rn(p.tauf, dtau);
@@ -420,7 +419,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
 
     Pkg p;
     Rng r;
-    p.steps = 0; p.W = 0; p.pend = 0; p.wf = 0;
+    p.steps = 0; p.W = 0; p.pend = 0; p.wf = 0; p.scat = false;
     bool active = false;
     int item = -1;
     const DevCloud *C = nullptr;
@@ -470,7 +469,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
                 const uint32_t pid = IT.pid_offset + (uint32_t)(gidx - P.prefix[item]);
                 r.init(P.seed, (uint32_t)IT.iteration, (uint32_t)IT.freq, pid, (uint32_t)IT.cloud,
                        (uint32_t)IT.source);
-                p.steps = 0; p.pend = 0;
+                p.steps = 0; p.pend = 0; p.scat = false;
                 if (emit(*C, IT, pid, r, p)) {
                     p.wf = ((p.W >> 20) ? (uint32_t)(p.W >> 20) : 1u) |
                            ((kSelf && IT.source == SOC_SRC_DUST) ? kHomeBit : 0u);
@@ -507,15 +506,15 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
         // does); a package's draws and operations keep their order
         {
             const unsigned act = __ballot_sync(kFull, active);
-            const unsigned sc = __ballot_sync(kFull, active && (p.wf & kScatBit));
-            if (sc && (__popc(sc) >= P.scatter_min || sc == act) && active && (p.wf & kScatBit)) {
+            const unsigned sc = __ballot_sync(kFull, active && p.scat);
+            if (sc && (__popc(sc) >= P.scatter_min || sc == act) && active && p.scat) {
                 hg_scatter(r, g, p);
                 set_inverse(p);
                 p.tauf = -log_pos(r.u());
-                p.wf &= ~kScatBit;
+                p.scat = false;
             }
         }
-        if (active && !(p.wf & kScatBit)) {
+        if (active && !p.scat) {
             const int res = step<kSelf>(*C, p, r, kabs, ksca, g, tally, P);
             if (res != kContinue) {
                 if (p.pend) {
