@@ -374,6 +374,11 @@ typedef struct soc_iterate_params {
                                   soc_iterate call on this cloud               */
     int32_t ali;               /* 1: accelerated update (diagonal operator,
                                   soc_update_temperature_ali)                  */
+    uint64_t n_weighted;       /* > 0: emission-weighted dust sampling with about
+                                  this many packages per frequency (replaces
+                                  n_per_cell), see soc_dust_weighted            */
+    uint32_t weighted_cap;     /* packages per cell at most (weighted sampling) */
+    int32_t reserved;
 } soc_iterate_params;
 
 typedef struct soc_iterate_result {

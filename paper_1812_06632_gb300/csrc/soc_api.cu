@@ -53,8 +53,8 @@ struct CloudHost {
     // iteration scratch (library owned)
     DevBuf<int64_t> tally, self_tally;
     DevBuf<double> A_const, A, A_self;
-    DevBuf<uint64_t> dust_w;
-    DevBuf<double> e_unit;
+    DevBuf<uint64_t> dust_w, dust_wp;
+    DevBuf<double> e_unit, e_unit_w;
     DevBuf<int64_t> stats;
 };
 
@@ -214,9 +214,9 @@ static void release_cloud(CloudHost *c)
 {
     c->cell.release(); c->parent.release(); c->leaf.release(); c->rho.release();
     c->volume.release(); c->kappa.release(); c->ps_pos.release(); c->ps_cdf.release();
-    c->tally.release(); c->A_const.release(); c->A.release(); c->dust_w.release();
+    c->tally.release(); c->A_const.release(); c->A.release(); c->dust_w.release(); c->dust_wp.release();
     c->self_tally.release(); c->A_self.release();
-    c->e_unit.release(); c->stats.release();
+    c->e_unit.release(); c->e_unit_w.release(); c->stats.release();
     c->freed = true;
 }
 
@@ -929,6 +929,12 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
     CK(cl.e_unit.alloc(nf), "alloc e_unit");
     CK(cl.stats.alloc((size_t)4 * nf), "alloc stats");
     if (prm->max_iter > 0) CK(cl.dust_w.alloc((size_t)nf * cl.n_leaf), "alloc dust weights");
+    const bool weighted = prm->n_weighted > 0;
+    if (weighted && prm->weighted_cap == 0) return fail(ctx, SOC_ERR_ARG, "weighted_cap must be >= 1");
+    if (weighted && prm->max_iter > 0) {
+        CK(cl.dust_wp.alloc((size_t)nf * (2 * cl.n_leaf + 1)), "alloc weighted sampling");
+        CK(cl.e_unit_w.alloc(nf), "alloc e_unit");
+    }
     const bool ali = prm->ali != 0;
     if (ali && prm->max_iter > 0) {
         CK(cl.self_tally.alloc((size_t)nf * n), "alloc self counters");
@@ -938,14 +944,18 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
     std::vector<int64_t> hstats(4 * nf);
     std::vector<soc_batch_item> items(nf);
     std::vector<double> e(nf);
+    std::vector<uint64_t> wcount(nf, 0);
     auto run_items = [&](int source, uint64_t npk, int iteration, const uint64_t *dw, uint32_t npc,
-                         int64_t *self) -> soc_status {
+                         int64_t *self, bool wsampled) -> soc_status {
         for (int f = 0; f < nf; ++f) {
             soc_batch_item &it = items[f];
             memset(&it, 0, sizeof it);
             it.cloud = cloud_id; it.freq = f; it.source = source; it.iteration = iteration;
-            it.pid_offset = 0; it.n_packages = npk; it.w0 = SOC_W_UNIT; it.tally_offset = (int64_t)f * n;
-            it.d_dust_w = dw ? dw + (size_t)f * cl.n_leaf : nullptr; it.n_per_cell = npc;
+            it.pid_offset = 0; it.n_packages = wsampled ? wcount[f] : npk; it.w0 = SOC_W_UNIT;
+            it.tally_offset = (int64_t)f * n;
+            it.d_dust_w = dw ? dw + (size_t)f * (wsampled ? 2 * cl.n_leaf + 1 : cl.n_leaf) : nullptr;
+            it.n_per_cell = npc;
+            it.reserved = wsampled ? SOC_ITEM_WEIGHTED : 0u;
         }
         CK(cudaMemsetAsync(cl.tally.p, 0, sizeof(int64_t) * nf * n, s), "zero tally");
         CK(cudaMemsetAsync(cl.stats.p, 0, sizeof(int64_t) * 4 * nf, s), "zero stats");
@@ -966,7 +976,7 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
     for (int k = 0; k < 2; ++k) {
         if (!nsrc[k]) continue;
         const int source = k == 0 ? SOC_SRC_BACKGROUND : SOC_SRC_POINT;
-        if ((st = run_items(source, nsrc[k], 0, nullptr, 1, nullptr))) return st;
+        if ((st = run_items(source, nsrc[k], 0, nullptr, 1, nullptr, false))) return st;
         if ((st = soc_package_energy(ctx, cloud_id, source, nsrc[k], e.data()))) return st;
         CK(cudaMemcpyAsync(cl.e_unit.p, e.data(), 8 * nf, cudaMemcpyHostToDevice, s), "copy e_unit");
         if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit.p, cl.A_const.p, cl.A_const.p, stream)))
@@ -981,16 +991,29 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
     int it_done = 0, conv = 0;
     double dT = 0.0;
     for (int k = 1; k <= prm->max_iter; ++k) {
-        if ((st = soc_dust_emission(ctx, cloud_id, d_T_out, 0, nf, prm->n_per_cell, cl.dust_w.p, cl.e_unit.p, stream)))
+        if ((st = soc_dust_emission(ctx, cloud_id, d_T_out, 0, nf, weighted ? 1u : prm->n_per_cell, cl.dust_w.p,
+                                    cl.e_unit.p, stream)))
             return st;
+        const double *e_dust = cl.e_unit.p;
+        if (weighted) {
+            if ((st = soc_dust_weighted(ctx, cloud_id, cl.dust_w.p, cl.e_unit.p, nf, prm->n_weighted,
+                                        prm->weighted_cap, cl.dust_wp.p, cl.e_unit_w.p, stream)))
+                return st;
+            for (int f = 0; f < nf; ++f)        // packages to trace = last prefix entry of each frequency
+                CK(cudaMemcpyAsync(&wcount[f], cl.dust_wp.p + (size_t)f * (2 * cl.n_leaf + 1) + 2 * cl.n_leaf,
+                                   sizeof(uint64_t), cudaMemcpyDeviceToHost, s), "read package counts");
+            CK(cudaStreamSynchronize(s), "sync");
+            e_dust = cl.e_unit_w.p;
+        }
         // frozen dust random numbers: the same RNG stream (iteration 1) every time
-        if ((st = run_items(SOC_SRC_DUST, (uint64_t)cl.n_leaf * prm->n_per_cell, 1, cl.dust_w.p, prm->n_per_cell,
-                            ali ? cl.self_tally.p : nullptr)))
+        if ((st = run_items(SOC_SRC_DUST, (uint64_t)cl.n_leaf * prm->n_per_cell, 1,
+                            weighted ? cl.dust_wp.p : cl.dust_w.p, prm->n_per_cell, ali ? cl.self_tally.p : nullptr,
+                            weighted)))
             return st;
-        if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit.p, cl.A_const.p, cl.A.p, stream)))
+        if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, e_dust, cl.A_const.p, cl.A.p, stream)))
             return st;
         if (ali) {
-            if ((st = soc_absorbed_power(ctx, cloud_id, cl.self_tally.p, n, cl.e_unit.p, nullptr, cl.A_self.p, stream)))
+            if ((st = soc_absorbed_power(ctx, cloud_id, cl.self_tally.p, n, e_dust, nullptr, cl.A_self.p, stream)))
                 return st;
             if ((st = soc_update_temperature_ali(ctx, cloud_id, cl.A.p, cl.A_self.p, d_T_out, ctx->d_maxdT.p, stream)))
                 return st;

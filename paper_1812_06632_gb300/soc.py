@@ -49,7 +49,8 @@ class BatchItem(C.Structure):
 class IterateParams(C.Structure):
     _fields_ = [("n_background", C.c_uint64), ("n_point", C.c_uint64), ("n_per_cell", C.c_uint32),
                 ("max_iter", C.c_int32), ("dT_tol", C.c_double), ("reuse_constant", C.c_int32),
-                ("ali", C.c_int32)]
+                ("ali", C.c_int32), ("n_weighted", C.c_uint64), ("weighted_cap", C.c_uint32),
+                ("reserved", C.c_int32)]
 
 
 class IterateResult(C.Structure):
@@ -343,8 +344,10 @@ class Context:
                                                _stream(stream)))
 
     def iterate(self, cloud_id, T_out, *, n_background=0, n_point=0, n_per_cell=1, max_iter=0,
-                dT_tol=0.1, T_seed=None, reuse_constant=False, ali=False, stream=None):
-        p = IterateParams(n_background, n_point, n_per_cell, max_iter, dT_tol, int(reuse_constant), int(ali))
+                dT_tol=0.1, T_seed=None, reuse_constant=False, ali=False, n_weighted=0, weighted_cap=10000,
+                stream=None):
+        p = IterateParams(n_background, n_point, n_per_cell, max_iter, dT_tol, int(reuse_constant), int(ali),
+                          n_weighted, weighted_cap, 0)
         r = IterateResult()
         hist = np.zeros(max(max_iter, 1), np.float64)
         self._check(lib.soc_iterate(self.h, cloud_id, C.byref(p), _t_ptr(T_seed), _t_ptr(T_out), C.byref(r),

@@ -90,3 +90,88 @@ def test_weighted_dust_tracing_bit_exact():
         assert st[k][0] == sto["escaped"] and st[k][3] == sto["emitted"]
         np.testing.assert_array_equal(sp[off:off + s["n_packages"]], so)
         off += s["n_packages"]
+
+
+def _dust_absorbed(ctx, cid, cl, T, nf, weighted, n_total, cap):
+    """Absorbed power from dust emission only (fixed T), one pass."""
+    leaf = cl.leaves()
+    nl = leaf.size
+    u = torch.zeros((nf, nl), dtype=torch.int64, device="cuda")
+    e = torch.zeros(nf, dtype=torch.float64, device="cuda")
+    ctx.dust_emission(cid, T, u, e, n_per_cell=1)
+    tally = torch.zeros(nf * cl.n_cells, dtype=torch.int64, device="cuda")
+    stats = torch.zeros((nf, 4), dtype=torch.int64, device="cuda")
+    if weighted:
+        out = torch.zeros((nf, 2 * nl + 1), dtype=torch.int64, device="cuda")
+        ew = torch.zeros(nf, dtype=torch.float64, device="cuda")
+        ctx.dust_weighted(cid, u, e, n_total, cap, out, ew)
+        torch.cuda.synchronize()
+        counts = out[:, 2 * nl].cpu().numpy()
+        specs = [dict(source=2, freq=f, n_packages=int(counts[f]), dust_w=out[f], weighted=True, iteration=1,
+                      tally_offset=f * cl.n_cells) for f in range(nf)]
+        e_use = ew
+    else:
+        per = max(1, n_total // nl)
+        u2 = torch.zeros((nf, nl), dtype=torch.int64, device="cuda")
+        ctx.dust_emission(cid, T, u2, e, n_per_cell=per)
+        specs = [dict(source=2, freq=f, n_packages=nl * per, dust_w=u2[f], n_per_cell=per, iteration=1,
+                      tally_offset=f * cl.n_cells) for f in range(nf)]
+        e_use = e
+    ctx.simulate(ctx.items(specs), tally, stats)
+    A = torch.zeros(cl.n_cells, dtype=torch.float64, device="cuda")
+    ctx.absorbed_power(cid, tally, cl.n_cells, e_use, A)
+    torch.cuda.synchronize()
+    return A.cpu().numpy(), int(stats[:, 3].sum().item() > 0)
+
+
+def test_weighted_sampling_lowers_noise_for_equal_budget():
+    """Two seeds, same temperatures with a hot core: the seed-to-seed spread of
+    the absorbed dust power (cells heated most by the dust) is smaller with
+    emission weighting than with the same number of uniform packages."""
+    w = I.config_c2(n=24, n_freq=16, n_packages=0, tau_1um=30.0)
+    cl = w.clouds[0]
+    n = 24
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r2 = ((i - 11.5) ** 2 + (j - 11.5) ** 2 + (k - 11.5) ** 2).ravel()
+    T_host = (15.0 + 250.0 * np.exp(-r2 / 8.0)).astype(np.float32)
+    T = torch.from_numpy(T_host).cuda()
+    nf = len(w.dust.nu)
+    budget = 2 * cl.n_cells
+    res = {}
+    from paper_1812_06632_gb300 import soc
+    for weighted in (False, True):
+        As = []
+        for seed in (11, 12):
+            ctx = soc.Context(0, seed)
+            ctx.dust_upload(w.dust.nu, w.dust.kabs, w.dust.ksca, w.dust.g)
+            cid = ctx.grid_upload(cl)
+            As.append(_dust_absorbed(ctx, cid, cl, T, nf, weighted, budget, 200)[0])
+            ctx.close()
+        res[weighted] = As
+    hot = np.argsort(res[False][0])[-200:]            # cells most heated by the dust
+    def spread(As):
+        a, b = As[0][hot], As[1][hot]
+        return float(np.sqrt(np.mean(((a - b) / (0.5 * (a + b))) ** 2)))
+    s_uni, s_w = spread(res[False]), spread(res[True])
+    # the same field in expectation
+    assert abs(res[True][0][hot].mean() / res[False][0][hot].mean() - 1) < 0.05
+    assert s_w < 0.8 * s_uni, (s_w, s_uni)
+
+
+def test_iterate_weighted_converges():
+    w = I.config_c3(root_n=8, max_refine=2, sigma=1.5, threshold=4.0, tau_peak_1um=200.0, n_freq=16,
+                    L_bol=3e36, side_pc=0.1, n_bg=20000, n_ps=20000)
+    cl = w.clouds[0]
+    from parity_helpers import gpu_context
+    res = {}
+    for mode in ("uniform", "weighted"):
+        ctx, ids = gpu_context(w)
+        T = torch.zeros(cl.n_cells, dtype=torch.float32, device="cuda")
+        kw = dict(n_weighted=2 * cl.leaves().size, weighted_cap=100) if mode == "weighted" else dict(n_per_cell=2)
+        r = ctx.iterate(ids[0], T, n_background=w.n_bg[0], n_point=w.n_ps[0], max_iter=40, dT_tol=0.1, **kw)
+        res[mode] = (r, T.cpu().numpy())
+        ctx.close()
+    assert res["uniform"][0]["converged"] and res["weighted"][0]["converged"]
+    leaf = cl.leaves()
+    Tu, Tw = res["uniform"][1][leaf], res["weighted"][1][leaf]
+    assert abs(Tw.mean() / Tu.mean() - 1) < 0.02
