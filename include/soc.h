@@ -288,6 +288,25 @@ soc_status soc_dust_weighted(soc_ctx *ctx, int cloud_id, const uint64_t *d_u, co
                              void *stream);
 
 /* ------------------------------------------------------------------------
+ * soc_dust_reweight -- new weights for an existing allocation (the prefix
+ * half of d_inout, as written by soc_dust_weighted, is read and kept), from
+ * new uniform weights u of soc_dust_emission (n_per_cell = 1):
+ *   n_c = prefix[c+1] - prefix[c];  E_ref = max over n_c > 0 of u_c / n_c;
+ *   W_c = n_c ? rint((u_c / n_c) / E_ref 2^32) : 0;
+ *   e_unit = e_unit_uniform E_ref / 2^32.
+ * Keeping the counts keeps every package's id -> cell map between dust
+ * iterations, so frozen random numbers (paper Sect. 3.2) give the same paths
+ * and the iteration converges like the uniform one.
+ *   d_u               device uint64 [n_freq][n_leaf].
+ *   d_inout           device uint64 [n_freq][2 n_leaf + 1]: W overwritten,
+ *                     prefix read.
+ *   d_e_unit          device double [n_freq], written.
+ * Deterministic.  Asynchronous on `stream`.
+ * ------------------------------------------------------------------------ */
+soc_status soc_dust_reweight(soc_ctx *ctx, int cloud_id, const uint64_t *d_u, const double *d_e_unit_uniform,
+                             int n_freq, uint64_t *d_inout, double *d_e_unit, void *stream);
+
+/* ------------------------------------------------------------------------
  * soc_absorbed_power -- frequency integral of the absorption counters (paper
  * Sect. 2.1.1: for equilibrium dust the integral of absorbed energy over
  * frequency is gathered on the device):
@@ -376,7 +395,9 @@ typedef struct soc_iterate_params {
                                   soc_update_temperature_ali)                  */
     uint64_t n_weighted;       /* > 0: emission-weighted dust sampling with about
                                   this many packages per frequency (replaces
-                                  n_per_cell), see soc_dust_weighted            */
+                                  n_per_cell), see soc_dust_weighted; the
+                                  allocation is made at the first dust
+                                  iteration and kept (soc_dust_reweight)       */
     uint32_t weighted_cap;     /* packages per cell at most (weighted sampling) */
     int32_t reserved;
 } soc_iterate_params;

@@ -185,3 +185,24 @@ def weighted_dust_sampling(u, e_unit_uniform, n_total, cap):
     prefix = np.zeros(u.size + 1, np.uint64)
     prefix[1:] = np.cumsum(n, dtype=np.uint64)
     return n, prefix, W, float(e_unit_uniform) * E_ref / W_UNIT
+
+
+def weighted_dust_reweight(u, e_unit_uniform, prefix):
+    """Weights for an existing (frozen) allocation n_c = prefix[c+1] - prefix[c]
+    at new temperatures: E_ref = max over cells with n_c > 0 of u_c / n_c,
+    W_c = rint((u_c / n_c) / E_ref 2^32), e_unit = e_unit_uniform E_ref / 2^32.
+    Frozen counts keep every package's id -> cell map, so iterations with
+    frozen random numbers follow the same paths."""
+    u = np.asarray(u, np.uint64)
+    pre = np.asarray(prefix, np.uint64)
+    n = (pre[1:] - pre[:-1]).astype(np.float64)
+    W = np.zeros(u.shape, np.uint64)
+    ok = n > 0
+    if not ok.any():
+        return W, 0.0
+    q = u[ok].astype(np.float64) / n[ok]
+    E_ref = float(q.max())
+    if not E_ref > 0:
+        return W, 0.0
+    W[ok] = np.rint(q / E_ref * W_UNIT).astype(np.uint64)
+    return W, float(e_unit_uniform) * E_ref / W_UNIT

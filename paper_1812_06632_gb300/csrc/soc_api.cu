@@ -818,6 +818,22 @@ soc_status soc_dust_weighted(soc_ctx *ctx, int cloud_id, const uint64_t *d_u, co
     return SOC_OK;
 }
 
+soc_status soc_dust_reweight(soc_ctx *ctx, int cloud_id, const uint64_t *d_u, const double *d_e_unit_uniform,
+                             int n_freq, uint64_t *d_inout, double *d_e_unit, void *stream)
+{
+    soc_status st = check_cloud(ctx, cloud_id);
+    if (st) return st;
+    if (!d_u || !d_e_unit_uniform || !d_inout || !d_e_unit || n_freq < 1)
+        return fail(ctx, SOC_ERR_ARG, "bad re-weighting arguments");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const CloudHost &cl = *ctx->clouds[cloud_id];
+    CK(ctx->d_wscratch.alloc((size_t)n_freq), "alloc weighted-sampling scratch");
+    CK(launch_dust_reweight(cl.n_leaf, n_freq, d_u, d_e_unit_uniform, d_inout, d_e_unit, ctx->d_wscratch.p,
+                            (cudaStream_t)stream),
+       "dust re-weighting");
+    return SOC_OK;
+}
+
 soc_status soc_absorbed_power(soc_ctx *ctx, int cloud_id, const int64_t *d_tally, int64_t tally_stride,
                               const double *d_e_unit, const double *d_A_in, double *d_A_out, void *stream)
 {
@@ -995,7 +1011,9 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
                                     cl.e_unit.p, stream)))
             return st;
         const double *e_dust = cl.e_unit.p;
-        if (weighted) {
+        if (weighted && k == 1) {
+            // the allocation is made once, from the first dust temperatures,
+            // and then frozen (only the weights follow T)
             if ((st = soc_dust_weighted(ctx, cloud_id, cl.dust_w.p, cl.e_unit.p, nf, prm->n_weighted,
                                         prm->weighted_cap, cl.dust_wp.p, cl.e_unit_w.p, stream)))
                 return st;
@@ -1003,8 +1021,12 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
                 CK(cudaMemcpyAsync(&wcount[f], cl.dust_wp.p + (size_t)f * (2 * cl.n_leaf + 1) + 2 * cl.n_leaf,
                                    sizeof(uint64_t), cudaMemcpyDeviceToHost, s), "read package counts");
             CK(cudaStreamSynchronize(s), "sync");
-            e_dust = cl.e_unit_w.p;
+        } else if (weighted) {
+            if ((st = soc_dust_reweight(ctx, cloud_id, cl.dust_w.p, cl.e_unit.p, nf, cl.dust_wp.p, cl.e_unit_w.p,
+                                        stream)))
+                return st;
         }
+        if (weighted) e_dust = cl.e_unit_w.p;
         // frozen dust random numbers: the same RNG stream (iteration 1) every time
         if ((st = run_items(SOC_SRC_DUST, (uint64_t)cl.n_leaf * prm->n_per_cell, 1,
                             weighted ? cl.dust_wp.p : cl.dust_w.p, prm->n_per_cell, ali ? cl.self_tally.p : nullptr,

@@ -99,6 +99,8 @@ cudaError_t launch_update_temperature(const DevCloud *dcl, int64_t n_cells, cons
 cudaError_t launch_dust_weighted(int64_t n_leaf, int n_freq, const uint64_t *u, const double *e_uni, uint64_t n_total,
                                  uint32_t cap, uint64_t *out, double *e_unit, unsigned long long *scratch,
                                  cudaStream_t s);
+cudaError_t launch_dust_reweight(int64_t n_leaf, int n_freq, const uint64_t *u, const double *e_uni, uint64_t *out,
+                                 double *e_unit, unsigned long long *scratch, cudaStream_t s);
 cudaError_t launch_update_temperature_ali(const DevCloud *dcl, int64_t n_cells, const TempTables &tt,
                                           const double *A, const double *A_self, float *T, double *max_dT,
                                           cudaStream_t s);

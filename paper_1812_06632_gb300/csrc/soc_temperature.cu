@@ -334,6 +334,63 @@ __global__ void wprefix_kernel(int64_t n_leaf, int n_freq, unsigned long long *o
     }
 }
 
+// Re-weighting with a frozen allocation (n from the prefix of `out`):
+// qmax[f] = max over leaves with n > 0 of u / n, kept as the bit pattern of a
+// non-negative double (ordered like its value, so an integer max works).
+__global__ void wqmax_kernel(const unsigned long long *u, int64_t n_leaf, const unsigned long long *out,
+                             unsigned long long *qmax)
+{
+    __shared__ unsigned long long smax[32];
+    const int f = blockIdx.y;
+    const unsigned long long *pre = out + (int64_t)f * (2 * n_leaf + 1) + n_leaf;
+    unsigned long long m = 0;
+    for (int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; li < n_leaf; li += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long n = pre[li + 1] - pre[li];
+        if (n) {
+            const double q = __ddiv_rn((double)u[(int64_t)f * n_leaf + li], (double)n);
+            const unsigned long long b = (unsigned long long)__double_as_longlong(q);
+            m = b > m ? b : m;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) smax[warp] = m;
+    __syncthreads();
+    if (warp == 0) {
+        m = lane < (int)((blockDim.x + 31) >> 5) ? smax[lane] : 0ull;
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+            m = t > m ? t : m;
+        }
+        if (lane == 0 && m) atomicMax(qmax + f, m);
+    }
+}
+
+// W = rint((u / n) / E_ref 2^32) with E_ref = qmax (0 where n = 0);
+// e_unit = e_unit_uniform E_ref / 2^32.
+__global__ void wreweight_kernel(const unsigned long long *u, int64_t n_leaf, const unsigned long long *qmax,
+                                 const double *e_uni, unsigned long long *out, double *e_unit)
+{
+    const int f = blockIdx.y;
+    const double E_ref = __longlong_as_double((long long)qmax[f]);
+    unsigned long long *W = out + (int64_t)f * (2 * n_leaf + 1);
+    const unsigned long long *pre = W + n_leaf;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        e_unit[f] = E_ref > 0.0 ? __ddiv_rn(__dmul_rn(e_uni[f], E_ref), 4294967296.0) : 0.0;
+    for (int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; li < n_leaf; li += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long n = pre[li + 1] - pre[li];
+        unsigned long long w = 0;
+        if (n && E_ref > 0.0) {
+            const double q = __ddiv_rn((double)u[(int64_t)f * n_leaf + li], (double)n);
+            w = (unsigned long long)rint(__dmul_rn(__ddiv_rn(q, E_ref), 4294967296.0));
+        }
+        W[li] = w;
+    }
+}
+
 int grid_for(int64_t n, int block)
 {
     int dev = 0, sms = 148;
@@ -388,6 +445,20 @@ cudaError_t launch_dust_weighted(int64_t n_leaf, int n_freq, const uint64_t *u, 
     wchunk_scan_kernel<<<(n_freq + 63) / 64, 64, 0, s>>>(chunk, n_chunks, n_freq);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     wprefix_kernel<<<g2, 256, 0, s>>>(n_leaf, n_freq, oo, chunk, n_chunks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dust_reweight(int64_t n_leaf, int n_freq, const uint64_t *u, const double *e_uni, uint64_t *out,
+                                 double *e_unit, unsigned long long *scratch, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * n_freq, s);
+    if (e != cudaSuccess) return e;
+    const auto *uu = reinterpret_cast<const unsigned long long *>(u);
+    auto *oo = reinterpret_cast<unsigned long long *>(out);
+    dim3 g((unsigned)std::min<int64_t>((n_leaf + 255) / 256, 1024), (unsigned)n_freq);
+    wqmax_kernel<<<g, 256, 0, s>>>(uu, n_leaf, oo, scratch);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    wreweight_kernel<<<g, 256, 0, s>>>(uu, n_leaf, scratch, e_uni, oo, e_unit);
     return cudaGetLastError();
 }
 

@@ -22,7 +22,7 @@ W_UNIT = 1 << 32
 
 EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "soc_grid_validate", "soc_grid_free",
            "soc_dust_upload", "soc_simulate_frequency_batch_ex", "soc_update_temperature_ali", "soc_map",
-           "soc_dust_weighted",
+           "soc_dust_weighted", "soc_dust_reweight",
            "soc_sources_upload", "soc_simulate_frequency_batch", "soc_package_energy",
            "soc_dust_emission", "soc_absorbed_power", "soc_update_temperature", "soc_iterate",
            "soc_set_launch", "soc_set_refill", "soc_set_scatter_batch", "soc_set_max_steps",
@@ -83,6 +83,7 @@ def _load():
         "soc_update_temperature_ali": ([P, I, P, P, P, P, P], I),
         "soc_map": ([P, I, P, I, P, P, I, I, C.c_double, P, C.c_double, P, P], I),
         "soc_dust_weighted": ([P, I, P, P, I, C.c_uint64, C.c_uint32, P, P, P], I),
+        "soc_dust_reweight": ([P, I, P, P, I, P, P, P], I),
         "soc_package_energy": ([P, I, I, U64, P], I),
         "soc_dust_emission": ([P, I, P, I, I, C.c_uint32, P, P, P], I),
         "soc_absorbed_power": ([P, I, P, C.c_int64, P, P, P, P], I),
@@ -322,6 +323,11 @@ class Context:
         n_freq = u.shape[0]
         self._check(lib.soc_dust_weighted(self.h, cloud_id, _t_ptr(u), _t_ptr(e_unit_uniform), n_freq, n_total, cap,
                                           _t_ptr(out), _t_ptr(e_unit), _stream(stream)))
+
+    def dust_reweight(self, cloud_id, u, e_unit_uniform, inout, e_unit, stream=None):
+        """soc_dust_reweight: new weights for the allocation held in inout."""
+        self._check(lib.soc_dust_reweight(self.h, cloud_id, _t_ptr(u), _t_ptr(e_unit_uniform), u.shape[0],
+                                          _t_ptr(inout), _t_ptr(e_unit), _stream(stream)))
 
     def absorbed_power(self, cloud_id, tally, stride, e_unit, A_out, A_in=None, stream=None):
         self._check(lib.soc_absorbed_power(self.h, cloud_id, _t_ptr(tally), stride, _t_ptr(e_unit),

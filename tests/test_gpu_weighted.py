@@ -92,6 +92,36 @@ def test_weighted_dust_tracing_bit_exact():
         off += s["n_packages"]
 
 
+def test_reweight_bit_exact():
+    """A frozen allocation re-weighted at new temperatures equals the oracle."""
+    w, cl, leaf, U, E = _setup(0, 0)
+    nf, nl = U.shape
+    ctx, ids = gpu_context(w)
+    out = torch.zeros((nf, 2 * nl + 1), dtype=torch.int64, device="cuda")
+    eo = torch.zeros(nf, dtype=torch.float64, device="cuda")
+    ctx.dust_weighted(ids[0], torch.from_numpy(U.view(np.int64)).cuda(), torch.from_numpy(E).cuda(), 5 * nl, 30,
+                      out, eo)
+    torch.cuda.synchronize()
+    first = out.cpu().numpy().view(np.uint64).copy()
+    rng = np.random.default_rng(21)
+    T2 = rng.uniform(8, 300, nl)
+    V = P.cell_volumes(oracle_grid(cl), cl.ell)
+    U2, E2 = [], []
+    for f in range(nf):
+        u, e = P.dust_weights(P.dust_luminosity(T2, cl.rho[leaf], V[leaf], w.dust.kabs[f], w.dust.nu[f]), 1)
+        U2.append(u); E2.append(e)
+    U2, E2 = np.array(U2), np.array(E2)
+    ctx.dust_reweight(ids[0], torch.from_numpy(U2.view(np.int64)).cuda(), torch.from_numpy(E2).cuda(), out, eo)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint64)
+    ge = eo.cpu().numpy()
+    np.testing.assert_array_equal(got[:, nl:], first[:, nl:])         # counts kept
+    for f in range(nf):
+        W, e = P.weighted_dust_reweight(U2[f], E2[f], first[f, nl:])
+        np.testing.assert_array_equal(got[f, :nl], W)
+        assert ge[f] == e or abs(ge[f] / e - 1) < 1e-15
+
+
 def _dust_absorbed(ctx, cid, cl, T, nf, weighted, n_total, cap):
     """Absorbed power from dust emission only (fixed T), one pass."""
     leaf = cl.leaves()
@@ -148,30 +178,38 @@ def test_weighted_sampling_lowers_noise_for_equal_budget():
             As.append(_dust_absorbed(ctx, cid, cl, T, nf, weighted, budget, 200)[0])
             ctx.close()
         res[weighted] = As
-    hot = np.argsort(res[False][0])[-200:]            # cells most heated by the dust
+    # cells around the hot core (chosen by geometry, not by a noisy sample)
+    hot = np.flatnonzero(r2 <= 20.0)
     def spread(As):
         a, b = As[0][hot], As[1][hot]
         return float(np.sqrt(np.mean(((a - b) / (0.5 * (a + b))) ** 2)))
     s_uni, s_w = spread(res[False]), spread(res[True])
     # the same field in expectation
-    assert abs(res[True][0][hot].mean() / res[False][0][hot].mean() - 1) < 0.05
+    m_uni = 0.5 * (res[False][0][hot].mean() + res[False][1][hot].mean())
+    m_w = 0.5 * (res[True][0][hot].mean() + res[True][1][hot].mean())
+    assert abs(m_w / m_uni - 1) < 0.05, (m_w, m_uni)
     assert s_w < 0.8 * s_uni, (s_w, s_uni)
 
 
 def test_iterate_weighted_converges():
+    """Dust iterations with emission weighting (cap 10000 packages per cell, as
+    in the paper's Sect. 4 test) converge with frozen random numbers and reach
+    the temperatures of a uniform run with 512x the packages.  A uniform run
+    with the weighted run's budget is biased low by its noise (few hits per
+    cell through the concave T(A)), far more than the weighted one."""
     w = I.config_c3(root_n=8, max_refine=2, sigma=1.5, threshold=4.0, tau_peak_1um=200.0, n_freq=16,
                     L_bol=3e36, side_pc=0.1, n_bg=20000, n_ps=20000)
     cl = w.clouds[0]
-    from parity_helpers import gpu_context
+    leaf = cl.leaves()
     res = {}
-    for mode in ("uniform", "weighted"):
+    for mode, kw in (("uniform", dict(n_per_cell=2)), ("reference", dict(n_per_cell=1024)),
+                     ("weighted", dict(n_weighted=2 * leaf.size, weighted_cap=10000))):
         ctx, ids = gpu_context(w)
         T = torch.zeros(cl.n_cells, dtype=torch.float32, device="cuda")
-        kw = dict(n_weighted=2 * cl.leaves().size, weighted_cap=100) if mode == "weighted" else dict(n_per_cell=2)
-        r = ctx.iterate(ids[0], T, n_background=w.n_bg[0], n_point=w.n_ps[0], max_iter=40, dT_tol=0.1, **kw)
-        res[mode] = (r, T.cpu().numpy())
+        r = ctx.iterate(ids[0], T, n_background=w.n_bg[0], n_point=w.n_ps[0], max_iter=20, dT_tol=0.1, **kw)
+        assert r["converged"], mode
+        res[mode] = float(T.cpu().numpy()[leaf].mean())
         ctx.close()
-    assert res["uniform"][0]["converged"] and res["weighted"][0]["converged"]
-    leaf = cl.leaves()
-    Tu, Tw = res["uniform"][1][leaf], res["weighted"][1][leaf]
-    assert abs(Tw.mean() / Tu.mean() - 1) < 0.02
+    err_w = abs(res["weighted"] / res["reference"] - 1)
+    err_u = abs(res["uniform"] / res["reference"] - 1)
+    assert err_w < 0.02 and err_u > 3 * err_w, res

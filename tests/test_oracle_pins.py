@@ -565,3 +565,16 @@ def test_weighted_dust_tracing_conserves_and_uses_prefix():
     tally, st, steps = oracle.trace(_grid(cl), source=oracle.SRC_DUST, kabs=0.3, ksca=0.2, g=0.1, seed=2, leaf=leaf,
                                     dust_w=W, dust_prefix=pref, n_packages=int(pref[-1]), want_steps=True)
     assert int(tally.sum()) + st["escaped"] == st["emitted"] == int((n * W).sum())
+
+
+def test_weighted_reweight_keeps_counts_and_energy():
+    rng = np.random.default_rng(12)
+    L0 = np.exp(rng.normal(0, 2, 500))
+    u0, e0 = P.dust_weights(L0, 1)
+    n, pref, W0, e_0 = P.weighted_dust_sampling(u0, e0, 3000, 40)
+    L1 = L0 * np.exp(rng.normal(0, 0.3, 500))          # new temperatures
+    u1, e1 = P.dust_weights(L1, 1)
+    W1, e_1 = P.weighted_dust_reweight(u1, e1, pref)
+    assert W1.max() == 2 ** 32 and np.all((W1 > 0) <= (n > 0))
+    ok = (n > 0) & (u1 > 2 ** 16)
+    np.testing.assert_allclose(n[ok] * W1[ok].astype(np.float64) * e_1, L1[ok], rtol=1e-4)
