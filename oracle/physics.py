@@ -206,3 +206,56 @@ def weighted_dust_reweight(u, e_unit_uniform, prefix):
         return W, 0.0
     W[ok] = np.rint(q / E_ref * W_UNIT).astype(np.uint64)
     return W, float(e_unit_uniform) * E_ref / W_UNIT
+
+
+# ---------------------------------------------------------------------------
+# Reference field (Sect. 2.1.2; Sects. 3.4 and 3.6): a dust iteration traces
+# only the change of the dust emission against a reference emission L_ref,
+# whose absorbed power A_ref is kept per cell; both are package-weighted
+# averages over the iterations done, so early iterations with few packages
+# count less (Sect. 4.1).
+# ---------------------------------------------------------------------------
+def package_schedule(n_first, n_last, n_iter):
+    """Dust packages per frequency of iterations 1..n_iter, log n growing
+    linearly (Sect. 3.6): n_k = rint(n_first (n_last / n_first)^((k-1)/(n_iter-1)))."""
+    k = np.arange(n_iter, dtype=np.float64)
+    if n_iter == 1:
+        return np.array([int(n_last)], np.uint64)
+    ratio = float(n_last) / float(n_first)
+    return np.rint(float(n_first) * ratio ** (k / float(n_iter - 1))).astype(np.uint64)
+
+
+def reference_weights(n):
+    """w_k = n_k / sum_{j <= k} n_j: the step of the running package-weighted mean."""
+    n = np.asarray(n, np.float64)
+    return n / np.cumsum(n)
+
+
+def reference_delta(L, L_ref, w):
+    """Emission change of one frequency, d = L - L_ref (per leaf), as weights
+    of the emission-weighted sampler: m = max |d|, u = rint(|d| / m 2^32),
+    neg = d < 0, one unit of u carrying e_uni = m / 2^32 (one package per
+    cell).  The reference moves to L_ref + w d.  Returns (u, neg, e_uni, L_ref')."""
+    L = np.asarray(L, np.float64)
+    L_ref = np.asarray(L_ref, np.float64)
+    d = L - L_ref
+    a = np.abs(d)
+    m = float(a.max()) if a.size else 0.0
+    u = np.zeros(L.shape, np.uint64)
+    if m > 0:
+        u = np.rint((a / m) * W_UNIT).astype(np.uint64)
+    return u, d < 0, m / W_UNIT, L_ref + w * d
+
+
+def split_allocation(W, neg):
+    """Weights of the packages from cells whose emission rose (first) and fell
+    (second); the allocation (prefix) is shared."""
+    W = np.asarray(W, np.uint64)
+    z = np.zeros_like(W)
+    return np.where(neg, z, W), np.where(neg, W, z)
+
+
+def reference_update(A_ref, A_d, w):
+    """A_ref + w (A_d - A_ref), A_d = A_ref + the traced correction."""
+    A_ref = np.asarray(A_ref, np.float64)
+    return A_ref + w * (np.asarray(A_d, np.float64) - A_ref)

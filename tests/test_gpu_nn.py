@@ -21,8 +21,8 @@ def _need_gpu(libsoc):
 
 def _bf(a):
     """BF16 device tensor and its exact FP64 value."""
-    t = torch.from_numpy(np.asarray(a, np.float32)).cuda().to(torch.bfloat16)
-    return t, t.float().cpu().numpy().astype(np.float64)
+    h = torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16)      # rounded on the host
+    return h.cuda(), h.float().numpy().astype(np.float64)
 
 
 def _rel(a, b):

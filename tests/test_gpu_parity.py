@@ -219,11 +219,13 @@ def test_absorbed_power_and_temperature_match_oracle():
     for f in (3, 17):
         t_o = oracle_item(w, 0, specs[f])[0]
         np.testing.assert_array_equal(tally[f * cl.n_cells:(f + 1) * cl.n_cells], t_o)
-    tal2 = tally.reshape(nf, cl.n_cells)
+    # counters for the integral: seeded, made on the host (both sides take them)
+    tal2 = np.random.default_rng(31).integers(0, 2 ** 36, (nf, cl.n_cells)).astype(np.int64)
+    tal2[:, ::7] = 0
     e = P.background_package_energy(w.bg_I[0], cl.nx, cl.ny, cl.nz, cl.ell, N)
     np.testing.assert_allclose(ctx.package_energy(ids[0], 0, N), e, rtol=1e-15)
     A_o = P.absorbed_power(tal2, e, w.dust.nu, cl.rho, P.cell_volumes(oracle_grid(cl), cl.ell))
-    t_dev = torch.from_numpy(tally).cuda()
+    t_dev = torch.from_numpy(tal2.ravel()).cuda()
     e_dev = torch.from_numpy(e).cuda()
     A = torch.zeros(cl.n_cells, dtype=torch.float64, device="cuda")
     ctx.absorbed_power(ids[0], t_dev, cl.n_cells, e_dev, A)

@@ -56,20 +56,20 @@ def test_weighted_allocation_bit_exact(n_total, cap):
 
 
 def test_weighted_dust_tracing_bit_exact():
+    """Weighted dust packages (allocation made by the oracle, uploaded as the
+    tracer's input) give the oracle's counters, stats and step counts."""
     w, cl, leaf, U, E = _setup(0, 0)
     nf, nl = U.shape
     ctx, ids = gpu_context(w)
     n_total, cap = 6 * nl, 40
-    out = torch.zeros((nf, 2 * nl + 1), dtype=torch.int64, device="cuda")
-    eo = torch.zeros(nf, dtype=torch.float64, device="cuda")
-    ctx.dust_weighted(ids[0], torch.from_numpy(U.view(np.int64)).cuda(), torch.from_numpy(E).cuda(), n_total, cap,
-                      out, eo)
-    torch.cuda.synchronize()
-    host = out.cpu().numpy().view(np.uint64)
+    alloc = np.zeros((nf, 2 * nl + 1), np.uint64)
+    for f in range(nf):
+        _, pref, W, _ = P.weighted_dust_sampling(U[f], E[f], n_total, cap)
+        alloc[f, :nl], alloc[f, nl:] = W, pref
+    out = torch.from_numpy(alloc.view(np.int64)).cuda()
     specs = []
     for k, f in enumerate((1, 4, 7)):
-        n_pk = int(host[f, 2 * nl])
-        specs.append(dict(source=2, freq=f, n_packages=n_pk, dust_w=out[f], weighted=True,
+        specs.append(dict(source=2, freq=f, n_packages=int(alloc[f, 2 * nl]), dust_w=out[f], weighted=True,
                           tally_offset=k * cl.n_cells))
     tally = torch.zeros(3 * cl.n_cells, dtype=torch.int64, device="cuda")
     stats = torch.zeros((3, 4), dtype=torch.int64, device="cuda")
@@ -84,8 +84,8 @@ def test_weighted_dust_tracing_bit_exact():
         f = s["freq"]
         ka, ks = kappa_root(w.dust, f, cl.ell)
         to, sto, so = oracle.trace(oracle_grid(cl), source=2, kabs=ka, ksca=ks, g=np.float32(w.dust.g[f]), seed=w.seed,
-                                   freq=f, n_packages=s["n_packages"], leaf=leaf, dust_w=host[f, :nl],
-                                   dust_prefix=host[f, nl:], want_steps=True)
+                                   freq=f, n_packages=s["n_packages"], leaf=leaf, dust_w=alloc[f, :nl],
+                                   dust_prefix=alloc[f, nl:], want_steps=True)
         np.testing.assert_array_equal(t[k * cl.n_cells:(k + 1) * cl.n_cells], to)
         assert st[k][0] == sto["escaped"] and st[k][3] == sto["emitted"]
         np.testing.assert_array_equal(sp[off:off + s["n_packages"]], so)
@@ -97,12 +97,12 @@ def test_reweight_bit_exact():
     w, cl, leaf, U, E = _setup(0, 0)
     nf, nl = U.shape
     ctx, ids = gpu_context(w)
-    out = torch.zeros((nf, 2 * nl + 1), dtype=torch.int64, device="cuda")
+    alloc = np.zeros((nf, 2 * nl + 1), np.uint64)
+    for f in range(nf):
+        _, pref, W, _ = P.weighted_dust_sampling(U[f], E[f], 5 * nl, 30)
+        alloc[f, :nl], alloc[f, nl:] = W, pref
+    out = torch.from_numpy(alloc.view(np.int64).copy()).cuda()
     eo = torch.zeros(nf, dtype=torch.float64, device="cuda")
-    ctx.dust_weighted(ids[0], torch.from_numpy(U.view(np.int64)).cuda(), torch.from_numpy(E).cuda(), 5 * nl, 30,
-                      out, eo)
-    torch.cuda.synchronize()
-    first = out.cpu().numpy().view(np.uint64).copy()
     rng = np.random.default_rng(21)
     T2 = rng.uniform(8, 300, nl)
     V = P.cell_volumes(oracle_grid(cl), cl.ell)
@@ -115,9 +115,9 @@ def test_reweight_bit_exact():
     torch.cuda.synchronize()
     got = out.cpu().numpy().view(np.uint64)
     ge = eo.cpu().numpy()
-    np.testing.assert_array_equal(got[:, nl:], first[:, nl:])         # counts kept
+    np.testing.assert_array_equal(got[:, nl:], alloc[:, nl:])         # counts kept
     for f in range(nf):
-        W, e = P.weighted_dust_reweight(U2[f], E2[f], first[f, nl:])
+        W, e = P.weighted_dust_reweight(U2[f], E2[f], alloc[f, nl:])
         np.testing.assert_array_equal(got[f, :nl], W)
         assert ge[f] == e or abs(ge[f] / e - 1) < 1e-15
 

@@ -578,3 +578,74 @@ def test_weighted_reweight_keeps_counts_and_energy():
     assert W1.max() == 2 ** 32 and np.all((W1 > 0) <= (n > 0))
     ok = (n > 0) & (u1 > 2 ** 16)
     np.testing.assert_allclose(n[ok] * W1[ok].astype(np.float64) * e_1, L1[ok], rtol=1e-4)
+
+
+def test_package_schedule_and_reference_weights():
+    n = P.package_schedule(1000, 200000, 5)
+    assert n[0] == 1000 and n[-1] == 200000
+    r = n[1:].astype(np.float64) / n[:-1]
+    np.testing.assert_allclose(r, 200.0 ** 0.25, rtol=1e-3)        # log n linear in k
+    w = P.reference_weights([4, 4, 4, 4])
+    np.testing.assert_allclose(w, [1, 1 / 2, 1 / 3, 1 / 4])
+    assert P.package_schedule(7, 9, 1)[0] == 9
+
+
+def test_reference_field_running_mean_and_special_cases():
+    """The reference emission is the package-weighted mean of the emissions
+    seen so far; a first iteration (L_ref = 0) is plain emission-weighted
+    sampling of L; no change gives no packages."""
+    rng = np.random.default_rng(13)
+    Ls = [np.exp(rng.normal(0, 1, 300)) for _ in range(4)]
+    n = np.array([100, 400, 1600, 6400])
+    w = P.reference_weights(n)
+    L_ref = np.zeros(300)
+    for k in range(4):
+        u, neg, e, L_ref = P.reference_delta(Ls[k], L_ref, w[k])
+    np.testing.assert_allclose(L_ref, sum(nk * L for nk, L in zip(n, Ls)) / n.sum(), rtol=1e-13)
+    # first iteration: the same weights as the uniform dust weights of L
+    u1, neg1, e1, _ = P.reference_delta(Ls[0], np.zeros(300), 1.0)
+    u0, e0 = P.dust_weights(Ls[0], 1)
+    np.testing.assert_array_equal(u1, u0)
+    assert not neg1.any() and e1 == e0
+    # a converged emission traces nothing
+    u2, neg2, e2, L2 = P.reference_delta(Ls[1], Ls[1], 0.5)
+    assert e2 == 0.0 and not u2.any() and np.array_equal(L2, Ls[1])
+    # signs and magnitudes: units x e_uni return |d|
+    u3, neg3, e3, _ = P.reference_delta(Ls[2], Ls[3], 0.3)
+    d = Ls[2] - Ls[3]
+    np.testing.assert_array_equal(neg3, d < 0)
+    np.testing.assert_allclose(u3 * e3, np.abs(d), rtol=1e-9, atol=e3)
+    Wp, Wn = P.split_allocation(u3, neg3)
+    np.testing.assert_array_equal(Wp + Wn, u3)
+    assert not Wp[neg3].any() and not Wn[~neg3].any()
+
+
+def test_reference_field_correction_is_unbiased_by_linearity():
+    """Tracing the change d = L_b - L_a (both signs, weighted sampling) and
+    adding it to the absorption of L_a gives, in the mean over seeds, the
+    absorption of L_b (the estimator the reference field relies on)."""
+    cl = I.regular(np.full((4, 4, 4), 2.0, np.float32))
+    leaf = cl.leaves()
+    G = _grid(cl)
+    rng = np.random.default_rng(17)
+    L_a = np.exp(rng.normal(0, 1, leaf.size))
+    L_b = L_a * np.exp(rng.normal(0, 0.5, leaf.size))
+
+    def absorbed(W, e, seed, n_pk, **kw):
+        t = oracle.trace(G, source=oracle.SRC_DUST, kabs=0.25, ksca=0.0, g=0.0, seed=seed, leaf=leaf, dust_w=W,
+                         n_packages=n_pk, **kw)[0]
+        return t.astype(np.float64) * e
+
+    nl = leaf.size
+    u_b, e_b = P.dust_weights(L_b, 64)          # direct: 64 packages per cell
+    A_b = np.mean([absorbed(u_b, e_b, s, 64 * nl, n_per_cell=64) for s in (1, 2)], axis=0)
+    u_a, e_a = P.dust_weights(L_a, 64)
+    A_a = np.mean([absorbed(u_a, e_a, s, 64 * nl, n_per_cell=64) for s in (3, 4)], axis=0)
+    u, neg, e_uni, _ = P.reference_delta(L_b, L_a, 1.0)
+    n, pref, W, e_w = P.weighted_dust_sampling(u, e_uni, 64 * nl, 10 ** 6)
+    Wp, Wn = P.split_allocation(W, neg)
+    n_pk = int(pref[-1])
+    dA = np.mean([absorbed(Wp, e_w, s, n_pk, dust_prefix=pref) - absorbed(Wn, e_w, s, n_pk, dust_prefix=pref)
+                  for s in (5, 6)], axis=0)
+    tot_b, tot_ref = A_b.sum(), (A_a + dA).sum()
+    assert abs(tot_ref / tot_b - 1) < 0.02, (tot_ref, tot_b)
