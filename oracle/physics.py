@@ -209,11 +209,14 @@ def weighted_dust_reweight(u, e_unit_uniform, prefix):
 
 
 # ---------------------------------------------------------------------------
-# Reference field (Sect. 2.1.2; Sects. 3.4 and 3.6): a dust iteration traces
-# only the change of the dust emission against a reference emission L_ref,
-# whose absorbed power A_ref is kept per cell; both are package-weighted
-# averages over the iterations done, so early iterations with few packages
-# count less (Sect. 4.1).
+# Reference field (Sect. 2.1.2; Sects. 3.4, 3.6 and 4.1).  The stored
+# reference is the absorbed power A_ref of each cell, the package-weighted
+# mean of the dust-absorption estimates of the iterations done (fresh random
+# numbers each iteration), so its noise falls with the number of iterations
+# and early iterations with few packages count less; T comes from
+# A_const + A_ref ("mean" reading).  The "difference" variant traces only the
+# change of the emission against a reference emission L_ref (also a running
+# mean) and takes T from A_const + A_ref + the traced change.
 # ---------------------------------------------------------------------------
 def package_schedule(n_first, n_last, n_iter):
     """Dust packages per frequency of iterations 1..n_iter, log n growing
@@ -256,6 +259,8 @@ def split_allocation(W, neg):
 
 
 def reference_update(A_ref, A_d, w):
-    """A_ref + w (A_d - A_ref), A_d = A_ref + the traced correction."""
+    """A_ref + w (A_d - A_ref): the running mean moved towards the estimate
+    A_d of this iteration (the full dust absorption in the "mean" reading,
+    A_ref + the traced change in the "difference" variant)."""
     A_ref = np.asarray(A_ref, np.float64)
     return A_ref + w * (np.asarray(A_d, np.float64) - A_ref)

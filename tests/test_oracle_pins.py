@@ -649,3 +649,31 @@ def test_reference_field_correction_is_unbiased_by_linearity():
                   for s in (5, 6)], axis=0)
     tot_b, tot_ref = A_b.sum(), (A_a + dA).sum()
     assert abs(tot_ref / tot_b - 1) < 0.02, (tot_ref, tot_b)
+
+
+def test_reference_mean_noise_falls_with_iterations():
+    """Mean reading at fixed emission: the running package-weighted mean of
+    independent absorption estimates has a seed-to-seed scatter that falls
+    as (number of iterations)^-1/2 (Sect. 2.1.2's ideal case)."""
+    cl = I.regular(np.full((4, 4, 4), 1.0, np.float32))
+    leaf = cl.leaves()
+    G = _grid(cl)
+    L = np.exp(np.random.default_rng(23).normal(0, 1, leaf.size))
+    u, e = P.dust_weights(L, 4)
+
+    def run(seed, K):
+        n = P.package_schedule(4 * leaf.size, 4 * leaf.size, K)
+        wk = P.reference_weights(n)
+        A = np.zeros(leaf.size)
+        for k in range(K):
+            t = oracle.trace(G, source=oracle.SRC_DUST, kabs=0.3, ksca=0.0, g=0.0, seed=seed, iteration=k + 1,
+                             leaf=leaf, dust_w=u, n_per_cell=4, n_packages=4 * leaf.size)[0]
+            A = P.reference_update(A, t[leaf] * e, wk[k])
+        return A
+
+    def scatter(K):
+        a, b = run(1, K), run(2, K)
+        return float(np.sqrt(np.mean(((a - b) / (0.5 * (a + b))) ** 2)))
+
+    s1, s4 = scatter(1), scatter(4)
+    assert 0.35 < s4 / s1 < 0.65, (s1, s4)          # 1/sqrt(4) = 0.5
