@@ -307,6 +307,44 @@ soc_status soc_dust_reweight(soc_ctx *ctx, int cloud_id, const uint64_t *d_u, co
                              int n_freq, uint64_t *d_inout, double *d_e_unit, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Reference-field building blocks (paper Sect. 2.1.2: a simulation estimates
+ * only a correction to the mean radiation field of the earlier iterations,
+ * storing the absorption of that reference field; Sects. 3.4, 3.6 and 4.1:
+ * package counts growing over the iterations, earlier iterations weighted
+ * less).  Arrays over (frequency, leaf) are frequency-major [n_freq][n_leaf],
+ * leaves in the order of the cloud's leaf list.  All asynchronous on
+ * `stream`; SOC_ERR_ARG for null pointers or n_freq < 1.
+ *
+ * soc_dust_luminosity: d_L (device double) = 4 pi rho V kabs B_nu(T) of every
+ *   leaf at frequencies freq_lo .. freq_lo + n_freq - 1 (erg/s/Hz).
+ *
+ * soc_reference_delta: per frequency, d = L - L_ref, m = max |d|,
+ *   d_u (device uint64) = rint(|d| / m 2^32), d_neg (device uint8) = d < 0,
+ *   d_e_unit_uniform (device double [n_freq]) = m / 2^32 (energy of one
+ *   unit of u with one package per cell: the input of soc_dust_weighted),
+ *   and L_ref (device double, in/out) += w d.
+ *
+ * soc_dust_split: splits allocations [n_freq][2 n_leaf + 1] (W then prefix,
+ *   from soc_dust_weighted) by d_neg: d_alloc keeps the weights of leaves
+ *   with d >= 0 (others 0), d_alloc_neg gets those of leaves with d < 0 and
+ *   a copy of the prefix; d_e_unit_neg = -d_e_unit, so that
+ *   soc_absorbed_power with it subtracts the falling cells' part.
+ *
+ * soc_reference_update: over the cloud's n_cells, d_A_ref (in/out) +=
+ *   w (d_A_d - d_A_ref); d_A_out (may be NULL) = d_A_const + X with
+ *   X = the updated d_A_ref if out_mean, else d_A_d (d_A_const may be NULL:
+ *   then X).
+ * ------------------------------------------------------------------------ */
+soc_status soc_dust_luminosity(soc_ctx *ctx, int cloud_id, const float *d_T, int freq_lo, int n_freq, double *d_L,
+                               void *stream);
+soc_status soc_reference_delta(soc_ctx *ctx, int cloud_id, int n_freq, const double *d_L, double *d_L_ref,
+                               double w, uint64_t *d_u, uint8_t *d_neg, double *d_e_unit_uniform, void *stream);
+soc_status soc_dust_split(soc_ctx *ctx, int cloud_id, int n_freq, const uint8_t *d_neg, uint64_t *d_alloc,
+                          uint64_t *d_alloc_neg, const double *d_e_unit, double *d_e_unit_neg, void *stream);
+soc_status soc_reference_update(soc_ctx *ctx, int cloud_id, double *d_A_ref, const double *d_A_d, double w,
+                                const double *d_A_const, double *d_A_out, int out_mean, void *stream);
+
+/* ------------------------------------------------------------------------
  * soc_absorbed_power -- frequency integral of the absorption counters (paper
  * Sect. 2.1.1: for equilibrium dust the integral of absorbed energy over
  * frequency is gathered on the device):
@@ -375,6 +413,12 @@ soc_status soc_map(soc_ctx *ctx, int cloud_id, const float *d_T, int freq, const
  * from T_{k-1} (with the same random numbers every iteration), add the
  * constant part and update T, until max |T_k - T_{k-1}| < dT_tol or
  * max_iter iterations.  Synchronises once per iteration (reads max |dT|).
+ * With a reference field, iteration k uses n_k dust packages per frequency
+ * (n_dust_first .. n_dust_last, or n_weighted), the reference step
+ * w_k = n_k / (n_1 + .. + n_k) and random-number iteration key k; mode 1
+ * traces the full emission (soc_dust_emission, soc_dust_weighted) and
+ * averages, mode 2 traces the change (soc_dust_luminosity ..
+ * soc_reference_update).
  *   d_T_seed          device float [n_cells] or NULL: initial temperatures
  *                     (e.g. a learned prediction); NULL uses T from the
  *                     constant sources alone.
@@ -399,7 +443,22 @@ typedef struct soc_iterate_params {
                                   allocation is made at the first dust
                                   iteration and kept (soc_dust_reweight)       */
     uint32_t weighted_cap;     /* packages per cell at most (weighted sampling) */
-    int32_t reserved;
+    int32_t reference_field;   /* reference field (paper Sect. 2.1.2), fresh
+                                  random numbers per dust iteration, emission-
+                                  weighted sampling, not with ali.
+                                  1 (mean): every dust iteration traces the
+                                  full dust emission; A_ref = package-weighted
+                                  mean of the estimates; T from A_const + A_ref.
+                                  2 (difference): traces only the change of
+                                  the emission against the running mean of the
+                                  earlier emissions; T from A_const + A_ref +
+                                  the traced change (the noise of the first
+                                  estimate stays in A_ref).                    */
+    uint64_t n_dust_first;     /* reference field: dust packages per frequency
+                                  of the first dust iteration (0: n_weighted
+                                  for every iteration)                         */
+    uint64_t n_dust_last;      /* ... and of iteration max_iter; log n grows
+                                  linearly in between (paper Sect. 3.6)       */
 } soc_iterate_params;
 
 typedef struct soc_iterate_result {

@@ -56,6 +56,10 @@ struct CloudHost {
     DevBuf<uint64_t> dust_w, dust_wp;
     DevBuf<double> e_unit, e_unit_w;
     DevBuf<int64_t> stats;
+    // reference field
+    DevBuf<double> L, L_ref, A_ref, A_d, e_unit_n;
+    DevBuf<uint8_t> neg;
+    DevBuf<uint64_t> dust_wn;
 };
 
 }  // namespace
@@ -217,6 +221,8 @@ static void release_cloud(CloudHost *c)
     c->tally.release(); c->A_const.release(); c->A.release(); c->dust_w.release(); c->dust_wp.release();
     c->self_tally.release(); c->A_self.release();
     c->e_unit.release(); c->e_unit_w.release(); c->stats.release();
+    c->L.release(); c->L_ref.release(); c->A_ref.release(); c->A_d.release(); c->e_unit_n.release();
+    c->neg.release(); c->dust_wn.release();
     c->freed = true;
 }
 
@@ -834,6 +840,68 @@ soc_status soc_dust_reweight(soc_ctx *ctx, int cloud_id, const uint64_t *d_u, co
     return SOC_OK;
 }
 
+soc_status soc_dust_luminosity(soc_ctx *ctx, int cloud_id, const float *d_T, int freq_lo, int n_freq, double *d_L,
+                               void *stream)
+{
+    soc_status st = check_cloud(ctx, cloud_id);
+    if (st) return st;
+    if (!d_T || !d_L || n_freq < 1 || freq_lo < 0 || freq_lo + n_freq > ctx->n_freq)
+        return fail(ctx, SOC_ERR_ARG, "bad dust-luminosity arguments");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if ((st = sync_clouds(ctx))) return st;
+    const CloudHost &cl = *ctx->clouds[cloud_id];
+    TempTables tt{ctx->n_freq, ctx->d_w_kabs.p, ctx->d_w.p, ctx->d_nu.p, ctx->d_kabs.p, ctx->d_lnE.p, ctx->d_lnT.p};
+    CK(launch_dust_luminosity(ctx->d_clouds.p + cloud_id, cl.n_leaf, tt, d_T, freq_lo, n_freq, d_L,
+                              (cudaStream_t)stream),
+       "dust luminosity");
+    return SOC_OK;
+}
+
+soc_status soc_reference_delta(soc_ctx *ctx, int cloud_id, int n_freq, const double *d_L, double *d_L_ref,
+                               double w, uint64_t *d_u, uint8_t *d_neg, double *d_e_unit_uniform, void *stream)
+{
+    soc_status st = check_cloud(ctx, cloud_id);
+    if (st) return st;
+    if (!d_L || !d_L_ref || !d_u || !d_neg || !d_e_unit_uniform || n_freq < 1 || !(w >= 0.0 && w <= 1.0))
+        return fail(ctx, SOC_ERR_ARG, "bad reference-delta arguments");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const CloudHost &cl = *ctx->clouds[cloud_id];
+    CK(ctx->d_wscratch.alloc((size_t)n_freq), "alloc scratch");
+    CK(launch_reference_delta(cl.n_leaf, n_freq, d_L, d_L_ref, w, d_u, d_neg, d_e_unit_uniform, ctx->d_wscratch.p,
+                              (cudaStream_t)stream),
+       "reference delta");
+    return SOC_OK;
+}
+
+soc_status soc_dust_split(soc_ctx *ctx, int cloud_id, int n_freq, const uint8_t *d_neg, uint64_t *d_alloc,
+                          uint64_t *d_alloc_neg, const double *d_e_unit, double *d_e_unit_neg, void *stream)
+{
+    soc_status st = check_cloud(ctx, cloud_id);
+    if (st) return st;
+    if (!d_neg || !d_alloc || !d_alloc_neg || !d_e_unit || !d_e_unit_neg || n_freq < 1 || d_alloc == d_alloc_neg)
+        return fail(ctx, SOC_ERR_ARG, "bad split arguments");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const CloudHost &cl = *ctx->clouds[cloud_id];
+    CK(launch_dust_split(cl.n_leaf, n_freq, d_neg, d_alloc, d_alloc_neg, d_e_unit, d_e_unit_neg,
+                         (cudaStream_t)stream),
+       "dust split");
+    return SOC_OK;
+}
+
+soc_status soc_reference_update(soc_ctx *ctx, int cloud_id, double *d_A_ref, const double *d_A_d, double w,
+                                const double *d_A_const, double *d_A_out, int out_mean, void *stream)
+{
+    soc_status st = check_cloud(ctx, cloud_id);
+    if (st) return st;
+    if (!d_A_ref || !d_A_d || !(w >= 0.0 && w <= 1.0)) return fail(ctx, SOC_ERR_ARG, "bad reference-update arguments");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const CloudHost &cl = *ctx->clouds[cloud_id];
+    CK(launch_reference_update(cl.n_cells, d_A_ref, d_A_d, w, d_A_const, d_A_out, out_mean != 0,
+                               (cudaStream_t)stream),
+       "reference update");
+    return SOC_OK;
+}
+
 soc_status soc_absorbed_power(soc_ctx *ctx, int cloud_id, const int64_t *d_tally, int64_t tally_stride,
                               const double *d_e_unit, const double *d_A_in, double *d_A_out, void *stream)
 {
@@ -951,6 +1019,33 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
         CK(cl.dust_wp.alloc((size_t)nf * (2 * cl.n_leaf + 1)), "alloc weighted sampling");
         CK(cl.e_unit_w.alloc(nf), "alloc e_unit");
     }
+    const int refmode = prm->reference_field;
+    if (refmode < 0 || refmode > 2) return fail(ctx, SOC_ERR_ARG, "reference_field must be 0, 1 or 2");
+    const bool reffield = refmode != 0;
+    if (reffield) {
+        if (prm->ali) return fail(ctx, SOC_ERR_ARG, "reference_field and ali together are not supported");
+        if (prm->weighted_cap == 0) return fail(ctx, SOC_ERR_ARG, "weighted_cap must be >= 1");
+        if (prm->n_dust_first == 0 && prm->n_weighted == 0)
+            return fail(ctx, SOC_ERR_ARG, "reference_field needs n_dust_first/n_dust_last or n_weighted");
+        if (prm->n_dust_first && prm->n_dust_last == 0)
+            return fail(ctx, SOC_ERR_ARG, "n_dust_last must be >= 1");
+    }
+    if (reffield && prm->max_iter > 0) {
+        CK(cl.A_ref.alloc(n), "alloc A_ref");
+        CK(cl.A_d.alloc(n), "alloc A_d");
+        CK(cl.dust_wp.alloc((size_t)nf * (2 * cl.n_leaf + 1)), "alloc weighted sampling");
+        CK(cl.e_unit_w.alloc(nf), "alloc e_unit");
+        CK(cudaMemsetAsync(cl.A_ref.p, 0, sizeof(double) * n, s), "zero A_ref");
+        if (refmode == 2) {
+            const size_t fl = (size_t)nf * cl.n_leaf;
+            CK(cl.L.alloc(fl), "alloc L");
+            CK(cl.L_ref.alloc(fl), "alloc L_ref");
+            CK(cl.neg.alloc(fl), "alloc signs");
+            CK(cl.dust_wn.alloc((size_t)nf * (2 * cl.n_leaf + 1)), "alloc weighted sampling");
+            CK(cl.e_unit_n.alloc(nf), "alloc e_unit");
+            CK(cudaMemsetAsync(cl.L_ref.p, 0, sizeof(double) * fl, s), "zero L_ref");
+        }
+    }
     const bool ali = prm->ali != 0;
     if (ali && prm->max_iter > 0) {
         CK(cl.self_tally.alloc((size_t)nf * n), "alloc self counters");
@@ -1006,7 +1101,75 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
     }
     int it_done = 0, conv = 0;
     double dT = 0.0;
+    double n_cum = 0.0;
     for (int k = 1; k <= prm->max_iter; ++k) {
+        if (reffield) {
+            // packages of this iteration: log n linear from n_dust_first to n_dust_last
+            uint64_t nk = prm->n_weighted;
+            if (prm->n_dust_first) {
+                const double t = prm->max_iter > 1 ? (double)(k - 1) / (double)(prm->max_iter - 1) : 1.0;
+                const double ratio = (double)prm->n_dust_last / (double)prm->n_dust_first;
+                nk = (uint64_t)std::max(1.0, rint((double)prm->n_dust_first * pow(ratio, t)));
+                if (prm->max_iter == 1) nk = prm->n_dust_last;
+            }
+            n_cum += (double)nk;
+            const double wk = (double)nk / n_cum;
+            if (refmode == 1) {
+                // full dust emission, fresh random numbers; A_ref = running mean of the estimates
+                if ((st = soc_dust_emission(ctx, cloud_id, d_T_out, 0, nf, 1u, cl.dust_w.p, cl.e_unit.p, stream)))
+                    return st;
+                if ((st = soc_dust_weighted(ctx, cloud_id, cl.dust_w.p, cl.e_unit.p, nf, nk, prm->weighted_cap,
+                                            cl.dust_wp.p, cl.e_unit_w.p, stream)))
+                    return st;
+                for (int f = 0; f < nf; ++f)
+                    CK(cudaMemcpyAsync(&wcount[f], cl.dust_wp.p + (size_t)f * (2 * cl.n_leaf + 1) + 2 * cl.n_leaf,
+                                       sizeof(uint64_t), cudaMemcpyDeviceToHost, s), "read package counts");
+                CK(cudaStreamSynchronize(s), "sync");
+                if ((st = run_items(SOC_SRC_DUST, 0, k, cl.dust_wp.p, 1, nullptr, true))) return st;
+                if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit_w.p, nullptr, cl.A_d.p, stream)))
+                    return st;
+                if ((st = soc_reference_update(ctx, cloud_id, cl.A_ref.p, cl.A_d.p, wk, cl.A_const.p, cl.A.p, 1,
+                                               stream)))
+                    return st;
+                if ((st = soc_update_temperature(ctx, cloud_id, cl.A.p, d_T_out, ctx->d_maxdT.p, stream))) return st;
+                CK(cudaMemcpyAsync(&dT, ctx->d_maxdT.p, sizeof(double), cudaMemcpyDeviceToHost, s), "read max dT");
+                CK(cudaStreamSynchronize(s), "sync");
+                if (dT_history) dT_history[k - 1] = dT;
+                it_done = k;
+                if (dT < prm->dT_tol) { conv = 1; break; }
+                continue;
+            }
+            if ((st = soc_dust_luminosity(ctx, cloud_id, d_T_out, 0, nf, cl.L.p, stream))) return st;
+            if ((st = soc_reference_delta(ctx, cloud_id, nf, cl.L.p, cl.L_ref.p, wk, cl.dust_w.p, cl.neg.p,
+                                          cl.e_unit.p, stream)))
+                return st;
+            if ((st = soc_dust_weighted(ctx, cloud_id, cl.dust_w.p, cl.e_unit.p, nf, nk, prm->weighted_cap,
+                                        cl.dust_wp.p, cl.e_unit_w.p, stream)))
+                return st;
+            if ((st = soc_dust_split(ctx, cloud_id, nf, cl.neg.p, cl.dust_wp.p, cl.dust_wn.p, cl.e_unit_w.p,
+                                     cl.e_unit_n.p, stream)))
+                return st;
+            for (int f = 0; f < nf; ++f)
+                CK(cudaMemcpyAsync(&wcount[f], cl.dust_wp.p + (size_t)f * (2 * cl.n_leaf + 1) + 2 * cl.n_leaf,
+                                   sizeof(uint64_t), cudaMemcpyDeviceToHost, s), "read package counts");
+            CK(cudaStreamSynchronize(s), "sync");
+            // rising cells, then falling cells (same packages ids, weights of the other sign are 0)
+            if ((st = run_items(SOC_SRC_DUST, 0, k, cl.dust_wp.p, 1, nullptr, true))) return st;
+            if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit_w.p, cl.A_ref.p, cl.A_d.p, stream)))
+                return st;
+            if ((st = run_items(SOC_SRC_DUST, 0, k, cl.dust_wn.p, 1, nullptr, true))) return st;
+            if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit_n.p, cl.A_d.p, cl.A_d.p, stream)))
+                return st;
+            if ((st = soc_reference_update(ctx, cloud_id, cl.A_ref.p, cl.A_d.p, wk, cl.A_const.p, cl.A.p, 0, stream)))
+                return st;
+            if ((st = soc_update_temperature(ctx, cloud_id, cl.A.p, d_T_out, ctx->d_maxdT.p, stream))) return st;
+            CK(cudaMemcpyAsync(&dT, ctx->d_maxdT.p, sizeof(double), cudaMemcpyDeviceToHost, s), "read max dT");
+            CK(cudaStreamSynchronize(s), "sync");
+            if (dT_history) dT_history[k - 1] = dT;
+            it_done = k;
+            if (dT < prm->dT_tol) { conv = 1; break; }
+            continue;
+        }
         if ((st = soc_dust_emission(ctx, cloud_id, d_T_out, 0, nf, weighted ? 1u : prm->n_per_cell, cl.dust_w.p,
                                     cl.e_unit.p, stream)))
             return st;
@@ -1139,7 +1302,7 @@ extern "C" soc_status soc_simulate_frequency_batch_noalloc(soc_ctx *ctx, const s
                 return fail(ctx, SOC_ERR_STATE, "item %d: cloud has no point sources", i);
         } else if (it.source == SOC_SRC_DUST) {
             if (!it.d_dust_w || it.n_per_cell == 0) return fail(ctx, SOC_ERR_ARG, "item %d: dust weights missing", i);
-            if (it.pid_offset + it.n_packages > (uint64_t)cl.n_leaf * it.n_per_cell)
+            if (!(it.reserved & SOC_ITEM_WEIGHTED) && it.pid_offset + it.n_packages > (uint64_t)cl.n_leaf * it.n_per_cell)
                 return fail(ctx, SOC_ERR_ARG, "item %d: more dust packages than n_leaf*n_per_cell", i);
         } else {
             return fail(ctx, SOC_ERR_ARG, "item %d: unknown source %d", i, it.source);

@@ -101,6 +101,14 @@ cudaError_t launch_dust_weighted(int64_t n_leaf, int n_freq, const uint64_t *u, 
                                  cudaStream_t s);
 cudaError_t launch_dust_reweight(int64_t n_leaf, int n_freq, const uint64_t *u, const double *e_uni, uint64_t *out,
                                  double *e_unit, unsigned long long *scratch, cudaStream_t s);
+cudaError_t launch_dust_luminosity(const DevCloud *dcl, int64_t n_leaf, const TempTables &tt, const float *T,
+                                   int freq_lo, int n_freq, double *L, cudaStream_t s);
+cudaError_t launch_reference_delta(int64_t n_leaf, int n_freq, const double *L, double *L_ref, double w, uint64_t *u,
+                                   uint8_t *neg, double *e_uni, unsigned long long *scratch, cudaStream_t s);
+cudaError_t launch_dust_split(int64_t n_leaf, int n_freq, const uint8_t *neg, uint64_t *alloc, uint64_t *alloc_neg,
+                              const double *e, double *e_neg, cudaStream_t s);
+cudaError_t launch_reference_update(int64_t n, double *A_ref, const double *A_d, double w, const double *A_const,
+                                    double *A_out, int out_mean, cudaStream_t s);
 cudaError_t launch_update_temperature_ali(const DevCloud *dcl, int64_t n_cells, const TempTables &tt,
                                           const double *A, const double *A_self, float *T, double *max_dT,
                                           cudaStream_t s);

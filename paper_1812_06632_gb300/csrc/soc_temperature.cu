@@ -340,33 +340,14 @@ __global__ void wprefix_kernel(int64_t n_leaf, int n_freq, unsigned long long *o
 __global__ void wqmax_kernel(const unsigned long long *u, int64_t n_leaf, const unsigned long long *out,
                              unsigned long long *qmax)
 {
-    __shared__ unsigned long long smax[32];
     const int f = blockIdx.y;
     const unsigned long long *pre = out + (int64_t)f * (2 * n_leaf + 1) + n_leaf;
-    unsigned long long m = 0;
+    double m = 0.0;
     for (int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; li < n_leaf; li += (int64_t)gridDim.x * blockDim.x) {
         const unsigned long long n = pre[li + 1] - pre[li];
-        if (n) {
-            const double q = __ddiv_rn((double)u[(int64_t)f * n_leaf + li], (double)n);
-            const unsigned long long b = (unsigned long long)__double_as_longlong(q);
-            m = b > m ? b : m;
-        }
+        if (n) m = fmax(m, __ddiv_rn((double)u[(int64_t)f * n_leaf + li], (double)n));
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
-        m = t > m ? t : m;
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) smax[warp] = m;
-    __syncthreads();
-    if (warp == 0) {
-        m = lane < (int)((blockDim.x + 31) >> 5) ? smax[lane] : 0ull;
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
-            m = t > m ? t : m;
-        }
-        if (lane == 0 && m) atomicMax(qmax + f, m);
-    }
+    block_max_to(m, qmax + f);
 }
 
 // W = rint((u / n) / E_ref 2^32) with E_ref = qmax (0 where n = 0);
@@ -388,6 +369,86 @@ __global__ void wreweight_kernel(const unsigned long long *u, int64_t n_leaf, co
             w = (unsigned long long)rint(__dmul_rn(__ddiv_rn(q, E_ref), 4294967296.0));
         }
         W[li] = w;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reference field (paper Sect. 2.1.2, Sects. 3.4 and 3.6).  Arrays over
+// (frequency, leaf) are frequency-major: [n_freq][n_leaf].
+// ---------------------------------------------------------------------------
+__global__ void dust_lum_kernel(const DevCloud *__restrict__ dcl, int64_t n_leaf, const TempTables tt,
+                                const float *__restrict__ T, int freq_lo, int n_freq, double *L)
+{
+    const DevCloud &C = *dcl;
+    const int fi = blockIdx.y;
+    for (int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; li < n_leaf; li += (int64_t)gridDim.x * blockDim.x)
+        L[(int64_t)fi * n_leaf + li] = dust_L(C, tt, T, __ldg(C.leaf + li), freq_lo + fi);
+}
+
+// m[f] = max over leaves of |L - L_ref|
+__global__ void refdelta_max_kernel(const double *__restrict__ L, const double *__restrict__ L_ref, int64_t n_leaf,
+                                    unsigned long long *m)
+{
+    const int f = blockIdx.y;
+    double v = 0.0;
+    for (int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; li < n_leaf; li += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = (int64_t)f * n_leaf + li;
+        v = fmax(v, fabs(__dsub_rn(L[k], L_ref[k])));
+    }
+    block_max_to(v, m + f);
+}
+
+// d = L - L_ref;  u = rint(|d| / m 2^32);  neg = d < 0;  L_ref += w d;
+// e_uni = m / 2^32.
+__global__ void refdelta_kernel(const double *__restrict__ L, double *L_ref, int64_t n_leaf, double w,
+                                const unsigned long long *__restrict__ m_bits, unsigned long long *u, uint8_t *neg,
+                                double *e_uni)
+{
+    const int f = blockIdx.y;
+    const double m = __longlong_as_double((long long)m_bits[f]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) e_uni[f] = __ddiv_rn(m, 4294967296.0);
+    for (int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; li < n_leaf; li += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = (int64_t)f * n_leaf + li;
+        const double lr = L_ref[k];
+        const double d = __dsub_rn(L[k], lr);
+        u[k] = m > 0.0 ? (unsigned long long)rint(__dmul_rn(__ddiv_rn(fabs(d), m), 4294967296.0)) : 0ull;
+        neg[k] = d < 0.0;
+        L_ref[k] = __dadd_rn(lr, __dmul_rn(w, d));
+    }
+}
+
+// Split an allocation [W | prefix] by the sign of the emission change: the
+// input keeps the weights of rising cells, `neg_out` gets those of falling
+// cells and a copy of the prefix; e_neg = -e.
+__global__ void dsplit_kernel(const uint8_t *__restrict__ neg, unsigned long long *alloc, unsigned long long *neg_out,
+                              int64_t n_leaf, const double *__restrict__ e, double *e_neg)
+{
+    const int f = blockIdx.y;
+    const int64_t row = (int64_t)f * (2 * n_leaf + 1);
+    if (blockIdx.x == 0 && threadIdx.x == 0) e_neg[f] = -e[f];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * n_leaf + 1; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long v = alloc[row + i];
+        if (i < n_leaf) {
+            const bool is_neg = neg[(int64_t)f * n_leaf + i] != 0;
+            neg_out[row + i] = is_neg ? v : 0ull;
+            if (is_neg) alloc[row + i] = 0ull;
+        } else {
+            neg_out[row + i] = v;
+        }
+    }
+}
+
+// A_ref += w (A_d - A_ref);  A_out = A_const + (out_mean ? new A_ref : A_d)
+// (A_const may be null).
+__global__ void refupdate_kernel(int64_t n, double *A_ref, const double *__restrict__ A_d, double w,
+                                 const double *__restrict__ A_const, double *A_out, int out_mean)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const double ar = A_ref[c], ad = A_d[c];
+        const double an = __dadd_rn(ar, __dmul_rn(w, __dsub_rn(ad, ar)));
+        A_ref[c] = an;
+        const double v = out_mean ? an : ad;
+        if (A_out) A_out[c] = A_const ? __dadd_rn(A_const[c], v) : v;
     }
 }
 
@@ -459,6 +520,46 @@ cudaError_t launch_dust_reweight(int64_t n_leaf, int n_freq, const uint64_t *u, 
     wqmax_kernel<<<g, 256, 0, s>>>(uu, n_leaf, oo, scratch);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     wreweight_kernel<<<g, 256, 0, s>>>(uu, n_leaf, scratch, e_uni, oo, e_unit);
+    return cudaGetLastError();
+}
+
+static dim3 leaf_grid(int64_t n, int n_freq)
+{
+    return dim3((unsigned)std::min<int64_t>((n + 255) / 256, 1024), (unsigned)n_freq);
+}
+
+cudaError_t launch_dust_luminosity(const DevCloud *dcl, int64_t n_leaf, const TempTables &tt, const float *T,
+                                   int freq_lo, int n_freq, double *L, cudaStream_t s)
+{
+    dust_lum_kernel<<<leaf_grid(n_leaf, n_freq), 256, 0, s>>>(dcl, n_leaf, tt, T, freq_lo, n_freq, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reference_delta(int64_t n_leaf, int n_freq, const double *L, double *L_ref, double w, uint64_t *u,
+                                   uint8_t *neg, double *e_uni, unsigned long long *scratch, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * n_freq, s);
+    if (e != cudaSuccess) return e;
+    refdelta_max_kernel<<<leaf_grid(n_leaf, n_freq), 256, 0, s>>>(L, L_ref, n_leaf, scratch);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    refdelta_kernel<<<leaf_grid(n_leaf, n_freq), 256, 0, s>>>(L, L_ref, n_leaf, w, scratch,
+                                                              reinterpret_cast<unsigned long long *>(u), neg, e_uni);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dust_split(int64_t n_leaf, int n_freq, const uint8_t *neg, uint64_t *alloc, uint64_t *alloc_neg,
+                              const double *e, double *e_neg, cudaStream_t s)
+{
+    dsplit_kernel<<<leaf_grid(2 * n_leaf + 1, n_freq), 256, 0, s>>>(
+        neg, reinterpret_cast<unsigned long long *>(alloc), reinterpret_cast<unsigned long long *>(alloc_neg), n_leaf,
+        e, e_neg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reference_update(int64_t n, double *A_ref, const double *A_d, double w, const double *A_const,
+                                    double *A_out, int out_mean, cudaStream_t s)
+{
+    refupdate_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, A_ref, A_d, w, A_const, A_out, out_mean);
     return cudaGetLastError();
 }
 

@@ -22,7 +22,8 @@ W_UNIT = 1 << 32
 
 EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "soc_grid_validate", "soc_grid_free",
            "soc_dust_upload", "soc_simulate_frequency_batch_ex", "soc_update_temperature_ali", "soc_map",
-           "soc_dust_weighted", "soc_dust_reweight",
+           "soc_dust_weighted", "soc_dust_reweight", "soc_dust_luminosity", "soc_reference_delta",
+           "soc_dust_split", "soc_reference_update",
            "soc_sources_upload", "soc_simulate_frequency_batch", "soc_package_energy",
            "soc_dust_emission", "soc_absorbed_power", "soc_update_temperature", "soc_iterate",
            "soc_set_launch", "soc_set_refill", "soc_set_scatter_batch", "soc_set_max_steps",
@@ -50,7 +51,7 @@ class IterateParams(C.Structure):
     _fields_ = [("n_background", C.c_uint64), ("n_point", C.c_uint64), ("n_per_cell", C.c_uint32),
                 ("max_iter", C.c_int32), ("dT_tol", C.c_double), ("reuse_constant", C.c_int32),
                 ("ali", C.c_int32), ("n_weighted", C.c_uint64), ("weighted_cap", C.c_uint32),
-                ("reserved", C.c_int32)]
+                ("reference_field", C.c_int32), ("n_dust_first", C.c_uint64), ("n_dust_last", C.c_uint64)]
 
 
 class IterateResult(C.Structure):
@@ -84,6 +85,10 @@ def _load():
         "soc_map": ([P, I, P, I, P, P, I, I, C.c_double, P, C.c_double, P, P], I),
         "soc_dust_weighted": ([P, I, P, P, I, C.c_uint64, C.c_uint32, P, P, P], I),
         "soc_dust_reweight": ([P, I, P, P, I, P, P, P], I),
+        "soc_dust_luminosity": ([P, I, P, I, I, P, P], I),
+        "soc_reference_delta": ([P, I, I, P, P, C.c_double, P, P, P, P], I),
+        "soc_dust_split": ([P, I, I, P, P, P, P, P, P], I),
+        "soc_reference_update": ([P, I, P, P, C.c_double, P, P, I, P], I),
         "soc_package_energy": ([P, I, I, U64, P], I),
         "soc_dust_emission": ([P, I, P, I, I, C.c_uint32, P, P, P], I),
         "soc_absorbed_power": ([P, I, P, C.c_int64, P, P, P, P], I),
@@ -329,6 +334,24 @@ class Context:
         self._check(lib.soc_dust_reweight(self.h, cloud_id, _t_ptr(u), _t_ptr(e_unit_uniform), u.shape[0],
                                           _t_ptr(inout), _t_ptr(e_unit), _stream(stream)))
 
+    def dust_luminosity(self, cloud_id, T, L, freq_lo=0, stream=None):
+        """soc_dust_luminosity: L (float64 [n_freq][n_leaf]) from T."""
+        self._check(lib.soc_dust_luminosity(self.h, cloud_id, _t_ptr(T), freq_lo, L.shape[0], _t_ptr(L),
+                                            _stream(stream)))
+
+    def reference_delta(self, cloud_id, L, L_ref, w, u, neg, e_unit_uniform, stream=None):
+        """soc_reference_delta: u (int64 view of uint64), neg (uint8), e; L_ref updated."""
+        self._check(lib.soc_reference_delta(self.h, cloud_id, L.shape[0], _t_ptr(L), _t_ptr(L_ref), float(w),
+                                            _t_ptr(u), _t_ptr(neg), _t_ptr(e_unit_uniform), _stream(stream)))
+
+    def dust_split(self, cloud_id, neg, alloc, alloc_neg, e_unit, e_unit_neg, stream=None):
+        self._check(lib.soc_dust_split(self.h, cloud_id, alloc.shape[0], _t_ptr(neg), _t_ptr(alloc),
+                                       _t_ptr(alloc_neg), _t_ptr(e_unit), _t_ptr(e_unit_neg), _stream(stream)))
+
+    def reference_update(self, cloud_id, A_ref, A_d, w, A_const=None, A_out=None, out_mean=False, stream=None):
+        self._check(lib.soc_reference_update(self.h, cloud_id, _t_ptr(A_ref), _t_ptr(A_d), float(w),
+                                             _t_ptr(A_const), _t_ptr(A_out), int(out_mean), _stream(stream)))
+
     def absorbed_power(self, cloud_id, tally, stride, e_unit, A_out, A_in=None, stream=None):
         self._check(lib.soc_absorbed_power(self.h, cloud_id, _t_ptr(tally), stride, _t_ptr(e_unit),
                                            _t_ptr(A_in), _t_ptr(A_out), _stream(stream)))
@@ -351,9 +374,10 @@ class Context:
 
     def iterate(self, cloud_id, T_out, *, n_background=0, n_point=0, n_per_cell=1, max_iter=0,
                 dT_tol=0.1, T_seed=None, reuse_constant=False, ali=False, n_weighted=0, weighted_cap=10000,
-                stream=None):
+                reference_field=False, n_dust_first=0, n_dust_last=0, stream=None):
+        modes = {False: 0, True: 1, 0: 0, 1: 1, 2: 2, "mean": 1, "difference": 2}
         p = IterateParams(n_background, n_point, n_per_cell, max_iter, dT_tol, int(reuse_constant), int(ali),
-                          n_weighted, weighted_cap, 0)
+                          n_weighted, weighted_cap, modes[reference_field], n_dust_first, n_dust_last)
         r = IterateResult()
         hist = np.zeros(max(max_iter, 1), np.float64)
         self._check(lib.soc_iterate(self.h, cloud_id, C.byref(p), _t_ptr(T_seed), _t_ptr(T_out), C.byref(r),

@@ -20,7 +20,7 @@ def kappa_root(dust, f, ell):
             np.float32(np.float64(dust.ksca[f]) * np.float64(ell)))
 
 
-def oracle_item(w, ci, spec, dust_w=None):
+def oracle_item(w, ci, spec, dust_w=None, dust_prefix=None):
     """Run one batch item on the oracle; returns (tally, stats, steps)."""
     cl = w.clouds[ci]
     f = spec.get("freq", 0)
@@ -36,6 +36,8 @@ def oracle_item(w, ci, spec, dust_w=None):
         kw["leaf"] = cl.leaves()
         kw["dust_w"] = dust_w
         kw["n_per_cell"] = spec.get("n_per_cell", 1)
+        if dust_prefix is not None:
+            kw["dust_prefix"] = dust_prefix
     return oracle.trace(oracle_grid(cl), **kw)
 
 
