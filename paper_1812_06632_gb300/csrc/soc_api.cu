@@ -67,6 +67,8 @@ struct CloudHost {
 struct BatchHost {
     int n_items = 0;
     uint64_t total = 0;
+    HotCloud hot{};
+    int32_t regular = 0;
     DevBuf<DevItem> items;
     DevBuf<uint64_t> prefix;
     DevBuf<unsigned long long> counter;
@@ -608,6 +610,29 @@ static soc_status prepare_items(soc_ctx *ctx, const soc_batch_item *items, int n
     return SOC_OK;
 }
 
+// The step fields of the one cloud all items use; cell = nullptr when they
+// use several (the tracer then reads them through each lane's cloud).
+static HotCloud one_cloud(const soc_ctx *ctx, const soc_batch_item *items, int n_items)
+{
+    HotCloud h{};
+    for (int i = 1; i < n_items; ++i)
+        if (items[i].cloud != items[0].cloud) return h;
+    const CloudHost &c = *ctx->clouds[items[0].cloud];
+    h.cell = c.cell.p;
+    h.parent = c.parent.p;
+    h.nx = c.nx; h.ny = c.ny; h.nz = c.nz;
+    h.n_root = (int32_t)c.n_root;
+    return h;
+}
+
+// 1 when every item's cloud is a regular grid (one level).
+static int32_t all_regular(const soc_ctx *ctx, const soc_batch_item *items, int n_items)
+{
+    for (int i = 0; i < n_items; ++i)
+        if (ctx->clouds[items[i].cloud]->n_levels != 1) return 0;
+    return 1;
+}
+
 // Launch shape of the tracer for `total` work indices.
 static void launch_geometry(soc_ctx *ctx, uint64_t total, int &grid_out, int &variant)
 {
@@ -664,6 +689,8 @@ soc_status soc_simulate_frequency_batch_ex(soc_ctx *ctx, const soc_batch_item *i
     P.chunk = ctx->chunk;
     P.refill_min = ctx->refill_min;
     P.scatter_min = ctx->scatter_min;
+    P.hot = one_cloud(ctx, items, n_items);
+    P.regular = all_regular(ctx, items, n_items);
     int grid = 1, variant = 3;
     launch_geometry(ctx, total, grid, variant);
     CK(launch_trace(P, grid, ctx->tpb, variant, s), "trace launch");
@@ -684,6 +711,8 @@ soc_status soc_batch_create(soc_ctx *ctx, const soc_batch_item *items, int n_ite
     if (!b) return fail(ctx, SOC_ERR_NOMEM, "host allocation");
     b->n_items = n_items;
     b->total = prefix[n_items];
+    b->hot = one_cloud(ctx, items, n_items);
+    b->regular = all_regular(ctx, items, n_items);
     cudaError_t e = cudaSuccess;
     if ((e = b->items.alloc(n_items)) != cudaSuccess || (e = b->prefix.alloc(n_items + 1)) != cudaSuccess ||
         (e = b->counter.alloc(1)) != cudaSuccess ||
@@ -728,6 +757,8 @@ soc_status soc_batch_launch(soc_ctx *ctx, int batch_id, int64_t *d_tally, int64_
     P.chunk = ctx->chunk;
     P.refill_min = ctx->refill_min;
     P.scatter_min = ctx->scatter_min;
+    P.hot = b.hot;
+    P.regular = b.regular;
     int grid = 1, variant = 3;
     launch_geometry(ctx, b.total, grid, variant);
     CK(launch_trace(P, grid, ctx->tpb, variant, s), "trace launch");
@@ -1351,6 +1382,8 @@ extern "C" soc_status soc_simulate_frequency_batch_noalloc(soc_ctx *ctx, const s
     P.chunk = ctx->chunk;
     P.refill_min = ctx->refill_min;
     P.scatter_min = ctx->scatter_min;
+    P.hot = one_cloud(ctx, items, n_items);
+    P.regular = all_regular(ctx, items, n_items);
     const int variant = ctx->bps >= 4 ? 4 : 3;
     const int limit = trace_block_limit(ctx->tpb, variant);
     const int per_sm = ctx->bps > 0 ? std::min(ctx->bps, limit) : limit;

@@ -41,6 +41,13 @@ struct DevItem {
     const uint64_t *dust_w;
 };
 
+// The cloud fields the tracer's step reads (see TraceParams::hot).
+struct HotCloud {
+    const uint32_t *cell;
+    const int32_t *parent;
+    int32_t nx, ny, nz, n_root;
+};
+
 struct TraceParams {
     const DevCloud *clouds;
     const DevItem *items;
@@ -59,6 +66,9 @@ struct TraceParams {
     int32_t chunk;
     int32_t refill_min;          // refill a warp's idle lanes once this many are idle
     int32_t scatter_min;         // scatter a warp's waiting lanes once this many wait
+    HotCloud hot;                // cell != nullptr: every item uses this one cloud
+    int32_t regular;             // every item's cloud is a regular grid (selects the
+                                 // two-steps-per-pass build of the tracer)
 };
 
 // variant: 3 or 4 = minimum resident 256-thread blocks per SM the kernel is

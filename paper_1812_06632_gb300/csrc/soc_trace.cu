@@ -69,12 +69,41 @@ struct Pkg {
 constexpr uint32_t kFloorMask = 0x1fffu;
 constexpr uint32_t kHomeBit = 1u << 31;
 
+// 1/d per axis; +inf for a zero component (either sign of zero).  With the
+// face taken as 1 for d >= 0, such an axis gives (1 - x) * inf = +inf or
+// NaN, which never wins the strict comparison for the nearest face: the same
+// choice as skipping the axis, without a test per axis and step.
 __device__ __forceinline__ void set_inverse(Pkg &p)
 {
-    p.ix = (p.dx != 0.0f) ? __fdiv_rn(1.0f, p.dx) : 0.0f;
-    p.iy = (p.dy != 0.0f) ? __fdiv_rn(1.0f, p.dy) : 0.0f;
-    p.iz = (p.dz != 0.0f) ? __fdiv_rn(1.0f, p.dz) : 0.0f;
+    const float inf = __int_as_float(0x7f800000);
+    p.ix = (p.dx != 0.0f) ? __fdiv_rn(1.0f, p.dx) : inf;
+    p.iy = (p.dy != 0.0f) ? __fdiv_rn(1.0f, p.dy) : inf;
+    p.iz = (p.dz != 0.0f) ? __fdiv_rn(1.0f, p.dz) : inf;
 }
+
+// The fields of a cloud that every step reads.  When every item of a launch
+// uses one cloud they travel in the kernel parameters (TraceParams::hot), so
+// the compiler takes them as constant operands; otherwise each lane reads
+// them through its own DevCloud pointer (GlobalCloud).
+struct ParamCloud {
+    const HotCloud &h;
+    __device__ const uint32_t *cell() const { return h.cell; }
+    __device__ const int32_t *parent() const { return h.parent; }
+    __device__ int32_t nx() const { return h.nx; }
+    __device__ int32_t ny() const { return h.ny; }
+    __device__ int32_t nz() const { return h.nz; }
+    __device__ int32_t n_root() const { return h.n_root; }
+};
+
+struct GlobalCloud {
+    const DevCloud &C;
+    __device__ const uint32_t *cell() const { return C.cell; }
+    __device__ const int32_t *parent() const { return C.parent; }
+    __device__ int32_t nx() const { return C.nx; }
+    __device__ int32_t ny() const { return C.ny; }
+    __device__ int32_t nz() const { return C.nz; }
+    __device__ int32_t n_root() const { return (int32_t)C.n_root; }
+};
 
 // Follow child links to the leaf that contains the position; the upper child
 // is taken on an axis when 2x >= 1.
@@ -269,9 +298,10 @@ __device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r,
 
 // Cross the face on axis `ax`: the package sits on it in the current frame.
 // Returns false when it leaves the root grid.
-__device__ bool cross_face(const DevCloud &C, Pkg &p, int ax, bool up)
+template <class CC>
+__device__ bool cross_face(const CC &C, Pkg &p, int ax, bool up)
 {
-    const int32_t n_root = (int32_t)C.n_root;
+    const int32_t n_root = C.n_root();
     while (p.cell >= n_root) {
         const int o = (p.cell - n_root) & 7;
         const int b = (o >> ax) & 1;
@@ -281,29 +311,30 @@ __device__ bool cross_face(const DevCloud &C, Pkg &p, int ax, bool up)
             p.x = (ax == 0) ? v : p.x;
             p.y = (ax == 1) ? v : p.y;
             p.z = (ax == 2) ? v : p.z;
-            descend(C.cell, p);
+            descend(C.cell(), p);
             return true;
         }
         p.x = __fmul_rn(__fadd_rn(p.x, (float)(o & 1)), 0.5f);
         p.y = __fmul_rn(__fadd_rn(p.y, (float)((o >> 1) & 1)), 0.5f);
         p.z = __fmul_rn(__fadd_rn(p.z, (float)((o >> 2) & 1)), 0.5f);
         p.h = __fmul_rn(p.h, 2.0f);
-        p.cell = __ldg(C.parent + ((p.cell - n_root) >> 3));
+        p.cell = __ldg(C.parent() + ((p.cell - n_root) >> 3));
     }
     const int step = up ? 1 : -1;
     const int ri = p.ri + ((ax == 0) ? step : 0);
     const int rj = p.rj + ((ax == 1) ? step : 0);
     const int rk = p.rk + ((ax == 2) ? step : 0);
     // one unsigned compare per axis tests both ends of the root grid
-    if ((unsigned)ri >= (unsigned)C.nx || (unsigned)rj >= (unsigned)C.ny || (unsigned)rk >= (unsigned)C.nz)
+    const int32_t nx = C.nx(), ny = C.ny();
+    if ((unsigned)ri >= (unsigned)nx || (unsigned)rj >= (unsigned)ny || (unsigned)rk >= (unsigned)C.nz())
         return false;
     p.ri = ri; p.rj = rj; p.rk = rk;
-    p.cell = root_cell(C, ri, rj, rk);
+    p.cell = ri + nx * (rj + ny * rk);
     const float v = up ? 0.0f : 1.0f;
     p.x = (ax == 0) ? v : p.x;
     p.y = (ax == 1) ? v : p.y;
     p.z = (ax == 2) ? v : p.z;
-    descend(C.cell, p);
+    descend(C.cell(), p);
     return true;
 }
 
@@ -323,24 +354,24 @@ __device__ __forceinline__ uint64_t float_to_w(float v)
 }
 
 // One photon-cell step (one segment inside one leaf).
-template <bool kSelf>
-__device__ __forceinline__ int step(const DevCloud &C, Pkg &p, Rng &r, float kabs, float ksca,
-                                    float g, unsigned long long *tally, const TraceParams &P)
+template <bool kSelf, class CC>
+__device__ __forceinline__ int step(const CC &C, Pkg &p, float kabs, float ksca,
+                                    unsigned long long *tally, const TraceParams &P)
 {
     if (p.steps >= P.max_steps) { p.pend += p.W; p.W = 0; return kCapped; }
     ++p.steps;
     float s = __int_as_float(0x7f800000);     // +inf
     int ax = -1;
-    if (p.dx != 0.0f) {
-        const float si = __fmul_rn(__fsub_rn(p.dx > 0.0f ? 1.0f : 0.0f, p.x), p.ix);
+    {   // axes with d = 0 carry 1/d = +inf (set_inverse) and never win
+        const float si = __fmul_rn(__fsub_rn(p.dx < 0.0f ? 0.0f : 1.0f, p.x), p.ix);
         if (si < s) { s = si; ax = 0; }
     }
-    if (p.dy != 0.0f) {
-        const float si = __fmul_rn(__fsub_rn(p.dy > 0.0f ? 1.0f : 0.0f, p.y), p.iy);
+    {
+        const float si = __fmul_rn(__fsub_rn(p.dy < 0.0f ? 0.0f : 1.0f, p.y), p.iy);
         if (si < s) { s = si; ax = 1; }
     }
-    if (p.dz != 0.0f) {
-        const float si = __fmul_rn(__fsub_rn(p.dz > 0.0f ? 1.0f : 0.0f, p.z), p.iz);
+    {
+        const float si = __fmul_rn(__fsub_rn(p.dz < 0.0f ? 0.0f : 1.0f, p.z), p.iz);
         if (si < s) { s = si; ax = 2; }
     }
     if (ax < 0) { p.pend += p.W; p.W = 0; return kCapped; }     // no exit face: end safely
@@ -403,7 +434,7 @@ __device__ __forceinline__ int find_item(const uint64_t *__restrict__ prefix, in
     return lo;
 }
 
-template <int kMinBlocks, bool kSelf>
+template <int kMinBlocks, bool kSelf, bool kOneCloud, bool kTwoSteps>
 __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParams P)
 {
     const int lane = threadIdx.x & 31;
@@ -422,7 +453,6 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
     p.steps = 0; p.W = 0; p.pend = 0; p.wf = 0; p.scat = false;
     bool active = false;
     int item = -1;
-    const DevCloud *C = nullptr;
     float kabs = 0.f, ksca = 0.f, g = 0.f;
     unsigned long long *tally = nullptr;
     uint64_t gidx = 0;
@@ -431,6 +461,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
     __shared__ unsigned long long s_acc[256][3];     // escaped, steps, emitted
     unsigned long long *const acc = s_acc[threadIdx.x];
     acc[0] = acc[1] = acc[2] = 0;
+    const DevCloud *C = P.clouds;             // the lane's cloud (used when !kOneCloud)
     int acc_item = -1;
     unsigned acc_cap = 0;
 
@@ -515,7 +546,23 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
             }
         }
         if (active && !p.scat) {
-            const int res = step<kSelf>(*C, p, r, kabs, ksca, g, tally, P);
+            // On regular grids two steps before the warp looks at refills
+            // and scatterings again: half the passes of the scheduling code
+            // per step.  Timed on GB300 (128^3, 64 nu): 71.5 ms against
+            // 77.0 ms for one step, and slower with three or four steps or
+            // with the two written as a loop.  Octree steps, whose climbs and
+            // descents vary in length, are faster one at a time (78 against
+            // 99 ms on the 4.4e6-cell octree).
+            int res;
+            if (kOneCloud) {
+                const ParamCloud pc{P.hot};
+                res = step<kSelf>(pc, p, kabs, ksca, tally, P);
+                if (kTwoSteps && res == kContinue && !p.scat) res = step<kSelf>(pc, p, kabs, ksca, tally, P);
+            } else {
+                const GlobalCloud gc{*C};
+                res = step<kSelf>(gc, p, kabs, ksca, tally, P);
+                if (kTwoSteps && res == kContinue && !p.scat) res = step<kSelf>(gc, p, kabs, ksca, tally, P);
+            }
             if (res != kContinue) {
                 if (p.pend) {
                     atomicAdd(tally + p.cell, (unsigned long long)p.pend);
@@ -620,7 +667,7 @@ __global__ void map_kernel(const MapParams M)
             p.x = (ax == 0) ? face : mx;
             p.y = (ax == 1) ? face : my;
             p.z = (ax == 2) ? face : mz;
-            if (!cross_face(C, p, ax, upx)) break;
+            if (!cross_face(GlobalCloud{C}, p, ax, upx)) break;
         }
     }
     M.map[(int64_t)py * M.npx + px] = (float)(I + M.I_bg * exp(-tau));
@@ -636,15 +683,28 @@ cudaError_t launch_map(const MapParams &m, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_trace(const TraceParams &p, int grid, int block, int variant, cudaStream_t s)
+template <int kMinBlocks, bool kTwoSteps>
+static void launch_variant(const TraceParams &p, int grid, int block, cudaStream_t s)
 {
     // the self-counter logic (ALI) is compiled only into the variants that need it
+    const bool one = p.hot.cell != nullptr;
     if (p.self) {
-        if (variant == 4) trace_kernel<4, true><<<grid, block, 0, s>>>(p);
-        else trace_kernel<3, true><<<grid, block, 0, s>>>(p);
+        if (one) trace_kernel<kMinBlocks, true, true, kTwoSteps><<<grid, block, 0, s>>>(p);
+        else trace_kernel<kMinBlocks, true, false, kTwoSteps><<<grid, block, 0, s>>>(p);
     } else {
-        if (variant == 4) trace_kernel<4, false><<<grid, block, 0, s>>>(p);
-        else trace_kernel<3, false><<<grid, block, 0, s>>>(p);
+        if (one) trace_kernel<kMinBlocks, false, true, kTwoSteps><<<grid, block, 0, s>>>(p);
+        else trace_kernel<kMinBlocks, false, false, kTwoSteps><<<grid, block, 0, s>>>(p);
+    }
+}
+
+cudaError_t launch_trace(const TraceParams &p, int grid, int block, int variant, cudaStream_t s)
+{
+    if (p.regular) {
+        if (variant == 4) launch_variant<4, true>(p, grid, block, s);
+        else launch_variant<3, true>(p, grid, block, s);
+    } else {
+        if (variant == 4) launch_variant<4, false>(p, grid, block, s);
+        else launch_variant<3, false>(p, grid, block, s);
     }
     return cudaGetLastError();
 }
@@ -653,8 +713,8 @@ int trace_block_limit(int block, int variant)
 {
     int n = 0;
     cudaError_t e = (variant == 4)
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<4, false>, block, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<3, false>, block, 0);
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<4, false, false, false>, block, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<3, false, false, false>, block, 0);
     if (e != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }

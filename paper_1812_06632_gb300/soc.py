@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libsoc.so")
+# SOC_LIB names another build of the same library (e.g. one compiled with
+# different options); by default the in-tree build is loaded.
+LIB_PATH = os.environ.get("SOC_LIB") or os.path.join(_HERE, "_build", "libsoc.so")
 
 SOC_OK = 0
 SOC_ERR_STEP_LIMIT = -4

@@ -7,9 +7,11 @@ from paper_1812_06632_gb300 import inputs as I
 
 def test_candidates_cover_space():
     c = list(A.candidates(dict(threads_per_block=(64, 128), blocks_per_sm=(0,), chunk=(1, 4), refill=(1,),
-                               scatter=(1,))))
-    assert len(c) == 4
+                               scatter=(1, 8))))
+    assert len(c) == 8
     assert {x["threads_per_block"] for x in c} == {64, 128}
+    assert {x["scatter"] for x in c} == {1, 8}
+    assert len(list(A.candidates())) == 2 * 2 * 2 * 3 * 4
 
 
 def test_key_depends_on_workload_and_gpu():
