@@ -474,11 +474,21 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *par
                        double *dT_history, void *stream);
 
 /* ------------------------------------------------------------------------
+ * soc_nn_error_flag -- 1 if a tensor-core convolution block gave up waiting
+ * for its matrix multiplies (each wait is bounded; the block then frees its
+ * tensor memory and returns without writing its outputs), else 0; the flag
+ * of the current device is cleared.  Synchronous with the device.
+ * ------------------------------------------------------------------------ */
+soc_status soc_nn_error_flag(int *flag);
+
+/* ------------------------------------------------------------------------
  * Learned temperature seed (not a step of the paper's method: a 3D U-Net that
  * maps the first, noisy temperature field and the log density to the
  * converged temperature and seeds soc_iterate; the Monte Carlo iterations
  * remain its judge).  Channels-last (N, side, side, side, C) tensors; BF16
- * activations and weights on tensor cores with FP32 accumulation; FP32
+ * activations and weights on tensor cores with FP32 accumulation (the
+ * convolutions and their input gradients on tcgen05 with the accumulator in
+ * tensor memory, the weight gradients on mma.sync); FP32
  * master weights, gradients and Adam moments.  Architecture: 4 levels with
  * 16-32-64-128 channels, two 3x3x3 convolutions (ReLU) per level, 2x2x2 max
  * pooling, nearest 2x upsampling, skip concatenation [upsampled, skip], a

@@ -8,13 +8,14 @@
 // moments.
 //
 // Convolutions (3x3x3, stride 1, zero padding 1) are implicit GEMMs:
-//   forward:  M = voxels, N = C_out, K = 27 C_in (tap-major, channel-minor);
+//   forward:  M = voxels, N = C_out, K = 27 C_in (tap-major, channel-minor),
+//             on the tcgen05 tensor cores with the accumulator in tensor
+//             memory;
 //   dgrad:    the forward kernel with the weights flipped in space and
 //             transposed in channels;
 //   wgrad:    M = C_out, N = C_in per tap, K = voxels (split over blocks,
-//             FP32 atomics).
-// Tiles are staged in shared memory and multiplied with
-// mma.sync.m16n8k16 (BF16 inputs, FP32 accumulators).
+//             FP32 atomics), tiles multiplied with mma.sync.m16n8k16.
+// BF16 inputs, FP32 accumulation throughout.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cmath>
@@ -50,23 +51,99 @@ struct ConvArgs {
     int relu, accumulate;           // accumulate: FP32 output += result
 };
 
-// Forward implicit-GEMM convolution.  Block: 128 threads (4 warps), 64 output
-// voxels x BN output channels; every warp owns 16 voxels.
-template <int BN>
-__global__ void __launch_bounds__(128) conv3d_kernel(const ConvArgs a)
+// ---------------------------------------------------------------------------
+// Forward (and dgrad) convolution on the 5th-generation tensor cores (tcgen05).
+//
+// A block of 128 threads computes 128 output voxels (the 128 lanes of the
+// accumulator in tensor memory) x n_tile output channels (columns).  K runs
+// over the 27 taps and, per tap, chunks of KC input channels; each chunk of
+// A (128 voxels x KC) and B (n_tile channels x KC) is copied to shared
+// memory in the canonical K-major layout without swizzling (8-row x 16-byte
+// core matrices, 128 bytes each: core (g, c) of rows 8g..8g+7 and elements
+// 8c..8c+7 at ((g * KC/8) + c) * 128 bytes, so the leading-dimension offset
+// (next core along K) is 128 B and the stride offset (next 8 rows) KC * 16 B).
+// Two stages alternate: thread 0 issues KC/16 MMAs (M = 128, N = n_tile,
+// K = 16, BF16 x BF16 -> FP32) per chunk and commits them to the stage's
+// mbarrier, which the block waits on before it overwrites that stage.  The
+// epilogue reads the accumulator with tcgen05.ld (warp w reads lanes
+// 32w..32w+31, i.e. its own 32 voxels), adds the bias, applies the ReLU and
+// stores BF16 or (accumulating) FP32.
+// Every wait is bounded: on a timeout the block raises the error flag, frees
+// its tensor memory and returns.
+// ---------------------------------------------------------------------------
+__device__ int g_tc_error;                    // set by a block whose wait timed out
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
-    __shared__ __align__(16) bf16 As[64][24];
-    __shared__ __align__(16) bf16 Bs[BN][24];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = lane >> 2, t2 = (lane & 3) * 2;
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start, leading and stride byte offsets
+// (all >> 4), descriptor version 1, no swizzling.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 and M >> 4.
+__host__ __device__ constexpr uint32_t mma_idesc(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
+{
+    for (uint32_t i = 0; i < (1u << 22); ++i) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(addr), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 16-byte asynchronous copy global -> shared through L1 (the 27 taps of a
+// tile re-read most of its input); src_bytes = 0 writes zeros
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+template <int KC>
+__global__ void __launch_bounds__(128) conv3d_tc_kernel(const ConvArgs a, int n_tile, uint32_t tmem_cols,
+                                                        int n_stages)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    constexpr int kPpr = KC / 8;                      // 16-byte pieces per row of a chunk
+    const int a_bytes = 128 * KC * 2, b_bytes = n_tile * KC * 2;
+    const int stage_bytes = a_bytes + b_bytes;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + n_stages * stage_bytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + n_stages * stage_bytes + 8 * n_stages);
+    const uint32_t smem0 = smem_u32(smem);
+    const int tid = threadIdx.x, warp = tid >> 5;
     const long long V = (long long)a.N * a.D * a.H * a.W;
-    const long long v0 = (long long)blockIdx.x * 64;
-    const int n0 = blockIdx.y * BN;
-    float acc[BN / 8][4];
-#pragma unroll
-    for (int i = 0; i < BN / 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-    const int r = tid >> 1, hh = tid & 1;
-    const long long v = v0 + r;
+    const long long v = (long long)blockIdx.x * 128 + tid;
+    const int n0 = blockIdx.y * n_tile;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(tmem_cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int k = 0; k < n_stages; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[k])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    // this thread's voxel (row of A and of the accumulator)
     const bool vin = v < V;
     int n = 0, z = 0, y = 0, x = 0;
     if (vin) {
@@ -75,56 +152,133 @@ __global__ void __launch_bounds__(128) conv3d_kernel(const ConvArgs a)
         y = (int)(q % a.H); q /= a.H;
         z = (int)(q % a.D); n = (int)(q / a.D);
     }
-    for (int tap = 0; tap < 27; ++tap) {
-        const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
-        const bool ok = vin && zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-        const long long src = ok ? ((((long long)n * a.D + zz) * a.H + yy) * a.W + xx) * a.in_stride + a.in_off : 0;
-        for (int c0 = 0; c0 < a.Cin; c0 += 16) {
-            uint4 av = make_uint4(0u, 0u, 0u, 0u);
-            if (ok) av = *reinterpret_cast<const uint4 *>(a.in + src + c0 + hh * 8);
-            *reinterpret_cast<uint4 *>(&As[r][hh * 8]) = av;
-            if (tid < BN * 2) {
-                const int br = tid >> 1, bh = tid & 1;
-                *reinterpret_cast<uint4 *>(&Bs[br][bh * 8]) = *reinterpret_cast<const uint4 *>(
-                    a.w + ((long long)(n0 + br) * 27 + tap) * a.Cin + c0 + bh * 8);
-            }
-            __syncthreads();
-            uint32_t af[4];
-            const int ar = warp * 16 + g;
-            af[0] = *reinterpret_cast<const uint32_t *>(&As[ar][t2]);
-            af[1] = *reinterpret_cast<const uint32_t *>(&As[ar + 8][t2]);
-            af[2] = *reinterpret_cast<const uint32_t *>(&As[ar][t2 + 8]);
-            af[3] = *reinterpret_cast<const uint32_t *>(&As[ar + 8][t2 + 8]);
+    const uint32_t idesc = mma_idesc(128, n_tile);
+    const int n_chunks = a.Cin / KC;
+    const int total = 27 * n_chunks;
+    const uint32_t r_off = (uint32_t)(((tid >> 3) * kPpr * 8 + (tid & 7)) * 16);   // row tid, core column 0
+
+    // copies of step t into its stage (t % n_stages); one commit group per step
+    auto issue = [&](int t) {
+        if (t < total) {
+            const uint32_t st = smem0 + (uint32_t)((t % n_stages) * stage_bytes);
+            const int tap = t / n_chunks, c0 = (t - tap * n_chunks) * KC;
+            const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
+            const bool ok = vin && zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+            const bf16 *src = a.in + (ok ? ((((long long)n * a.D + zz) * a.H + yy) * a.W + xx) * a.in_stride : 0) +
+                              a.in_off + c0;
 #pragma unroll
-            for (int nt = 0; nt < BN / 8; ++nt) {
-                uint32_t bfr[2];
-                bfr[0] = *reinterpret_cast<const uint32_t *>(&Bs[nt * 8 + g][t2]);
-                bfr[1] = *reinterpret_cast<const uint32_t *>(&Bs[nt * 8 + g][t2 + 8]);
-                mma16816(acc[nt], af, bfr);
+            for (int c = 0; c < kPpr; ++c) cp_async16(st + r_off + c * 128, src + c * 8, ok ? 16u : 0u);
+            for (int i = tid; i < n_tile * kPpr; i += 128) {
+                const int co = i / kPpr, c = i - co * kPpr;
+                cp_async16(st + a_bytes + ((co >> 3) * kPpr * 8 + (co & 7)) * 16 + c * 128,
+                           a.w + ((long long)(n0 + co) * 27 + tap) * a.Cin + c0 + c * 8, 16u);
             }
-            __syncthreads();
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    // a timed-out wait is turned into a block-wide decision (so every thread
+    // passes the same barriers) and ends the main loop
+    // copies run n_stages - 2 steps ahead: at step t every thread waits (on
+    // the stage's mbarrier) for the multiplies of step t - 2, refills that
+    // stage with the copies of step t + n_stages - 2, waits for its own
+    // copies of step t, and one barrier per step hands the stage to the MMA
+    // thread; the multiplies of steps t - 1 and t keep the tensor core busy
+    bool ok_run = true;
+    int last = -1;                                    // last step whose MMAs were committed
+    const int ahead = n_stages - 2;
+    for (int t = 0; t < ahead; ++t) issue(t);
+    for (int step = 0; step < total; ++step) {
+        const int s = step % n_stages;
+        const int nxt = step + ahead;
+        bool waited = true;
+        if (step >= 2 && nxt < total) {
+            const int prev = step - 2;
+            waited = mbar_wait(smem_u32(&mbar[prev % n_stages]), (uint32_t)(prev / n_stages) & 1u);
+        }
+        if (waited) issue(nxt);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        // this step's copies: all but the newest `ahead` groups are complete
+        if (ahead >= 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+        else asm volatile("cp.async.wait_group 1;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (!__syncthreads_and(waited)) { ok_run = false; break; }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem0 + (uint32_t)(s * stage_bytes), b0 = a0 + (uint32_t)a_bytes;
+#pragma unroll
+            for (int j = 0; j < KC / 16; ++j) {
+                const uint64_t ad = smem_desc(a0 + j * 256, 128, kPpr * 128);
+                const uint64_t bd = smem_desc(b0 + j * 256, 128, kPpr * 128);
+                const uint32_t acc = (step > 0 || j > 0) ? 1u : 0u;
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(&mbar[s])) : "memory");
+        }
+        last = step;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // the last commit covers every MMA issued before it
+    {
+        bool done = true;
+        if (last >= 0) done = mbar_wait(smem_u32(&mbar[last % n_stages]), (uint32_t)(last / n_stages) & 1u);
+        ok_run = __syncthreads_and(ok_run && done);
+    }
+    if (!ok_run) {
+        atomicExch(&g_tc_error, 1);
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c = 0; c < n_tile; c += 16) {
+            uint32_t r[16];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                           "=r"(r[14]), "=r"(r[15])
+                         : "r"(row_addr + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (!vin) continue;
+            float val[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                float t = __uint_as_float(r[j]);
+                if (a.bias) t += a.bias[n0 + c + j];
+                if (a.relu) t = fmaxf(t, 0.f);
+                val[j] = t;
+            }
+            const long long o = v * a.out_stride + a.out_off + n0 + c;
+            if (a.out_f32) {
+                float4 *dst = reinterpret_cast<float4 *>(a.out_f32 + o);
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    float4 w4 = make_float4(val[4 * q4], val[4 * q4 + 1], val[4 * q4 + 2], val[4 * q4 + 3]);
+                    if (a.accumulate) {
+                        const float4 old = dst[q4];
+                        w4.x += old.x; w4.y += old.y; w4.z += old.z; w4.w += old.w;
+                    }
+                    dst[q4] = w4;
+                }
+            } else {
+                uint32_t pk[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(val[2 * j], val[2 * j + 1]);
+                    pk[j] = *reinterpret_cast<const uint32_t *>(&h2);
+                }
+                uint4 *dst = reinterpret_cast<uint4 *>(a.out + o);
+                dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
         }
     }
-#pragma unroll
-    for (int nt = 0; nt < BN / 8; ++nt) {
-#pragma unroll
-        for (int hf = 0; hf < 2; ++hf) {
-            const long long vo = v0 + warp * 16 + g + hf * 8;
-            if (vo >= V) continue;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int co = n0 + nt * 8 + t2 + j;
-                float val = acc[nt][hf * 2 + j];
-                if (a.bias) val += a.bias[co];
-                if (a.relu) val = fmaxf(val, 0.f);
-                const long long o = vo * a.out_stride + a.out_off + co;
-                if (a.out_f32) {
-                    a.out_f32[o] = a.accumulate ? a.out_f32[o] + val : val;
-                } else {
-                    a.out[o] = __float2bfloat16_rn(val);
-                }
-            }
-        }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols) : "memory");
     }
 }
 
@@ -409,15 +563,60 @@ inline int grid_1d(long long n, int block = 256)
 
 inline int pick_bn(int C) { return (C % 64 == 0) ? 64 : (C % 32 == 0) ? 32 : 16; }
 
-cudaError_t conv_launch(const ConvArgs &a, cudaStream_t s)
+// Output channels per block of the tensor-core convolution: a multiple of
+// 16 dividing C_out, at most 256, narrowed (down to 16) while the blocks
+// would cover fewer than half the SMs (narrow tiles re-read A, so they only
+// pay on the smallest grids).
+inline int tc_n_tile(int Cout, long long v_tiles, int sms)
+{
+    int t = 256;
+    while (t > 16 && (t > Cout || Cout % t)) t -= 16;
+    while (t > 16 && 2 * v_tiles * (Cout / t) < (long long)sms) {
+        int u = t - 16;
+        while (u > 16 && Cout % u) u -= 16;
+        t = u;
+    }
+    return t;
+}
+
+template <int KC>
+cudaError_t tc_launch(const ConvArgs &a, cudaStream_t s)
 {
     const long long V = (long long)a.N * a.D * a.H * a.W;
-    const int bn = pick_bn(a.Cout);
-    dim3 grid((unsigned)((V + 63) / 64), (unsigned)(a.Cout / bn));
-    if (bn == 64) conv3d_kernel<64><<<grid, 128, 0, s>>>(a);
-    else if (bn == 32) conv3d_kernel<32><<<grid, 128, 0, s>>>(a);
-    else conv3d_kernel<16><<<grid, 128, 0, s>>>(a);
+    const long long v_tiles = (V + 127) / 128;
+    int dev = 0, sms = 148, sm_smem = 0, blk_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&blk_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int n_tile = tc_n_tile(a.Cout, v_tiles, sms);
+    uint32_t cols = 32;
+    while ((int)cols < n_tile) cols <<= 1;
+    // stages of A + B copies: 3 or 4 (copies 1 or 2 steps ahead), within
+    // 72 KB where possible (keeps 3 blocks per SM on the larger tiles)
+    const int stage_bytes = 128 * KC * 2 + n_tile * KC * 2;
+    int stages = 73728 / stage_bytes;
+    stages = stages < 3 ? 3 : (stages > 4 ? 4 : stages);
+    // shared memory padded so that no more blocks are resident on an SM than
+    // its 512 columns of tensor memory can hold
+    const int need = stages * stage_bytes + 8 * stages + 16;
+    const int max_blocks = 512 / (int)cols;
+    const int pad = sm_smem / (max_blocks + 1) + 1024;
+    int bytes = need > pad ? need : pad;
+    if (bytes > blk_max) bytes = blk_max;
+    if (need > blk_max) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(conv3d_tc_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)v_tiles, (unsigned)(a.Cout / n_tile));
+    conv3d_tc_kernel<KC><<<grid, 128, bytes, s>>>(a, n_tile, cols, stages);
     return cudaGetLastError();
+}
+
+cudaError_t conv_launch(const ConvArgs &a, cudaStream_t s)
+{
+    if (a.Cin % 64 == 0) return tc_launch<64>(a, s);
+    if (a.Cin % 32 == 0) return tc_launch<32>(a, s);
+    return tc_launch<16>(a, s);
 }
 
 cudaError_t wgrad_launch(const WgradArgs &a0, cudaStream_t s)
@@ -799,6 +998,15 @@ soc_status soc_unet_adam(int net_id, float lr, void *stream)
 }
 
 // --- single-operation entry points (for parity tests and reuse) -----------
+soc_status soc_nn_error_flag(int *flag)
+{
+    if (!flag) return SOC_ERR_ARG;
+    int zero = 0;
+    if (cudaMemcpyFromSymbol(flag, g_tc_error, sizeof(int)) != cudaSuccess) return SOC_ERR_CUDA;
+    if (cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int)) != cudaSuccess) return SOC_ERR_CUDA;
+    return SOC_OK;
+}
+
 soc_status soc_nn_conv3d(const void *x, int N, int D, int H, int W, int Cin, const void *w, const float *bias, int Cout,
                          int relu, void *y_bf16, float *y_f32, void *stream)
 {

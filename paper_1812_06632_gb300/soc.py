@@ -33,7 +33,8 @@ EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "so
            "soc_capture_end", "soc_graph_launch", "soc_graph_destroy",
            "soc_unet_create", "soc_unet_destroy", "soc_unet_param_count", "soc_unet_set_params",
            "soc_unet_get_params", "soc_unet_forward", "soc_unet_backward", "soc_unet_adam",
-           "soc_nn_conv3d", "soc_nn_conv3d_dgrad", "soc_nn_conv3d_wgrad", "soc_simulate_frequency_batch_noalloc"]
+           "soc_nn_conv3d", "soc_nn_conv3d_dgrad", "soc_nn_conv3d_wgrad", "soc_nn_error_flag",
+           "soc_simulate_frequency_batch_noalloc"]
 
 
 class GridDesc(C.Structure):
@@ -115,6 +116,7 @@ def _load():
         "soc_unet_backward": ([I, P, P, P, P, P], I),
         "soc_unet_adam": ([I, C.c_float, P], I),
         "soc_nn_conv3d": ([P, I, I, I, I, I, P, P, I, I, P, P, P], I),
+        "soc_nn_error_flag": ([C.POINTER(I)], I),
         "soc_nn_conv3d_dgrad": ([P, I, I, I, I, I, P, I, P, P, P], I),
         "soc_nn_conv3d_wgrad": ([P, P, I, I, I, I, I, I, P, P, P], I),
         "soc_set_max_steps": ([P, C.c_uint32], I),
@@ -435,6 +437,14 @@ class UNet:
 
     def adam(self, lr, stream=None):
         _nn_check(lib.soc_unet_adam(self.id, C.c_float(lr), _stream(stream)), "soc_unet_adam")
+
+
+def nn_error_flag():
+    """soc_nn_error_flag: 1 if a tensor-core convolution block timed out
+    (the flag is cleared)."""
+    f = C.c_int(0)
+    _nn_check(lib.soc_nn_error_flag(C.byref(f)), "soc_nn_error_flag")
+    return f.value
 
 
 def conv3d(x, w, bias=None, relu=False, out=None, out_f32=None, stream=None):
