@@ -177,6 +177,45 @@ def compare(net, seeds, side, stats, max_iter=60, tol=0.1, log=print):
     return rows
 
 
+def seed_bound(seeds, side=64, max_iter=60, tol=0.1, other_seed=7, log=print):
+    """What any seed can gain here: dust iterations to max |dT| < tol from
+    (a) the run's own converged T (a perfect predictor), (b) the converged T
+    of an independent Monte Carlo realisation of the same cloud (context
+    seed `other_seed`: a prediction as good as the method's own answer but
+    without this run's frozen noise) and (c) T1 (the plain start)."""
+    import torch
+    from . import soc
+    rows = []
+    for s in seeds:
+        w = I.config_c4(int(s), side=side)
+        n = w.clouds[0].n_cells
+        runs = {}
+        for cseed in (w.seed, other_seed):
+            ctx = soc.Context(0, cseed)
+            ctx.dust_upload(w.dust.nu, w.dust.kabs, w.dust.ksca, w.dust.g)
+            cid = ctx.grid_upload(w.clouds[0])
+            ctx.sources_upload(cid, w.bg_I[0], w.ps_pos[0], w.ps_L[0])
+            T1 = torch.empty(n, dtype=torch.float32, device="cuda")
+            T = torch.empty_like(T1)
+            iteration0(ctx, cid, w, T1)
+            iterate_from(ctx, cid, T1, T, max_iter, tol)
+            runs[cseed] = (ctx, cid, T1, T)
+        ctx, cid, T1, T = runs[w.seed]
+        T_other = runs[other_seed][3]
+        row = dict(seed=int(s))
+        for name, start in (("own_converged", T), ("other_realisation", T_other), ("T1", T1)):
+            out = torch.empty_like(T1)
+            row[name + "_iters"] = iterate_from(ctx, cid, start.contiguous(), out, max_iter, tol)["iterations"]
+        d = (T_other - T).double()
+        row["realisations_max_abs_dT_K"] = float(d.abs().max().item())
+        row["realisations_rms_rel_dT"] = float(((T_other.double() / T.double() - 1) ** 2).mean().sqrt().item())
+        for c in runs.values():
+            c[0].close()
+        rows.append(row)
+        log(json.dumps(row))
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser(description="learned temperature seed: data, training, comparison")
     ap.add_argument("--side", type=int, default=64)
@@ -187,7 +226,14 @@ def main():
     ap.add_argument("--tol", type=float, default=0.1)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--out", default=os.path.join("gpurun_out", "learned_seed.json"))
+    ap.add_argument("--bound", action="store_true",
+                    help="only measure what an ideal seed can gain on the test clouds (no training)")
     a = ap.parse_args()
+    if a.bound:
+        rows = seed_bound(np.arange(2000, 2000 + a.test), a.side, a.max_iter, a.tol)
+        keys = ["own_converged_iters", "other_realisation_iters", "T1_iters"]
+        print(json.dumps({k: float(np.mean([r[k] for r in rows])) for k in keys}))
+        return
     t0 = time.perf_counter()
     train_seeds = np.arange(1000, 1000 + a.train)
     test_seeds = np.arange(2000, 2000 + a.test)
