@@ -449,6 +449,65 @@ def run_extra(args):
     print(json.dumps(out), flush=True)
 
 
+# the U-Net's convolutions: (C_in, C_out, level) in forward order (level l has side S / 2^l)
+UNET_LAYERS = [(16, 16, 0), (16, 16, 0), (16, 32, 1), (32, 32, 1), (32, 64, 2), (64, 64, 2), (64, 128, 3),
+               (128, 128, 3), (192, 64, 2), (64, 64, 2), (96, 32, 1), (32, 32, 1), (48, 16, 0), (16, 16, 0),
+               (16, 16, 0)]
+
+
+def run_unet(args):
+    """Learned-seed network (batch 4, 64^3): forward and training step
+    (forward, input and weight gradients, Adam) timed with CUDA events;
+    convolution FLOPs (2 x voxels x 27 x C_in x C_out per layer) against the
+    measured BF16 tensor peak."""
+    import torch
+    from paper_1812_06632_gb300 import build as B
+    B.build()
+    from paper_1812_06632_gb300 import soc
+    torch.cuda.set_device(0)
+    batch, side = 4, 64
+    fwd_flops = sum(2.0 * batch * (side >> lv) ** 3 * 27 * ci * co for ci, co, lv in UNET_LAYERS)
+    # backward: input gradients of every layer but the first, weight gradients of all
+    ci0, co0, lv0 = UNET_LAYERS[0]
+    train_flops = 3 * fwd_flops - 2.0 * batch * (side >> lv0) ** 3 * 27 * ci0 * co0
+    net = soc.UNet(batch, side)
+    rng = np.random.default_rng(0)
+    net.set_params((rng.standard_normal(net.n_params) * 0.05).astype(np.float32))
+    x = torch.randn(batch, side, side, side, 2, device="cuda")
+    t = torch.randn(batch, side, side, side, device="cuda")
+    pred = torch.empty(batch, side, side, side, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / args.steps
+
+    ms_f = timed(lambda: net.forward(x, pred))
+    ms_t = timed(lambda: (net.backward(x, t, pred, loss), net.adam(1e-4)))
+    peak = _peaks()[0]
+    tf_f = fwd_flops / (ms_f / 1e3) / 1e12
+    out = {"metric": "U-Net convolution TFLOP/s", "workload": "unet", "value": tf_f, "unit": "TFLOP/s",
+           "config": {"batch": batch, "side": side, "layers": len(UNET_LAYERS), "params": net.n_params},
+           "forward_ms": ms_f, "forward_tflop": fwd_flops / 1e12,
+           "train_step_ms": ms_t, "train_step_tflop": train_flops / 1e12,
+           "train_step_tflops": train_flops / (ms_t / 1e3) / 1e12,
+           "roofline": {"bound": "tensor", "achieved": tf_f, "peak": peak["bf16_tflops"], "unit": "TFLOP/s",
+                        "frac": tf_f / peak["bf16_tflops"], "traffic": None,
+                        "peak_source": "measured bf16_tflops (cuBLAS burst)"},
+           "tensor_error_flag": soc.nn_error_flag()}
+    net.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -480,8 +539,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=4096, help="oracle packages per frequency")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
-                    help="c2 (default, the headline 128^3 x 64 nu pass), c3 octree, c5 uneven 64-cloud batch")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "unet"],
+                    help="c2 (default, the headline 128^3 x 64 nu pass), c3 octree, c5 uneven 64-cloud batch, "
+                         "unet (the learned seed's network)")
     ap.add_argument("--freq-stride", type=int, default=1,
                     help="trace every k-th frequency only (profiling captures of a smaller case)")
     ap.add_argument("--packages", type=int, default=N_PACKAGES,
@@ -489,6 +549,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "unet":
+        run_unet(args)
     elif args.workload != "c2":
         run_extra(args)
     else:
