@@ -13,7 +13,7 @@
  *    context's device (e.g. torch tensors); the library never frees them.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Calls taking a stream are asynchronous on it unless stated.
- *  - Fixed point: one photon package starts with SOC_W_UNIT = 2^32 weight
+ *  - Fixed point: one photon package starts with SOC_W_UNIT = 2^31 weight
  *    units; absorption counters ("tallies") are int64 sums of weight units.
  *  - Lengths: the kernels work in root-cell units; physical sizes (cm)
  *    enter only through the root-cell side of each grid.
@@ -41,7 +41,7 @@ typedef int soc_status;
 #define SOC_SRC_POINT      1
 #define SOC_SRC_DUST       2
 
-#define SOC_W_UNIT   4294967296ull      /* 2^32 */
+#define SOC_W_UNIT   2147483648ull      /* 2^31 */
 #define SOC_MAX_LEVELS 16
 
 typedef struct soc_ctx soc_ctx;
@@ -141,11 +141,12 @@ soc_status soc_sources_upload(soc_ctx *ctx, int cloud_id, const double *bg_I_nu,
  *     iteration       RNG stream selector (key word 1 gets iteration << 16);
  *     pid_offset      first package id (packages pid_offset .. +n_packages-1);
  *     n_packages      number of packages (< 2^32 - pid_offset);
- *     w0              initial weight of background / point packages (1..2^32);
+ *     w0              initial weight of background / point packages (1..2^31);
  *     tally_offset    element offset in d_tally of this item's cell 0: the
  *                     item adds its deposits to d_tally[tally_offset + cell];
  *     d_dust_w        device [n_leaf] uint64: initial weight of the packages
- *                     of each leaf (leaves in cell order), SOC_SRC_DUST only;
+ *                     of each leaf (leaves in cell order, each <= SOC_W_UNIT;
+ *                     larger values are not checked), SOC_SRC_DUST only;
  *     n_per_cell      dust packages per leaf (n_packages = n_leaf*n_per_cell).
  *     reserved        flags: SOC_ITEM_WEIGHTED (dust) = emission-weighted
  *                     sampling: d_dust_w holds [n_leaf] weights followed by
@@ -246,9 +247,9 @@ soc_status soc_graph_destroy(soc_ctx *ctx, int graph_id);
 
 /* Per-package energy of background / point-source packages (paper Sect. 2.2
  * sources): the energy in erg/s/Hz carried by one weight unit when
- * n_packages packages of weight 2^32 are launched at every frequency.
- *   background: pi I_nu S / n_packages / 2^32 (S = box surface, cm^2);
- *   point:      sum_k L_nu,k / n_packages / 2^32.
+ * n_packages packages of weight 2^31 are launched at every frequency.
+ *   background: pi I_nu S / n_packages / 2^31 (S = box surface, cm^2);
+ *   point:      sum_k L_nu,k / n_packages / 2^31.
  * e_unit: host [n_freq].  Synchronous (host only). */
 soc_status soc_package_energy(soc_ctx *ctx, int cloud_id, int source, uint64_t n_packages,
                               double *e_unit);
@@ -259,8 +260,8 @@ soc_status soc_package_energy(soc_ctx *ctx, int cloud_id, int source, uint64_t n
  * inside the cell).  For every leaf c and frequency index f in
  * [freq_lo, freq_lo + n_freq):
  *   L_c = 4 pi rho_c V_c kabs(nu) B_nu(T_c)   (FP64),
- *   d_w[(f - freq_lo)*n_leaf + leaf(c)] = rint(2^32 L_c / max_c L_c),
- *   d_e_unit[f - freq_lo] = max_c L_c / n_per_cell / 2^32.
+ *   d_w[(f - freq_lo)*n_leaf + leaf(c)] = rint(2^31 L_c / max_c L_c),
+ *   d_e_unit[f - freq_lo] = max_c L_c / n_per_cell / 2^31.
  *   d_T               device float [n_cells] (leaf temperatures; parents ignored).
  *   d_w               device uint64 [n_freq][n_leaf].
  *   d_e_unit          device double [n_freq].
@@ -272,11 +273,11 @@ soc_status soc_dust_emission(soc_ctx *ctx, int cloud_id, const float *d_T, int f
 /* ------------------------------------------------------------------------
  * soc_dust_weighted -- emission-weighted dust sampling (paper Sect. 3.2:
  * packages per cell in proportion to the cell's luminosity, with a cap on
- * any single cell).  From the uniform weights u = rint(2^32 L / max L) of
+ * any single cell).  From the uniform weights u = rint(2^31 L / max L) of
  * soc_dust_emission (n_per_cell = 1) and its d_e_unit, per frequency:
  *   S = sum u;  n_c = u_c ? min(cap, ceil(N u_c / S)) : 0;
- *   E_ref = max(S / N, 2^32 / cap);  W_c = rint((u_c / n_c) / E_ref 2^32);
- *   e_unit = e_unit_uniform E_ref / 2^32  (energy of one weight unit).
+ *   E_ref = max(S / N, 2^31 / cap);  W_c = rint((u_c / n_c) / E_ref 2^31);
+ *   e_unit = e_unit_uniform E_ref / 2^31  (energy of one weight unit).
  *   d_u               device uint64 [n_freq][n_leaf].
  *   d_out             device uint64 [n_freq][2 n_leaf + 1]: W then the
  *                     exclusive prefix of n (last entry = packages to trace).
@@ -292,8 +293,8 @@ soc_status soc_dust_weighted(soc_ctx *ctx, int cloud_id, const uint64_t *d_u, co
  * half of d_inout, as written by soc_dust_weighted, is read and kept), from
  * new uniform weights u of soc_dust_emission (n_per_cell = 1):
  *   n_c = prefix[c+1] - prefix[c];  E_ref = max over n_c > 0 of u_c / n_c;
- *   W_c = n_c ? rint((u_c / n_c) / E_ref 2^32) : 0;
- *   e_unit = e_unit_uniform E_ref / 2^32.
+ *   W_c = n_c ? rint((u_c / n_c) / E_ref 2^31) : 0;
+ *   e_unit = e_unit_uniform E_ref / 2^31.
  * Keeping the counts keeps every package's id -> cell map between dust
  * iterations, so frozen random numbers (paper Sect. 3.2) give the same paths
  * and the iteration converges like the uniform one.
@@ -319,8 +320,8 @@ soc_status soc_dust_reweight(soc_ctx *ctx, int cloud_id, const uint64_t *d_u, co
  *   leaf at frequencies freq_lo .. freq_lo + n_freq - 1 (erg/s/Hz).
  *
  * soc_reference_delta: per frequency, d = L - L_ref, m = max |d|,
- *   d_u (device uint64) = rint(|d| / m 2^32), d_neg (device uint8) = d < 0,
- *   d_e_unit_uniform (device double [n_freq]) = m / 2^32 (energy of one
+ *   d_u (device uint64) = rint(|d| / m 2^31), d_neg (device uint8) = d < 0,
+ *   d_e_unit_uniform (device double [n_freq]) = m / 2^31 (energy of one
  *   unit of u with one package per cell: the input of soc_dust_weighted),
  *   and L_ref (device double, in/out) += w d.
  *

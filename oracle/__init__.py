@@ -31,7 +31,7 @@ _lock = threading.Lock()
 _lib = None
 
 SRC_BACKGROUND, SRC_POINT, SRC_DUST = 0, 1, 2
-W_UNIT = 1 << 32          # fixed-point units of one package's initial weight
+W_UNIT = 1 << 31          # fixed-point units of one package's initial weight
 
 
 def build(force: bool = False) -> str:

@@ -20,7 +20,7 @@ from scipy.optimize import brentq
 H_PLANCK = 6.62607015e-27      # erg s
 K_BOLTZ = 1.380649e-16         # erg / K
 C_LIGHT = 2.99792458e10        # cm / s
-W_UNIT = 2.0 ** 32             # fixed-point units of one package's initial weight
+W_UNIT = 2.0 ** 31             # fixed-point units of one package's initial weight
 
 T_MIN = 2.7                    # K: temperature of cells that absorb nothing
 T_MAX = 3000.0                 # K: upper end of the solver's range
@@ -111,7 +111,7 @@ def background_package_energy(I_nu, nx, ny, nz, ell, n_packages):
     """Energy per unit of weight of a background package.  An isotropic
     intensity I_nu outside the box sends pi I_nu per unit area through every
     face, so the packages share pi I_nu S (S the box surface); one package
-    starts with 2^32 units."""
+    starts with 2^31 units."""
     S = 2.0 * (nx * ny + ny * nz + nz * nx) * ell * ell
     return np.pi * np.asarray(I_nu, np.float64) * S / n_packages / W_UNIT
 
@@ -140,8 +140,8 @@ def dust_luminosity(T, rho, volume, kabs_nu, nu):
 
 def dust_weights(L, n_per_cell):
     """Fixed-point initial weights of dust packages at one frequency: every
-    cell sends n_per_cell packages; W_c = rint(2^32 L_c / max L), and one unit
-    then carries e_unit = (max L / n_per_cell) / 2^32.  Returns (W uint64, e_unit)."""
+    cell sends n_per_cell packages; W_c = rint(2^31 L_c / max L), and one unit
+    then carries e_unit = (max L / n_per_cell) / 2^31.  Returns (W uint64, e_unit)."""
     L = np.asarray(L, np.float64)
     Lmax = float(L.max()) if L.size else 0.0
     if not Lmax > 0:
@@ -164,12 +164,12 @@ def temperature_ali(A, A_self, T_old, nu, kabs, beta_max=0.99, **kw):
 def weighted_dust_sampling(u, e_unit_uniform, n_total, cap):
     """Emission-weighted dust sampling (paper Sect. 3.2: packages per cell in
     proportion to the cell's luminosity, at most `cap` from any cell), built
-    from the uniform weights u_c = rint(2^32 L_c / max L) of one frequency:
+    from the uniform weights u_c = rint(2^31 L_c / max L) of one frequency:
       S = sum u_c (integer),
       n_c = 0 if u_c = 0 else min(cap, ceil(N u_c / S)),
-      E_ref = max(S / N, 2^32 / cap)  (in units of max L / 2^32),
-      W_c = rint((u_c / n_c) / E_ref * 2^32)  (<= 2^32),
-      one fixed-point unit carries e_unit_uniform * E_ref / 2^32.
+      E_ref = max(S / N, 2^31 / cap)  (in units of max L / 2^31),
+      W_c = rint((u_c / n_c) / E_ref * 2^31)  (<= 2^31),
+      one fixed-point unit carries e_unit_uniform * E_ref / 2^31.
     Returns (n uint64, exclusive prefix uint64 [n_leaf + 1], W uint64, e_unit)."""
     u = np.asarray(u, np.uint64)
     S = int(u.sum(dtype=np.uint64))
@@ -190,7 +190,7 @@ def weighted_dust_sampling(u, e_unit_uniform, n_total, cap):
 def weighted_dust_reweight(u, e_unit_uniform, prefix):
     """Weights for an existing (frozen) allocation n_c = prefix[c+1] - prefix[c]
     at new temperatures: E_ref = max over cells with n_c > 0 of u_c / n_c,
-    W_c = rint((u_c / n_c) / E_ref 2^32), e_unit = e_unit_uniform E_ref / 2^32.
+    W_c = rint((u_c / n_c) / E_ref 2^31), e_unit = e_unit_uniform E_ref / 2^31.
     Frozen counts keep every package's id -> cell map, so iterations with
     frozen random numbers follow the same paths."""
     u = np.asarray(u, np.uint64)
@@ -236,8 +236,8 @@ def reference_weights(n):
 
 def reference_delta(L, L_ref, w):
     """Emission change of one frequency, d = L - L_ref (per leaf), as weights
-    of the emission-weighted sampler: m = max |d|, u = rint(|d| / m 2^32),
-    neg = d < 0, one unit of u carrying e_uni = m / 2^32 (one package per
+    of the emission-weighted sampler: m = max |d|, u = rint(|d| / m 2^31),
+    neg = d < 0, one unit of u carrying e_uni = m / 2^31 (one package per
     cell).  The reference moves to L_ref + w d.  Returns (u, neg, e_uni, L_ref')."""
     L = np.asarray(L, np.float64)
     L_ref = np.asarray(L_ref, np.float64)

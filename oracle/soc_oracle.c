@@ -22,7 +22,7 @@
  * as continuous attenuation of the package weight, free paths drawn in
  * scattering optical depth, Henyey-Greenstein scattering, cosine-weighted
  * background entry through the six faces, isotropic point sources, uniform
- * in-cell dust emission, and uint64 fixed-point counters (2^32 units per
+ * in-cell dust emission, and uint64 fixed-point counters (2^31 units per
  * package) so that energy is conserved exactly.
  *
  * Arithmetic: IEEE binary32, round-to-nearest-even, one rounding per written
@@ -435,7 +435,7 @@ static int cross_face(const oracle_grid *G, pkg_t *p, int a)
  *            s' = min(tau_f / ksh, s), else s' = s;
  *   q      = 1 - exp(-((rho * kabs) * h) * s'),
  *            dep = min(W, rint(float(W) * q)), W -= dep (exact in integers);
- *   W < max(W0 / 2^20, 1) (W0 = initial weight; 2^12 for a full package)
+ *   W < max(W0 / 2^20, 1) (W0 = initial weight; 2^11 for a full package)
  *            ends the package with W deposited in the cell;
  *   a scattering moves x by d s', draws a new HG direction and a new tau_f;
  *   a face crossing subtracts dtau from tau_f, flushes the cell's merged

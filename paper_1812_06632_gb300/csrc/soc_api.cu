@@ -562,12 +562,12 @@ soc_status soc_package_energy(soc_ctx *ctx, int cloud_id, int source, uint64_t n
     if (source == SOC_SRC_BACKGROUND) {
         if (cl.bg_I.empty()) return fail(ctx, SOC_ERR_STATE, "no background uploaded");
         const double S = 2.0 * ((double)cl.nx * cl.ny + (double)cl.ny * cl.nz + (double)cl.nz * cl.nx) * cl.ell * cl.ell;
-        for (int f = 0; f < nf; ++f) e_unit[f] = kPi * cl.bg_I[f] * S / (double)n_packages / 4294967296.0;
+        for (int f = 0; f < nf; ++f) e_unit[f] = kPi * cl.bg_I[f] * S / (double)n_packages / kWUnit;
         return SOC_OK;
     }
     if (source == SOC_SRC_POINT) {
         if (cl.n_ps == 0) return fail(ctx, SOC_ERR_STATE, "no point sources uploaded");
-        for (int f = 0; f < nf; ++f) e_unit[f] = cl.ps_L_total[f] / (double)n_packages / 4294967296.0;
+        for (int f = 0; f < nf; ++f) e_unit[f] = cl.ps_L_total[f] / (double)n_packages / kWUnit;
         return SOC_OK;
     }
     return fail(ctx, SOC_ERR_ARG, "source must be background or point");
@@ -590,7 +590,7 @@ static soc_status prepare_items(soc_ctx *ctx, const soc_batch_item *items, int n
             return fail(ctx, SOC_ERR_ARG, "item %d: package ids exceed 2^32", i);
         if (it.tally_offset < 0) return fail(ctx, SOC_ERR_ARG, "item %d: negative tally offset", i);
         if (it.source == SOC_SRC_BACKGROUND || it.source == SOC_SRC_POINT) {
-            if (it.w0 == 0 || it.w0 > SOC_W_UNIT) return fail(ctx, SOC_ERR_ARG, "item %d: w0 out of [1, 2^32]", i);
+            if (it.w0 == 0 || it.w0 > SOC_W_UNIT) return fail(ctx, SOC_ERR_ARG, "item %d: w0 out of [1, 2^31]", i);
             if (it.source == SOC_SRC_POINT && cl.n_ps == 0)
                 return fail(ctx, SOC_ERR_STATE, "item %d: cloud has no point sources", i);
         } else if (it.source == SOC_SRC_DUST) {
@@ -1328,7 +1328,7 @@ extern "C" soc_status soc_simulate_frequency_batch_noalloc(soc_ctx *ctx, const s
             return fail(ctx, SOC_ERR_ARG, "item %d: package ids exceed 2^32", i);
         if (it.tally_offset < 0) return fail(ctx, SOC_ERR_ARG, "item %d: negative tally offset", i);
         if (it.source == SOC_SRC_BACKGROUND || it.source == SOC_SRC_POINT) {
-            if (it.w0 == 0 || it.w0 > SOC_W_UNIT) return fail(ctx, SOC_ERR_ARG, "item %d: w0 out of [1, 2^32]", i);
+            if (it.w0 == 0 || it.w0 > SOC_W_UNIT) return fail(ctx, SOC_ERR_ARG, "item %d: w0 out of [1, 2^31]", i);
             if (it.source == SOC_SRC_POINT && cl.n_ps == 0)
                 return fail(ctx, SOC_ERR_STATE, "item %d: cloud has no point sources", i);
         } else if (it.source == SOC_SRC_DUST) {

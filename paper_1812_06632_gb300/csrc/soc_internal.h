@@ -8,6 +8,7 @@
 namespace soc {
 
 constexpr uint32_t kLinkBit = 0x80000000u;   // cell word: bit 31 = refined
+constexpr double kWUnit = 2147483648.0;      // fixed-point units of one full package (SOC_W_UNIT)
 constexpr int kTableN = 4096;                // T grid of the emission table
 constexpr double kTMin = 2.7, kTMax = 3000.0;
 

@@ -207,7 +207,7 @@ __global__ void dust_weight_kernel(const DevCloud *__restrict__ dcl, int64_t n_l
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (tid < n_freq) {
         const double m = __longlong_as_double((long long)Lmax[tid]);
-        e_unit[tid] = __ddiv_rn(__ddiv_rn(m, (double)n_per_cell), 4294967296.0);
+        e_unit[tid] = __ddiv_rn(__ddiv_rn(m, (double)n_per_cell), kWUnit);
     }
     for (int64_t li = tid; li < n_leaf; li += (int64_t)gridDim.x * blockDim.x) {
         const int32_t cell = __ldg(C.leaf + li);
@@ -216,7 +216,7 @@ __global__ void dust_weight_kernel(const DevCloud *__restrict__ dcl, int64_t n_l
             unsigned long long W = 0;
             if (m > 0.0) {
                 const double L = dust_L(C, tt, T, cell, freq_lo + fi);
-                W = (unsigned long long)rint(__dmul_rn(__ddiv_rn(L, m), 4294967296.0));
+                W = (unsigned long long)rint(__dmul_rn(__ddiv_rn(L, m), kWUnit));
             }
             w[(int64_t)fi * n_leaf + li] = W;
         }
@@ -226,7 +226,7 @@ __global__ void dust_weight_kernel(const DevCloud *__restrict__ dcl, int64_t n_l
 // ---------------------------------------------------------------------------
 // Emission-weighted dust sampling (paper Sect. 3.2: packages per cell in
 // proportion to its luminosity, at most `cap` per cell), from the uniform
-// weights u = rint(2^32 L / max L) of each frequency.  Integer sums and a
+// weights u = rint(2^31 L / max L) of each frequency.  Integer sums and a
 // fixed operation order keep the allocation deterministic.
 // out layout per frequency: [W: n_leaf][prefix: n_leaf + 1] (uint64).
 // ---------------------------------------------------------------------------
@@ -260,7 +260,7 @@ __global__ void wsum_kernel(const unsigned long long *u, int64_t n_leaf, int n_f
 }
 
 // n = min(cap, ceil(N u / S)) (0 for u = 0) into the prefix slot (shifted by
-// one), W = rint((u / n) / E_ref 2^32), E_ref = max(S / N, 2^32 / cap); and
+// one), W = rint((u / n) / E_ref 2^31), E_ref = max(S / N, 2^31 / cap); and
 // the per-chunk sums of n.
 __global__ void walloc_kernel(const unsigned long long *u, int64_t n_leaf, int n_freq, const unsigned long long *S,
                               double n_total, double cap, const double *e_uni, unsigned long long *out, double *e_unit,
@@ -268,11 +268,11 @@ __global__ void walloc_kernel(const unsigned long long *u, int64_t n_leaf, int n
 {
     const int f = blockIdx.y;
     const double Sf = (double)S[f];
-    const double E_ref = fmax(__ddiv_rn(Sf, n_total), __ddiv_rn(4294967296.0, cap));
+    const double E_ref = fmax(__ddiv_rn(Sf, n_total), __ddiv_rn(kWUnit, cap));
     unsigned long long *W = out + (int64_t)f * (2 * n_leaf + 1);
     unsigned long long *pre = W + n_leaf;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        e_unit[f] = Sf > 0.0 ? __ddiv_rn(__dmul_rn(e_uni[f], E_ref), 4294967296.0) : 0.0;
+        e_unit[f] = Sf > 0.0 ? __ddiv_rn(__dmul_rn(e_uni[f], E_ref), kWUnit) : 0.0;
         pre[0] = 0;
     }
     for (int64_t k = blockIdx.x; k < n_chunks; k += gridDim.x) {
@@ -282,7 +282,7 @@ __global__ void walloc_kernel(const unsigned long long *u, int64_t n_leaf, int n
             unsigned long long n = 0, w = 0;
             if (uc && Sf > 0.0) {
                 n = (unsigned long long)fmin(cap, ceil(__ddiv_rn(__dmul_rn(n_total, (double)uc), Sf)));
-                w = (unsigned long long)rint(__dmul_rn(__ddiv_rn(__ddiv_rn((double)uc, (double)n), E_ref), 4294967296.0));
+                w = (unsigned long long)rint(__dmul_rn(__ddiv_rn(__ddiv_rn((double)uc, (double)n), E_ref), kWUnit));
             }
             W[li] = w;
             pre[li + 1] = n;
@@ -350,8 +350,8 @@ __global__ void wqmax_kernel(const unsigned long long *u, int64_t n_leaf, const 
     block_max_to(m, qmax + f);
 }
 
-// W = rint((u / n) / E_ref 2^32) with E_ref = qmax (0 where n = 0);
-// e_unit = e_unit_uniform E_ref / 2^32.
+// W = rint((u / n) / E_ref 2^31) with E_ref = qmax (0 where n = 0);
+// e_unit = e_unit_uniform E_ref / 2^31.
 __global__ void wreweight_kernel(const unsigned long long *u, int64_t n_leaf, const unsigned long long *qmax,
                                  const double *e_uni, unsigned long long *out, double *e_unit)
 {
@@ -360,13 +360,13 @@ __global__ void wreweight_kernel(const unsigned long long *u, int64_t n_leaf, co
     unsigned long long *W = out + (int64_t)f * (2 * n_leaf + 1);
     const unsigned long long *pre = W + n_leaf;
     if (blockIdx.x == 0 && threadIdx.x == 0)
-        e_unit[f] = E_ref > 0.0 ? __ddiv_rn(__dmul_rn(e_uni[f], E_ref), 4294967296.0) : 0.0;
+        e_unit[f] = E_ref > 0.0 ? __ddiv_rn(__dmul_rn(e_uni[f], E_ref), kWUnit) : 0.0;
     for (int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; li < n_leaf; li += (int64_t)gridDim.x * blockDim.x) {
         const unsigned long long n = pre[li + 1] - pre[li];
         unsigned long long w = 0;
         if (n && E_ref > 0.0) {
             const double q = __ddiv_rn((double)u[(int64_t)f * n_leaf + li], (double)n);
-            w = (unsigned long long)rint(__dmul_rn(__ddiv_rn(q, E_ref), 4294967296.0));
+            w = (unsigned long long)rint(__dmul_rn(__ddiv_rn(q, E_ref), kWUnit));
         }
         W[li] = w;
     }
@@ -398,20 +398,20 @@ __global__ void refdelta_max_kernel(const double *__restrict__ L, const double *
     block_max_to(v, m + f);
 }
 
-// d = L - L_ref;  u = rint(|d| / m 2^32);  neg = d < 0;  L_ref += w d;
-// e_uni = m / 2^32.
+// d = L - L_ref;  u = rint(|d| / m 2^31);  neg = d < 0;  L_ref += w d;
+// e_uni = m / 2^31.
 __global__ void refdelta_kernel(const double *__restrict__ L, double *L_ref, int64_t n_leaf, double w,
                                 const unsigned long long *__restrict__ m_bits, unsigned long long *u, uint8_t *neg,
                                 double *e_uni)
 {
     const int f = blockIdx.y;
     const double m = __longlong_as_double((long long)m_bits[f]);
-    if (blockIdx.x == 0 && threadIdx.x == 0) e_uni[f] = __ddiv_rn(m, 4294967296.0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) e_uni[f] = __ddiv_rn(m, kWUnit);
     for (int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; li < n_leaf; li += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = (int64_t)f * n_leaf + li;
         const double lr = L_ref[k];
         const double d = __dsub_rn(L[k], lr);
-        u[k] = m > 0.0 ? (unsigned long long)rint(__dmul_rn(__ddiv_rn(fabs(d), m), 4294967296.0)) : 0ull;
+        u[k] = m > 0.0 ? (unsigned long long)rint(__dmul_rn(__ddiv_rn(fabs(d), m), kWUnit)) : 0ull;
         neg[k] = d < 0.0;
         L_ref[k] = __dadd_rn(lr, __dmul_rn(w, d));
     }

@@ -9,8 +9,9 @@
 // interleaving of creation and tracking suggested in Sect. 4.2).  One launch
 // covers every (cloud, frequency, source) item of a batch.
 //
-// Arithmetic: the FP32 sequence of soc_fp32.cuh; deposits are uint64 fixed
-// point (2^32 units per package) and are merged per cell before one 64-bit
+// Arithmetic: the FP32 sequence of soc_fp32.cuh; deposits are fixed point
+// (2^31 units per package, so a package's weight and its pending deposits
+// fit 32-bit registers) and are merged per cell before one 64-bit
 // atomic add, so the counters are exact and independent of scheduling.
 // Compiled with -fmad=false.
 #include <cuda_runtime.h>
@@ -58,9 +59,9 @@ struct Pkg {
     float ix, iy, iz;             // 1/d (unused where d == 0)
     float rho;                    // density of the current leaf
     float tauf;                   // remaining scattering optical depth
-    uint64_t W;                   // weight (fixed point)
-    uint64_t pend;                // deposits in the current cell not yet added
-    uint32_t wf;                  // bits 0..12: weight floor max(W0 / 2^20, 1) (<= 2^12);
+    uint32_t W;                   // weight (fixed point, <= 2^31)
+    uint32_t pend;                // deposits in the current cell not yet added (<= W0)
+    uint32_t wf;                  // bits 0..12: weight floor max(W0 / 2^20, 1) (<= 2^11);
                                   // kHomeBit: dust package still in its emission cell
     uint32_t steps;
     bool scat;                    // waiting for its scattering (new direction, new free path)
@@ -243,7 +244,7 @@ __device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r,
         p.dx = (a == 0) ? da : d1;
         p.dy = (a == 0) ? d1 : (a == 1) ? da : d2;
         p.dz = (a == 2) ? da : d2;
-        p.W = it.w0;
+        p.W = (uint32_t)it.w0;
         p.cell = root_cell(C, p.ri, p.rj, p.rk);
         descend(C.cell, p);
         return true;
@@ -257,7 +258,7 @@ __device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r,
         p.rj = root_axis(__ldg(C.ps_pos + 3 * k + 1), C.ny, p.y);
         p.rk = root_axis(__ldg(C.ps_pos + 3 * k + 2), C.nz, p.z);
         isotropic(r, p);
-        p.W = it.w0;
+        p.W = (uint32_t)it.w0;
         p.cell = root_cell(C, p.ri, p.rj, p.rk);
         descend(C.cell, p);
         return true;
@@ -278,7 +279,7 @@ __device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r,
         li = (int32_t)(pid / it.n_per_cell);
     }
     p.cell = __ldg(C.leaf + li);
-    p.W = __ldg(reinterpret_cast<const unsigned long long *>(it.dust_w) + li);
+    p.W = (uint32_t)__ldg(reinterpret_cast<const unsigned long long *>(it.dust_w) + li);
     if (p.W == 0) return false;
     int L = 0;
     while (L + 1 < C.n_levels && (int64_t)p.cell >= C.level_start[L + 1]) ++L;
@@ -340,17 +341,16 @@ __device__ bool cross_face(const CC &C, Pkg &p, int ax, bool up)
 
 enum StepResult { kContinue = 0, kAbsorbed = 1, kEscaped = 2, kCapped = 3 };
 
-// float(W) with round-to-nearest for 0 <= W <= 2^32, through the 32-bit
-// converter (64-bit conversions run on the slow double-precision pipe).
-__device__ __forceinline__ float w_to_float(uint64_t W)
+// float(W) with round-to-nearest (W <= 2^31).
+__device__ __forceinline__ float w_to_float(uint32_t W)
 {
-    return (W >> 32) ? 4294967296.0f : __uint2float_rn((uint32_t)W);
+    return __uint2float_rn(W);
 }
 
-// rint(v) as an integer for 0 <= v <= 2^32 (v = float(W) * q, q <= 1).
-__device__ __forceinline__ uint64_t float_to_w(float v)
+// rint(v) as an integer for 0 <= v <= 2^31 (v = float(W) * q, q <= 1).
+__device__ __forceinline__ uint32_t float_to_w(float v)
 {
-    return (v >= 4294967296.0f) ? (1ull << 32) : (uint64_t)__float2uint_rn(v);
+    return __float2uint_rn(v);
 }
 
 // One photon-cell step (one segment inside one leaf).
@@ -387,12 +387,12 @@ __device__ __forceinline__ int step(const CC &C, Pkg &p, float kabs, float ksca,
     if (tau_abs > 0.0f) {
         const float q = one_minus_exp(tau_abs);
         const float prod = __fmul_rn(w_to_float(p.W), q);
-        uint64_t dep = float_to_w(prod);
+        uint32_t dep = float_to_w(prod);
         dep = dep > p.W ? p.W : dep;
         p.W -= dep;
         p.pend += dep;
     }
-    if (p.W < (uint64_t)(kSelf ? (p.wf & kFloorMask) : p.wf)) { p.pend += p.W; p.W = 0; return kAbsorbed; }
+    if (p.W < (kSelf ? (p.wf & kFloorMask) : p.wf)) { p.pend += p.W; p.W = 0; return kAbsorbed; }
     if (scatter) {
         p.x = clamp01(__fadd_rn(p.x, __fmul_rn(p.dx, sp)));
         p.y = clamp01(__fadd_rn(p.y, __fmul_rn(p.dy, sp)));
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
                        (uint32_t)IT.source);
                 p.steps = 0; p.pend = 0; p.scat = false;
                 if (emit(*C, IT, pid, r, p)) {
-                    p.wf = ((p.W >> 20) ? (uint32_t)(p.W >> 20) : 1u) |
+                    p.wf = ((p.W >> 20) ? (p.W >> 20) : 1u) |
                            ((kSelf && IT.source == SOC_SRC_DUST) ? kHomeBit : 0u);
                     set_inverse(p);
                     p.tauf = -log_pos(r.u());

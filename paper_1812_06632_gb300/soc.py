@@ -20,7 +20,7 @@ LIB_PATH = os.environ.get("SOC_LIB") or os.path.join(_HERE, "_build", "libsoc.so
 SOC_OK = 0
 SOC_ERR_STEP_LIMIT = -4
 SRC_BACKGROUND, SRC_POINT, SRC_DUST = 0, 1, 2
-W_UNIT = 1 << 32
+W_UNIT = 1 << 31
 
 EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "soc_grid_validate", "soc_grid_free",
            "soc_dust_upload", "soc_simulate_frequency_batch_ex", "soc_update_temperature_ali", "soc_map",

@@ -7,7 +7,7 @@ import numpy as np
 import oracle
 from oracle import physics as P
 
-W_UNIT = 1 << 32
+W_UNIT = 1 << 31
 
 
 def oracle_grid(cl):

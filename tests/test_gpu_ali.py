@@ -25,7 +25,7 @@ def test_self_counters_bit_exact():
     ctx, ids = gpu_context(w)
     leaf = cl.leaves()
     rng = np.random.default_rng(2)
-    dw = rng.integers(0, 2 ** 32, leaf.size).astype(np.uint64)
+    dw = rng.integers(0, 2 ** 31, leaf.size).astype(np.uint64)
     dw_t = torch.from_numpy(dw.view(np.int64)).cuda()
     specs = [dict(source=2, freq=f, n_packages=leaf.size, dust_w=dw_t, tally_offset=k * cl.n_cells)
              for k, f in enumerate((10, 40, 60))]

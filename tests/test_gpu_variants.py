@@ -36,7 +36,7 @@ def _mixed_workload():
 
 
 def _dust_weights(n, seed):
-    return np.random.default_rng(seed).integers(1, 2 ** 32, n).astype(np.uint64)
+    return np.random.default_rng(seed).integers(1, 2 ** 31, n).astype(np.uint64)
 
 
 @pytest.mark.parametrize("self_counters", [False, True])

@@ -171,7 +171,7 @@ def test_conservation_exact(source, octree):
     if source == oracle.SRC_DUST:
         leaf = cl.leaves()
         rng = np.random.default_rng(3)
-        dw = rng.integers(0, 2 ** 32, leaf.size).astype(np.uint64)
+        dw = rng.integers(0, 2 ** 31, leaf.size).astype(np.uint64)
         dw[::7] = 0
         kw.update(leaf=leaf, dust_w=dw, n_per_cell=2)
         n = 2 * leaf.size
@@ -473,9 +473,9 @@ def test_thin_cube_mc_temperature_matches_closed_form():
 def test_dust_weights():
     L = np.array([0.0, 1.0, 2.5, 5.0, 5.0 * (1 - 2 ** -40)])
     W, e = P.dust_weights(L, 3)
-    assert W[3] == 2 ** 32 and W[0] == 0 and W[1] == round(2 ** 32 / 5)
-    assert W[4] == 2 ** 32
-    assert abs(e * 2 ** 32 * 3 - 5.0) < 1e-12
+    assert W[3] == 2 ** 31 and W[0] == 0 and W[1] == round(2 ** 31 / 5)
+    assert W[4] == 2 ** 31
+    assert abs(e * 2 ** 31 * 3 - 5.0) < 1e-12
 
 
 def test_faint_dust_package_is_not_dumped_into_its_own_cell():
@@ -487,7 +487,7 @@ def test_faint_dust_package_is_not_dumped_into_its_own_cell():
     leaf = cl.leaves()
     G = _grid(cl)
     kw = dict(source=oracle.SRC_DUST, kabs=0.05, ksca=0.0, seed=4, leaf=leaf, n_per_cell=1, n_packages=leaf.size)
-    big = oracle.trace(G, dust_w=np.full(leaf.size, 2 ** 32, np.uint64), **kw)[0].astype(np.float64)
+    big = oracle.trace(G, dust_w=np.full(leaf.size, 2 ** 31, np.uint64), **kw)[0].astype(np.float64)
     small = oracle.trace(G, dust_w=np.full(leaf.size, 2 ** 11, np.uint64), **kw)[0].astype(np.float64)
     assert small.sum() > 0
     np.testing.assert_allclose(small / small.sum(), big / big.sum(), atol=2e-3)
@@ -500,13 +500,13 @@ def test_self_absorption_counter():
     cl = I.regular(np.ones((6, 6, 6), np.float32))
     leaf = cl.leaves()
     kw = dict(source=oracle.SRC_DUST, ksca=0.3, g=0.2, seed=8, leaf=leaf, n_per_cell=2, n_packages=2 * leaf.size,
-              dust_w=np.full(leaf.size, 2 ** 32, np.uint64))
+              dust_w=np.full(leaf.size, 2 ** 31, np.uint64))
     self_t = np.zeros(cl.n_cells, np.int64)
     tally, st, _ = oracle.trace(_grid(cl), kabs=0.2, self_tally=self_t, **kw)
     assert np.all(self_t <= tally) and self_t.sum() > 0
     one = I.regular(np.ones((1, 1, 1), np.float32))
     s1 = np.zeros(1, np.int64)
-    t1, _, _ = oracle.trace(_grid(one), kabs=0.7, self_tally=s1, leaf=one.leaves(), dust_w=np.full(1, 2 ** 32, np.uint64),
+    t1, _, _ = oracle.trace(_grid(one), kabs=0.7, self_tally=s1, leaf=one.leaves(), dust_w=np.full(1, 2 ** 31, np.uint64),
                             source=oracle.SRC_DUST, ksca=0.4, g=0.0, seed=3, n_per_cell=500, n_packages=500)
     assert s1[0] == t1[0] > 0
     s2 = np.zeros(cl.n_cells, np.int64)
@@ -546,7 +546,7 @@ def test_weighted_dust_sampling_allocation():
     n, pref, W, e = P.weighted_dust_sampling(u, e_uni, N, cap)
     assert n.max() <= cap and n[7] == cap
     assert np.all((n > 0) == (u > 0)) and pref[-1] == n.sum()
-    assert np.all(W <= 2 ** 32) and W.max() == 2 ** 32
+    assert np.all(W <= 2 ** 31) and W.max() == 2 ** 31
     emitted = n.astype(np.float64) * W.astype(np.float64) * e
     ok = u > 2 ** 12
     np.testing.assert_allclose(emitted[ok], L[ok], rtol=2e-3)
@@ -560,7 +560,7 @@ def test_weighted_dust_tracing_conserves_and_uses_prefix():
     cl = I.regular(np.ones((5, 5, 5), np.float32))
     leaf = cl.leaves()
     rng = np.random.default_rng(6)
-    u = rng.integers(0, 2 ** 32, leaf.size).astype(np.uint64)
+    u = rng.integers(0, 2 ** 31, leaf.size).astype(np.uint64)
     n, pref, W, e = P.weighted_dust_sampling(u, 1.0, 3 * leaf.size, 40)
     tally, st, steps = oracle.trace(_grid(cl), source=oracle.SRC_DUST, kabs=0.3, ksca=0.2, g=0.1, seed=2, leaf=leaf,
                                     dust_w=W, dust_prefix=pref, n_packages=int(pref[-1]), want_steps=True)
@@ -575,7 +575,7 @@ def test_weighted_reweight_keeps_counts_and_energy():
     L1 = L0 * np.exp(rng.normal(0, 0.3, 500))          # new temperatures
     u1, e1 = P.dust_weights(L1, 1)
     W1, e_1 = P.weighted_dust_reweight(u1, e1, pref)
-    assert W1.max() == 2 ** 32 and np.all((W1 > 0) <= (n > 0))
+    assert W1.max() == 2 ** 31 and np.all((W1 > 0) <= (n > 0))
     ok = (n > 0) & (u1 > 2 ** 16)
     np.testing.assert_allclose(n[ok] * W1[ok].astype(np.float64) * e_1, L1[ok], rtol=1e-4)
 

@@ -40,7 +40,7 @@ def test_noalloc_entry_matches_ordinary_entry_twice(libsoc):
     ctx, ids = gpu_context(w)
     nl = cl.leaves().size
     rng = np.random.default_rng(5)
-    dw = torch.from_numpy(rng.integers(0, 2 ** 32, nl).astype(np.int64)).cuda()
+    dw = torch.from_numpy(rng.integers(0, 2 ** 31, nl).astype(np.int64)).cuda()
     specs = _specs(cl, nl, dw)
     items = ctx.items(specs)
     total = sum(s["n_packages"] for s in specs)
