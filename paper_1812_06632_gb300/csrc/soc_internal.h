@@ -69,7 +69,8 @@ struct TraceParams {
     int32_t scatter_min;         // scatter a warp's waiting lanes once this many wait
     HotCloud hot;                // cell != nullptr: every item uses this one cloud
     int32_t regular;             // every item's cloud is a regular grid (selects the
-                                 // two-steps-per-pass build of the tracer)
+                                 // tracer build without octree traversal, two steps
+                                 // per pass)
 };
 
 // variant: 3 or 4 = minimum resident 256-thread blocks per SM the kernel is

@@ -298,12 +298,13 @@ __device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r,
 }
 
 // Cross the face on axis `ax`: the package sits on it in the current frame.
-// Returns false when it leaves the root grid.
-template <class CC>
+// Returns false when it leaves the root grid.  kRegular: every cell is a
+// root leaf (a one-level grid), so there is nothing to climb or descend.
+template <bool kRegular = false, class CC>
 __device__ bool cross_face(const CC &C, Pkg &p, int ax, bool up)
 {
     const int32_t n_root = C.n_root();
-    while (p.cell >= n_root) {
+    while (!kRegular && p.cell >= n_root) {
         const int o = (p.cell - n_root) & 7;
         const int b = (o >> ax) & 1;
         if (up ? (b == 0) : (b == 1)) {
@@ -335,7 +336,8 @@ __device__ bool cross_face(const CC &C, Pkg &p, int ax, bool up)
     p.x = (ax == 0) ? v : p.x;
     p.y = (ax == 1) ? v : p.y;
     p.z = (ax == 2) ? v : p.z;
-    descend(C.cell(), p);
+    if (kRegular) p.rho = __uint_as_float(__ldg(C.cell() + p.cell));
+    else descend(C.cell(), p);
     return true;
 }
 
@@ -354,7 +356,7 @@ __device__ __forceinline__ uint32_t float_to_w(float v)
 }
 
 // One photon-cell step (one segment inside one leaf).
-template <bool kSelf, class CC>
+template <bool kSelf, bool kRegular, class CC>
 __device__ __forceinline__ int step(const CC &C, Pkg &p, float kabs, float ksca,
                                     unsigned long long *tally, const TraceParams &P)
 {
@@ -420,7 +422,7 @@ __device__ __forceinline__ int step(const CC &C, Pkg &p, float kabs, float ksca,
     p.x = (ax == 0) ? face : mx;
     p.y = (ax == 1) ? face : my;
     p.z = (ax == 2) ? face : mz;
-    if (!cross_face(C, p, ax, up)) return kEscaped;
+    if (!cross_face<kRegular>(C, p, ax, up)) return kEscaped;
     return kContinue;
 }
 
@@ -434,7 +436,7 @@ __device__ __forceinline__ int find_item(const uint64_t *__restrict__ prefix, in
     return lo;
 }
 
-template <int kMinBlocks, bool kSelf, bool kOneCloud, bool kTwoSteps>
+template <int kMinBlocks, bool kSelf, bool kOneCloud, bool kRegular>
 __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParams P)
 {
     const int lane = threadIdx.x & 31;
@@ -546,9 +548,10 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
             }
         }
         if (active && !p.scat) {
-            // On regular grids two steps before the warp looks at refills
-            // and scatterings again: half the passes of the scheduling code
-            // per step.  Timed on GB300 (128^3, 64 nu): 71.5 ms against
+            // On regular grids (kRegular: no octree climbs or descents in a
+            // step) two steps before the warp looks at refills and
+            // scatterings again: half the passes of the scheduling code per
+            // step.  Timed on GB300 (128^3, 64 nu): 71.5 ms against
             // 77.0 ms for one step, and slower with three or four steps or
             // with the two written as a loop.  Octree steps, whose climbs and
             // descents vary in length, are faster one at a time (78 against
@@ -556,12 +559,12 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
             int res;
             if (kOneCloud) {
                 const ParamCloud pc{P.hot};
-                res = step<kSelf>(pc, p, kabs, ksca, tally, P);
-                if (kTwoSteps && res == kContinue && !p.scat) res = step<kSelf>(pc, p, kabs, ksca, tally, P);
+                res = step<kSelf, kRegular>(pc, p, kabs, ksca, tally, P);
+                if (kRegular && res == kContinue && !p.scat) res = step<kSelf, kRegular>(pc, p, kabs, ksca, tally, P);
             } else {
                 const GlobalCloud gc{*C};
-                res = step<kSelf>(gc, p, kabs, ksca, tally, P);
-                if (kTwoSteps && res == kContinue && !p.scat) res = step<kSelf>(gc, p, kabs, ksca, tally, P);
+                res = step<kSelf, kRegular>(gc, p, kabs, ksca, tally, P);
+                if (kRegular && res == kContinue && !p.scat) res = step<kSelf, kRegular>(gc, p, kabs, ksca, tally, P);
             }
             if (res != kContinue) {
                 if (p.pend) {
@@ -683,17 +686,17 @@ cudaError_t launch_map(const MapParams &m, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int kMinBlocks, bool kTwoSteps>
+template <int kMinBlocks, bool kRegular>
 static void launch_variant(const TraceParams &p, int grid, int block, cudaStream_t s)
 {
     // the self-counter logic (ALI) is compiled only into the variants that need it
     const bool one = p.hot.cell != nullptr;
     if (p.self) {
-        if (one) trace_kernel<kMinBlocks, true, true, kTwoSteps><<<grid, block, 0, s>>>(p);
-        else trace_kernel<kMinBlocks, true, false, kTwoSteps><<<grid, block, 0, s>>>(p);
+        if (one) trace_kernel<kMinBlocks, true, true, kRegular><<<grid, block, 0, s>>>(p);
+        else trace_kernel<kMinBlocks, true, false, kRegular><<<grid, block, 0, s>>>(p);
     } else {
-        if (one) trace_kernel<kMinBlocks, false, true, kTwoSteps><<<grid, block, 0, s>>>(p);
-        else trace_kernel<kMinBlocks, false, false, kTwoSteps><<<grid, block, 0, s>>>(p);
+        if (one) trace_kernel<kMinBlocks, false, true, kRegular><<<grid, block, 0, s>>>(p);
+        else trace_kernel<kMinBlocks, false, false, kRegular><<<grid, block, 0, s>>>(p);
     }
 }
 
