@@ -36,8 +36,8 @@ WORKLOAD = "lognormal 128^3, 64 nu (3e11-3e15 Hz), 1e6 background packages/nu, H
 # DRAM bytes (read + write) per photon-cell step of trace_kernel from one ncu
 # capture (small case of the same workload, scaled by steps), valid only for
 # the kernel source it was taken on.
-TRACE_DRAM = {"source_sha1": "1125e48610523005514f4686f67d979bd2df3022", "bytes_per_step": 2.0953,
-              "warp_instructions_per_step": 9.466,
+TRACE_DRAM = {"source_sha1": "649dadf512fff626e8027269b9ac87f2b89dde10", "bytes_per_step": 2.2570,
+              "warp_instructions_per_step": 8.576,
               "profile": "profiles/trace_kernel_lognormal128_8nu_1e6pkg_full.md"}
 # issue-rate peak: 4 warp-instructions per cycle per SM (4 schedulers)
 ISSUE_PER_SM_CYCLE = 4
