@@ -15,6 +15,7 @@ arm of this project) on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import tempfile
 import json
 import multiprocessing as mp
 import os
@@ -144,7 +145,9 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # raw samples go to the system's temporary directory (or SOC_CLOCKS_DIR)
+        d = os.environ.get("SOC_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_bench_{os.getpid()}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)

@@ -6,7 +6,8 @@ background and point sources only) and the converged T (dust re-emission
 iterated with frozen random numbers until max |dT| < tol).  The network maps
 (log T1, log rho), normalised, to log T - log T1.  A seeded run replaces the
 start T1 by T1 exp(prediction); the Monte Carlo iterations then continue to
-the same fixed point, so they remain both the fallback and the judge.
+the same fixed point, so they remain both the fallback and the measure of the
+seed's error.
 """
 from __future__ import annotations
 
@@ -225,7 +226,7 @@ def main():
     ap.add_argument("--max-iter", type=int, default=60)
     ap.add_argument("--tol", type=float, default=0.1)
     ap.add_argument("--lr", type=float, default=2e-3)
-    ap.add_argument("--out", default=os.path.join("gpurun_out", "learned_seed.json"))
+    ap.add_argument("--out", default="learned_seed.json")
     ap.add_argument("--bound", action="store_true",
                     help="only measure what an ideal seed can gain on the test clouds (no training)")
     a = ap.parse_args()
