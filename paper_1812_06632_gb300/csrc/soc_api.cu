@@ -93,6 +93,10 @@ struct soc_ctx {
     DevBuf<unsigned long long> d_lmax;
     DevBuf<unsigned long long> d_wscratch;
     DevBuf<double> d_maxdT;
+    DevBuf<int64_t> d_level_start;
+    // pinned staging of grid uploads (grows to the largest grid)
+    uint32_t *h_stage = nullptr;
+    size_t h_stage_n = 0;
     // prepared batches and graphs
     std::vector<struct BatchHost *> batches;
     std::vector<cudaGraphExec_t> graphs;
@@ -252,6 +256,8 @@ void soc_destroy(soc_ctx *ctx)
     ctx->d_items.release(); ctx->d_prefix.release(); ctx->d_counter.release(); ctx->d_lmax.release();
     ctx->d_maxdT.release();
     ctx->d_wscratch.release();
+    ctx->d_level_start.release();
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     for (BatchHost *b : ctx->batches)
         if (b) { b->items.release(); b->prefix.release(); b->counter.release(); delete b; }
     for (cudaGraphExec_t g : ctx->graphs)
@@ -394,24 +400,25 @@ extern "C" soc_status soc_grid_upload(soc_ctx *ctx, const soc_grid_desc *d, int 
     std::vector<int64_t> &start = g.start;
     std::vector<int32_t> &child = g.child;
     std::vector<int32_t> &parent = g.parent;
-    int lv = 0;
-    // device images
-    std::vector<uint32_t> word(n);
-    std::vector<float> rho(n);
-    std::vector<double> vol(n);
+    // cell words (tagged links or FP32 densities, -0 stored as +0) are built
+    // in pinned memory and copied once; densities and volumes are derived
+    // from them on the device
+    if (ctx->h_stage_n < (size_t)n) {
+        if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+        ctx->h_stage = nullptr;
+        ctx->h_stage_n = 0;
+        CK(cudaMallocHost(&ctx->h_stage, sizeof(uint32_t) * (size_t)std::max<int64_t>(n, 1)), "pinned staging");
+        ctx->h_stage_n = (size_t)n;
+    }
+    uint32_t *word = ctx->h_stage;
     std::vector<int32_t> leaf;
     leaf.reserve(n);
-    const double ell3 = (d->root_cell_size * d->root_cell_size) * d->root_cell_size;
     for (int64_t c = 0; c < n; ++c) {
-        while (c >= start[lv + 1]) ++lv;
-        vol[c] = std::ldexp(ell3, -3 * lv);
         if (child[c] >= 0) {
             word[c] = kLinkBit | (uint32_t)child[c];
-            rho[c] = 0.0f;
         } else {
             const float r = d->rho[c] == 0.0f ? 0.0f : d->rho[c];      // no -0
             memcpy(&word[c], &r, 4);
-            rho[c] = r;
             leaf.push_back((int32_t)c);
         }
     }
@@ -420,15 +427,20 @@ extern "C" soc_status soc_grid_upload(soc_ctx *ctx, const soc_grid_desc *d, int 
     cl->nx = d->nx; cl->ny = d->ny; cl->nz = d->nz; cl->n_levels = d->n_levels;
     cl->n_cells = n; cl->n_root = n_root; cl->n_leaf = (int64_t)leaf.size(); cl->level_start = start;
     cl->ell = d->root_cell_size;
+    const double ell3 = (d->root_cell_size * d->root_cell_size) * d->root_cell_size;
     cudaError_t e = cudaSuccess;
     if ((e = cl->cell.alloc(n)) == cudaSuccess && (e = cl->parent.alloc(n_oct)) == cudaSuccess &&
         (e = cl->leaf.alloc(leaf.size())) == cudaSuccess && (e = cl->rho.alloc(n)) == cudaSuccess &&
-        (e = cl->volume.alloc(n)) == cudaSuccess &&
-        (e = cudaMemcpy(cl->cell.p, word.data(), 4 * n, cudaMemcpyHostToDevice)) == cudaSuccess &&
-        (e = cudaMemcpy(cl->parent.p, parent.data(), 4 * n_oct, cudaMemcpyHostToDevice)) == cudaSuccess &&
+        (e = cl->volume.alloc(n)) == cudaSuccess && (e = ctx->d_level_start.alloc(start.size())) == cudaSuccess &&
+        (e = cudaMemcpy(cl->cell.p, word, 4 * n, cudaMemcpyHostToDevice)) == cudaSuccess &&
+        (n_oct == 0 ||
+         (e = cudaMemcpy(cl->parent.p, parent.data(), 4 * n_oct, cudaMemcpyHostToDevice)) == cudaSuccess) &&
         (e = cudaMemcpy(cl->leaf.p, leaf.data(), 4 * leaf.size(), cudaMemcpyHostToDevice)) == cudaSuccess &&
-        (e = cudaMemcpy(cl->rho.p, rho.data(), 4 * n, cudaMemcpyHostToDevice)) == cudaSuccess &&
-        (e = cudaMemcpy(cl->volume.p, vol.data(), 8 * n, cudaMemcpyHostToDevice)) == cudaSuccess) {
+        (e = cudaMemcpy(ctx->d_level_start.p, start.data(), 8 * start.size(), cudaMemcpyHostToDevice)) ==
+            cudaSuccess &&
+        (e = launch_cell_init(cl->cell.p, n, ctx->d_level_start.p, d->n_levels, ell3, cl->rho.p, cl->volume.p, 0)) ==
+            cudaSuccess &&
+        (e = cudaStreamSynchronize(0)) == cudaSuccess) {
     }
     if (e != cudaSuccess) {
         cl->cell.release(); cl->parent.release(); cl->leaf.release(); cl->rho.release(); cl->volume.release();

@@ -121,6 +121,8 @@ cudaError_t launch_dust_split(int64_t n_leaf, int n_freq, const uint8_t *neg, ui
                               const double *e, double *e_neg, cudaStream_t s);
 cudaError_t launch_reference_update(int64_t n, double *A_ref, const double *A_d, double w, const double *A_const,
                                     double *A_out, int out_mean, cudaStream_t s);
+cudaError_t launch_cell_init(const uint32_t *word, int64_t n, const int64_t *start, int n_levels, double ell3,
+                             float *rho, double *vol, cudaStream_t s);
 cudaError_t launch_update_temperature_ali(const DevCloud *dcl, int64_t n_cells, const TempTables &tt,
                                           const double *A, const double *A_self, float *T, double *max_dT,
                                           cudaStream_t s);

@@ -452,6 +452,20 @@ __global__ void refupdate_kernel(int64_t n, double *A_ref, const double *__restr
     }
 }
 
+// Per-cell FP32 density (0 for refined cells) and FP64 volume ell^3 2^-3L
+// from the uploaded cell words and the level offsets (at most 16 levels).
+__global__ void cell_init_kernel(const uint32_t *__restrict__ word, int64_t n, const int64_t *__restrict__ start,
+                                 int n_levels, double ell3, float *rho, double *vol)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        int L = 0;
+        while (L + 1 < n_levels && c >= start[L + 1]) ++L;
+        vol[c] = scalbn(ell3, -3 * L);
+        const uint32_t w = word[c];
+        rho[c] = (w & kLinkBit) ? 0.0f : __uint_as_float(w);
+    }
+}
+
 int grid_for(int64_t n, int block)
 {
     int dev = 0, sms = 148;
@@ -560,6 +574,13 @@ cudaError_t launch_reference_update(int64_t n, double *A_ref, const double *A_d,
                                     double *A_out, int out_mean, cudaStream_t s)
 {
     refupdate_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, A_ref, A_d, w, A_const, A_out, out_mean);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_init(const uint32_t *word, int64_t n, const int64_t *start, int n_levels, double ell3,
+                             float *rho, double *vol, cudaStream_t s)
+{
+    cell_init_kernel<<<grid_for(n, 256), 256, 0, s>>>(word, n, start, n_levels, ell3, rho, vol);
     return cudaGetLastError();
 }
 
