@@ -78,3 +78,15 @@ def test_malformed_grids_rejected(libsoc, case):
     st, msg = _v(libsoc, oc, rho=rho, first_child=child, parent=parent, **over)
     assert st in (-1, -2), (case, st, msg)
     assert msg and msg != "ok"
+
+
+def test_weight_unit_agrees_across_header_binding_and_oracle(libsoc):
+    """The fixed-point unit of one package is the same constant in the C-ABI
+    header, the binding, the test helpers and the oracle (C and FP64 parts)."""
+    import oracle
+    from oracle import physics as P
+    from parity_helpers import W_UNIT as helper_unit
+    src = open(os.path.join(ROOT, "include", "soc.h")).read()
+    m = re.search(r"#define\s+SOC_W_UNIT\s+(\d+)ull", src)
+    header_unit = int(m.group(1))
+    assert header_unit == libsoc.W_UNIT == helper_unit == oracle.W_UNIT == int(P.W_UNIT) == 1 << 31
