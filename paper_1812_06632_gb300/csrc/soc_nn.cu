@@ -112,13 +112,16 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 
-template <int KC>
+// A step covers TK consecutive taps x KC channels (TK > 1 only with KC = C_in,
+// so that the weights of consecutive taps are contiguous): K = TK * KC.
+template <int KC, int TK>
 __global__ void __launch_bounds__(128) conv3d_tc_kernel(const ConvArgs a, int n_tile, uint32_t tmem_cols,
                                                         int n_stages)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
-    constexpr int kPpr = KC / 8;                      // 16-byte pieces per row of a chunk
-    const int a_bytes = 128 * KC * 2, b_bytes = n_tile * KC * 2;
+    constexpr int kPpt = KC / 8;                      // 16-byte pieces per tap and row
+    constexpr int kPpr = TK * kPpt;                   // 16-byte pieces per row of a step
+    const int a_bytes = 128 * TK * KC * 2, b_bytes = n_tile * TK * KC * 2;
     const int stage_bytes = a_bytes + b_bytes;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + n_stages * stage_bytes);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + n_stages * stage_bytes + 8 * n_stages);
@@ -154,24 +157,31 @@ __global__ void __launch_bounds__(128) conv3d_tc_kernel(const ConvArgs a, int n_
     }
     const uint32_t idesc = mma_idesc(128, n_tile);
     const int n_chunks = a.Cin / KC;
-    const int total = 27 * n_chunks;
+    const int total = (27 / TK) * n_chunks;
     const uint32_t r_off = (uint32_t)(((tid >> 3) * kPpr * 8 + (tid & 7)) * 16);   // row tid, core column 0
 
     // copies of step t into its stage (t % n_stages); one commit group per step
     auto issue = [&](int t) {
         if (t < total) {
             const uint32_t st = smem0 + (uint32_t)((t % n_stages) * stage_bytes);
-            const int tap = t / n_chunks, c0 = (t - tap * n_chunks) * KC;
-            const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
-            const bool ok = vin && zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-            const bf16 *src = a.in + (ok ? ((((long long)n * a.D + zz) * a.H + yy) * a.W + xx) * a.in_stride : 0) +
-                              a.in_off + c0;
+            const int tg = t / n_chunks, c0 = (t - tg * n_chunks) * KC;
 #pragma unroll
-            for (int c = 0; c < kPpr; ++c) cp_async16(st + r_off + c * 128, src + c * 8, ok ? 16u : 0u);
+            for (int i = 0; i < TK; ++i) {
+                const int tap = tg * TK + i;
+                const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
+                const bool ok = vin && zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+                const bf16 *src = a.in +
+                                  (ok ? ((((long long)n * a.D + zz) * a.H + yy) * a.W + xx) * a.in_stride : 0) +
+                                  a.in_off + c0;
+#pragma unroll
+                for (int c = 0; c < kPpt; ++c)
+                    cp_async16(st + r_off + (i * kPpt + c) * 128, src + c * 8, ok ? 16u : 0u);
+            }
+            // weights of taps tg*TK .. tg*TK + TK - 1 (contiguous when TK > 1)
             for (int i = tid; i < n_tile * kPpr; i += 128) {
                 const int co = i / kPpr, c = i - co * kPpr;
                 cp_async16(st + a_bytes + ((co >> 3) * kPpr * 8 + (co & 7)) * 16 + c * 128,
-                           a.w + ((long long)(n0 + co) * 27 + tap) * a.Cin + c0 + c * 8, 16u);
+                           a.w + ((long long)(n0 + co) * 27 + tg * TK) * a.Cin + c0 + c * 8, 16u);
             }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
@@ -207,7 +217,7 @@ __global__ void __launch_bounds__(128) conv3d_tc_kernel(const ConvArgs a, int n_
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = smem0 + (uint32_t)(s * stage_bytes), b0 = a0 + (uint32_t)a_bytes;
 #pragma unroll
-            for (int j = 0; j < KC / 16; ++j) {
+            for (int j = 0; j < TK * KC / 16; ++j) {
                 const uint64_t ad = smem_desc(a0 + j * 256, 128, kPpr * 128);
                 const uint64_t bd = smem_desc(b0 + j * 256, 128, kPpr * 128);
                 const uint32_t acc = (step > 0 || j > 0) ? 1u : 0u;
@@ -579,7 +589,7 @@ inline int tc_n_tile(int Cout, long long v_tiles, int sms)
     return t;
 }
 
-template <int KC>
+template <int KC, int TK>
 cudaError_t tc_launch(const ConvArgs &a, cudaStream_t s)
 {
     const long long V = (long long)a.N * a.D * a.H * a.W;
@@ -594,7 +604,7 @@ cudaError_t tc_launch(const ConvArgs &a, cudaStream_t s)
     while ((int)cols < n_tile) cols <<= 1;
     // stages of A + B copies: 3 or 4 (copies 1 or 2 steps ahead), within
     // 72 KB where possible (keeps 3 blocks per SM on the larger tiles)
-    const int stage_bytes = 128 * KC * 2 + n_tile * KC * 2;
+    const int stage_bytes = (128 + n_tile) * TK * KC * 2;
     int stages = 73728 / stage_bytes;
     stages = stages < 3 ? 3 : (stages > 4 ? 4 : stages);
     // shared memory padded so that no more blocks are resident on an SM than
@@ -605,18 +615,29 @@ cudaError_t tc_launch(const ConvArgs &a, cudaStream_t s)
     int bytes = need > pad ? need : pad;
     if (bytes > blk_max) bytes = blk_max;
     if (need > blk_max) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(conv3d_tc_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(conv3d_tc_kernel<KC, TK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)v_tiles, (unsigned)(a.Cout / n_tile));
-    conv3d_tc_kernel<KC><<<grid, 128, bytes, s>>>(a, n_tile, cols, stages);
+    conv3d_tc_kernel<KC, TK><<<grid, 128, bytes, s>>>(a, n_tile, cols, stages);
     return cudaGetLastError();
 }
 
+// K per step: 3 taps of all channels for 16 or 32 input channels, all
+// channels of one tap up to 96, else 64/32/16-channel chunks of one tap.
 cudaError_t conv_launch(const ConvArgs &a, cudaStream_t s)
 {
-    if (a.Cin % 64 == 0) return tc_launch<64>(a, s);
-    if (a.Cin % 32 == 0) return tc_launch<32>(a, s);
-    return tc_launch<16>(a, s);
+    switch (a.Cin) {
+    case 16: return tc_launch<16, 3>(a, s);
+    case 32: return tc_launch<32, 3>(a, s);
+    case 48: return tc_launch<48, 1>(a, s);
+    case 64: return tc_launch<64, 1>(a, s);
+    case 80: return tc_launch<80, 1>(a, s);
+    case 96: return tc_launch<96, 1>(a, s);
+    default: break;
+    }
+    if (a.Cin % 64 == 0) return tc_launch<64, 1>(a, s);
+    if (a.Cin % 32 == 0) return tc_launch<32, 1>(a, s);
+    return tc_launch<16, 1>(a, s);
 }
 
 cudaError_t wgrad_launch(const WgradArgs &a0, cudaStream_t s)

@@ -29,7 +29,9 @@ def _rel(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
 
 
-@pytest.mark.parametrize("shape,cin,cout", [((2, 5, 6, 7), 32, 48), ((1, 9, 4, 3), 16, 16), ((1, 8, 8, 8), 192, 64)])
+@pytest.mark.parametrize("shape,cin,cout", [((2, 5, 6, 7), 32, 48), ((1, 9, 4, 3), 16, 16), ((1, 8, 8, 8), 192, 64),
+                                             ((1, 6, 5, 4), 48, 32), ((2, 4, 4, 4), 96, 16), ((1, 4, 5, 6), 80, 256),
+                                             ((1, 3, 3, 3), 320, 32)])
 def test_conv3d_forward_dgrad_wgrad(libsoc, shape, cin, cout):
     rng = np.random.default_rng(cin + cout)
     x, x64 = _bf(rng.standard_normal(shape + (cin,)))
