@@ -487,9 +487,9 @@ soc_status soc_nn_error_flag(int *flag);
  * maps the first, noisy temperature field and the log density to the
  * converged temperature and seeds soc_iterate; the Monte Carlo iterations
  * remain its judge).  Channels-last (N, side, side, side, C) tensors; BF16
- * activations and weights on tensor cores with FP32 accumulation (the
- * convolutions and their input gradients on tcgen05 with the accumulator in
- * tensor memory, the weight gradients on mma.sync); FP32
+ * activations and weights on the tcgen05 tensor cores with FP32
+ * accumulation in tensor memory (convolutions, input and weight gradients);
+ * FP32
  * master weights, gradients and Adam moments.  Architecture: 4 levels with
  * 16-32-64-128 channels, two 3x3x3 convolutions (ReLU) per level, 2x2x2 max
  * pooling, nearest 2x upsampling, skip concatenation [upsampled, skip], a

@@ -14,7 +14,7 @@
 //   dgrad:    the forward kernel with the weights flipped in space and
 //             transposed in channels;
 //   wgrad:    M = C_out, N = C_in per tap, K = voxels (split over blocks,
-//             FP32 atomics), tiles multiplied with mma.sync.m16n8k16.
+//             FP32 atomics), on the tcgen05 tensor cores as well.
 // BF16 inputs, FP32 accumulation throughout.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -29,15 +29,6 @@ namespace soc {
 namespace nn {
 
 using bf16 = __nv_bfloat16;
-
-__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2])
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
 
 struct ConvArgs {
     const bf16 *in;
@@ -314,84 +305,170 @@ struct WgradArgs {
     long long vox_per_block;
 };
 
-// gw[co][tap][ci] += sum_v gy[v][co] x[v + off(tap)][ci].  Block: 128 threads,
-// COT output channels (16 per warp) x 16 input channels of one tap, over a
-// range of voxels (K), 16 voxels per MMA step.
-template <int COT>
-__global__ void __launch_bounds__(128) conv3d_wgrad_kernel(const WgradArgs a)
+// ---------------------------------------------------------------------------
+// Weight gradient on the tcgen05 tensor cores:
+//   gw[co][tap][ci] += sum_v x[v + off(tap)][ci] gy[v][co]
+// The M = 128 rows of the accumulator are (tap, input channel) pairs: a
+// block takes TT = 128 / ci_tile consecutive taps of ci_tile input channels
+// (8 taps of 16 channels, 4 of 32, 2 of 64, 1 of 128), N = n_tile output
+// channels, K = voxels (split over blocks, FP32 atomics).  Both operands are
+// staged MN-major: one 16-byte global row (8 channels of one voxel) is one
+// row of a core matrix (8 K-rows of 8 consecutive M or N elements, 128
+// bytes).  Core (mn, k) of A sits at (k * 16 + mn) * 128 bytes, of B at
+// (k * n_tile / 8 + mn) * 128: the stride between cores along M/N (the
+// descriptor's stride offset) is 128 B, along K (its leading offset)
+// 16 * 128 or n_tile / 8 * 128 B.  A step covers kWgKV = 64 voxels (four
+// MMAs with K = 16); two threads share a voxel.
+// ---------------------------------------------------------------------------
+constexpr int kWgKV = 64;
+
+__host__ __device__ constexpr uint32_t mma_idesc_mn(int m, int n)
 {
-    __shared__ __align__(16) bf16 Ast[COT][24];   // [co][voxel]
-    __shared__ __align__(16) bf16 Bst[16][24];    // [ci][voxel]
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = lane >> 2, t2 = (lane & 3) * 2;
+    return mma_idesc(m, n) | (1u << 15) | (1u << 16);       // A and B MN-major
+}
+
+__global__ void __launch_bounds__(128) conv3d_wgrad_tc_kernel(const WgradArgs a, int ci_tile, int n_tile,
+                                                             uint32_t tmem_cols, int n_stages)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int a_bytes = 128 * kWgKV * 2, b_bytes = n_tile * kWgKV * 2;
+    const int stage_bytes = a_bytes + b_bytes;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + n_stages * stage_bytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + n_stages * stage_bytes + 8 * n_stages);
+    const uint32_t smem0 = smem_u32(smem);
+    const int tid = threadIdx.x, warp = tid >> 5;
     const long long V = (long long)a.N * a.D * a.H * a.W;
-    const int co0 = blockIdx.y * COT;
-    const int tap = blockIdx.z % 27;
-    const int ci0 = (blockIdx.z / 27) * 16;
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const int TT = 128 / ci_tile;                         // taps per block
+    const int n_co_tiles = a.Cout / n_tile;
+    const int tap0 = blockIdx.y * TT;
+    const int ci0 = (blockIdx.z / n_co_tiles) * ci_tile;
+    const int co0 = (blockIdx.z % n_co_tiles) * n_tile;
     const long long vb = (long long)blockIdx.x * a.vox_per_block;
     const long long ve = vb + a.vox_per_block < V ? vb + a.vox_per_block : V;
-    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-    const bool warp_on = warp * 16 < COT;
-    for (long long k0 = vb; k0 < ve; k0 += 16) {
-        // gy tile: 16 voxels x COT channels, 8 channels per thread
-        for (int e = tid; e < 16 * (COT / 8); e += 128) {
-            const int kv = e / (COT / 8), cg = e % (COT / 8);
-            const long long vv = k0 + kv;
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            if (vv < ve) val = *reinterpret_cast<const uint4 *>(a.gy + vv * a.gy_stride + a.gy_off + co0 + cg * 8);
-            const bf16 *pv = reinterpret_cast<const bf16 *>(&val);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) Ast[cg * 8 + j][kv] = pv[j];
-        }
-        // x tile: 16 voxels shifted by the tap x 16 channels
-        if (tid < 32) {
-            const int kv = tid >> 1, hh = tid & 1;
-            const long long vv = k0 + kv;
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            if (vv < ve) {
-                long long q = vv;
-                const int xx = (int)(q % a.W) + dx; q /= a.W;
-                const int yy = (int)(q % a.H) + dy; q /= a.H;
-                const int zz = (int)(q % a.D) + dz;
-                const long long nn = q / a.D;
-                if (zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
-                    val = *reinterpret_cast<const uint4 *>(
-                        a.x + (((nn * a.D + zz) * a.H + yy) * a.W + xx) * a.x_stride + a.x_off + ci0 + hh * 8);
-            }
-            const bf16 *pv = reinterpret_cast<const bf16 *>(&val);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) Bst[hh * 8 + j][kv] = pv[j];
-        }
-        __syncthreads();
-        if (warp_on) {
-            uint32_t af[4];
-            const int ar = warp * 16 + g;
-            af[0] = *reinterpret_cast<const uint32_t *>(&Ast[ar][t2]);
-            af[1] = *reinterpret_cast<const uint32_t *>(&Ast[ar + 8][t2]);
-            af[2] = *reinterpret_cast<const uint32_t *>(&Ast[ar][t2 + 8]);
-            af[3] = *reinterpret_cast<const uint32_t *>(&Ast[ar + 8][t2 + 8]);
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-                uint32_t bfr[2];
-                bfr[0] = *reinterpret_cast<const uint32_t *>(&Bst[nt * 8 + g][t2]);
-                bfr[1] = *reinterpret_cast<const uint32_t *>(&Bst[nt * 8 + g][t2 + 8]);
-                mma16816(acc[nt], af, bfr);
-            }
-        }
-        __syncthreads();
+    const int total = (int)((ve - vb + kWgKV - 1) / kWgKV);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(tmem_cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (!warp_on) return;
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-        for (int hf = 0; hf < 2; ++hf)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int co = co0 + warp * 16 + g + hf * 8;
-                const int ci = ci0 + nt * 8 + t2 + j;
-                atomicAdd(a.gw + ((long long)co * 27 + tap) * a.Cin + ci, acc[nt][hf * 2 + j]);
+    if (tid == 0) {
+        for (int k = 0; k < n_stages; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[k])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    const int NC = n_tile / 8, CP = ci_tile / 8;           // 16-byte pieces per voxel of B and per tap of A
+    const uint32_t a_lbo = 16 * 128, b_lbo = (uint32_t)NC * 128;      // stride between cores along K
+    const uint32_t idesc = mma_idesc_mn(128, n_tile);
+    const int kv = tid & (kWgKV - 1), half = tid >> 6;                 // this thread's voxel and half
+
+    auto issue = [&](int t) {
+        if (t < total) {
+            const uint32_t st = smem0 + (uint32_t)((t % n_stages) * stage_bytes);
+            const long long v = vb + (long long)t * kWgKV + kv;
+            const bool vin = v < ve;
+            int xx0 = 0, yy0 = 0, zz0 = 0;
+            long long nn = 0;
+            if (vin) {
+                long long q = v;
+                xx0 = (int)(q % a.W); q /= a.W;
+                yy0 = (int)(q % a.H); q /= a.H;
+                zz0 = (int)(q % a.D); nn = q / a.D;
             }
+            // A: the 16 pieces of this voxel's row of cores: piece p = tap
+            // (p / CP) of the block, channels ci0 + (p % CP) * 8
+            const uint32_t arow = st + (uint32_t)(((kv >> 3) * 16) * 128 + (kv & 7) * 16);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int pc = half * 8 + i;
+                const int tl = pc / CP, c8 = pc - tl * CP;
+                const int tap = tap0 + tl;
+                const int zz = zz0 + tap / 9 - 1, yy = yy0 + (tap / 3) % 3 - 1, xx = xx0 + tap % 3 - 1;
+                const bool ok = vin && tap < 27 && zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+                const long long sv = ok ? ((nn * a.D + zz) * a.H + yy) * a.W + xx : 0;
+                cp_async16(arow + pc * 128, a.x + sv * a.x_stride + a.x_off + ci0 + c8 * 8, ok ? 16u : 0u);
+            }
+            // B: gy[v][co0 .. co0 + n_tile - 1], half of the NC pieces
+            const uint32_t brow = st + (uint32_t)a_bytes + (uint32_t)(((kv >> 3) * NC) * 128 + (kv & 7) * 16);
+            for (int nc = half * (NC / 2); nc < (half + 1) * (NC / 2); ++nc)
+                cp_async16(brow + nc * 128, a.gy + (vin ? v * a.gy_stride : 0) + a.gy_off + co0 + nc * 8,
+                           vin ? 16u : 0u);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    bool ok_run = true;
+    int last = -1;
+    const int ahead = n_stages - 2;
+    for (int t = 0; t < ahead; ++t) issue(t);
+    for (int step = 0; step < total; ++step) {
+        const int s = step % n_stages;
+        const int nxt = step + ahead;
+        bool waited = true;
+        if (step >= 2 && nxt < total) {
+            const int prev = step - 2;
+            waited = mbar_wait(smem_u32(&mbar[prev % n_stages]), (uint32_t)(prev / n_stages) & 1u);
+        }
+        if (waited) issue(nxt);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        if (ahead >= 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+        else asm volatile("cp.async.wait_group 1;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (!__syncthreads_and(waited)) { ok_run = false; break; }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem0 + (uint32_t)(s * stage_bytes), b0 = a0 + (uint32_t)a_bytes;
+#pragma unroll
+            for (int j = 0; j < kWgKV / 16; ++j) {
+                const uint64_t ad = smem_desc(a0 + j * 2 * a_lbo, a_lbo, 128);
+                const uint64_t bd = smem_desc(b0 + j * 2 * b_lbo, b_lbo, 128);
+                const uint32_t acc = (step > 0 || j > 0) ? 1u : 0u;
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(&mbar[s])) : "memory");
+        }
+        last = step;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    {
+        bool done = true;
+        if (last >= 0) done = mbar_wait(smem_u32(&mbar[last % n_stages]), (uint32_t)(last / n_stages) & 1u);
+        ok_run = __syncthreads_and(ok_run && done);
+    }
+    if (!ok_run) {
+        atomicExch(&g_tc_error, 1);
+    } else if (last >= 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        const int tap = tap0 + tid / ci_tile, ci = ci0 + tid % ci_tile;   // accumulator lane = (tap, ci)
+        for (int c = 0; c < n_tile; c += 16) {
+            uint32_t r[16];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                           "=r"(r[14]), "=r"(r[15])
+                         : "r"(row_addr + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (tap >= 27) continue;
+            float *dst = a.gw + ((long long)(co0 + c) * 27 + tap) * a.Cin + ci;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) atomicAdd(dst + (long long)j * 27 * a.Cin, __uint_as_float(r[j]));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols) : "memory");
+    }
 }
 
 // Bias gradient: gb[c] += sum_v gy[v][c] (BF16 gradient, dense C channels).
@@ -571,7 +648,6 @@ inline int grid_1d(long long n, int block = 256)
     return (int)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
 }
 
-inline int pick_bn(int C) { return (C % 64 == 0) ? 64 : (C % 32 == 0) ? 32 : 16; }
 
 // Output channels per block of the tensor-core convolution: a multiple of
 // 16 dividing C_out, at most 256, narrowed (down to 16) while the blocks
@@ -644,13 +720,43 @@ cudaError_t wgrad_launch(const WgradArgs &a0, cudaStream_t s)
 {
     WgradArgs a = a0;
     const long long V = (long long)a.N * a.D * a.H * a.W;
-    a.vox_per_block = 4096;
-    const int cot = pick_bn(a.Cout);
-    dim3 grid((unsigned)((V + a.vox_per_block - 1) / a.vox_per_block), (unsigned)(a.Cout / cot),
-              (unsigned)(27 * (a.Cin / 16)));
-    if (cot == 64) conv3d_wgrad_kernel<64><<<grid, 128, 0, s>>>(a);
-    else if (cot == 32) conv3d_wgrad_kernel<32><<<grid, 128, 0, s>>>(a);
-    else conv3d_wgrad_kernel<16><<<grid, 128, 0, s>>>(a);
+    int dev = 0, sms = 148, sm_smem = 0, blk_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&blk_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // input-channel tile: 16, 32, 64 or 128 (dividing C_in), 128 / tile taps
+    // per block; output-channel tile: a multiple of 16, at most 256
+    int ci_tile = 128;
+    while (ci_tile > 16 && a.Cin % ci_tile) ci_tile >>= 1;
+    if (a.Cin % ci_tile) return cudaErrorInvalidValue;
+    int n_tile = 256;
+    while (n_tile > 16 && (n_tile > a.Cout || a.Cout % n_tile)) n_tile -= 16;
+    const int TT = 128 / ci_tile;
+    const int tap_groups = (27 + TT - 1) / TT;
+    const long long tiles = (long long)tap_groups * (a.Cin / ci_tile) * (a.Cout / n_tile);
+    // split the voxels so that there are about 4 blocks per SM
+    long long chunks = (4LL * sms + tiles - 1) / tiles;
+    long long per = (V + chunks - 1) / chunks;
+    per = (per + kWgKV - 1) / kWgKV * kWgKV;
+    if (per < kWgKV) per = kWgKV;
+    a.vox_per_block = per;
+    chunks = (V + per - 1) / per;
+    uint32_t cols = 32;
+    while ((int)cols < n_tile) cols <<= 1;
+    const int stage_bytes = (128 + n_tile) * kWgKV * 2;
+    int stages = 73728 / stage_bytes;
+    stages = stages < 3 ? 3 : (stages > 4 ? 4 : stages);
+    const int need = stages * stage_bytes + 8 * stages + 16;
+    const int max_blocks = 512 / (int)cols;
+    const int pad = sm_smem / (max_blocks + 1) + 1024;
+    int bytes = need > pad ? need : pad;
+    if (need > blk_max) return cudaErrorInvalidValue;
+    if (bytes > blk_max) bytes = blk_max;
+    cudaError_t e = cudaFuncSetAttribute(conv3d_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)chunks, (unsigned)tap_groups, (unsigned)((a.Cin / ci_tile) * (a.Cout / n_tile)));
+    conv3d_wgrad_tc_kernel<<<grid, 128, bytes, s>>>(a, ci_tile, n_tile, cols, stages);
     return cudaGetLastError();
 }
 
