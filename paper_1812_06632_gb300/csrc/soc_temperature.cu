@@ -30,11 +30,28 @@ __device__ __forceinline__ double planck(double nu, double T)
     return __ddiv_rn(pre, expm1(x));
 }
 
+// w_f e_unit_f is formed once per block (the same FP64 product for every
+// cell; kShared, dynamic shared memory for n_freq doubles) or per cell (very
+// long frequency tables), the sum over frequencies per cell in frequency
+// order either way.
+constexpr int kWfShared = 4096;
+
+__device__ __forceinline__ double wf_of(const double *s_wf, const double *w, const double *e_unit, int f, bool shared)
+{
+    return shared ? s_wf[f] : __dmul_rn(__ldg(w + f), __ldg(e_unit + f));
+}
+
+template <bool kShared>
 __global__ void absorbed_power_kernel(const DevCloud *__restrict__ dcl, int64_t n_cells,
                                       const long long *__restrict__ tally, int64_t stride,
                                       const double *__restrict__ e_unit, const double *__restrict__ w,
                                       int n_freq, const double *A_in, double *A_out)
 {
+    extern __shared__ double s_wf[];
+    if (kShared) {
+        for (int f = threadIdx.x; f < n_freq; f += blockDim.x) s_wf[f] = __dmul_rn(__ldg(w + f), __ldg(e_unit + f));
+        __syncthreads();
+    }
     const DevCloud &C = *dcl;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n_cells;
          c += (int64_t)gridDim.x * blockDim.x) {
@@ -42,10 +59,9 @@ __global__ void absorbed_power_kernel(const DevCloud *__restrict__ dcl, int64_t 
         const double rv = __dmul_rn((double)__ldg(C.rho + c), __ldg(C.volume + c));
         if (!(rv > 0.0)) { A_out[c] = a0; continue; }
         double acc = 0.0;
-        for (int f = 0; f < n_freq; ++f) {
-            const double wf = __dmul_rn(__ldg(w + f), __ldg(e_unit + f));
-            acc = __dadd_rn(acc, __dmul_rn(wf, (double)__ldg(tally + (int64_t)f * stride + c)));
-        }
+        for (int f = 0; f < n_freq; ++f)
+            acc = __dadd_rn(acc, __dmul_rn(wf_of(s_wf, w, e_unit, f, kShared),
+                                           (double)__ldg(tally + (int64_t)f * stride + c)));
         A_out[c] = __dadd_rn(a0, __ddiv_rn(acc, rv));
     }
 }
@@ -482,8 +498,12 @@ cudaError_t launch_absorbed_power(const DevCloud *dcl, int64_t n_cells, const in
                                   const double *e_unit, const double *w, int n_freq, const double *A_in,
                                   double *A_out, cudaStream_t s)
 {
-    absorbed_power_kernel<<<grid_for(n_cells, 256), 256, 0, s>>>(
-        dcl, n_cells, reinterpret_cast<const long long *>(tally), stride, e_unit, w, n_freq, A_in, A_out);
+    if (n_freq <= kWfShared)
+        absorbed_power_kernel<true><<<grid_for(n_cells, 256), 256, sizeof(double) * (size_t)n_freq, s>>>(
+            dcl, n_cells, reinterpret_cast<const long long *>(tally), stride, e_unit, w, n_freq, A_in, A_out);
+    else
+        absorbed_power_kernel<false><<<grid_for(n_cells, 256), 256, 0, s>>>(
+            dcl, n_cells, reinterpret_cast<const long long *>(tally), stride, e_unit, w, n_freq, A_in, A_out);
     return cudaGetLastError();
 }
 
