@@ -124,7 +124,7 @@ def cpu_baseline(per_freq: int = 300, cores: int | None = None):
         res = pool.map(_oracle_worker, chunks)
     wall = time.perf_counter() - t0
     steps = sum(r[0] for r in res)
-    return dict(value=steps / wall, unit="photon-cell steps/s", cores=cores, kind="oracle",
+    return dict(value=steps / wall, unit="photon-cell steps/s", cores=cores, kind="oracle", wall_s=wall,
                 sample=f"64 frequencies x {per_freq} background packages of the same 128^3 workload "
                        f"({steps} steps, {wall:.1f} s wall on {cores} processes)")
 
@@ -523,8 +523,9 @@ def run_reference(args):
             per_step.append(cb)
     v = statistics.mean(c["value"] for c in per_step)
     steps_per_pass = None
+    ms = 1e3 * statistics.mean(c["wall_s"] for c in per_step)       # wall time of one sample
     out = {"impl": "reference", "metric": "photon-cell steps/s", "value": v, "unit": "photon-cell steps/s",
-           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic", "config": {"workload": WORKLOAD, "steps_per_pass": steps_per_pass},
            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": v,
