@@ -37,8 +37,8 @@ WORKLOAD = "lognormal 128^3, 64 nu (3e11-3e15 Hz), 1e6 background packages/nu, H
 # DRAM bytes (read + write) per photon-cell step of trace_kernel from one ncu
 # capture (small case of the same workload, scaled by steps), valid only for
 # the kernel source it was taken on.
-TRACE_DRAM = {"source_sha1": "649dadf512fff626e8027269b9ac87f2b89dde10", "bytes_per_step": 2.2570,
-              "warp_instructions_per_step": 8.576,
+TRACE_DRAM = {"source_sha1": "b046d4a358f0ccee50fe3853d628366d8edbb00e", "bytes_per_step": 2.2889,
+              "warp_instructions_per_step": 8.577,
               "profile": "profiles/trace_kernel_lognormal128_8nu_1e6pkg_full.md"}
 # issue-rate peak: 4 warp-instructions per cycle per SM (4 schedulers)
 ISSUE_PER_SM_CYCLE = 4
@@ -385,6 +385,9 @@ def run_extra(args):
         w = I.config_c3()
     else:
         w = I.config_c5()
+    if args.packages != N_PACKAGES:                  # smaller launches for profiling captures
+        w.n_bg = [min(n, args.packages) for n in w.n_bg]
+        w.n_ps = [min(n, args.packages) for n in w.n_ps]
     t_gen = time.perf_counter() - t_gen
     nf = len(w.dust.nu)
     ctx = soc.Context(0, w.seed)
@@ -396,7 +399,7 @@ def run_extra(args):
         ids.append(cid)
     for ci, cl in enumerate(w.clouds):
         for src, npk in ((0, w.n_bg[ci]), (1, w.n_ps[ci])):
-            for f in range(nf):
+            for f in range(0, nf, args.freq_stride):
                 specs.append(dict(cloud=ids[ci], source=src, freq=f, n_packages=npk, tally_offset=off))
                 off += cl.n_cells
     stream = torch.cuda.Stream()
@@ -423,11 +426,11 @@ def run_extra(args):
     t_ok = int(tally.sum().item()) + int(st[:, 0].sum()) == int(st[:, 3].sum())
     out = {"metric": "photon-cell steps/s", "value": steps / (ms / 1e3), "unit": "photon-cell steps/s",
            "workload": args.workload, "ms_per_launch": ms, "steps_per_launch": steps, "items": len(specs),
-           "clouds": len(w.clouds), "cells": int(sum(c.n_cells for c in w.clouds)), "frequencies": nf,
+           "clouds": len(w.clouds), "cells": int(sum(c.n_cells for c in w.clouds)), "frequencies": len(range(0, nf, args.freq_stride)),
            "packages": int(sum(s["n_packages"] for s in specs)), "energy_conserved": bool(t_ok),
            "roofline_hbm_frac_12B": steps * BYTES_PER_STEP / (ms / 1e3) / 1e9 / _peaks()[0]["hbm_gbs"],
            "input_generation_s": t_gen}
-    if args.workload == "c3":
+    if args.workload == "c3" and not args.no_convergence:
         cl = w.clouds[0]
         out["convergence"] = {}
         Ts = {}
@@ -550,6 +553,8 @@ def main():
                     help="trace every k-th frequency only (profiling captures of a smaller case)")
     ap.add_argument("--packages", type=int, default=N_PACKAGES,
                     help="packages per frequency (smaller only for profiling captures)")
+    ap.add_argument("--no-convergence", action="store_true",
+                    help="c3: skip the time-to-convergence runs (profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -104,7 +104,7 @@ struct soc_ctx {
     int tpb = 256, bps = 4, chunk = 16, refill_min = 8, scatter_min = 8;   // autotuned on the 128^3 x 64 nu workload
     uint32_t max_steps = 10000000u;
     int sms = 0;
-    int occ[2][8] = {};           // resident blocks/SM per (build, threads/32), from soc_create
+    int occ[2][2][8] = {};        // resident blocks/SM per (regular grid, build, threads/32), from soc_create
 };
 
 namespace {
@@ -210,8 +210,9 @@ soc_status soc_create(soc_ctx **out, int device, uint64_t seed)
     ctx->device = device;
     ctx->seed = seed;
     cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
-    for (int v = 3; v <= 4; ++v)
-        for (int t = 32; t <= 256; t += 32) ctx->occ[v - 3][t / 32 - 1] = trace_block_limit(t, v);
+    for (int g = 0; g < 2; ++g)
+        for (int v = 3; v <= 4; ++v)
+            for (int t = 32; t <= 256; t += 32) ctx->occ[g][v - 3][t / 32 - 1] = trace_block_limit(t, v, g == 1);
     if (ctx->d_counter.alloc(1) != cudaSuccess || ctx->d_maxdT.alloc(1) != cudaSuccess) {
         delete ctx;
         return SOC_ERR_NOMEM;
@@ -646,10 +647,10 @@ static int32_t all_regular(const soc_ctx *ctx, const soc_batch_item *items, int 
 }
 
 // Launch shape of the tracer for `total` work indices.
-static void launch_geometry(soc_ctx *ctx, uint64_t total, int &grid_out, int &variant)
+static void launch_geometry(soc_ctx *ctx, uint64_t total, bool regular, int &grid_out, int &variant)
 {
     variant = ctx->bps >= 4 ? 4 : 3;
-    const int limit = std::max(1, ctx->occ[variant - 3][ctx->tpb / 32 - 1]);
+    const int limit = std::max(1, ctx->occ[regular ? 1 : 0][variant - 3][ctx->tpb / 32 - 1]);
     const int per_sm = ctx->bps > 0 ? std::min(ctx->bps, limit) : limit;
     const uint64_t warps_needed = (total + 31) / 32;
     int64_t grid = (int64_t)ctx->sms * per_sm;
@@ -704,7 +705,7 @@ soc_status soc_simulate_frequency_batch_ex(soc_ctx *ctx, const soc_batch_item *i
     P.hot = one_cloud(ctx, items, n_items);
     P.regular = all_regular(ctx, items, n_items);
     int grid = 1, variant = 3;
-    launch_geometry(ctx, total, grid, variant);
+    launch_geometry(ctx, total, P.regular != 0, grid, variant);
     CK(launch_trace(P, grid, ctx->tpb, variant, s), "trace launch");
     // the host copies above used pageable buffers: they are staged before return
     return SOC_OK;
@@ -772,7 +773,7 @@ soc_status soc_batch_launch(soc_ctx *ctx, int batch_id, int64_t *d_tally, int64_
     P.hot = b.hot;
     P.regular = b.regular;
     int grid = 1, variant = 3;
-    launch_geometry(ctx, b.total, grid, variant);
+    launch_geometry(ctx, b.total, P.regular != 0, grid, variant);
     CK(launch_trace(P, grid, ctx->tpb, variant, s), "trace launch");
     return SOC_OK;
 }
@@ -1397,7 +1398,7 @@ extern "C" soc_status soc_simulate_frequency_batch_noalloc(soc_ctx *ctx, const s
     P.hot = one_cloud(ctx, items, n_items);
     P.regular = all_regular(ctx, items, n_items);
     const int variant = ctx->bps >= 4 ? 4 : 3;
-    const int limit = trace_block_limit(ctx->tpb, variant);
+    const int limit = trace_block_limit(ctx->tpb, variant, P.regular != 0);
     const int per_sm = ctx->bps > 0 ? std::min(ctx->bps, limit) : limit;
     const uint64_t warps_needed = (total + 31) / 32;
     int64_t grid = (int64_t)ctx->sms * per_sm;

@@ -76,7 +76,7 @@ struct TraceParams {
 // variant: 3 or 4 = minimum resident 256-thread blocks per SM the kernel is
 // compiled for (register budget 80 or 64 per thread)
 cudaError_t launch_trace(const TraceParams &p, int grid, int block, int variant, cudaStream_t s);
-int trace_block_limit(int block, int variant);   // max resident blocks/SM
+int trace_block_limit(int block, int variant, bool regular);   // max resident blocks/SM
 
 // Surface-brightness map of one frequency seen along direction d (rays
 // travel along d); pixel (px, py) centre = c + ((px+0.5) - npx/2) pix e1 +

@@ -106,12 +106,31 @@ struct GlobalCloud {
     __device__ int32_t n_root() const { return (int32_t)C.n_root; }
 };
 
+// The ancestors of a lane's current cell (entry L: the index of the
+// ancestor at level L), in dynamic shared memory, kAncRows words per thread
+// (an odd count, so lanes reading the same level hit distinct banks): an
+// octree climb reads its parent from here (tens of cycles) rather than
+// following the parent link in global memory (an L2 round trip that the next
+// step waits on).  Levels 0 .. SOC_MAX_LEVELS-2 are enough, since only cells
+// above the deepest level have children.
+constexpr int kAncRows = SOC_MAX_LEVELS - 1;
+
+// Level of a cell from its side h = 2^-L (h only ever halves or doubles).
+__device__ __forceinline__ int level_of(float h)
+{
+    return 127 - (int)(__float_as_uint(h) >> 23);
+}
+
 // Follow child links to the leaf that contains the position; the upper child
-// is taken on an axis when 2x >= 1.
-__device__ __forceinline__ void descend(const uint32_t *__restrict__ cells, Pkg &p)
+// is taken on an axis when 2x >= 1.  kStack: push every cell left on the way
+// down onto the lane's ancestor rows.
+template <bool kStack = false>
+__device__ __forceinline__ void descend(const uint32_t *__restrict__ cells, Pkg &p, int32_t *anc = nullptr)
 {
     uint32_t w = __ldg(cells + p.cell);
+    int L = kStack ? level_of(p.h) : 0;
     while (w & kLinkBit) {
+        if (kStack) anc[L++] = p.cell;
         const float x2 = __fmul_rn(2.0f, p.x), y2 = __fmul_rn(2.0f, p.y), z2 = __fmul_rn(2.0f, p.z);
         const int bx = x2 >= 1.0f, by = y2 >= 1.0f, bz = z2 >= 1.0f;
         p.x = __fsub_rn(x2, (float)bx);
@@ -207,8 +226,10 @@ __device__ __forceinline__ int32_t root_cell(const DevCloud &C, int i, int j, in
 }
 
 // Emission (Sect. 2.2 background and point sources, Sect. 3.2 dust).  Returns
-// false for a dust package of zero weight (nothing to trace).
-__device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r, Pkg &p)
+// false for a dust package of zero weight (nothing to trace).  kStack: also
+// fill the lane's ancestor rows for the cell it starts in.
+template <bool kStack>
+__device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r, Pkg &p, int32_t *anc)
 {
     p.h = 1.0f;
     if (it.source == SOC_SRC_BACKGROUND) {
@@ -246,7 +267,7 @@ __device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r,
         p.dz = (a == 2) ? da : d2;
         p.W = (uint32_t)it.w0;
         p.cell = root_cell(C, p.ri, p.rj, p.rk);
-        descend(C.cell, p);
+        descend<kStack>(C.cell, p, anc);
         return true;
     }
     if (it.source == SOC_SRC_POINT) {
@@ -260,7 +281,7 @@ __device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r,
         isotropic(r, p);
         p.W = (uint32_t)it.w0;
         p.cell = root_cell(C, p.ri, p.rj, p.rk);
-        descend(C.cell, p);
+        descend<kStack>(C.cell, p, anc);
         return true;
     }
     // dust: n_per_cell packages from every leaf, or (weighted sampling) the
@@ -284,11 +305,15 @@ __device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r,
     int L = 0;
     while (L + 1 < C.n_levels && (int64_t)p.cell >= C.level_start[L + 1]) ++L;
     p.h = __uint_as_float((uint32_t)(127 - L) << 23);        // 2^-L
-    int32_t anc = p.cell;
-    while ((int64_t)anc >= C.n_root) anc = __ldg(C.parent + ((anc - C.n_root) >> 3));
-    p.ri = anc % C.nx;
-    p.rj = (anc / C.nx) % C.ny;
-    p.rk = anc / (C.nx * C.ny);
+    int32_t a = p.cell;
+    while ((int64_t)a >= C.n_root) {
+        a = __ldg(C.parent + ((a - C.n_root) >> 3));
+        if (kStack) anc[--L] = a;
+    }
+    const int32_t root = a;
+    p.ri = root % C.nx;
+    p.rj = (root / C.nx) % C.ny;
+    p.rk = root / (C.nx * C.ny);
     p.rho = __uint_as_float(__ldg(C.cell + p.cell));
     p.x = r.u();
     p.y = r.u();
@@ -300,10 +325,13 @@ __device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r,
 // Cross the face on axis `ax`: the package sits on it in the current frame.
 // Returns false when it leaves the root grid.  kRegular: every cell is a
 // root leaf (a one-level grid), so there is nothing to climb or descend.
-template <bool kRegular = false, class CC>
-__device__ bool cross_face(const CC &C, Pkg &p, int ax, bool up)
+// kStack: climbs pop the lane's ancestor rows and descents push them (the
+// same cells the parent links give).
+template <bool kRegular = false, bool kStack = false, class CC>
+__device__ bool cross_face(const CC &C, Pkg &p, int ax, bool up, int32_t *anc = nullptr)
 {
     const int32_t n_root = C.n_root();
+    int L = kStack ? level_of(p.h) : 0;
     while (!kRegular && p.cell >= n_root) {
         const int o = (p.cell - n_root) & 7;
         const int b = (o >> ax) & 1;
@@ -313,14 +341,14 @@ __device__ bool cross_face(const CC &C, Pkg &p, int ax, bool up)
             p.x = (ax == 0) ? v : p.x;
             p.y = (ax == 1) ? v : p.y;
             p.z = (ax == 2) ? v : p.z;
-            descend(C.cell(), p);
+            descend<kStack>(C.cell(), p, anc);
             return true;
         }
         p.x = __fmul_rn(__fadd_rn(p.x, (float)(o & 1)), 0.5f);
         p.y = __fmul_rn(__fadd_rn(p.y, (float)((o >> 1) & 1)), 0.5f);
         p.z = __fmul_rn(__fadd_rn(p.z, (float)((o >> 2) & 1)), 0.5f);
         p.h = __fmul_rn(p.h, 2.0f);
-        p.cell = __ldg(C.parent() + ((p.cell - n_root) >> 3));
+        p.cell = kStack ? anc[--L] : __ldg(C.parent() + ((p.cell - n_root) >> 3));
     }
     const int step = up ? 1 : -1;
     const int ri = p.ri + ((ax == 0) ? step : 0);
@@ -337,7 +365,7 @@ __device__ bool cross_face(const CC &C, Pkg &p, int ax, bool up)
     p.y = (ax == 1) ? v : p.y;
     p.z = (ax == 2) ? v : p.z;
     if (kRegular) p.rho = __uint_as_float(__ldg(C.cell() + p.cell));
-    else descend(C.cell(), p);
+    else descend<kStack>(C.cell(), p, anc);
     return true;
 }
 
@@ -358,7 +386,7 @@ __device__ __forceinline__ uint32_t float_to_w(float v)
 // One photon-cell step (one segment inside one leaf).
 template <bool kSelf, bool kRegular, class CC>
 __device__ __forceinline__ int step(const CC &C, Pkg &p, float kabs, float ksca,
-                                    unsigned long long *tally, const TraceParams &P)
+                                    unsigned long long *tally, const TraceParams &P, int32_t *anc)
 {
     if (p.steps >= P.max_steps) { p.pend += p.W; p.W = 0; return kCapped; }
     ++p.steps;
@@ -422,7 +450,7 @@ __device__ __forceinline__ int step(const CC &C, Pkg &p, float kabs, float ksca,
     p.x = (ax == 0) ? face : mx;
     p.y = (ax == 1) ? face : my;
     p.z = (ax == 2) ? face : mz;
-    if (!cross_face<kRegular>(C, p, ax, up)) return kEscaped;
+    if (!cross_face<kRegular, !kRegular>(C, p, ax, up, anc)) return kEscaped;
     return kContinue;
 }
 
@@ -463,6 +491,10 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
     __shared__ unsigned long long s_acc[256][3];     // escaped, steps, emitted
     unsigned long long *const acc = s_acc[threadIdx.x];
     acc[0] = acc[1] = acc[2] = 0;
+    // octree launches: the lane's ancestors (regular-grid launches get no
+    // dynamic shared memory and never touch them)
+    extern __shared__ int32_t s_anc[];
+    int32_t *const anc = s_anc + kAncRows * threadIdx.x;
     const DevCloud *C = P.clouds;             // the lane's cloud (used when !kOneCloud)
     int acc_item = -1;
     unsigned acc_cap = 0;
@@ -503,7 +535,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
                 r.init(P.seed, (uint32_t)IT.iteration, (uint32_t)IT.freq, pid, (uint32_t)IT.cloud,
                        (uint32_t)IT.source);
                 p.steps = 0; p.pend = 0; p.scat = false;
-                if (emit(*C, IT, pid, r, p)) {
+                if (emit<!kRegular>(*C, IT, pid, r, p, anc)) {
                     p.wf = ((p.W >> 20) ? (p.W >> 20) : 1u) |
                            ((kSelf && IT.source == SOC_SRC_DUST) ? kHomeBit : 0u);
                     set_inverse(p);
@@ -559,12 +591,12 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
             int res;
             if (kOneCloud) {
                 const ParamCloud pc{P.hot};
-                res = step<kSelf, kRegular>(pc, p, kabs, ksca, tally, P);
-                if (kRegular && res == kContinue && !p.scat) res = step<kSelf, kRegular>(pc, p, kabs, ksca, tally, P);
+                res = step<kSelf, kRegular>(pc, p, kabs, ksca, tally, P, anc);
+                if (kRegular && res == kContinue && !p.scat) res = step<kSelf, kRegular>(pc, p, kabs, ksca, tally, P, anc);
             } else {
                 const GlobalCloud gc{*C};
-                res = step<kSelf, kRegular>(gc, p, kabs, ksca, tally, P);
-                if (kRegular && res == kContinue && !p.scat) res = step<kSelf, kRegular>(gc, p, kabs, ksca, tally, P);
+                res = step<kSelf, kRegular>(gc, p, kabs, ksca, tally, P, anc);
+                if (kRegular && res == kContinue && !p.scat) res = step<kSelf, kRegular>(gc, p, kabs, ksca, tally, P, anc);
             }
             if (res != kContinue) {
                 if (p.pend) {
@@ -686,17 +718,24 @@ cudaError_t launch_map(const MapParams &m, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Dynamic shared memory of a tracer launch: the ancestor rows of octree launches.
+static size_t trace_smem(int block, bool regular)
+{
+    return regular ? 0 : (size_t)block * kAncRows * sizeof(int32_t);
+}
+
 template <int kMinBlocks, bool kRegular>
 static void launch_variant(const TraceParams &p, int grid, int block, cudaStream_t s)
 {
     // the self-counter logic (ALI) is compiled only into the variants that need it
     const bool one = p.hot.cell != nullptr;
+    const size_t sm = trace_smem(block, kRegular);
     if (p.self) {
-        if (one) trace_kernel<kMinBlocks, true, true, kRegular><<<grid, block, 0, s>>>(p);
-        else trace_kernel<kMinBlocks, true, false, kRegular><<<grid, block, 0, s>>>(p);
+        if (one) trace_kernel<kMinBlocks, true, true, kRegular><<<grid, block, sm, s>>>(p);
+        else trace_kernel<kMinBlocks, true, false, kRegular><<<grid, block, sm, s>>>(p);
     } else {
-        if (one) trace_kernel<kMinBlocks, false, true, kRegular><<<grid, block, 0, s>>>(p);
-        else trace_kernel<kMinBlocks, false, false, kRegular><<<grid, block, 0, s>>>(p);
+        if (one) trace_kernel<kMinBlocks, false, true, kRegular><<<grid, block, sm, s>>>(p);
+        else trace_kernel<kMinBlocks, false, false, kRegular><<<grid, block, sm, s>>>(p);
     }
 }
 
@@ -712,12 +751,19 @@ cudaError_t launch_trace(const TraceParams &p, int grid, int block, int variant,
     return cudaGetLastError();
 }
 
-int trace_block_limit(int block, int variant)
+int trace_block_limit(int block, int variant, bool regular)
 {
     int n = 0;
-    cudaError_t e = (variant == 4)
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<4, false, false, false>, block, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<3, false, false, false>, block, 0);
+    const size_t sm = trace_smem(block, regular);
+    cudaError_t e;
+    if (regular)
+        e = (variant == 4)
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<4, false, false, true>, block, sm)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<3, false, false, true>, block, sm);
+    else
+        e = (variant == 4)
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<4, false, false, false>, block, sm)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<3, false, false, false>, block, sm);
     if (e != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }
