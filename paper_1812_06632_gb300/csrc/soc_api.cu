@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 #include "soc_internal.h"
 
@@ -307,21 +308,84 @@ namespace {
 
 struct GridCheck {
     std::vector<int64_t> start;
-    std::vector<int32_t> child, parent;
-    int64_t n = 0, n_root = 0;
+    std::vector<int32_t> parent;
+    int64_t n = 0, n_root = 0, n_leaf = 0;
 };
 
-// Host validation of a grid description (paper Sect. 2.1.1 layout).
-soc_status validate_grid(soc_ctx *ctx, const soc_grid_desc *d, GridCheck &g)
+// One pass of the cell checks over cells [c0, c1): child links (from the
+// child array, or the paper's negative-density encoding), leaf densities,
+// link targets (the next level, octet-aligned) and one parent per octet
+// (claimed by compare-and-swap, so chunks can run concurrently).  With `word`
+// the cell words are written too.  Stops at the chunk's first bad cell.
+struct CellPass {
+    int64_t bad_cell = INT64_MAX;     // first bad cell of the chunk
+    std::string msg;
+    int64_t dup_octet = INT64_MAX;    // lowest octet claimed twice
+    int64_t leaves = 0;
+};
+
+void cell_pass(const soc_grid_desc *d, const std::vector<int64_t> &start, int64_t n_root, int64_t c0,
+               int64_t c1, int32_t *parent, uint32_t *word, CellPass &r)
+{
+    if (c0 >= c1) return;
+    int lv = 0;
+    while (c0 >= start[lv + 1]) ++lv;
+    char buf[160];
+    for (int64_t c = c0; c < c1; ++c) {
+        while (c >= start[lv + 1]) ++lv;
+        const float rho = d->rho[c];
+        int32_t fc = -1;
+        if (d->first_child) {
+            fc = d->first_child[c] < 0 ? -1 : d->first_child[c];
+        } else if (rho < 0.0f) {
+            const float v = -rho;
+            if (!(v < 16777216.0f) || v != std::floor(v)) {
+                snprintf(buf, sizeof buf, "cell %lld: negative-density link %g not an exact index", (long long)c,
+                         (double)rho);
+                r.bad_cell = c; r.msg = buf;
+                return;
+            }
+            fc = (int32_t)v;
+        }
+        if (fc < 0) {
+            if (!std::isfinite(rho) || rho < 0.0f) {
+                snprintf(buf, sizeof buf, "leaf %lld has invalid density %g", (long long)c, (double)rho);
+                r.bad_cell = c; r.msg = buf;
+                return;
+            }
+            if (word) {
+                const float v = rho == 0.0f ? 0.0f : rho;          // no -0
+                memcpy(&word[c], &v, 4);
+            }
+            ++r.leaves;
+            continue;
+        }
+        if (lv + 1 >= d->n_levels || fc < start[lv + 1] || fc + 8 > start[lv + 2] || (fc - n_root) % 8 != 0) {
+            snprintf(buf, sizeof buf, "cell %lld (level %d): child link %d out of range", (long long)c, lv + 1, fc);
+            r.bad_cell = c; r.msg = buf;
+            return;
+        }
+        const int64_t k = (fc - n_root) / 8;
+        int32_t expect = -1;
+        if (!__atomic_compare_exchange_n(parent + k, &expect, (int32_t)c, false, __ATOMIC_RELAXED,
+                                         __ATOMIC_RELAXED))
+            r.dup_octet = std::min(r.dup_octet, k);
+        if (word) word[c] = kLinkBit | (uint32_t)fc;
+    }
+}
+
+// Checks of a grid description that need no pass over its cells; fills the
+// level starts (with a sentinel entry n at the end).
+soc_status grid_header(soc_ctx *ctx, const soc_grid_desc *d, std::vector<int64_t> &start, int64_t &n_root)
 {
     if (!d || !d->rho || !d->cells_per_level) return fail(ctx, SOC_ERR_ARG, "null argument");
     if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(ctx, SOC_ERR_ARG, "root grid must be >= 1 cell per axis");
     if (d->n_levels < 1 || d->n_levels > SOC_MAX_LEVELS) return fail(ctx, SOC_ERR_ARG, "n_levels out of [1, 16]");
     if (!(d->root_cell_size > 0.0) || !std::isfinite(d->root_cell_size))
         return fail(ctx, SOC_ERR_ARG, "root_cell_size must be positive");
-    const int64_t n_root = (int64_t)d->nx * d->ny * d->nz;
+    n_root = (int64_t)d->nx * d->ny * d->nz;
     if (n_root >= (int64_t)1 << 31) return fail(ctx, SOC_ERR_GRID, "more than 2^31 - 1 root cells");
-    std::vector<int64_t> start(d->n_levels + 1, 0);
+    start.assign(d->n_levels + 2, 0);
     for (int L = 0; L < d->n_levels; ++L) {
         const int64_t c = d->cells_per_level[L];
         if (c < 0 || (L == 0 && c != n_root) || (L > 0 && c % 8 != 0))
@@ -329,48 +393,65 @@ soc_status validate_grid(soc_ctx *ctx, const soc_grid_desc *d, GridCheck &g)
         start[L + 1] = start[L] + c;
         if (start[L + 1] >= (int64_t)1 << 31) return fail(ctx, SOC_ERR_GRID, "more than 2^31 - 1 cells");
     }
+    start[d->n_levels + 1] = start[d->n_levels];
+    return SOC_OK;
+}
+
+// Host validation of a grid description (paper Sect. 2.1.1 layout) after
+// grid_header; with `word` and `leaf` (room for every cell) it also writes
+// the cell words and the leaf list.  Large grids are split over host
+// threads; the error reported is the one at the lowest cell index, then at
+// the lowest octet.
+soc_status grid_cells(soc_ctx *ctx, const soc_grid_desc *d, std::vector<int64_t> &start, int64_t n_root,
+                      GridCheck &g, uint32_t *word = nullptr, int32_t *leaf = nullptr)
+{
     const int64_t n = start[d->n_levels];
     const int64_t n_oct = (n - n_root) / 8;
-    std::vector<int32_t> child(n, -1);
-    for (int64_t c = 0; c < n; ++c) {
-        if (d->first_child) {
-            child[c] = d->first_child[c] < 0 ? -1 : d->first_child[c];
-        } else if (d->rho[c] < 0.0f) {
-            const float v = -d->rho[c];
-            if (!(v < 16777216.0f) || v != std::floor(v))
-                return fail(ctx, SOC_ERR_GRID, "cell %lld: negative-density link %g not an exact index",
-                            (long long)c, (double)d->rho[c]);
-            child[c] = (int32_t)v;
-        }
-    }
     std::vector<int32_t> parent(n_oct, -1);
-    int lv = 0;
-    for (int64_t c = 0; c < n; ++c) {
-        while (c >= start[lv + 1]) ++lv;
-        const int32_t fc = child[c];
-        if (fc < 0) {
-            const float r = d->rho[c];
-            if (!std::isfinite(r) || r < 0.0f)
-                return fail(ctx, SOC_ERR_GRID, "leaf %lld has invalid density %g", (long long)c, (double)r);
-            continue;
-        }
-        if (lv + 1 >= d->n_levels || fc < start[lv + 1] || fc + 8 > start[lv + 2] || (fc - n_root) % 8 != 0)
-            return fail(ctx, SOC_ERR_GRID, "cell %lld (level %d): child link %d out of range", (long long)c,
-                        lv + 1, fc);
-        const int64_t k = (fc - n_root) / 8;
-        if (parent[k] != -1) return fail(ctx, SOC_ERR_GRID, "octet %lld has two parents", (long long)k);
-        parent[k] = (int32_t)c;
+    unsigned hw = std::thread::hardware_concurrency();
+    const int n_thr = n >= ((int64_t)1 << 18) ? (int)std::max(1u, std::min(hw, 16u)) : 1;
+    std::vector<CellPass> part(n_thr);
+    auto bounds = [&](int t) { return std::make_pair(n * t / n_thr, n * (t + 1) / n_thr); };
+    auto run = [&](auto &&fn) {
+        if (n_thr == 1) { fn(0); return; }
+        std::vector<std::thread> th;
+        th.reserve(n_thr);
+        for (int t = 0; t < n_thr; ++t) th.emplace_back(fn, t);
+        for (auto &x : th) x.join();
+    };
+    run([&](int t) {
+        const auto b = bounds(t);
+        cell_pass(d, start, n_root, b.first, b.second, parent.data(), word, part[t]);
+    });
+    int64_t dup = INT64_MAX;
+    for (const CellPass &r : part) {
+        if (r.bad_cell != INT64_MAX) return fail(ctx, SOC_ERR_GRID, "%s", r.msg.c_str());
+        dup = std::min(dup, r.dup_octet);
     }
+    if (dup != INT64_MAX) return fail(ctx, SOC_ERR_GRID, "octet %lld has two parents", (long long)dup);
     for (int64_t k = 0; k < n_oct; ++k) {
         if (parent[k] < 0) return fail(ctx, SOC_ERR_GRID, "octet %lld has no parent", (long long)k);
         if (d->parent && d->parent[k] != parent[k])
             return fail(ctx, SOC_ERR_GRID, "parent[%lld] = %d, links say %d", (long long)k, d->parent[k], parent[k]);
     }
+    int64_t n_leaf = 0;
+    for (const CellPass &r : part) n_leaf += r.leaves;
+    if (word && leaf) {                    // leaf list: each chunk from its offset, in cell order
+        std::vector<int64_t> off(n_thr, 0);
+        for (int t = 1; t < n_thr; ++t) off[t] = off[t - 1] + part[t - 1].leaves;
+        run([&](int t) {
+            const auto b = bounds(t);
+            int32_t *out = leaf + off[t];
+            for (int64_t c = b.first; c < b.second; ++c)
+                if (!(word[c] & kLinkBit)) *out++ = (int32_t)c;
+        });
+    }
+    start.pop_back();
     g.start.swap(start);
-    g.child.swap(child);
     g.parent.swap(parent);
     g.n = n;
     g.n_root = n_root;
+    g.n_leaf = n_leaf;
     return SOC_OK;
 }
 
@@ -382,7 +463,10 @@ extern "C" soc_status soc_grid_validate(const soc_grid_desc *desc, char *msg, in
 {
     soc_ctx tmp;
     GridCheck g;
-    soc_status st = validate_grid(&tmp, desc, g);
+    std::vector<int64_t> start;
+    int64_t n_root = 0;
+    soc_status st = grid_header(&tmp, desc, start, n_root);
+    if (st == SOC_OK) st = grid_cells(&tmp, desc, start, n_root, g);
     if (msg && msg_len > 0) {
         strncpy(msg, st == SOC_OK ? "ok" : tmp.err.c_str(), (size_t)msg_len - 1);
         msg[msg_len - 1] = '\0';
@@ -394,49 +478,43 @@ extern "C" soc_status soc_grid_upload(soc_ctx *ctx, const soc_grid_desc *d, int 
 {
     if (!ctx || !cloud_id) return fail(ctx, SOC_ERR_ARG, "null argument");
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    GridCheck g;
-    soc_status vs = validate_grid(ctx, d, g);
-    if (vs != SOC_OK) return vs;
-    const int64_t n = g.n, n_root = g.n_root, n_oct = (int64_t)g.parent.size();
-    std::vector<int64_t> &start = g.start;
-    std::vector<int32_t> &child = g.child;
-    std::vector<int32_t> &parent = g.parent;
-    // cell words (tagged links or FP32 densities, -0 stored as +0) are built
-    // in pinned memory and copied once; densities and volumes are derived
-    // from them on the device
-    if (ctx->h_stage_n < (size_t)n) {
+    std::vector<int64_t> lstart;
+    int64_t n_root0 = 0;
+    soc_status hs = grid_header(ctx, d, lstart, n_root0);
+    if (hs != SOC_OK) return hs;
+    // cell words (tagged links or FP32 densities, -0 stored as +0) and the
+    // leaf list are written in pinned memory by the validating pass and
+    // copied once each; densities and volumes are derived on the device
+    const int64_t n_max = lstart[d->n_levels];
+    if (ctx->h_stage_n < (size_t)n_max) {
         if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
         ctx->h_stage = nullptr;
         ctx->h_stage_n = 0;
-        CK(cudaMallocHost(&ctx->h_stage, sizeof(uint32_t) * (size_t)std::max<int64_t>(n, 1)), "pinned staging");
-        ctx->h_stage_n = (size_t)n;
+        CK(cudaMallocHost(&ctx->h_stage, 2 * sizeof(uint32_t) * (size_t)std::max<int64_t>(n_max, 1)),
+           "pinned staging");
+        ctx->h_stage_n = (size_t)n_max;
     }
     uint32_t *word = ctx->h_stage;
-    std::vector<int32_t> leaf;
-    leaf.reserve(n);
-    for (int64_t c = 0; c < n; ++c) {
-        if (child[c] >= 0) {
-            word[c] = kLinkBit | (uint32_t)child[c];
-        } else {
-            const float r = d->rho[c] == 0.0f ? 0.0f : d->rho[c];      // no -0
-            memcpy(&word[c], &r, 4);
-            leaf.push_back((int32_t)c);
-        }
-    }
+    int32_t *leaf = reinterpret_cast<int32_t *>(ctx->h_stage + ctx->h_stage_n);
+    GridCheck g;
+    soc_status vs = grid_cells(ctx, d, lstart, n_root0, g, word, leaf);
+    if (vs != SOC_OK) return vs;
+    const int64_t n = g.n, n_root = g.n_root, n_oct = (int64_t)g.parent.size(), n_leaf = g.n_leaf;
+    std::vector<int64_t> &start = g.start;
     CloudHost *cl = new (std::nothrow) CloudHost();
     if (!cl) return fail(ctx, SOC_ERR_NOMEM, "host allocation");
     cl->nx = d->nx; cl->ny = d->ny; cl->nz = d->nz; cl->n_levels = d->n_levels;
-    cl->n_cells = n; cl->n_root = n_root; cl->n_leaf = (int64_t)leaf.size(); cl->level_start = start;
+    cl->n_cells = n; cl->n_root = n_root; cl->n_leaf = n_leaf; cl->level_start = start;
     cl->ell = d->root_cell_size;
     const double ell3 = (d->root_cell_size * d->root_cell_size) * d->root_cell_size;
     cudaError_t e = cudaSuccess;
     if ((e = cl->cell.alloc(n)) == cudaSuccess && (e = cl->parent.alloc(n_oct)) == cudaSuccess &&
-        (e = cl->leaf.alloc(leaf.size())) == cudaSuccess && (e = cl->rho.alloc(n)) == cudaSuccess &&
+        (e = cl->leaf.alloc(n_leaf)) == cudaSuccess && (e = cl->rho.alloc(n)) == cudaSuccess &&
         (e = cl->volume.alloc(n)) == cudaSuccess && (e = ctx->d_level_start.alloc(start.size())) == cudaSuccess &&
         (e = cudaMemcpy(cl->cell.p, word, 4 * n, cudaMemcpyHostToDevice)) == cudaSuccess &&
         (n_oct == 0 ||
-         (e = cudaMemcpy(cl->parent.p, parent.data(), 4 * n_oct, cudaMemcpyHostToDevice)) == cudaSuccess) &&
-        (e = cudaMemcpy(cl->leaf.p, leaf.data(), 4 * leaf.size(), cudaMemcpyHostToDevice)) == cudaSuccess &&
+         (e = cudaMemcpy(cl->parent.p, g.parent.data(), 4 * n_oct, cudaMemcpyHostToDevice)) == cudaSuccess) &&
+        (e = cudaMemcpy(cl->leaf.p, leaf, 4 * n_leaf, cudaMemcpyHostToDevice)) == cudaSuccess &&
         (e = cudaMemcpy(ctx->d_level_start.p, start.data(), 8 * start.size(), cudaMemcpyHostToDevice)) ==
             cudaSuccess &&
         (e = launch_cell_init(cl->cell.p, n, ctx->d_level_start.p, d->n_levels, ell3, cl->rho.p, cl->volume.p, 0)) ==

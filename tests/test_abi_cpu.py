@@ -80,6 +80,50 @@ def test_malformed_grids_rejected(libsoc, case):
     assert msg and msg != "ok"
 
 
+def test_large_grid_checks_report_the_first_bad_cell(libsoc):
+    """Grids of 2^18 cells and more are checked by several host threads: the
+    error reported is still the one at the lowest cell index, and a planted
+    error is found in whichever chunk it falls."""
+    n = 64
+    rho = np.random.default_rng(0).uniform(0.5, 2.0, n ** 3).astype(np.float32)
+    reg = I.regular(rho.reshape(n, n, n))
+    assert _v(libsoc, reg)[0] == 0
+    for bad in (0, 70_000, n ** 3 - 1):
+        r = reg.rho.copy()
+        r[bad] = np.nan
+        st, msg = _v(libsoc, reg, rho=r)
+        assert st == -2 and f"leaf {bad} " in msg, msg
+    r = reg.rho.copy()
+    r[250_000] = -1.0
+    r[90_000] = np.inf
+    st, msg = _v(libsoc, reg, rho=r)
+    assert st == -2 and "leaf 90000 " in msg, msg
+
+
+def test_large_octree_checks(libsoc):
+    """An octree of more than 2^18 cells (threaded checks): valid as built;
+    two parents for one octet, an orphan octet and a bad leaf are found."""
+    oc = I.config_c3(root_n=32, max_refine=2, threshold=2.0).clouds[0]
+    assert oc.n_cells >= 1 << 18 and oc.n_levels == 3
+    assert _v(libsoc, oc)[0] == 0
+    assert _v(libsoc, oc, rho=oc.paper_encoding(), first_child=None, parent=None)[0] == 0
+    refined = np.nonzero(oc.child >= 0)[0]
+    leaves = np.nonzero(oc.child < 0)[0]
+    root_refined = refined[refined < oc.nx * oc.ny * oc.nz]     # two far-apart cells of one level
+    child = oc.child.copy()
+    child[root_refined[-1]] = child[root_refined[0]]
+    st, msg = _v(libsoc, oc, first_child=child, parent=None)
+    assert st == -2 and "two parents" in msg, msg
+    child = oc.child.copy()
+    child[refined[len(refined) // 2]] = -1
+    st, msg = _v(libsoc, oc, first_child=child, parent=None)
+    assert st == -2, msg
+    rho = oc.rho.copy()
+    rho[leaves[-1]] = -3.0
+    st, msg = _v(libsoc, oc, rho=rho)
+    assert st == -2 and f"leaf {leaves[-1]} " in msg, msg
+
+
 def test_weight_unit_agrees_across_header_binding_and_oracle(libsoc):
     """The fixed-point unit of one package is the same constant in the C-ABI
     header, the binding, the test helpers and the oracle (C and FP64 parts)."""
