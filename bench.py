@@ -38,7 +38,7 @@ WORKLOAD = "lognormal 128^3, 64 nu (3e11-3e15 Hz), 1e6 background packages/nu, H
 # capture (small case of the same workload, scaled by steps), valid only for
 # the kernel source it was taken on.
 TRACE_DRAM = {"source_sha1": "b046d4a358f0ccee50fe3853d628366d8edbb00e", "bytes_per_step": 2.2889,
-              "warp_instructions_per_step": 8.577,
+              "warp_instructions_per_step": 8.577, "l2_bytes_per_step": 74.15,
               "profile": "profiles/trace_kernel_lognormal128_8nu_1e6pkg_full.md"}
 # issue-rate peak: 4 warp-instructions per cycle per SM (4 schedulers)
 ISSUE_PER_SM_CYCLE = 4
@@ -69,6 +69,26 @@ def _issue_roofline(steps, ms, sms, clock_mhz):
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "warp-instructions/s",
             "frac": achieved / peak, "instructions_per_unit": TRACE_DRAM["warp_instructions_per_step"],
             "peak_source": f"4 issue slots/cycle/SM x {sms} SMs x {clock_mhz:.0f} MHz (median SM clock in the run)"}
+
+
+def l2_bandwidth(mib: int = 32, iters: int = 200):
+    """L2 read bandwidth (GB/s) of this GPU: a float32 vector of `mib` MiB,
+    resident in L2 after one pass, summed `iters` times back to back and timed
+    with CUDA events (a read-only stream; the result is kept live)."""
+    import torch
+    x = torch.ones(mib << 18, dtype=torch.float32, device="cuda")
+    acc = torch.zeros((), dtype=torch.float32, device="cuda")
+    for _ in range(5):
+        acc += x.sum()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(iters):
+        acc += x.sum()
+    b.record()
+    torch.cuda.synchronize()
+    assert acc.item() > 0
+    return x.numel() * 4 * iters / (a.elapsed_time(b) / 1e3) / 1e9
 
 
 def _peaks():
@@ -124,7 +144,11 @@ def cpu_baseline(per_freq: int = 300, cores: int | None = None):
         res = pool.map(_oracle_worker, chunks)
     wall = time.perf_counter() - t0
     steps = sum(r[0] for r in res)
+    # one core's rate: each process timed its own single-threaded loop (all
+    # of them running at once)
+    per_core = statistics.mean(r[0] / r[1] for r in res if r[1] > 0)
     return dict(value=steps / wall, unit="photon-cell steps/s", cores=cores, kind="oracle", wall_s=wall,
+                per_core_value=per_core,
                 sample=f"64 frequencies x {per_freq} background packages of the same 128^3 workload "
                        f"({steps} steps, {wall:.1f} s wall on {cores} processes)")
 
@@ -340,6 +364,14 @@ def run_gpu(args):
                 "kernel": "trace_kernel", "peak_source": f"{peak_kind} hbm_gbs (copy)",
                 "bytes_per_unit": BYTES_PER_STEP, "units_per_launch": steps_per_step,
                 "ms_per_launch": ms_trace, "launch_includes": "counter reset (1.07 GB memset) + tracer"}
+    # the same algorithmic bytes against this GPU's L2 read bandwidth, and the
+    # L2 sector traffic ncu counted for this kernel (32-byte sectors, so a
+    # 4-byte cell-word miss or an 8-byte counter update moves a whole sector)
+    l2 = l2_bandwidth()
+    roofline["l2"] = {"achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
+                      "peak_source": "bench.l2_bandwidth (32 MiB float32 sum, L2-resident)",
+                      "lts_bytes_per_unit": (TRACE_DRAM["l2_bytes_per_step"]
+                                             if TRACE_DRAM["source_sha1"] == _trace_source_sha1() else None)}
     out = {
         "metric": "photon-cell steps/s", "value": value, "unit": "photon-cell steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all,

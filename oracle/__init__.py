@@ -6,11 +6,15 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 product path (``paper_1812_06632_gb300``) never imports, links or executes
 anything here, and this package imports nothing from the product path.
 
-Two parts:
+Three parts:
 
 * ``soc_oracle.c`` (built with gcc into ``liboracle.so`` by :func:`build`):
   the tracer in the FP32 contract, one package at a time.  Its integer
   counters are what the CUDA tracer must reproduce bit for bit.
+* ``soc_oracle64.c`` (``liboracle64.so``, :func:`trace64`): the same Monte
+  Carlo, on the same random numbers, in FP64 with libm exp/log and real
+  weights; it states how far the FP32 contract's counters are from an FP64
+  run.
 * :mod:`oracle.physics`: FP64 NumPy/SciPy definitions of the Planck law, the
   frequency quadrature, the normalisation of the counters to absorbed power
   and the equilibrium temperature (root-finding).
@@ -26,26 +30,35 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "soc_oracle.c")
+_SRC64 = os.path.join(_HERE, "soc_oracle64.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_LIB64_PATH = os.path.join(_HERE, "_build", "liboracle64.so")
 _lock = threading.Lock()
 _lib = None
+_lib64 = None
 
 SRC_BACKGROUND, SRC_POINT, SRC_DUST = 0, 1, 2
 W_UNIT = 1 << 31          # fixed-point units of one package's initial weight
 
 
-def build(force: bool = False) -> str:
-    """Compile soc_oracle.c with gcc (FP32 contract flags).  Returns the path."""
-    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+def _gcc(out: str, srcs, force: bool) -> str:
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if (not force and os.path.exists(out)
+            and all(os.path.getmtime(out) >= os.path.getmtime(s) for s in srcs)):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-           "-fno-unsafe-math-optimizations", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+           "-fno-unsafe-math-optimizations", "-fPIC", "-shared", "-o", tmp, *srcs, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile soc_oracle.c (FP32 contract flags: one rounding per written
+    operation) and the FP64 oracle with gcc.  Returns the FP32 oracle's path."""
+    _gcc(_LIB64_PATH, [_SRC64, _SRC], force)     # the FP64 tracer draws through the same Philox
+    return _gcc(_LIB_PATH, [_SRC], force)
 
 
 class _Grid(C.Structure):
@@ -89,6 +102,22 @@ def lib():
                                                  C.c_uint32, P, C.POINTER(_Stats)]
             _lib.oracle_trace_pencil.restype = C.c_uint32
         return _lib
+
+
+class _Stats64(C.Structure):
+    _fields_ = [("escaped", C.c_double), ("capped", C.c_int64),
+                ("steps", C.c_int64), ("emitted", C.c_double)]
+
+
+def lib64():
+    global _lib64
+    with _lock:
+        if _lib64 is None:
+            build()
+            _lib64 = C.CDLL(_LIB64_PATH)
+            _lib64.oracle64_trace.argtypes = [C.POINTER(_Grid), C.POINTER(_Item), C.c_uint32, C.c_uint32,
+                                              C.c_void_p, C.POINTER(_Stats64), C.c_void_p]
+        return _lib64
 
 
 def _ptr(a):
@@ -204,6 +233,35 @@ def trace(grid: Grid, *, source: int, kabs: float, ksca: float, g: float = 0.0,
     gc = grid._c()
     lib().oracle_trace(C.byref(gc), C.byref(it), pid_lo, pid_lo + n_packages,
                        _ptr(tally), C.byref(st), _ptr(steps), _ptr(self_tally))
+    stats = dict(escaped=st.escaped, capped=st.capped, steps=st.steps, emitted=st.emitted)
+    return tally, stats, steps
+
+
+def trace64(grid: Grid, *, source: int, kabs: float, ksca: float, g: float = 0.0,
+            seed: int = 1, freq: int = 0, iteration: int = 0, cloud: int = 0,
+            pid_lo: int = 0, n_packages: int, w0: int = W_UNIT, max_steps: int = 10_000_000,
+            ps_pos=None, ps_cdf=None, n_per_cell: int = 1, leaf=None, dust_w=None,
+            tally=None, want_steps: bool = False, dust_prefix=None):
+    """The FP64 oracle on the same item and packages as :func:`trace` (same
+    arguments; the opacities and g are taken as the same FP32 values).
+    Returns (tally float64[n_cells] in weight units, stats dict with float
+    escaped/emitted, per-package steps or None)."""
+    if tally is None:
+        tally = np.zeros(grid.n_cells, np.float64)
+    ps_pos_a = None if ps_pos is None else np.ascontiguousarray(ps_pos, np.float32).ravel()
+    ps_cdf_a = None if ps_cdf is None else np.ascontiguousarray(ps_cdf, np.float32)
+    leaf_a = None if leaf is None else np.ascontiguousarray(leaf, np.int32)
+    dust_a = None if dust_w is None else np.ascontiguousarray(dust_w, np.uint64)
+    pref_a = None if dust_prefix is None else np.ascontiguousarray(dust_prefix, np.uint64)
+    it = _Item(source, freq, iteration, cloud, seed & (2**64 - 1),
+               np.float32(kabs), np.float32(ksca), np.float32(g), w0, max_steps,
+               0 if ps_cdf_a is None else ps_cdf_a.size, _ptr(ps_pos_a), _ptr(ps_cdf_a),
+               n_per_cell, 0 if leaf_a is None else leaf_a.size, _ptr(leaf_a), _ptr(dust_a), _ptr(pref_a))
+    st = _Stats64()
+    steps = np.zeros(n_packages, np.uint32) if want_steps else None
+    gc = grid._c()
+    lib64().oracle64_trace(C.byref(gc), C.byref(it), pid_lo, pid_lo + n_packages, _ptr(tally), C.byref(st),
+                           _ptr(steps))
     stats = dict(escaped=st.escaped, capped=st.capped, steps=st.steps, emitted=st.emitted)
     return tally, stats, steps
 
