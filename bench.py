@@ -114,7 +114,19 @@ def _oracle_worker(args):
     for f in freqs:
         _, st, _ = oracle_item(w, 0, dict(source=0, freq=f, pid_offset=pid_lo, n_packages=n))
         steps += st["steps"]
-    return steps, time.perf_counter() - t0
+    t_fp32 = time.perf_counter() - t0
+    # the FP64 oracle on an eighth of the same packages, timed separately
+    import oracle
+    from parity_helpers import kappa_root, oracle_grid
+    G = oracle_grid(w.clouds[0])
+    steps64 = 0
+    t0 = time.perf_counter()
+    for f in freqs:
+        ka, ks = kappa_root(w.dust, f, w.clouds[0].ell)
+        _, st, _ = oracle.trace64(G, source=0, kabs=ka, ksca=ks, g=np.float32(w.dust.g[f]), seed=w.seed,
+                                  freq=f, pid_lo=pid_lo, n_packages=max(n // 8, 1))
+        steps64 += st["steps"]
+    return steps, t_fp32, steps64, time.perf_counter() - t0
 
 
 _W = None
@@ -142,15 +154,20 @@ def cpu_baseline(per_freq: int = 300, cores: int | None = None):
         pool.map(_warm, range(cores))
         t0 = time.perf_counter()
         res = pool.map(_oracle_worker, chunks)
-    wall = time.perf_counter() - t0
+    # the FP32 oracle's wall time: the slowest process's loop (each process
+    # then times the FP64 oracle on its own)
+    wall = max(r[1] for r in res)
     steps = sum(r[0] for r in res)
     # one core's rate: each process timed its own single-threaded loop (all
     # of them running at once)
     per_core = statistics.mean(r[0] / r[1] for r in res if r[1] > 0)
+    fp64 = sum(r[2] for r in res) / max(r[3] for r in res)
     return dict(value=steps / wall, unit="photon-cell steps/s", cores=cores, kind="oracle", wall_s=wall,
-                per_core_value=per_core,
+                per_core_value=per_core, fp64_oracle_value=fp64,
                 sample=f"64 frequencies x {per_freq} background packages of the same 128^3 workload "
-                       f"({steps} steps, {wall:.1f} s wall on {cores} processes)")
+                       f"({steps} steps, {wall:.1f} s wall on {cores} processes); per_core_value: one "
+                       f"process's own rate; fp64_oracle_value: the FP64 oracle on an eighth of the "
+                       f"same packages, all processes")
 
 
 def _warm(_):
@@ -159,6 +176,7 @@ def _warm(_):
     _workload_cache(I)
     import oracle
     oracle.lib()
+    oracle.lib64()
     return 0
 
 
