@@ -554,6 +554,19 @@ soc_status soc_set_scatter_batch(soc_ctx *ctx, int min_lanes);
  * their weight deposited and counted in stats[1]. */
 soc_status soc_set_max_steps(soc_ctx *ctx, uint32_t max_steps);
 
+/* ------------------------------------------------------------------------
+ * soc_probe_read -- measurement helper for the tracer's roofline (not part
+ * of the method): one launch that reads the device buffer d_buf of `bytes`
+ * bytes `reps` times over with 16-byte loads that bypass L1, on `stream`
+ * (cudaStream_t or NULL).  A buffer that fits in L2 is read from L2 after
+ * the first pass, so (bytes x reps) / launch time is the L2 read bandwidth;
+ * a larger one measures HBM.  The caller times it (CUDA events on the same
+ * stream).  d_buf: device pointer, 16-byte aligned; bytes: a positive
+ * multiple of 16; reps >= 1; otherwise SOC_ERR_ARG.  The contents are not
+ * changed.
+ * ------------------------------------------------------------------------ */
+soc_status soc_probe_read(soc_ctx *ctx, const void *d_buf, uint64_t bytes, int32_t reps, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,6 +14,13 @@
 
 using namespace soc;
 
+namespace soc {
+// Read-bandwidth probe (measurement only, soc_temperature.cu): `reps` passes
+// of 16-byte loads over buf.
+cudaError_t launch_probe_read(const void *buf, uint64_t bytes, int reps, int sms, unsigned long long *sink,
+                              cudaStream_t s);
+}
+
 namespace {
 
 constexpr double kPi = 3.141592653589793;
@@ -294,6 +301,16 @@ soc_status soc_set_scatter_batch(soc_ctx *ctx, int min_lanes)
     if (!ctx) return SOC_ERR_ARG;
     if (min_lanes < 1 || min_lanes > 32) return fail(ctx, SOC_ERR_ARG, "min_lanes must be in [1, 32]");
     ctx->scatter_min = min_lanes;
+    return SOC_OK;
+}
+
+soc_status soc_probe_read(soc_ctx *ctx, const void *d_buf, uint64_t bytes, int32_t reps, void *stream)
+{
+    if (!ctx) return SOC_ERR_ARG;
+    if (!d_buf || bytes == 0 || bytes % 16 || reinterpret_cast<uintptr_t>(d_buf) % 16 || reps < 1)
+        return fail(ctx, SOC_ERR_ARG, "probe buffer must be 16-byte aligned, a positive multiple of 16 bytes");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    CK(launch_probe_read(d_buf, bytes, reps, ctx->sms, nullptr, static_cast<cudaStream_t>(stream)), "probe launch");
     return SOC_OK;
 }
 

