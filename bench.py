@@ -581,8 +581,9 @@ def run_reference(args):
     v = statistics.mean(c["value"] for c in per_step)
     steps_per_pass = None
     ms = 1e3 * statistics.mean(c["wall_s"] for c in per_step)       # wall time of one sample
+    # the oracle runs on the host cores of rank 0 alone, whatever the launch's world size
     out = {"impl": "reference", "metric": "photon-cell steps/s", "value": v, "unit": "photon-cell steps/s",
-           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "n_gpus": int(os.environ.get("WORLD_SIZE", args.gpus)), "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic", "config": {"workload": WORKLOAD, "steps_per_pass": steps_per_pass},
            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": v,
