@@ -42,6 +42,14 @@ TRACE_DRAM = {"source_sha1": "b046d4a358f0ccee50fe3853d628366d8edbb00e", "bytes_
               "profile": "profiles/trace_kernel_lognormal128_8nu_1e6pkg_full.md"}
 # issue-rate peak: 4 warp-instructions per cycle per SM (4 schedulers)
 ISSUE_PER_SM_CYCLE = 4
+# FP32 operations one photon-cell step of the method needs (no scattering),
+# counted from the FP32 contract: exit distances 3 x (sub, mul) + 3 compares;
+# scattering depth (rho ksca) h, x s and 2 compares; absorption depth
+# ((rho kabs) h) sp and 1 compare; 1 - e^-tau ~20 (reduction + degree-7
+# polynomial, or the short series); deposit float(W) x q and its rounding 3;
+# tau_f update 1; the move 3 x (mul, add, min, max)
+FP32_OPS_PER_STEP = 54
+FP32_LANES_PER_SM = 128
 
 
 def _trace_source_sha1():
@@ -412,6 +420,12 @@ def run_gpu(args):
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         mhz = (out["clocks"] or {}).get("sm_mhz")
         out["roofline_alu"] = _issue_roofline(steps_per_step, ms_trace, sms, mhz)
+        if mhz:
+            fp32 = FP32_OPS_PER_STEP * steps_per_step / (ms_trace / 1e3)
+            peak32 = FP32_LANES_PER_SM * sms * mhz * 1e6
+            out["roofline"]["fp32"] = {"achieved": fp32, "peak": peak32, "unit": "FP32 op/s", "frac": fp32 / peak32,
+                                       "ops_per_unit": FP32_OPS_PER_STEP,
+                                       "peak_source": f"128 FP32 lanes/SM x {sms} SMs x {mhz:.0f} MHz"}
         print(json.dumps(out), flush=True)
     ctx.graph_destroy(g_trace)
     ctx.graph_destroy(g_temp)
