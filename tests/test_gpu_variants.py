@@ -174,3 +174,46 @@ def test_full_size_uneven_batch_sampled_parity():
     for ci in (0, 17, 40, 63):
         ks = [k for k in range(len(specs)) if owner[k] == ci]
         _sample_and_check(w, ci, specs, (ks[3], ks[nf + 20]), steps, starts, rng, 3)
+
+
+def _deep_octree(ell):
+    """2^3 root grid with one path refined down to the deepest level the
+    library accepts (16 levels), plus a second octet per level: packages near
+    the path climb and descend through all 15 ancestor levels."""
+    rho = np.random.default_rng(12).uniform(0.5, 2.0, (2, 2, 2)).astype(np.float32)
+    cl = I.regular(rho, ell=ell)
+    c, octant = 7, 7
+    for level in range(15):
+        extra = cl.level_start[-2] + ((c - cl.level_start[-2] + 3) % (cl.level_start[-1] - cl.level_start[-2]))
+        cl = I.refine_cells(cl, sorted({int(c), int(extra)}))
+        c = int(cl.child[c]) + octant
+        octant = 7 - octant
+    return cl
+
+
+@pytest.mark.parametrize("source", [0, 1, 2])
+def test_deepest_octree_bit_exact(source):
+    base = I.config_c3(root_n=6, max_refine=1, n_freq=8)
+    cl = _deep_octree(base.clouds[0].ell)
+    assert cl.n_levels == 16
+    w = I.Workload("deep16", [cl], base.dust, [base.bg_I[0]], [np.array([[1.6667, 1.6666, 1.6668]])],
+                   [base.ps_L[0][:1]], [0], [0], seed=3)
+    ctx, ids = gpu_context(w)
+    f = 4                                   # tau_abs ~ 1, tau_sca ~ 0.2 per root cell
+    n = cl.leaves().size if source == 2 else 4000
+    spec = dict(cloud=ids[0], source=source, freq=f, n_packages=n, tally_offset=0)
+    dw = None
+    if source == 2:
+        dw = np.random.default_rng(2).integers(1, 2 ** 31, cl.leaves().size).astype(np.uint64)
+        spec["dust_w"] = torch.from_numpy(dw.view(np.int64)).cuda()
+    t, st, sp = run_gpu(ctx, [spec], cl.n_cells)
+    spec.pop("dust_w", None)
+    to, sto, so = oracle_item(w, 0, dict(spec, cloud=0), dust_w=dw)
+    np.testing.assert_array_equal(t, to)
+    assert st[0][0] == sto["escaped"] and st[0][2] == sto["steps"] and st[0][3] == sto["emitted"]
+    np.testing.assert_array_equal(sp, so)
+    # refined levels were crossed; the point source (placed on the refined
+    # path) and dust (emitted from every leaf) reach the deepest level
+    assert t[cl.level_start[2]:].sum() > 0
+    if source != 0:
+        assert t[cl.level_start[15]:cl.level_start[16]].sum() > 0
