@@ -35,7 +35,7 @@ typedef int soc_status;
 #define SOC_ERR_CUDA       -3   /* a CUDA runtime call failed                        */
 #define SOC_ERR_STEP_LIMIT -4   /* packages were ended by the step cap               */
 #define SOC_ERR_STATE      -5   /* call order: e.g. simulation before soc_dust_upload */
-#define SOC_ERR_NOMEM      -6   /* device allocation failed                          */
+#define SOC_ERR_NOMEM      -6   /* device or host allocation failed                  */
 
 #define SOC_SRC_BACKGROUND 0
 #define SOC_SRC_POINT      1

@@ -6,8 +6,10 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <exception>
 #include <new>
 #include <string>
+#include <system_error>
 #include <thread>
 #include <vector>
 #include "soc_internal.h"
@@ -134,6 +136,23 @@ soc_status cuda_fail(soc_ctx *c, cudaError_t e, const char *where)
                 cudaGetErrorString(e));
 }
 
+// Runs the body of an entry point: an exception (a failed host allocation,
+// host threads that could not start) becomes a status and never crosses the
+// C ABI.
+template <class F>
+soc_status guarded(soc_ctx *ctx, F &&body)
+{
+    try {
+        return body();
+    } catch (const std::bad_alloc &) {
+        return fail(ctx, SOC_ERR_NOMEM, "host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(ctx, SOC_ERR_NOMEM, "host resources: %s", e.what());
+    } catch (...) {
+        return fail(ctx, SOC_ERR_NOMEM, "host resources: unknown exception");
+    }
+}
+
 #define CK(expr, where)                                          \
     do {                                                         \
         cudaError_t e_ = (expr);                                 \
@@ -208,25 +227,27 @@ extern "C" {
 
 soc_status soc_create(soc_ctx **out, int device, uint64_t seed)
 {
-    if (!out) return SOC_ERR_ARG;
-    *out = nullptr;
-    int n = 0;
-    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return SOC_ERR_CUDA;
-    if (cudaSetDevice(device) != cudaSuccess) return SOC_ERR_CUDA;
-    soc_ctx *ctx = new (std::nothrow) soc_ctx();
-    if (!ctx) return SOC_ERR_NOMEM;
-    ctx->device = device;
-    ctx->seed = seed;
-    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
-    for (int g = 0; g < 2; ++g)
-        for (int v = 3; v <= 4; ++v)
-            for (int t = 32; t <= 256; t += 32) ctx->occ[g][v - 3][t / 32 - 1] = trace_block_limit(t, v, g == 1);
-    if (ctx->d_counter.alloc(1) != cudaSuccess || ctx->d_maxdT.alloc(1) != cudaSuccess) {
-        delete ctx;
-        return SOC_ERR_NOMEM;
-    }
-    *out = ctx;
-    return SOC_OK;
+    return guarded(nullptr, [&]() -> soc_status {
+        if (!out) return SOC_ERR_ARG;
+        *out = nullptr;
+        int n = 0;
+        if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return SOC_ERR_CUDA;
+        if (cudaSetDevice(device) != cudaSuccess) return SOC_ERR_CUDA;
+        soc_ctx *ctx = new (std::nothrow) soc_ctx();
+        if (!ctx) return SOC_ERR_NOMEM;
+        ctx->device = device;
+        ctx->seed = seed;
+        cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+        for (int g = 0; g < 2; ++g)
+            for (int v = 3; v <= 4; ++v)
+                for (int t = 32; t <= 256; t += 32) ctx->occ[g][v - 3][t / 32 - 1] = trace_block_limit(t, v, g == 1);
+        if (ctx->d_counter.alloc(1) != cudaSuccess || ctx->d_maxdT.alloc(1) != cudaSuccess) {
+            delete ctx;
+            return SOC_ERR_NOMEM;
+        }
+        *out = ctx;
+        return SOC_OK;
+    });
 }
 
 static void release_cloud(CloudHost *c)
@@ -243,13 +264,15 @@ static void release_cloud(CloudHost *c)
 
 soc_status soc_grid_free(soc_ctx *ctx, int cloud_id)
 {
-    soc_status st = check_cloud(ctx, cloud_id);
-    if (st) return st;
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    CK(cudaDeviceSynchronize(), "synchronize before free");
-    release_cloud(ctx->clouds[cloud_id]);
-    ctx->clouds_dirty = true;
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        CK(cudaDeviceSynchronize(), "synchronize before free");
+        release_cloud(ctx->clouds[cloud_id]);
+        ctx->clouds_dirty = true;
+        return SOC_OK;
+    });
 }
 
 void soc_destroy(soc_ctx *ctx)
@@ -278,47 +301,57 @@ const char *soc_last_error(const soc_ctx *ctx) { return ctx ? ctx->err.c_str() :
 
 soc_status soc_set_launch(soc_ctx *ctx, int threads_per_block, int blocks_per_sm, int chunk)
 {
-    if (!ctx) return SOC_ERR_ARG;
-    if (threads_per_block < 32 || threads_per_block > 256 || threads_per_block % 32)
-        return fail(ctx, SOC_ERR_ARG, "threads_per_block must be a multiple of 32 in [32, 256]");
-    if (blocks_per_sm < 0 || chunk < 1 || chunk > 1024) return fail(ctx, SOC_ERR_ARG, "bad blocks_per_sm/chunk");
-    ctx->tpb = threads_per_block;
-    ctx->bps = blocks_per_sm;
-    ctx->chunk = chunk;
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx) return SOC_ERR_ARG;
+        if (threads_per_block < 32 || threads_per_block > 256 || threads_per_block % 32)
+            return fail(ctx, SOC_ERR_ARG, "threads_per_block must be a multiple of 32 in [32, 256]");
+        if (blocks_per_sm < 0 || chunk < 1 || chunk > 1024) return fail(ctx, SOC_ERR_ARG, "bad blocks_per_sm/chunk");
+        ctx->tpb = threads_per_block;
+        ctx->bps = blocks_per_sm;
+        ctx->chunk = chunk;
+        return SOC_OK;
+    });
 }
 
 soc_status soc_set_refill(soc_ctx *ctx, int min_idle_lanes)
 {
-    if (!ctx) return SOC_ERR_ARG;
-    if (min_idle_lanes < 1 || min_idle_lanes > 32) return fail(ctx, SOC_ERR_ARG, "min_idle_lanes must be in [1, 32]");
-    ctx->refill_min = min_idle_lanes;
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx) return SOC_ERR_ARG;
+        if (min_idle_lanes < 1 || min_idle_lanes > 32) return fail(ctx, SOC_ERR_ARG, "min_idle_lanes must be in [1, 32]");
+        ctx->refill_min = min_idle_lanes;
+        return SOC_OK;
+    });
 }
 
 soc_status soc_set_scatter_batch(soc_ctx *ctx, int min_lanes)
 {
-    if (!ctx) return SOC_ERR_ARG;
-    if (min_lanes < 1 || min_lanes > 32) return fail(ctx, SOC_ERR_ARG, "min_lanes must be in [1, 32]");
-    ctx->scatter_min = min_lanes;
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx) return SOC_ERR_ARG;
+        if (min_lanes < 1 || min_lanes > 32) return fail(ctx, SOC_ERR_ARG, "min_lanes must be in [1, 32]");
+        ctx->scatter_min = min_lanes;
+        return SOC_OK;
+    });
 }
 
 soc_status soc_probe_read(soc_ctx *ctx, const void *d_buf, uint64_t bytes, int32_t reps, void *stream)
 {
-    if (!ctx) return SOC_ERR_ARG;
-    if (!d_buf || bytes == 0 || bytes % 16 || reinterpret_cast<uintptr_t>(d_buf) % 16 || reps < 1)
-        return fail(ctx, SOC_ERR_ARG, "probe buffer must be 16-byte aligned, a positive multiple of 16 bytes");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    CK(launch_probe_read(d_buf, bytes, reps, ctx->sms, nullptr, static_cast<cudaStream_t>(stream)), "probe launch");
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx) return SOC_ERR_ARG;
+        if (!d_buf || bytes == 0 || bytes % 16 || reinterpret_cast<uintptr_t>(d_buf) % 16 || reps < 1)
+            return fail(ctx, SOC_ERR_ARG, "probe buffer must be 16-byte aligned, a positive multiple of 16 bytes");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        CK(launch_probe_read(d_buf, bytes, reps, ctx->sms, nullptr, static_cast<cudaStream_t>(stream)), "probe launch");
+        return SOC_OK;
+    });
 }
 
 soc_status soc_set_max_steps(soc_ctx *ctx, uint32_t max_steps)
 {
-    if (!ctx || max_steps == 0) return SOC_ERR_ARG;
-    ctx->max_steps = max_steps;
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx || max_steps == 0) return SOC_ERR_ARG;
+        ctx->max_steps = max_steps;
+        return SOC_OK;
+    });
 }
 
 namespace {
@@ -433,7 +466,13 @@ soc_status grid_cells(soc_ctx *ctx, const soc_grid_desc *d, std::vector<int64_t>
         if (n_thr == 1) { fn(0); return; }
         std::vector<std::thread> th;
         th.reserve(n_thr);
-        for (int t = 0; t < n_thr; ++t) th.emplace_back(fn, t);
+        int t = 0;
+        try {
+            for (; t < n_thr; ++t) th.emplace_back(fn, t);
+        } catch (const std::system_error &) {
+            // fewer threads than chunks could start: the rest run on this one
+        }
+        for (int u = t; u < n_thr; ++u) fn(u);
         for (auto &x : th) x.join();
     };
     run([&](int t) {
@@ -478,207 +517,217 @@ thread_local std::string g_validate_msg;
 
 extern "C" soc_status soc_grid_validate(const soc_grid_desc *desc, char *msg, int msg_len)
 {
-    soc_ctx tmp;
-    GridCheck g;
-    std::vector<int64_t> start;
-    int64_t n_root = 0;
-    soc_status st = grid_header(&tmp, desc, start, n_root);
-    if (st == SOC_OK) st = grid_cells(&tmp, desc, start, n_root, g);
-    if (msg && msg_len > 0) {
-        strncpy(msg, st == SOC_OK ? "ok" : tmp.err.c_str(), (size_t)msg_len - 1);
-        msg[msg_len - 1] = '\0';
-    }
-    return st;
+    return guarded(nullptr, [&]() -> soc_status {
+        soc_ctx tmp;
+        GridCheck g;
+        std::vector<int64_t> start;
+        int64_t n_root = 0;
+        soc_status st = grid_header(&tmp, desc, start, n_root);
+        if (st == SOC_OK) st = grid_cells(&tmp, desc, start, n_root, g);
+        if (msg && msg_len > 0) {
+            strncpy(msg, st == SOC_OK ? "ok" : tmp.err.c_str(), (size_t)msg_len - 1);
+            msg[msg_len - 1] = '\0';
+        }
+        return st;
+    });
 }
 
 extern "C" soc_status soc_grid_upload(soc_ctx *ctx, const soc_grid_desc *d, int *cloud_id)
 {
-    if (!ctx || !cloud_id) return fail(ctx, SOC_ERR_ARG, "null argument");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    std::vector<int64_t> lstart;
-    int64_t n_root0 = 0;
-    soc_status hs = grid_header(ctx, d, lstart, n_root0);
-    if (hs != SOC_OK) return hs;
-    // cell words (tagged links or FP32 densities, -0 stored as +0) and the
-    // leaf list are written in pinned memory by the validating pass and
-    // copied once each; densities and volumes are derived on the device
-    const int64_t n_max = lstart[d->n_levels];
-    if (ctx->h_stage_n < (size_t)n_max) {
-        if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
-        ctx->h_stage = nullptr;
-        ctx->h_stage_n = 0;
-        CK(cudaMallocHost(&ctx->h_stage, 2 * sizeof(uint32_t) * (size_t)std::max<int64_t>(n_max, 1)),
-           "pinned staging");
-        ctx->h_stage_n = (size_t)n_max;
-    }
-    uint32_t *word = ctx->h_stage;
-    int32_t *leaf = reinterpret_cast<int32_t *>(ctx->h_stage + ctx->h_stage_n);
-    GridCheck g;
-    soc_status vs = grid_cells(ctx, d, lstart, n_root0, g, word, leaf);
-    if (vs != SOC_OK) return vs;
-    const int64_t n = g.n, n_root = g.n_root, n_oct = (int64_t)g.parent.size(), n_leaf = g.n_leaf;
-    std::vector<int64_t> &start = g.start;
-    CloudHost *cl = new (std::nothrow) CloudHost();
-    if (!cl) return fail(ctx, SOC_ERR_NOMEM, "host allocation");
-    cl->nx = d->nx; cl->ny = d->ny; cl->nz = d->nz; cl->n_levels = d->n_levels;
-    cl->n_cells = n; cl->n_root = n_root; cl->n_leaf = n_leaf; cl->level_start = start;
-    cl->ell = d->root_cell_size;
-    const double ell3 = (d->root_cell_size * d->root_cell_size) * d->root_cell_size;
-    cudaError_t e = cudaSuccess;
-    if ((e = cl->cell.alloc(n)) == cudaSuccess && (e = cl->parent.alloc(n_oct)) == cudaSuccess &&
-        (e = cl->leaf.alloc(n_leaf)) == cudaSuccess && (e = cl->rho.alloc(n)) == cudaSuccess &&
-        (e = cl->volume.alloc(n)) == cudaSuccess && (e = ctx->d_level_start.alloc(start.size())) == cudaSuccess &&
-        (e = cudaMemcpy(cl->cell.p, word, 4 * n, cudaMemcpyHostToDevice)) == cudaSuccess &&
-        (n_oct == 0 ||
-         (e = cudaMemcpy(cl->parent.p, g.parent.data(), 4 * n_oct, cudaMemcpyHostToDevice)) == cudaSuccess) &&
-        (e = cudaMemcpy(cl->leaf.p, leaf, 4 * n_leaf, cudaMemcpyHostToDevice)) == cudaSuccess &&
-        (e = cudaMemcpy(ctx->d_level_start.p, start.data(), 8 * start.size(), cudaMemcpyHostToDevice)) ==
-            cudaSuccess &&
-        (e = launch_cell_init(cl->cell.p, n, ctx->d_level_start.p, d->n_levels, ell3, cl->rho.p, cl->volume.p, 0)) ==
-            cudaSuccess &&
-        (e = cudaStreamSynchronize(0)) == cudaSuccess) {
-    }
-    if (e != cudaSuccess) {
-        cl->cell.release(); cl->parent.release(); cl->leaf.release(); cl->rho.release(); cl->volume.release();
-        delete cl;
-        return cuda_fail(ctx, e, "grid upload");
-    }
-    ctx->clouds.push_back(cl);
-    ctx->clouds_dirty = true;
-    soc_status st = build_cloud_tables(ctx, *cl);
-    if (st != SOC_OK) return st;
-    *cloud_id = (int)ctx->clouds.size() - 1;
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx || !cloud_id) return fail(ctx, SOC_ERR_ARG, "null argument");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        std::vector<int64_t> lstart;
+        int64_t n_root0 = 0;
+        soc_status hs = grid_header(ctx, d, lstart, n_root0);
+        if (hs != SOC_OK) return hs;
+        // cell words (tagged links or FP32 densities, -0 stored as +0) and the
+        // leaf list are written in pinned memory by the validating pass and
+        // copied once each; densities and volumes are derived on the device
+        const int64_t n_max = lstart[d->n_levels];
+        if (ctx->h_stage_n < (size_t)n_max) {
+            if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+            ctx->h_stage = nullptr;
+            ctx->h_stage_n = 0;
+            CK(cudaMallocHost(&ctx->h_stage, 2 * sizeof(uint32_t) * (size_t)std::max<int64_t>(n_max, 1)),
+               "pinned staging");
+            ctx->h_stage_n = (size_t)n_max;
+        }
+        uint32_t *word = ctx->h_stage;
+        int32_t *leaf = reinterpret_cast<int32_t *>(ctx->h_stage + ctx->h_stage_n);
+        GridCheck g;
+        soc_status vs = grid_cells(ctx, d, lstart, n_root0, g, word, leaf);
+        if (vs != SOC_OK) return vs;
+        const int64_t n = g.n, n_root = g.n_root, n_oct = (int64_t)g.parent.size(), n_leaf = g.n_leaf;
+        std::vector<int64_t> &start = g.start;
+        CloudHost *cl = new (std::nothrow) CloudHost();
+        if (!cl) return fail(ctx, SOC_ERR_NOMEM, "host allocation");
+        cl->nx = d->nx; cl->ny = d->ny; cl->nz = d->nz; cl->n_levels = d->n_levels;
+        cl->n_cells = n; cl->n_root = n_root; cl->n_leaf = n_leaf; cl->level_start = start;
+        cl->ell = d->root_cell_size;
+        const double ell3 = (d->root_cell_size * d->root_cell_size) * d->root_cell_size;
+        cudaError_t e = cudaSuccess;
+        if ((e = cl->cell.alloc(n)) == cudaSuccess && (e = cl->parent.alloc(n_oct)) == cudaSuccess &&
+            (e = cl->leaf.alloc(n_leaf)) == cudaSuccess && (e = cl->rho.alloc(n)) == cudaSuccess &&
+            (e = cl->volume.alloc(n)) == cudaSuccess && (e = ctx->d_level_start.alloc(start.size())) == cudaSuccess &&
+            (e = cudaMemcpy(cl->cell.p, word, 4 * n, cudaMemcpyHostToDevice)) == cudaSuccess &&
+            (n_oct == 0 ||
+             (e = cudaMemcpy(cl->parent.p, g.parent.data(), 4 * n_oct, cudaMemcpyHostToDevice)) == cudaSuccess) &&
+            (e = cudaMemcpy(cl->leaf.p, leaf, 4 * n_leaf, cudaMemcpyHostToDevice)) == cudaSuccess &&
+            (e = cudaMemcpy(ctx->d_level_start.p, start.data(), 8 * start.size(), cudaMemcpyHostToDevice)) ==
+                cudaSuccess &&
+            (e = launch_cell_init(cl->cell.p, n, ctx->d_level_start.p, d->n_levels, ell3, cl->rho.p, cl->volume.p, 0)) ==
+                cudaSuccess &&
+            (e = cudaStreamSynchronize(0)) == cudaSuccess) {
+        }
+        if (e != cudaSuccess) {
+            cl->cell.release(); cl->parent.release(); cl->leaf.release(); cl->rho.release(); cl->volume.release();
+            delete cl;
+            return cuda_fail(ctx, e, "grid upload");
+        }
+        ctx->clouds.push_back(cl);
+        ctx->clouds_dirty = true;
+        soc_status st = build_cloud_tables(ctx, *cl);
+        if (st != SOC_OK) return st;
+        *cloud_id = (int)ctx->clouds.size() - 1;
+        return SOC_OK;
+    });
 }
 
 soc_status soc_dust_upload(soc_ctx *ctx, int n_freq, const double *nu, const double *kabs, const double *ksca,
                            const double *g)
 {
-    if (!ctx || n_freq < 1 || n_freq > 65535 || !nu || !kabs || !ksca || !g)
-        return fail(ctx, SOC_ERR_ARG, "bad dust arguments");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    for (int f = 0; f < n_freq; ++f) {
-        if (!(nu[f] > 0) || (f && !(nu[f] > nu[f - 1])) || !(kabs[f] >= 0) || !(ksca[f] >= 0) ||
-            !std::isfinite(kabs[f]) || !std::isfinite(ksca[f]) || !(std::fabs(g[f]) < 1.0))
-            return fail(ctx, SOC_ERR_ARG, "dust table entry %d invalid", f);
-    }
-    ctx->n_freq = n_freq;
-    ctx->nu.assign(nu, nu + n_freq);
-    ctx->kabs.assign(kabs, kabs + n_freq);
-    ctx->ksca.assign(ksca, ksca + n_freq);
-    ctx->g.assign(g, g + n_freq);
-    ctx->w = trapezoid(ctx->nu);
-    std::vector<float> gf(n_freq);
-    std::vector<double> wk(n_freq);
-    for (int f = 0; f < n_freq; ++f) {
-        gf[f] = (float)g[f];
-        wk[f] = 4.0 * kPi * ctx->w[f] * kabs[f];
-    }
-    // emission table E(T_k), T_k log-spaced in [kTMin, kTMax]
-    std::vector<double> lnE(kTableN), lnT(kTableN);
-    const double l0 = std::log(kTMin), l1 = std::log(kTMax);
-    for (int k = 0; k < kTableN; ++k) {
-        lnT[k] = l0 + (l1 - l0) * k / (kTableN - 1);
-        const double T = std::exp(lnT[k]);
-        double E = 0.0;
-        for (int f = 0; f < n_freq; ++f) E += wk[f] * planck_host(ctx->nu[f], T);
-        lnE[k] = std::log(std::max(E, 1e-300));
-    }
-    CK(ctx->d_g.alloc(n_freq), "alloc");
-    CK(ctx->d_w.alloc(n_freq), "alloc");
-    CK(ctx->d_w_kabs.alloc(n_freq), "alloc");
-    CK(ctx->d_nu.alloc(n_freq), "alloc");
-    CK(ctx->d_kabs.alloc(n_freq), "alloc");
-    CK(ctx->d_lnE.alloc(kTableN), "alloc");
-    CK(ctx->d_lnT.alloc(kTableN), "alloc");
-    CK(ctx->d_lmax.alloc(n_freq), "alloc");
-    CK(cudaMemcpy(ctx->d_g.p, gf.data(), 4 * n_freq, cudaMemcpyHostToDevice), "copy");
-    CK(cudaMemcpy(ctx->d_w.p, ctx->w.data(), 8 * n_freq, cudaMemcpyHostToDevice), "copy");
-    CK(cudaMemcpy(ctx->d_w_kabs.p, wk.data(), 8 * n_freq, cudaMemcpyHostToDevice), "copy");
-    CK(cudaMemcpy(ctx->d_nu.p, nu, 8 * n_freq, cudaMemcpyHostToDevice), "copy");
-    CK(cudaMemcpy(ctx->d_kabs.p, kabs, 8 * n_freq, cudaMemcpyHostToDevice), "copy");
-    CK(cudaMemcpy(ctx->d_lnE.p, lnE.data(), 8 * kTableN, cudaMemcpyHostToDevice), "copy");
-    CK(cudaMemcpy(ctx->d_lnT.p, lnT.data(), 8 * kTableN, cudaMemcpyHostToDevice), "copy");
-    for (CloudHost *c : ctx->clouds) {
-        soc_status st = build_cloud_tables(ctx, *c);
-        if (st != SOC_OK) return st;
-        if (c->n_ps && c->ps_cdf.n != (size_t)c->n_ps * n_freq)
-            return fail(ctx, SOC_ERR_STATE, "sources were uploaded for another frequency grid");
-    }
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx || n_freq < 1 || n_freq > 65535 || !nu || !kabs || !ksca || !g)
+            return fail(ctx, SOC_ERR_ARG, "bad dust arguments");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        for (int f = 0; f < n_freq; ++f) {
+            if (!(nu[f] > 0) || (f && !(nu[f] > nu[f - 1])) || !(kabs[f] >= 0) || !(ksca[f] >= 0) ||
+                !std::isfinite(kabs[f]) || !std::isfinite(ksca[f]) || !(std::fabs(g[f]) < 1.0))
+                return fail(ctx, SOC_ERR_ARG, "dust table entry %d invalid", f);
+        }
+        ctx->n_freq = n_freq;
+        ctx->nu.assign(nu, nu + n_freq);
+        ctx->kabs.assign(kabs, kabs + n_freq);
+        ctx->ksca.assign(ksca, ksca + n_freq);
+        ctx->g.assign(g, g + n_freq);
+        ctx->w = trapezoid(ctx->nu);
+        std::vector<float> gf(n_freq);
+        std::vector<double> wk(n_freq);
+        for (int f = 0; f < n_freq; ++f) {
+            gf[f] = (float)g[f];
+            wk[f] = 4.0 * kPi * ctx->w[f] * kabs[f];
+        }
+        // emission table E(T_k), T_k log-spaced in [kTMin, kTMax]
+        std::vector<double> lnE(kTableN), lnT(kTableN);
+        const double l0 = std::log(kTMin), l1 = std::log(kTMax);
+        for (int k = 0; k < kTableN; ++k) {
+            lnT[k] = l0 + (l1 - l0) * k / (kTableN - 1);
+            const double T = std::exp(lnT[k]);
+            double E = 0.0;
+            for (int f = 0; f < n_freq; ++f) E += wk[f] * planck_host(ctx->nu[f], T);
+            lnE[k] = std::log(std::max(E, 1e-300));
+        }
+        CK(ctx->d_g.alloc(n_freq), "alloc");
+        CK(ctx->d_w.alloc(n_freq), "alloc");
+        CK(ctx->d_w_kabs.alloc(n_freq), "alloc");
+        CK(ctx->d_nu.alloc(n_freq), "alloc");
+        CK(ctx->d_kabs.alloc(n_freq), "alloc");
+        CK(ctx->d_lnE.alloc(kTableN), "alloc");
+        CK(ctx->d_lnT.alloc(kTableN), "alloc");
+        CK(ctx->d_lmax.alloc(n_freq), "alloc");
+        CK(cudaMemcpy(ctx->d_g.p, gf.data(), 4 * n_freq, cudaMemcpyHostToDevice), "copy");
+        CK(cudaMemcpy(ctx->d_w.p, ctx->w.data(), 8 * n_freq, cudaMemcpyHostToDevice), "copy");
+        CK(cudaMemcpy(ctx->d_w_kabs.p, wk.data(), 8 * n_freq, cudaMemcpyHostToDevice), "copy");
+        CK(cudaMemcpy(ctx->d_nu.p, nu, 8 * n_freq, cudaMemcpyHostToDevice), "copy");
+        CK(cudaMemcpy(ctx->d_kabs.p, kabs, 8 * n_freq, cudaMemcpyHostToDevice), "copy");
+        CK(cudaMemcpy(ctx->d_lnE.p, lnE.data(), 8 * kTableN, cudaMemcpyHostToDevice), "copy");
+        CK(cudaMemcpy(ctx->d_lnT.p, lnT.data(), 8 * kTableN, cudaMemcpyHostToDevice), "copy");
+        for (CloudHost *c : ctx->clouds) {
+            soc_status st = build_cloud_tables(ctx, *c);
+            if (st != SOC_OK) return st;
+            if (c->n_ps && c->ps_cdf.n != (size_t)c->n_ps * n_freq)
+                return fail(ctx, SOC_ERR_STATE, "sources were uploaded for another frequency grid");
+        }
+        return SOC_OK;
+    });
 }
 
 soc_status soc_sources_upload(soc_ctx *ctx, int cloud_id, const double *bg_I_nu, int n_ps, const double *ps_pos,
                               const double *ps_L_nu)
 {
-    soc_status st = check_cloud(ctx, cloud_id);
-    if (st) return st;
-    if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
-    if (n_ps < 0 || (n_ps > 0 && (!ps_pos || !ps_L_nu))) return fail(ctx, SOC_ERR_ARG, "bad point sources");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    CloudHost &cl = *ctx->clouds[cloud_id];
-    const int nf = ctx->n_freq;
-    cl.bg_I.clear();
-    if (bg_I_nu) {
-        for (int f = 0; f < nf; ++f)
-            if (!(bg_I_nu[f] >= 0) || !std::isfinite(bg_I_nu[f])) return fail(ctx, SOC_ERR_ARG, "bad bg_I_nu[%d]", f);
-        cl.bg_I.assign(bg_I_nu, bg_I_nu + nf);
-    }
-    cl.n_ps = n_ps;
-    cl.ps_L_total.assign(nf, 0.0);
-    if (n_ps > 0) {
-        const int nr[3] = {cl.nx, cl.ny, cl.nz};
-        std::vector<float> pos(3 * n_ps);
-        for (int k = 0; k < n_ps; ++k)
-            for (int a = 0; a < 3; ++a) {
-                const double v = ps_pos[3 * k + a];
-                if (!(v > 0.0 && v < nr[a])) return fail(ctx, SOC_ERR_ARG, "point source %d outside the grid", k);
-                pos[3 * k + a] = (float)v;
-            }
-        std::vector<float> cdf((size_t)nf * n_ps);
-        for (int f = 0; f < nf; ++f) {
-            double tot = 0.0;
-            for (int k = 0; k < n_ps; ++k) {
-                const double L = ps_L_nu[(size_t)k * nf + f];
-                if (!(L >= 0) || !std::isfinite(L)) return fail(ctx, SOC_ERR_ARG, "bad ps_L_nu");
-                tot += L;
-            }
-            cl.ps_L_total[f] = tot;
-            double run = 0.0;
-            for (int k = 0; k < n_ps; ++k) {
-                run += ps_L_nu[(size_t)k * nf + f];
-                cdf[(size_t)f * n_ps + k] = (float)(run / (tot > 0 ? tot : 1.0));
-            }
-            cdf[(size_t)f * n_ps + n_ps - 1] = 1.0f;
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
+        if (n_ps < 0 || (n_ps > 0 && (!ps_pos || !ps_L_nu))) return fail(ctx, SOC_ERR_ARG, "bad point sources");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        CloudHost &cl = *ctx->clouds[cloud_id];
+        const int nf = ctx->n_freq;
+        cl.bg_I.clear();
+        if (bg_I_nu) {
+            for (int f = 0; f < nf; ++f)
+                if (!(bg_I_nu[f] >= 0) || !std::isfinite(bg_I_nu[f])) return fail(ctx, SOC_ERR_ARG, "bad bg_I_nu[%d]", f);
+            cl.bg_I.assign(bg_I_nu, bg_I_nu + nf);
         }
-        CK(cl.ps_pos.alloc(pos.size()), "alloc");
-        CK(cl.ps_cdf.alloc(cdf.size()), "alloc");
-        CK(cudaMemcpy(cl.ps_pos.p, pos.data(), 4 * pos.size(), cudaMemcpyHostToDevice), "copy");
-        CK(cudaMemcpy(cl.ps_cdf.p, cdf.data(), 4 * cdf.size(), cudaMemcpyHostToDevice), "copy");
-    }
-    ctx->clouds_dirty = true;
-    return SOC_OK;
+        cl.n_ps = n_ps;
+        cl.ps_L_total.assign(nf, 0.0);
+        if (n_ps > 0) {
+            const int nr[3] = {cl.nx, cl.ny, cl.nz};
+            std::vector<float> pos(3 * n_ps);
+            for (int k = 0; k < n_ps; ++k)
+                for (int a = 0; a < 3; ++a) {
+                    const double v = ps_pos[3 * k + a];
+                    if (!(v > 0.0 && v < nr[a])) return fail(ctx, SOC_ERR_ARG, "point source %d outside the grid", k);
+                    pos[3 * k + a] = (float)v;
+                }
+            std::vector<float> cdf((size_t)nf * n_ps);
+            for (int f = 0; f < nf; ++f) {
+                double tot = 0.0;
+                for (int k = 0; k < n_ps; ++k) {
+                    const double L = ps_L_nu[(size_t)k * nf + f];
+                    if (!(L >= 0) || !std::isfinite(L)) return fail(ctx, SOC_ERR_ARG, "bad ps_L_nu");
+                    tot += L;
+                }
+                cl.ps_L_total[f] = tot;
+                double run = 0.0;
+                for (int k = 0; k < n_ps; ++k) {
+                    run += ps_L_nu[(size_t)k * nf + f];
+                    cdf[(size_t)f * n_ps + k] = (float)(run / (tot > 0 ? tot : 1.0));
+                }
+                cdf[(size_t)f * n_ps + n_ps - 1] = 1.0f;
+            }
+            CK(cl.ps_pos.alloc(pos.size()), "alloc");
+            CK(cl.ps_cdf.alloc(cdf.size()), "alloc");
+            CK(cudaMemcpy(cl.ps_pos.p, pos.data(), 4 * pos.size(), cudaMemcpyHostToDevice), "copy");
+            CK(cudaMemcpy(cl.ps_cdf.p, cdf.data(), 4 * cdf.size(), cudaMemcpyHostToDevice), "copy");
+        }
+        ctx->clouds_dirty = true;
+        return SOC_OK;
+    });
 }
 
 soc_status soc_package_energy(soc_ctx *ctx, int cloud_id, int source, uint64_t n_packages, double *e_unit)
 {
-    soc_status st = check_cloud(ctx, cloud_id);
-    if (st) return st;
-    if (!e_unit || n_packages == 0) return fail(ctx, SOC_ERR_ARG, "bad arguments");
-    const CloudHost &cl = *ctx->clouds[cloud_id];
-    const int nf = ctx->n_freq;
-    if (source == SOC_SRC_BACKGROUND) {
-        if (cl.bg_I.empty()) return fail(ctx, SOC_ERR_STATE, "no background uploaded");
-        const double S = 2.0 * ((double)cl.nx * cl.ny + (double)cl.ny * cl.nz + (double)cl.nz * cl.nx) * cl.ell * cl.ell;
-        for (int f = 0; f < nf; ++f) e_unit[f] = kPi * cl.bg_I[f] * S / (double)n_packages / kWUnit;
-        return SOC_OK;
-    }
-    if (source == SOC_SRC_POINT) {
-        if (cl.n_ps == 0) return fail(ctx, SOC_ERR_STATE, "no point sources uploaded");
-        for (int f = 0; f < nf; ++f) e_unit[f] = cl.ps_L_total[f] / (double)n_packages / kWUnit;
-        return SOC_OK;
-    }
-    return fail(ctx, SOC_ERR_ARG, "source must be background or point");
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        if (!e_unit || n_packages == 0) return fail(ctx, SOC_ERR_ARG, "bad arguments");
+        const CloudHost &cl = *ctx->clouds[cloud_id];
+        const int nf = ctx->n_freq;
+        if (source == SOC_SRC_BACKGROUND) {
+            if (cl.bg_I.empty()) return fail(ctx, SOC_ERR_STATE, "no background uploaded");
+            const double S = 2.0 * ((double)cl.nx * cl.ny + (double)cl.ny * cl.nz + (double)cl.nz * cl.nx) * cl.ell * cl.ell;
+            for (int f = 0; f < nf; ++f) e_unit[f] = kPi * cl.bg_I[f] * S / (double)n_packages / kWUnit;
+            return SOC_OK;
+        }
+        if (source == SOC_SRC_POINT) {
+            if (cl.n_ps == 0) return fail(ctx, SOC_ERR_STATE, "no point sources uploaded");
+            for (int f = 0; f < nf; ++f) e_unit[f] = cl.ps_L_total[f] / (double)n_packages / kWUnit;
+            return SOC_OK;
+        }
+        return fail(ctx, SOC_ERR_ARG, "source must be background or point");
+    });
 }
 
 // Check the batch items and convert them to the device form (host vectors).
@@ -757,518 +806,590 @@ static void launch_geometry(soc_ctx *ctx, uint64_t total, bool regular, int &gri
 soc_status soc_simulate_frequency_batch(soc_ctx *ctx, const soc_batch_item *items, int n_items, int64_t *d_tally,
                                         int64_t *d_stats, uint32_t *d_pkg_steps, void *stream)
 {
-    return soc_simulate_frequency_batch_ex(ctx, items, n_items, d_tally, nullptr, d_stats, d_pkg_steps, stream);
+    return guarded(ctx, [&]() -> soc_status {
+        return soc_simulate_frequency_batch_ex(ctx, items, n_items, d_tally, nullptr, d_stats, d_pkg_steps, stream);
+    });
 }
 
 soc_status soc_simulate_frequency_batch_ex(soc_ctx *ctx, const soc_batch_item *items, int n_items, int64_t *d_tally,
                                            int64_t *d_self, int64_t *d_stats, uint32_t *d_pkg_steps, void *stream)
 {
-    if (!ctx || !items || n_items < 1 || !d_tally || !d_stats) return fail(ctx, SOC_ERR_ARG, "null argument");
-    if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    cudaStream_t s = (cudaStream_t)stream;
-    std::vector<DevItem> dv;
-    std::vector<uint64_t> prefix;
-    soc_status pst = prepare_items(ctx, items, n_items, dv, prefix);
-    if (pst != SOC_OK) return pst;
-    const uint64_t total = prefix[n_items];
-    soc_status st = sync_clouds(ctx);
-    if (st) return st;
-    if (total == 0) return SOC_OK;
-    CK(ctx->d_items.alloc(n_items), "alloc items");
-    CK(ctx->d_prefix.alloc(n_items + 1), "alloc prefix");
-    CK(cudaMemcpyAsync(ctx->d_items.p, dv.data(), sizeof(DevItem) * n_items, cudaMemcpyHostToDevice, s), "copy items");
-    CK(cudaMemcpyAsync(ctx->d_prefix.p, prefix.data(), 8 * (n_items + 1), cudaMemcpyHostToDevice, s), "copy prefix");
-    CK(cudaMemsetAsync(ctx->d_counter.p, 0, sizeof(unsigned long long), s), "zero counter");
-    TraceParams P;
-    P.clouds = ctx->d_clouds.p;
-    P.items = ctx->d_items.p;
-    P.prefix = ctx->d_prefix.p;
-    P.g_hg = ctx->d_g.p;
-    P.tally = reinterpret_cast<unsigned long long *>(d_tally);
-    P.self = reinterpret_cast<unsigned long long *>(d_self);
-    P.stats = reinterpret_cast<unsigned long long *>(d_stats);
-    P.pkg_steps = d_pkg_steps;
-    P.counter = ctx->d_counter.p;
-    P.total = total;
-    P.seed = ctx->seed;
-    P.n_items = n_items;
-    P.max_steps = ctx->max_steps;
-    P.chunk = ctx->chunk;
-    P.refill_min = ctx->refill_min;
-    P.scatter_min = ctx->scatter_min;
-    P.hot = one_cloud(ctx, items, n_items);
-    P.regular = all_regular(ctx, items, n_items);
-    int grid = 1, variant = 3;
-    launch_geometry(ctx, total, P.regular != 0, grid, variant);
-    CK(launch_trace(P, grid, ctx->tpb, variant, s), "trace launch");
-    // the host copies above used pageable buffers: they are staged before return
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx || !items || n_items < 1 || !d_tally || !d_stats) return fail(ctx, SOC_ERR_ARG, "null argument");
+        if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        cudaStream_t s = (cudaStream_t)stream;
+        std::vector<DevItem> dv;
+        std::vector<uint64_t> prefix;
+        soc_status pst = prepare_items(ctx, items, n_items, dv, prefix);
+        if (pst != SOC_OK) return pst;
+        const uint64_t total = prefix[n_items];
+        soc_status st = sync_clouds(ctx);
+        if (st) return st;
+        if (total == 0) return SOC_OK;
+        CK(ctx->d_items.alloc(n_items), "alloc items");
+        CK(ctx->d_prefix.alloc(n_items + 1), "alloc prefix");
+        CK(cudaMemcpyAsync(ctx->d_items.p, dv.data(), sizeof(DevItem) * n_items, cudaMemcpyHostToDevice, s), "copy items");
+        CK(cudaMemcpyAsync(ctx->d_prefix.p, prefix.data(), 8 * (n_items + 1), cudaMemcpyHostToDevice, s), "copy prefix");
+        CK(cudaMemsetAsync(ctx->d_counter.p, 0, sizeof(unsigned long long), s), "zero counter");
+        TraceParams P;
+        P.clouds = ctx->d_clouds.p;
+        P.items = ctx->d_items.p;
+        P.prefix = ctx->d_prefix.p;
+        P.g_hg = ctx->d_g.p;
+        P.tally = reinterpret_cast<unsigned long long *>(d_tally);
+        P.self = reinterpret_cast<unsigned long long *>(d_self);
+        P.stats = reinterpret_cast<unsigned long long *>(d_stats);
+        P.pkg_steps = d_pkg_steps;
+        P.counter = ctx->d_counter.p;
+        P.total = total;
+        P.seed = ctx->seed;
+        P.n_items = n_items;
+        P.max_steps = ctx->max_steps;
+        P.chunk = ctx->chunk;
+        P.refill_min = ctx->refill_min;
+        P.scatter_min = ctx->scatter_min;
+        P.hot = one_cloud(ctx, items, n_items);
+        P.regular = all_regular(ctx, items, n_items);
+        int grid = 1, variant = 3;
+        launch_geometry(ctx, total, P.regular != 0, grid, variant);
+        CK(launch_trace(P, grid, ctx->tpb, variant, s), "trace launch");
+        // the host copies above used pageable buffers: they are staged before return
+        return SOC_OK;
+    });
 }
 
 soc_status soc_batch_create(soc_ctx *ctx, const soc_batch_item *items, int n_items, int *batch_id)
 {
-    if (!ctx || !items || n_items < 1 || !batch_id) return fail(ctx, SOC_ERR_ARG, "null argument");
-    if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    std::vector<DevItem> dv;
-    std::vector<uint64_t> prefix;
-    soc_status st = prepare_items(ctx, items, n_items, dv, prefix);
-    if (st != SOC_OK) return st;
-    BatchHost *b = new (std::nothrow) BatchHost();
-    if (!b) return fail(ctx, SOC_ERR_NOMEM, "host allocation");
-    b->n_items = n_items;
-    b->total = prefix[n_items];
-    b->hot = one_cloud(ctx, items, n_items);
-    b->regular = all_regular(ctx, items, n_items);
-    cudaError_t e = cudaSuccess;
-    if ((e = b->items.alloc(n_items)) != cudaSuccess || (e = b->prefix.alloc(n_items + 1)) != cudaSuccess ||
-        (e = b->counter.alloc(1)) != cudaSuccess ||
-        (e = cudaMemcpy(b->items.p, dv.data(), sizeof(DevItem) * n_items, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b->prefix.p, prefix.data(), 8 * (n_items + 1), cudaMemcpyHostToDevice)) != cudaSuccess) {
-        b->items.release(); b->prefix.release(); b->counter.release();
-        delete b;
-        return cuda_fail(ctx, e, "batch upload");
-    }
-    ctx->batches.push_back(b);
-    *batch_id = (int)ctx->batches.size() - 1;
-    return sync_clouds(ctx);                 // the launch must not need to upload the grid table
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx || !items || n_items < 1 || !batch_id) return fail(ctx, SOC_ERR_ARG, "null argument");
+        if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        std::vector<DevItem> dv;
+        std::vector<uint64_t> prefix;
+        soc_status st = prepare_items(ctx, items, n_items, dv, prefix);
+        if (st != SOC_OK) return st;
+        BatchHost *b = new (std::nothrow) BatchHost();
+        if (!b) return fail(ctx, SOC_ERR_NOMEM, "host allocation");
+        b->n_items = n_items;
+        b->total = prefix[n_items];
+        b->hot = one_cloud(ctx, items, n_items);
+        b->regular = all_regular(ctx, items, n_items);
+        cudaError_t e = cudaSuccess;
+        if ((e = b->items.alloc(n_items)) != cudaSuccess || (e = b->prefix.alloc(n_items + 1)) != cudaSuccess ||
+            (e = b->counter.alloc(1)) != cudaSuccess ||
+            (e = cudaMemcpy(b->items.p, dv.data(), sizeof(DevItem) * n_items, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(b->prefix.p, prefix.data(), 8 * (n_items + 1), cudaMemcpyHostToDevice)) != cudaSuccess) {
+            b->items.release(); b->prefix.release(); b->counter.release();
+            delete b;
+            return cuda_fail(ctx, e, "batch upload");
+        }
+        ctx->batches.push_back(b);
+        *batch_id = (int)ctx->batches.size() - 1;
+        return sync_clouds(ctx);                 // the launch must not need to upload the grid table
+    });
 }
 
 soc_status soc_batch_launch(soc_ctx *ctx, int batch_id, int64_t *d_tally, int64_t tally_len, int64_t *d_stats,
                             uint32_t *d_pkg_steps, void *stream)
 {
-    if (!ctx || batch_id < 0 || batch_id >= (int)ctx->batches.size() || !ctx->batches[batch_id])
-        return fail(ctx, SOC_ERR_ARG, "bad batch id");
-    if (!d_tally || !d_stats || tally_len < 0) return fail(ctx, SOC_ERR_ARG, "null argument");
-    if (ctx->clouds_dirty) return fail(ctx, SOC_ERR_STATE, "grids changed after soc_batch_create");
-    const BatchHost &b = *ctx->batches[batch_id];
-    cudaStream_t s = (cudaStream_t)stream;
-    if (tally_len) CK(cudaMemsetAsync(d_tally, 0, sizeof(int64_t) * tally_len, s), "zero tally");
-    CK(cudaMemsetAsync(d_stats, 0, sizeof(int64_t) * 4 * b.n_items, s), "zero stats");
-    if (b.total == 0) return SOC_OK;
-    CK(cudaMemsetAsync(b.counter.p, 0, sizeof(unsigned long long), s), "zero counter");
-    TraceParams P;
-    P.clouds = ctx->d_clouds.p;
-    P.items = b.items.p;
-    P.prefix = b.prefix.p;
-    P.g_hg = ctx->d_g.p;
-    P.tally = reinterpret_cast<unsigned long long *>(d_tally);
-    P.self = nullptr;
-    P.stats = reinterpret_cast<unsigned long long *>(d_stats);
-    P.pkg_steps = d_pkg_steps;
-    P.counter = b.counter.p;
-    P.total = b.total;
-    P.seed = ctx->seed;
-    P.n_items = b.n_items;
-    P.max_steps = ctx->max_steps;
-    P.chunk = ctx->chunk;
-    P.refill_min = ctx->refill_min;
-    P.scatter_min = ctx->scatter_min;
-    P.hot = b.hot;
-    P.regular = b.regular;
-    int grid = 1, variant = 3;
-    launch_geometry(ctx, b.total, P.regular != 0, grid, variant);
-    CK(launch_trace(P, grid, ctx->tpb, variant, s), "trace launch");
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx || batch_id < 0 || batch_id >= (int)ctx->batches.size() || !ctx->batches[batch_id])
+            return fail(ctx, SOC_ERR_ARG, "bad batch id");
+        if (!d_tally || !d_stats || tally_len < 0) return fail(ctx, SOC_ERR_ARG, "null argument");
+        if (ctx->clouds_dirty) return fail(ctx, SOC_ERR_STATE, "grids changed after soc_batch_create");
+        const BatchHost &b = *ctx->batches[batch_id];
+        cudaStream_t s = (cudaStream_t)stream;
+        if (tally_len) CK(cudaMemsetAsync(d_tally, 0, sizeof(int64_t) * tally_len, s), "zero tally");
+        CK(cudaMemsetAsync(d_stats, 0, sizeof(int64_t) * 4 * b.n_items, s), "zero stats");
+        if (b.total == 0) return SOC_OK;
+        CK(cudaMemsetAsync(b.counter.p, 0, sizeof(unsigned long long), s), "zero counter");
+        TraceParams P;
+        P.clouds = ctx->d_clouds.p;
+        P.items = b.items.p;
+        P.prefix = b.prefix.p;
+        P.g_hg = ctx->d_g.p;
+        P.tally = reinterpret_cast<unsigned long long *>(d_tally);
+        P.self = nullptr;
+        P.stats = reinterpret_cast<unsigned long long *>(d_stats);
+        P.pkg_steps = d_pkg_steps;
+        P.counter = b.counter.p;
+        P.total = b.total;
+        P.seed = ctx->seed;
+        P.n_items = b.n_items;
+        P.max_steps = ctx->max_steps;
+        P.chunk = ctx->chunk;
+        P.refill_min = ctx->refill_min;
+        P.scatter_min = ctx->scatter_min;
+        P.hot = b.hot;
+        P.regular = b.regular;
+        int grid = 1, variant = 3;
+        launch_geometry(ctx, b.total, P.regular != 0, grid, variant);
+        CK(launch_trace(P, grid, ctx->tpb, variant, s), "trace launch");
+        return SOC_OK;
+    });
 }
 
 soc_status soc_batch_destroy(soc_ctx *ctx, int batch_id)
 {
-    if (!ctx || batch_id < 0 || batch_id >= (int)ctx->batches.size() || !ctx->batches[batch_id])
-        return fail(ctx, SOC_ERR_ARG, "bad batch id");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    CK(cudaDeviceSynchronize(), "synchronize before free");
-    BatchHost *b = ctx->batches[batch_id];
-    b->items.release(); b->prefix.release(); b->counter.release();
-    delete b;
-    ctx->batches[batch_id] = nullptr;
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx || batch_id < 0 || batch_id >= (int)ctx->batches.size() || !ctx->batches[batch_id])
+            return fail(ctx, SOC_ERR_ARG, "bad batch id");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        CK(cudaDeviceSynchronize(), "synchronize before free");
+        BatchHost *b = ctx->batches[batch_id];
+        b->items.release(); b->prefix.release(); b->counter.release();
+        delete b;
+        ctx->batches[batch_id] = nullptr;
+        return SOC_OK;
+    });
 }
 
 soc_status soc_capture_begin(soc_ctx *ctx, void *stream)
 {
-    if (!ctx || !stream) return fail(ctx, SOC_ERR_ARG, "capture needs a non-default stream");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    soc_status st = sync_clouds(ctx);
-    if (st) return st;
-    CK(cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx || !stream) return fail(ctx, SOC_ERR_ARG, "capture needs a non-default stream");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        soc_status st = sync_clouds(ctx);
+        if (st) return st;
+        CK(cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        return SOC_OK;
+    });
 }
 
 soc_status soc_capture_end(soc_ctx *ctx, void *stream, int *graph_id)
 {
-    if (!ctx || !stream || !graph_id) return fail(ctx, SOC_ERR_ARG, "null argument");
-    cudaGraph_t g = nullptr;
-    CK(cudaStreamEndCapture((cudaStream_t)stream, &g), "end capture");
-    cudaGraphExec_t ex = nullptr;
-    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
-    ctx->graphs.push_back(ex);
-    *graph_id = (int)ctx->graphs.size() - 1;
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx || !stream || !graph_id) return fail(ctx, SOC_ERR_ARG, "null argument");
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamEndCapture((cudaStream_t)stream, &g), "end capture");
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+        ctx->graphs.push_back(ex);
+        *graph_id = (int)ctx->graphs.size() - 1;
+        return SOC_OK;
+    });
 }
 
 soc_status soc_graph_launch(soc_ctx *ctx, int graph_id, void *stream)
 {
-    if (!ctx || graph_id < 0 || graph_id >= (int)ctx->graphs.size() || !ctx->graphs[graph_id])
-        return fail(ctx, SOC_ERR_ARG, "bad graph id");
-    CK(cudaGraphLaunch(ctx->graphs[graph_id], (cudaStream_t)stream), "graph launch");
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx || graph_id < 0 || graph_id >= (int)ctx->graphs.size() || !ctx->graphs[graph_id])
+            return fail(ctx, SOC_ERR_ARG, "bad graph id");
+        CK(cudaGraphLaunch(ctx->graphs[graph_id], (cudaStream_t)stream), "graph launch");
+        return SOC_OK;
+    });
 }
 
 soc_status soc_graph_destroy(soc_ctx *ctx, int graph_id)
 {
-    if (!ctx || graph_id < 0 || graph_id >= (int)ctx->graphs.size() || !ctx->graphs[graph_id])
-        return fail(ctx, SOC_ERR_ARG, "bad graph id");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    CK(cudaDeviceSynchronize(), "synchronize before free");
-    cudaGraphExecDestroy(ctx->graphs[graph_id]);
-    ctx->graphs[graph_id] = nullptr;
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx || graph_id < 0 || graph_id >= (int)ctx->graphs.size() || !ctx->graphs[graph_id])
+            return fail(ctx, SOC_ERR_ARG, "bad graph id");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        CK(cudaDeviceSynchronize(), "synchronize before free");
+        cudaGraphExecDestroy(ctx->graphs[graph_id]);
+        ctx->graphs[graph_id] = nullptr;
+        return SOC_OK;
+    });
 }
 
 soc_status soc_dust_emission(soc_ctx *ctx, int cloud_id, const float *d_T, int freq_lo, int n_freq,
                              uint32_t n_per_cell, uint64_t *d_w, double *d_e_unit, void *stream)
 {
-    soc_status st = check_cloud(ctx, cloud_id);
-    if (st) return st;
-    if (!d_T || !d_w || !d_e_unit || n_per_cell == 0 || freq_lo < 0 || n_freq < 1 || freq_lo + n_freq > ctx->n_freq)
-        return fail(ctx, SOC_ERR_ARG, "bad dust-emission arguments");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    if ((st = sync_clouds(ctx))) return st;
-    const CloudHost &cl = *ctx->clouds[cloud_id];
-    TempTables tt{ctx->n_freq, ctx->d_w_kabs.p, ctx->d_w.p, ctx->d_nu.p, ctx->d_kabs.p, ctx->d_lnE.p, ctx->d_lnT.p};
-    CK(launch_dust_emission(ctx->d_clouds.p + cloud_id, cl.n_leaf, tt, d_T, freq_lo, n_freq, n_per_cell, d_w,
-                            d_e_unit, ctx->d_lmax.p, (cudaStream_t)stream),
-       "dust emission");
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        if (!d_T || !d_w || !d_e_unit || n_per_cell == 0 || freq_lo < 0 || n_freq < 1 || freq_lo + n_freq > ctx->n_freq)
+            return fail(ctx, SOC_ERR_ARG, "bad dust-emission arguments");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        if ((st = sync_clouds(ctx))) return st;
+        const CloudHost &cl = *ctx->clouds[cloud_id];
+        TempTables tt{ctx->n_freq, ctx->d_w_kabs.p, ctx->d_w.p, ctx->d_nu.p, ctx->d_kabs.p, ctx->d_lnE.p, ctx->d_lnT.p};
+        CK(launch_dust_emission(ctx->d_clouds.p + cloud_id, cl.n_leaf, tt, d_T, freq_lo, n_freq, n_per_cell, d_w,
+                                d_e_unit, ctx->d_lmax.p, (cudaStream_t)stream),
+           "dust emission");
+        return SOC_OK;
+    });
 }
 
 soc_status soc_dust_weighted(soc_ctx *ctx, int cloud_id, const uint64_t *d_u, const double *d_e_unit_uniform,
                              int n_freq, uint64_t n_total, uint32_t cap, uint64_t *d_out, double *d_e_unit, void *stream)
 {
-    soc_status st = check_cloud(ctx, cloud_id);
-    if (st) return st;
-    if (!d_u || !d_e_unit_uniform || !d_out || !d_e_unit || n_freq < 1 || n_total < 1 || cap < 1)
-        return fail(ctx, SOC_ERR_ARG, "bad weighted-sampling arguments");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    const CloudHost &cl = *ctx->clouds[cloud_id];
-    const int64_t n_chunks = (cl.n_leaf + 1023) / 1024;
-    CK(ctx->d_wscratch.alloc((size_t)n_freq * (1 + n_chunks)), "alloc weighted-sampling scratch");
-    CK(launch_dust_weighted(cl.n_leaf, n_freq, d_u, d_e_unit_uniform, n_total, cap, d_out, d_e_unit,
-                            ctx->d_wscratch.p, (cudaStream_t)stream),
-       "weighted sampling");
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        if (!d_u || !d_e_unit_uniform || !d_out || !d_e_unit || n_freq < 1 || n_total < 1 || cap < 1)
+            return fail(ctx, SOC_ERR_ARG, "bad weighted-sampling arguments");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        const CloudHost &cl = *ctx->clouds[cloud_id];
+        const int64_t n_chunks = (cl.n_leaf + 1023) / 1024;
+        CK(ctx->d_wscratch.alloc((size_t)n_freq * (1 + n_chunks)), "alloc weighted-sampling scratch");
+        CK(launch_dust_weighted(cl.n_leaf, n_freq, d_u, d_e_unit_uniform, n_total, cap, d_out, d_e_unit,
+                                ctx->d_wscratch.p, (cudaStream_t)stream),
+           "weighted sampling");
+        return SOC_OK;
+    });
 }
 
 soc_status soc_dust_reweight(soc_ctx *ctx, int cloud_id, const uint64_t *d_u, const double *d_e_unit_uniform,
                              int n_freq, uint64_t *d_inout, double *d_e_unit, void *stream)
 {
-    soc_status st = check_cloud(ctx, cloud_id);
-    if (st) return st;
-    if (!d_u || !d_e_unit_uniform || !d_inout || !d_e_unit || n_freq < 1)
-        return fail(ctx, SOC_ERR_ARG, "bad re-weighting arguments");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    const CloudHost &cl = *ctx->clouds[cloud_id];
-    CK(ctx->d_wscratch.alloc((size_t)n_freq), "alloc weighted-sampling scratch");
-    CK(launch_dust_reweight(cl.n_leaf, n_freq, d_u, d_e_unit_uniform, d_inout, d_e_unit, ctx->d_wscratch.p,
-                            (cudaStream_t)stream),
-       "dust re-weighting");
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        if (!d_u || !d_e_unit_uniform || !d_inout || !d_e_unit || n_freq < 1)
+            return fail(ctx, SOC_ERR_ARG, "bad re-weighting arguments");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        const CloudHost &cl = *ctx->clouds[cloud_id];
+        CK(ctx->d_wscratch.alloc((size_t)n_freq), "alloc weighted-sampling scratch");
+        CK(launch_dust_reweight(cl.n_leaf, n_freq, d_u, d_e_unit_uniform, d_inout, d_e_unit, ctx->d_wscratch.p,
+                                (cudaStream_t)stream),
+           "dust re-weighting");
+        return SOC_OK;
+    });
 }
 
 soc_status soc_dust_luminosity(soc_ctx *ctx, int cloud_id, const float *d_T, int freq_lo, int n_freq, double *d_L,
                                void *stream)
 {
-    soc_status st = check_cloud(ctx, cloud_id);
-    if (st) return st;
-    if (!d_T || !d_L || n_freq < 1 || freq_lo < 0 || freq_lo + n_freq > ctx->n_freq)
-        return fail(ctx, SOC_ERR_ARG, "bad dust-luminosity arguments");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    if ((st = sync_clouds(ctx))) return st;
-    const CloudHost &cl = *ctx->clouds[cloud_id];
-    TempTables tt{ctx->n_freq, ctx->d_w_kabs.p, ctx->d_w.p, ctx->d_nu.p, ctx->d_kabs.p, ctx->d_lnE.p, ctx->d_lnT.p};
-    CK(launch_dust_luminosity(ctx->d_clouds.p + cloud_id, cl.n_leaf, tt, d_T, freq_lo, n_freq, d_L,
-                              (cudaStream_t)stream),
-       "dust luminosity");
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        if (!d_T || !d_L || n_freq < 1 || freq_lo < 0 || freq_lo + n_freq > ctx->n_freq)
+            return fail(ctx, SOC_ERR_ARG, "bad dust-luminosity arguments");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        if ((st = sync_clouds(ctx))) return st;
+        const CloudHost &cl = *ctx->clouds[cloud_id];
+        TempTables tt{ctx->n_freq, ctx->d_w_kabs.p, ctx->d_w.p, ctx->d_nu.p, ctx->d_kabs.p, ctx->d_lnE.p, ctx->d_lnT.p};
+        CK(launch_dust_luminosity(ctx->d_clouds.p + cloud_id, cl.n_leaf, tt, d_T, freq_lo, n_freq, d_L,
+                                  (cudaStream_t)stream),
+           "dust luminosity");
+        return SOC_OK;
+    });
 }
 
 soc_status soc_reference_delta(soc_ctx *ctx, int cloud_id, int n_freq, const double *d_L, double *d_L_ref,
                                double w, uint64_t *d_u, uint8_t *d_neg, double *d_e_unit_uniform, void *stream)
 {
-    soc_status st = check_cloud(ctx, cloud_id);
-    if (st) return st;
-    if (!d_L || !d_L_ref || !d_u || !d_neg || !d_e_unit_uniform || n_freq < 1 || !(w >= 0.0 && w <= 1.0))
-        return fail(ctx, SOC_ERR_ARG, "bad reference-delta arguments");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    const CloudHost &cl = *ctx->clouds[cloud_id];
-    CK(ctx->d_wscratch.alloc((size_t)n_freq), "alloc scratch");
-    CK(launch_reference_delta(cl.n_leaf, n_freq, d_L, d_L_ref, w, d_u, d_neg, d_e_unit_uniform, ctx->d_wscratch.p,
-                              (cudaStream_t)stream),
-       "reference delta");
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        if (!d_L || !d_L_ref || !d_u || !d_neg || !d_e_unit_uniform || n_freq < 1 || !(w >= 0.0 && w <= 1.0))
+            return fail(ctx, SOC_ERR_ARG, "bad reference-delta arguments");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        const CloudHost &cl = *ctx->clouds[cloud_id];
+        CK(ctx->d_wscratch.alloc((size_t)n_freq), "alloc scratch");
+        CK(launch_reference_delta(cl.n_leaf, n_freq, d_L, d_L_ref, w, d_u, d_neg, d_e_unit_uniform, ctx->d_wscratch.p,
+                                  (cudaStream_t)stream),
+           "reference delta");
+        return SOC_OK;
+    });
 }
 
 soc_status soc_dust_split(soc_ctx *ctx, int cloud_id, int n_freq, const uint8_t *d_neg, uint64_t *d_alloc,
                           uint64_t *d_alloc_neg, const double *d_e_unit, double *d_e_unit_neg, void *stream)
 {
-    soc_status st = check_cloud(ctx, cloud_id);
-    if (st) return st;
-    if (!d_neg || !d_alloc || !d_alloc_neg || !d_e_unit || !d_e_unit_neg || n_freq < 1 || d_alloc == d_alloc_neg)
-        return fail(ctx, SOC_ERR_ARG, "bad split arguments");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    const CloudHost &cl = *ctx->clouds[cloud_id];
-    CK(launch_dust_split(cl.n_leaf, n_freq, d_neg, d_alloc, d_alloc_neg, d_e_unit, d_e_unit_neg,
-                         (cudaStream_t)stream),
-       "dust split");
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        if (!d_neg || !d_alloc || !d_alloc_neg || !d_e_unit || !d_e_unit_neg || n_freq < 1 || d_alloc == d_alloc_neg)
+            return fail(ctx, SOC_ERR_ARG, "bad split arguments");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        const CloudHost &cl = *ctx->clouds[cloud_id];
+        CK(launch_dust_split(cl.n_leaf, n_freq, d_neg, d_alloc, d_alloc_neg, d_e_unit, d_e_unit_neg,
+                             (cudaStream_t)stream),
+           "dust split");
+        return SOC_OK;
+    });
 }
 
 soc_status soc_reference_update(soc_ctx *ctx, int cloud_id, double *d_A_ref, const double *d_A_d, double w,
                                 const double *d_A_const, double *d_A_out, int out_mean, void *stream)
 {
-    soc_status st = check_cloud(ctx, cloud_id);
-    if (st) return st;
-    if (!d_A_ref || !d_A_d || !(w >= 0.0 && w <= 1.0)) return fail(ctx, SOC_ERR_ARG, "bad reference-update arguments");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    const CloudHost &cl = *ctx->clouds[cloud_id];
-    CK(launch_reference_update(cl.n_cells, d_A_ref, d_A_d, w, d_A_const, d_A_out, out_mean != 0,
-                               (cudaStream_t)stream),
-       "reference update");
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        if (!d_A_ref || !d_A_d || !(w >= 0.0 && w <= 1.0)) return fail(ctx, SOC_ERR_ARG, "bad reference-update arguments");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        const CloudHost &cl = *ctx->clouds[cloud_id];
+        CK(launch_reference_update(cl.n_cells, d_A_ref, d_A_d, w, d_A_const, d_A_out, out_mean != 0,
+                                   (cudaStream_t)stream),
+           "reference update");
+        return SOC_OK;
+    });
 }
 
 soc_status soc_absorbed_power(soc_ctx *ctx, int cloud_id, const int64_t *d_tally, int64_t tally_stride,
                               const double *d_e_unit, const double *d_A_in, double *d_A_out, void *stream)
 {
-    soc_status st = check_cloud(ctx, cloud_id);
-    if (st) return st;
-    const CloudHost &cl = *ctx->clouds[cloud_id];
-    if (!d_tally || !d_e_unit || !d_A_out || tally_stride < cl.n_cells)
-        return fail(ctx, SOC_ERR_ARG, "bad absorbed-power arguments");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    if ((st = sync_clouds(ctx))) return st;
-    CK(launch_absorbed_power(ctx->d_clouds.p + cloud_id, cl.n_cells, d_tally, tally_stride, d_e_unit, ctx->d_w.p,
-                             ctx->n_freq, d_A_in, d_A_out, (cudaStream_t)stream),
-       "absorbed power");
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        const CloudHost &cl = *ctx->clouds[cloud_id];
+        if (!d_tally || !d_e_unit || !d_A_out || tally_stride < cl.n_cells)
+            return fail(ctx, SOC_ERR_ARG, "bad absorbed-power arguments");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        if ((st = sync_clouds(ctx))) return st;
+        CK(launch_absorbed_power(ctx->d_clouds.p + cloud_id, cl.n_cells, d_tally, tally_stride, d_e_unit, ctx->d_w.p,
+                                 ctx->n_freq, d_A_in, d_A_out, (cudaStream_t)stream),
+           "absorbed power");
+        return SOC_OK;
+    });
 }
 
 soc_status soc_update_temperature(soc_ctx *ctx, int cloud_id, const double *d_A, float *d_T, double *d_max_dT,
                                   void *stream)
 {
-    soc_status st = check_cloud(ctx, cloud_id);
-    if (st) return st;
-    if (!d_A || !d_T) return fail(ctx, SOC_ERR_ARG, "null argument");
-    if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    if ((st = sync_clouds(ctx))) return st;
-    const CloudHost &cl = *ctx->clouds[cloud_id];
-    TempTables tt{ctx->n_freq, ctx->d_w_kabs.p, ctx->d_w.p, ctx->d_nu.p, ctx->d_kabs.p, ctx->d_lnE.p, ctx->d_lnT.p};
-    CK(launch_update_temperature(ctx->d_clouds.p + cloud_id, cl.n_cells, tt, d_A, d_T, d_max_dT,
-                                 (cudaStream_t)stream),
-       "temperature");
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        if (!d_A || !d_T) return fail(ctx, SOC_ERR_ARG, "null argument");
+        if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        if ((st = sync_clouds(ctx))) return st;
+        const CloudHost &cl = *ctx->clouds[cloud_id];
+        TempTables tt{ctx->n_freq, ctx->d_w_kabs.p, ctx->d_w.p, ctx->d_nu.p, ctx->d_kabs.p, ctx->d_lnE.p, ctx->d_lnT.p};
+        CK(launch_update_temperature(ctx->d_clouds.p + cloud_id, cl.n_cells, tt, d_A, d_T, d_max_dT,
+                                     (cudaStream_t)stream),
+           "temperature");
+        return SOC_OK;
+    });
 }
 
 soc_status soc_update_temperature_ali(soc_ctx *ctx, int cloud_id, const double *d_A, const double *d_A_self, float *d_T,
                                       double *d_max_dT, void *stream)
 {
-    soc_status st = check_cloud(ctx, cloud_id);
-    if (st) return st;
-    if (!d_A || !d_A_self || !d_T) return fail(ctx, SOC_ERR_ARG, "null argument");
-    if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    if ((st = sync_clouds(ctx))) return st;
-    const CloudHost &cl = *ctx->clouds[cloud_id];
-    TempTables tt{ctx->n_freq, ctx->d_w_kabs.p, ctx->d_w.p, ctx->d_nu.p, ctx->d_kabs.p, ctx->d_lnE.p, ctx->d_lnT.p};
-    CK(launch_update_temperature_ali(ctx->d_clouds.p + cloud_id, cl.n_cells, tt, d_A, d_A_self, d_T, d_max_dT,
-                                     (cudaStream_t)stream),
-       "temperature (ALI)");
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        if (!d_A || !d_A_self || !d_T) return fail(ctx, SOC_ERR_ARG, "null argument");
+        if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        if ((st = sync_clouds(ctx))) return st;
+        const CloudHost &cl = *ctx->clouds[cloud_id];
+        TempTables tt{ctx->n_freq, ctx->d_w_kabs.p, ctx->d_w.p, ctx->d_nu.p, ctx->d_kabs.p, ctx->d_lnE.p, ctx->d_lnT.p};
+        CK(launch_update_temperature_ali(ctx->d_clouds.p + cloud_id, cl.n_cells, tt, d_A, d_A_self, d_T, d_max_dT,
+                                         (cudaStream_t)stream),
+           "temperature (ALI)");
+        return SOC_OK;
+    });
 }
 
 soc_status soc_map(soc_ctx *ctx, int cloud_id, const float *d_T, int freq, const double *dir, const double *up, int npx,
                    int npy, double pix_size, const double *center, double I_bg, float *d_map, void *stream)
 {
-    soc_status st = check_cloud(ctx, cloud_id);
-    if (st) return st;
-    if (!d_T || !dir || !up || !center || !d_map || npx < 1 || npy < 1 || !(pix_size > 0.0))
-        return fail(ctx, SOC_ERR_ARG, "bad map arguments");
-    if (freq < 0 || freq >= ctx->n_freq) return fail(ctx, SOC_ERR_ARG, "bad frequency index");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    if ((st = sync_clouds(ctx))) return st;
-    const CloudHost &cl = *ctx->clouds[cloud_id];
-    MapParams M;
-    memset(&M, 0, sizeof M);
-    const double dn = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
-    if (!(dn > 0.0)) return fail(ctx, SOC_ERR_ARG, "zero view direction");
-    for (int a = 0; a < 3; ++a) M.d[a] = dir[a] / dn;
-    // e1 = up x d (normalised), e2 = d x e1
-    double e1[3] = {up[1] * M.d[2] - up[2] * M.d[1], up[2] * M.d[0] - up[0] * M.d[2], up[0] * M.d[1] - up[1] * M.d[0]};
-    const double n1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
-    if (!(n1 > 1e-12)) return fail(ctx, SOC_ERR_ARG, "up vector parallel to the view direction");
-    for (int a = 0; a < 3; ++a) M.e1[a] = e1[a] / n1;
-    M.e2[0] = M.d[1] * M.e1[2] - M.d[2] * M.e1[1];
-    M.e2[1] = M.d[2] * M.e1[0] - M.d[0] * M.e1[2];
-    M.e2[2] = M.d[0] * M.e1[1] - M.d[1] * M.e1[0];
-    for (int a = 0; a < 3; ++a) M.c[a] = center[a];
-    M.cloud = ctx->d_clouds.p + cloud_id;
-    M.T = d_T;
-    M.map = d_map;
-    M.pix = pix_size;
-    M.nu = ctx->nu[freq];
-    const double kext = ctx->kabs[freq] + ctx->ksca[freq];
-    M.kext_root = kext * cl.ell;
-    M.kabs_over_kext = kext > 0.0 ? ctx->kabs[freq] / kext : 0.0;
-    M.I_bg = I_bg;
-    M.npx = npx;
-    M.npy = npy;
-    M.max_cells = 100000000u;
-    CK(launch_map(M, (cudaStream_t)stream), "map");
-    return SOC_OK;
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        if (!d_T || !dir || !up || !center || !d_map || npx < 1 || npy < 1 || !(pix_size > 0.0))
+            return fail(ctx, SOC_ERR_ARG, "bad map arguments");
+        if (freq < 0 || freq >= ctx->n_freq) return fail(ctx, SOC_ERR_ARG, "bad frequency index");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        if ((st = sync_clouds(ctx))) return st;
+        const CloudHost &cl = *ctx->clouds[cloud_id];
+        MapParams M;
+        memset(&M, 0, sizeof M);
+        const double dn = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+        if (!(dn > 0.0)) return fail(ctx, SOC_ERR_ARG, "zero view direction");
+        for (int a = 0; a < 3; ++a) M.d[a] = dir[a] / dn;
+        // e1 = up x d (normalised), e2 = d x e1
+        double e1[3] = {up[1] * M.d[2] - up[2] * M.d[1], up[2] * M.d[0] - up[0] * M.d[2], up[0] * M.d[1] - up[1] * M.d[0]};
+        const double n1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+        if (!(n1 > 1e-12)) return fail(ctx, SOC_ERR_ARG, "up vector parallel to the view direction");
+        for (int a = 0; a < 3; ++a) M.e1[a] = e1[a] / n1;
+        M.e2[0] = M.d[1] * M.e1[2] - M.d[2] * M.e1[1];
+        M.e2[1] = M.d[2] * M.e1[0] - M.d[0] * M.e1[2];
+        M.e2[2] = M.d[0] * M.e1[1] - M.d[1] * M.e1[0];
+        for (int a = 0; a < 3; ++a) M.c[a] = center[a];
+        M.cloud = ctx->d_clouds.p + cloud_id;
+        M.T = d_T;
+        M.map = d_map;
+        M.pix = pix_size;
+        M.nu = ctx->nu[freq];
+        const double kext = ctx->kabs[freq] + ctx->ksca[freq];
+        M.kext_root = kext * cl.ell;
+        M.kabs_over_kext = kext > 0.0 ? ctx->kabs[freq] / kext : 0.0;
+        M.I_bg = I_bg;
+        M.npx = npx;
+        M.npy = npy;
+        M.max_cells = 100000000u;
+        CK(launch_map(M, (cudaStream_t)stream), "map");
+        return SOC_OK;
+    });
 }
 
 soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm, const float *d_T_seed,
                        float *d_T_out, soc_iterate_result *res, double *dT_history, void *stream)
 {
-    soc_status st = check_cloud(ctx, cloud_id);
-    if (st) return st;
-    if (!prm || !d_T_out || prm->max_iter < 0) return fail(ctx, SOC_ERR_ARG, "bad iterate arguments");
-    if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    CloudHost &cl = *ctx->clouds[cloud_id];
-    cudaStream_t s = (cudaStream_t)stream;
-    const int nf = ctx->n_freq;
-    const int64_t n = cl.n_cells;
-    if (prm->n_background && cl.bg_I.empty()) return fail(ctx, SOC_ERR_STATE, "no background uploaded");
-    if (prm->n_point && cl.n_ps == 0) return fail(ctx, SOC_ERR_STATE, "no point sources uploaded");
-    CK(cl.tally.alloc((size_t)nf * n), "alloc tally");
-    CK(cl.A_const.alloc(n), "alloc A");
-    CK(cl.A.alloc(n), "alloc A");
-    CK(cl.e_unit.alloc(nf), "alloc e_unit");
-    CK(cl.stats.alloc((size_t)4 * nf), "alloc stats");
-    if (prm->max_iter > 0) CK(cl.dust_w.alloc((size_t)nf * cl.n_leaf), "alloc dust weights");
-    const bool weighted = prm->n_weighted > 0;
-    if (weighted && prm->weighted_cap == 0) return fail(ctx, SOC_ERR_ARG, "weighted_cap must be >= 1");
-    if (weighted && prm->max_iter > 0) {
-        CK(cl.dust_wp.alloc((size_t)nf * (2 * cl.n_leaf + 1)), "alloc weighted sampling");
-        CK(cl.e_unit_w.alloc(nf), "alloc e_unit");
-    }
-    const int refmode = prm->reference_field;
-    if (refmode < 0 || refmode > 2) return fail(ctx, SOC_ERR_ARG, "reference_field must be 0, 1 or 2");
-    const bool reffield = refmode != 0;
-    if (reffield) {
-        if (prm->ali) return fail(ctx, SOC_ERR_ARG, "reference_field and ali together are not supported");
-        if (prm->weighted_cap == 0) return fail(ctx, SOC_ERR_ARG, "weighted_cap must be >= 1");
-        if (prm->n_dust_first == 0 && prm->n_weighted == 0)
-            return fail(ctx, SOC_ERR_ARG, "reference_field needs n_dust_first/n_dust_last or n_weighted");
-        if (prm->n_dust_first && prm->n_dust_last == 0)
-            return fail(ctx, SOC_ERR_ARG, "n_dust_last must be >= 1");
-    }
-    if (reffield && prm->max_iter > 0) {
-        CK(cl.A_ref.alloc(n), "alloc A_ref");
-        CK(cl.A_d.alloc(n), "alloc A_d");
-        CK(cl.dust_wp.alloc((size_t)nf * (2 * cl.n_leaf + 1)), "alloc weighted sampling");
-        CK(cl.e_unit_w.alloc(nf), "alloc e_unit");
-        CK(cudaMemsetAsync(cl.A_ref.p, 0, sizeof(double) * n, s), "zero A_ref");
-        if (refmode == 2) {
-            const size_t fl = (size_t)nf * cl.n_leaf;
-            CK(cl.L.alloc(fl), "alloc L");
-            CK(cl.L_ref.alloc(fl), "alloc L_ref");
-            CK(cl.neg.alloc(fl), "alloc signs");
-            CK(cl.dust_wn.alloc((size_t)nf * (2 * cl.n_leaf + 1)), "alloc weighted sampling");
-            CK(cl.e_unit_n.alloc(nf), "alloc e_unit");
-            CK(cudaMemsetAsync(cl.L_ref.p, 0, sizeof(double) * fl, s), "zero L_ref");
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        if (!prm || !d_T_out || prm->max_iter < 0) return fail(ctx, SOC_ERR_ARG, "bad iterate arguments");
+        if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        CloudHost &cl = *ctx->clouds[cloud_id];
+        cudaStream_t s = (cudaStream_t)stream;
+        const int nf = ctx->n_freq;
+        const int64_t n = cl.n_cells;
+        if (prm->n_background && cl.bg_I.empty()) return fail(ctx, SOC_ERR_STATE, "no background uploaded");
+        if (prm->n_point && cl.n_ps == 0) return fail(ctx, SOC_ERR_STATE, "no point sources uploaded");
+        CK(cl.tally.alloc((size_t)nf * n), "alloc tally");
+        CK(cl.A_const.alloc(n), "alloc A");
+        CK(cl.A.alloc(n), "alloc A");
+        CK(cl.e_unit.alloc(nf), "alloc e_unit");
+        CK(cl.stats.alloc((size_t)4 * nf), "alloc stats");
+        if (prm->max_iter > 0) CK(cl.dust_w.alloc((size_t)nf * cl.n_leaf), "alloc dust weights");
+        const bool weighted = prm->n_weighted > 0;
+        if (weighted && prm->weighted_cap == 0) return fail(ctx, SOC_ERR_ARG, "weighted_cap must be >= 1");
+        if (weighted && prm->max_iter > 0) {
+            CK(cl.dust_wp.alloc((size_t)nf * (2 * cl.n_leaf + 1)), "alloc weighted sampling");
+            CK(cl.e_unit_w.alloc(nf), "alloc e_unit");
         }
-    }
-    const bool ali = prm->ali != 0;
-    if (ali && prm->max_iter > 0) {
-        CK(cl.self_tally.alloc((size_t)nf * n), "alloc self counters");
-        CK(cl.A_self.alloc(n), "alloc A_self");
-    }
-    int64_t steps = 0, capped = 0;
-    std::vector<int64_t> hstats(4 * nf);
-    std::vector<soc_batch_item> items(nf);
-    std::vector<double> e(nf);
-    std::vector<uint64_t> wcount(nf, 0);
-    auto run_items = [&](int source, uint64_t npk, int iteration, const uint64_t *dw, uint32_t npc,
-                         int64_t *self, bool wsampled) -> soc_status {
-        for (int f = 0; f < nf; ++f) {
-            soc_batch_item &it = items[f];
-            memset(&it, 0, sizeof it);
-            it.cloud = cloud_id; it.freq = f; it.source = source; it.iteration = iteration;
-            it.pid_offset = 0; it.n_packages = wsampled ? wcount[f] : npk; it.w0 = SOC_W_UNIT;
-            it.tally_offset = (int64_t)f * n;
-            it.d_dust_w = dw ? dw + (size_t)f * (wsampled ? 2 * cl.n_leaf + 1 : cl.n_leaf) : nullptr;
-            it.n_per_cell = npc;
-            it.reserved = wsampled ? SOC_ITEM_WEIGHTED : 0u;
-        }
-        CK(cudaMemsetAsync(cl.tally.p, 0, sizeof(int64_t) * nf * n, s), "zero tally");
-        CK(cudaMemsetAsync(cl.stats.p, 0, sizeof(int64_t) * 4 * nf, s), "zero stats");
-        if (self) CK(cudaMemsetAsync(self, 0, sizeof(int64_t) * nf * n, s), "zero self counters");
-        soc_status r = soc_simulate_frequency_batch_ex(ctx, items.data(), nf, cl.tally.p, self, cl.stats.p, nullptr,
-                                                       stream);
-        if (r) return r;
-        CK(cudaMemcpyAsync(hstats.data(), cl.stats.p, sizeof(int64_t) * 4 * nf, cudaMemcpyDeviceToHost, s), "stats");
-        CK(cudaStreamSynchronize(s), "sync");
-        for (int f = 0; f < nf; ++f) { capped += hstats[4 * f + 1]; steps += hstats[4 * f + 2]; }
-        return SOC_OK;
-    };
-    // iteration 0: constant sources, kept as A_const
-    if (prm->reuse_constant && !cl.has_const)
-        return fail(ctx, SOC_ERR_STATE, "reuse_constant: no earlier iteration 0 on this cloud");
-    if (!prm->reuse_constant) CK(cudaMemsetAsync(cl.A_const.p, 0, sizeof(double) * n, s), "zero A");
-    const uint64_t nsrc[2] = {prm->reuse_constant ? 0 : prm->n_background, prm->reuse_constant ? 0 : prm->n_point};
-    for (int k = 0; k < 2; ++k) {
-        if (!nsrc[k]) continue;
-        const int source = k == 0 ? SOC_SRC_BACKGROUND : SOC_SRC_POINT;
-        if ((st = run_items(source, nsrc[k], 0, nullptr, 1, nullptr, false))) return st;
-        if ((st = soc_package_energy(ctx, cloud_id, source, nsrc[k], e.data()))) return st;
-        CK(cudaMemcpyAsync(cl.e_unit.p, e.data(), 8 * nf, cudaMemcpyHostToDevice, s), "copy e_unit");
-        if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit.p, cl.A_const.p, cl.A_const.p, stream)))
-            return st;
-    }
-    cl.has_const = true;
-    if (d_T_seed) {
-        CK(cudaMemcpyAsync(d_T_out, d_T_seed, sizeof(float) * n, cudaMemcpyDeviceToDevice, s), "copy seed");
-    } else {
-        if ((st = soc_update_temperature(ctx, cloud_id, cl.A_const.p, d_T_out, nullptr, stream))) return st;
-    }
-    int it_done = 0, conv = 0;
-    double dT = 0.0;
-    double n_cum = 0.0;
-    for (int k = 1; k <= prm->max_iter; ++k) {
+        const int refmode = prm->reference_field;
+        if (refmode < 0 || refmode > 2) return fail(ctx, SOC_ERR_ARG, "reference_field must be 0, 1 or 2");
+        const bool reffield = refmode != 0;
         if (reffield) {
-            // packages of this iteration: log n linear from n_dust_first to n_dust_last
-            uint64_t nk = prm->n_weighted;
-            if (prm->n_dust_first) {
-                const double t = prm->max_iter > 1 ? (double)(k - 1) / (double)(prm->max_iter - 1) : 1.0;
-                const double ratio = (double)prm->n_dust_last / (double)prm->n_dust_first;
-                nk = (uint64_t)std::max(1.0, rint((double)prm->n_dust_first * pow(ratio, t)));
-                if (prm->max_iter == 1) nk = prm->n_dust_last;
+            if (prm->ali) return fail(ctx, SOC_ERR_ARG, "reference_field and ali together are not supported");
+            if (prm->weighted_cap == 0) return fail(ctx, SOC_ERR_ARG, "weighted_cap must be >= 1");
+            if (prm->n_dust_first == 0 && prm->n_weighted == 0)
+                return fail(ctx, SOC_ERR_ARG, "reference_field needs n_dust_first/n_dust_last or n_weighted");
+            if (prm->n_dust_first && prm->n_dust_last == 0)
+                return fail(ctx, SOC_ERR_ARG, "n_dust_last must be >= 1");
+        }
+        if (reffield && prm->max_iter > 0) {
+            CK(cl.A_ref.alloc(n), "alloc A_ref");
+            CK(cl.A_d.alloc(n), "alloc A_d");
+            CK(cl.dust_wp.alloc((size_t)nf * (2 * cl.n_leaf + 1)), "alloc weighted sampling");
+            CK(cl.e_unit_w.alloc(nf), "alloc e_unit");
+            CK(cudaMemsetAsync(cl.A_ref.p, 0, sizeof(double) * n, s), "zero A_ref");
+            if (refmode == 2) {
+                const size_t fl = (size_t)nf * cl.n_leaf;
+                CK(cl.L.alloc(fl), "alloc L");
+                CK(cl.L_ref.alloc(fl), "alloc L_ref");
+                CK(cl.neg.alloc(fl), "alloc signs");
+                CK(cl.dust_wn.alloc((size_t)nf * (2 * cl.n_leaf + 1)), "alloc weighted sampling");
+                CK(cl.e_unit_n.alloc(nf), "alloc e_unit");
+                CK(cudaMemsetAsync(cl.L_ref.p, 0, sizeof(double) * fl, s), "zero L_ref");
             }
-            n_cum += (double)nk;
-            const double wk = (double)nk / n_cum;
-            if (refmode == 1) {
-                // full dust emission, fresh random numbers; A_ref = running mean of the estimates
-                if ((st = soc_dust_emission(ctx, cloud_id, d_T_out, 0, nf, 1u, cl.dust_w.p, cl.e_unit.p, stream)))
+        }
+        const bool ali = prm->ali != 0;
+        if (ali && prm->max_iter > 0) {
+            CK(cl.self_tally.alloc((size_t)nf * n), "alloc self counters");
+            CK(cl.A_self.alloc(n), "alloc A_self");
+        }
+        int64_t steps = 0, capped = 0;
+        std::vector<int64_t> hstats(4 * nf);
+        std::vector<soc_batch_item> items(nf);
+        std::vector<double> e(nf);
+        std::vector<uint64_t> wcount(nf, 0);
+        auto run_items = [&](int source, uint64_t npk, int iteration, const uint64_t *dw, uint32_t npc,
+                             int64_t *self, bool wsampled) -> soc_status {
+            for (int f = 0; f < nf; ++f) {
+                soc_batch_item &it = items[f];
+                memset(&it, 0, sizeof it);
+                it.cloud = cloud_id; it.freq = f; it.source = source; it.iteration = iteration;
+                it.pid_offset = 0; it.n_packages = wsampled ? wcount[f] : npk; it.w0 = SOC_W_UNIT;
+                it.tally_offset = (int64_t)f * n;
+                it.d_dust_w = dw ? dw + (size_t)f * (wsampled ? 2 * cl.n_leaf + 1 : cl.n_leaf) : nullptr;
+                it.n_per_cell = npc;
+                it.reserved = wsampled ? SOC_ITEM_WEIGHTED : 0u;
+            }
+            CK(cudaMemsetAsync(cl.tally.p, 0, sizeof(int64_t) * nf * n, s), "zero tally");
+            CK(cudaMemsetAsync(cl.stats.p, 0, sizeof(int64_t) * 4 * nf, s), "zero stats");
+            if (self) CK(cudaMemsetAsync(self, 0, sizeof(int64_t) * nf * n, s), "zero self counters");
+            soc_status r = soc_simulate_frequency_batch_ex(ctx, items.data(), nf, cl.tally.p, self, cl.stats.p, nullptr,
+                                                           stream);
+            if (r) return r;
+            CK(cudaMemcpyAsync(hstats.data(), cl.stats.p, sizeof(int64_t) * 4 * nf, cudaMemcpyDeviceToHost, s), "stats");
+            CK(cudaStreamSynchronize(s), "sync");
+            for (int f = 0; f < nf; ++f) { capped += hstats[4 * f + 1]; steps += hstats[4 * f + 2]; }
+            return SOC_OK;
+        };
+        // iteration 0: constant sources, kept as A_const
+        if (prm->reuse_constant && !cl.has_const)
+            return fail(ctx, SOC_ERR_STATE, "reuse_constant: no earlier iteration 0 on this cloud");
+        if (!prm->reuse_constant) CK(cudaMemsetAsync(cl.A_const.p, 0, sizeof(double) * n, s), "zero A");
+        const uint64_t nsrc[2] = {prm->reuse_constant ? 0 : prm->n_background, prm->reuse_constant ? 0 : prm->n_point};
+        for (int k = 0; k < 2; ++k) {
+            if (!nsrc[k]) continue;
+            const int source = k == 0 ? SOC_SRC_BACKGROUND : SOC_SRC_POINT;
+            if ((st = run_items(source, nsrc[k], 0, nullptr, 1, nullptr, false))) return st;
+            if ((st = soc_package_energy(ctx, cloud_id, source, nsrc[k], e.data()))) return st;
+            CK(cudaMemcpyAsync(cl.e_unit.p, e.data(), 8 * nf, cudaMemcpyHostToDevice, s), "copy e_unit");
+            if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit.p, cl.A_const.p, cl.A_const.p, stream)))
+                return st;
+        }
+        cl.has_const = true;
+        if (d_T_seed) {
+            CK(cudaMemcpyAsync(d_T_out, d_T_seed, sizeof(float) * n, cudaMemcpyDeviceToDevice, s), "copy seed");
+        } else {
+            if ((st = soc_update_temperature(ctx, cloud_id, cl.A_const.p, d_T_out, nullptr, stream))) return st;
+        }
+        int it_done = 0, conv = 0;
+        double dT = 0.0;
+        double n_cum = 0.0;
+        for (int k = 1; k <= prm->max_iter; ++k) {
+            if (reffield) {
+                // packages of this iteration: log n linear from n_dust_first to n_dust_last
+                uint64_t nk = prm->n_weighted;
+                if (prm->n_dust_first) {
+                    const double t = prm->max_iter > 1 ? (double)(k - 1) / (double)(prm->max_iter - 1) : 1.0;
+                    const double ratio = (double)prm->n_dust_last / (double)prm->n_dust_first;
+                    nk = (uint64_t)std::max(1.0, rint((double)prm->n_dust_first * pow(ratio, t)));
+                    if (prm->max_iter == 1) nk = prm->n_dust_last;
+                }
+                n_cum += (double)nk;
+                const double wk = (double)nk / n_cum;
+                if (refmode == 1) {
+                    // full dust emission, fresh random numbers; A_ref = running mean of the estimates
+                    if ((st = soc_dust_emission(ctx, cloud_id, d_T_out, 0, nf, 1u, cl.dust_w.p, cl.e_unit.p, stream)))
+                        return st;
+                    if ((st = soc_dust_weighted(ctx, cloud_id, cl.dust_w.p, cl.e_unit.p, nf, nk, prm->weighted_cap,
+                                                cl.dust_wp.p, cl.e_unit_w.p, stream)))
+                        return st;
+                    for (int f = 0; f < nf; ++f)
+                        CK(cudaMemcpyAsync(&wcount[f], cl.dust_wp.p + (size_t)f * (2 * cl.n_leaf + 1) + 2 * cl.n_leaf,
+                                           sizeof(uint64_t), cudaMemcpyDeviceToHost, s), "read package counts");
+                    CK(cudaStreamSynchronize(s), "sync");
+                    if ((st = run_items(SOC_SRC_DUST, 0, k, cl.dust_wp.p, 1, nullptr, true))) return st;
+                    if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit_w.p, nullptr, cl.A_d.p, stream)))
+                        return st;
+                    if ((st = soc_reference_update(ctx, cloud_id, cl.A_ref.p, cl.A_d.p, wk, cl.A_const.p, cl.A.p, 1,
+                                                   stream)))
+                        return st;
+                    if ((st = soc_update_temperature(ctx, cloud_id, cl.A.p, d_T_out, ctx->d_maxdT.p, stream))) return st;
+                    CK(cudaMemcpyAsync(&dT, ctx->d_maxdT.p, sizeof(double), cudaMemcpyDeviceToHost, s), "read max dT");
+                    CK(cudaStreamSynchronize(s), "sync");
+                    if (dT_history) dT_history[k - 1] = dT;
+                    it_done = k;
+                    if (dT < prm->dT_tol) { conv = 1; break; }
+                    continue;
+                }
+                if ((st = soc_dust_luminosity(ctx, cloud_id, d_T_out, 0, nf, cl.L.p, stream))) return st;
+                if ((st = soc_reference_delta(ctx, cloud_id, nf, cl.L.p, cl.L_ref.p, wk, cl.dust_w.p, cl.neg.p,
+                                              cl.e_unit.p, stream)))
                     return st;
                 if ((st = soc_dust_weighted(ctx, cloud_id, cl.dust_w.p, cl.e_unit.p, nf, nk, prm->weighted_cap,
                                             cl.dust_wp.p, cl.e_unit_w.p, stream)))
+                    return st;
+                if ((st = soc_dust_split(ctx, cloud_id, nf, cl.neg.p, cl.dust_wp.p, cl.dust_wn.p, cl.e_unit_w.p,
+                                         cl.e_unit_n.p, stream)))
                     return st;
                 for (int f = 0; f < nf; ++f)
                     CK(cudaMemcpyAsync(&wcount[f], cl.dust_wp.p + (size_t)f * (2 * cl.n_leaf + 1) + 2 * cl.n_leaf,
                                        sizeof(uint64_t), cudaMemcpyDeviceToHost, s), "read package counts");
                 CK(cudaStreamSynchronize(s), "sync");
+                // rising cells, then falling cells (same packages ids, weights of the other sign are 0)
                 if ((st = run_items(SOC_SRC_DUST, 0, k, cl.dust_wp.p, 1, nullptr, true))) return st;
-                if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit_w.p, nullptr, cl.A_d.p, stream)))
+                if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit_w.p, cl.A_ref.p, cl.A_d.p, stream)))
                     return st;
-                if ((st = soc_reference_update(ctx, cloud_id, cl.A_ref.p, cl.A_d.p, wk, cl.A_const.p, cl.A.p, 1,
-                                               stream)))
+                if ((st = run_items(SOC_SRC_DUST, 0, k, cl.dust_wn.p, 1, nullptr, true))) return st;
+                if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit_n.p, cl.A_d.p, cl.A_d.p, stream)))
+                    return st;
+                if ((st = soc_reference_update(ctx, cloud_id, cl.A_ref.p, cl.A_d.p, wk, cl.A_const.p, cl.A.p, 0, stream)))
                     return st;
                 if ((st = soc_update_temperature(ctx, cloud_id, cl.A.p, d_T_out, ctx->d_maxdT.p, stream))) return st;
                 CK(cudaMemcpyAsync(&dT, ctx->d_maxdT.p, sizeof(double), cudaMemcpyDeviceToHost, s), "read max dT");
@@ -1278,86 +1399,56 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
                 if (dT < prm->dT_tol) { conv = 1; break; }
                 continue;
             }
-            if ((st = soc_dust_luminosity(ctx, cloud_id, d_T_out, 0, nf, cl.L.p, stream))) return st;
-            if ((st = soc_reference_delta(ctx, cloud_id, nf, cl.L.p, cl.L_ref.p, wk, cl.dust_w.p, cl.neg.p,
-                                          cl.e_unit.p, stream)))
+            if ((st = soc_dust_emission(ctx, cloud_id, d_T_out, 0, nf, weighted ? 1u : prm->n_per_cell, cl.dust_w.p,
+                                        cl.e_unit.p, stream)))
                 return st;
-            if ((st = soc_dust_weighted(ctx, cloud_id, cl.dust_w.p, cl.e_unit.p, nf, nk, prm->weighted_cap,
-                                        cl.dust_wp.p, cl.e_unit_w.p, stream)))
+            const double *e_dust = cl.e_unit.p;
+            if (weighted && k == 1) {
+                // the allocation is made once, from the first dust temperatures,
+                // and then frozen (only the weights follow T)
+                if ((st = soc_dust_weighted(ctx, cloud_id, cl.dust_w.p, cl.e_unit.p, nf, prm->n_weighted,
+                                            prm->weighted_cap, cl.dust_wp.p, cl.e_unit_w.p, stream)))
+                    return st;
+                for (int f = 0; f < nf; ++f)        // packages to trace = last prefix entry of each frequency
+                    CK(cudaMemcpyAsync(&wcount[f], cl.dust_wp.p + (size_t)f * (2 * cl.n_leaf + 1) + 2 * cl.n_leaf,
+                                       sizeof(uint64_t), cudaMemcpyDeviceToHost, s), "read package counts");
+                CK(cudaStreamSynchronize(s), "sync");
+            } else if (weighted) {
+                if ((st = soc_dust_reweight(ctx, cloud_id, cl.dust_w.p, cl.e_unit.p, nf, cl.dust_wp.p, cl.e_unit_w.p,
+                                            stream)))
+                    return st;
+            }
+            if (weighted) e_dust = cl.e_unit_w.p;
+            // frozen dust random numbers: the same RNG stream (iteration 1) every time
+            if ((st = run_items(SOC_SRC_DUST, (uint64_t)cl.n_leaf * prm->n_per_cell, 1,
+                                weighted ? cl.dust_wp.p : cl.dust_w.p, prm->n_per_cell, ali ? cl.self_tally.p : nullptr,
+                                weighted)))
                 return st;
-            if ((st = soc_dust_split(ctx, cloud_id, nf, cl.neg.p, cl.dust_wp.p, cl.dust_wn.p, cl.e_unit_w.p,
-                                     cl.e_unit_n.p, stream)))
+            if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, e_dust, cl.A_const.p, cl.A.p, stream)))
                 return st;
-            for (int f = 0; f < nf; ++f)
-                CK(cudaMemcpyAsync(&wcount[f], cl.dust_wp.p + (size_t)f * (2 * cl.n_leaf + 1) + 2 * cl.n_leaf,
-                                   sizeof(uint64_t), cudaMemcpyDeviceToHost, s), "read package counts");
-            CK(cudaStreamSynchronize(s), "sync");
-            // rising cells, then falling cells (same packages ids, weights of the other sign are 0)
-            if ((st = run_items(SOC_SRC_DUST, 0, k, cl.dust_wp.p, 1, nullptr, true))) return st;
-            if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit_w.p, cl.A_ref.p, cl.A_d.p, stream)))
+            if (ali) {
+                if ((st = soc_absorbed_power(ctx, cloud_id, cl.self_tally.p, n, e_dust, nullptr, cl.A_self.p, stream)))
+                    return st;
+                if ((st = soc_update_temperature_ali(ctx, cloud_id, cl.A.p, cl.A_self.p, d_T_out, ctx->d_maxdT.p, stream)))
+                    return st;
+            } else if ((st = soc_update_temperature(ctx, cloud_id, cl.A.p, d_T_out, ctx->d_maxdT.p, stream))) {
                 return st;
-            if ((st = run_items(SOC_SRC_DUST, 0, k, cl.dust_wn.p, 1, nullptr, true))) return st;
-            if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, cl.e_unit_n.p, cl.A_d.p, cl.A_d.p, stream)))
-                return st;
-            if ((st = soc_reference_update(ctx, cloud_id, cl.A_ref.p, cl.A_d.p, wk, cl.A_const.p, cl.A.p, 0, stream)))
-                return st;
-            if ((st = soc_update_temperature(ctx, cloud_id, cl.A.p, d_T_out, ctx->d_maxdT.p, stream))) return st;
+            }
             CK(cudaMemcpyAsync(&dT, ctx->d_maxdT.p, sizeof(double), cudaMemcpyDeviceToHost, s), "read max dT");
             CK(cudaStreamSynchronize(s), "sync");
             if (dT_history) dT_history[k - 1] = dT;
             it_done = k;
             if (dT < prm->dT_tol) { conv = 1; break; }
-            continue;
         }
-        if ((st = soc_dust_emission(ctx, cloud_id, d_T_out, 0, nf, weighted ? 1u : prm->n_per_cell, cl.dust_w.p,
-                                    cl.e_unit.p, stream)))
-            return st;
-        const double *e_dust = cl.e_unit.p;
-        if (weighted && k == 1) {
-            // the allocation is made once, from the first dust temperatures,
-            // and then frozen (only the weights follow T)
-            if ((st = soc_dust_weighted(ctx, cloud_id, cl.dust_w.p, cl.e_unit.p, nf, prm->n_weighted,
-                                        prm->weighted_cap, cl.dust_wp.p, cl.e_unit_w.p, stream)))
-                return st;
-            for (int f = 0; f < nf; ++f)        // packages to trace = last prefix entry of each frequency
-                CK(cudaMemcpyAsync(&wcount[f], cl.dust_wp.p + (size_t)f * (2 * cl.n_leaf + 1) + 2 * cl.n_leaf,
-                                   sizeof(uint64_t), cudaMemcpyDeviceToHost, s), "read package counts");
-            CK(cudaStreamSynchronize(s), "sync");
-        } else if (weighted) {
-            if ((st = soc_dust_reweight(ctx, cloud_id, cl.dust_w.p, cl.e_unit.p, nf, cl.dust_wp.p, cl.e_unit_w.p,
-                                        stream)))
-                return st;
+        if (res) {
+            res->iterations = it_done;
+            res->converged = conv;
+            res->final_max_dT = dT;
+            res->steps = steps;
+            res->capped = capped;
         }
-        if (weighted) e_dust = cl.e_unit_w.p;
-        // frozen dust random numbers: the same RNG stream (iteration 1) every time
-        if ((st = run_items(SOC_SRC_DUST, (uint64_t)cl.n_leaf * prm->n_per_cell, 1,
-                            weighted ? cl.dust_wp.p : cl.dust_w.p, prm->n_per_cell, ali ? cl.self_tally.p : nullptr,
-                            weighted)))
-            return st;
-        if ((st = soc_absorbed_power(ctx, cloud_id, cl.tally.p, n, e_dust, cl.A_const.p, cl.A.p, stream)))
-            return st;
-        if (ali) {
-            if ((st = soc_absorbed_power(ctx, cloud_id, cl.self_tally.p, n, e_dust, nullptr, cl.A_self.p, stream)))
-                return st;
-            if ((st = soc_update_temperature_ali(ctx, cloud_id, cl.A.p, cl.A_self.p, d_T_out, ctx->d_maxdT.p, stream)))
-                return st;
-        } else if ((st = soc_update_temperature(ctx, cloud_id, cl.A.p, d_T_out, ctx->d_maxdT.p, stream))) {
-            return st;
-        }
-        CK(cudaMemcpyAsync(&dT, ctx->d_maxdT.p, sizeof(double), cudaMemcpyDeviceToHost, s), "read max dT");
-        CK(cudaStreamSynchronize(s), "sync");
-        if (dT_history) dT_history[k - 1] = dT;
-        it_done = k;
-        if (dT < prm->dT_tol) { conv = 1; break; }
-    }
-    if (res) {
-        res->iterations = it_done;
-        res->converged = conv;
-        res->final_max_dT = dT;
-        res->steps = steps;
-        res->capped = capped;
-    }
-    return capped ? fail(ctx, SOC_ERR_STEP_LIMIT, "%lld packages hit the step cap", (long long)capped) : SOC_OK;
+        return capped ? fail(ctx, SOC_ERR_STEP_LIMIT, "%lld packages hit the step cap", (long long)capped) : SOC_OK;
+    });
 }
 
 }  // extern "C"
@@ -1405,100 +1496,102 @@ extern "C" soc_status soc_simulate_frequency_batch_noalloc(soc_ctx *ctx, const s
                                                            int64_t *d_tally, int64_t *d_stats, uint32_t *d_pkg_steps,
                                                            void *stream)
 {
-    if (!ctx || !items || n_items < 1 || !d_tally || !d_stats) return fail(ctx, SOC_ERR_ARG, "null argument");
-    if (n_items > kNoAllocMaxItems)
-        return fail(ctx, SOC_ERR_ARG, "n_items %d exceeds the allocation-free limit of %d items", n_items,
-                    kNoAllocMaxItems);
-    if ((int)ctx->clouds.size() > kNoAllocMaxClouds)
-        return fail(ctx, SOC_ERR_ARG, "%d grids exceed the allocation-free limit of %d grids",
-                    (int)ctx->clouds.size(), kNoAllocMaxClouds);
-    if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
-    if (ctx->device < 0 || ctx->device >= kMaxDevices) return fail(ctx, SOC_ERR_ARG, "device index too large");
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    // set-up, once per device, with that device current: the host-side name
-    // g_noalloc_scratch is only a stand-in, the kernel needs the device address
-    if (!g_noalloc_addr[ctx->device]) {
-        void *addr = nullptr;
-        CK(cudaGetSymbolAddress(&addr, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)");
-        g_noalloc_addr[ctx->device] = addr;
-    }
-    NoAllocLayout *S = static_cast<NoAllocLayout *>(g_noalloc_addr[ctx->device]);
-    cudaStream_t s = (cudaStream_t)stream;
-    t_prefix[0] = 0;
-    for (int i = 0; i < n_items; ++i) {
-        const soc_batch_item &it = items[i];
-        if (it.cloud < 0 || it.cloud >= (int)ctx->clouds.size() || ctx->clouds[it.cloud]->freed)
-            return fail(ctx, SOC_ERR_ARG, "item %d: bad or freed cloud", i);
-        const CloudHost &cl = *ctx->clouds[it.cloud];
-        if (it.freq < 0 || it.freq >= ctx->n_freq) return fail(ctx, SOC_ERR_ARG, "item %d: bad freq", i);
-        if (it.iteration < 0 || it.iteration > 65535) return fail(ctx, SOC_ERR_ARG, "item %d: bad iteration", i);
-        if (it.pid_offset + it.n_packages > 0xFFFFFFFFull || it.pid_offset > 0xFFFFFFFFull)
-            return fail(ctx, SOC_ERR_ARG, "item %d: package ids exceed 2^32", i);
-        if (it.tally_offset < 0) return fail(ctx, SOC_ERR_ARG, "item %d: negative tally offset", i);
-        if (it.source == SOC_SRC_BACKGROUND || it.source == SOC_SRC_POINT) {
-            if (it.w0 == 0 || it.w0 > SOC_W_UNIT) return fail(ctx, SOC_ERR_ARG, "item %d: w0 out of [1, 2^31]", i);
-            if (it.source == SOC_SRC_POINT && cl.n_ps == 0)
-                return fail(ctx, SOC_ERR_STATE, "item %d: cloud has no point sources", i);
-        } else if (it.source == SOC_SRC_DUST) {
-            if (!it.d_dust_w || it.n_per_cell == 0) return fail(ctx, SOC_ERR_ARG, "item %d: dust weights missing", i);
-            if (!(it.reserved & SOC_ITEM_WEIGHTED) && it.pid_offset + it.n_packages > (uint64_t)cl.n_leaf * it.n_per_cell)
-                return fail(ctx, SOC_ERR_ARG, "item %d: more dust packages than n_leaf*n_per_cell", i);
-        } else {
-            return fail(ctx, SOC_ERR_ARG, "item %d: unknown source %d", i, it.source);
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx || !items || n_items < 1 || !d_tally || !d_stats) return fail(ctx, SOC_ERR_ARG, "null argument");
+        if (n_items > kNoAllocMaxItems)
+            return fail(ctx, SOC_ERR_ARG, "n_items %d exceeds the allocation-free limit of %d items", n_items,
+                        kNoAllocMaxItems);
+        if ((int)ctx->clouds.size() > kNoAllocMaxClouds)
+            return fail(ctx, SOC_ERR_ARG, "%d grids exceed the allocation-free limit of %d grids",
+                        (int)ctx->clouds.size(), kNoAllocMaxClouds);
+        if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
+        if (ctx->device < 0 || ctx->device >= kMaxDevices) return fail(ctx, SOC_ERR_ARG, "device index too large");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        // set-up, once per device, with that device current: the host-side name
+        // g_noalloc_scratch is only a stand-in, the kernel needs the device address
+        if (!g_noalloc_addr[ctx->device]) {
+            void *addr = nullptr;
+            CK(cudaGetSymbolAddress(&addr, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)");
+            g_noalloc_addr[ctx->device] = addr;
         }
-        DevItem &d = t_items[i];
-        d.cloud = it.cloud; d.freq = it.freq; d.source = it.source; d.iteration = it.iteration;
-        d.pid_offset = (uint32_t)it.pid_offset; d.n_per_cell = it.n_per_cell ? it.n_per_cell : 1;
-        d.flags = (it.source == SOC_SRC_DUST && (it.reserved & SOC_ITEM_WEIGHTED)) ? kItemWeighted : 0u;
-        d.w0 = it.w0; d.tally_offset = it.tally_offset; d.dust_w = it.d_dust_w;
-        t_prefix[i + 1] = t_prefix[i] + it.n_packages;
-    }
-    const uint64_t total = t_prefix[n_items];
-    if (total == 0) return SOC_OK;
-    const int nc = (int)ctx->clouds.size();
-    for (int i = 0; i < nc; ++i) {
-        const CloudHost &c = *ctx->clouds[i];
-        DevCloud &d = t_clouds[i];
-        memset(&d, 0, sizeof d);
-        if (c.freed) continue;
-        d.cell = c.cell.p; d.parent = c.parent.p; d.leaf = c.leaf.p; d.rho = c.rho.p;
-        d.volume = c.volume.p; d.kappa = c.kappa.p; d.ps_pos = c.ps_pos.p; d.ps_cdf = c.ps_cdf.p;
-        d.nx = c.nx; d.ny = c.ny; d.nz = c.nz; d.n_levels = c.n_levels; d.n_ps = c.n_ps;
-        d.n_cells = c.n_cells; d.n_root = c.n_root; d.n_leaf = c.n_leaf;
-        for (int L = 0; L <= c.n_levels; ++L) d.level_start[L] = c.level_start[L];
-        for (int L = c.n_levels + 1; L <= SOC_MAX_LEVELS; ++L) d.level_start[L] = c.n_cells;
-    }
-    CK(cudaMemcpyAsync(S->clouds, t_clouds, sizeof(DevCloud) * nc, cudaMemcpyHostToDevice, s), "copy grid table");
-    CK(cudaMemcpyAsync(S->items, t_items, sizeof(DevItem) * n_items, cudaMemcpyHostToDevice, s), "copy items");
-    CK(cudaMemcpyAsync(S->prefix, t_prefix, sizeof(uint64_t) * (n_items + 1), cudaMemcpyHostToDevice, s),
-       "copy prefix");
-    CK(cudaMemsetAsync(&S->counter, 0, sizeof(unsigned long long), s), "zero counter");   // must start at 0
-    TraceParams P;
-    P.clouds = S->clouds;
-    P.items = S->items;
-    P.prefix = S->prefix;
-    P.g_hg = ctx->d_g.p;
-    P.tally = reinterpret_cast<unsigned long long *>(d_tally);
-    P.self = nullptr;
-    P.stats = reinterpret_cast<unsigned long long *>(d_stats);
-    P.pkg_steps = d_pkg_steps;
-    P.counter = &S->counter;
-    P.total = total;
-    P.seed = ctx->seed;
-    P.n_items = n_items;
-    P.max_steps = ctx->max_steps;
-    P.chunk = ctx->chunk;
-    P.refill_min = ctx->refill_min;
-    P.scatter_min = ctx->scatter_min;
-    P.hot = one_cloud(ctx, items, n_items);
-    P.regular = all_regular(ctx, items, n_items);
-    const int variant = ctx->bps >= 4 ? 4 : 3;
-    const int limit = trace_block_limit(ctx->tpb, variant, P.regular != 0);
-    const int per_sm = ctx->bps > 0 ? std::min(ctx->bps, limit) : limit;
-    const uint64_t warps_needed = (total + 31) / 32;
-    int64_t grid = (int64_t)ctx->sms * per_sm;
-    const int64_t grid_need = (int64_t)((warps_needed * 32 + ctx->tpb - 1) / ctx->tpb);
-    if (grid_need < grid) grid = grid_need < 1 ? 1 : grid_need;
-    CK(launch_trace(P, (int)grid, ctx->tpb, variant, s), "trace launch");
-    return SOC_OK;
+        NoAllocLayout *S = static_cast<NoAllocLayout *>(g_noalloc_addr[ctx->device]);
+        cudaStream_t s = (cudaStream_t)stream;
+        t_prefix[0] = 0;
+        for (int i = 0; i < n_items; ++i) {
+            const soc_batch_item &it = items[i];
+            if (it.cloud < 0 || it.cloud >= (int)ctx->clouds.size() || ctx->clouds[it.cloud]->freed)
+                return fail(ctx, SOC_ERR_ARG, "item %d: bad or freed cloud", i);
+            const CloudHost &cl = *ctx->clouds[it.cloud];
+            if (it.freq < 0 || it.freq >= ctx->n_freq) return fail(ctx, SOC_ERR_ARG, "item %d: bad freq", i);
+            if (it.iteration < 0 || it.iteration > 65535) return fail(ctx, SOC_ERR_ARG, "item %d: bad iteration", i);
+            if (it.pid_offset + it.n_packages > 0xFFFFFFFFull || it.pid_offset > 0xFFFFFFFFull)
+                return fail(ctx, SOC_ERR_ARG, "item %d: package ids exceed 2^32", i);
+            if (it.tally_offset < 0) return fail(ctx, SOC_ERR_ARG, "item %d: negative tally offset", i);
+            if (it.source == SOC_SRC_BACKGROUND || it.source == SOC_SRC_POINT) {
+                if (it.w0 == 0 || it.w0 > SOC_W_UNIT) return fail(ctx, SOC_ERR_ARG, "item %d: w0 out of [1, 2^31]", i);
+                if (it.source == SOC_SRC_POINT && cl.n_ps == 0)
+                    return fail(ctx, SOC_ERR_STATE, "item %d: cloud has no point sources", i);
+            } else if (it.source == SOC_SRC_DUST) {
+                if (!it.d_dust_w || it.n_per_cell == 0) return fail(ctx, SOC_ERR_ARG, "item %d: dust weights missing", i);
+                if (!(it.reserved & SOC_ITEM_WEIGHTED) && it.pid_offset + it.n_packages > (uint64_t)cl.n_leaf * it.n_per_cell)
+                    return fail(ctx, SOC_ERR_ARG, "item %d: more dust packages than n_leaf*n_per_cell", i);
+            } else {
+                return fail(ctx, SOC_ERR_ARG, "item %d: unknown source %d", i, it.source);
+            }
+            DevItem &d = t_items[i];
+            d.cloud = it.cloud; d.freq = it.freq; d.source = it.source; d.iteration = it.iteration;
+            d.pid_offset = (uint32_t)it.pid_offset; d.n_per_cell = it.n_per_cell ? it.n_per_cell : 1;
+            d.flags = (it.source == SOC_SRC_DUST && (it.reserved & SOC_ITEM_WEIGHTED)) ? kItemWeighted : 0u;
+            d.w0 = it.w0; d.tally_offset = it.tally_offset; d.dust_w = it.d_dust_w;
+            t_prefix[i + 1] = t_prefix[i] + it.n_packages;
+        }
+        const uint64_t total = t_prefix[n_items];
+        if (total == 0) return SOC_OK;
+        const int nc = (int)ctx->clouds.size();
+        for (int i = 0; i < nc; ++i) {
+            const CloudHost &c = *ctx->clouds[i];
+            DevCloud &d = t_clouds[i];
+            memset(&d, 0, sizeof d);
+            if (c.freed) continue;
+            d.cell = c.cell.p; d.parent = c.parent.p; d.leaf = c.leaf.p; d.rho = c.rho.p;
+            d.volume = c.volume.p; d.kappa = c.kappa.p; d.ps_pos = c.ps_pos.p; d.ps_cdf = c.ps_cdf.p;
+            d.nx = c.nx; d.ny = c.ny; d.nz = c.nz; d.n_levels = c.n_levels; d.n_ps = c.n_ps;
+            d.n_cells = c.n_cells; d.n_root = c.n_root; d.n_leaf = c.n_leaf;
+            for (int L = 0; L <= c.n_levels; ++L) d.level_start[L] = c.level_start[L];
+            for (int L = c.n_levels + 1; L <= SOC_MAX_LEVELS; ++L) d.level_start[L] = c.n_cells;
+        }
+        CK(cudaMemcpyAsync(S->clouds, t_clouds, sizeof(DevCloud) * nc, cudaMemcpyHostToDevice, s), "copy grid table");
+        CK(cudaMemcpyAsync(S->items, t_items, sizeof(DevItem) * n_items, cudaMemcpyHostToDevice, s), "copy items");
+        CK(cudaMemcpyAsync(S->prefix, t_prefix, sizeof(uint64_t) * (n_items + 1), cudaMemcpyHostToDevice, s),
+           "copy prefix");
+        CK(cudaMemsetAsync(&S->counter, 0, sizeof(unsigned long long), s), "zero counter");   // must start at 0
+        TraceParams P;
+        P.clouds = S->clouds;
+        P.items = S->items;
+        P.prefix = S->prefix;
+        P.g_hg = ctx->d_g.p;
+        P.tally = reinterpret_cast<unsigned long long *>(d_tally);
+        P.self = nullptr;
+        P.stats = reinterpret_cast<unsigned long long *>(d_stats);
+        P.pkg_steps = d_pkg_steps;
+        P.counter = &S->counter;
+        P.total = total;
+        P.seed = ctx->seed;
+        P.n_items = n_items;
+        P.max_steps = ctx->max_steps;
+        P.chunk = ctx->chunk;
+        P.refill_min = ctx->refill_min;
+        P.scatter_min = ctx->scatter_min;
+        P.hot = one_cloud(ctx, items, n_items);
+        P.regular = all_regular(ctx, items, n_items);
+        const int variant = ctx->bps >= 4 ? 4 : 3;
+        const int limit = trace_block_limit(ctx->tpb, variant, P.regular != 0);
+        const int per_sm = ctx->bps > 0 ? std::min(ctx->bps, limit) : limit;
+        const uint64_t warps_needed = (total + 31) / 32;
+        int64_t grid = (int64_t)ctx->sms * per_sm;
+        const int64_t grid_need = (int64_t)((warps_needed * 32 + ctx->tpb - 1) / ctx->tpb);
+        if (grid_need < grid) grid = grid_need < 1 ? 1 : grid_need;
+        CK(launch_trace(P, (int)grid, ctx->tpb, variant, s), "trace launch");
+        return SOC_OK;
+    });
 }
