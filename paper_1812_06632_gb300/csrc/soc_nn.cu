@@ -1019,7 +1019,13 @@ soc_status soc_unet_create(int device, int batch, int side, int *net_id)
         cudaMemset(n->w32[l].p, 0, n->w32[l].n * 4); cudaMemset(n->b32[l].p, 0, n->b32[l].n * 4);
         cudaMemset(n->w16[l].p, 0, n->w16[l].n * 2);
     }
-    g_nets.nets.push_back(n);
+    try {                                  // no exception crosses the C ABI
+        g_nets.nets.push_back(n);
+    } catch (...) {
+        n->release();
+        delete n;
+        return SOC_ERR_NOMEM;
+    }
     *net_id = (int)g_nets.nets.size() - 1;
     return SOC_OK;
 }
