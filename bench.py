@@ -529,6 +529,29 @@ UNET_LAYERS = [(16, 16, 0), (16, 16, 0), (16, 32, 1), (32, 32, 1), (32, 64, 2), 
                (16, 16, 0)]
 
 
+def run_learned(args):
+    """The second half of the headline metric: wall time to converged T
+    (max|dT| < 0.1 K with frozen dust random numbers), learned-seeded against
+    plain, on the same GPU.  Generates the training clouds with the plain
+    Monte Carlo path, trains the U-Net, then runs the test clouds both ways
+    (about a minute and a half in all)."""
+    import torch
+    from paper_1812_06632_gb300 import build as B
+    B.build()
+    from paper_1812_06632_gb300 import learned as L
+    torch.cuda.set_device(0)
+    s = L.run(log=lambda *a, **k: None)
+    n = s["n_test"]
+    out = {"metric": "wall time to converged T (max|dT|<0.1K), learned-seeded", "value": s["learned_total_s"] / n,
+           "unit": "s per cloud", "higher_is_better": False, "workload": "learned",
+           "plain_value": s["plain_total_s"] / n, "learned_over_plain": s["learned_total_s"] / s["plain_total_s"],
+           "learned_dust_iterations_mean": s["learned_iters_mean"], "plain_dust_iterations_mean": s["plain_iters_mean"],
+           "data_seconds": s["data_seconds"], "train_seconds": s["train_seconds"],
+           "config": {"workload": f"{n} test clouds of {s['side']}^3 (C4 recipe), {s['n_train']} training clouds, "
+                                  f"{s['epochs']} epochs, tolerance {s['tol_K']} K"}}
+    print(json.dumps(out), flush=True)
+
+
 def run_unet(args):
     """Learned-seed network (batch 4, 64^3): forward and training step
     (forward, input and weight gradients, Adam) timed with CUDA events;
@@ -615,9 +638,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=8192, help="oracle packages per frequency")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "unet"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "unet", "learned"],
                     help="c2 (default, the headline 128^3 x 64 nu pass), c3 octree, c5 uneven 64-cloud batch, "
-                         "unet (the learned seed's network)")
+                         "unet (the learned seed's network), learned (time to convergence, learned vs plain)")
     ap.add_argument("--freq-stride", type=int, default=1,
                     help="trace every k-th frequency only (profiling captures of a smaller case)")
     ap.add_argument("--packages", type=int, default=N_PACKAGES,
@@ -629,6 +652,8 @@ def main():
         run_reference(args)
     elif args.workload == "unet":
         run_unet(args)
+    elif args.workload == "learned":
+        run_learned(args)
     elif args.workload != "c2":
         run_extra(args)
     else:

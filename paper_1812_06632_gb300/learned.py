@@ -217,6 +217,34 @@ def seed_bound(seeds, side=64, max_iter=60, tol=0.1, other_seed=7, log=print):
     return rows
 
 
+def run(side=64, n_train=160, n_test=20, epochs=60, max_iter=60, tol=0.1, lr=2e-3, log=print):
+    """The whole comparison: data from the plain Monte Carlo path (training
+    clouds), training, then plain against learned-seeded runs to max|dT| <
+    tol on the test clouds.  Returns the summary (times in seconds)."""
+    t0 = time.perf_counter()
+    train_seeds = np.arange(1000, 1000 + n_train)
+    test_seeds = np.arange(2000, 2000 + n_test)
+    T1, T, rho, info = make_dataset(train_seeds, side, max_iter, tol, log=log)
+    t_data = time.perf_counter() - t0
+    stats = norm_stats(T1, rho)
+    X = np.stack([features(T1[i], rho[i], side, stats) for i in range(len(train_seeds))])
+    Y = (np.log(np.clip(T, T_MIN, T_MAX)) - np.log(np.clip(T1, T_MIN, T_MAX))).reshape(-1, side, side, side)
+    stats["y_mean"] = float(Y.mean())
+    stats["y_std"] = float(Y.std() + 1e-12)
+    Y = ((Y - stats["y_mean"]) / stats["y_std"]).astype(np.float32)
+    t1 = time.perf_counter()
+    net, hist = train(X, Y, side, epochs=epochs, lr=lr, log=log)
+    t_train = time.perf_counter() - t1
+    rows = compare(net, test_seeds, side, stats, max_iter, tol, log=log)
+    summary = dict(side=side, n_train=n_train, n_test=n_test, epochs=epochs, tol_K=tol,
+                   data_seconds=t_data, train_seconds=t_train, loss_history=hist, train_info=info,
+                   test=rows, norm=stats,
+                   plain_total_s=sum(r["plain_s"] for r in rows), learned_total_s=sum(r["learned_s"] for r in rows),
+                   plain_iters_mean=float(np.mean([r["plain_iters"] for r in rows])),
+                   learned_iters_mean=float(np.mean([r["learned_iters"] for r in rows])))
+    return summary
+
+
 def main():
     ap = argparse.ArgumentParser(description="learned temperature seed: data, training, comparison")
     ap.add_argument("--side", type=int, default=64)
@@ -235,27 +263,7 @@ def main():
         keys = ["own_converged_iters", "other_realisation_iters", "T1_iters"]
         print(json.dumps({k: float(np.mean([r[k] for r in rows])) for k in keys}))
         return
-    t0 = time.perf_counter()
-    train_seeds = np.arange(1000, 1000 + a.train)
-    test_seeds = np.arange(2000, 2000 + a.test)
-    T1, T, rho, info = make_dataset(train_seeds, a.side, a.max_iter, a.tol)
-    t_data = time.perf_counter() - t0
-    stats = norm_stats(T1, rho)
-    X = np.stack([features(T1[i], rho[i], a.side, stats) for i in range(len(train_seeds))])
-    Y = (np.log(np.clip(T, T_MIN, T_MAX)) - np.log(np.clip(T1, T_MIN, T_MAX))).reshape(-1, a.side, a.side, a.side)
-    stats["y_mean"] = float(Y.mean())
-    stats["y_std"] = float(Y.std() + 1e-12)
-    Y = ((Y - stats["y_mean"]) / stats["y_std"]).astype(np.float32)
-    t1 = time.perf_counter()
-    net, hist = train(X, Y, a.side, epochs=a.epochs, lr=a.lr)
-    t_train = time.perf_counter() - t1
-    rows = compare(net, test_seeds, a.side, stats, a.max_iter, a.tol)
-    summary = dict(side=a.side, n_train=a.train, n_test=a.test, epochs=a.epochs, tol_K=a.tol,
-                   data_seconds=t_data, train_seconds=t_train, loss_history=hist, train_info=info,
-                   test=rows, norm=stats,
-                   plain_total_s=sum(r["plain_s"] for r in rows), learned_total_s=sum(r["learned_s"] for r in rows),
-                   plain_iters_mean=float(np.mean([r["plain_iters"] for r in rows])),
-                   learned_iters_mean=float(np.mean([r["learned_iters"] for r in rows])))
+    summary = run(a.side, a.train, a.test, a.epochs, a.max_iter, a.tol, a.lr)
     os.makedirs(os.path.dirname(a.out) or ".", exist_ok=True)
     with open(a.out, "w") as f:
         json.dump(summary, f, indent=1)
