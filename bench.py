@@ -37,8 +37,8 @@ WORKLOAD = "lognormal 128^3, 64 nu (3e11-3e15 Hz), 1e6 background packages/nu, H
 # DRAM bytes (read + write) per photon-cell step of trace_kernel from one ncu
 # capture (small case of the same workload, scaled by steps), valid only for
 # the kernel source it was taken on.
-TRACE_DRAM = {"source_sha1": "b046d4a358f0ccee50fe3853d628366d8edbb00e", "bytes_per_step": 2.2889,
-              "warp_instructions_per_step": 8.577, "l2_bytes_per_step": 74.15,
+TRACE_DRAM = {"source_sha1": "75cc69b4e9403b22d34aa1a752f6d63d6783bbf2", "bytes_per_step": 2.3214,
+              "warp_instructions_per_step": 8.576, "l2_bytes_per_step": 74.15,
               "profile": "profiles/trace_kernel_lognormal128_8nu_1e6pkg_full.md"}
 # issue-rate peak: 4 warp-instructions per cycle per SM (4 schedulers)
 ISSUE_PER_SM_CYCLE = 4

@@ -114,6 +114,8 @@ struct GlobalCloud {
 // step waits on).  Levels 0 .. SOC_MAX_LEVELS-2 are enough, since only cells
 // above the deepest level have children.
 constexpr int kAncRows = SOC_MAX_LEVELS - 1;
+// lanes that wait for a descent before the warp runs the descent phase
+constexpr int kDescendMin = 4;
 
 // Level of a cell from its side h = 2^-L (h only ever halves or doubles).
 __device__ __forceinline__ int level_of(float h)
@@ -322,11 +324,21 @@ __device__ bool emit(const DevCloud &C, const DevItem &it, uint32_t pid, Rng &r,
     return true;
 }
 
+// Entered cell of an octree crossing in the tracer: a leaf gives its
+// density; a refined cell leaves rho = -1, "descent pending", and the warp
+// runs the descent in a phase of its own (trace_kernel) instead of here.
+__device__ __forceinline__ void enter_cell(const uint32_t *__restrict__ cells, Pkg &p)
+{
+    const uint32_t w = __ldg(cells + p.cell);
+    p.rho = (w & kLinkBit) ? -1.0f : __uint_as_float(w);
+}
+
 // Cross the face on axis `ax`: the package sits on it in the current frame.
 // Returns false when it leaves the root grid.  kRegular: every cell is a
 // root leaf (a one-level grid), so there is nothing to climb or descend.
-// kStack: climbs pop the lane's ancestor rows and descents push them (the
-// same cells the parent links give).
+// kStack (the tracer's octree builds): climbs pop the lane's ancestor rows,
+// and the descent into a refined neighbour is left pending (enter_cell);
+// otherwise (maps) the parent links are followed and the descent is done here.
 template <bool kRegular = false, bool kStack = false, class CC>
 __device__ bool cross_face(const CC &C, Pkg &p, int ax, bool up, int32_t *anc = nullptr)
 {
@@ -341,7 +353,8 @@ __device__ bool cross_face(const CC &C, Pkg &p, int ax, bool up, int32_t *anc = 
             p.x = (ax == 0) ? v : p.x;
             p.y = (ax == 1) ? v : p.y;
             p.z = (ax == 2) ? v : p.z;
-            descend<kStack>(C.cell(), p, anc);
+            if (kStack) enter_cell(C.cell(), p);
+            else descend(C.cell(), p);
             return true;
         }
         p.x = __fmul_rn(__fadd_rn(p.x, (float)(o & 1)), 0.5f);
@@ -365,7 +378,8 @@ __device__ bool cross_face(const CC &C, Pkg &p, int ax, bool up, int32_t *anc = 
     p.y = (ax == 1) ? v : p.y;
     p.z = (ax == 2) ? v : p.z;
     if (kRegular) p.rho = __uint_as_float(__ldg(C.cell() + p.cell));
-    else descend<kStack>(C.cell(), p, anc);
+    else if (kStack) enter_cell(C.cell(), p);
+    else descend(C.cell(), p);
     return true;
 }
 
@@ -567,19 +581,29 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
             continue;
         }
         // scattering phase: run the Henyey-Greenstein draw for the waiting
-        // lanes together once scatter_min of them wait (or every active lane
-        // does); a package's draws and operations keep their order
+        // lanes together once scatter_min of them wait (or no active lane can
+        // step); a package's draws and operations keep their order.
+        // Descent phase (octrees): lanes that crossed into a refined cell
+        // descend to the leaf together, once kDescendMin of them wait (or no
+        // lane can step), rather than each inside its own step while the
+        // rest of the warp waits.  Timed on GB300 (4.4e6-cell octree, 64 nu):
+        // 213.5 ms against 241.7 ms with the descent inside the step, counters
+        // unchanged; thresholds 1 to 6 lie within 1 %.
         {
             const unsigned act = __ballot_sync(kFull, active);
             const unsigned sc = __ballot_sync(kFull, active && p.scat);
-            if (sc && (__popc(sc) >= P.scatter_min || sc == act) && active && p.scat) {
+            const unsigned dn = kRegular ? 0u : __ballot_sync(kFull, active && p.rho < 0.0f);
+            const bool stuck = kRegular ? (sc == act) : ((act & ~(sc | dn)) == 0u);
+            if (sc && (__popc(sc) >= P.scatter_min || stuck) && active && p.scat) {
                 hg_scatter(r, g, p);
                 set_inverse(p);
                 p.tauf = -log_pos(r.u());
                 p.scat = false;
             }
+            if (!kRegular && dn && (__popc(dn) >= kDescendMin || stuck) && active && p.rho < 0.0f)
+                descend<true>(kOneCloud ? P.hot.cell : C->cell, p, anc);
         }
-        if (active && !p.scat) {
+        if (active && !p.scat && (kRegular || !(p.rho < 0.0f))) {
             // On regular grids (kRegular: no octree climbs or descents in a
             // step) two steps before the warp looks at refills and
             // scatterings again: half the passes of the scheduling code per
