@@ -552,6 +552,83 @@ def run_learned(args):
     print(json.dumps(out), flush=True)
 
 
+def _map_segments(n, d, e1, e2, center, npx, npy, pix):
+    """Leaf segments of every pixel's ray through a regular n^3 grid (root
+    units): 1 + the cell planes crossed per axis between entry and exit."""
+    px = ((np.arange(npx) + 0.5) - 0.5 * npx) * pix
+    py = ((np.arange(npy) + 0.5) - 0.5 * npy) * pix
+    X, Y = np.meshgrid(px, py)
+    o = center[None, None, :] + X[..., None] * e1[None, None, :] + Y[..., None] * e2[None, None, :]
+    t0 = np.full(X.shape, -np.inf); t1 = np.full(X.shape, np.inf)
+    for a in range(3):
+        if d[a] == 0.0:
+            continue
+        ta, tb = (0.0 - o[..., a]) / d[a], (n - o[..., a]) / d[a]
+        t0 = np.maximum(t0, np.minimum(ta, tb)); t1 = np.minimum(t1, np.maximum(ta, tb))
+    hit = t0 < t1
+    segs = np.ones(X.shape)
+    for a in range(3):
+        xa0 = np.clip(o[..., a] + t0 * d[a], 0, n - 1e-9)
+        xa1 = np.clip(o[..., a] + t1 * d[a], 0, n - 1e-9)
+        segs += np.abs(np.floor(xa1) - np.floor(xa0))
+    return float(segs[hit].sum()), int(hit.sum())
+
+
+def run_map(args):
+    """Surface-brightness maps (the mapping kernel): 2048^2 pixels of the
+    128^3 bench cloud along an oblique direction at 4 frequencies, timed with
+    CUDA events; leaf segments counted from the grid geometry."""
+    import torch
+    from paper_1812_06632_gb300 import build as B
+    B.build()
+    from paper_1812_06632_gb300 import inputs as I
+    from paper_1812_06632_gb300 import soc
+    torch.cuda.set_device(0)
+    w = I.config_c2(n_packages=0)
+    cl = w.clouds[0]
+    n = cl.nx
+    ctx = soc.Context(0, w.seed)
+    ctx.dust_upload(w.dust.nu, w.dust.kabs, w.dust.ksca, w.dust.g)
+    cid = ctx.grid_upload(cl)
+    rho = torch.from_numpy(cl.rho).cuda()
+    T = (12.0 + 8.0 * torch.log1p(rho)).float()          # a smooth synthetic temperature field
+    d = np.array([1.0, 0.7, 0.4]); d /= np.linalg.norm(d)
+    up = np.array([0.0, 0.0, 1.0])
+    e1 = np.cross(up, d); e1 /= np.linalg.norm(e1)
+    e2 = np.cross(d, e1)
+    npx = npy = 2048
+    pix = 1.8 * n / npx
+    center = np.array([n / 2.0] * 3)
+    segs, rays = _map_segments(n, d, e1, e2, center, npx, npy, pix)
+    out = torch.empty((npy, npx), dtype=torch.float32, device="cuda")
+    freqs = (10, 30, 45, 60)
+    for f in freqs:
+        ctx.map(cid, T, f, d, up, npx, npy, pix, center, out)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(max(args.steps, 1)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for f in freqs:
+            ctx.map(cid, T, f, d, up, npx, npy, pix, center, out)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) / len(freqs))
+    ms = statistics.mean(ts)
+    peaks, kind = _peaks()
+    gbs = 8 * segs / (ms / 1e3) / 1e9
+    out_line = {"metric": "map leaf segments/s", "value": segs / (ms / 1e3), "unit": "segments/s",
+                "workload": "map", "ms_per_map": ms, "segments_per_map": segs, "rays_per_map": rays,
+                "pixels_per_s": npx * npy / (ms / 1e3),
+                "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                             "frac": gbs / peaks["hbm_gbs"], "bytes_per_unit": 8,
+                             "peak_source": f"{kind} hbm_gbs (copy)"},
+                "config": {"workload": f"128^3 lognormal cloud, {npx}x{npy} pixels, direction (1, 0.7, 0.4), "
+                                       f"frequencies {list(freqs)}"}}
+    ctx.close()
+    print(json.dumps(out_line), flush=True)
+
+
 def run_unet(args):
     """Learned-seed network (batch 4, 64^3): forward and training step
     (forward, input and weight gradients, Adam) timed with CUDA events;
@@ -638,7 +715,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=8192, help="oracle packages per frequency")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "unet", "learned"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "unet", "learned", "map"],
                     help="c2 (default, the headline 128^3 x 64 nu pass), c3 octree, c5 uneven 64-cloud batch, "
                          "unet (the learned seed's network), learned (time to convergence, learned vs plain)")
     ap.add_argument("--freq-stride", type=int, default=1,
@@ -654,6 +731,8 @@ def main():
         run_unet(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "map":
+        run_map(args)
     elif args.workload != "c2":
         run_extra(args)
     else:

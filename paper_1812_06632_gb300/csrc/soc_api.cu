@@ -104,6 +104,7 @@ struct soc_ctx {
     DevBuf<unsigned long long> d_wscratch;
     DevBuf<double> d_maxdT;
     DevBuf<int64_t> d_level_start;
+    DevBuf<double> d_map_S;       // per-cell source function of the last map
     // pinned staging of grid uploads (grows to the largest grid)
     uint32_t *h_stage = nullptr;
     size_t h_stage_n = 0;
@@ -289,6 +290,7 @@ void soc_destroy(soc_ctx *ctx)
     ctx->d_maxdT.release();
     ctx->d_wscratch.release();
     ctx->d_level_start.release();
+    ctx->d_map_S.release();
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     for (BatchHost *b : ctx->batches)
         if (b) { b->items.release(); b->prefix.release(); b->counter.release(); delete b; }
@@ -1216,7 +1218,9 @@ soc_status soc_map(soc_ctx *ctx, int cloud_id, const float *d_T, int freq, const
         M.npx = npx;
         M.npy = npy;
         M.max_cells = 100000000u;
-        CK(launch_map(M, (cudaStream_t)stream), "map");
+        CK(ctx->d_map_S.alloc(cl.n_cells), "map source scratch");
+        M.S = ctx->d_map_S.p;
+        CK(launch_map(M, cl.n_cells, ctx->sms, (cudaStream_t)stream), "map");
         return SOC_OK;
     });
 }

@@ -84,6 +84,7 @@ int trace_block_limit(int block, int variant, bool regular);   // max resident b
 struct MapParams {
     const DevCloud *cloud;
     const float *T;               // [n_cells]
+    double *S;                    // [n_cells] scratch: (kabs/kext) B_nu(T) per cell
     float *map;                   // [npy][npx]
     double d[3], e1[3], e2[3], c[3];
     double pix, nu, kext_root, kabs_over_kext, I_bg;
@@ -91,7 +92,8 @@ struct MapParams {
     uint32_t max_cells;
 };
 
-cudaError_t launch_map(const MapParams &m, cudaStream_t s);
+// source-function pass over the n_cells cells into m.S, then one thread per pixel
+cudaError_t launch_map(const MapParams &m, int64_t n_cells, int sms, cudaStream_t s);
 
 struct TempTables {
     int n_freq;

@@ -660,6 +660,15 @@ __device__ __forceinline__ double planck_d(double nu, double T)
     return (2.0 * h * nu * nu * nu / (c * c)) / expm1(h * nu / (k * T));
 }
 
+// Source function of every cell at the map's frequency, (kabs/kext) B_nu(T),
+// in FP64: one Planck evaluation per cell instead of one per ray segment.
+__global__ void map_source_kernel(const float *__restrict__ T, int64_t n, double nu, double ratio,
+                                  double *__restrict__ S)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+        S[c] = ratio * planck_d(nu, (double)T[c]);
+}
+
 __global__ void map_kernel(const MapParams M)
 {
     const int px = blockIdx.x * blockDim.x + threadIdx.x;
@@ -684,7 +693,7 @@ __global__ void map_kernel(const MapParams M)
         if (ta > t0) { t0 = ta; ea = a; }
         if (tb < t1) t1 = tb;
     }
-    double I = 0.0, tau = 0.0;
+    double I = 0.0, trans = 1.0;
     if (ea >= 0 && t0 < t1) {
         Pkg p;
         p.h = 1.0f;
@@ -703,7 +712,7 @@ __global__ void map_kernel(const MapParams M)
         p.x = lx; p.y = ly; p.z = lz;
         p.cell = root_cell(C, p.ri, p.rj, p.rk);
         descend(C.cell, p);
-        const double kext = M.kext_root, ratio = M.kabs_over_kext;
+        const double kext = M.kext_root;
         for (uint32_t it = 0; it < M.max_cells; ++it) {
             float s = __int_as_float(0x7f800000);
             int ax = -1;
@@ -713,9 +722,15 @@ __global__ void map_kernel(const MapParams M)
             if (ax < 0) break;
             const double dtau = (double)p.rho * kext * (double)p.h * (double)s;
             if (dtau > 0.0) {
-                const double Tc = (double)__ldg(M.T + p.cell);
-                I += ratio * planck_d(M.nu, Tc) * (-expm1(-dtau)) * exp(-tau);
-                tau += dtau;
+                // the segment emits S (1 - e^-dtau), seen through the
+                // transmission of everything in front of it.  The segment's
+                // factors are FP32 (relative error ~1e-7 each, no
+                // cancellation: 1 - e^-x by expm1f, e^-x by 1 - q below 0.5
+                // and by expf above); the sums and products stay FP64.
+                const float tf = (float)dtau;
+                const double q = (double)-expm1f(-tf);
+                I += __ldg(M.S + p.cell) * q * trans;
+                trans *= (dtau < 0.5) ? 1.0 - q : (double)expf(-tf);
             }
             const float da = (ax == 0) ? p.dx : (ax == 1) ? p.dy : p.dz;
             const bool upx = da > 0.0f;
@@ -729,13 +744,14 @@ __global__ void map_kernel(const MapParams M)
             if (!cross_face(GlobalCloud{C}, p, ax, upx)) break;
         }
     }
-    M.map[(int64_t)py * M.npx + px] = (float)(I + M.I_bg * exp(-tau));
+    M.map[(int64_t)py * M.npx + px] = (float)(I + M.I_bg * trans);
 }
 
 }  // namespace
 
-cudaError_t launch_map(const MapParams &m, cudaStream_t s)
+cudaError_t launch_map(const MapParams &m, int64_t n_cells, int sms, cudaStream_t s)
 {
+    map_source_kernel<<<sms * 4, 256, 0, s>>>(m.T, n_cells, m.nu, m.kabs_over_kext, m.S);
     dim3 block(16, 16);
     dim3 grid((m.npx + 15) / 16, (m.npy + 15) / 16);
     map_kernel<<<grid, block, 0, s>>>(m);

@@ -50,3 +50,15 @@ def test_map_octree(direction):
     T = rng.uniform(8.0, 200.0, cl.n_cells)
     up = [0, 1, 0] if abs(direction[1]) < 0.9 else [1, 0, 0]
     _compare(w, T, 9, direction, up, 33, 29, 0.31, [4.0, 4.0, 4.0], I_bg=1e-16)
+
+
+@pytest.mark.parametrize("f,I_bg", [(36, 3e-7), (40, 3e-7), (44, 1e-6), (55, 1e-6)])
+def test_map_optically_thick_with_bright_background(f, I_bg):
+    """Hot dust (300-1000 K) on lines of sight of optical depth ~4, ~12, ~40
+    and ~1000 across the cloud, in front of a background brighter than the
+    cloud's own emission: the FP32 segment factors keep the FP64
+    accumulation within the same bound."""
+    w = I.config_c2(n=32, n_freq=64, n_packages=0, tau_1um=50.0)
+    cl = w.clouds[0]
+    T = np.random.default_rng(f).uniform(300.0, 1000.0, cl.n_cells)
+    _compare(w, T, f, [0.45, 0.52, -0.73], [0, 0, 1], 48, 40, 1.1, [16.0, 16.0, 16.0], I_bg=I_bg)
