@@ -134,3 +134,30 @@ def test_weight_unit_agrees_across_header_binding_and_oracle(libsoc):
     m = re.search(r"#define\s+SOC_W_UNIT\s+(\d+)ull", src)
     header_unit = int(m.group(1))
     assert header_unit == libsoc.W_UNIT == helper_unit == oracle.W_UNIT == int(P.W_UNIT) == 1 << 31
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """With its library missing the binding raises at import: there is no
+    CPU fallback to fall through to."""
+    import subprocess
+    import sys
+    env = dict(os.environ, SOC_LIB=str(tmp_path / "absent" / "libsoc.so"))
+    r = subprocess.run([sys.executable, "-c", "import paper_1812_06632_gb300.soc"], cwd=ROOT, env=env,
+                       capture_output=True, text=True)
+    assert r.returncode != 0 and "missing" in r.stderr
+
+
+def test_product_path_never_touches_the_oracle():
+    """No file of the package or of include/ imports, links or loads the
+    oracle (only tests/, smoke() and bench.py's CPU legs may)."""
+    pat = re.compile(r"^\s*(import\s+oracle|from\s+oracle\b)|liboracle|soc_oracle", re.M)
+    hits = []
+    for d in ("paper_1812_06632_gb300", "include"):
+        for dp, _, fs in os.walk(os.path.join(ROOT, d)):
+            if "_build" in dp or "__pycache__" in dp:
+                continue
+            for f in fs:
+                if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                    if pat.search(open(os.path.join(dp, f), errors="replace").read()):
+                        hits.append(os.path.join(dp, f))
+    assert not hits, hits
