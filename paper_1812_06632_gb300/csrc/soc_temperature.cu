@@ -197,9 +197,13 @@ __device__ __forceinline__ double dust_L(const DevCloud &C, const TempTables &tt
     return __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(4.0 * kPi, rho), V), __ldg(tt.kabs + f)), B);
 }
 
+// Luminosities of every (frequency, leaf) and their maximum per frequency.
+// L is kept in the weight array (FP64 bits in the uint64 slots) for
+// dust_weight_kernel, which turns it into the weight in place: one Planck
+// evaluation per (leaf, frequency) instead of two.
 __global__ void dust_max_kernel(const DevCloud *__restrict__ dcl, int64_t n_leaf, const TempTables tt,
                                 const float *__restrict__ T, int freq_lo, int n_freq,
-                                unsigned long long *Lmax)
+                                unsigned long long *Lmax, double *__restrict__ Lout)
 {
     const DevCloud &C = *dcl;
     for (int fi = 0; fi < n_freq; ++fi) {
@@ -207,6 +211,7 @@ __global__ void dust_max_kernel(const DevCloud *__restrict__ dcl, int64_t n_leaf
         for (int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; li < n_leaf;
              li += (int64_t)gridDim.x * blockDim.x) {
             const double L = dust_L(C, tt, T, __ldg(C.leaf + li), freq_lo + fi);
+            Lout[(int64_t)fi * n_leaf + li] = L;
             m = L > m ? L : m;
         }
         block_max_to(m, Lmax + fi);
@@ -219,22 +224,21 @@ __global__ void dust_weight_kernel(const DevCloud *__restrict__ dcl, int64_t n_l
                                    const unsigned long long *__restrict__ Lmax, unsigned long long *w,
                                    double *e_unit)
 {
-    const DevCloud &C = *dcl;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (tid < n_freq) {
         const double m = __longlong_as_double((long long)Lmax[tid]);
         e_unit[tid] = __ddiv_rn(__ddiv_rn(m, (double)n_per_cell), kWUnit);
     }
     for (int64_t li = tid; li < n_leaf; li += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t cell = __ldg(C.leaf + li);
         for (int fi = 0; fi < n_freq; ++fi) {
             const double m = __longlong_as_double((long long)__ldg(Lmax + fi));
+            unsigned long long &slot = w[(int64_t)fi * n_leaf + li];
             unsigned long long W = 0;
             if (m > 0.0) {
-                const double L = dust_L(C, tt, T, cell, freq_lo + fi);
+                const double L = __longlong_as_double((long long)slot);   // from dust_max_kernel
                 W = (unsigned long long)rint(__dmul_rn(__ddiv_rn(L, m), kWUnit));
             }
-            w[(int64_t)fi * n_leaf + li] = W;
+            slot = W;
         }
     }
 }
@@ -654,7 +658,8 @@ cudaError_t launch_dust_emission(const DevCloud *dcl, int64_t n_leaf, const Temp
 {
     cudaError_t e = cudaMemsetAsync(scratch_max, 0, sizeof(unsigned long long) * n_freq, s);
     if (e != cudaSuccess) return e;
-    dust_max_kernel<<<grid_for(n_leaf, 256), 256, 0, s>>>(dcl, n_leaf, tt, T, freq_lo, n_freq, scratch_max);
+    dust_max_kernel<<<grid_for(n_leaf, 256), 256, 0, s>>>(dcl, n_leaf, tt, T, freq_lo, n_freq, scratch_max,
+                                                          reinterpret_cast<double *>(w));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int64_t n = n_leaf > n_freq ? n_leaf : n_freq;
     dust_weight_kernel<<<grid_for(n, 256), 256, 0, s>>>(dcl, n_leaf, tt, T, freq_lo, n_freq, n_per_cell,
