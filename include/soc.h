@@ -486,11 +486,10 @@ soc_status soc_nn_error_flag(int *flag);
  * Learned temperature seed (not a step of the paper's method: a 3D U-Net that
  * maps the first, noisy temperature field and the log density to the
  * converged temperature and seeds soc_iterate; the Monte Carlo iterations
- * remain its judge).  Channels-last (N, side, side, side, C) tensors; BF16
- * activations and weights on the tcgen05 tensor cores with FP32
- * accumulation in tensor memory (convolutions, input and weight gradients);
- * FP32
- * master weights, gradients and Adam moments.  Architecture: 4 levels with
+ * then check the seed and remain its fallback).  Channels-last (N, side,
+ * side, side, C) tensors; BF16 activations and weights on the tcgen05 tensor
+ * cores with FP32 accumulation in tensor memory (convolutions, input and
+ * weight gradients); FP32 master weights, gradients and Adam moments.  Architecture: 4 levels with
  * 16-32-64-128 channels, two 3x3x3 convolutions (ReLU) per level, 2x2x2 max
  * pooling, nearest 2x upsampling, skip concatenation [upsampled, skip], a
  * 3x3x3 output convolution (channel 0 = prediction).  side % 8 == 0.
