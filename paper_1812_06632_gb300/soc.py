@@ -4,6 +4,20 @@ Every computation runs in the CUDA library; this module converts NumPy
 arrays / torch tensors to pointers and raises on error statuses.  It raises
 at import time if libsoc.so has not been built (there is no fallback).
 Device buffers are torch CUDA tensors owned by the caller.
+
+A run to converged temperatures, for a cloud built by ``inputs``::
+
+    ctx = Context(0, seed=1)
+    ctx.dust_upload(nu, kabs, ksca, g)              # FP64 tables per frequency
+    cid = ctx.grid_upload(cloud)                    # validated, level-ordered octree
+    ctx.sources_upload(cid, bg_I, ps_pos, ps_L)     # background and point sources
+    T = torch.empty(cloud.n_cells, device="cuda")
+    r = ctx.iterate(cid, T, n_background=10**6, n_point=10**6, max_iter=40, dT_tol=0.1)
+    # r["iterations"], r["converged"], r["history"] (max |dT| per dust iteration)
+
+Single tracer launches (``items`` / ``simulate``), prepared batches and CUDA
+graphs, the FP64 normalisation and temperature steps, maps and the learned
+seed are exposed one call each, as in the header.
 """
 from __future__ import annotations
 
@@ -386,6 +400,16 @@ class Context:
     def iterate(self, cloud_id, T_out, *, n_background=0, n_point=0, n_per_cell=1, max_iter=0,
                 dT_tol=0.1, T_seed=None, reuse_constant=False, ali=False, n_weighted=0, weighted_cap=10000,
                 reference_field=False, n_dust_first=0, n_dust_last=0, stream=None):
+        """soc_iterate: the iteration driver.  Iteration 0 traces the constant
+        sources (n_background / n_point packages per frequency) and solves T;
+        each dust iteration re-emits from the previous T (n_per_cell per leaf,
+        or n_weighted in all with at most weighted_cap per cell) with frozen
+        random numbers, until max |dT| < dT_tol or max_iter.  T_seed (device
+        float [n_cells]) replaces iteration 0's T as the dust start;
+        ali=True uses the diagonal operator; reference_field "mean" or
+        "difference" with package counts growing from n_dust_first to
+        n_dust_last.  T_out receives the temperatures.  Returns iterations,
+        converged, final_max_dT, steps, capped and the max |dT| history."""
         modes = {False: 0, True: 1, 0: 0, 1: 1, 2: 2, "mean": 1, "difference": 2}
         p = IterateParams(n_background, n_point, n_per_cell, max_iter, dT_tol, int(reuse_constant), int(ali),
                           n_weighted, weighted_cap, modes[reference_field], n_dust_first, n_dust_last)
