@@ -405,8 +405,10 @@ class Context:
         each dust iteration re-emits from the previous T (n_per_cell per leaf,
         or n_weighted in all with at most weighted_cap per cell) with frozen
         random numbers, until max |dT| < dT_tol or max_iter.  T_seed (device
-        float [n_cells]) replaces iteration 0's T as the dust start;
-        ali=True uses the diagonal operator; reference_field "mean" or
+        float [n_cells]) replaces the constant sources' T as the dust start;
+        reuse_constant=True skips iteration 0 and reuses the constant-source
+        absorption of the previous call on this cloud; ali=True uses the
+        diagonal operator; reference_field "mean" or
         "difference" with package counts growing from n_dust_first to
         n_dust_last.  T_out receives the temperatures.  Returns iterations,
         converged, final_max_dT, steps, capped and the max |dT| history."""
