@@ -176,6 +176,21 @@ def test_step_cap_matches_oracle():
     _compare_item(w, 0, spec, tally, stats[0], steps, cl.n_cells)
 
 
+def test_step_cap_on_an_octree_matches_oracle():
+    """Capped packages on an octree, where a crossing into a refined cell
+    leaves the descent to the warp's descent phase: the cap still ends each
+    package after the same steps, in the same leaf, as the oracle."""
+    w = I.config_c3(root_n=8, max_refine=3, threshold=3.0, tau_peak_1um=80.0, n_freq=8)
+    cl = w.clouds[0]
+    ctx, ids = gpu_context(w)
+    ctx.set_max_steps(7)
+    for src in (0, 1):
+        spec = dict(source=src, freq=5, n_packages=3000)
+        tally, stats, steps = run_gpu(ctx, [spec], cl.n_cells)
+        assert stats[0][1] > 0 and steps.max() == 7
+        _compare_item(w, 0, dict(spec, max_steps=7), tally, stats[0], steps, cl.n_cells)
+
+
 @pytest.mark.parametrize("case", ["one_cell", "empty_density", "opaque"])
 def test_degenerate_grids(case):
     if case == "one_cell":
