@@ -37,7 +37,7 @@ WORKLOAD = "lognormal 128^3, 64 nu (3e11-3e15 Hz), 1e6 background packages/nu, H
 # DRAM bytes (read + write) per photon-cell step of trace_kernel from one ncu
 # capture (small case of the same workload, scaled by steps), valid only for
 # the kernel source it was taken on.
-TRACE_DRAM = {"source_sha1": "802596e6be1f42c6bb15bbc3e42ef09cfdc4fbc7", "bytes_per_step": 2.3701,
+TRACE_DRAM = {"source_sha1": "75097b93f7958fab4aef04583d48a9afa1f6423c", "bytes_per_step": 2.3019,
               "warp_instructions_per_step": 8.576, "l2_bytes_per_step": 74.15,
               "profile": "profiles/trace_kernel_lognormal128_8nu_1e6pkg_full.md"}
 # issue-rate peak: 4 warp-instructions per cycle per SM (4 schedulers)

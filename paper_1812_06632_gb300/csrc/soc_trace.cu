@@ -712,7 +712,7 @@ __global__ void map_kernel(const MapParams M)
         p.x = lx; p.y = ly; p.z = lz;
         p.cell = root_cell(C, p.ri, p.rj, p.rk);
         descend(C.cell, p);
-        const double kext = M.kext_root;
+        const float kext = (float)M.kext_root;
         for (uint32_t it = 0; it < M.max_cells; ++it) {
             float s = __int_as_float(0x7f800000);
             int ax = -1;
@@ -720,17 +720,18 @@ __global__ void map_kernel(const MapParams M)
             if (p.dy != 0.0f) { const float si = __fmul_rn(__fsub_rn(p.dy > 0.0f ? 1.0f : 0.0f, p.y), p.iy); if (si < s) { s = si; ax = 1; } }
             if (p.dz != 0.0f) { const float si = __fmul_rn(__fsub_rn(p.dz > 0.0f ? 1.0f : 0.0f, p.z), p.iz); if (si < s) { s = si; ax = 2; } }
             if (ax < 0) break;
-            const double dtau = (double)p.rho * kext * (double)p.h * (double)s;
-            if (dtau > 0.0) {
+            const float dtau = __fmul_rn(__fmul_rn(__fmul_rn(p.rho, kext), p.h), s);
+            if (dtau > 0.0f) {
                 // the segment emits S (1 - e^-dtau), seen through the
                 // transmission of everything in front of it.  The segment's
-                // factors are FP32 (relative error ~1e-7 each, no
-                // cancellation: 1 - e^-x by expm1f, e^-x by 1 - q below 0.5
-                // and by expf above); the sums and products stay FP64.
-                const float tf = (float)dtau;
-                const double q = (double)-expm1f(-tf);
-                I += __ldg(M.S + p.cell) * q * trans;
-                trans *= (dtau < 0.5) ? 1.0 - q : (double)expf(-tf);
+                // optical depth and factors are FP32, as in the tracer
+                // (relative error ~1e-7 each, no cancellation: 1 - e^-x by
+                // expm1f, e^-x by 1 - q below 0.5 and by expf above); the
+                // running intensity and transmission stay FP64 (the FP64
+                // pipe bounds this kernel: four FP64 operations a segment).
+                const float q = -expm1f(-dtau);
+                I = fma(__ldg(M.S + p.cell), (double)q * trans, I);
+                trans *= (double)((dtau < 0.5f) ? __fsub_rn(1.0f, q) : expf(-dtau));
             }
             const float da = (ax == 0) ? p.dx : (ax == 1) ? p.dy : p.dz;
             const bool upx = da > 0.0f;
