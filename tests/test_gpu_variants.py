@@ -217,3 +217,42 @@ def test_deepest_octree_bit_exact(source):
     assert t[cl.level_start[2]:].sum() > 0
     if source != 0:
         assert t[cl.level_start[15]:cl.level_start[16]].sum() > 0
+
+
+def _host_mem_gb():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    return 0.0
+
+
+def test_grid_of_2_30_cells_bit_exact():
+    """A 1024^3 regular grid (2^30 cells: 4 GiB of cell words, 8 GiB of
+    counters per item, so byte offsets past 2^32 everywhere): background and
+    point-source packages give the oracle's counters bit for bit."""
+    if _host_mem_gb() < 64 or torch.cuda.get_device_properties(0).total_memory < 64 * 2 ** 30:
+        pytest.skip("needs 64 GiB of host and device memory")
+    n = 1024
+    rho = np.random.default_rng(7).random(n ** 3, dtype=np.float32)
+    rho += np.float32(0.5)
+    cl = I.regular(rho.reshape(n, n, n), ell=1.0)
+    del rho
+    dust = I.Dust(np.array([1e14]), np.array([2e-3]), np.array([1e-3]), np.array([0.4]))
+    w = I.Workload("big", [cl], dust, [np.array([1.0])], [np.array([[511.3, 300.7, 700.2]])], [np.ones((1, 1))],
+                   [0], [0], seed=17)
+    ctx, ids = gpu_context(w)
+    for src in (0, 1):
+        spec = dict(source=src, freq=0, n_packages=2000, tally_offset=0)
+        t, st, sp = run_gpu(ctx, [spec], cl.n_cells)
+        to, sto, so = oracle_item(w, 0, dict(spec, cloud=0))
+        assert np.array_equal(t, to)
+        assert st[0][0] == sto["escaped"] and st[0][2] == sto["steps"] and st[0][3] == sto["emitted"]
+        np.testing.assert_array_equal(sp, so)
+        # packages reach the far corner of the grid (cell indices near 2^30)
+        assert t[(n ** 3) * 3 // 4:].sum() > 0
+        del t, to
+    ctx.close()
