@@ -113,8 +113,12 @@ def lib64():
     global _lib64
     with _lock:
         if _lib64 is None:
-            build()
-            _lib64 = C.CDLL(_LIB64_PATH)
+            # SOC_ORACLE64_LIB: a deliberately broken copy, for the mutation tests
+            path = os.environ.get("SOC_ORACLE64_LIB")
+            if not path:
+                build()
+                path = _LIB64_PATH
+            _lib64 = C.CDLL(path)
             _lib64.oracle64_trace.argtypes = [C.POINTER(_Grid), C.POINTER(_Item), C.c_uint32, C.c_uint32,
                                               C.c_void_p, C.POINTER(_Stats64), C.c_void_p]
         return _lib64

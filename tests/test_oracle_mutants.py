@@ -48,3 +48,36 @@ def test_pins_catch_mutant(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],
                        env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+# The FP64 tracer: its own pins plus its agreement with the FP32 contract
+# (test_oracle_fp64.py) must catch a slip planted in it.
+SRC64 = os.path.join(ROOT, "oracle", "soc_oracle64.c")
+MUTANTS64 = {
+    "fp64_uniform_not_cosine_entry": ("p->d[a] = low ? sqrt(u) : -sqrt(u);", "p->d[a] = low ? u : -u;"),
+    "fp64_hg_sign": ("(1.0 + g * g - q * q) / (2.0 * g)", "(1.0 + g * g - q) / (2.0 * g)"),
+    "fp64_level_scale_dropped": ("-expm1(-rho * it->kabs * p->h * seg)", "-expm1(-rho * it->kabs * seg)"),
+    "fp64_free_path_halved": ("double tauf = -log(draw(s));", "double tauf = -0.5 * log(draw(s));"),
+    "fp64_climb_drops_octant": ("p->x[i] = 0.5 * (p->x[i] + ((oct >> i) & 1));", "p->x[i] = 0.5 * p->x[i];"),
+    "fp64_escape_not_counted": ("if (!next_cell(G, p, axis)) { st->escaped += p->W; break; }",
+                                "if (!next_cell(G, p, axis)) { break; }"),
+    "fp64_stream_key_without_freq": ("^ ((uint32_t)it->iteration << 16) ^ (uint32_t)it->freq;",
+                                     "^ ((uint32_t)it->iteration << 16);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS64))
+def test_fp64_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS64[name]
+    src = open(SRC64).read()
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    mut = tmp_path / "mut64.c"
+    mut.write_text(src.replace(old, new, 1))
+    so = tmp_path / "libmut64.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                    "-o", str(so), str(mut), SRC, "-lm"], check=True)
+    env = dict(os.environ, SOC_ORACLE64_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_fp64.py")],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
