@@ -37,7 +37,7 @@ WORKLOAD = "lognormal 128^3, 64 nu (3e11-3e15 Hz), 1e6 background packages/nu, H
 # DRAM bytes (read + write) per photon-cell step of trace_kernel from one ncu
 # capture (small case of the same workload, scaled by steps), valid only for
 # the kernel source it was taken on.
-TRACE_DRAM = {"source_sha1": "75097b93f7958fab4aef04583d48a9afa1f6423c", "bytes_per_step": 2.3019,
+TRACE_DRAM = {"source_sha1": "6c7e518edaaee0f5ffe00b379aab5122a70c5b16", "bytes_per_step": 2.2397,
               "warp_instructions_per_step": 8.576, "l2_bytes_per_step": 74.15,
               "profile": "profiles/trace_kernel_lognormal128_8nu_1e6pkg_full.md"}
 # issue-rate peak: 4 warp-instructions per cycle per SM (4 schedulers)

@@ -401,7 +401,10 @@ soc_status soc_update_temperature_ali(soc_ctx *ctx, int cloud_id, const double *
  * (kabs/kext) B_nu(T) (1 - e^-dtau) e^-tau_front; I_bg (erg/s/cm^2/Hz/sr)
  * enters from behind attenuated by the total optical depth.
  *   d_T     device float [n_cells];  d_map  device float [npy][npx].
- * FP32 cell-local traversal as the tracer, FP64 accumulation.  Asynchronous.
+ * FP32 cell-local traversal and segment optical depths as in the tracer;
+ * the source function per cell and the accumulation along the ray in FP64.
+ * Uses a per-context scratch of n_cells doubles (calls on one context must
+ * not overlap on the GPU).  Asynchronous.
  * ------------------------------------------------------------------------ */
 soc_status soc_map(soc_ctx *ctx, int cloud_id, const float *d_T, int freq, const double *dir, const double *up,
                    int npx, int npy, double pix_size, const double *center, double I_bg, float *d_map,

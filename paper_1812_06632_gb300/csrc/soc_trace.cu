@@ -4,10 +4,14 @@
 // absorption counters; Sect. 2.2 sources; Sect. 3.2 uniform dust emission).
 //
 // Scheduling: one package per lane.  A warp takes chunk*32 consecutive work
-// indices at a time from a global counter; whenever a lane's package ends
-// the lane takes the next index of the warp's chunk (per-lane refill, the
-// interleaving of creation and tracking suggested in Sect. 4.2).  One launch
-// covers every (cloud, frequency, source) item of a batch.
+// indices at a time from a global counter; lanes whose packages ended take
+// the next indices of the warp's chunk once refill_min of them are idle
+// (per-lane refill in batches, the interleaving of creation and tracking
+// suggested in Sect. 4.2).  Each pass of the warp's loop then runs, for the
+// lanes waiting on them, the scattering phase and (octrees) the descent
+// phase, and steps the other lanes: two steps on regular grids, one on
+// octrees.  One launch covers every (cloud, frequency, source) item of a
+// batch.
 //
 // Arithmetic: the FP32 sequence of soc_fp32.cuh; deposits are fixed point
 // (2^31 units per package, so a package's weight and its pending deposits
@@ -651,8 +655,10 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
 // chosen frequencies and directions from the solved temperatures).  One
 // thread per pixel: the ray enters the root box (FP64 slab test), then walks
 // the leaves with the tracer's FP32 cell-local traversal; along each segment
-// of optical depth dtau = rho kext_root h s the intensity gains
-// S (1 - e^-dtau) e^-tau_front with S = (kabs / kext) B_nu(T_cell), in FP64.
+// of optical depth dtau = rho kext_root h s (FP32) the intensity gains
+// S (1 - e^-dtau) e^-tau_front, with S = (kabs / kext) B_nu(T_cell) computed
+// once per cell in FP64 (map_source_kernel) and the intensity and the
+// transmission e^-tau_front accumulated in FP64.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double planck_d(double nu, double T)
 {
