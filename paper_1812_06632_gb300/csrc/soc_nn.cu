@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 #include "soc_internal.h"
@@ -837,15 +838,22 @@ using namespace soc::nn;
 
 namespace {
 
+// Networks by id.  The table is shared by all host threads; the mutex guards
+// its entries (a network itself is used by one thread at a time).
 struct NetRegistry {
+    std::mutex m;
     std::vector<Net *> nets;
 };
 NetRegistry g_nets;
 
 Net *net_of(int id)
 {
-    if (id < 0 || id >= (int)g_nets.nets.size() || !g_nets.nets[id]) return nullptr;
-    Net *n = g_nets.nets[id];
+    Net *n = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_nets.m);
+        if (id < 0 || id >= (int)g_nets.nets.size() || !g_nets.nets[id]) return nullptr;
+        n = g_nets.nets[id];
+    }
     if (cudaSetDevice(n->device) != cudaSuccess) return nullptr;
     return n;
 }
@@ -1020,13 +1028,14 @@ soc_status soc_unet_create(int device, int batch, int side, int *net_id)
         cudaMemset(n->w16[l].p, 0, n->w16[l].n * 2);
     }
     try {                                  // no exception crosses the C ABI
+        std::lock_guard<std::mutex> lock(g_nets.m);
         g_nets.nets.push_back(n);
+        *net_id = (int)g_nets.nets.size() - 1;
     } catch (...) {
         n->release();
         delete n;
         return SOC_ERR_NOMEM;
     }
-    *net_id = (int)g_nets.nets.size() - 1;
     return SOC_OK;
 }
 
@@ -1034,10 +1043,13 @@ soc_status soc_unet_destroy(int net_id)
 {
     Net *n = net_of(net_id);
     if (!n) return SOC_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> lock(g_nets.m);
+        g_nets.nets[net_id] = nullptr;
+    }
     cudaDeviceSynchronize();
     n->release();
     delete n;
-    g_nets.nets[net_id] = nullptr;
     return SOC_OK;
 }
 
