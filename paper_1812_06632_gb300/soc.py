@@ -152,7 +152,17 @@ def _np_ptr(a):
 
 
 def _t_ptr(t):
-    return None if t is None else C.c_void_p(t.data_ptr())
+    """Device pointer of a torch tensor.  Every tensor the library takes is
+    caller-owned device memory read or written as one dense array: a host
+    tensor or a strided view would have the kernels address the wrong memory,
+    so both are refused here, before any launch."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libsoc takes CUDA tensors (got a host tensor)")
+    if not t.is_contiguous():
+        raise ValueError("libsoc takes contiguous tensors (got a strided view)")
+    return C.c_void_p(t.data_ptr())
 
 
 def _stream(stream):

@@ -161,3 +161,12 @@ def test_product_path_never_touches_the_oracle():
                     if pat.search(open(os.path.join(dp, f), errors="replace").read()):
                         hits.append(os.path.join(dp, f))
     assert not hits, hits
+
+
+def test_binding_refuses_host_and_strided_tensors(libsoc):
+    """Device-pointer arguments must be dense CUDA tensors: anything else is
+    refused on the host, before a kernel could address the wrong memory."""
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        libsoc._t_ptr(torch.zeros(4))
+    assert libsoc._t_ptr(None) is None
