@@ -397,6 +397,28 @@ def test_noise_scales_as_inverse_sqrt_n():
     assert 3.3 < r < 4.8       # sqrt(16) = 4
 
 
+def test_noise_grows_as_2_to_the_level_for_background_heating():
+    """Sect. 3.1: each level of refinement cuts the packages crossing a cell
+    by four, so the relative noise of a cell's absorbed power grows as 2^L
+    for background heating.  Thin uniform box, root cells split once and
+    some of those split again: the scatter of absorbed power per volume
+    among the leaves of one level doubles from level to level."""
+    cl = I.regular(np.ones((4, 4, 4), np.float32))
+    cl = I.refine_cells(cl, np.arange(32, 64))                       # upper half: level 1
+    l1 = np.arange(cl.level_start[1], cl.level_start[2])
+    cl = I.refine_cells(cl, l1[::2])                                 # half of those: level 2
+    G = _grid(cl)
+    t, st, _ = oracle.trace(G, source=0, kabs=1e-3, ksca=0.0, seed=31, n_packages=400_000)
+    vol = 8.0 ** -np.repeat(np.arange(3), np.diff(cl.level_start))
+    leaf = cl.child < 0
+    a = t / vol
+    rel = []
+    for L in range(3):
+        m = leaf & (np.repeat(np.arange(3), np.diff(cl.level_start)) == L)
+        rel.append(a[m].std() / a[m].mean())
+    assert 1.5 < rel[1] / rel[0] < 2.7 and 1.5 < rel[2] / rel[1] < 2.7, rel
+
+
 # ----------------------------------------------------------------------------
 # FP64 physics
 # ----------------------------------------------------------------------------
