@@ -154,7 +154,7 @@ def cpu_baseline(per_freq: int = 300, cores: int | None = None):
     over `cores` spawned processes (package ranges)."""
     import oracle
     oracle.build()
-    cores = cores or os.cpu_count() or 1
+    cores = max(1, min(cores or os.cpu_count() or 1, per_freq))     # at least one package per process
     freqs = list(range(64))
     chunks = [(freqs, k * (per_freq // cores), per_freq // cores) for k in range(cores)]
     ctx = mp.get_context("spawn")
