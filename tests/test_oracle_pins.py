@@ -336,6 +336,25 @@ def test_octree_refinement_does_not_change_root_absorption():
     assert s1["steps"] > s0["steps"]
 
 
+def test_point_sources_chosen_in_proportion_to_luminosity():
+    """Several point sources (Sect. 3.1 tests one; the reading: a package
+    picks its source with probability L_k / sum L at its frequency, all
+    packages carrying equal energy).  An opaque cube keeps each package's
+    energy in its source's cell: the cells' shares are the luminosity
+    fractions."""
+    cl = I.regular(np.ones((5, 5, 5), np.float32))
+    L = np.array([[3.0], [1.0], [4.0]])
+    pos = np.array([[0.5, 0.5, 0.5], [2.5, 2.5, 2.5], [4.5, 3.5, 0.5]])
+    cdf = P.point_source_cdf(L)[0]
+    N = 60_000
+    t, st, _ = oracle.trace(_grid(cl), source=1, kabs=200.0, ksca=0.0, seed=4, n_packages=N,
+                            ps_pos=pos, ps_cdf=cdf)
+    cells = [int(p[0]) + 5 * (int(p[1]) + 5 * int(p[2])) for p in pos]
+    share = t[cells] / st["emitted"]
+    expect = L[:, 0] / L.sum()
+    assert np.all(np.abs(share - expect) < 4 * np.sqrt(expect * (1 - expect) / N) + 1e-3), (share, expect)
+
+
 # ----------------------------------------------------------------------------
 # scattering
 # ----------------------------------------------------------------------------
