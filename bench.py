@@ -156,7 +156,9 @@ def cpu_baseline(per_freq: int = 300, cores: int | None = None):
     oracle.build()
     cores = max(1, min(cores or os.cpu_count() or 1, per_freq))     # at least one package per process
     freqs = list(range(64))
-    chunks = [(freqs, k * (per_freq // cores), per_freq // cores) for k in range(cores)]
+    # package ranges of (nearly) equal length covering all per_freq packages
+    base, extra = divmod(per_freq, cores)
+    chunks = [(freqs, k * base + min(k, extra), base + (1 if k < extra else 0)) for k in range(cores)]
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(cores) as pool:

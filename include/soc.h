@@ -162,7 +162,9 @@ soc_status soc_sources_upload(soc_ctx *ctx, int cloud_id, const double *bg_I_nu,
  *   d_pkg_steps       device uint32 [sum of n_packages] or NULL: steps of each
  *                     package, in item order then package order.
  * Deterministic: results depend only on inputs and the seed, not on launch
- * shape.  Asynchronous on `stream`.
+ * shape.  Asynchronous on `stream`.  The item table is copied from host
+ * memory, so the call cannot be captured into a CUDA graph: on a capturing
+ * stream it returns SOC_ERR_STATE (capture soc_batch_launch instead).
  * ------------------------------------------------------------------------ */
 #define SOC_ITEM_WEIGHTED 1u   /* soc_batch_item.reserved flag: weighted dust sampling */
 
@@ -206,10 +208,13 @@ soc_status soc_simulate_frequency_batch_ex(soc_ctx *ctx, const soc_batch_item *i
  *   loads the library keeps until the process exits.  No cudaMalloc, cudaFree
  *   or allocating library routine is called.
  *   Limits: n_items <= SOC_NOALLOC_MAX_ITEMS and at most
- *   SOC_NOALLOC_MAX_CLOUDS grids uploaded on the context; larger requests
- *   fail with SOC_ERR_ARG.
+ *   SOC_NOALLOC_MAX_CLOUDS grids uploaded on the context (freed grids still
+ *   count); larger requests fail with SOC_ERR_ARG.
  *   The first call on a device looks up the array's device address (set-up
- *   for that device); make that first call before any stream capture.
+ *   for that device; threads that race on it store the same address).
+ *   Like soc_simulate_frequency_batch it copies its tables from host memory,
+ *   so it cannot be captured into a CUDA graph: on a capturing stream it
+ *   returns SOC_ERR_STATE (graphs use soc_batch_create / soc_batch_launch).
  *   All calls share the one array: calls that overlap on the GPU (other
  *   streams, other contexts on the same device) race and must be ordered by
  *   the caller.
@@ -369,6 +374,11 @@ soc_status soc_absorbed_power(soc_ctx *ctx, int cloud_id, const int64_t *d_tally
  * inversion: ln A is bracketed in ln E(T_k) (4096 log-spaced T_k) and ln T
  * interpolated linearly (error < 2e-7 relative on a 64-point grid).
  * A >= E(3000 K) gives 3000 K.
+ * The temperature update of an iteration is two calls: soc_absorbed_power
+ * (once per counter array, accumulating into A) and this one.  They stand in
+ * for one call taking the constant-source and the dust counters together, so
+ * that counters of different energy units (background, point-source and dust
+ * packages) are combined into A without a second copy of either.
  *   d_A               device double [n_cells].
  *   d_T               device float [n_cells], in/out: holds T_prev on entry.
  *   d_max_dT          device double [1] or NULL: receives max |T - T_prev|

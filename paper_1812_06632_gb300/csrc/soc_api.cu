@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <exception>
 #include <new>
 #include <string>
@@ -192,21 +193,25 @@ soc_status build_cloud_tables(soc_ctx *ctx, CloudHost &cl)
     return SOC_OK;
 }
 
+// The device form of one grid (no heap use: also called by the
+// allocation-free tracer entry).  A freed grid gets an all-zero entry.
+void fill_dev_cloud(const CloudHost &c, DevCloud &d)
+{
+    memset(&d, 0, sizeof d);
+    if (c.freed) return;
+    d.cell = c.cell.p; d.parent = c.parent.p; d.leaf = c.leaf.p; d.rho = c.rho.p;
+    d.volume = c.volume.p; d.kappa = c.kappa.p; d.ps_pos = c.ps_pos.p; d.ps_cdf = c.ps_cdf.p;
+    d.nx = c.nx; d.ny = c.ny; d.nz = c.nz; d.n_levels = c.n_levels; d.n_ps = c.n_ps;
+    d.n_cells = c.n_cells; d.n_root = c.n_root; d.n_leaf = c.n_leaf;
+    for (int L = 0; L <= c.n_levels; ++L) d.level_start[L] = c.level_start[L];
+    for (int L = c.n_levels + 1; L <= SOC_MAX_LEVELS; ++L) d.level_start[L] = c.n_cells;
+}
+
 soc_status sync_clouds(soc_ctx *ctx)
 {
     if (!ctx->clouds_dirty) return SOC_OK;
     std::vector<DevCloud> v(ctx->clouds.size());
-    for (size_t i = 0; i < ctx->clouds.size(); ++i) {
-        const CloudHost &c = *ctx->clouds[i];
-        DevCloud &d = v[i];
-        memset(&d, 0, sizeof d);
-        d.cell = c.cell.p; d.parent = c.parent.p; d.leaf = c.leaf.p; d.rho = c.rho.p;
-        d.volume = c.volume.p; d.kappa = c.kappa.p; d.ps_pos = c.ps_pos.p; d.ps_cdf = c.ps_cdf.p;
-        d.nx = c.nx; d.ny = c.ny; d.nz = c.nz; d.n_levels = c.n_levels; d.n_ps = c.n_ps;
-        d.n_cells = c.n_cells; d.n_root = c.n_root; d.n_leaf = c.n_leaf;
-        for (int L = 0; L <= c.n_levels; ++L) d.level_start[L] = c.level_start[L];
-        for (int L = c.n_levels + 1; L <= SOC_MAX_LEVELS; ++L) d.level_start[L] = c.n_cells;
-    }
+    for (size_t i = 0; i < ctx->clouds.size(); ++i) fill_dev_cloud(*ctx->clouds[i], v[i]);
     CK(ctx->d_clouds.alloc(v.size()), "alloc cloud table");
     CK(cudaMemcpy(ctx->d_clouds.p, v.data(), sizeof(DevCloud) * v.size(), cudaMemcpyHostToDevice),
        "copy cloud table");
@@ -732,41 +737,58 @@ soc_status soc_package_energy(soc_ctx *ctx, int cloud_id, int source, uint64_t n
     });
 }
 
+// Check batch item i against the context and write its device form into d
+// (no heap use: also called by the allocation-free tracer entry).
+static soc_status check_item(soc_ctx *ctx, const soc_batch_item &it, int i, DevItem &d)
+{
+    if (it.cloud < 0 || it.cloud >= (int)ctx->clouds.size() || ctx->clouds[it.cloud]->freed)
+        return fail(ctx, SOC_ERR_ARG, "item %d: bad or freed cloud", i);
+    const CloudHost &cl = *ctx->clouds[it.cloud];
+    if (it.freq < 0 || it.freq >= ctx->n_freq) return fail(ctx, SOC_ERR_ARG, "item %d: bad freq", i);
+    if (it.iteration < 0 || it.iteration > 65535) return fail(ctx, SOC_ERR_ARG, "item %d: bad iteration", i);
+    if (it.pid_offset + it.n_packages > 0xFFFFFFFFull || it.pid_offset > 0xFFFFFFFFull)
+        return fail(ctx, SOC_ERR_ARG, "item %d: package ids exceed 2^32", i);
+    if (it.tally_offset < 0) return fail(ctx, SOC_ERR_ARG, "item %d: negative tally offset", i);
+    if (it.source == SOC_SRC_BACKGROUND || it.source == SOC_SRC_POINT) {
+        if (it.w0 == 0 || it.w0 > SOC_W_UNIT) return fail(ctx, SOC_ERR_ARG, "item %d: w0 out of [1, 2^31]", i);
+        if (it.source == SOC_SRC_POINT && cl.n_ps == 0)
+            return fail(ctx, SOC_ERR_STATE, "item %d: cloud has no point sources", i);
+    } else if (it.source == SOC_SRC_DUST) {
+        if (!it.d_dust_w || it.n_per_cell == 0) return fail(ctx, SOC_ERR_ARG, "item %d: dust weights missing", i);
+        if (!(it.reserved & SOC_ITEM_WEIGHTED) && it.pid_offset + it.n_packages > (uint64_t)cl.n_leaf * it.n_per_cell)
+            return fail(ctx, SOC_ERR_ARG, "item %d: more dust packages than n_leaf*n_per_cell", i);
+    } else {
+        return fail(ctx, SOC_ERR_ARG, "item %d: unknown source %d", i, it.source);
+    }
+    memset(&d, 0, sizeof d);
+    d.cloud = it.cloud; d.freq = it.freq; d.source = it.source; d.iteration = it.iteration;
+    d.pid_offset = (uint32_t)it.pid_offset; d.n_per_cell = it.n_per_cell ? it.n_per_cell : 1;
+    d.flags = (it.source == SOC_SRC_DUST && (it.reserved & SOC_ITEM_WEIGHTED)) ? kItemWeighted : 0u;
+    d.w0 = it.w0; d.tally_offset = it.tally_offset; d.dust_w = it.d_dust_w;
+    return SOC_OK;
+}
+
+// Check every item and write the device forms and the exclusive prefix of
+// package counts into caller-given arrays dv[n_items], prefix[n_items + 1].
+static soc_status prepare_items_into(soc_ctx *ctx, const soc_batch_item *items, int n_items, DevItem *dv,
+                                     uint64_t *prefix)
+{
+    prefix[0] = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const soc_status st = check_item(ctx, items[i], i, dv[i]);
+        if (st != SOC_OK) return st;
+        prefix[i + 1] = prefix[i] + items[i].n_packages;
+    }
+    return SOC_OK;
+}
+
 // Check the batch items and convert them to the device form (host vectors).
 static soc_status prepare_items(soc_ctx *ctx, const soc_batch_item *items, int n_items, std::vector<DevItem> &dv,
                                 std::vector<uint64_t> &prefix)
 {
     dv.assign(n_items, DevItem{});
     prefix.assign(n_items + 1, 0);
-    for (int i = 0; i < n_items; ++i) {
-        const soc_batch_item &it = items[i];
-        if (it.cloud < 0 || it.cloud >= (int)ctx->clouds.size() || ctx->clouds[it.cloud]->freed)
-            return fail(ctx, SOC_ERR_ARG, "item %d: bad or freed cloud", i);
-        const CloudHost &cl = *ctx->clouds[it.cloud];
-        if (it.freq < 0 || it.freq >= ctx->n_freq) return fail(ctx, SOC_ERR_ARG, "item %d: bad freq", i);
-        if (it.iteration < 0 || it.iteration > 65535) return fail(ctx, SOC_ERR_ARG, "item %d: bad iteration", i);
-        if (it.pid_offset + it.n_packages > 0xFFFFFFFFull || it.pid_offset > 0xFFFFFFFFull)
-            return fail(ctx, SOC_ERR_ARG, "item %d: package ids exceed 2^32", i);
-        if (it.tally_offset < 0) return fail(ctx, SOC_ERR_ARG, "item %d: negative tally offset", i);
-        if (it.source == SOC_SRC_BACKGROUND || it.source == SOC_SRC_POINT) {
-            if (it.w0 == 0 || it.w0 > SOC_W_UNIT) return fail(ctx, SOC_ERR_ARG, "item %d: w0 out of [1, 2^31]", i);
-            if (it.source == SOC_SRC_POINT && cl.n_ps == 0)
-                return fail(ctx, SOC_ERR_STATE, "item %d: cloud has no point sources", i);
-        } else if (it.source == SOC_SRC_DUST) {
-            if (!it.d_dust_w || it.n_per_cell == 0) return fail(ctx, SOC_ERR_ARG, "item %d: dust weights missing", i);
-            if (!(it.reserved & SOC_ITEM_WEIGHTED) && it.pid_offset + it.n_packages > (uint64_t)cl.n_leaf * it.n_per_cell)
-                return fail(ctx, SOC_ERR_ARG, "item %d: more dust packages than n_leaf*n_per_cell", i);
-        } else {
-            return fail(ctx, SOC_ERR_ARG, "item %d: unknown source %d", i, it.source);
-        }
-        DevItem &d = dv[i];
-        d.cloud = it.cloud; d.freq = it.freq; d.source = it.source; d.iteration = it.iteration;
-        d.pid_offset = (uint32_t)it.pid_offset; d.n_per_cell = it.n_per_cell ? it.n_per_cell : 1;
-        d.flags = (it.source == SOC_SRC_DUST && (it.reserved & SOC_ITEM_WEIGHTED)) ? kItemWeighted : 0u;
-        d.w0 = it.w0; d.tally_offset = it.tally_offset; d.dust_w = it.d_dust_w;
-        prefix[i + 1] = prefix[i] + it.n_packages;
-    }
-    return SOC_OK;
+    return prepare_items_into(ctx, items, n_items, dv.data(), prefix.data());
 }
 
 // The step fields of the one cloud all items use; cell = nullptr when they
@@ -805,6 +827,24 @@ static void launch_geometry(soc_ctx *ctx, uint64_t total, bool regular, int &gri
     grid_out = (int)grid;
 }
 
+// SOC_ERR_STATE when `s` is being captured into a CUDA graph: the direct
+// tracer entries copy their tables from pageable host memory, which a
+// capture cannot hold (prepared batches, soc_batch_launch, can be captured).
+static soc_status refuse_capture(soc_ctx *ctx, cudaStream_t s, const char *who)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();            // not sticky: leave no error for the next launch check
+        return fail(ctx, SOC_ERR_STATE, "%s: stream capture state unavailable (%s); use soc_batch_launch in graphs",
+                    who, cudaGetErrorString(e));
+    }
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(ctx, SOC_ERR_STATE, "%s copies from host memory and cannot be captured; "
+                    "capture soc_batch_launch instead", who);
+    return SOC_OK;
+}
+
 soc_status soc_simulate_frequency_batch(soc_ctx *ctx, const soc_batch_item *items, int n_items, int64_t *d_tally,
                                         int64_t *d_stats, uint32_t *d_pkg_steps, void *stream)
 {
@@ -821,6 +861,7 @@ soc_status soc_simulate_frequency_batch_ex(soc_ctx *ctx, const soc_batch_item *i
         if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
         CK(cudaSetDevice(ctx->device), "cudaSetDevice");
         cudaStream_t s = (cudaStream_t)stream;
+        if (soc_status cst = refuse_capture(ctx, s, "soc_simulate_frequency_batch")) return cst;
         std::vector<DevItem> dv;
         std::vector<uint64_t> prefix;
         soc_status pst = prepare_items(ctx, items, n_items, dv, prefix);
@@ -1468,7 +1509,9 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
 // per-call scratch -- the work counter, the item table and its prefix sums,
 // and the grid table -- in one file-scope device array of fixed size, so it
 // never calls cudaMalloc, cudaFree or any allocating library routine.  The
-// caller still passes the counters and statistics buffers.
+// caller still passes the counters and statistics buffers.  The item checks
+// and the device forms of items and grids are the ones the ordinary entry
+// uses (check_item, fill_dev_cloud), written into static host arrays.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -1487,7 +1530,10 @@ struct NoAllocLayout {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocLayout)];
 
 constexpr int kMaxDevices = 64;
-void *g_noalloc_addr[kMaxDevices] = {};       // device address of g_noalloc_scratch, per device
+// Device address of g_noalloc_scratch, per device.  Host threads making their
+// first call on one device at the same time may both look it up; they store
+// the same address, and the atomics make that race well defined.
+std::atomic<void *> g_noalloc_addr[kMaxDevices];
 
 // Host staging for the tables (static storage: no heap use either).
 thread_local uint64_t t_prefix[kNoAllocMaxItems + 1];
@@ -1506,64 +1552,26 @@ extern "C" soc_status soc_simulate_frequency_batch_noalloc(soc_ctx *ctx, const s
             return fail(ctx, SOC_ERR_ARG, "n_items %d exceeds the allocation-free limit of %d items", n_items,
                         kNoAllocMaxItems);
         if ((int)ctx->clouds.size() > kNoAllocMaxClouds)
-            return fail(ctx, SOC_ERR_ARG, "%d grids exceed the allocation-free limit of %d grids",
-                        (int)ctx->clouds.size(), kNoAllocMaxClouds);
+            return fail(ctx, SOC_ERR_ARG, "%d grids uploaded (freed ones included) exceed the allocation-free "
+                        "limit of %d grids", (int)ctx->clouds.size(), kNoAllocMaxClouds);
         if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
         if (ctx->device < 0 || ctx->device >= kMaxDevices) return fail(ctx, SOC_ERR_ARG, "device index too large");
         CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        cudaStream_t s = (cudaStream_t)stream;
+        if (soc_status cst = refuse_capture(ctx, s, "soc_simulate_frequency_batch_noalloc")) return cst;
         // set-up, once per device, with that device current: the host-side name
         // g_noalloc_scratch is only a stand-in, the kernel needs the device address
-        if (!g_noalloc_addr[ctx->device]) {
-            void *addr = nullptr;
+        void *addr = g_noalloc_addr[ctx->device].load(std::memory_order_acquire);
+        if (!addr) {
             CK(cudaGetSymbolAddress(&addr, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)");
-            g_noalloc_addr[ctx->device] = addr;
+            g_noalloc_addr[ctx->device].store(addr, std::memory_order_release);
         }
-        NoAllocLayout *S = static_cast<NoAllocLayout *>(g_noalloc_addr[ctx->device]);
-        cudaStream_t s = (cudaStream_t)stream;
-        t_prefix[0] = 0;
-        for (int i = 0; i < n_items; ++i) {
-            const soc_batch_item &it = items[i];
-            if (it.cloud < 0 || it.cloud >= (int)ctx->clouds.size() || ctx->clouds[it.cloud]->freed)
-                return fail(ctx, SOC_ERR_ARG, "item %d: bad or freed cloud", i);
-            const CloudHost &cl = *ctx->clouds[it.cloud];
-            if (it.freq < 0 || it.freq >= ctx->n_freq) return fail(ctx, SOC_ERR_ARG, "item %d: bad freq", i);
-            if (it.iteration < 0 || it.iteration > 65535) return fail(ctx, SOC_ERR_ARG, "item %d: bad iteration", i);
-            if (it.pid_offset + it.n_packages > 0xFFFFFFFFull || it.pid_offset > 0xFFFFFFFFull)
-                return fail(ctx, SOC_ERR_ARG, "item %d: package ids exceed 2^32", i);
-            if (it.tally_offset < 0) return fail(ctx, SOC_ERR_ARG, "item %d: negative tally offset", i);
-            if (it.source == SOC_SRC_BACKGROUND || it.source == SOC_SRC_POINT) {
-                if (it.w0 == 0 || it.w0 > SOC_W_UNIT) return fail(ctx, SOC_ERR_ARG, "item %d: w0 out of [1, 2^31]", i);
-                if (it.source == SOC_SRC_POINT && cl.n_ps == 0)
-                    return fail(ctx, SOC_ERR_STATE, "item %d: cloud has no point sources", i);
-            } else if (it.source == SOC_SRC_DUST) {
-                if (!it.d_dust_w || it.n_per_cell == 0) return fail(ctx, SOC_ERR_ARG, "item %d: dust weights missing", i);
-                if (!(it.reserved & SOC_ITEM_WEIGHTED) && it.pid_offset + it.n_packages > (uint64_t)cl.n_leaf * it.n_per_cell)
-                    return fail(ctx, SOC_ERR_ARG, "item %d: more dust packages than n_leaf*n_per_cell", i);
-            } else {
-                return fail(ctx, SOC_ERR_ARG, "item %d: unknown source %d", i, it.source);
-            }
-            DevItem &d = t_items[i];
-            d.cloud = it.cloud; d.freq = it.freq; d.source = it.source; d.iteration = it.iteration;
-            d.pid_offset = (uint32_t)it.pid_offset; d.n_per_cell = it.n_per_cell ? it.n_per_cell : 1;
-            d.flags = (it.source == SOC_SRC_DUST && (it.reserved & SOC_ITEM_WEIGHTED)) ? kItemWeighted : 0u;
-            d.w0 = it.w0; d.tally_offset = it.tally_offset; d.dust_w = it.d_dust_w;
-            t_prefix[i + 1] = t_prefix[i] + it.n_packages;
-        }
+        NoAllocLayout *S = static_cast<NoAllocLayout *>(addr);
+        if (soc_status pst = prepare_items_into(ctx, items, n_items, t_items, t_prefix)) return pst;
         const uint64_t total = t_prefix[n_items];
         if (total == 0) return SOC_OK;
         const int nc = (int)ctx->clouds.size();
-        for (int i = 0; i < nc; ++i) {
-            const CloudHost &c = *ctx->clouds[i];
-            DevCloud &d = t_clouds[i];
-            memset(&d, 0, sizeof d);
-            if (c.freed) continue;
-            d.cell = c.cell.p; d.parent = c.parent.p; d.leaf = c.leaf.p; d.rho = c.rho.p;
-            d.volume = c.volume.p; d.kappa = c.kappa.p; d.ps_pos = c.ps_pos.p; d.ps_cdf = c.ps_cdf.p;
-            d.nx = c.nx; d.ny = c.ny; d.nz = c.nz; d.n_levels = c.n_levels; d.n_ps = c.n_ps;
-            d.n_cells = c.n_cells; d.n_root = c.n_root; d.n_leaf = c.n_leaf;
-            for (int L = 0; L <= c.n_levels; ++L) d.level_start[L] = c.level_start[L];
-            for (int L = c.n_levels + 1; L <= SOC_MAX_LEVELS; ++L) d.level_start[L] = c.n_cells;
-        }
+        for (int i = 0; i < nc; ++i) fill_dev_cloud(*ctx->clouds[i], t_clouds[i]);
         CK(cudaMemcpyAsync(S->clouds, t_clouds, sizeof(DevCloud) * nc, cudaMemcpyHostToDevice, s), "copy grid table");
         CK(cudaMemcpyAsync(S->items, t_items, sizeof(DevItem) * n_items, cudaMemcpyHostToDevice, s), "copy items");
         CK(cudaMemcpyAsync(S->prefix, t_prefix, sizeof(uint64_t) * (n_items + 1), cudaMemcpyHostToDevice, s),
@@ -1588,14 +1596,9 @@ extern "C" soc_status soc_simulate_frequency_batch_noalloc(soc_ctx *ctx, const s
         P.scatter_min = ctx->scatter_min;
         P.hot = one_cloud(ctx, items, n_items);
         P.regular = all_regular(ctx, items, n_items);
-        const int variant = ctx->bps >= 4 ? 4 : 3;
-        const int limit = trace_block_limit(ctx->tpb, variant, P.regular != 0);
-        const int per_sm = ctx->bps > 0 ? std::min(ctx->bps, limit) : limit;
-        const uint64_t warps_needed = (total + 31) / 32;
-        int64_t grid = (int64_t)ctx->sms * per_sm;
-        const int64_t grid_need = (int64_t)((warps_needed * 32 + ctx->tpb - 1) / ctx->tpb);
-        if (grid_need < grid) grid = grid_need < 1 ? 1 : grid_need;
-        CK(launch_trace(P, (int)grid, ctx->tpb, variant, s), "trace launch");
+        int grid = 1, variant = 3;
+        launch_geometry(ctx, total, P.regular != 0, grid, variant);     // occupancy cached at soc_create
+        CK(launch_trace(P, grid, ctx->tpb, variant, s), "trace launch");
         return SOC_OK;
     });
 }
