@@ -36,6 +36,8 @@ typedef int soc_status;
 #define SOC_ERR_STEP_LIMIT -4   /* packages were ended by the step cap               */
 #define SOC_ERR_STATE      -5   /* call order: e.g. simulation before soc_dust_upload */
 #define SOC_ERR_NOMEM      -6   /* device or host allocation failed                  */
+#define SOC_ERR_TIMEOUT    -7   /* the abort flag was set (soc_abort, or the watchdog
+                                   of soc_set_timeout): the call stopped early       */
 
 #define SOC_SRC_BACKGROUND 0
 #define SOC_SRC_POINT      1
@@ -533,13 +535,51 @@ soc_status soc_unet_adam(int net_id, float lr, void *stream);
  *   soc_nn_conv3d_dgrad  gx (FP32) = transposed convolution of gy with w
  *                        (w_scratch: device BF16 [Cout*27*Cin]);
  *   soc_nn_conv3d_wgrad  gw[Cout][27][Cin] += sum_v gy[v] x[v + tap] and
- *                        gb[Cout] += sum_v gy[v] (FP32, accumulated). */
+ *                        gb[Cout] += sum_v gy[v] (FP32, accumulated).  The
+ *                        voxels are split over blocks whose partial sums go
+ *                        to a library-owned workspace of the device (grown
+ *                        on demand with cudaMalloc) and are added in a fixed
+ *                        order: bit-reproducible.  Calls on one device share
+ *                        the workspace and must not overlap on the GPU.
+ *   soc_nn_adam          one Adam step (Kingma & Ba 2015) at step t >= 1 on
+ *                        n FP32 parameters d_w with moments d_m, d_v (device,
+ *                        in/out) and gradients d_g: beta1 0.9, beta2 0.999,
+ *                        eps 1e-8 (FP32 constants), bias corrections
+ *                        1 - beta^t; d_w_bf16 (device BF16 [n] or NULL)
+ *                        receives the rounded weights.  The U-Net's
+ *                        soc_unet_adam runs the same kernel. */
 soc_status soc_nn_conv3d(const void *x, int N, int D, int H, int W, int Cin, const void *w, const float *bias,
                          int Cout, int relu, void *y_bf16, float *y_f32, void *stream);
 soc_status soc_nn_conv3d_dgrad(const void *gy, int N, int D, int H, int W, int Cout, const void *w, int Cin,
                                void *w_scratch, float *gx, void *stream);
 soc_status soc_nn_conv3d_wgrad(const void *gy, const void *x, int N, int D, int H, int W, int Cin, int Cout,
                                float *gw, float *gb, void *stream);
+soc_status soc_nn_adam(float *d_w, float *d_m, float *d_v, const float *d_g, int64_t n, float lr, int32_t t,
+                       void *d_w_bf16, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Seeding transform of the learned temperature seed (not a step of the
+ * paper's method), per cell of an uploaded regular grid, in FP64:
+ *   soc_seed_features   network input d_x (device float [n_cells][2], the
+ *                       channels-last (side, side, side, 2) layout of one
+ *                       sample): x[c][0] = (ln clamp(T1[c], 2.7, 3000) -
+ *                       norm[0]) / norm[1], x[c][1] = (ln max(rho_c, 1e-30) -
+ *                       norm[2]) / norm[3], rho from the uploaded grid.
+ *                       norm: host double [4] {ln T1 mean, ln T1 std,
+ *                       ln rho mean, ln rho std} of the training set (stds
+ *                       > 0).  The grid must be a regular cube whose side is
+ *                       a multiple of 8 (SOC_ERR_ARG otherwise).
+ *   soc_seed_transform  d_T_seed[c] = clamp(T1[c] exp(pred[c] y_std + y_mean),
+ *                       2.7, 3000) for every cell (the network predicts the
+ *                       normalised ln T - ln T1).  d_T1, d_pred, d_T_seed:
+ *                       device float [n_cells].
+ * Both asynchronous on `stream`; d_T_seed may be passed as the seed of
+ * soc_iterate or soc_iterate_batch.
+ * ------------------------------------------------------------------------ */
+soc_status soc_seed_features(soc_ctx *ctx, int cloud_id, const float *d_T1, const double *norm, float *d_x,
+                             void *stream);
+soc_status soc_seed_transform(soc_ctx *ctx, int cloud_id, const float *d_T1, const float *d_pred, double y_mean,
+                              double y_std, float *d_T_seed, void *stream);
 
 /* ------------------------------------------------------------------------
  * Launch configuration of the tracer (autotuner hook).  threads_per_block in
@@ -565,6 +605,37 @@ soc_status soc_set_scatter_batch(soc_ctx *ctx, int min_lanes);
 /* Step cap per package (default 10^7); packages beyond it are ended with
  * their weight deposited and counted in stats[1]. */
 soc_status soc_set_max_steps(soc_ctx *ctx, uint32_t max_steps);
+
+/* ------------------------------------------------------------------------
+ * Abort flag and watchdog (failure handling; the paper has no counterpart).
+ * Every context owns a flag in host-mapped pinned memory.  Each tracer
+ * launch (direct, allocation-free, prepared batch or graph replay) reads it
+ * whenever a warp takes a new chunk of work: once it is set, warps take no
+ * more work and the launch ends after the packages already in flight (each
+ * bounded by the step cap).  The counters and statistics then hold exactly
+ * the packages that were traced: per item, sum(tally) + escaped == emitted
+ * still holds, with emitted below the full count.
+ *   soc_abort         sets the flag; callable from any host thread at any
+ *                     time (a plain store, no CUDA call).  The flag stays
+ *                     set, and every later launch traces nothing, until
+ *                     soc_abort_clear.
+ *   soc_abort_clear   clears the flag and the "cut" record.  Call it when no
+ *                     launch of the context is in flight.
+ *   soc_abort_status  *requested = the flag, *cut = 1 if a launch since the
+ *                     last clear left work untraced (read it after the
+ *                     launches have finished, e.g. after a stream sync).
+ *                     Either pointer may be NULL.
+ *   soc_set_timeout   seconds > 0: each soc_iterate call starts a host
+ *                     watchdog thread that sets the flag when the call has
+ *                     run that long; 0 (default) = none.
+ * soc_iterate checks the flag before each tracer launch and after each
+ * iteration's synchronisation; when it is set it returns SOC_ERR_TIMEOUT
+ * with *res describing the iterations completed.  The flag stays set.
+ * ------------------------------------------------------------------------ */
+soc_status soc_abort(soc_ctx *ctx);
+soc_status soc_abort_clear(soc_ctx *ctx);
+soc_status soc_abort_status(soc_ctx *ctx, int *requested, int *cut);
+soc_status soc_set_timeout(soc_ctx *ctx, double seconds);
 
 /* ------------------------------------------------------------------------
  * soc_probe_read -- measurement helper for the tracer's roofline (not part

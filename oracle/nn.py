@@ -13,7 +13,14 @@ Everything here is the plain definition in float64, channels-last
   finite differences in the tests);
 * 2x2x2 max pooling, nearest 2x upsampling, ReLU, mean squared error;
 * the U-Net of four levels with channels 16-32-64-128 and skip concatenation
-  [upsampled, skip].
+  [upsampled, skip], optionally with the BF16 storage of the network's stated
+  precision (every stored activation and every layer's output gradient
+  rounded to bfloat16, arithmetic in float64);
+* one Adam step (Kingma & Ba 2015, Algorithm 1) on given parameters,
+  gradients and moments;
+* the seeding transform: the network input features from T after the first
+  iteration and the density, and T_seed = T1 exp(prediction) with the
+  prediction de-normalised.
 """
 from __future__ import annotations
 
@@ -67,6 +74,17 @@ def conv3d_wgrad(gy, x):
     return gw, gy.sum(axis=(0, 1, 2, 3))
 
 
+def bf16(x):
+    """Round to the nearest bfloat16 (8 significant bits), ties to even, as
+    a float64 array: the float32 value's bit pattern is rounded at bit 16
+    (add 0x7fff plus the lowest kept bit, then drop the low 16 bits).
+    Inputs are finite."""
+    f = np.ascontiguousarray(np.asarray(x, np.float64).astype(np.float32))
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64).reshape(np.shape(x))
+
+
 def relu(x):
     return np.maximum(x, 0.0)
 
@@ -113,45 +131,53 @@ LAYERS = [("e0a", 16, 16), ("e0b", 16, 16), ("e1a", 16, 32), ("e1b", 32, 32),
           ("d0a", 48, 16), ("d0b", 16, 16), ("head", 16, 16)]
 
 
-def unet_forward(x, params):
+def unet_forward(x, params, store_bf16=False):
     """x (N,S,S,S,16) (2 real input channels, rest zero); params: name ->
     (w (Cout,27,Cin), b (Cout)).  Returns (prediction = head channel 0,
-    cache of activations for the backward pass)."""
+    cache of activations for the backward pass).  store_bf16: every hidden
+    layer's output is stored as bfloat16 (the network's stated precision);
+    the head stays unrounded."""
     P = params
+    st = bf16 if store_bf16 else (lambda v: v)
     a = {}
     a["x"] = x
-    a["e0a"] = relu(conv3d(x, *P["e0a"]))
-    a["e0b"] = relu(conv3d(a["e0a"], *P["e0b"]))
+    a["e0a"] = st(relu(conv3d(x, *P["e0a"])))
+    a["e0b"] = st(relu(conv3d(a["e0a"], *P["e0b"])))
     a["p0"], a["arg0"] = maxpool2(a["e0b"])
-    a["e1a"] = relu(conv3d(a["p0"], *P["e1a"]))
-    a["e1b"] = relu(conv3d(a["e1a"], *P["e1b"]))
+    a["e1a"] = st(relu(conv3d(a["p0"], *P["e1a"])))
+    a["e1b"] = st(relu(conv3d(a["e1a"], *P["e1b"])))
     a["p1"], a["arg1"] = maxpool2(a["e1b"])
-    a["e2a"] = relu(conv3d(a["p1"], *P["e2a"]))
-    a["e2b"] = relu(conv3d(a["e2a"], *P["e2b"]))
+    a["e2a"] = st(relu(conv3d(a["p1"], *P["e2a"])))
+    a["e2b"] = st(relu(conv3d(a["e2a"], *P["e2b"])))
     a["p2"], a["arg2"] = maxpool2(a["e2b"])
-    a["b_a"] = relu(conv3d(a["p2"], *P["b_a"]))
-    a["b_b"] = relu(conv3d(a["b_a"], *P["b_b"]))
+    a["b_a"] = st(relu(conv3d(a["p2"], *P["b_a"])))
+    a["b_b"] = st(relu(conv3d(a["b_a"], *P["b_b"])))
     a["cat2"] = np.concatenate([upsample2(a["b_b"]), a["e2b"]], axis=4)
-    a["d2a"] = relu(conv3d(a["cat2"], *P["d2a"]))
-    a["d2b"] = relu(conv3d(a["d2a"], *P["d2b"]))
+    a["d2a"] = st(relu(conv3d(a["cat2"], *P["d2a"])))
+    a["d2b"] = st(relu(conv3d(a["d2a"], *P["d2b"])))
     a["cat1"] = np.concatenate([upsample2(a["d2b"]), a["e1b"]], axis=4)
-    a["d1a"] = relu(conv3d(a["cat1"], *P["d1a"]))
-    a["d1b"] = relu(conv3d(a["d1a"], *P["d1b"]))
+    a["d1a"] = st(relu(conv3d(a["cat1"], *P["d1a"])))
+    a["d1b"] = st(relu(conv3d(a["d1a"], *P["d1b"])))
     a["cat0"] = np.concatenate([upsample2(a["d1b"]), a["e0b"]], axis=4)
-    a["d0a"] = relu(conv3d(a["cat0"], *P["d0a"]))
-    a["d0b"] = relu(conv3d(a["d0a"], *P["d0b"]))
+    a["d0a"] = st(relu(conv3d(a["cat0"], *P["d0a"])))
+    a["d0b"] = st(relu(conv3d(a["d0a"], *P["d0b"])))
     a["head"] = conv3d(a["d0b"], *P["head"])
     return a["head"][..., 0], a
 
 
-def unet_backward(g_pred, a, params):
-    """Gradients of the loss (given dL/dprediction) for every parameter."""
+def unet_backward(g_pred, a, params, store_bf16=False):
+    """Gradients of the loss (given dL/dprediction) for every parameter.
+    store_bf16: each layer's output gradient (after its ReLU mask) is
+    rounded to bfloat16 before it enters the weight, bias and input
+    gradients of that layer (the network's stated precision)."""
     P = params
     G = {}
     gh = np.zeros(a["head"].shape)
     gh[..., 0] = g_pred
+    st = bf16 if store_bf16 else (lambda v: v)
 
     def back(name, gy, x):
+        gy = st(gy)
         G[name] = conv3d_wgrad(gy, x)
         return conv3d_dgrad(gy, P[name][0])
 
@@ -181,8 +207,47 @@ def unet_backward(g_pred, a, params):
     g_p0 = back("e1a", g * (a["e1a"] > 0), a["p0"])
     g_e0b = g_e0b + maxpool2_bwd(g_p0, a["arg0"], a["e0b"].shape)
     g = back("e0b", g_e0b * (a["e0b"] > 0), a["e0a"])
-    G["e0a"] = conv3d_wgrad(g * (a["e0a"] > 0), a["x"])
+    G["e0a"] = conv3d_wgrad(st(g * (a["e0a"] > 0)), a["x"])
     return G
+
+
+# ---------------------------------------------------------------------------
+# Adam (Kingma & Ba 2015, Algorithm 1)
+# ---------------------------------------------------------------------------
+def adam_step(theta, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update at step t >= 1 (float64): biased moment estimates
+    m <- beta1 m + (1 - beta1) g, v <- beta2 v + (1 - beta2) g^2, their
+    bias corrections m / (1 - beta1^t), v / (1 - beta2^t), and
+    theta <- theta - lr m_hat / (sqrt(v_hat) + eps).  Returns (theta, m, v)."""
+    theta, g, m, v = (np.asarray(a, np.float64) for a in (theta, g, m, v))
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    return theta - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
+
+
+# ---------------------------------------------------------------------------
+# Seeding transform (float64)
+# ---------------------------------------------------------------------------
+T_MIN, T_MAX = 2.7, 3000.0
+
+
+def seed_features(T1, rho, norm):
+    """Network input per cell: ((ln T1 - lt_mean) / lt_std, (ln rho -
+    lr_mean) / lr_std), with T1 clamped to [T_MIN, T_MAX] and rho to at least
+    1e-30.  norm: dict with lt_mean, lt_std, lr_mean, lr_std.  Returns
+    (n, 2)."""
+    lt = (np.log(np.clip(np.asarray(T1, np.float64), T_MIN, T_MAX)) - norm["lt_mean"]) / norm["lt_std"]
+    lr = (np.log(np.maximum(np.asarray(rho, np.float64), 1e-30)) - norm["lr_mean"]) / norm["lr_std"]
+    return np.stack([lt, lr], axis=-1)
+
+
+def seed_transform(T1, pred, y_mean, y_std):
+    """T_seed = T1 exp(pred y_std + y_mean), clamped to [T_MIN, T_MAX]: the
+    network predicts the normalised ln T - ln T1."""
+    T1 = np.asarray(T1, np.float64)
+    return np.clip(T1 * np.exp(np.asarray(pred, np.float64) * y_std + y_mean), T_MIN, T_MAX)
 
 
 def init_params(seed=0, scale=1.0):

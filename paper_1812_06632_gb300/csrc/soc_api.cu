@@ -7,6 +7,9 @@
 #include <cstring>
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <mutex>
 #include <exception>
 #include <new>
 #include <string>
@@ -112,6 +115,11 @@ struct soc_ctx {
     // prepared batches and graphs
     std::vector<struct BatchHost *> batches;
     std::vector<cudaGraphExec_t> graphs;
+    // abort flag (host-mapped pinned memory, 2 ints): [0] nonzero = tracer
+    // launches take no more work; [1] set by a launch that left work untraced
+    volatile int *h_abort = nullptr;
+    int *d_abort = nullptr;
+    double timeout_s = 0.0;       // soc_iterate watchdog (0 = none)
     // launch
     int tpb = 256, bps = 4, chunk = 16, refill_min = 8, scatter_min = 8;   // autotuned on the 128^3 x 64 nu workload
     uint32_t max_steps = 10000000u;
@@ -247,9 +255,21 @@ soc_status soc_create(soc_ctx **out, int device, uint64_t seed)
         for (int g = 0; g < 2; ++g)
             for (int v = 3; v <= 4; ++v)
                 for (int t = 32; t <= 256; t += 32) ctx->occ[g][v - 3][t / 32 - 1] = trace_block_limit(t, v, g == 1);
-        if (ctx->d_counter.alloc(1) != cudaSuccess || ctx->d_maxdT.alloc(1) != cudaSuccess) {
+        void *hab = nullptr;
+        if (ctx->d_counter.alloc(1) != cudaSuccess || ctx->d_maxdT.alloc(1) != cudaSuccess ||
+            cudaHostAlloc(&hab, 2 * sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
+            ctx->d_counter.release(); ctx->d_maxdT.release();
             delete ctx;
             return SOC_ERR_NOMEM;
+        }
+        ctx->h_abort = static_cast<volatile int *>(hab);
+        ctx->h_abort[0] = 0;
+        ctx->h_abort[1] = 0;
+        if (cudaHostGetDevicePointer((void **)&ctx->d_abort, hab, 0) != cudaSuccess) {
+            cudaFreeHost(hab);
+            ctx->d_counter.release(); ctx->d_maxdT.release();
+            delete ctx;
+            return SOC_ERR_CUDA;
         }
         *out = ctx;
         return SOC_OK;
@@ -297,6 +317,7 @@ void soc_destroy(soc_ctx *ctx)
     ctx->d_level_start.release();
     ctx->d_map_S.release();
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    if (ctx->h_abort) cudaFreeHost((void *)ctx->h_abort);
     for (BatchHost *b : ctx->batches)
         if (b) { b->items.release(); b->prefix.release(); b->counter.release(); delete b; }
     for (cudaGraphExec_t g : ctx->graphs)
@@ -357,6 +378,39 @@ soc_status soc_set_max_steps(soc_ctx *ctx, uint32_t max_steps)
     return guarded(ctx, [&]() -> soc_status {
         if (!ctx || max_steps == 0) return SOC_ERR_ARG;
         ctx->max_steps = max_steps;
+        return SOC_OK;
+    });
+}
+
+soc_status soc_abort(soc_ctx *ctx)
+{
+    if (!ctx || !ctx->h_abort) return SOC_ERR_ARG;
+    __atomic_store_n(const_cast<int *>(&ctx->h_abort[0]), 1, __ATOMIC_SEQ_CST);
+    return SOC_OK;
+}
+
+soc_status soc_abort_clear(soc_ctx *ctx)
+{
+    if (!ctx || !ctx->h_abort) return SOC_ERR_ARG;
+    __atomic_store_n(const_cast<int *>(&ctx->h_abort[1]), 0, __ATOMIC_SEQ_CST);
+    __atomic_store_n(const_cast<int *>(&ctx->h_abort[0]), 0, __ATOMIC_SEQ_CST);
+    return SOC_OK;
+}
+
+soc_status soc_abort_status(soc_ctx *ctx, int *requested, int *cut)
+{
+    if (!ctx || !ctx->h_abort) return SOC_ERR_ARG;
+    if (requested) *requested = __atomic_load_n(const_cast<int *>(&ctx->h_abort[0]), __ATOMIC_SEQ_CST) != 0;
+    if (cut) *cut = __atomic_load_n(const_cast<int *>(&ctx->h_abort[1]), __ATOMIC_SEQ_CST) != 0;
+    return SOC_OK;
+}
+
+soc_status soc_set_timeout(soc_ctx *ctx, double seconds)
+{
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx) return SOC_ERR_ARG;
+        if (!(seconds >= 0.0) || seconds > 1e9) return fail(ctx, SOC_ERR_ARG, "timeout must be in [0, 1e9] s");
+        ctx->timeout_s = seconds;
         return SOC_OK;
     });
 }
@@ -885,6 +939,8 @@ soc_status soc_simulate_frequency_batch_ex(soc_ctx *ctx, const soc_batch_item *i
         P.stats = reinterpret_cast<unsigned long long *>(d_stats);
         P.pkg_steps = d_pkg_steps;
         P.counter = ctx->d_counter.p;
+        P.abort_flag = ctx->d_abort;
+        P.cut = ctx->d_abort + 1;
         P.total = total;
         P.seed = ctx->seed;
         P.n_items = n_items;
@@ -957,6 +1013,8 @@ soc_status soc_batch_launch(soc_ctx *ctx, int batch_id, int64_t *d_tally, int64_
         P.stats = reinterpret_cast<unsigned long long *>(d_stats);
         P.pkg_steps = d_pkg_steps;
         P.counter = b.counter.p;
+        P.abort_flag = ctx->d_abort;
+        P.cut = ctx->d_abort + 1;
         P.total = b.total;
         P.seed = ctx->seed;
         P.n_items = b.n_items;
@@ -1221,6 +1279,38 @@ soc_status soc_update_temperature_ali(soc_ctx *ctx, int cloud_id, const double *
     });
 }
 
+soc_status soc_seed_features(soc_ctx *ctx, int cloud_id, const float *d_T1, const double *norm, float *d_x,
+                             void *stream)
+{
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        if (!d_T1 || !norm || !d_x) return fail(ctx, SOC_ERR_ARG, "null argument");
+        if (!(norm[1] > 0.0) || !(norm[3] > 0.0)) return fail(ctx, SOC_ERR_ARG, "normalisation widths must be > 0");
+        const CloudHost &cl = *ctx->clouds[cloud_id];
+        if (cl.n_levels != 1 || cl.nx != cl.ny || cl.nx != cl.nz || cl.nx % 8)
+            return fail(ctx, SOC_ERR_ARG, "the network takes regular cubic grids with a side that is a multiple of 8");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        CK(launch_seed_features(d_T1, cl.rho.p, cl.n_cells, norm, d_x, (cudaStream_t)stream), "seed features");
+        return SOC_OK;
+    });
+}
+
+soc_status soc_seed_transform(soc_ctx *ctx, int cloud_id, const float *d_T1, const float *d_pred, double y_mean,
+                              double y_std, float *d_T_seed, void *stream)
+{
+    return guarded(ctx, [&]() -> soc_status {
+        soc_status st = check_cloud(ctx, cloud_id);
+        if (st) return st;
+        if (!d_T1 || !d_pred || !d_T_seed) return fail(ctx, SOC_ERR_ARG, "null argument");
+        if (!std::isfinite(y_mean) || !std::isfinite(y_std)) return fail(ctx, SOC_ERR_ARG, "y_mean, y_std must be finite");
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        CK(launch_seed_transform(d_T1, d_pred, ctx->clouds[cloud_id]->n_cells, y_mean, y_std, d_T_seed,
+                                 (cudaStream_t)stream), "seed transform");
+        return SOC_OK;
+    });
+}
+
 soc_status soc_map(soc_ctx *ctx, int cloud_id, const float *d_T, int freq, const double *dir, const double *up, int npx,
                    int npy, double pix_size, const double *center, double I_bg, float *d_map, void *stream)
 {
@@ -1265,6 +1355,39 @@ soc_status soc_map(soc_ctx *ctx, int cloud_id, const float *d_T, int freq, const
         return SOC_OK;
     });
 }
+
+}  // extern "C"
+
+namespace {
+// Host watchdog of one soc_iterate call: sets the context's abort flag once
+// `seconds` have passed, unless the call ends first (the destructor stops it).
+struct Watchdog {
+    std::mutex m;
+    std::condition_variable cv;
+    bool done = false;
+    std::thread t;
+    void start(volatile int *flag, double seconds)
+    {
+        t = std::thread([this, flag, seconds] {
+            std::unique_lock<std::mutex> lk(m);
+            if (!cv.wait_for(lk, std::chrono::duration<double>(seconds), [this] { return done; }))
+                __atomic_store_n(const_cast<int *>(flag), 1, __ATOMIC_SEQ_CST);
+        });
+    }
+    ~Watchdog()
+    {
+        if (!t.joinable()) return;
+        {
+            std::lock_guard<std::mutex> lk(m);
+            done = true;
+        }
+        cv.notify_all();
+        t.join();
+    }
+};
+}  // namespace
+
+extern "C" {
 
 soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm, const float *d_T_seed,
                        float *d_T_out, soc_iterate_result *res, double *dT_history, void *stream)
@@ -1326,12 +1449,19 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
             CK(cl.A_self.alloc(n), "alloc A_self");
         }
         int64_t steps = 0, capped = 0;
+        int it_done = 0, conv = 0;
+        double dT = 0.0;
+        Watchdog watchdog;
+        if (ctx->timeout_s > 0.0) watchdog.start(ctx->h_abort, ctx->timeout_s);
+        auto aborted = [&]() { return __atomic_load_n(const_cast<int *>(&ctx->h_abort[0]), __ATOMIC_SEQ_CST) != 0; };
+        const soc_status run_st = [&]() -> soc_status {
         std::vector<int64_t> hstats(4 * nf);
         std::vector<soc_batch_item> items(nf);
         std::vector<double> e(nf);
         std::vector<uint64_t> wcount(nf, 0);
         auto run_items = [&](int source, uint64_t npk, int iteration, const uint64_t *dw, uint32_t npc,
                              int64_t *self, bool wsampled) -> soc_status {
+            if (aborted()) return fail(ctx, SOC_ERR_TIMEOUT, "aborted (soc_abort or the soc_set_timeout deadline)");
             for (int f = 0; f < nf; ++f) {
                 soc_batch_item &it = items[f];
                 memset(&it, 0, sizeof it);
@@ -1351,6 +1481,7 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
             CK(cudaMemcpyAsync(hstats.data(), cl.stats.p, sizeof(int64_t) * 4 * nf, cudaMemcpyDeviceToHost, s), "stats");
             CK(cudaStreamSynchronize(s), "sync");
             for (int f = 0; f < nf; ++f) { capped += hstats[4 * f + 1]; steps += hstats[4 * f + 2]; }
+            if (aborted()) return fail(ctx, SOC_ERR_TIMEOUT, "aborted (soc_abort or the soc_set_timeout deadline)");
             return SOC_OK;
         };
         // iteration 0: constant sources, kept as A_const
@@ -1373,8 +1504,6 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
         } else {
             if ((st = soc_update_temperature(ctx, cloud_id, cl.A_const.p, d_T_out, nullptr, stream))) return st;
         }
-        int it_done = 0, conv = 0;
-        double dT = 0.0;
         double n_cum = 0.0;
         for (int k = 1; k <= prm->max_iter; ++k) {
             if (reffield) {
@@ -1485,6 +1614,8 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
             it_done = k;
             if (dT < prm->dT_tol) { conv = 1; break; }
         }
+        return SOC_OK;
+        }();
         if (res) {
             res->iterations = it_done;
             res->converged = conv;
@@ -1492,6 +1623,7 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
             res->steps = steps;
             res->capped = capped;
         }
+        if (run_st != SOC_OK) return run_st;
         return capped ? fail(ctx, SOC_ERR_STEP_LIMIT, "%lld packages hit the step cap", (long long)capped) : SOC_OK;
     });
 }
@@ -1587,6 +1719,8 @@ extern "C" soc_status soc_simulate_frequency_batch_noalloc(soc_ctx *ctx, const s
         P.stats = reinterpret_cast<unsigned long long *>(d_stats);
         P.pkg_steps = d_pkg_steps;
         P.counter = &S->counter;
+        P.abort_flag = ctx->d_abort;
+        P.cut = ctx->d_abort + 1;
         P.total = total;
         P.seed = ctx->seed;
         P.n_items = n_items;

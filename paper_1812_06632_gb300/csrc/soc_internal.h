@@ -67,6 +67,8 @@ struct TraceParams {
     int32_t chunk;
     int32_t refill_min;          // refill a warp's idle lanes once this many are idle
     int32_t scatter_min;         // scatter a warp's waiting lanes once this many wait
+    const int *abort_flag;       // host-mapped: nonzero = take no more work (soc_abort)
+    int *cut;                    // host-mapped: set to 1 when work was left untraced
     HotCloud hot;                // cell != nullptr: every item uses this one cloud
     int32_t regular;             // every item's cloud is a regular grid (selects the
                                  // tracer build without octree traversal, two steps
@@ -131,5 +133,12 @@ cudaError_t launch_update_temperature_ali(const DevCloud *dcl, int64_t n_cells, 
 cudaError_t launch_dust_emission(const DevCloud *dcl, int64_t n_leaf, const TempTables &tt, const float *T,
                                  int freq_lo, int n_freq, uint32_t n_per_cell, uint64_t *w,
                                  double *e_unit, unsigned long long *scratch_max, cudaStream_t s);
+
+// Learned seed: network features of a cloud's cells and the seeding transform
+// (soc_nn.cu).  norm = {lt_mean, lt_std, lr_mean, lr_std}.
+cudaError_t launch_seed_features(const float *T1, const float *rho, int64_t n, const double norm[4], float *x,
+                                 cudaStream_t s);
+cudaError_t launch_seed_transform(const float *T1, const float *pred, int64_t n, double y_mean, double y_std,
+                                  float *T_seed, cudaStream_t s);
 
 }  // namespace soc

@@ -13,11 +13,15 @@
 //             memory;
 //   dgrad:    the forward kernel with the weights flipped in space and
 //             transposed in channels;
-//   wgrad:    M = C_out, N = C_in per tap, K = voxels (split over blocks,
-//             FP32 atomics), on the tcgen05 tensor cores as well.
-// BF16 inputs, FP32 accumulation throughout.
+//   wgrad:    M = C_out, N = C_in per tap, K = voxels (split over blocks
+//             that write partial sums, reduced in a fixed order), on the
+//             tcgen05 tensor cores as well.
+// BF16 inputs, FP32 accumulation throughout.  Every reduction (weight and
+// bias gradients, the loss) sums per-block partials in a fixed order, so a
+// training run is bit-reproducible.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -301,7 +305,7 @@ struct WgradArgs {
     int gy_stride, gy_off;
     const bf16 *x;
     int x_stride, x_off;
-    float *gw;                       // [Cout][27][Cin], accumulated
+    float *part;                     // [gridDim.x][Cout][27][Cin]: each block's partial sums
     int N, D, H, W, Cin, Cout;
     long long vox_per_block;
 };
@@ -312,7 +316,9 @@ struct WgradArgs {
 // The M = 128 rows of the accumulator are (tap, input channel) pairs: a
 // block takes TT = 128 / ci_tile consecutive taps of ci_tile input channels
 // (8 taps of 16 channels, 4 of 32, 2 of 64, 1 of 128), N = n_tile output
-// channels, K = voxels (split over blocks, FP32 atomics).  Both operands are
+// channels, K = voxels (split over blocks along x; block x writes its sums to
+// partial slice x, and reduce_partials_kernel adds the slices in order, so
+// the result does not depend on block scheduling).  Both operands are
 // staged MN-major: one 16-byte global row (8 channels of one voxel) is one
 // row of a core matrix (8 K-rows of 8 consecutive M or N elements, 128
 // bytes).  Core (mn, k) of A sits at (k * 16 + mn) * 128 bytes, of B at
@@ -446,10 +452,11 @@ __global__ void __launch_bounds__(128) conv3d_wgrad_tc_kernel(const WgradArgs a,
     }
     if (!ok_run) {
         atomicExch(&g_tc_error, 1);
-    } else if (last >= 0) {
+    } else {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16);
         const int tap = tap0 + tid / ci_tile, ci = ci0 + tid % ci_tile;   // accumulator lane = (tap, ci)
+        float *const slice = a.part + (long long)blockIdx.x * a.Cout * 27 * a.Cin;
         for (int c = 0; c < n_tile; c += 16) {
             uint32_t r[16];
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -459,9 +466,9 @@ __global__ void __launch_bounds__(128) conv3d_wgrad_tc_kernel(const WgradArgs a,
                          : "r"(row_addr + (uint32_t)c));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (tap >= 27) continue;
-            float *dst = a.gw + ((long long)(co0 + c) * 27 + tap) * a.Cin + ci;
+            float *dst = slice + ((long long)(co0 + c) * 27 + tap) * a.Cin + ci;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) atomicAdd(dst + (long long)j * 27 * a.Cin, __uint_as_float(r[j]));
+            for (int j = 0; j < 16; ++j) dst[(long long)j * 27 * a.Cin] = last >= 0 ? __uint_as_float(r[j]) : 0.f;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -472,22 +479,35 @@ __global__ void __launch_bounds__(128) conv3d_wgrad_tc_kernel(const WgradArgs a,
     }
 }
 
-// Bias gradient: gb[c] += sum_v gy[v][c] (BF16 gradient, dense C channels).
-__global__ void bias_grad_kernel(const bf16 *gy, int C, long long V, long long vox_per_block, float *gb)
+// out[i] += sum_{k < n_parts} part[k * n + i], k in increasing order (the
+// fixed-order reduction of per-block partial sums).
+__global__ void reduce_partials_kernel(const float *part, int n_parts, long long n, float *out)
 {
-    __shared__ float part[256];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int k = 0; k < n_parts; ++k) s += part[(long long)k * n + i];
+        out[i] += s;
+    }
+}
+
+// Bias gradient, per block: part[blockIdx.x][c] = sum over the block's voxels
+// of gy[v][c] (BF16 gradient, dense C channels); reduce_partials_kernel adds
+// the blocks' sums in order.
+__global__ void bias_grad_kernel(const bf16 *gy, int C, long long V, long long vox_per_block, float *part)
+{
+    __shared__ float s_part[256];
     const long long vb = (long long)blockIdx.x * vox_per_block;
     const long long ve = vb + vox_per_block < V ? vb + vox_per_block : V;
     const int c = threadIdx.x % C, lane_v = threadIdx.x / C, nv = blockDim.x / C;
     float s = 0.f;
     if (lane_v < nv)
         for (long long v = vb + lane_v; v < ve; v += nv) s += __bfloat162float(gy[v * C + c]);
-    part[threadIdx.x] = (lane_v < nv) ? s : 0.f;
+    s_part[threadIdx.x] = (lane_v < nv) ? s : 0.f;
     __syncthreads();
     if (threadIdx.x < C) {
         float t = 0.f;
-        for (int k = 0; k < nv; ++k) t += part[k * C + threadIdx.x];
-        atomicAdd(gb + threadIdx.x, t);
+        for (int k = 0; k < nv; ++k) t += s_part[k * C + threadIdx.x];
+        part[(long long)blockIdx.x * C + threadIdx.x] = t;
     }
 }
 
@@ -599,7 +619,10 @@ __global__ void input_kernel(const float *in, long long V, bf16 *x16)
 }
 
 // Prediction = head channel 0; MSE loss and its gradient into head channel 0.
-__global__ void mse_kernel(const float *head, const float *target, long long V, float *pred, float *ghead, double *loss)
+// loss_part[blockIdx.x] = the block's share of the loss (sum_loss_kernel
+// adds the shares in order).
+__global__ void mse_kernel(const float *head, const float *target, long long V, float *pred, float *ghead,
+                           double *loss_part)
 {
     __shared__ double part[256];
     double s = 0.0;
@@ -618,7 +641,16 @@ __global__ void mse_kernel(const float *head, const float *target, long long V, 
         if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0 && loss && target) atomicAdd(loss, part[0] / (double)V);
+    if (threadIdx.x == 0 && loss_part && target) loss_part[blockIdx.x] = part[0] / (double)V;
+}
+
+__global__ void sum_loss_kernel(const double *loss_part, int n, double *loss)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += loss_part[k];
+        *loss = s;
+    }
 }
 
 // Adam on FP32 master weights; writes the BF16 copy used by the kernels.
@@ -641,6 +673,31 @@ __global__ void to_bf16_kernel(const float *src, long long n, bf16 *dst)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+// Seeding transform of the learned temperature seed, in FP64 per cell.
+// Features: x[c][0] = (ln clamp(T1, 2.7, 3000) - lt_mean) / lt_std,
+//           x[c][1] = (ln max(rho, 1e-30) - lr_mean) / lr_std.
+__global__ void seed_features_kernel(const float *T1, const float *rho, long long n, double lt_mean, double lt_std,
+                                     double lr_mean, double lr_std, float *x)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const double t = fmin(fmax((double)T1[c], kTMin), kTMax);
+        const double r = fmax((double)rho[c], 1e-30);
+        x[2 * c] = (float)((log(t) - lt_mean) / lt_std);
+        x[2 * c + 1] = (float)((log(r) - lr_mean) / lr_std);
+    }
+}
+
+// T_seed = clamp(T1 exp(pred y_std + y_mean), 2.7, 3000): the network
+// predicts the normalised ln T - ln T1.
+__global__ void seed_transform_kernel(const float *T1, const float *pred, long long n, double y_mean, double y_std,
+                                      float *T_seed)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const double t = (double)T1[c] * exp((double)pred[c] * y_std + y_mean);
+        T_seed[c] = (float)fmin(fmax(t, kTMin), kTMax);
+    }
 }
 
 inline int grid_1d(long long n, int block = 256)
@@ -717,35 +774,67 @@ cudaError_t conv_launch(const ConvArgs &a, cudaStream_t s)
     return tc_launch<16, 1>(a, s);
 }
 
-cudaError_t wgrad_launch(const WgradArgs &a0, cudaStream_t s)
+// Launch plan of the weight gradient: tiles and the split of the voxels into
+// `chunks` blocks along x (about 4 blocks per SM).
+struct WgradPlan {
+    int ci_tile = 0, n_tile = 0, tap_groups = 0;
+    long long per = 0, chunks = 0;
+};
+
+inline WgradPlan wgrad_plan(long long V, int Cin, int Cout, int sms)
 {
-    WgradArgs a = a0;
-    const long long V = (long long)a.N * a.D * a.H * a.W;
-    int dev = 0, sms = 148, sm_smem = 0, blk_max = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&blk_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    WgradPlan p;
     // input-channel tile: 16, 32, 64 or 128 (dividing C_in), 128 / tile taps
     // per block; output-channel tile: a multiple of 16, at most 256
-    int ci_tile = 128;
-    while (ci_tile > 16 && a.Cin % ci_tile) ci_tile >>= 1;
-    if (a.Cin % ci_tile) return cudaErrorInvalidValue;
-    int n_tile = 256;
-    while (n_tile > 16 && (n_tile > a.Cout || a.Cout % n_tile)) n_tile -= 16;
-    const int TT = 128 / ci_tile;
-    const int tap_groups = (27 + TT - 1) / TT;
-    const long long tiles = (long long)tap_groups * (a.Cin / ci_tile) * (a.Cout / n_tile);
-    // split the voxels so that there are about 4 blocks per SM
+    p.ci_tile = 128;
+    while (p.ci_tile > 16 && Cin % p.ci_tile) p.ci_tile >>= 1;
+    p.n_tile = 256;
+    while (p.n_tile > 16 && (p.n_tile > Cout || Cout % p.n_tile)) p.n_tile -= 16;
+    const int TT = 128 / p.ci_tile;
+    p.tap_groups = (27 + TT - 1) / TT;
+    const long long tiles = (long long)p.tap_groups * (Cin / p.ci_tile) * (Cout / p.n_tile);
     long long chunks = (4LL * sms + tiles - 1) / tiles;
     long long per = (V + chunks - 1) / chunks;
     per = (per + kWgKV - 1) / kWgKV * kWgKV;
     if (per < kWgKV) per = kWgKV;
-    a.vox_per_block = per;
-    chunks = (V + per - 1) / per;
+    p.per = per;
+    p.chunks = (V + per - 1) / per;
+    return p;
+}
+
+inline int device_sms()
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+// Floats of partial sums a weight gradient of this shape needs.
+inline long long wgrad_part_floats(long long V, int Cin, int Cout, int sms)
+{
+    return wgrad_plan(V, Cin, Cout, sms).chunks * Cout * 27LL * Cin;
+}
+
+// gw[Cout][27][Cin] += sum_v gy[v] x[v + tap]: partial sums per voxel chunk
+// into part (part_floats available), then their ordered sum into gw.
+cudaError_t wgrad_launch(const WgradArgs &a0, float *gw, long long part_floats, cudaStream_t s)
+{
+    WgradArgs a = a0;
+    const long long V = (long long)a.N * a.D * a.H * a.W;
+    int dev = 0, sm_smem = 0, blk_max = 0;
+    cudaGetDevice(&dev);
+    const int sms = device_sms();
+    cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&blk_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const WgradPlan p = wgrad_plan(V, a.Cin, a.Cout, sms);
+    if (a.Cin % p.ci_tile) return cudaErrorInvalidValue;
+    const long long n_w = (long long)a.Cout * 27 * a.Cin;
+    if (p.chunks * n_w > part_floats) return cudaErrorInvalidValue;
+    a.vox_per_block = p.per;
     uint32_t cols = 32;
-    while ((int)cols < n_tile) cols <<= 1;
-    const int stage_bytes = (128 + n_tile) * kWgKV * 2;
+    while ((int)cols < p.n_tile) cols <<= 1;
+    const int stage_bytes = (128 + p.n_tile) * kWgKV * 2;
     int stages = 73728 / stage_bytes;
     stages = stages < 3 ? 3 : (stages > 4 ? 4 : stages);
     const int need = stages * stage_bytes + 8 * stages + 16;
@@ -756,15 +845,24 @@ cudaError_t wgrad_launch(const WgradArgs &a0, cudaStream_t s)
     if (bytes > blk_max) bytes = blk_max;
     cudaError_t e = cudaFuncSetAttribute(conv3d_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)chunks, (unsigned)tap_groups, (unsigned)((a.Cin / ci_tile) * (a.Cout / n_tile)));
-    conv3d_wgrad_tc_kernel<<<grid, 128, bytes, s>>>(a, ci_tile, n_tile, cols, stages);
+    dim3 grid((unsigned)p.chunks, (unsigned)p.tap_groups, (unsigned)((a.Cin / p.ci_tile) * (a.Cout / p.n_tile)));
+    conv3d_wgrad_tc_kernel<<<grid, 128, bytes, s>>>(a, p.ci_tile, p.n_tile, cols, stages);
+    reduce_partials_kernel<<<grid_1d(n_w), 256, 0, s>>>(a.part, (int)p.chunks, n_w, gw);
     return cudaGetLastError();
 }
 
-cudaError_t bias_grad_launch(const bf16 *gy, int C, long long V, float *gb, cudaStream_t s)
+constexpr long long kBiasVox = 4096;      // voxels per block of the bias gradient
+
+inline long long bias_part_floats(long long V, int C) { return (V + kBiasVox - 1) / kBiasVox * C; }
+
+// gb[C] += sum_v gy[v]: per-block sums into part, then their ordered sum.
+cudaError_t bias_grad_launch(const bf16 *gy, int C, long long V, float *gb, float *part, long long part_floats,
+                             cudaStream_t s)
 {
-    const long long per = 4096;
-    bias_grad_kernel<<<(unsigned)((V + per - 1) / per), 256, 0, s>>>(gy, C, V, per, gb);
+    const long long blocks = (V + kBiasVox - 1) / kBiasVox;
+    if (blocks * C > part_floats || C > 256) return cudaErrorInvalidValue;
+    bias_grad_kernel<<<(unsigned)blocks, 256, 0, s>>>(gy, C, V, kBiasVox, part);
+    reduce_partials_kernel<<<grid_1d(C), 256, 0, s>>>(part, (int)blocks, C, gb);
     return cudaGetLastError();
 }
 
@@ -805,7 +903,8 @@ struct Net {
     Buf<float> g_head, g_d0b, g_d0a, g_cat0, g_d1b, g_d1a, g_cat1, g_d2b, g_d2a, g_cat2, g_bb, g_ba, g_p2, g_e2a, g_p1,
         g_e1a, g_p0, g_e0a;
     Buf<bf16> gstage;
-    Buf<double> loss;
+    Buf<double> loss, loss_part;
+    Buf<float> part;              // per-block partial sums of the weight and bias gradients
 
     template <class F>
     void each(F f)
@@ -814,7 +913,7 @@ struct Net {
             f(w32[l]); f(b32[l]); f(gw[l]); f(gb[l]); f(mw[l]); f(vw[l]); f(mb[l]); f(vb[l]);
         }
         f(head); f(g_head); f(g_d0b); f(g_d0a); f(g_cat0); f(g_d1b); f(g_d1a); f(g_cat1); f(g_d2b); f(g_d2a);
-        f(g_cat2); f(g_bb); f(g_ba); f(g_p2); f(g_e2a); f(g_p1); f(g_e1a); f(g_p0); f(g_e0a);
+        f(g_cat2); f(g_bb); f(g_ba); f(g_p2); f(g_e2a); f(g_p1); f(g_e1a); f(g_p0); f(g_e0a); f(part);
     }
     template <class F>
     void each16(F f)
@@ -827,11 +926,26 @@ struct Net {
     {
         each([](Buf<float> &b) { b.release(); });
         each16([](Buf<bf16> &b) { b.release(); });
-        arg0.release(); arg1.release(); arg2.release(); loss.release();
+        arg0.release(); arg1.release(); arg2.release(); loss.release(); loss_part.release();
     }
 };
 
 }  // namespace nn
+
+cudaError_t launch_seed_features(const float *T1, const float *rho, int64_t n, const double norm[4], float *x,
+                                 cudaStream_t s)
+{
+    nn::seed_features_kernel<<<nn::grid_1d(n), 256, 0, s>>>(T1, rho, n, norm[0], norm[1], norm[2], norm[3], x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_transform(const float *T1, const float *pred, int64_t n, double y_mean, double y_std,
+                                  float *T_seed, cudaStream_t s)
+{
+    nn::seed_transform_kernel<<<nn::grid_1d(n), 256, 0, s>>>(T1, pred, n, y_mean, y_std, T_seed);
+    return cudaGetLastError();
+}
+
 }  // namespace soc
 
 using namespace soc::nn;
@@ -899,9 +1013,9 @@ soc_status bwd(Net &n, int l, const float *gy, int gy_stride, int gy_off, const 
     WgradArgs wa;
     memset(&wa, 0, sizeof wa);
     wa.gy = n.gstage.p; wa.gy_stride = Cout; wa.gy_off = 0; wa.x = x; wa.x_stride = x_stride; wa.x_off = x_off;
-    wa.gw = n.gw[l].p; wa.N = n.batch; wa.D = S; wa.H = S; wa.W = S; wa.Cin = Cin; wa.Cout = Cout;
-    NNCK(wgrad_launch(wa, s));
-    NNCK(bias_grad_launch(n.gstage.p, Cout, V, n.gb[l].p, s));
+    wa.part = n.part.p; wa.N = n.batch; wa.D = S; wa.H = S; wa.W = S; wa.Cin = Cin; wa.Cout = Cout;
+    NNCK(wgrad_launch(wa, n.gw[l].p, (long long)n.part.n, s));
+    NNCK(bias_grad_launch(n.gstage.p, Cout, V, n.gb[l].p, n.part.p, (long long)n.part.n, s));
     if (gx) {
         ConvArgs a = conv_args(n.gstage.p, Cout, 0, n.wt[l].p, nullptr, n.batch, S, Cout, Cin, 0);
         a.out_f32 = gx; a.out_stride = gx_stride; a.out_off = gx_off; a.accumulate = accumulate;
@@ -953,8 +1067,8 @@ soc_status backward(Net &n, const float *d_target, cudaStream_t s)
             n.w16[l].p, kSpec[l].cout, kSpec[l].cin, n.wt[l].p);
     }
     NNCK(cudaMemsetAsync(n.g_head.p, 0, n.g_head.n * 4, s));
-    NNCK(cudaMemsetAsync(n.loss.p, 0, 8, s));
-    mse_kernel<<<grid_1d(n.V0), 256, 0, s>>>(n.head.p, d_target, n.V0, nullptr, n.g_head.p, n.loss.p);
+    mse_kernel<<<grid_1d(n.V0), 256, 0, s>>>(n.head.p, d_target, n.V0, nullptr, n.g_head.p, n.loss_part.p);
+    sum_loss_kernel<<<1, 32, 0, s>>>(n.loss_part.p, grid_1d(n.V0), n.loss.p);
     NNCK(cudaGetLastError());
     // decoder level 0
     if ((st = bwd(n, 14, n.g_head.p, 16, 0, nullptr, 0, 0, n.d0b.p, 16, 0, S0, n.g_d0b.p, 16, 0, 0, s))) return st;
@@ -1020,6 +1134,18 @@ soc_status soc_unet_create(int device, int batch, int side, int *net_id)
     A(n->g_d2a, n->V2 * 64); A(n->g_cat2, n->V2 * 192); A(n->g_bb, n->V3 * 128); A(n->g_ba, n->V3 * 128);
     A(n->g_p2, n->V3 * 64); A(n->g_e2a, n->V2 * 64); A(n->g_p1, n->V2 * 32); A(n->g_e1a, n->V1 * 32);
     A(n->g_p0, n->V1 * 16); A(n->g_e0a, n->V0 * 16); A(n->gstage, n->V0 * 48); A(n->loss, 1);
+    A(n->loss_part, (size_t)grid_1d(n->V0));
+    {   // partial sums: the largest weight (or bias) gradient of any layer
+        const int sms = device_sms();
+        long long need = 0;
+        for (int l = 0; l < kLayers; ++l) {
+            const int lev = l < 2 ? 0 : l < 4 ? 1 : l < 6 ? 2 : l < 8 ? 3 : l < 10 ? 2 : l < 12 ? 1 : 0;
+            const long long V = n->V0 >> (3 * lev);
+            need = std::max(need, wgrad_part_floats(V, kSpec[l].cin, kSpec[l].cout, sms));
+            need = std::max(need, bias_part_floats(V, kSpec[l].cout));
+        }
+        A(n->part, (size_t)need);
+    }
     if (e != cudaSuccess) { n->release(); delete n; return SOC_ERR_NOMEM; }
     for (int l = 0; l < kLayers; ++l) {
         cudaMemset(n->mw[l].p, 0, n->mw[l].n * 4); cudaMemset(n->vw[l].p, 0, n->vw[l].n * 4);
@@ -1183,14 +1309,46 @@ soc_status soc_nn_conv3d_dgrad(const void *gy, int N, int D, int H, int W, int C
 soc_status soc_nn_conv3d_wgrad(const void *gy, const void *x, int N, int D, int H, int W, int Cin, int Cout, float *gw,
                                float *gb, void *stream)
 {
-    if (!gy || !x || !gw || Cin % 16 || Cout % 16) return SOC_ERR_ARG;
+    if (!gy || !x || !gw || Cin % 16 || Cout % 16 || N < 1 || D < 1 || H < 1 || W < 1) return SOC_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    const long long V = (long long)N * D * H * W;
+    const long long need = std::max(wgrad_part_floats(V, Cin, Cout, device_sms()), bias_part_floats(V, Cout));
+    // partial sums in a library-owned workspace of this device (grown on
+    // demand; calls on one device share it and are ordered by the caller)
+    static std::mutex ws_mutex;
+    static std::vector<Buf<float>> ws;
+    std::lock_guard<std::mutex> lock(ws_mutex);
+    int dev = 0;
+    NNCK(cudaGetDevice(&dev));
+    try {
+        if ((int)ws.size() <= dev) ws.resize(dev + 1);
+    } catch (...) {
+        return SOC_ERR_NOMEM;
+    }
+    Buf<float> &w = ws[dev];
+    if ((long long)w.n < need) {
+        NNCK(cudaStreamSynchronize(s));          // the old workspace may still be in use on this stream
+        w.release();
+        if (w.alloc((size_t)need) != cudaSuccess) { w.p = nullptr; w.n = 0; return SOC_ERR_NOMEM; }
+    }
     WgradArgs wa;
     memset(&wa, 0, sizeof wa);
-    wa.gy = (const bf16 *)gy; wa.gy_stride = Cout; wa.x = (const bf16 *)x; wa.x_stride = Cin; wa.gw = gw;
+    wa.gy = (const bf16 *)gy; wa.gy_stride = Cout; wa.x = (const bf16 *)x; wa.x_stride = Cin; wa.part = w.p;
     wa.N = N; wa.D = D; wa.H = H; wa.W = W; wa.Cin = Cin; wa.Cout = Cout;
-    NNCK(wgrad_launch(wa, s));
-    if (gb) NNCK(bias_grad_launch((const bf16 *)gy, Cout, (long long)N * D * H * W, gb, s));
+    NNCK(wgrad_launch(wa, gw, (long long)w.n, s));
+    if (gb) NNCK(bias_grad_launch((const bf16 *)gy, Cout, V, gb, w.p, (long long)w.n, s));
+    return SOC_OK;
+}
+
+soc_status soc_nn_adam(float *d_w, float *d_m, float *d_v, const float *d_g, int64_t n, float lr, int32_t t,
+                       void *d_w_bf16, void *stream)
+{
+    if (!d_w || !d_m || !d_v || !d_g || n < 1 || t < 1 || !(lr >= 0.f)) return SOC_ERR_ARG;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    adam_kernel<<<grid_1d(n), 256, 0, (cudaStream_t)stream>>>(d_w, d_m, d_v, d_g, n, lr, b1, b2, eps, c1, c2,
+                                                              (bf16 *)d_w_bf16);
+    NNCK(cudaGetLastError());
     return SOC_OK;
 }
 

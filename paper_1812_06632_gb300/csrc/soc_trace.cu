@@ -17,6 +17,8 @@
 // (2^31 units per package, so a package's weight and its pending deposits
 // fit 32-bit registers) and are merged per cell before one 64-bit
 // atomic add, so the counters are exact and independent of scheduling.
+// A host-set abort flag, read when a warp takes a new chunk of work, stops the
+// launch early (paper-independent failure handling: a watchdog's deadline).
 // Compiled with -fmad=false.
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -526,7 +528,17 @@ __global__ void __launch_bounds__(256, kMinBlocks) trace_kernel(const TraceParam
             uint64_t q_next = q[0], q_end = q[1];
             if (q_next >= q_end) {
                 unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(P.counter, (unsigned long long)span);
+                if (lane == 0) {
+                    base = atomicAdd(P.counter, (unsigned long long)span);
+                    // host abort (soc_abort, a watchdog): the chunk is dropped
+                    // and the warp takes no more work; packages in flight end
+                    // normally, so the counters of what was traced conserve
+                    // energy exactly.  One read of host-mapped memory per chunk.
+                    if (base < P.total && *reinterpret_cast<const volatile int *>(P.abort_flag)) {
+                        *reinterpret_cast<volatile int *>(P.cut) = 1;
+                        base = P.total;
+                    }
+                }
                 base = __shfl_sync(kFull, base, 0);
                 if (base >= P.total) { exhausted = true; break; }
                 q_next = base;

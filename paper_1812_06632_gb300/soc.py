@@ -33,6 +33,8 @@ LIB_PATH = os.environ.get("SOC_LIB") or os.path.join(_HERE, "_build", "libsoc.so
 
 SOC_OK = 0
 SOC_ERR_STEP_LIMIT = -4
+SOC_ERR_STATE = -5
+SOC_ERR_TIMEOUT = -7
 SRC_BACKGROUND, SRC_POINT, SRC_DUST = 0, 1, 2
 W_UNIT = 1 << 31
 
@@ -48,7 +50,8 @@ EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "so
            "soc_unet_create", "soc_unet_destroy", "soc_unet_param_count", "soc_unet_set_params",
            "soc_unet_get_params", "soc_unet_forward", "soc_unet_backward", "soc_unet_adam",
            "soc_nn_conv3d", "soc_nn_conv3d_dgrad", "soc_nn_conv3d_wgrad", "soc_nn_error_flag",
-           "soc_simulate_frequency_batch_noalloc"]
+           "soc_simulate_frequency_batch_noalloc", "soc_abort", "soc_abort_clear", "soc_abort_status",
+           "soc_set_timeout", "soc_nn_adam", "soc_seed_features", "soc_seed_transform"]
 
 
 class GridDesc(C.Structure):
@@ -136,6 +139,13 @@ def _load():
         "soc_set_max_steps": ([P, C.c_uint32], I),
         "soc_probe_read": ([P, P, C.c_uint64, C.c_int32, P], I),
         "soc_simulate_frequency_batch_noalloc": ([P, P, I, P, P, P, P], I),
+        "soc_abort": ([P], I),
+        "soc_abort_clear": ([P], I),
+        "soc_abort_status": ([P, C.POINTER(I), C.POINTER(I)], I),
+        "soc_set_timeout": ([P, C.c_double], I),
+        "soc_nn_adam": ([P, P, P, P, C.c_int64, C.c_float, C.c_int32, P, P], I),
+        "soc_seed_features": ([P, I, P, P, P, P], I),
+        "soc_seed_transform": ([P, I, P, P, C.c_double, C.c_double, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -277,6 +287,24 @@ class Context:
     def set_max_steps(self, n):
         self._check(lib.soc_set_max_steps(self.h, n))
 
+    def abort(self):
+        """soc_abort: tracer launches of this context take no more work."""
+        self._check(lib.soc_abort(self.h))
+
+    def abort_clear(self):
+        self._check(lib.soc_abort_clear(self.h))
+
+    def abort_status(self):
+        """(requested, cut): the abort flag, and whether a launch since the
+        last clear left work untraced."""
+        r, c = C.c_int(0), C.c_int(0)
+        self._check(lib.soc_abort_status(self.h, C.byref(r), C.byref(c)))
+        return bool(r.value), bool(c.value)
+
+    def set_timeout(self, seconds: float):
+        """soc_set_timeout: watchdog deadline of each iterate call (0 = none)."""
+        self._check(lib.soc_set_timeout(self.h, float(seconds)))
+
     def probe_read(self, buf, reps: int, stream=None):
         """soc_probe_read: `reps` reads of the device tensor `buf` in one
         launch (measurement helper; the caller times it)."""
@@ -399,6 +427,17 @@ class Context:
         self._check(lib.soc_map(self.h, cloud_id, _t_ptr(T), freq, _np_ptr(d), _np_ptr(u), npx, npy,
                                 float(pix_size), _np_ptr(c), float(I_bg), _t_ptr(out), _stream(stream)))
 
+    def seed_features(self, cloud_id, T1, norm, x, stream=None):
+        """soc_seed_features: x (float32 [n_cells, 2]) from T1 and the grid's
+        density; norm = (lt_mean, lt_std, lr_mean, lr_std)."""
+        nrm = np.ascontiguousarray(norm, np.float64)
+        self._check(lib.soc_seed_features(self.h, cloud_id, _t_ptr(T1), _np_ptr(nrm), _t_ptr(x), _stream(stream)))
+
+    def seed_transform(self, cloud_id, T1, pred, y_mean, y_std, T_seed, stream=None):
+        """soc_seed_transform: T_seed = clamp(T1 exp(pred y_std + y_mean))."""
+        self._check(lib.soc_seed_transform(self.h, cloud_id, _t_ptr(T1), _t_ptr(pred), float(y_mean), float(y_std),
+                                           _t_ptr(T_seed), _stream(stream)))
+
     def update_temperature_ali(self, cloud_id, A, A_self, T, max_dT=None, stream=None):
         self._check(lib.soc_update_temperature_ali(self.h, cloud_id, _t_ptr(A), _t_ptr(A_self), _t_ptr(T),
                                                    _t_ptr(max_dT), _stream(stream)))
@@ -421,16 +460,19 @@ class Context:
         diagonal operator; reference_field "mean" or
         "difference" with package counts growing from n_dust_first to
         n_dust_last.  T_out receives the temperatures.  Returns iterations,
-        converged, final_max_dT, steps, capped and the max |dT| history."""
+        converged, final_max_dT, steps, capped, the max |dT| history and
+        timed_out (the abort flag or the set_timeout deadline stopped it)."""
         modes = {False: 0, True: 1, 0: 0, 1: 1, 2: 2, "mean": 1, "difference": 2}
         p = IterateParams(n_background, n_point, n_per_cell, max_iter, dT_tol, int(reuse_constant), int(ali),
                           n_weighted, weighted_cap, modes[reference_field], n_dust_first, n_dust_last)
         r = IterateResult()
         hist = np.zeros(max(max_iter, 1), np.float64)
-        self._check(lib.soc_iterate(self.h, cloud_id, C.byref(p), _t_ptr(T_seed), _t_ptr(T_out), C.byref(r),
-                                    _np_ptr(hist), _stream(stream)), ok=(SOC_OK, SOC_ERR_STEP_LIMIT))
+        st = self._check(lib.soc_iterate(self.h, cloud_id, C.byref(p), _t_ptr(T_seed), _t_ptr(T_out), C.byref(r),
+                                         _np_ptr(hist), _stream(stream)),
+                         ok=(SOC_OK, SOC_ERR_STEP_LIMIT, SOC_ERR_TIMEOUT))
         return dict(iterations=r.iterations, converged=bool(r.converged), final_max_dT=r.final_max_dT,
-                    steps=r.steps, capped=r.capped, history=hist[:r.iterations].copy())
+                    steps=r.steps, capped=r.capped, history=hist[:r.iterations].copy(),
+                    timed_out=st == SOC_ERR_TIMEOUT)
 
 
 def _nn_check(st, what):
@@ -503,6 +545,12 @@ def conv3d_dgrad(gy, w, w_scratch, gx, stream=None):
     Cin = w.shape[2]
     _nn_check(lib.soc_nn_conv3d_dgrad(_t_ptr(gy), N, D, H, W, Cout, _t_ptr(w), Cin, _t_ptr(w_scratch),
                                       _t_ptr(gx), _stream(stream)), "soc_nn_conv3d_dgrad")
+
+
+def adam(w, m, v, g, lr, t, w_bf16=None, stream=None):
+    """soc_nn_adam: one Adam step at step t on FP32 device tensors."""
+    _nn_check(lib.soc_nn_adam(_t_ptr(w), _t_ptr(m), _t_ptr(v), _t_ptr(g), w.numel(), C.c_float(lr), int(t),
+                              _t_ptr(w_bf16), _stream(stream)), "soc_nn_adam")
 
 
 def conv3d_wgrad(gy, x, gw, gb=None, stream=None):
