@@ -428,36 +428,50 @@ def run_gpu(args):
             out["roofline"]["fp32"] = {"achieved": fp32, "peak": peak32, "unit": "FP32 op/s", "frac": fp32 / peak32,
                                        "ops_per_unit": FP32_OPS_PER_STEP,
                                        "peak_source": f"128 FP32 lanes/SM x {sms} SMs x {mhz:.0f} MHz"}
-        print(json.dumps(out), flush=True)
     ctx.graph_destroy(g_trace)
     ctx.graph_destroy(g_temp)
     ctx.batch_destroy(batch)
     ctx.close()
+    del tally, stats, flush
+    torch.cuda.empty_cache()
+    if rank == 0:
+        if world == 1 and not args.no_workloads:
+            # the octree pass, the uneven 64-cloud batch and the learned-seeded
+            # time to convergence, each timed on its own (CUDA events for the
+            # launches, host wall clock for the iterations), with its clocks
+            out["workloads"] = {
+                "c3_octree": extra_workload("c3", steps=3, warmup=2),
+                "c5_batch": extra_workload("c5", steps=3, warmup=2),
+                "learned": learned_record(),
+            }
+        print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_extra(args):
-    """Secondary workloads (one JSON line each; not the headline):
+def extra_workload(workload, steps, warmup, packages=N_PACKAGES, freq_stride=1, autotune=False,
+                   convergence=True):
+    """Secondary workloads (a record each):
     c3: octree cloud (64^3 root + 3 levels, 4.4e6 cells), background + 3 point
         sources, 64 nu x 1e6 packages each, one graph-replayed launch per
-        pass; plus plain time to converged T (max |dT| < 0.1 K);
+        pass; plus plain and ALI time to converged T (max |dT| < 0.1 K);
     c5: 64 clouds of side 32-128, 32 nu, background + point sources,
-        1e5-1e6 packages per cloud, all in one persistent launch."""
+        1e5-1e6 packages per cloud, all in one persistent launch.
+    Launches timed with CUDA events on the launching stream, clocks sampled
+    during the timed launches."""
     import torch
     from paper_1812_06632_gb300 import build as B
     B.build()
     from paper_1812_06632_gb300 import inputs as I
     from paper_1812_06632_gb300 import soc
-    torch.cuda.set_device(0)
     t_gen = time.perf_counter()
-    if args.workload == "c3":
+    if workload == "c3":
         w = I.config_c3()
     else:
         w = I.config_c5()
-    if args.packages != N_PACKAGES:                  # smaller launches for profiling captures
-        w.n_bg = [min(n, args.packages) for n in w.n_bg]
-        w.n_ps = [min(n, args.packages) for n in w.n_ps]
+    if packages != N_PACKAGES:                  # smaller launches for profiling captures
+        w.n_bg = [min(n, packages) for n in w.n_bg]
+        w.n_ps = [min(n, packages) for n in w.n_ps]
     t_gen = time.perf_counter() - t_gen
     nf = len(w.dust.nu)
     ctx = soc.Context(0, w.seed)
@@ -469,12 +483,12 @@ def run_extra(args):
         ids.append(cid)
     for ci, cl in enumerate(w.clouds):
         for src, npk in ((0, w.n_bg[ci]), (1, w.n_ps[ci])):
-            for f in range(0, nf, args.freq_stride):
+            for f in range(0, nf, freq_stride):
                 specs.append(dict(cloud=ids[ci], source=src, freq=f, n_packages=npk, tally_offset=off))
                 off += cl.n_cells
     stream = torch.cuda.Stream()
     tuned = None
-    if args.autotune:
+    if autotune:
         # the project's autotuner on this very batch (every candidate must
         # give the same counters), then the launch below uses its choice
         from paper_1812_06632_gb300 import autotune as A
@@ -492,27 +506,34 @@ def run_extra(args):
     ctx.capture_begin(stream)
     ctx.batch_launch(batch, tally, stats, stream=stream)
     g = ctx.capture_end(stream)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         ctx.graph_launch(g, stream=stream)
     stream.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for k in range(args.steps):
-        ev[k][0].record(stream)
-        ctx.graph_launch(g, stream=stream)
-        ev[k][1].record(stream)
-    stream.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with Clocks(torch.cuda.current_device()) as clk:
+        for k in range(steps):
+            ev[k][0].record(stream)
+            ctx.graph_launch(g, stream=stream)
+            ev[k][1].record(stream)
+        stream.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
     st = stats.cpu().numpy()
-    steps = float(st[:, 2].sum())
+    n_steps = float(st[:, 2].sum())
     assert np.all(st[:, 1] == 0)
     t_ok = int(tally.sum().item()) + int(st[:, 0].sum()) == int(st[:, 3].sum())
-    out = {"metric": "photon-cell steps/s", "value": steps / (ms / 1e3), "unit": "photon-cell steps/s",
-           "workload": args.workload, "ms_per_launch": ms, "steps_per_launch": steps, "items": len(specs),
-           "clouds": len(w.clouds), "cells": int(sum(c.n_cells for c in w.clouds)), "frequencies": len(range(0, nf, args.freq_stride)),
+    peaks, peak_kind = _peaks()
+    gbs = n_steps * BYTES_PER_STEP / (ms / 1e3) / 1e9
+    out = {"metric": "photon-cell steps/s", "value": n_steps / (ms / 1e3), "unit": "photon-cell steps/s",
+           "workload": workload, "ms_per_launch": ms, "launches_timed": steps, "steps_per_launch": n_steps,
+           "items": len(specs), "clouds": len(w.clouds), "cells": int(sum(c.n_cells for c in w.clouds)),
+           "frequencies": len(range(0, nf, freq_stride)),
            "packages": int(sum(s["n_packages"] for s in specs)), "energy_conserved": bool(t_ok),
-           "roofline_hbm_frac_12B": steps * BYTES_PER_STEP / (ms / 1e3) / 1e9 / _peaks()[0]["hbm_gbs"],
-           "input_generation_s": t_gen, "autotune": tuned}
-    if args.workload == "c3" and not args.no_convergence:
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": gbs / peaks["hbm_gbs"], "bytes_per_unit": BYTES_PER_STEP,
+                        "peak_source": f"{peak_kind} hbm_gbs (copy)",
+                        "note": "12 B per photon-cell step; the +4 B per octree level moved are not counted"},
+           "clocks": clk.summary(), "input_generation_s": t_gen, "autotune": tuned}
+    if workload == "c3" and convergence:
         cl = w.clouds[0]
         out["convergence"] = {}
         Ts = {}
@@ -534,6 +555,16 @@ def run_extra(args):
     ctx.graph_destroy(g)
     ctx.batch_destroy(batch)
     ctx.close()
+    del tally, stats
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_extra(args):
+    import torch
+    torch.cuda.set_device(0)
+    out = extra_workload(args.workload, args.steps, args.warmup, args.packages, args.freq_stride, args.autotune,
+                         not args.no_convergence)
     print(json.dumps(out), flush=True)
 
 
@@ -543,27 +574,53 @@ UNET_LAYERS = [(16, 16, 0), (16, 16, 0), (16, 32, 1), (32, 32, 1), (32, 64, 2), 
                (16, 16, 0)]
 
 
-def run_learned(args):
+def learned_record():
     """The second half of the headline metric: wall time to converged T
-    (max|dT| < 0.1 K with frozen dust random numbers), learned-seeded against
-    plain, on the same GPU.  Generates the training clouds with the plain
-    Monte Carlo path, trains the U-Net, then runs the test clouds both ways
-    (about a minute and a half in all)."""
+    (max|dT| < 0.1 K, frozen dust random numbers) of the 20 held-out hot-core
+    clouds, learned-seeded against plain, each as one batched run (one
+    tracer launch per iteration for every unconverged cloud) after a shared
+    iteration 0, with the committed trained weights.  Host wall clock around
+    synchronised runs; clocks sampled throughout."""
+    import torch
+    from paper_1812_06632_gb300 import learned as L
+    if not os.path.exists(L.WEIGHTS):
+        return {"unavailable": f"no trained weights ({os.path.relpath(L.WEIGHTS, ROOT)}); "
+                               "train with python -m paper_1812_06632_gb300.learned"}
+    params, norm, meta, digest = L.load_weights()
+    with Clocks(torch.cuda.current_device()) as clk:
+        c = L.compare(params, norm, L.TEST, log=lambda *a, **k: None)
+    n = c["n_clouds"]
+    return {"metric": "wall time to converged T (max|dT|<0.1K), learned-seeded", "value": c["learned_s"],
+            "unit": f"s for the batch of {n} clouds", "higher_is_better": False, "plain_value": c["plain_s"],
+            "learned_over_plain": c["learned_s"] / c["plain_s"],
+            "constant_sources_s": c["constant_s"], "plain_dust_s": c["plain_dust_s"],
+            "learned_dust_s": c["learned_dust_s"],
+            "plain_dust_iterations": c["plain_iterations"], "learned_dust_iterations": c["learned_iterations"],
+            "plain_iterations_total": int(sum(c["plain_iterations"])),
+            "learned_iterations_total": int(sum(c["learned_iterations"])),
+            "plain_steps": c["plain_steps"], "learned_steps": c["learned_steps"],
+            "converged": bool(c["plain_converged"] and c["learned_converged"]),
+            "max_abs_T_difference_K": c["max_abs_T_difference_K"],
+            "seed_max_err_K_mean": float(np.mean(c["seed_max_err_K"])),
+            "T1_max_err_K_mean": float(np.mean(c["T1_max_err_K"])),
+            "weights_sha256": digest, "trained": {k: meta.get(k) for k in ("best_epoch", "epochs_run", "train", "val")},
+            "clocks": clk.summary(),
+            "config": {"workload": f"{n} held-out hot-core clouds of {c['side']}^3 (seeds {L.TEST[0]}-{L.TEST[-1]}), "
+                                   "64 nu, 2e5 background + 2e5 point packages per nu, 1 dust package per cell "
+                                   f"per nu, tolerance {c['tol_K']} K"}}
+
+
+def run_learned(args):
+    """--workload learned: the learned-vs-plain record alone (--retrain: first
+    regenerate the data and train, writing the weights file)."""
     import torch
     from paper_1812_06632_gb300 import build as B
     B.build()
-    from paper_1812_06632_gb300 import learned as L
     torch.cuda.set_device(0)
-    s = L.run(log=lambda *a, **k: None)
-    n = s["n_test"]
-    out = {"metric": "wall time to converged T (max|dT|<0.1K), learned-seeded", "value": s["learned_total_s"] / n,
-           "unit": "s per cloud", "higher_is_better": False, "workload": "learned",
-           "plain_value": s["plain_total_s"] / n, "learned_over_plain": s["learned_total_s"] / s["plain_total_s"],
-           "learned_dust_iterations_mean": s["learned_iters_mean"], "plain_dust_iterations_mean": s["plain_iters_mean"],
-           "data_seconds": s["data_seconds"], "train_seconds": s["train_seconds"],
-           "config": {"workload": f"{n} test clouds of {s['side']}^3 (C4 recipe), {s['n_train']} training clouds, "
-                                  f"{s['epochs']} epochs, tolerance {s['tol_K']} K"}}
-    print(json.dumps(out), flush=True)
+    if args.retrain:
+        from paper_1812_06632_gb300 import learned as L
+        L.run(log=lambda *a, **k: None)
+    print(json.dumps({"workload": "learned", **learned_record()}), flush=True)
 
 
 def _map_segments(n, d, e1, e2, center, npx, npy, pix):
@@ -740,7 +797,20 @@ def main():
                     help="c3: skip the time-to-convergence runs (profiling captures)")
     ap.add_argument("--autotune", action="store_true",
                     help="c3/c5: run the launch autotuner on the batch first (16 candidates)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="c2: leave out the octree, batch and learned sub-records")
+    ap.add_argument("--retrain", action="store_true",
+                    help="learned: regenerate the training clouds and train before the comparison")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: relaunch this command under torchrun
+        import socket
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+               "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *sys.argv[1:]]
+        sys.exit(subprocess.call(cmd))
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "unet":

@@ -490,6 +490,32 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *par
                        double *dT_history, void *stream);
 
 /* ------------------------------------------------------------------------
+ * soc_iterate_batch -- soc_iterate for n_clouds clouds at once: iteration 0
+ * traces the background and point sources of every cloud in one tracer
+ * launch, and each dust iteration traces the re-emission of every cloud not
+ * yet converged in one launch (paper Sect. 4.2: many work items interleaved
+ * in one kernel), then updates each cloud's T.  A cloud leaves the batch once
+ * its max |dT| < dT_tol.  Each cloud's results (T, iterations, steps) are
+ * bit-identical to soc_iterate on that cloud alone (the packages, their
+ * random numbers and their integer counters do not depend on the launch).
+ * Synchronises once per iteration.
+ *   cloud_ids         host int [n_clouds], distinct uploaded clouds.
+ *   params            as soc_iterate; n_weighted and reference_field must
+ *                     be 0 (SOC_ERR_ARG), ali is supported.
+ *   d_T_seed          host array [n_clouds] of device float pointers, or
+ *                     NULL; a NULL entry starts that cloud from the constant
+ *                     sources' T.
+ *   d_T_out           host array [n_clouds] of device float [n_cells].
+ *   res               host [n_clouds] or NULL.
+ *   dT_history        host double [n_clouds][max_iter] or NULL.
+ * Scratch: counters for every item of one launch (library-owned, kept for
+ * the next call).  Abort flag and watchdog as soc_iterate.
+ * ------------------------------------------------------------------------ */
+soc_status soc_iterate_batch(soc_ctx *ctx, int n_clouds, const int *cloud_ids, const soc_iterate_params *params,
+                             const float *const *d_T_seed, float *const *d_T_out, soc_iterate_result *res,
+                             double *dT_history, void *stream);
+
+/* ------------------------------------------------------------------------
  * soc_nn_error_flag -- 1 if a tensor-core convolution block gave up waiting
  * for its matrix multiplies (each wait is bounded; the block then frees its
  * tensor memory and returns without writing its outputs), else 0; the flag
@@ -569,17 +595,37 @@ soc_status soc_nn_adam(float *d_w, float *d_m, float *d_v, const float *d_g, int
  *                       ln rho mean, ln rho std} of the training set (stds
  *                       > 0).  The grid must be a regular cube whose side is
  *                       a multiple of 8 (SOC_ERR_ARG otherwise).
- *   soc_seed_transform  d_T_seed[c] = clamp(T1[c] exp(pred[c] y_std + y_mean),
- *                       2.7, 3000) for every cell (the network predicts the
- *                       normalised ln T - ln T1).  d_T1, d_pred, d_T_seed:
- *                       device float [n_cells].
- * Both asynchronous on `stream`; d_T_seed may be passed as the seed of
+ *   soc_seed_transform  for every cell (the network predicts the normalised
+ *                       y = ln T - ln T1):
+ *                         y = shrink (pred[c] y_std + y_mean);
+ *                         with an envelope (n_bins > 0): bin b of ln T1
+ *                         (n_bins equal bins over [lnT1_lo, lnT1_hi), the
+ *                         end bins extended), y = min(max(y, y_lo[b]), y_hi[b]);
+ *                         d_T_seed[c] = clamp(T1[c] exp(y), 2.7, 3000).
+ *                       map: host soc_seed_map (copied into the launch).
+ *                       d_T1, d_pred, d_T_seed: device float [n_cells].
+ *   soc_nn_seed_features  the features of soc_seed_features from caller
+ *                       arrays (no context): d_T1, d_rho device float [n],
+ *                       d_x device float [n][2] (e.g. a training set kept
+ *                       after its clouds were freed).
+ * All asynchronous on `stream`; d_T_seed may be passed as the seed of
  * soc_iterate or soc_iterate_batch.
  * ------------------------------------------------------------------------ */
 soc_status soc_seed_features(soc_ctx *ctx, int cloud_id, const float *d_T1, const double *norm, float *d_x,
                              void *stream);
-soc_status soc_seed_transform(soc_ctx *ctx, int cloud_id, const float *d_T1, const float *d_pred, double y_mean,
-                              double y_std, float *d_T_seed, void *stream);
+#define SOC_SEED_MAX_BINS 64
+typedef struct soc_seed_map {
+    double y_mean, y_std;      /* de-normalisation of the prediction            */
+    double shrink;             /* factor on the de-normalised prediction (> 0) */
+    int32_t n_bins;            /* 0: no envelope; else 1..SOC_SEED_MAX_BINS     */
+    int32_t reserved;
+    double lnT1_lo, lnT1_hi;   /* the bins' range of ln T1 (lo < hi)            */
+    double y_lo[SOC_SEED_MAX_BINS], y_hi[SOC_SEED_MAX_BINS];   /* per-bin bounds */
+} soc_seed_map;
+soc_status soc_seed_transform(soc_ctx *ctx, int cloud_id, const float *d_T1, const float *d_pred,
+                              const soc_seed_map *map, float *d_T_seed, void *stream);
+soc_status soc_nn_seed_features(const float *d_T1, const float *d_rho, int64_t n, const double *norm, float *d_x,
+                                void *stream);
 
 /* ------------------------------------------------------------------------
  * Launch configuration of the tracer (autotuner hook).  threads_per_block in

@@ -243,11 +243,21 @@ def seed_features(T1, rho, norm):
     return np.stack([lt, lr], axis=-1)
 
 
-def seed_transform(T1, pred, y_mean, y_std):
-    """T_seed = T1 exp(pred y_std + y_mean), clamped to [T_MIN, T_MAX]: the
-    network predicts the normalised ln T - ln T1."""
+def seed_transform(T1, pred, y_mean, y_std, shrink=1.0, envelope=None):
+    """T_seed = T1 exp(y), clamped to [T_MIN, T_MAX], with y = shrink (pred
+    y_std + y_mean) (the network predicts the normalised ln T - ln T1) and,
+    given an envelope (lnT1_lo, lnT1_hi, y_lo[n], y_hi[n]), y bounded to
+    [y_lo[b], y_hi[b]] of the bin b of ln T1 (clamped to [T_MIN, T_MAX]) among
+    n equal bins over [lnT1_lo, lnT1_hi), the end bins extended."""
     T1 = np.asarray(T1, np.float64)
-    return np.clip(T1 * np.exp(np.asarray(pred, np.float64) * y_std + y_mean), T_MIN, T_MAX)
+    y = shrink * (np.asarray(pred, np.float64) * y_std + y_mean)
+    if envelope is not None:
+        lo, hi, ylo, yhi = envelope
+        n = len(ylo)
+        lt = np.log(np.clip(T1, T_MIN, T_MAX))
+        b = np.clip(np.floor((lt - lo) / (hi - lo) * n).astype(np.int64), 0, n - 1)
+        y = np.minimum(np.maximum(y, np.asarray(ylo, np.float64)[b]), np.asarray(yhi, np.float64)[b])
+    return np.clip(T1 * np.exp(y), T_MIN, T_MAX)
 
 
 def init_params(seed=0, scale=1.0):

@@ -120,6 +120,10 @@ struct soc_ctx {
     volatile int *h_abort = nullptr;
     int *d_abort = nullptr;
     double timeout_s = 0.0;       // soc_iterate watchdog (0 = none)
+    // soc_iterate_batch scratch: counters of every item of a launch, self
+    // counters (ALI), statistics and per-cloud max |dT|
+    DevBuf<int64_t> b_tally, b_self, b_stats;
+    DevBuf<double> b_maxdT;
     // launch
     int tpb = 256, bps = 4, chunk = 16, refill_min = 8, scatter_min = 8;   // autotuned on the 128^3 x 64 nu workload
     uint32_t max_steps = 10000000u;
@@ -316,6 +320,7 @@ void soc_destroy(soc_ctx *ctx)
     ctx->d_wscratch.release();
     ctx->d_level_start.release();
     ctx->d_map_S.release();
+    ctx->b_tally.release(); ctx->b_self.release(); ctx->b_stats.release(); ctx->b_maxdT.release();
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->h_abort) cudaFreeHost((void *)ctx->h_abort);
     for (BatchHost *b : ctx->batches)
@@ -1296,17 +1301,24 @@ soc_status soc_seed_features(soc_ctx *ctx, int cloud_id, const float *d_T1, cons
     });
 }
 
-soc_status soc_seed_transform(soc_ctx *ctx, int cloud_id, const float *d_T1, const float *d_pred, double y_mean,
-                              double y_std, float *d_T_seed, void *stream)
+soc_status soc_seed_transform(soc_ctx *ctx, int cloud_id, const float *d_T1, const float *d_pred,
+                              const soc_seed_map *map, float *d_T_seed, void *stream)
 {
     return guarded(ctx, [&]() -> soc_status {
         soc_status st = check_cloud(ctx, cloud_id);
         if (st) return st;
-        if (!d_T1 || !d_pred || !d_T_seed) return fail(ctx, SOC_ERR_ARG, "null argument");
-        if (!std::isfinite(y_mean) || !std::isfinite(y_std)) return fail(ctx, SOC_ERR_ARG, "y_mean, y_std must be finite");
+        if (!d_T1 || !d_pred || !map || !d_T_seed) return fail(ctx, SOC_ERR_ARG, "null argument");
+        if (!std::isfinite(map->y_mean) || !std::isfinite(map->y_std) || !(map->shrink > 0.0) ||
+            !std::isfinite(map->shrink))
+            return fail(ctx, SOC_ERR_ARG, "y_mean, y_std must be finite and shrink > 0");
+        if (map->n_bins < 0 || map->n_bins > SOC_SEED_MAX_BINS ||
+            (map->n_bins > 0 && !(map->lnT1_hi > map->lnT1_lo)))
+            return fail(ctx, SOC_ERR_ARG, "envelope: n_bins in [0, %d] and lnT1_lo < lnT1_hi", SOC_SEED_MAX_BINS);
+        for (int b = 0; b < map->n_bins; ++b)
+            if (!(map->y_lo[b] <= map->y_hi[b])) return fail(ctx, SOC_ERR_ARG, "envelope bin %d: y_lo > y_hi", b);
         CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-        CK(launch_seed_transform(d_T1, d_pred, ctx->clouds[cloud_id]->n_cells, y_mean, y_std, d_T_seed,
-                                 (cudaStream_t)stream), "seed transform");
+        CK(launch_seed_transform(d_T1, d_pred, ctx->clouds[cloud_id]->n_cells, *map, d_T_seed, (cudaStream_t)stream),
+           "seed transform");
         return SOC_OK;
     });
 }
@@ -1625,6 +1637,214 @@ soc_status soc_iterate(soc_ctx *ctx, int cloud_id, const soc_iterate_params *prm
         }
         if (run_st != SOC_OK) return run_st;
         return capped ? fail(ctx, SOC_ERR_STEP_LIMIT, "%lld packages hit the step cap", (long long)capped) : SOC_OK;
+    });
+}
+
+soc_status soc_iterate_batch(soc_ctx *ctx, int n_clouds, const int *cloud_ids, const soc_iterate_params *prm,
+                             const float *const *d_T_seed, float *const *d_T_out, soc_iterate_result *res,
+                             double *dT_history, void *stream)
+{
+    return guarded(ctx, [&]() -> soc_status {
+        if (!ctx || n_clouds < 1 || !cloud_ids || !prm || !d_T_out || prm->max_iter < 0)
+            return fail(ctx, SOC_ERR_ARG, "bad iterate_batch arguments");
+        if (prm->n_weighted || prm->reference_field)
+            return fail(ctx, SOC_ERR_ARG, "iterate_batch: weighted sampling and the reference field are per-cloud "
+                        "options (soc_iterate)");
+        if (ctx->n_freq == 0) return fail(ctx, SOC_ERR_STATE, "soc_dust_upload must come first");
+        if (prm->max_iter > 0 && prm->n_per_cell == 0) return fail(ctx, SOC_ERR_ARG, "n_per_cell must be >= 1");
+        for (int k = 0; k < n_clouds; ++k) {
+            soc_status st = check_cloud(ctx, cloud_ids[k]);
+            if (st) return st;
+            if (!d_T_out[k]) return fail(ctx, SOC_ERR_ARG, "d_T_out[%d] is NULL", k);
+            for (int j = 0; j < k; ++j)
+                if (cloud_ids[j] == cloud_ids[k]) return fail(ctx, SOC_ERR_ARG, "cloud %d listed twice", cloud_ids[k]);
+            const CloudHost &cl = *ctx->clouds[cloud_ids[k]];
+            if (prm->reuse_constant && !cl.has_const)
+                return fail(ctx, SOC_ERR_STATE, "reuse_constant: no earlier iteration 0 on cloud %d", cloud_ids[k]);
+            if (!prm->reuse_constant && prm->n_background && cl.bg_I.empty())
+                return fail(ctx, SOC_ERR_STATE, "cloud %d: no background uploaded", cloud_ids[k]);
+            if (!prm->reuse_constant && prm->n_point && cl.n_ps == 0)
+                return fail(ctx, SOC_ERR_STATE, "cloud %d: no point sources uploaded", cloud_ids[k]);
+        }
+        CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int nf = ctx->n_freq;
+        const bool ali = prm->ali != 0;
+        // per-cloud buffers (as soc_iterate) and the batch's shared scratch
+        int64_t cells_all = 0;
+        for (int k = 0; k < n_clouds; ++k) {
+            CloudHost &cl = *ctx->clouds[cloud_ids[k]];
+            CK(cl.A_const.alloc(cl.n_cells), "alloc A");
+            CK(cl.A.alloc(cl.n_cells), "alloc A");
+            CK(cl.e_unit.alloc(nf), "alloc e_unit");
+            if (prm->max_iter > 0) CK(cl.dust_w.alloc((size_t)nf * cl.n_leaf), "alloc dust weights");
+            if (ali && prm->max_iter > 0) CK(cl.A_self.alloc(cl.n_cells), "alloc A_self");
+            cells_all += cl.n_cells;
+        }
+        const int n_src = (prm->reuse_constant ? 0 : (prm->n_background ? 1 : 0) + (prm->n_point ? 1 : 0));
+        const int per_cloud_items = std::max(n_src, prm->max_iter > 0 ? 1 : 0) * nf;
+        CK(ctx->b_tally.alloc((size_t)std::max(n_src, 1) * nf * cells_all), "alloc batch counters");
+        if (ali && prm->max_iter > 0) CK(ctx->b_self.alloc((size_t)nf * cells_all), "alloc batch self counters");
+        CK(ctx->b_stats.alloc((size_t)4 * std::max(per_cloud_items, 1) * n_clouds), "alloc batch stats");
+        CK(ctx->b_maxdT.alloc(n_clouds), "alloc max dT");
+        std::vector<int64_t> hstats(4 * (size_t)std::max(per_cloud_items, 1) * n_clouds);
+        std::vector<double> hdT(n_clouds, 0.0);
+        std::vector<int64_t> steps(n_clouds, 0), capped(n_clouds, 0);
+        std::vector<int> it_done(n_clouds, 0), conv(n_clouds, 0);
+        std::vector<soc_batch_item> items;
+        std::vector<int> item_cloud;          // batch position of each item's cloud
+        std::vector<int64_t> base(n_clouds);  // element offset of each cloud's slices in b_tally
+        Watchdog watchdog;
+        if (ctx->timeout_s > 0.0) watchdog.start(ctx->h_abort, ctx->timeout_s);
+        auto aborted = [&]() { return __atomic_load_n(const_cast<int *>(&ctx->h_abort[0]), __ATOMIC_SEQ_CST) != 0; };
+        // one tracer launch over `items`, then per-cloud statistics
+        auto launch = [&](int64_t *self) -> soc_status {
+            if (aborted()) return fail(ctx, SOC_ERR_TIMEOUT, "aborted (soc_abort or the soc_set_timeout deadline)");
+            const int n_items = (int)items.size();
+            CK(cudaMemsetAsync(ctx->b_stats.p, 0, sizeof(int64_t) * 4 * n_items, s), "zero stats");
+            soc_status r = soc_simulate_frequency_batch_ex(ctx, items.data(), n_items, ctx->b_tally.p, self,
+                                                           ctx->b_stats.p, nullptr, stream);
+            if (r) return r;
+            CK(cudaMemcpyAsync(hstats.data(), ctx->b_stats.p, sizeof(int64_t) * 4 * n_items, cudaMemcpyDeviceToHost, s),
+               "stats");
+            CK(cudaStreamSynchronize(s), "sync");
+            for (int i = 0; i < n_items; ++i) {
+                capped[item_cloud[i]] += hstats[4 * i + 1];
+                steps[item_cloud[i]] += hstats[4 * i + 2];
+            }
+            if (aborted()) return fail(ctx, SOC_ERR_TIMEOUT, "aborted (soc_abort or the soc_set_timeout deadline)");
+            return SOC_OK;
+        };
+        const soc_status run_st = [&]() -> soc_status {
+            soc_status st;
+            // iteration 0: background and point sources of every cloud in one launch
+            if (!prm->reuse_constant) {
+                items.clear(); item_cloud.clear();
+                int64_t off = 0;
+                for (int k = 0; k < n_clouds; ++k) {
+                    const CloudHost &cl = *ctx->clouds[cloud_ids[k]];
+                    base[k] = off;
+                    for (int c = 0; c < 2; ++c) {
+                        const uint64_t npk = c == 0 ? prm->n_background : prm->n_point;
+                        if (!npk) continue;
+                        for (int f = 0; f < nf; ++f) {
+                            soc_batch_item it;
+                            memset(&it, 0, sizeof it);
+                            it.cloud = cloud_ids[k]; it.freq = f;
+                            it.source = c == 0 ? SOC_SRC_BACKGROUND : SOC_SRC_POINT;
+                            it.n_packages = npk; it.w0 = SOC_W_UNIT; it.tally_offset = off; it.n_per_cell = 1;
+                            items.push_back(it);
+                            item_cloud.push_back(k);
+                            off += cl.n_cells;
+                        }
+                    }
+                }
+                if (!items.empty()) {
+                    CK(cudaMemsetAsync(ctx->b_tally.p, 0, sizeof(int64_t) * off, s), "zero counters");
+                    if ((st = launch(nullptr))) return st;
+                }
+                std::vector<double> e(nf);
+                for (int k = 0; k < n_clouds; ++k) {
+                    CloudHost &cl = *ctx->clouds[cloud_ids[k]];
+                    CK(cudaMemsetAsync(cl.A_const.p, 0, sizeof(double) * cl.n_cells, s), "zero A");
+                    int64_t o = base[k];
+                    for (int c = 0; c < 2; ++c) {
+                        const uint64_t npk = c == 0 ? prm->n_background : prm->n_point;
+                        if (!npk) continue;
+                        const int source = c == 0 ? SOC_SRC_BACKGROUND : SOC_SRC_POINT;
+                        if ((st = soc_package_energy(ctx, cloud_ids[k], source, npk, e.data()))) return st;
+                        CK(cudaMemcpyAsync(cl.e_unit.p, e.data(), 8 * nf, cudaMemcpyHostToDevice, s), "copy e_unit");
+                        if ((st = soc_absorbed_power(ctx, cloud_ids[k], ctx->b_tally.p + o, cl.n_cells, cl.e_unit.p,
+                                                     cl.A_const.p, cl.A_const.p, stream)))
+                            return st;
+                        o += (int64_t)nf * cl.n_cells;
+                    }
+                    cl.has_const = true;
+                }
+            }
+            // start temperatures
+            for (int k = 0; k < n_clouds; ++k) {
+                CloudHost &cl = *ctx->clouds[cloud_ids[k]];
+                const float *seed = d_T_seed ? d_T_seed[k] : nullptr;
+                if (seed) {
+                    CK(cudaMemcpyAsync(d_T_out[k], seed, sizeof(float) * cl.n_cells, cudaMemcpyDeviceToDevice, s),
+                       "copy seed");
+                } else if ((st = soc_update_temperature(ctx, cloud_ids[k], cl.A_const.p, d_T_out[k], nullptr, stream))) {
+                    return st;
+                }
+            }
+            // dust iterations: every unconverged cloud's re-emission in one launch
+            for (int it_k = 1; it_k <= prm->max_iter; ++it_k) {
+                items.clear(); item_cloud.clear();
+                int64_t off = 0;
+                std::vector<int> active;
+                for (int k = 0; k < n_clouds; ++k) {
+                    if (conv[k]) continue;
+                    CloudHost &cl = *ctx->clouds[cloud_ids[k]];
+                    if ((st = soc_dust_emission(ctx, cloud_ids[k], d_T_out[k], 0, nf, prm->n_per_cell, cl.dust_w.p,
+                                                cl.e_unit.p, stream)))
+                        return st;
+                    base[k] = off;
+                    for (int f = 0; f < nf; ++f) {
+                        soc_batch_item it;
+                        memset(&it, 0, sizeof it);
+                        it.cloud = cloud_ids[k]; it.freq = f; it.source = SOC_SRC_DUST;
+                        it.iteration = 1;      // frozen dust random numbers, as soc_iterate
+                        it.n_packages = (uint64_t)cl.n_leaf * prm->n_per_cell; it.w0 = SOC_W_UNIT;
+                        it.tally_offset = off; it.d_dust_w = cl.dust_w.p + (size_t)f * cl.n_leaf;
+                        it.n_per_cell = prm->n_per_cell;
+                        items.push_back(it);
+                        item_cloud.push_back(k);
+                        off += cl.n_cells;
+                    }
+                    active.push_back(k);
+                }
+                if (active.empty()) break;
+                CK(cudaMemsetAsync(ctx->b_tally.p, 0, sizeof(int64_t) * off, s), "zero counters");
+                if (ali) CK(cudaMemsetAsync(ctx->b_self.p, 0, sizeof(int64_t) * off, s), "zero self counters");
+                if ((st = launch(ali ? ctx->b_self.p : nullptr))) return st;
+                for (int k : active) {
+                    CloudHost &cl = *ctx->clouds[cloud_ids[k]];
+                    if ((st = soc_absorbed_power(ctx, cloud_ids[k], ctx->b_tally.p + base[k], cl.n_cells, cl.e_unit.p,
+                                                 cl.A_const.p, cl.A.p, stream)))
+                        return st;
+                    if (ali) {
+                        if ((st = soc_absorbed_power(ctx, cloud_ids[k], ctx->b_self.p + base[k], cl.n_cells,
+                                                     cl.e_unit.p, nullptr, cl.A_self.p, stream)))
+                            return st;
+                        if ((st = soc_update_temperature_ali(ctx, cloud_ids[k], cl.A.p, cl.A_self.p, d_T_out[k],
+                                                             ctx->b_maxdT.p + k, stream)))
+                            return st;
+                    } else if ((st = soc_update_temperature(ctx, cloud_ids[k], cl.A.p, d_T_out[k], ctx->b_maxdT.p + k,
+                                                            stream))) {
+                        return st;
+                    }
+                }
+                CK(cudaMemcpyAsync(hdT.data(), ctx->b_maxdT.p, sizeof(double) * n_clouds, cudaMemcpyDeviceToHost, s),
+                   "read max dT");
+                CK(cudaStreamSynchronize(s), "sync");
+                for (int k : active) {
+                    if (dT_history) dT_history[(size_t)k * prm->max_iter + (it_k - 1)] = hdT[k];
+                    it_done[k] = it_k;
+                    if (hdT[k] < prm->dT_tol) conv[k] = 1;
+                }
+            }
+            return SOC_OK;
+        }();
+        int64_t capped_all = 0;
+        for (int k = 0; k < n_clouds; ++k) {
+            capped_all += capped[k];
+            if (res) {
+                res[k].iterations = it_done[k];
+                res[k].converged = conv[k];
+                res[k].final_max_dT = it_done[k] ? hdT[k] : 0.0;
+                res[k].steps = steps[k];
+                res[k].capped = capped[k];
+            }
+        }
+        if (run_st != SOC_OK) return run_st;
+        return capped_all ? fail(ctx, SOC_ERR_STEP_LIMIT, "%lld packages hit the step cap", (long long)capped_all)
+                          : SOC_OK;
     });
 }
 

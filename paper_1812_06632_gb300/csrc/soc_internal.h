@@ -138,7 +138,7 @@ cudaError_t launch_dust_emission(const DevCloud *dcl, int64_t n_leaf, const Temp
 // (soc_nn.cu).  norm = {lt_mean, lt_std, lr_mean, lr_std}.
 cudaError_t launch_seed_features(const float *T1, const float *rho, int64_t n, const double norm[4], float *x,
                                  cudaStream_t s);
-cudaError_t launch_seed_transform(const float *T1, const float *pred, int64_t n, double y_mean, double y_std,
+cudaError_t launch_seed_transform(const float *T1, const float *pred, int64_t n, const soc_seed_map &map,
                                   float *T_seed, cudaStream_t s);
 
 }  // namespace soc

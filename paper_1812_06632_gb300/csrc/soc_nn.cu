@@ -689,14 +689,22 @@ __global__ void seed_features_kernel(const float *T1, const float *rho, long lon
     }
 }
 
-// T_seed = clamp(T1 exp(pred y_std + y_mean), 2.7, 3000): the network
-// predicts the normalised ln T - ln T1.
-__global__ void seed_transform_kernel(const float *T1, const float *pred, long long n, double y_mean, double y_std,
+// T_seed = clamp(T1 exp(y), 2.7, 3000) with y = shrink (pred y_std + y_mean)
+// (the network predicts the normalised ln T - ln T1), bounded by the
+// envelope of its bin of ln T1 when the map has one.
+__global__ void seed_transform_kernel(const float *T1, const float *pred, long long n, const soc_seed_map m,
                                       float *T_seed)
 {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        const double t = (double)T1[c] * exp((double)pred[c] * y_std + y_mean);
-        T_seed[c] = (float)fmin(fmax(t, kTMin), kTMax);
+        const double t1 = (double)T1[c];
+        double y = m.shrink * ((double)pred[c] * m.y_std + m.y_mean);
+        if (m.n_bins > 0) {
+            const double lt = log(fmin(fmax(t1, kTMin), kTMax));
+            int b = (int)floor((lt - m.lnT1_lo) / (m.lnT1_hi - m.lnT1_lo) * m.n_bins);
+            b = b < 0 ? 0 : (b >= m.n_bins ? m.n_bins - 1 : b);
+            y = fmin(fmax(y, m.y_lo[b]), m.y_hi[b]);
+        }
+        T_seed[c] = (float)fmin(fmax(t1 * exp(y), kTMin), kTMax);
     }
 }
 
@@ -939,10 +947,10 @@ cudaError_t launch_seed_features(const float *T1, const float *rho, int64_t n, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_seed_transform(const float *T1, const float *pred, int64_t n, double y_mean, double y_std,
+cudaError_t launch_seed_transform(const float *T1, const float *pred, int64_t n, const soc_seed_map &map,
                                   float *T_seed, cudaStream_t s)
 {
-    nn::seed_transform_kernel<<<nn::grid_1d(n), 256, 0, s>>>(T1, pred, n, y_mean, y_std, T_seed);
+    nn::seed_transform_kernel<<<nn::grid_1d(n), 256, 0, s>>>(T1, pred, n, map, T_seed);
     return cudaGetLastError();
 }
 
@@ -1255,7 +1263,10 @@ soc_status soc_unet_adam(int net_id, float lr, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     n->adam_t += 1;
-    const float c1 = 1.f - powf(b1, (float)n->adam_t), c2 = 1.f - powf(b2, (float)n->adam_t);
+    // bias corrections 1 - beta^t in double (in FP32, 1 - 0.999^t cancels:
+    // 7e-6 relative error at t = 2), then rounded once
+    const float c1 = (float)(1.0 - std::pow((double)b1, (double)n->adam_t));
+    const float c2 = (float)(1.0 - std::pow((double)b2, (double)n->adam_t));
     for (int l = 0; l < kLayers; ++l) {
         adam_kernel<<<grid_1d((long long)n->w32[l].n), 256, 0, s>>>(n->w32[l].p, n->mw[l].p, n->vw[l].p, n->gw[l].p,
                                                                    (long long)n->w32[l].n, lr, b1, b2, eps, c1, c2,
@@ -1340,12 +1351,21 @@ soc_status soc_nn_conv3d_wgrad(const void *gy, const void *x, int N, int D, int 
     return SOC_OK;
 }
 
+soc_status soc_nn_seed_features(const float *d_T1, const float *d_rho, int64_t n, const double *norm, float *d_x,
+                                void *stream)
+{
+    if (!d_T1 || !d_rho || !norm || !d_x || n < 1 || !(norm[1] > 0.0) || !(norm[3] > 0.0)) return SOC_ERR_ARG;
+    NNCK(soc::launch_seed_features(d_T1, d_rho, n, norm, d_x, (cudaStream_t)stream));
+    return SOC_OK;
+}
+
 soc_status soc_nn_adam(float *d_w, float *d_m, float *d_v, const float *d_g, int64_t n, float lr, int32_t t,
                        void *d_w_bf16, void *stream)
 {
     if (!d_w || !d_m || !d_v || !d_g || n < 1 || t < 1 || !(lr >= 0.f)) return SOC_ERR_ARG;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    const float c1 = (float)(1.0 - std::pow((double)b1, (double)t));
+    const float c2 = (float)(1.0 - std::pow((double)b2, (double)t));
     adam_kernel<<<grid_1d(n), 256, 0, (cudaStream_t)stream>>>(d_w, d_m, d_v, d_g, n, lr, b1, b2, eps, c1, c2,
                                                               (bf16 *)d_w_bf16);
     NNCK(cudaGetLastError());

@@ -327,24 +327,38 @@ def config_c5(n_clouds: int = 64, n_freq: int = 32, seed: int = 5, sizes=None,
                     seed=1, extra=dict(sizes=np.asarray(sizes), taus=taus))
 
 
-def config_c4(seed: int, side: int = 64, n_freq: int = 64, side_pc: float = 0.2, n_bg: int = 200_000,
-              n_ps: int = 200_000) -> Workload:
-    """One cloud of the learned-seed training set: side^3 lognormal GRF
-    (field seed = seed, sigma_lnrho ~ U(1, 2)), mean-density centre-to-face
-    tau(1 um) ~ logU(1, 50), 1-3 blackbody point sources (1e4 K,
-    L ~ logU(1e36, 1e37) erg/s) at random positions in the inner half, plus the
-    3-blackbody background.  All draws from numpy.random.default_rng(seed)."""
-    rng = np.random.default_rng(10_000 + seed)
-    sigma = float(rng.uniform(1.0, 2.0))
-    tau = float(np.exp(rng.uniform(np.log(1.0), np.log(50.0))))
-    k = int(rng.integers(1, 4))
-    pos = rng.uniform(0.25, 0.75, size=(k, 3)) * side
-    Lb = np.exp(rng.uniform(np.log(1e36), np.log(1e37), size=k))
-    rho = lognormal_density(side, seed, sigma, -3.5).astype(np.float32)
-    ell = side_pc * PC_CM / side
-    cl = regular(rho, ell=ell)
+def config_c4(seeds, side: int = 64, n_freq: int = 64, side_pc: float = 0.15, n_bg: int = 200_000,
+              n_ps: int = 200_000, tau_range=(1000.0, 5000.0), L_range=(1e38, 5e38)) -> Workload:
+    """Clouds of the learned-seed set, one per seed, in one workload that
+    shares a single opacity table: hot-core clouds after the setup of the
+    paper's convergence test (Sect. 3.3: a cloud shrunk and made denser, with
+    an internal source heating the nearest cells to hundreds of K, so that
+    dust re-emission matters over a large volume and the temperatures
+    converge only after many iterations).  Per seed, all draws from
+    numpy.random.default_rng(10_000 + seed): side^3 lognormal GRF (field seed
+    = seed, sigma_lnrho ~ U(1, 2), P(k) ~ k^-3.5); mean-density centre-to-face
+    tau_ext(1 um) ~ logU(tau_range), set through the density scale (the
+    opacity is normalised so that unit density gives tau = 1); 1-2 blackbody
+    point sources (1e4 K) with total luminosity ~ logU(L_range) erg/s,
+    shared equally, at uniform positions in the inner 30 % of the box; the
+    3-blackbody background; side_pc parsecs per side."""
+    seeds = [int(s) for s in np.atleast_1d(seeds)]
     nu = frequency_grid(n_freq)
-    dust = power_law_dust(nu, tau / ((side / 2) * ell))
-    L = np.stack([stellar_luminosity(nu, 1e4, l) for l in Lb])
-    return Workload(f"c4_lognormal{side}_seed{seed}", [cl], dust, [diluted_blackbodies(nu)], [pos], [L],
-                    [n_bg], [n_ps], seed=1, extra=dict(sigma=sigma, tau=tau, n_sources=k))
+    ell = side_pc * PC_CM / side
+    dust = power_law_dust(nu, 1.0 / ((side / 2) * ell))
+    clouds, pos, Ls, extra = [], [], [], []
+    for seed in seeds:
+        rng = np.random.default_rng(10_000 + seed)
+        sigma = float(rng.uniform(1.0, 2.0))
+        tau = float(np.exp(rng.uniform(np.log(tau_range[0]), np.log(tau_range[1]))))
+        k = int(rng.integers(1, 3))
+        p = rng.uniform(0.35, 0.65, size=(k, 3)) * side
+        L_tot = float(np.exp(rng.uniform(np.log(L_range[0]), np.log(L_range[1]))))
+        rho = lognormal_density(side, seed, sigma, -3.5)
+        clouds.append(regular((rho * tau).astype(np.float32), ell=ell))
+        pos.append(p)
+        Ls.append(np.stack([stellar_luminosity(nu, 1e4, L_tot / k) for _ in range(k)]))
+        extra.append(dict(seed=seed, sigma=sigma, tau=tau, n_sources=k, L=L_tot))
+    bg = diluted_blackbodies(nu)
+    return Workload(f"c4_hotcore{side}_{len(seeds)}clouds", clouds, dust, [bg] * len(seeds), pos, Ls,
+                    [n_bg] * len(seeds), [n_ps] * len(seeds), seed=1, extra=dict(clouds=extra))

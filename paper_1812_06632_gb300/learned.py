@@ -1,17 +1,36 @@
-"""Learned temperature seed: data from plain Monte Carlo iterations, training
-on the library's own network kernels, and seeded versus plain convergence.
+"""Learned temperature seed, in batched form: training data from the plain
+Monte Carlo iteration of many clouds at once, training on the library's own
+network kernels, and seeded against plain convergence of a batch of
+held-out clouds.  Every step of a seeded run is a library call on the GPU.
 
-For every cloud the Monte Carlo path gives T1 (temperatures after iteration 0:
-background and point sources only) and the converged T (dust re-emission
-iterated with frozen random numbers until max |dT| < tol).  The network maps
-(log T1, log rho), normalised, to log T - log T1.  A seeded run replaces the
-start T1 by T1 exp(prediction); the Monte Carlo iterations then continue to
-the same fixed point, so they remain both the fallback and the measure of the
-seed's error.
+Clouds (inputs.config_c4): hot-core clouds after the paper's convergence
+test (Sect. 3.3), where dust re-emission matters over a large volume and the
+plain iteration needs tens of dust iterations.  For every cloud the Monte
+Carlo path gives T1 (temperatures after iteration 0: background and point
+sources only) and the converged T (dust re-emission iterated with frozen
+random numbers until max |dT| < tol).  The network maps the features
+(normalised ln T1, ln rho; soc_seed_features) to the normalised
+y = ln T - ln T1.  A seeded run starts its dust iterations from T1 exp(y)
+(soc_seed_transform) instead of T1, y the de-normalised prediction; the
+iterations then continue to the same fixed point, so they are both the
+fallback and the measure of the seed's error.
+
+Two bounds keep the seed from overshooting where the emission (~T^6) makes
+an overshoot costly: y >= 0 holds exactly (dust re-emission only adds
+absorbed power, so the converged T is never below T1), and y stays inside the
+envelope of the training data per bin of ln T1 (the hottest cells next to the
+sources are rare and far outside the network's typical inputs).  A shrink
+factor on y, chosen on the validation clouds by the dust iterations it
+needs, moves the seed towards T1, from below.
+
+The 200 cloud seeds 1000..1199 split 160 / 20 / 20 into training,
+validation (early stopping: the weights of the epoch with the lowest
+validation loss are kept; the shrink factor) and test clouds.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import time
@@ -21,68 +40,104 @@ import numpy as np
 from . import inputs as I
 
 T_MIN, T_MAX = 2.7, 3000.0
+TRAIN = list(range(1000, 1160))
+VAL = list(range(1160, 1180))
+TEST = list(range(1180, 1200))
+HERE = os.path.dirname(os.path.abspath(__file__))
+WEIGHTS = os.path.join(HERE, "data", "unet_c4_hotcore.npz")
+PACKAGES = dict(n_background=200_000, n_point=200_000)
 
 
-def _ctx_for(w, soc):
-    ctx = soc.Context(0, w.seed)
+def context(w, seed=None):
+    """One library context holding every cloud of the workload."""
+    from . import soc
+    ctx = soc.Context(0, w.seed if seed is None else seed)
     ctx.dust_upload(w.dust.nu, w.dust.kabs, w.dust.ksca, w.dust.g)
-    cid = ctx.grid_upload(w.clouds[0])
-    ctx.sources_upload(cid, w.bg_I[0], w.ps_pos[0], w.ps_L[0])
-    return ctx, cid
+    ids = []
+    for ci, cl in enumerate(w.clouds):
+        cid = ctx.grid_upload(cl)
+        ctx.sources_upload(cid, w.bg_I[ci], w.ps_pos[ci], w.ps_L[ci])
+        ids.append(cid)
+    return ctx, ids
 
 
-def iteration0(ctx, cid, w, T):
-    """Constant sources once: T <- T1 (kept in the context for reuse)."""
-    return ctx.iterate(cid, T, n_background=w.n_bg[0], n_point=w.n_ps[0], max_iter=0)
+def empty_fields(w):
+    import torch
+    return [torch.empty(cl.n_cells, dtype=torch.float32, device="cuda") for cl in w.clouds]
 
 
-def iterate_from(ctx, cid, T_start, T_out, max_iter, tol):
-    """Dust iterations from T_start, reusing iteration 0's absorption."""
-    return ctx.iterate(cid, T_out, n_per_cell=1, max_iter=max_iter, dT_tol=tol, T_seed=T_start, reuse_constant=True)
+def constant_iteration(ctx, ids, T1s):
+    """Iteration 0 of every cloud (background and point sources, one tracer
+    launch): T1s <- T1, the constant-source absorption kept for reuse."""
+    rows, _ = ctx.iterate_batch(ids, T1s, max_iter=0, **PACKAGES)
+    return rows
 
 
-def simulate_cloud(w, max_iter=60, tol=0.1):
-    """(T1, T_converged, plain-run info) for one cloud, on the GPU."""
+def dust_iterations(ctx, ids, T_outs, seeds=None, max_iter=300, tol=0.1):
+    """Dust iterations of every cloud to max |dT| < tol, reusing iteration 0
+    (seeds: start temperatures, or None for T1)."""
+    rows, _ = ctx.iterate_batch(ids, T_outs, n_per_cell=1, max_iter=max_iter, dT_tol=tol, T_seeds=seeds,
+                                reuse_constant=True)
+    return rows
+
+
+def make_dataset(seeds, side=64, chunk=20, max_iter=300, tol=0.1, log=print):
+    """Plain Monte Carlo T1 and converged T of every cloud, `chunk` clouds per
+    batched run.  Returns (T1, T, rho) as device tensors [n, side^3] and one
+    info row per cloud."""
+    import torch
+    T1s, Ts, rhos, info = [], [], [], []
+    for c0 in range(0, len(seeds), chunk):
+        w = I.config_c4(seeds[c0:c0 + chunk], side=side)
+        ctx, ids = context(w)
+        T1 = empty_fields(w)
+        T = empty_fields(w)
+        t0 = time.perf_counter()
+        constant_iteration(ctx, ids, T1)
+        rows = dust_iterations(ctx, ids, T, max_iter=max_iter, tol=tol)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        for k, r in enumerate(rows):
+            info.append(dict(**w.extra["clouds"][k], iterations=r["iterations"], converged=r["converged"]))
+        T1s += T1
+        Ts += T
+        rhos += [torch.from_numpy(cl.rho).cuda() for cl in w.clouds]
+        log(f"clouds {seeds[c0]}..{seeds[min(c0 + chunk, len(seeds)) - 1]}: {dt:.1f} s, iterations "
+            f"{[r['iterations'] for r in rows]}")
+        ctx.close()
+    return torch.stack(T1s), torch.stack(Ts), torch.stack(rhos), info
+
+
+def norm_stats(T1, T, rho):
+    """Means and widths of the network's inputs and target over a data set."""
+    import torch
+    lt = torch.log(T1.double().clamp(T_MIN, T_MAX))
+    lr = torch.log(rho.double().clamp_min(1e-30))
+    y = torch.log(T.double().clamp(T_MIN, T_MAX)) - lt
+    return dict(lt_mean=lt.mean().item(), lt_std=lt.std().item() + 1e-12, lr_mean=lr.mean().item(),
+                lr_std=lr.std().item() + 1e-12, y_mean=y.mean().item(), y_std=y.std().item() + 1e-12)
+
+
+def _norm4(norm):
+    return [norm["lt_mean"], norm["lt_std"], norm["lr_mean"], norm["lr_std"]]
+
+
+def features(T1, rho, norm, side):
+    """Network inputs [n, side, side, side, 2] by the library's feature kernel."""
     import torch
     from . import soc
-    ctx, cid = _ctx_for(w, soc)
-    n = w.clouds[0].n_cells
-    T1 = torch.empty(n, dtype=torch.float32, device="cuda")
-    iteration0(ctx, cid, w, T1)
-    T = torch.empty_like(T1)
-    r = iterate_from(ctx, cid, T1, T, max_iter, tol)
-    torch.cuda.synchronize()
-    out = (T1.cpu().numpy(), T.cpu().numpy(), r)
-    ctx.close()
-    return out
+    x = torch.empty((T1.shape[0], side, side, side, 2), dtype=torch.float32, device="cuda")
+    for k in range(T1.shape[0]):
+        soc.seed_features(T1[k].contiguous(), rho[k].contiguous(), _norm4(norm), x[k])
+    return x
 
 
-def features(T1, rho, side, stats):
-    """Network input (side^3 x 2, normalised log T1 and log rho)."""
-    lt = (np.log(np.clip(T1, T_MIN, T_MAX)) - stats["lt_mean"]) / stats["lt_std"]
-    lr = (np.log(np.maximum(rho, 1e-30)) - stats["lr_mean"]) / stats["lr_std"]
-    return np.stack([lt, lr], axis=-1).reshape(side, side, side, 2).astype(np.float32)
-
-
-def make_dataset(seeds, side=64, max_iter=60, tol=0.1, log=print):
-    """Plain-MC inputs and targets for the given cloud seeds."""
-    T1s, Ts, rhos, info = [], [], [], []
-    for s in seeds:
-        w = I.config_c4(int(s), side=side)
-        t0 = time.perf_counter()
-        T1, T, r = simulate_cloud(w, max_iter, tol)
-        T1s.append(T1); Ts.append(T); rhos.append(w.clouds[0].rho.copy())
-        info.append(dict(seed=int(s), iterations=r["iterations"], converged=r["converged"],
-                         seconds=time.perf_counter() - t0, **w.extra))
-        log(f"cloud {s}: {r['iterations']} iterations, converged={r['converged']}, max T {T.max():.1f} K")
-    return np.array(T1s), np.array(Ts), np.array(rhos), info
-
-
-def norm_stats(T1, rho):
-    lt = np.log(np.clip(T1, T_MIN, T_MAX))
-    lr = np.log(np.maximum(rho, 1e-30))
-    return dict(lt_mean=float(lt.mean()), lt_std=float(lt.std() + 1e-12),
-                lr_mean=float(lr.mean()), lr_std=float(lr.std() + 1e-12))
+def targets(T1, T, norm, side):
+    """Training targets: normalised ln T - ln T1 (the inverse of the seeding
+    transform), [n, side, side, side]."""
+    import torch
+    y = torch.log(T.double().clamp(T_MIN, T_MAX)) - torch.log(T1.double().clamp(T_MIN, T_MAX))
+    return ((y - norm["y_mean"]) / norm["y_std"]).float().reshape(-1, side, side, side).contiguous()
 
 
 def init_params(seed=0):
@@ -100,174 +155,296 @@ def init_params(seed=0):
     return np.concatenate(out).astype(np.float32)
 
 
-def train(X, Y, side, epochs=30, batch=4, lr=1e-3, seed=0, log=print):
-    """Adam on MSE of the normalised residual (Y is already normalised, so a
-    constant predictor scores 1); the learning rate decays linearly to 10 %.
-    Returns the trained net and the loss history."""
+def _mse(net, X, Y, batch):
+    """Mean squared error of the network over a data set (forward only)."""
+    import torch
+    side = X.shape[1]
+    pred = torch.empty((batch, side, side, side), dtype=torch.float32, device="cuda")
+    tot, n = 0.0, 0
+    for b0 in range(0, X.shape[0] - batch + 1, batch):
+        net.forward(X[b0:b0 + batch].contiguous(), pred)
+        tot += float(((pred - Y[b0:b0 + batch]) ** 2).double().mean().item()) * batch
+        n += batch
+    return tot / max(n, 1)
+
+
+def train(X, Y, Xv, Yv, epochs=80, patience=12, batch=4, lr=2e-3, seed=0, log=print):
+    """Adam on the MSE of the normalised target (a constant predictor scores
+    1), learning rate decaying linearly to 10 %; after every epoch the
+    validation loss decides which weights are kept, and training stops after
+    `patience` epochs without improvement.  Returns (best parameters, train
+    loss history, validation loss history, best epoch)."""
     import torch
     from . import soc
+    side = X.shape[1]
     net = soc.UNet(batch, side)
     net.set_params(init_params(seed))
     rng = np.random.default_rng(seed)
     n = X.shape[0]
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
-    hist = []
-    Xd = torch.from_numpy(X).cuda()
-    Yd = torch.from_numpy(Y).cuda()
+    hist, vhist = [], []
+    best, best_ep = None, -1
     for ep in range(epochs):
-        perm = rng.permutation(n)
+        perm = torch.from_numpy(rng.permutation(n)).cuda()
         tot = 0.0
         for b0 in range(0, n - batch + 1, batch):
-            idx = torch.from_numpy(perm[b0:b0 + batch]).cuda()
-            xb = Xd.index_select(0, idx).contiguous()
-            yb = Yd.index_select(0, idx).contiguous()
-            net.backward(xb, yb, loss=loss)
+            idx = perm[b0:b0 + batch]
+            net.backward(X.index_select(0, idx).contiguous(), Y.index_select(0, idx).contiguous(), loss=loss)
             net.adam(lr * (1.0 - 0.9 * ep / max(1, epochs - 1)))
             tot += loss.item()
         hist.append(tot / max(1, n // batch))
-        log(f"epoch {ep}: loss {hist[-1]:.5f}")
-    return net, hist
+        vhist.append(_mse(net, Xv, Yv, batch))
+        if best is None or vhist[-1] < min(vhist[:-1]):
+            best, best_ep = net.get_params(), ep
+        log(f"epoch {ep}: train {hist[-1]:.4f} val {vhist[-1]:.4f}")
+        if ep - best_ep >= patience:
+            break
+    net.close()
+    return best, hist, vhist, best_ep
 
 
-def predict_seed(net, T1, rho, side, stats):
-    """T1 exp(prediction), clamped to the solver's range."""
+ENV_BINS = 64
+
+
+def envelope(T1, T, n_bins=ENV_BINS):
+    """Per-bin range of y = ln T - ln T1 over a data set, bins equal in
+    ln T1 over [ln 2.7, ln 3000); empty bins take the nearest filled bin's
+    range.  Returns (lnT1_lo, lnT1_hi, y_lo[n], y_hi[n]) with y_lo >= 0."""
     import torch
-    x = torch.from_numpy(np.repeat(features(T1, rho, side, stats)[None], net.batch, axis=0)).cuda()
-    pred = torch.empty((net.batch, side, side, side), dtype=torch.float32, device="cuda")
-    net.forward(x, pred)
-    p = pred[0].reshape(-1) * stats["y_std"] + stats["y_mean"]
-    return torch.clamp(torch.from_numpy(T1).cuda() * torch.exp(p), T_MIN, T_MAX).contiguous()
+    lo, hi = float(np.log(T_MIN)), float(np.log(T_MAX))
+    lt = torch.log(T1.double().clamp(T_MIN, T_MAX)).reshape(-1)
+    y = (torch.log(T.double().clamp(T_MIN, T_MAX)).reshape(-1) - lt)
+    b = torch.clamp(torch.floor((lt - lo) / (hi - lo) * n_bins).long(), 0, n_bins - 1)
+    ymin = torch.full((n_bins,), float("inf"), dtype=torch.float64, device=y.device).scatter_reduce(
+        0, b, y, reduce="amin")
+    ymax = torch.full((n_bins,), float("-inf"), dtype=torch.float64, device=y.device).scatter_reduce(
+        0, b, y, reduce="amax")
+    ymin, ymax = ymin.cpu().numpy(), ymax.cpu().numpy()
+    filled = np.flatnonzero(np.isfinite(ymin))
+    for k in range(n_bins):
+        if not np.isfinite(ymin[k]):
+            j = filled[np.argmin(np.abs(filled - k))]
+            ymin[k], ymax[k] = ymin[j], ymax[j]
+    return lo, hi, np.maximum(ymin, 0.0), np.maximum(ymax, 0.0)
 
 
-def compare(net, seeds, side, stats, max_iter=60, tol=0.1, log=print):
-    """Wall time to max |dT| < tol for plain and learned-seeded iteration on
-    the given (held-out) clouds; both start with the same iteration 0."""
-    import torch
+def seed_map(norm, shrink=1.0, env=None):
     from . import soc
-    rows = []
-    # one untimed forward: loads the network's kernels before the timed runs
-    w0 = I.config_c4(int(seeds[0]), side=side)
-    predict_seed(net, np.full(w0.clouds[0].n_cells, 10.0, np.float32), w0.clouds[0].rho, side, stats)
+    return soc.seed_map(norm["y_mean"], norm["y_std"], shrink, env)
+
+
+def save_weights(path, params, norm, meta, shrink=1.0, env=None):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    e = dict(shrink=shrink, env=None if env is None else [env[0], env[1], list(map(float, env[2])),
+                                                          list(map(float, env[3]))])
+    np.savez_compressed(path, params=params.astype(np.float32), norm=json.dumps(norm), meta=json.dumps(meta),
+                        seedmap=json.dumps(e))
+
+
+def load_weights(path=WEIGHTS):
+    """(parameters, normalisation with the seed map's shrink and envelope,
+    metadata, sha256 of the file)."""
+    with open(path, "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()
+    z = np.load(path)
+    norm = json.loads(str(z["norm"]))
+    if "seedmap" in z.files:
+        e = json.loads(str(z["seedmap"]))
+        norm["shrink"] = e["shrink"]
+        norm["env"] = e["env"]
+    return z["params"], norm, json.loads(str(z["meta"])), digest
+
+
+class Seeder:
+    """The trained network ready for a batch of n clouds of one side (its
+    buffers are allocated once, like loading a model)."""
+
+    def __init__(self, params, norm, n, side):
+        import torch
+        from . import soc
+        self.norm, self.side = norm, side
+        self.net = soc.UNet(n, side)
+        self.net.set_params(params)
+        self.x = torch.empty((n, side, side, side, 2), dtype=torch.float32, device="cuda")
+        self.pred = torch.empty((n, side, side, side), dtype=torch.float32, device="cuda")
+
+    def seeds(self, ctx, ids, T1s, shrink=None):
+        """T_seed of every cloud: features, one batched network forward and
+        the seeding transform (shrink and envelope of the map), all on the
+        GPU.  shrink overrides the stored factor (validation sweeps)."""
+        import torch
+        out = []
+        for k, cid in enumerate(ids):
+            ctx.seed_features(cid, T1s[k], _norm4(self.norm), self.x[k])
+        self.net.forward(self.x, self.pred)
+        m = seed_map(self.norm, self.norm.get("shrink", 1.0) if shrink is None else shrink, self.norm.get("env"))
+        for k, cid in enumerate(ids):
+            t = torch.empty_like(T1s[k])
+            ctx.seed_transform(cid, T1s[k], self.pred[k].reshape(-1), m, t)
+            out.append(t)
+        return out
+
+    def close(self):
+        self.net.close()
+
+
+def compare(params, norm, seeds=TEST, side=64, max_iter=300, tol=0.1, log=print):
+    """Wall time to max |dT| < tol of the batch of clouds `seeds`: iteration 0
+    (shared), then the dust iterations plain and learned-seeded, each as one
+    batched run (one tracer launch per iteration for every unconverged
+    cloud).  The seeded time includes the features, the network forward and
+    the transform."""
+    import torch
+    w = I.config_c4(seeds, side=side)
+    ctx, ids = context(w)
+    seeder = Seeder(params, norm, len(ids), side)
+    # warm-up (kernel loading) on a throw-away cloud of the same recipe
+    w0 = I.config_c4([seeds[0]], side=side)
+    c0, i0 = context(w0)
+    T0 = empty_fields(w0)
+    constant_iteration(c0, i0, T0)
+    dust_iterations(c0, i0, empty_fields(w0), max_iter=1)
+    Seeder(params, norm, 1, side).seeds(c0, i0, T0)
+    c0.close()
     torch.cuda.synchronize()
-    for s in seeds:
-        w = I.config_c4(int(s), side=side)
-        res = {}
-        for mode in ("plain", "learned"):
-            ctx, cid = _ctx_for(w, soc)
-            n = w.clouds[0].n_cells
-            T1 = torch.empty(n, dtype=torch.float32, device="cuda")
-            T = torch.empty_like(T1)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            iteration0(ctx, cid, w, T1)
-            if mode == "learned":
-                seed_T = predict_seed(net, T1.cpu().numpy(), w.clouds[0].rho, side, stats)
-            else:
-                seed_T = T1
-            r = iterate_from(ctx, cid, seed_T, T, max_iter, tol)
-            torch.cuda.synchronize()
-            res[mode] = dict(seconds=time.perf_counter() - t0, iterations=r["iterations"],
-                             converged=r["converged"], T=T.cpu().numpy())
-            ctx.close()
-        d = float(np.abs(res["plain"]["T"] - res["learned"]["T"]).max())
-        rows.append(dict(seed=int(s), plain_s=res["plain"]["seconds"], learned_s=res["learned"]["seconds"],
-                         plain_iters=res["plain"]["iterations"], learned_iters=res["learned"]["iterations"],
-                         plain_converged=res["plain"]["converged"], learned_converged=res["learned"]["converged"],
-                         max_abs_T_difference=d))
-        log(json.dumps(rows[-1]))
-    return rows
 
-
-def seed_bound(seeds, side=64, max_iter=60, tol=0.1, other_seed=7, log=print):
-    """What any seed can gain here: dust iterations to max |dT| < tol from
-    (a) the run's own converged T (a perfect predictor), (b) the converged T
-    of an independent Monte Carlo realisation of the same cloud (context
-    seed `other_seed`: a prediction as good as the method's own answer but
-    without this run's frozen noise) and (c) T1 (the plain start)."""
-    import torch
-    from . import soc
-    rows = []
-    for s in seeds:
-        w = I.config_c4(int(s), side=side)
-        n = w.clouds[0].n_cells
-        runs = {}
-        for cseed in (w.seed, other_seed):
-            ctx = soc.Context(0, cseed)
-            ctx.dust_upload(w.dust.nu, w.dust.kabs, w.dust.ksca, w.dust.g)
-            cid = ctx.grid_upload(w.clouds[0])
-            ctx.sources_upload(cid, w.bg_I[0], w.ps_pos[0], w.ps_L[0])
-            T1 = torch.empty(n, dtype=torch.float32, device="cuda")
-            T = torch.empty_like(T1)
-            iteration0(ctx, cid, w, T1)
-            iterate_from(ctx, cid, T1, T, max_iter, tol)
-            runs[cseed] = (ctx, cid, T1, T)
-        ctx, cid, T1, T = runs[w.seed]
-        T_other = runs[other_seed][3]
-        row = dict(seed=int(s))
-        for name, start in (("own_converged", T), ("other_realisation", T_other), ("T1", T1)):
-            out = torch.empty_like(T1)
-            row[name + "_iters"] = iterate_from(ctx, cid, start.contiguous(), out, max_iter, tol)["iterations"]
-        d = (T_other - T).double()
-        row["realisations_max_abs_dT_K"] = float(d.abs().max().item())
-        row["realisations_rms_rel_dT"] = float(((T_other.double() / T.double() - 1) ** 2).mean().sqrt().item())
-        for c in runs.values():
-            c[0].close()
-        rows.append(row)
-        log(json.dumps(row))
-    return rows
-
-
-def run(side=64, n_train=160, n_test=20, epochs=60, max_iter=60, tol=0.1, lr=2e-3, log=print):
-    """The whole comparison: data from the plain Monte Carlo path (training
-    clouds), training, then plain against learned-seeded runs to max|dT| <
-    tol on the test clouds.  Returns the summary (times in seconds)."""
+    T1 = empty_fields(w)
     t0 = time.perf_counter()
-    train_seeds = np.arange(1000, 1000 + n_train)
-    test_seeds = np.arange(2000, 2000 + n_test)
-    T1, T, rho, info = make_dataset(train_seeds, side, max_iter, tol, log=log)
+    constant_iteration(ctx, ids, T1)
+    torch.cuda.synchronize()
+    t_const = time.perf_counter() - t0
+
+    T_plain = empty_fields(w)
+    t0 = time.perf_counter()
+    plain = dust_iterations(ctx, ids, T_plain, max_iter=max_iter, tol=tol)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+
+    T_learn = empty_fields(w)
+    t0 = time.perf_counter()
+    s = seeder.seeds(ctx, ids, T1)
+    learn = dust_iterations(ctx, ids, T_learn, seeds=s, max_iter=max_iter, tol=tol)
+    torch.cuda.synchronize()
+    t_learn = time.perf_counter() - t0
+
+    # seed quality: max |T_seed - T_converged| against the same for T1
+    seed_err = [float((s[k] - T_plain[k]).abs().max().item()) for k in range(len(ids))]
+    t1_err = [float((T1[k] - T_plain[k]).abs().max().item()) for k in range(len(ids))]
+    dmax = max(float((T_plain[k] - T_learn[k]).abs().max().item()) for k in range(len(ids)))
+    seeder.close()
+    ctx.close()
+    out = dict(n_clouds=len(ids), side=side, tol_K=tol, constant_s=t_const, plain_dust_s=t_plain,
+               learned_dust_s=t_learn, plain_s=t_const + t_plain, learned_s=t_const + t_learn,
+               plain_iterations=[r["iterations"] for r in plain], learned_iterations=[r["iterations"] for r in learn],
+               plain_converged=all(r["converged"] for r in plain), learned_converged=all(r["converged"] for r in learn),
+               plain_steps=int(sum(r["steps"] for r in plain)), learned_steps=int(sum(r["steps"] for r in learn)),
+               max_abs_T_difference_K=dmax, seed_max_err_K=seed_err, T1_max_err_K=t1_err)
+    log(json.dumps({k: v for k, v in out.items() if k not in ("seed_max_err_K", "T1_max_err_K")}))
+    return out
+
+
+SHRINKS = (0.5, 0.65, 0.8, 0.9, 1.0)
+
+
+def choose_shrink(params, norm, seeds=VAL, side=64, max_iter=300, tol=0.1, shrinks=SHRINKS, log=print):
+    """Dust iterations of the validation clouds for every shrink factor
+    (and plain); returns (the factor with the fewest in total, table)."""
+    w = I.config_c4(seeds, side=side)
+    ctx, ids = context(w)
+    seeder = Seeder(params, norm, len(ids), side)
+    T1 = empty_fields(w)
+    constant_iteration(ctx, ids, T1)
+    table = {"plain": sum(r["iterations"] for r in dust_iterations(ctx, ids, empty_fields(w), None, max_iter, tol))}
+    for a in shrinks:
+        s = seeder.seeds(ctx, ids, T1, shrink=a)
+        table[str(a)] = sum(r["iterations"] for r in dust_iterations(ctx, ids, empty_fields(w), s, max_iter, tol))
+    seeder.close()
+    ctx.close()
+    best = min(shrinks, key=lambda a: table[str(a)])
+    log(json.dumps({"validation_dust_iterations": table, "shrink": best}))
+    return best, table
+
+
+def run(side=64, epochs=80, patience=12, max_iter=300, tol=0.1, lr=2e-3, out=WEIGHTS, log=print):
+    """Data (plain Monte Carlo on the training and validation clouds),
+    training with validation-based stopping, the envelope from the training
+    data, the shrink factor from the validation clouds, the weights saved to
+    `out`, and the comparison on the test clouds."""
+    t0 = time.perf_counter()
+    T1, T, rho, info = make_dataset(TRAIN + VAL, side, max_iter=max_iter, tol=tol, log=log)
     t_data = time.perf_counter() - t0
-    stats = norm_stats(T1, rho)
-    X = np.stack([features(T1[i], rho[i], side, stats) for i in range(len(train_seeds))])
-    Y = (np.log(np.clip(T, T_MIN, T_MAX)) - np.log(np.clip(T1, T_MIN, T_MAX))).reshape(-1, side, side, side)
-    stats["y_mean"] = float(Y.mean())
-    stats["y_std"] = float(Y.std() + 1e-12)
-    Y = ((Y - stats["y_mean"]) / stats["y_std"]).astype(np.float32)
+    ntr = len(TRAIN)
+    norm = norm_stats(T1[:ntr], T[:ntr], rho[:ntr])
+    env = envelope(T1[:ntr], T[:ntr])
+    X = features(T1, rho, norm, side)
+    Y = targets(T1, T, norm, side)
+    del T1, T, rho
     t1 = time.perf_counter()
-    net, hist = train(X, Y, side, epochs=epochs, lr=lr, log=log)
+    params, hist, vhist, best_ep = train(X[:ntr], Y[:ntr], X[ntr:], Y[ntr:], epochs=epochs, patience=patience,
+                                         lr=lr, log=log)
     t_train = time.perf_counter() - t1
-    rows = compare(net, test_seeds, side, stats, max_iter, tol, log=log)
-    summary = dict(side=side, n_train=n_train, n_test=n_test, epochs=epochs, tol_K=tol,
-                   data_seconds=t_data, train_seconds=t_train, loss_history=hist, train_info=info,
-                   test=rows, norm=stats,
-                   plain_total_s=sum(r["plain_s"] for r in rows), learned_total_s=sum(r["learned_s"] for r in rows),
-                   plain_iters_mean=float(np.mean([r["plain_iters"] for r in rows])),
-                   learned_iters_mean=float(np.mean([r["learned_iters"] for r in rows])))
-    return summary
+    del X, Y
+    norm["env"] = [env[0], env[1], list(map(float, env[2])), list(map(float, env[3]))]
+    shrink, table = choose_shrink(params, norm, VAL, side, max_iter, tol, log=log)
+    norm["shrink"] = shrink
+    meta = dict(train=[TRAIN[0], TRAIN[-1]], val=[VAL[0], VAL[-1]], side=side, epochs_run=len(hist),
+                best_epoch=best_ep, train_loss=hist, val_loss=vhist, lr=lr, tol_K=tol,
+                data_seconds=t_data, train_seconds=t_train, train_info=info, validation_iterations=table)
+    if out:
+        save_weights(out, params, {k: v for k, v in norm.items() if k not in ("env", "shrink")}, meta, shrink, env)
+    cmp_ = compare(params, norm, TEST, side, max_iter, tol, log=log)
+    return dict(meta=meta, norm=norm, test=cmp_)
+
+
+def seed_bound(seeds=TEST, side=64, max_iter=300, tol=0.1, other_seed=7, log=print):
+    """What any seed can gain on these clouds: dust iterations to max |dT| <
+    tol from (a) each run's own converged T (a perfect predictor), (b) the
+    converged T of an independent Monte Carlo realisation of the same cloud
+    (context seed `other_seed`: as good as the method's own answer, without
+    this run's frozen noise) and (c) T1 (the plain start)."""
+    w = I.config_c4(seeds, side=side)
+    runs = {}
+    for cs in (w.seed, other_seed):
+        ctx, ids = context(w, cs)
+        T1, T = empty_fields(w), empty_fields(w)
+        constant_iteration(ctx, ids, T1)
+        rows = dust_iterations(ctx, ids, T, max_iter=max_iter, tol=tol)
+        runs[cs] = (ctx, ids, T1, T, rows)
+    ctx, ids, T1, T, rows = runs[w.seed]
+    out = dict(T1=[r["iterations"] for r in rows])
+    for name, start in (("own_converged", T), ("other_realisation", runs[other_seed][3])):
+        r2 = dust_iterations(ctx, ids, empty_fields(w), seeds=[t.clone() for t in start], max_iter=max_iter, tol=tol)
+        out[name] = [r["iterations"] for r in r2]
+    for c in runs.values():
+        c[0].close()
+    log(json.dumps(out))
+    return out
 
 
 def main():
     ap = argparse.ArgumentParser(description="learned temperature seed: data, training, comparison")
     ap.add_argument("--side", type=int, default=64)
-    ap.add_argument("--train", type=int, default=160)
-    ap.add_argument("--test", type=int, default=20)
-    ap.add_argument("--epochs", type=int, default=60)
-    ap.add_argument("--max-iter", type=int, default=60)
+    ap.add_argument("--epochs", type=int, default=80)
+    ap.add_argument("--patience", type=int, default=12)
+    ap.add_argument("--max-iter", type=int, default=300)
     ap.add_argument("--tol", type=float, default=0.1)
     ap.add_argument("--lr", type=float, default=2e-3)
-    ap.add_argument("--out", default="learned_seed.json")
-    ap.add_argument("--bound", action="store_true",
-                    help="only measure what an ideal seed can gain on the test clouds (no training)")
+    ap.add_argument("--out", default=WEIGHTS, help="where the trained weights are written")
+    ap.add_argument("--summary", default="", help="JSON summary file")
+    ap.add_argument("--bound", action="store_true", help="only the seed bound on the test clouds")
+    ap.add_argument("--evaluate", action="store_true", help="only the comparison, with the saved weights")
     a = ap.parse_args()
     if a.bound:
-        rows = seed_bound(np.arange(2000, 2000 + a.test), a.side, a.max_iter, a.tol)
-        keys = ["own_converged_iters", "other_realisation_iters", "T1_iters"]
-        print(json.dumps({k: float(np.mean([r[k] for r in rows])) for k in keys}))
+        seed_bound(TEST, a.side, a.max_iter, a.tol)
         return
-    summary = run(a.side, a.train, a.test, a.epochs, a.max_iter, a.tol, a.lr)
-    os.makedirs(os.path.dirname(a.out) or ".", exist_ok=True)
-    with open(a.out, "w") as f:
-        json.dump(summary, f, indent=1)
-    print(json.dumps({k: v for k, v in summary.items() if k not in ("loss_history", "train_info", "test")}))
+    if a.evaluate:
+        params, norm, meta, digest = load_weights(a.out)
+        compare(params, norm, TEST, a.side, a.max_iter, a.tol)
+        return
+    s = run(a.side, a.epochs, a.patience, a.max_iter, a.tol, a.lr, a.out)
+    if a.summary:
+        with open(a.summary, "w") as f:
+            json.dump(s, f, indent=1)
 
 
 if __name__ == "__main__":

@@ -51,7 +51,8 @@ EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "so
            "soc_unet_get_params", "soc_unet_forward", "soc_unet_backward", "soc_unet_adam",
            "soc_nn_conv3d", "soc_nn_conv3d_dgrad", "soc_nn_conv3d_wgrad", "soc_nn_error_flag",
            "soc_simulate_frequency_batch_noalloc", "soc_abort", "soc_abort_clear", "soc_abort_status",
-           "soc_set_timeout", "soc_nn_adam", "soc_seed_features", "soc_seed_transform"]
+           "soc_set_timeout", "soc_nn_adam", "soc_seed_features", "soc_seed_transform",
+           "soc_iterate_batch", "soc_nn_seed_features"]
 
 
 class GridDesc(C.Structure):
@@ -72,6 +73,29 @@ class IterateParams(C.Structure):
                 ("max_iter", C.c_int32), ("dT_tol", C.c_double), ("reuse_constant", C.c_int32),
                 ("ali", C.c_int32), ("n_weighted", C.c_uint64), ("weighted_cap", C.c_uint32),
                 ("reference_field", C.c_int32), ("n_dust_first", C.c_uint64), ("n_dust_last", C.c_uint64)]
+
+
+SEED_MAX_BINS = 64
+
+
+class SeedMap(C.Structure):
+    _fields_ = [("y_mean", C.c_double), ("y_std", C.c_double), ("shrink", C.c_double), ("n_bins", C.c_int32),
+                ("reserved", C.c_int32), ("lnT1_lo", C.c_double), ("lnT1_hi", C.c_double),
+                ("y_lo", C.c_double * SEED_MAX_BINS), ("y_hi", C.c_double * SEED_MAX_BINS)]
+
+
+def seed_map(y_mean, y_std, shrink=1.0, envelope=None):
+    """SeedMap from the de-normalisation, the shrink factor and an optional
+    envelope (lnT1_lo, lnT1_hi, y_lo[n], y_hi[n])."""
+    m = SeedMap()
+    m.y_mean, m.y_std, m.shrink = float(y_mean), float(y_std), float(shrink)
+    if envelope is not None:
+        lo, hi, ylo, yhi = envelope
+        m.n_bins = len(ylo)
+        m.lnT1_lo, m.lnT1_hi = float(lo), float(hi)
+        for b in range(m.n_bins):
+            m.y_lo[b], m.y_hi[b] = float(ylo[b]), float(yhi[b])
+    return m
 
 
 class IterateResult(C.Structure):
@@ -145,7 +169,9 @@ def _load():
         "soc_set_timeout": ([P, C.c_double], I),
         "soc_nn_adam": ([P, P, P, P, C.c_int64, C.c_float, C.c_int32, P, P], I),
         "soc_seed_features": ([P, I, P, P, P, P], I),
-        "soc_seed_transform": ([P, I, P, P, C.c_double, C.c_double, P, P], I),
+        "soc_seed_transform": ([P, I, P, P, C.POINTER(SeedMap), P, P], I),
+        "soc_iterate_batch": ([P, I, P, C.POINTER(IterateParams), P, P, P, P, P], I),
+        "soc_nn_seed_features": ([P, P, C.c_int64, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -433,10 +459,12 @@ class Context:
         nrm = np.ascontiguousarray(norm, np.float64)
         self._check(lib.soc_seed_features(self.h, cloud_id, _t_ptr(T1), _np_ptr(nrm), _t_ptr(x), _stream(stream)))
 
-    def seed_transform(self, cloud_id, T1, pred, y_mean, y_std, T_seed, stream=None):
-        """soc_seed_transform: T_seed = clamp(T1 exp(pred y_std + y_mean))."""
-        self._check(lib.soc_seed_transform(self.h, cloud_id, _t_ptr(T1), _t_ptr(pred), float(y_mean), float(y_std),
-                                           _t_ptr(T_seed), _stream(stream)))
+    def seed_transform(self, cloud_id, T1, pred, smap, T_seed, stream=None):
+        """soc_seed_transform: T_seed = clamp(T1 exp(y)) with y the
+        de-normalised, shrunk and envelope-bounded prediction (smap: SeedMap,
+        see seed_map)."""
+        self._check(lib.soc_seed_transform(self.h, cloud_id, _t_ptr(T1), _t_ptr(pred), C.byref(smap), _t_ptr(T_seed),
+                                           _stream(stream)))
 
     def update_temperature_ali(self, cloud_id, A, A_self, T, max_dT=None, stream=None):
         self._check(lib.soc_update_temperature_ali(self.h, cloud_id, _t_ptr(A), _t_ptr(A_self), _t_ptr(T),
@@ -473,6 +501,29 @@ class Context:
         return dict(iterations=r.iterations, converged=bool(r.converged), final_max_dT=r.final_max_dT,
                     steps=r.steps, capped=r.capped, history=hist[:r.iterations].copy(),
                     timed_out=st == SOC_ERR_TIMEOUT)
+
+    def iterate_batch(self, cloud_ids, T_outs, *, n_background=0, n_point=0, n_per_cell=1, max_iter=0, dT_tol=0.1,
+                       T_seeds=None, reuse_constant=False, ali=False, stream=None):
+        """soc_iterate_batch: soc_iterate for several clouds, one tracer launch per
+        iteration for all clouds not yet converged.  T_outs / T_seeds: lists of
+        device tensors (T_seeds entries may be None).  Returns one dict per cloud
+        (as iterate) and timed_out."""
+        n = len(cloud_ids)
+        ids = (C.c_int * n)(*cloud_ids)
+        outs = (C.c_void_p * n)(*[t.data_ptr() for t in T_outs])
+        for t in T_outs:
+            _t_ptr(t)
+        seeds = None
+        if T_seeds is not None:
+            seeds = (C.c_void_p * n)(*[None if t is None else _t_ptr(t).value for t in T_seeds])
+        p = IterateParams(n_background, n_point, n_per_cell, max_iter, dT_tol, int(reuse_constant), int(ali), 0, 0, 0, 0, 0)
+        res = (IterateResult * n)()
+        hist = np.zeros((n, max(max_iter, 1)), np.float64)
+        st = self._check(lib.soc_iterate_batch(self.h, n, ids, C.byref(p), seeds, outs, res, _np_ptr(hist),
+                                               _stream(stream)), ok=(SOC_OK, SOC_ERR_STEP_LIMIT, SOC_ERR_TIMEOUT))
+        rows = [dict(iterations=r.iterations, converged=bool(r.converged), final_max_dT=r.final_max_dT, steps=r.steps,
+                     capped=r.capped, history=hist[k, :r.iterations].copy()) for k, r in enumerate(res)]
+        return rows, st == SOC_ERR_TIMEOUT
 
 
 def _nn_check(st, what):
@@ -545,6 +596,13 @@ def conv3d_dgrad(gy, w, w_scratch, gx, stream=None):
     Cin = w.shape[2]
     _nn_check(lib.soc_nn_conv3d_dgrad(_t_ptr(gy), N, D, H, W, Cout, _t_ptr(w), Cin, _t_ptr(w_scratch),
                                       _t_ptr(gx), _stream(stream)), "soc_nn_conv3d_dgrad")
+
+
+def seed_features(T1, rho, norm, x, stream=None):
+    """soc_nn_seed_features: x (float32 [n, 2]) from device T1 and rho."""
+    nrm = np.ascontiguousarray(norm, np.float64)
+    _nn_check(lib.soc_nn_seed_features(_t_ptr(T1), _t_ptr(rho), T1.numel(), _np_ptr(nrm), _t_ptr(x), _stream(stream)),
+              "soc_nn_seed_features")
 
 
 def adam(w, m, v, g, lr, t, w_bf16=None, stream=None):

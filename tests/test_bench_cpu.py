@@ -53,3 +53,17 @@ def test_map_segment_count_matches_brute_force():
             total += 1 + int((np.diff(cells, axis=0) != 0).sum())
             hit += 1
     assert rays == hit and segs == total
+
+
+def test_gpus_flag_launches_one_process_per_rank():
+    """`bench.py --gpus 2` outside torchrun relaunches itself under
+    torch.distributed.run with two ranks; the reference arm then runs on rank
+    0 alone, which reports the launch's world size."""
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
+                        "--warmup", "1", "--cpu-sample", "32"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600, env={k: v for k, v in os.environ.items() if k != "WORLD_SIZE"})
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.strip().splitlines() if l.startswith("{")]
+    assert len(lines) == 1                       # rank 1 prints nothing
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2
