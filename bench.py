@@ -113,26 +113,32 @@ def _peaks():
 # CPU oracle on a bounded sample (worker processes are spawned)
 # ---------------------------------------------------------------------------
 def _oracle_worker(args):
+    """The oracle (FP32 contract, then FP64 on an eighth of the packages) on
+    background packages pid_lo .. pid_lo + n - 1 of the given frequencies."""
     sys.path.insert(0, ROOT)
     freqs, pid_lo, n = args
     from paper_1812_06632_gb300 import inputs as I
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from parity_helpers import oracle_item
+    import oracle
     w = _workload_cache(I)
+    cl = w.clouds[0]
+    G = oracle.Grid(cl.nx, cl.ny, cl.nz, cl.level_start, cl.rho, cl.child, cl.parent)
+
+    def kappa(f):        # FP32 opacity per root-cell length, as the library derives it
+        return (np.float32(np.float64(w.dust.kabs[f]) * np.float64(cl.ell)),
+                np.float32(np.float64(w.dust.ksca[f]) * np.float64(cl.ell)))
+
     steps = 0
     t0 = time.perf_counter()
     for f in freqs:
-        _, st, _ = oracle_item(w, 0, dict(source=0, freq=f, pid_offset=pid_lo, n_packages=n))
+        ka, ks = kappa(f)
+        _, st, _ = oracle.trace(G, source=0, kabs=ka, ksca=ks, g=np.float32(w.dust.g[f]), seed=w.seed, freq=f,
+                                pid_lo=pid_lo, n_packages=n)
         steps += st["steps"]
     t_fp32 = time.perf_counter() - t0
-    # the FP64 oracle on an eighth of the same packages, timed separately
-    import oracle
-    from parity_helpers import kappa_root, oracle_grid
-    G = oracle_grid(w.clouds[0])
     steps64 = 0
     t0 = time.perf_counter()
     for f in freqs:
-        ka, ks = kappa_root(w.dust, f, w.clouds[0].ell)
+        ka, ks = kappa(f)
         _, st, _ = oracle.trace64(G, source=0, kabs=ka, ksca=ks, g=np.float32(w.dust.g[f]), seed=w.seed,
                                   freq=f, pid_lo=pid_lo, n_packages=max(n // 8, 1))
         steps64 += st["steps"]
@@ -602,7 +608,7 @@ def learned_record():
             "converged": bool(c["plain_converged"] and c["learned_converged"]),
             "max_abs_T_difference_K": c["max_abs_T_difference_K"],
             "seed_max_err_K_mean": float(np.mean(c["seed_max_err_K"])),
-            "T1_max_err_K_mean": float(np.mean(c["T1_max_err_K"])),
+            "start_max_err_K_mean": float(np.mean(c["start_max_err_K"])), "seed_after": c["seed_after"],
             "weights_sha256": digest, "trained": {k: meta.get(k) for k in ("best_epoch", "epochs_run", "train", "val")},
             "clocks": clk.summary(),
             "config": {"workload": f"{n} held-out hot-core clouds of {c['side']}^3 (seeds {L.TEST[0]}-{L.TEST[-1]}), "
@@ -783,7 +789,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=8192, help="oracle packages per frequency")
+    ap.add_argument("--cpu-sample", type=int, default=32768,
+                    help="oracle packages per frequency (about 20 s of CPU work over all host cores)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "unet", "learned", "map"],

@@ -81,31 +81,45 @@ def dust_iterations(ctx, ids, T_outs, seeds=None, max_iter=300, tol=0.1):
     return rows
 
 
-def make_dataset(seeds, side=64, chunk=20, max_iter=300, tol=0.1, log=print):
-    """Plain Monte Carlo T1 and converged T of every cloud, `chunk` clouds per
-    batched run.  Returns (T1, T, rho) as device tensors [n, side^3] and one
-    info row per cloud."""
+def first_iterations(ctx, ids, w, k, tol=0.1):
+    """Iteration 0 and then k plain dust iterations of every cloud: returns
+    (T1, T_k, rows of the k iterations).  T_k is the network's input; the
+    dust iterations are a deterministic map (frozen random numbers), so
+    continuing from T_k repeats the uninterrupted plain run."""
+    T1 = empty_fields(w)
+    constant_iteration(ctx, ids, T1)
+    if k == 0:
+        return T1, [t.clone() for t in T1], [dict(iterations=0, converged=False) for _ in ids]
+    Tk = empty_fields(w)
+    rows = dust_iterations(ctx, ids, Tk, max_iter=k, tol=tol)
+    return T1, Tk, rows
+
+
+def make_dataset(seeds, side=64, seed_after=2, chunk=20, max_iter=300, tol=0.1, log=print):
+    """Plain Monte Carlo of every cloud, `chunk` clouds per batched run: the
+    temperatures after `seed_after` dust iterations (T_k) and the converged
+    T.  Returns (T_k, T, rho) as device tensors [n, side^3] and one info row
+    per cloud (plain dust iterations in all)."""
     import torch
-    T1s, Ts, rhos, info = [], [], [], []
+    Tks, Ts, rhos, info = [], [], [], []
     for c0 in range(0, len(seeds), chunk):
         w = I.config_c4(seeds[c0:c0 + chunk], side=side)
         ctx, ids = context(w)
-        T1 = empty_fields(w)
-        T = empty_fields(w)
         t0 = time.perf_counter()
-        constant_iteration(ctx, ids, T1)
-        rows = dust_iterations(ctx, ids, T, max_iter=max_iter, tol=tol)
+        T1, Tk, rows_k = first_iterations(ctx, ids, w, seed_after, tol)
+        T = empty_fields(w)
+        rows = dust_iterations(ctx, ids, T, seeds=Tk, max_iter=max_iter, tol=tol)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        its = [rk["iterations"] + (0 if rk["converged"] else r["iterations"]) for rk, r in zip(rows_k, rows)]
         for k, r in enumerate(rows):
-            info.append(dict(**w.extra["clouds"][k], iterations=r["iterations"], converged=r["converged"]))
-        T1s += T1
+            info.append(dict(**w.extra["clouds"][k], iterations=its[k], converged=r["converged"]))
+        Tks += Tk
         Ts += T
         rhos += [torch.from_numpy(cl.rho).cuda() for cl in w.clouds]
-        log(f"clouds {seeds[c0]}..{seeds[min(c0 + chunk, len(seeds)) - 1]}: {dt:.1f} s, iterations "
-            f"{[r['iterations'] for r in rows]}")
+        log(f"clouds {seeds[c0]}..{seeds[min(c0 + chunk, len(seeds)) - 1]}: {dt:.1f} s, iterations {its}")
         ctx.close()
-    return torch.stack(T1s), torch.stack(Ts), torch.stack(rhos), info
+    return torch.stack(Tks), torch.stack(Ts), torch.stack(rhos), info
 
 
 def norm_stats(T1, T, rho):
@@ -292,9 +306,11 @@ def compare(params, norm, seeds=TEST, side=64, max_iter=300, tol=0.1, log=print)
     """Wall time to max |dT| < tol of the batch of clouds `seeds`: iteration 0
     (shared), then the dust iterations plain and learned-seeded, each as one
     batched run (one tracer launch per iteration for every unconverged
-    cloud).  The seeded time includes the features, the network forward and
-    the transform."""
+    cloud).  The seeded run makes norm["seed_after"] plain dust iterations,
+    then seeds every cloud from their result (features, network forward,
+    transform, all in its time) and iterates on."""
     import torch
+    k = int(norm.get("seed_after", 0))
     w = I.config_c4(seeds, side=side)
     ctx, ids = context(w)
     seeder = Seeder(params, norm, len(ids), side)
@@ -322,24 +338,32 @@ def compare(params, norm, seeds=TEST, side=64, max_iter=300, tol=0.1, log=print)
 
     T_learn = empty_fields(w)
     t0 = time.perf_counter()
-    s = seeder.seeds(ctx, ids, T1)
+    if k > 0:
+        Tk = empty_fields(w)
+        first = dust_iterations(ctx, ids, Tk, max_iter=k, tol=tol)
+    else:
+        Tk, first = T1, [dict(iterations=0, converged=False) for _ in ids]
+    s = seeder.seeds(ctx, ids, Tk)
+    s = [Tk[j] if first[j]["converged"] else s[j] for j in range(len(ids))]
     learn = dust_iterations(ctx, ids, T_learn, seeds=s, max_iter=max_iter, tol=tol)
     torch.cuda.synchronize()
     t_learn = time.perf_counter() - t0
+    learn_its = [f["iterations"] + r["iterations"] for f, r in zip(first, learn)]
 
-    # seed quality: max |T_seed - T_converged| against the same for T1
-    seed_err = [float((s[k] - T_plain[k]).abs().max().item()) for k in range(len(ids))]
-    t1_err = [float((T1[k] - T_plain[k]).abs().max().item()) for k in range(len(ids))]
-    dmax = max(float((T_plain[k] - T_learn[k]).abs().max().item()) for k in range(len(ids)))
+    # seed quality: max |T_seed - T_converged| against the same for T_k (the start it replaces)
+    seed_err = [float((s[j] - T_plain[j]).abs().max().item()) for j in range(len(ids))]
+    tk_err = [float((Tk[j] - T_plain[j]).abs().max().item()) for j in range(len(ids))]
+    dmax = max(float((T_plain[j] - T_learn[j]).abs().max().item()) for j in range(len(ids)))
     seeder.close()
     ctx.close()
-    out = dict(n_clouds=len(ids), side=side, tol_K=tol, constant_s=t_const, plain_dust_s=t_plain,
+    out = dict(n_clouds=len(ids), side=side, tol_K=tol, seed_after=k, constant_s=t_const, plain_dust_s=t_plain,
                learned_dust_s=t_learn, plain_s=t_const + t_plain, learned_s=t_const + t_learn,
-               plain_iterations=[r["iterations"] for r in plain], learned_iterations=[r["iterations"] for r in learn],
+               plain_iterations=[r["iterations"] for r in plain], learned_iterations=learn_its,
                plain_converged=all(r["converged"] for r in plain), learned_converged=all(r["converged"] for r in learn),
-               plain_steps=int(sum(r["steps"] for r in plain)), learned_steps=int(sum(r["steps"] for r in learn)),
-               max_abs_T_difference_K=dmax, seed_max_err_K=seed_err, T1_max_err_K=t1_err)
-    log(json.dumps({k: v for k, v in out.items() if k not in ("seed_max_err_K", "T1_max_err_K")}))
+               plain_steps=int(sum(r["steps"] for r in plain)),
+               learned_steps=int(sum(r["steps"] for r in learn) + sum(f.get("steps", 0) for f in first)),
+               max_abs_T_difference_K=dmax, seed_max_err_K=seed_err, start_max_err_K=tk_err)
+    log(json.dumps({k_: v for k_, v in out.items() if k_ not in ("seed_max_err_K", "start_max_err_K")}))
     return out
 
 
@@ -349,15 +373,17 @@ SHRINKS = (0.5, 0.65, 0.8, 0.9, 1.0)
 def choose_shrink(params, norm, seeds=VAL, side=64, max_iter=300, tol=0.1, shrinks=SHRINKS, log=print):
     """Dust iterations of the validation clouds for every shrink factor
     (and plain); returns (the factor with the fewest in total, table)."""
+    k = int(norm.get("seed_after", 0))
     w = I.config_c4(seeds, side=side)
     ctx, ids = context(w)
     seeder = Seeder(params, norm, len(ids), side)
-    T1 = empty_fields(w)
-    constant_iteration(ctx, ids, T1)
+    T1, Tk, first = first_iterations(ctx, ids, w, k, tol)
+    done = sum(f["iterations"] for f in first)
     table = {"plain": sum(r["iterations"] for r in dust_iterations(ctx, ids, empty_fields(w), None, max_iter, tol))}
     for a in shrinks:
-        s = seeder.seeds(ctx, ids, T1, shrink=a)
-        table[str(a)] = sum(r["iterations"] for r in dust_iterations(ctx, ids, empty_fields(w), s, max_iter, tol))
+        s = seeder.seeds(ctx, ids, Tk, shrink=a)
+        s = [Tk[j] if first[j]["converged"] else s[j] for j in range(len(ids))]
+        table[str(a)] = done + sum(r["iterations"] for r in dust_iterations(ctx, ids, empty_fields(w), s, max_iter, tol))
     seeder.close()
     ctx.close()
     best = min(shrinks, key=lambda a: table[str(a)])
@@ -365,13 +391,18 @@ def choose_shrink(params, norm, seeds=VAL, side=64, max_iter=300, tol=0.1, shrin
     return best, table
 
 
-def run(side=64, epochs=80, patience=12, max_iter=300, tol=0.1, lr=2e-3, out=WEIGHTS, log=print):
+SEED_AFTER = 2
+
+
+def run(side=64, epochs=80, patience=12, max_iter=300, tol=0.1, lr=2e-3, out=WEIGHTS, seed_after=SEED_AFTER,
+        log=print):
     """Data (plain Monte Carlo on the training and validation clouds),
     training with validation-based stopping, the envelope from the training
     data, the shrink factor from the validation clouds, the weights saved to
-    `out`, and the comparison on the test clouds."""
+    `out`, and the comparison on the test clouds.  The network's input is T
+    after `seed_after` plain dust iterations."""
     t0 = time.perf_counter()
-    T1, T, rho, info = make_dataset(TRAIN + VAL, side, max_iter=max_iter, tol=tol, log=log)
+    T1, T, rho, info = make_dataset(TRAIN + VAL, side, seed_after, max_iter=max_iter, tol=tol, log=log)
     t_data = time.perf_counter() - t0
     ntr = len(TRAIN)
     norm = norm_stats(T1[:ntr], T[:ntr], rho[:ntr])
@@ -385,13 +416,14 @@ def run(side=64, epochs=80, patience=12, max_iter=300, tol=0.1, lr=2e-3, out=WEI
     t_train = time.perf_counter() - t1
     del X, Y
     norm["env"] = [env[0], env[1], list(map(float, env[2])), list(map(float, env[3]))]
+    norm["seed_after"] = seed_after
     shrink, table = choose_shrink(params, norm, VAL, side, max_iter, tol, log=log)
     norm["shrink"] = shrink
     meta = dict(train=[TRAIN[0], TRAIN[-1]], val=[VAL[0], VAL[-1]], side=side, epochs_run=len(hist),
                 best_epoch=best_ep, train_loss=hist, val_loss=vhist, lr=lr, tol_K=tol,
                 data_seconds=t_data, train_seconds=t_train, train_info=info, validation_iterations=table)
     if out:
-        save_weights(out, params, {k: v for k, v in norm.items() if k not in ("env", "shrink")}, meta, shrink, env)
+        save_weights(out, params, {k_: v for k_, v in norm.items() if k_ not in ("env", "shrink")}, meta, shrink, env)
     cmp_ = compare(params, norm, TEST, side, max_iter, tol, log=log)
     return dict(meta=meta, norm=norm, test=cmp_)
 
@@ -429,6 +461,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=300)
     ap.add_argument("--tol", type=float, default=0.1)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--seed-after", type=int, default=SEED_AFTER,
+                    help="plain dust iterations before the network seeds the rest")
     ap.add_argument("--out", default=WEIGHTS, help="where the trained weights are written")
     ap.add_argument("--summary", default="", help="JSON summary file")
     ap.add_argument("--bound", action="store_true", help="only the seed bound on the test clouds")
@@ -441,7 +475,7 @@ def main():
         params, norm, meta, digest = load_weights(a.out)
         compare(params, norm, TEST, a.side, a.max_iter, a.tol)
         return
-    s = run(a.side, a.epochs, a.patience, a.max_iter, a.tol, a.lr, a.out)
+    s = run(a.side, a.epochs, a.patience, a.max_iter, a.tol, a.lr, a.out, a.seed_after)
     if a.summary:
         with open(a.summary, "w") as f:
             json.dump(s, f, indent=1)

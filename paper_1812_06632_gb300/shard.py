@@ -81,7 +81,7 @@ class LibraryBackend:
     def trace(self, specs, tally):
         """Adds the items' deposits to tally; returns their photon-cell steps."""
         stats = self.torch.zeros((len(specs), 4), dtype=self.torch.int64, device="cuda")
-        self.ctx.simulate(self.ctx.items(specs), tally, stats)
+        self.ctx.simulate(self.ctx.items([dict(s, cloud=self.cid) for s in specs]), tally, stats)
         return int(stats[:, 2].sum().item())
 
     def package_energy(self, source, n_total):
