@@ -536,8 +536,11 @@ soc_status soc_nn_error_flag(int *flag);
  * 3x3x3 output convolution (channel 0 = prediction).  side % 8 == 0.
  * Parameters are packed layer by layer (15 layers in forward order), each as
  * w[Cout][27][Cin] then b[Cout], FP32; soc_unet_param_count() floats.
- *   soc_unet_create     device buffers for a batch size and cube side.
- *   soc_unet_forward    d_input (N,S,S,S,2) FP32 device -> d_pred (N,S,S,S).
+ *   soc_unet_create     device buffers for a batch size, cube side and number
+ *                       of input channels n_inputs (1..16; the first layer
+ *                       always has 16 input channels, the ones beyond
+ *                       n_inputs read zeros).
+ *   soc_unet_forward    d_input (N,S,S,S,n_inputs) FP32 device -> d_pred (N,S,S,S).
  *   soc_unet_backward   forward, MSE loss against d_target (N,S,S,S), and
  *                       the gradients of every parameter (kept in the net);
  *                       d_pred / d_loss (device double) optional.
@@ -545,7 +548,7 @@ soc_status soc_nn_error_flag(int *flag);
  *   soc_unet_get_params host copy of the parameters (grads = 0) or of their
  *                       gradients (grads = 1).  Synchronous.
  * ------------------------------------------------------------------------ */
-soc_status soc_unet_create(int device, int batch, int side, int *net_id);
+soc_status soc_unet_create(int device, int batch, int side, int n_inputs, int *net_id);
 soc_status soc_unet_destroy(int net_id);
 int64_t soc_unet_param_count(void);
 soc_status soc_unet_set_params(int net_id, const float *host_params);
@@ -586,15 +589,19 @@ soc_status soc_nn_adam(float *d_w, float *d_m, float *d_v, const float *d_g, int
 /* ------------------------------------------------------------------------
  * Seeding transform of the learned temperature seed (not a step of the
  * paper's method), per cell of an uploaded regular grid, in FP64:
- *   soc_seed_features   network input d_x (device float [n_cells][2], the
- *                       channels-last (side, side, side, 2) layout of one
- *                       sample): x[c][0] = (ln clamp(T1[c], 2.7, 3000) -
- *                       norm[0]) / norm[1], x[c][1] = (ln max(rho_c, 1e-30) -
- *                       norm[2]) / norm[3], rho from the uploaded grid.
- *                       norm: host double [4] {ln T1 mean, ln T1 std,
- *                       ln rho mean, ln rho std} of the training set (stds
- *                       > 0).  The grid must be a regular cube whose side is
- *                       a multiple of 8 (SOC_ERR_ARG otherwise).
+ *   soc_seed_features   network input d_x (device float [n_cells][n_features],
+ *                       the channels-last (side, side, side, n_features)
+ *                       layout of one sample), n_features 2 or 3:
+ *                       x[c][0] = (ln clamp(T[c], 2.7, 3000) - norm[0]) / norm[1],
+ *                       x[c][1] = (ln max(rho_c, 1e-30) - norm[2]) / norm[3],
+ *                       x[c][2] = (ln clamp(T[c]) - ln clamp(T_prev[c]) -
+ *                                  norm[4]) / norm[5]   (n_features = 3:
+ *                       the last iteration's change; d_T_prev required),
+ *                       rho from the uploaded grid.  norm: host double
+ *                       [2 n_features], {mean, width} of each feature over
+ *                       the training set (widths > 0).  The grid must be a
+ *                       regular cube whose side is a multiple of 8
+ *                       (SOC_ERR_ARG otherwise).
  *   soc_seed_transform  for every cell (the network predicts the normalised
  *                       y = ln T - ln T1):
  *                         y = shrink (pred[c] y_std + y_mean);
@@ -605,14 +612,14 @@ soc_status soc_nn_adam(float *d_w, float *d_m, float *d_v, const float *d_g, int
  *                       map: host soc_seed_map (copied into the launch).
  *                       d_T1, d_pred, d_T_seed: device float [n_cells].
  *   soc_nn_seed_features  the features of soc_seed_features from caller
- *                       arrays (no context): d_T1, d_rho device float [n],
- *                       d_x device float [n][2] (e.g. a training set kept
- *                       after its clouds were freed).
+ *                       arrays (no context): d_T, d_T_prev, d_rho device
+ *                       float [n], d_x device float [n][n_features] (e.g. a
+ *                       training set kept after its clouds were freed).
  * All asynchronous on `stream`; d_T_seed may be passed as the seed of
  * soc_iterate or soc_iterate_batch.
  * ------------------------------------------------------------------------ */
-soc_status soc_seed_features(soc_ctx *ctx, int cloud_id, const float *d_T1, const double *norm, float *d_x,
-                             void *stream);
+soc_status soc_seed_features(soc_ctx *ctx, int cloud_id, const float *d_T, const float *d_T_prev, const double *norm,
+                             int n_features, float *d_x, void *stream);
 #define SOC_SEED_MAX_BINS 64
 typedef struct soc_seed_map {
     double y_mean, y_std;      /* de-normalisation of the prediction            */
@@ -624,8 +631,8 @@ typedef struct soc_seed_map {
 } soc_seed_map;
 soc_status soc_seed_transform(soc_ctx *ctx, int cloud_id, const float *d_T1, const float *d_pred,
                               const soc_seed_map *map, float *d_T_seed, void *stream);
-soc_status soc_nn_seed_features(const float *d_T1, const float *d_rho, int64_t n, const double *norm, float *d_x,
-                                void *stream);
+soc_status soc_nn_seed_features(const float *d_T, const float *d_T_prev, const float *d_rho, int64_t n,
+                                const double *norm, int n_features, float *d_x, void *stream);
 
 /* ------------------------------------------------------------------------
  * Launch configuration of the tracer (autotuner hook).  threads_per_block in

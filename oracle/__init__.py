@@ -93,7 +93,7 @@ def lib():
             _lib.oracle_philox4x32_10.argtypes = [P, P, P]
             _lib.oracle_u01.argtypes = [C.c_uint32]
             _lib.oracle_u01.restype = C.c_float
-            for n in ("oracle_exp_neg_v", "oracle_one_minus_exp_v", "oracle_log_v"):
+            for n in ("oracle_one_minus_exp_v", "oracle_log_v"):
                 getattr(_lib, n).argtypes = [P, P, C.c_int64]
             _lib.oracle_trace.argtypes = [C.POINTER(_Grid), C.POINTER(_Item), C.c_uint32,
                                           C.c_uint32, P, C.POINTER(_Stats), P, P]
@@ -149,11 +149,6 @@ def _vec(fn, x):
     y = np.empty_like(x)
     fn(_ptr(x), _ptr(y), x.size)
     return y
-
-
-def exp_neg(x):
-    """Contract exp(x), x <= 0 (FP32)."""
-    return _vec(lib().oracle_exp_neg_v, x)
 
 
 def one_minus_exp(tau):

@@ -233,14 +233,19 @@ def adam_step(theta, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 T_MIN, T_MAX = 2.7, 3000.0
 
 
-def seed_features(T1, rho, norm):
-    """Network input per cell: ((ln T1 - lt_mean) / lt_std, (ln rho -
-    lr_mean) / lr_std), with T1 clamped to [T_MIN, T_MAX] and rho to at least
-    1e-30.  norm: dict with lt_mean, lt_std, lr_mean, lr_std.  Returns
-    (n, 2)."""
-    lt = (np.log(np.clip(np.asarray(T1, np.float64), T_MIN, T_MAX)) - norm["lt_mean"]) / norm["lt_std"]
-    lr = (np.log(np.maximum(np.asarray(rho, np.float64), 1e-30)) - norm["lr_mean"]) / norm["lr_std"]
-    return np.stack([lt, lr], axis=-1)
+def seed_features(T, rho, norm, T_prev=None):
+    """Network input per cell: ((ln T - lt_mean) / lt_std, (ln rho -
+    lr_mean) / lr_std) and, given T_prev, ((ln T - ln T_prev) - ld_mean) /
+    ld_std, with temperatures clamped to [T_MIN, T_MAX] and rho to at least
+    1e-30.  norm: dict with lt_mean, lt_std, lr_mean, lr_std (ld_mean,
+    ld_std).  Returns (n, 2) or (n, 3)."""
+    lT = np.log(np.clip(np.asarray(T, np.float64), T_MIN, T_MAX))
+    cols = [(lT - norm["lt_mean"]) / norm["lt_std"],
+            (np.log(np.maximum(np.asarray(rho, np.float64), 1e-30)) - norm["lr_mean"]) / norm["lr_std"]]
+    if T_prev is not None:
+        lP = np.log(np.clip(np.asarray(T_prev, np.float64), T_MIN, T_MAX))
+        cols.append((lT - lP - norm["ld_mean"]) / norm["ld_std"])
+    return np.stack(cols, axis=-1)
 
 
 def seed_transform(T1, pred, y_mean, y_std, shrink=1.0, envelope=None):

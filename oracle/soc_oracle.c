@@ -26,9 +26,10 @@
  * package) so that energy is conserved exactly.
  *
  * Arithmetic: IEEE binary32, round-to-nearest-even, one rounding per written
- * operation (compiled with -ffp-contract=off and without fast-math).  exp and
- * log are the project's own polynomials (Cody-Waite reduction + Taylor series;
- * atanh series), not libm.
+ * operation (compiled with -ffp-contract=off and without fast-math); the
+ * fused multiply-adds the contract names are explicit fmaf calls.  1 - exp
+ * and log are the project's own polynomials (Cody-Waite reduction + Taylor
+ * series; atanh series), not libm.
  */
 #include <stdint.h>
 #include <string.h>
@@ -106,40 +107,33 @@ static const float SQRT2F = 0x1.6a09e6p+0f;      /* RN(sqrt 2)                  
 static float bits_to_float(uint32_t b) { float f; memcpy(&f, &b, 4); return f; }
 static uint32_t float_to_bits(float f) { uint32_t b; memcpy(&b, &f, 4); return b; }
 
-/* exp(x) for x <= 0.  Cody-Waite: x = k ln2 + r, |r| <= ln2/2, Taylor of
- * degree 7 with coefficients RN(1/n!), Horner order from the top. */
-float oracle_exp_neg(float x)
-{
-    if (x < -87.0f) return 0.0f;
-    if (x > 0.0f) x = 0.0f;
-    float t = rintf(x * LOG2E);                 /* k as an integral float, in [-126, 0] */
-    int k = (int)t;
-    float r = (x - t * LN2_HI) - t * LN2_LO;
-    float p = 0x1.a01a02p-13f;                  /* 1/7! */
-    p = p * r + 0x1.6c16c2p-10f;                /* 1/6! */
-    p = p * r + 0x1.111112p-7f;                 /* 1/5! */
-    p = p * r + 0x1.555556p-5f;                 /* 1/4! */
-    p = p * r + 0x1.555556p-3f;                 /* 1/3! */
-    p = p * r + 0.5f;
-    p = p * r + 1.0f;
-    p = p * r + 1.0f;
-    float scale = bits_to_float((uint32_t)(k + 127) << 23);
-    return p * scale;
-}
-
-/* 1 - exp(-tau), tau >= 0.  Series tau(1 - tau/2(1 - tau/3(...(1 - tau/8))))
- * below 0.5 (no cancellation for thin cells), else 1 - exp(-tau). */
+/* 1 - exp(-tau), tau >= 0, with full relative accuracy at every tau and no
+ * branch on tau: x = max(-tau, -87) = k ln2 + r (Cody-Waite: k = rint(x / ln2),
+ * r = x - k LN2_HI - k LN2_LO by two fused multiply-adds, |r| <= ln2/2);
+ * e^r - 1 = r P(r), P the Taylor series of (e^r - 1)/r to degree 6 with
+ * coefficients RN(1/n!), in Horner form with fused multiply-adds; then
+ * 1 - e^x = (1 - 2^k) - 2^k (e^r - 1) as one fused multiply-add.  For tau
+ * below ln2/2 (k = 0) the result is -(e^r - 1) itself, so thin cells keep
+ * full relative accuracy.  tau <= 0 (or NaN) gives 0.  fmaf is the C99
+ * fused multiply-add, rounded once (the CUDA side uses __fmaf_rn). */
 float oracle_one_minus_exp(float tau)
 {
-    static const float inv[9] = { 0.0f, 1.0f, 0x1p-1f, 0x1.555556p-2f, 0x1p-2f,
-                                  0x1.99999ap-3f, 0x1.555556p-3f, 0x1.24924ap-3f, 0x1p-3f };
-    if (!(tau > 0.0f)) return 0.0f;
-    if (tau < 0.5f) {
-        float p = 1.0f;
-        for (int k = 8; k >= 2; --k) p = 1.0f - (tau * inv[k]) * p;
-        return tau * p;
-    }
-    return 1.0f - oracle_exp_neg(-tau);
+    const float x = fmaxf(-tau, -87.0f);
+    const float t = rintf(x * LOG2E);           /* k as an integral float, in [-126, 0] */
+    const int k = (int)t;
+    float r = fmaf(-t, LN2_HI, x);
+    r = fmaf(-t, LN2_LO, r);
+    float p = 0x1.a01a02p-13f;                  /* 1/7! */
+    p = fmaf(p, r, 0x1.6c16c2p-10f);            /* 1/6! */
+    p = fmaf(p, r, 0x1.111112p-7f);             /* 1/5! */
+    p = fmaf(p, r, 0x1.555556p-5f);             /* 1/4! */
+    p = fmaf(p, r, 0x1.555556p-3f);             /* 1/3! */
+    p = fmaf(p, r, 0.5f);
+    p = fmaf(p, r, 1.0f);
+    const float em1 = r * p;                    /* e^r - 1 */
+    const float scale = bits_to_float((uint32_t)(k + 127) << 23);      /* 2^k */
+    const float q = fmaf(-scale, em1, 1.0f - scale);
+    return (tau > 0.0f) ? q : 0.0f;
 }
 
 /* ln(u) for u in (0,1) (any positive normal u works).  u = m 2^e with
@@ -553,7 +547,6 @@ void oracle_trace(const oracle_grid *G, const oracle_item *it, uint32_t pid_lo, 
 }
 
 /* Elementwise wrappers used by the tests that pin the elementary functions. */
-void oracle_exp_neg_v(const float *x, float *y, int64_t n) { for (int64_t i = 0; i < n; ++i) y[i] = oracle_exp_neg(x[i]); }
 void oracle_one_minus_exp_v(const float *x, float *y, int64_t n) { for (int64_t i = 0; i < n; ++i) y[i] = oracle_one_minus_exp(x[i]); }
 void oracle_log_v(const float *x, float *y, int64_t n) { for (int64_t i = 0; i < n; ++i) y[i] = oracle_log(x[i]); }
 

@@ -1,12 +1,14 @@
 // soc_fp32.cuh -- the FP32 arithmetic of the package tracer on the device.
 //
 // Every operation is one IEEE binary32 operation with round-to-nearest-even,
-// written with the _rn intrinsics so that no multiply-add is ever fused; the
-// translation unit is also compiled with -fmad=false.  The results are
-// therefore fixed by the operation sequence alone, which is what lets the
-// counters be compared bit for bit with an independent CPU evaluation.
+// written with the _rn intrinsics; multiply-adds are fused only where an
+// explicit __fmaf_rn says so (one rounding, as C99 fmaf), and the
+// translation unit is compiled with -fmad=false so that the compiler fuses
+// nothing else.  The results are therefore fixed by the operation sequence
+// alone, which is what lets the counters be compared bit for bit with an
+// independent CPU evaluation.
 //
-// exp and log are this project's own: Cody-Waite reduction with a Taylor
+// 1 - exp and log are this project's own: Cody-Waite reduction with a Taylor
 // polynomial, and the atanh series; the constants are 1/n!, 1/k, ln 2 split
 // into a 16-bit head and its remainder, 1/ln 2 and sqrt 2, each rounded to
 // binary32.
@@ -44,44 +46,33 @@ __device__ __forceinline__ float u01(uint32_t x)
 }
 
 // ---------------------------------------------------------------------------
-// exp(x), x <= 0.
+// 1 - exp(-tau), tau >= 0, with full relative accuracy at every tau and no
+// branch on tau (lanes of a warp in thin and thick cells stay converged):
+// x = max(-tau, -87) = k ln2 + r (Cody-Waite: k = rint(x / ln 2), r by two
+// fused multiply-adds, |r| <= ln2/2); e^r - 1 = r P(r), P the Taylor series
+// of (e^r - 1)/r to degree 6 with coefficients RN(1/n!) in Horner form with
+// fused multiply-adds; 1 - e^x = (1 - 2^k) - 2^k (e^r - 1) as one fused
+// multiply-add.  Below tau = ln2/2 (k = 0) the result is -(e^r - 1) itself.
+// tau <= 0 (or NaN) gives 0.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float exp_neg(float x)
-{
-    if (x < -87.0f) return 0.0f;
-    x = fminf(x, 0.0f);
-    const int k = __float2int_rn(__fmul_rn(x, 0x1.715476p+0f));        // rint(x / ln 2)
-    const float t = __int2float_rn(k);
-    const float r = __fsub_rn(__fsub_rn(x, __fmul_rn(t, 0x1.62e4p-1f)), // x - k ln2_hi
-                              __fmul_rn(t, 0x1.7f7d1cp-20f));           //   - k ln2_lo
-    float p = 0x1.a01a02p-13f;                                          // 1/7!
-    p = __fadd_rn(__fmul_rn(p, r), 0x1.6c16c2p-10f);                     // 1/6!
-    p = __fadd_rn(__fmul_rn(p, r), 0x1.111112p-7f);                      // 1/5!
-    p = __fadd_rn(__fmul_rn(p, r), 0x1.555556p-5f);                      // 1/4!
-    p = __fadd_rn(__fmul_rn(p, r), 0x1.555556p-3f);                      // 1/3!
-    p = __fadd_rn(__fmul_rn(p, r), 0.5f);
-    p = __fadd_rn(__fmul_rn(p, r), 1.0f);
-    p = __fadd_rn(__fmul_rn(p, r), 1.0f);
-    return __fmul_rn(p, __uint_as_float((uint32_t)(k + 127) << 23));     // * 2^k
-}
-
-// 1 - exp(-tau), tau >= 0; below 0.5 the alternating series in nested form
-// tau (1 - tau/2 (1 - tau/3 (... (1 - tau/8)))), which keeps relative accuracy
-// for optically thin segments.
 __device__ __forceinline__ float one_minus_exp(float tau)
 {
-    if (!(tau > 0.0f)) return 0.0f;
-    if (tau < 0.5f) {
-        float p = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(tau, 0x1p-3f), 1.0f));        // k = 8
-        p = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(tau, 0x1.24924ap-3f), p));          // k = 7
-        p = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(tau, 0x1.555556p-3f), p));          // k = 6
-        p = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(tau, 0x1.99999ap-3f), p));          // k = 5
-        p = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(tau, 0x1p-2f), p));                 // k = 4
-        p = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(tau, 0x1.555556p-2f), p));          // k = 3
-        p = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(tau, 0x1p-1f), p));                 // k = 2
-        return __fmul_rn(tau, p);
-    }
-    return __fsub_rn(1.0f, exp_neg(-tau));
+    const float x = fmaxf(-tau, -87.0f);
+    const int k = __float2int_rn(__fmul_rn(x, 0x1.715476p+0f));         // rint(x / ln 2)
+    const float t = __int2float_rn(k);
+    float r = __fmaf_rn(-t, 0x1.62e4p-1f, x);                           // x - k ln2_hi
+    r = __fmaf_rn(-t, 0x1.7f7d1cp-20f, r);                              //   - k ln2_lo
+    float p = 0x1.a01a02p-13f;                                          // 1/7!
+    p = __fmaf_rn(p, r, 0x1.6c16c2p-10f);                               // 1/6!
+    p = __fmaf_rn(p, r, 0x1.111112p-7f);                                // 1/5!
+    p = __fmaf_rn(p, r, 0x1.555556p-5f);                                // 1/4!
+    p = __fmaf_rn(p, r, 0x1.555556p-3f);                                // 1/3!
+    p = __fmaf_rn(p, r, 0.5f);
+    p = __fmaf_rn(p, r, 1.0f);
+    const float em1 = __fmul_rn(r, p);                                  // e^r - 1
+    const float sc = __uint_as_float((uint32_t)(k + 127) << 23);         // 2^k
+    const float q = __fmaf_rn(-sc, em1, __fsub_rn(1.0f, sc));
+    return tau > 0.0f ? q : 0.0f;
 }
 
 // ln(u), u positive and normal.  u = m 2^e with m in (sqrt(1/2), sqrt 2];

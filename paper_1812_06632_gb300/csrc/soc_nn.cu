@@ -609,12 +609,13 @@ __global__ void upsample_bwd_kernel(const float *g_out, int out_stride, int out_
     }
 }
 
-// Network input: x16[v][0..1] = bf16(in[v][0..1]), channels 2..15 zero.
-__global__ void input_kernel(const float *in, long long V, bf16 *x16)
+// Network input: x16[v][0..n_in-1] = bf16(in[v][0..n_in-1]), the other
+// channels of the 16 zero.
+__global__ void input_kernel(const float *in, long long V, int n_in, bf16 *x16)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V * 16; i += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(i % 16);
-        x16[i] = __float2bfloat16_rn(c < 2 ? in[(i / 16) * 2 + c] : 0.f);
+        x16[i] = __float2bfloat16_rn(c < n_in ? in[(i / 16) * n_in + c] : 0.f);
     }
 }
 
@@ -676,16 +677,22 @@ __global__ void to_bf16_kernel(const float *src, long long n, bf16 *dst)
 }
 
 // Seeding transform of the learned temperature seed, in FP64 per cell.
-// Features: x[c][0] = (ln clamp(T1, 2.7, 3000) - lt_mean) / lt_std,
-//           x[c][1] = (ln max(rho, 1e-30) - lr_mean) / lr_std.
-__global__ void seed_features_kernel(const float *T1, const float *rho, long long n, double lt_mean, double lt_std,
-                                     double lr_mean, double lr_std, float *x)
+// Features (nf = 2 or 3 per cell):
+//   x[c][0] = (ln clamp(T, 2.7, 3000) - norm[0]) / norm[1],
+//   x[c][1] = (ln max(rho, 1e-30) - norm[2]) / norm[3],
+//   x[c][2] = (ln clamp(T) - ln clamp(T_prev) - norm[4]) / norm[5]  (nf = 3).
+__global__ void seed_features_kernel(const float *T, const float *T_prev, const float *rho, long long n, int nf,
+                                     const SeedNorm nm, float *x)
 {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        const double t = fmin(fmax((double)T1[c], kTMin), kTMax);
+        const double lt = log(fmin(fmax((double)T[c], kTMin), kTMax));
         const double r = fmax((double)rho[c], 1e-30);
-        x[2 * c] = (float)((log(t) - lt_mean) / lt_std);
-        x[2 * c + 1] = (float)((log(r) - lr_mean) / lr_std);
+        x[nf * c] = (float)((lt - nm.v[0]) / nm.v[1]);
+        x[nf * c + 1] = (float)((log(r) - nm.v[2]) / nm.v[3]);
+        if (nf == 3) {
+            const double lp = log(fmin(fmax((double)T_prev[c], kTMin), kTMax));
+            x[nf * c + 2] = (float)((lt - lp - nm.v[4]) / nm.v[5]);
+        }
     }
 }
 
@@ -897,7 +904,7 @@ struct Buf {
 
 struct Net {
     int device = 0;
-    int batch = 0, S = 0;
+    int batch = 0, S = 0, n_in = 2;              // n_in: real input channels (of the 16)
     long long V0 = 0, V1 = 0, V2 = 0, V3 = 0;     // voxels per level (all samples)
     // parameters
     Buf<float> w32[kLayers], b32[kLayers], gw[kLayers], gb[kLayers], mw[kLayers], vw[kLayers], mb[kLayers], vb[kLayers];
@@ -940,10 +947,12 @@ struct Net {
 
 }  // namespace nn
 
-cudaError_t launch_seed_features(const float *T1, const float *rho, int64_t n, const double norm[4], float *x,
-                                 cudaStream_t s)
+cudaError_t launch_seed_features(const float *T, const float *T_prev, const float *rho, int64_t n, int n_features,
+                                 const double *norm, float *x, cudaStream_t s)
 {
-    nn::seed_features_kernel<<<nn::grid_1d(n), 256, 0, s>>>(T1, rho, n, norm[0], norm[1], norm[2], norm[3], x);
+    SeedNorm nm{};
+    for (int k = 0; k < 2 * n_features; ++k) nm.v[k] = norm[k];
+    nn::seed_features_kernel<<<nn::grid_1d(n), 256, 0, s>>>(T, T_prev, rho, n, n_features, nm, x);
     return cudaGetLastError();
 }
 
@@ -1036,7 +1045,7 @@ soc_status forward(Net &n, const float *d_in, cudaStream_t s)
 {
     const int S0 = n.S, S1 = S0 / 2, S2 = S0 / 4, S3 = S0 / 8;
     soc_status st;
-    input_kernel<<<grid_1d(n.V0 * 16), 256, 0, s>>>(d_in, n.V0, n.x16.p);
+    input_kernel<<<grid_1d(n.V0 * 16), 256, 0, s>>>(d_in, n.V0, n.n_in, n.x16.p);
     NNCK(cudaGetLastError());
     if ((st = fwd(n, 0, n.x16.p, 16, 0, S0, n.e0a.p, 16, 0, s))) return st;
     if ((st = fwd(n, 1, n.e0a.p, 16, 0, S0, n.cat0.p, 48, 32, s))) return st;
@@ -1113,15 +1122,16 @@ soc_status backward(Net &n, const float *d_target, cudaStream_t s)
 
 extern "C" {
 
-soc_status soc_unet_create(int device, int batch, int side, int *net_id)
+soc_status soc_unet_create(int device, int batch, int side, int n_inputs, int *net_id)
 {
-    if (!net_id || batch < 1 || side < 8 || side % 8 != 0) return SOC_ERR_ARG;
+    if (!net_id || batch < 1 || side < 8 || side % 8 != 0 || n_inputs < 1 || n_inputs > 16) return SOC_ERR_ARG;
     if (cudaSetDevice(device) != cudaSuccess) return SOC_ERR_CUDA;
     Net *n = new (std::nothrow) Net();
     if (!n) return SOC_ERR_NOMEM;
     n->device = device;
     n->batch = batch;
     n->S = side;
+    n->n_in = n_inputs;
     n->V0 = (long long)batch * side * side * side;
     n->V1 = n->V0 / 8; n->V2 = n->V1 / 8; n->V3 = n->V2 / 8;
     cudaError_t e = cudaSuccess;
@@ -1351,11 +1361,15 @@ soc_status soc_nn_conv3d_wgrad(const void *gy, const void *x, int N, int D, int 
     return SOC_OK;
 }
 
-soc_status soc_nn_seed_features(const float *d_T1, const float *d_rho, int64_t n, const double *norm, float *d_x,
-                                void *stream)
+soc_status soc_nn_seed_features(const float *d_T, const float *d_T_prev, const float *d_rho, int64_t n,
+                                const double *norm, int n_features, float *d_x, void *stream)
 {
-    if (!d_T1 || !d_rho || !norm || !d_x || n < 1 || !(norm[1] > 0.0) || !(norm[3] > 0.0)) return SOC_ERR_ARG;
-    NNCK(soc::launch_seed_features(d_T1, d_rho, n, norm, d_x, (cudaStream_t)stream));
+    if (!d_T || !d_rho || !norm || !d_x || n < 1 || (n_features != 2 && n_features != 3) ||
+        (n_features == 3 && !d_T_prev))
+        return SOC_ERR_ARG;
+    for (int k = 1; k < 2 * n_features; k += 2)
+        if (!(norm[k] > 0.0)) return SOC_ERR_ARG;
+    NNCK(soc::launch_seed_features(d_T, d_T_prev, d_rho, n, n_features, norm, d_x, (cudaStream_t)stream));
     return SOC_OK;
 }
 

@@ -379,10 +379,12 @@ __device__ bool cross_face(const CC &C, Pkg &p, int ax, bool up, int32_t *anc = 
         return false;
     p.ri = ri; p.rj = rj; p.rk = rk;
     p.cell = ri + nx * (rj + ny * rk);
-    const float v = up ? 0.0f : 1.0f;
-    p.x = (ax == 0) ? v : p.x;
-    p.y = (ax == 1) ? v : p.y;
-    p.z = (ax == 2) ? v : p.z;
+    if (!kRegular) {            // (regular grids: the step already put it there)
+        const float v = up ? 0.0f : 1.0f;
+        p.x = (ax == 0) ? v : p.x;
+        p.y = (ax == 1) ? v : p.y;
+        p.z = (ax == 2) ? v : p.z;
+    }
     if (kRegular) p.rho = __uint_as_float(__ldg(C.cell() + p.cell));
     else if (kStack) enter_cell(C.cell(), p);
     else descend(C.cell(), p);
@@ -425,7 +427,8 @@ __device__ __forceinline__ int step(const CC &C, Pkg &p, float kabs, float ksca,
         if (si < s) { s = si; ax = 2; }
     }
     if (ax < 0) { p.pend += p.W; p.W = 0; return kCapped; }     // no exit face: end safely
-    const float ksh = __fmul_rn(__fmul_rn(p.rho, ksca), p.h);
+    // on regular grids h = 1 and the multiplications by h are exact: left out
+    const float ksh = kRegular ? __fmul_rn(p.rho, ksca) : __fmul_rn(__fmul_rn(p.rho, ksca), p.h);
     const float dtau = __fmul_rn(ksh, s);
     float sp = s;
     bool scatter = false;
@@ -433,7 +436,8 @@ __device__ __forceinline__ int step(const CC &C, Pkg &p, float kabs, float ksca,
         sp = fminf(__fdiv_rn(p.tauf, ksh), s);
         scatter = true;
     }
-    const float tau_abs = __fmul_rn(__fmul_rn(__fmul_rn(p.rho, kabs), p.h), sp);
+    const float tau_abs = kRegular ? __fmul_rn(__fmul_rn(p.rho, kabs), sp)
+                                   : __fmul_rn(__fmul_rn(__fmul_rn(p.rho, kabs), p.h), sp);
     if (tau_abs > 0.0f) {
         const float q = one_minus_exp(tau_abs);
         const float prod = __fmul_rn(w_to_float(p.W), q);
@@ -463,7 +467,11 @@ __device__ __forceinline__ int step(const CC &C, Pkg &p, float kabs, float ksca,
     // stay converged)
     const float da = (ax == 0) ? p.dx : (ax == 1) ? p.dy : p.dz;
     const bool up = da > 0.0f;
-    const float face = up ? 1.0f : 0.0f;
+    // regular grids: the exit coordinate goes straight to the neighbour's
+    // entry face (0 when moving up, 1 when moving down), which is where the
+    // crossing puts it; octrees place it on the exit face first (a climb
+    // rescales it)
+    const float face = (up != kRegular) ? 1.0f : 0.0f;
     const float mx = clamp01(__fadd_rn(p.x, __fmul_rn(p.dx, s)));
     const float my = clamp01(__fadd_rn(p.y, __fmul_rn(p.dy, s)));
     const float mz = clamp01(__fadd_rn(p.z, __fmul_rn(p.dz, s)));

@@ -9,11 +9,14 @@ plain iteration needs tens of dust iterations.  For every cloud the Monte
 Carlo path gives T1 (temperatures after iteration 0: background and point
 sources only) and the converged T (dust re-emission iterated with frozen
 random numbers until max |dT| < tol).  The network maps the features
-(normalised ln T1, ln rho; soc_seed_features) to the normalised
-y = ln T - ln T1.  A seeded run starts its dust iterations from T1 exp(y)
-(soc_seed_transform) instead of T1, y the de-normalised prediction; the
-iterations then continue to the same fixed point, so they are both the
-fallback and the measure of the seed's error.
+(soc_seed_features: normalised ln T_k, ln rho and ln T_k - ln T_{k-1}, T_k
+the temperatures after k plain dust iterations) to the normalised
+y = ln T - ln T_k.  The last change carries the slow mode of the iteration
+(T - T_k ~ (T_k - T_{k-1}) r / (1 - r) for a mode that shrinks by r per
+iteration), which the network learns to extrapolate.  A seeded run makes k
+plain dust iterations, then continues from T_k exp(y) (soc_seed_transform), y
+the de-normalised prediction; the iterations then continue to the same fixed
+point, so they are both the fallback and the measure of the seed's error.
 
 Two bounds keep the seed from overshooting where the emission (~T^6) makes
 an overshoot costly: y >= 0 holds exactly (dust re-emission only adds
@@ -81,76 +84,93 @@ def dust_iterations(ctx, ids, T_outs, seeds=None, max_iter=300, tol=0.1):
     return rows
 
 
-def first_iterations(ctx, ids, w, k, tol=0.1):
-    """Iteration 0 and then k plain dust iterations of every cloud: returns
-    (T1, T_k, rows of the k iterations).  T_k is the network's input; the
-    dust iterations are a deterministic map (frozen random numbers), so
-    continuing from T_k repeats the uninterrupted plain run."""
-    T1 = empty_fields(w)
-    constant_iteration(ctx, ids, T1)
-    if k == 0:
-        return T1, [t.clone() for t in T1], [dict(iterations=0, converged=False) for _ in ids]
-    Tk = empty_fields(w)
-    rows = dust_iterations(ctx, ids, Tk, max_iter=k, tol=tol)
-    return T1, Tk, rows
+def snapshots(ctx, ids, w, ks, tol=0.1):
+    """Iteration 0 and then plain dust iterations of every cloud, keeping the
+    temperatures after k iterations for every k in ks (0 = T1).  Returns
+    ({k: [T_k per cloud]}, dust iterations done per cloud, converged per
+    cloud).  The dust iterations are a deterministic map (frozen random
+    numbers), so continuing from a snapshot repeats the uninterrupted run."""
+    ks = sorted(set(int(k) for k in ks))
+    T = empty_fields(w)
+    constant_iteration(ctx, ids, T)
+    out, k_prev = {}, 0
+    done, conv = [0] * len(ids), [False] * len(ids)
+    for k in ks:
+        if k > k_prev:
+            nxt = empty_fields(w)
+            rows = dust_iterations(ctx, ids, nxt, seeds=T, max_iter=k - k_prev, tol=tol)
+            for j, r in enumerate(rows):
+                if not conv[j]:
+                    done[j] += r["iterations"]
+                    conv[j] = r["converged"]
+            T = nxt
+        out[k] = [t.clone() for t in T]
+        k_prev = k
+    return out, done, conv
 
 
-def make_dataset(seeds, side=64, seed_after=2, chunk=20, max_iter=300, tol=0.1, log=print):
+def make_dataset(seeds, side=64, seed_after=(3,), chunk=20, max_iter=300, tol=0.1, log=print):
     """Plain Monte Carlo of every cloud, `chunk` clouds per batched run: the
-    temperatures after `seed_after` dust iterations (T_k) and the converged
-    T.  Returns (T_k, T, rho) as device tensors [n, side^3] and one info row
+    temperatures after k - 1 and k dust iterations for every k in
+    `seed_after` (the network's candidate inputs) and the converged T.
+    Returns ({k: T_k}, T, rho) as device tensors [n, side^3] and one info row
     per cloud (plain dust iterations in all)."""
     import torch
-    Tks, Ts, rhos, info = [], [], [], []
+    ks = sorted(set(int(k) for k in seed_after) | set(int(k) - 1 for k in seed_after))
+    snaps, Ts, rhos, info = {k: [] for k in ks}, [], [], []
     for c0 in range(0, len(seeds), chunk):
         w = I.config_c4(seeds[c0:c0 + chunk], side=side)
         ctx, ids = context(w)
         t0 = time.perf_counter()
-        T1, Tk, rows_k = first_iterations(ctx, ids, w, seed_after, tol)
-        T = empty_fields(w)
-        rows = dust_iterations(ctx, ids, T, seeds=Tk, max_iter=max_iter, tol=tol)
+        sn, done, conv = snapshots(ctx, ids, w, ks, tol)
+        for k in ks:
+            snaps[k] += sn[k]
+        final = empty_fields(w)
+        rows = dust_iterations(ctx, ids, final, seeds=sn[ks[-1]], max_iter=max_iter, tol=tol)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        its = [rk["iterations"] + (0 if rk["converged"] else r["iterations"]) for rk, r in zip(rows_k, rows)]
-        for k, r in enumerate(rows):
-            info.append(dict(**w.extra["clouds"][k], iterations=its[k], converged=r["converged"]))
-        Tks += Tk
-        Ts += T
+        its = [done[j] + (0 if conv[j] else r["iterations"]) for j, r in enumerate(rows)]
+        for j, r in enumerate(rows):
+            info.append(dict(**w.extra["clouds"][j], iterations=its[j], converged=conv[j] or r["converged"]))
+        Ts += final
         rhos += [torch.from_numpy(cl.rho).cuda() for cl in w.clouds]
         log(f"clouds {seeds[c0]}..{seeds[min(c0 + chunk, len(seeds)) - 1]}: {dt:.1f} s, iterations {its}")
         ctx.close()
-    return torch.stack(Tks), torch.stack(Ts), torch.stack(rhos), info
+    return {k: torch.stack(v) for k, v in snaps.items()}, torch.stack(Ts), torch.stack(rhos), info
 
 
-def norm_stats(T1, T, rho):
-    """Means and widths of the network's inputs and target over a data set."""
+def norm_stats(Tk, Tp, T, rho):
+    """Means and widths of the network's three inputs and of its target over
+    a data set (Tk: the input temperatures, Tp: one iteration earlier)."""
     import torch
-    lt = torch.log(T1.double().clamp(T_MIN, T_MAX))
+    lt = torch.log(Tk.double().clamp(T_MIN, T_MAX))
     lr = torch.log(rho.double().clamp_min(1e-30))
+    ld = lt - torch.log(Tp.double().clamp(T_MIN, T_MAX))
     y = torch.log(T.double().clamp(T_MIN, T_MAX)) - lt
     return dict(lt_mean=lt.mean().item(), lt_std=lt.std().item() + 1e-12, lr_mean=lr.mean().item(),
-                lr_std=lr.std().item() + 1e-12, y_mean=y.mean().item(), y_std=y.std().item() + 1e-12)
+                lr_std=lr.std().item() + 1e-12, ld_mean=ld.mean().item(), ld_std=ld.std().item() + 1e-12,
+                y_mean=y.mean().item(), y_std=y.std().item() + 1e-12)
 
 
-def _norm4(norm):
-    return [norm["lt_mean"], norm["lt_std"], norm["lr_mean"], norm["lr_std"]]
+def _norm6(norm):
+    return [norm["lt_mean"], norm["lt_std"], norm["lr_mean"], norm["lr_std"], norm["ld_mean"], norm["ld_std"]]
 
 
-def features(T1, rho, norm, side):
-    """Network inputs [n, side, side, side, 2] by the library's feature kernel."""
+def features(Tk, Tp, rho, norm, side):
+    """Network inputs [n, side, side, side, 3] by the library's feature kernel."""
     import torch
     from . import soc
-    x = torch.empty((T1.shape[0], side, side, side, 2), dtype=torch.float32, device="cuda")
-    for k in range(T1.shape[0]):
-        soc.seed_features(T1[k].contiguous(), rho[k].contiguous(), _norm4(norm), x[k])
+    x = torch.empty((Tk.shape[0], side, side, side, 3), dtype=torch.float32, device="cuda")
+    for k in range(Tk.shape[0]):
+        soc.seed_features(Tk[k].contiguous(), rho[k].contiguous(), _norm6(norm), x[k], T_prev=Tp[k].contiguous())
     return x
 
 
-def targets(T1, T, norm, side):
-    """Training targets: normalised ln T - ln T1 (the inverse of the seeding
+def targets(Tk, T, norm, side):
+    """Training targets: normalised ln T - ln T_k (the inverse of the seeding
     transform), [n, side, side, side]."""
     import torch
-    y = torch.log(T.double().clamp(T_MIN, T_MAX)) - torch.log(T1.double().clamp(T_MIN, T_MAX))
+    y = torch.log(T.double().clamp(T_MIN, T_MAX)) - torch.log(Tk.double().clamp(T_MIN, T_MAX))
     return ((y - norm["y_mean"]) / norm["y_std"]).float().reshape(-1, side, side, side).contiguous()
 
 
@@ -182,31 +202,41 @@ def _mse(net, X, Y, batch):
     return tot / max(n, 1)
 
 
-def train(X, Y, Xv, Yv, epochs=80, patience=12, batch=4, lr=2e-3, seed=0, log=print):
+def repeats(iterations, cap=8):
+    """How often each cloud enters an epoch: slow clouds (many plain dust
+    iterations, where a seed saves the most) several times, up to `cap`
+    times the median cloud."""
+    it = np.asarray(iterations, np.float64)
+    return np.clip(np.rint(it / np.median(it)), 1, cap).astype(np.int64)
+
+
+def train(X, Y, Xv, Yv, epochs=80, patience=12, batch=4, lr=2e-3, seed=0, reps=None, log=print):
     """Adam on the MSE of the normalised target (a constant predictor scores
-    1), learning rate decaying linearly to 10 %; after every epoch the
-    validation loss decides which weights are kept, and training stops after
-    `patience` epochs without improvement.  Returns (best parameters, train
-    loss history, validation loss history, best epoch)."""
+    1), learning rate decaying linearly to 10 %; each epoch visits cloud c
+    reps[c] times (default once); after every epoch the validation loss
+    decides which weights are kept, and training stops after `patience`
+    epochs without improvement.  Returns (best parameters, train loss
+    history, validation loss history, best epoch)."""
     import torch
     from . import soc
     side = X.shape[1]
-    net = soc.UNet(batch, side)
+    net = soc.UNet(batch, side, n_inputs=X.shape[-1])
     net.set_params(init_params(seed))
     rng = np.random.default_rng(seed)
     n = X.shape[0]
+    order = np.repeat(np.arange(n), np.ones(n, np.int64) if reps is None else reps)
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
     hist, vhist = [], []
     best, best_ep = None, -1
     for ep in range(epochs):
-        perm = torch.from_numpy(rng.permutation(n)).cuda()
+        perm = torch.from_numpy(rng.permutation(order)).cuda()
         tot = 0.0
-        for b0 in range(0, n - batch + 1, batch):
+        for b0 in range(0, order.size - batch + 1, batch):
             idx = perm[b0:b0 + batch]
             net.backward(X.index_select(0, idx).contiguous(), Y.index_select(0, idx).contiguous(), loss=loss)
             net.adam(lr * (1.0 - 0.9 * ep / max(1, epochs - 1)))
             tot += loss.item()
-        hist.append(tot / max(1, n // batch))
+        hist.append(tot / max(1, order.size // batch))
         vhist.append(_mse(net, Xv, Yv, batch))
         if best is None or vhist[-1] < min(vhist[:-1]):
             best, best_ep = net.get_params(), ep
@@ -277,24 +307,25 @@ class Seeder:
         import torch
         from . import soc
         self.norm, self.side = norm, side
-        self.net = soc.UNet(n, side)
+        self.net = soc.UNet(n, side, n_inputs=3)
         self.net.set_params(params)
-        self.x = torch.empty((n, side, side, side, 2), dtype=torch.float32, device="cuda")
+        self.x = torch.empty((n, side, side, side, 3), dtype=torch.float32, device="cuda")
         self.pred = torch.empty((n, side, side, side), dtype=torch.float32, device="cuda")
 
-    def seeds(self, ctx, ids, T1s, shrink=None):
-        """T_seed of every cloud: features, one batched network forward and
-        the seeding transform (shrink and envelope of the map), all on the
-        GPU.  shrink overrides the stored factor (validation sweeps)."""
+    def seeds(self, ctx, ids, Tks, Tps, shrink=None):
+        """T_seed of every cloud from T_k and T_{k-1}: features, one batched
+        network forward and the seeding transform (shrink and envelope of
+        the map), all on the GPU.  shrink overrides the stored factor
+        (validation sweeps)."""
         import torch
         out = []
         for k, cid in enumerate(ids):
-            ctx.seed_features(cid, T1s[k], _norm4(self.norm), self.x[k])
+            ctx.seed_features(cid, Tks[k], _norm6(self.norm), self.x[k], T_prev=Tps[k])
         self.net.forward(self.x, self.pred)
         m = seed_map(self.norm, self.norm.get("shrink", 1.0) if shrink is None else shrink, self.norm.get("env"))
         for k, cid in enumerate(ids):
-            t = torch.empty_like(T1s[k])
-            ctx.seed_transform(cid, T1s[k], self.pred[k].reshape(-1), m, t)
+            t = torch.empty_like(Tks[k])
+            ctx.seed_transform(cid, Tks[k], self.pred[k].reshape(-1), m, t)
             out.append(t)
         return out
 
@@ -310,7 +341,7 @@ def compare(params, norm, seeds=TEST, side=64, max_iter=300, tol=0.1, log=print)
     then seeds every cloud from their result (features, network forward,
     transform, all in its time) and iterates on."""
     import torch
-    k = int(norm.get("seed_after", 0))
+    k = int(norm["seed_after"])
     w = I.config_c4(seeds, side=side)
     ctx, ids = context(w)
     seeder = Seeder(params, norm, len(ids), side)
@@ -320,7 +351,7 @@ def compare(params, norm, seeds=TEST, side=64, max_iter=300, tol=0.1, log=print)
     T0 = empty_fields(w0)
     constant_iteration(c0, i0, T0)
     dust_iterations(c0, i0, empty_fields(w0), max_iter=1)
-    Seeder(params, norm, 1, side).seeds(c0, i0, T0)
+    Seeder(params, norm, 1, side).seeds(c0, i0, T0, T0)
     c0.close()
     torch.cuda.synchronize()
 
@@ -338,17 +369,21 @@ def compare(params, norm, seeds=TEST, side=64, max_iter=300, tol=0.1, log=print)
 
     T_learn = empty_fields(w)
     t0 = time.perf_counter()
-    if k > 0:
-        Tk = empty_fields(w)
-        first = dust_iterations(ctx, ids, Tk, max_iter=k, tol=tol)
-    else:
-        Tk, first = T1, [dict(iterations=0, converged=False) for _ in ids]
-    s = seeder.seeds(ctx, ids, Tk)
-    s = [Tk[j] if first[j]["converged"] else s[j] for j in range(len(ids))]
+    # k - 1 plain dust iterations, then one more (T_{k-1}, T_k), then the seed
+    Tp = T1
+    first = [dict(iterations=0, converged=False, steps=0) for _ in ids]
+    if k > 1:
+        Tp = empty_fields(w)
+        first = dust_iterations(ctx, ids, Tp, seeds=T1, max_iter=k - 1, tol=tol)
+    Tk = empty_fields(w)
+    last = dust_iterations(ctx, ids, Tk, seeds=Tp, max_iter=1, tol=tol)
+    s = seeder.seeds(ctx, ids, Tk, Tp)
+    done = [f["converged"] or l["converged"] for f, l in zip(first, last)]
+    s = [Tk[j] if done[j] else s[j] for j in range(len(ids))]
     learn = dust_iterations(ctx, ids, T_learn, seeds=s, max_iter=max_iter, tol=tol)
     torch.cuda.synchronize()
     t_learn = time.perf_counter() - t0
-    learn_its = [f["iterations"] + r["iterations"] for f, r in zip(first, learn)]
+    learn_its = [f["iterations"] + l["iterations"] + r["iterations"] for f, l, r in zip(first, last, learn)]
 
     # seed quality: max |T_seed - T_converged| against the same for T_k (the start it replaces)
     seed_err = [float((s[j] - T_plain[j]).abs().max().item()) for j in range(len(ids))]
@@ -361,7 +396,8 @@ def compare(params, norm, seeds=TEST, side=64, max_iter=300, tol=0.1, log=print)
                plain_iterations=[r["iterations"] for r in plain], learned_iterations=learn_its,
                plain_converged=all(r["converged"] for r in plain), learned_converged=all(r["converged"] for r in learn),
                plain_steps=int(sum(r["steps"] for r in plain)),
-               learned_steps=int(sum(r["steps"] for r in learn) + sum(f.get("steps", 0) for f in first)),
+               learned_steps=int(sum(r["steps"] for r in learn) + sum(f["steps"] for f in first)
+                                 + sum(l["steps"] for l in last)),
                max_abs_T_difference_K=dmax, seed_max_err_K=seed_err, start_max_err_K=tk_err)
     log(json.dumps({k_: v for k_, v in out.items() if k_ not in ("seed_max_err_K", "start_max_err_K")}))
     return out
@@ -373,55 +409,67 @@ SHRINKS = (0.5, 0.65, 0.8, 0.9, 1.0)
 def choose_shrink(params, norm, seeds=VAL, side=64, max_iter=300, tol=0.1, shrinks=SHRINKS, log=print):
     """Dust iterations of the validation clouds for every shrink factor
     (and plain); returns (the factor with the fewest in total, table)."""
-    k = int(norm.get("seed_after", 0))
+    k = int(norm["seed_after"])
     w = I.config_c4(seeds, side=side)
     ctx, ids = context(w)
     seeder = Seeder(params, norm, len(ids), side)
-    T1, Tk, first = first_iterations(ctx, ids, w, k, tol)
-    done = sum(f["iterations"] for f in first)
+    sn, done, conv = snapshots(ctx, ids, w, (k - 1, k), tol)
     table = {"plain": sum(r["iterations"] for r in dust_iterations(ctx, ids, empty_fields(w), None, max_iter, tol))}
     for a in shrinks:
-        s = seeder.seeds(ctx, ids, Tk, shrink=a)
-        s = [Tk[j] if first[j]["converged"] else s[j] for j in range(len(ids))]
-        table[str(a)] = done + sum(r["iterations"] for r in dust_iterations(ctx, ids, empty_fields(w), s, max_iter, tol))
+        s = seeder.seeds(ctx, ids, sn[k], sn[k - 1], shrink=a)
+        s = [sn[k][j] if conv[j] else s[j] for j in range(len(ids))]
+        rows = dust_iterations(ctx, ids, empty_fields(w), s, max_iter, tol)
+        table[str(a)] = sum(done) + sum(0 if conv[j] else r["iterations"] for j, r in enumerate(rows))
     seeder.close()
     ctx.close()
     best = min(shrinks, key=lambda a: table[str(a)])
-    log(json.dumps({"validation_dust_iterations": table, "shrink": best}))
+    log(json.dumps({"seed_after": k, "validation_dust_iterations": table, "shrink": best}))
     return best, table
 
 
-SEED_AFTER = 2
+SEED_AFTER = (3, 5)
 
 
 def run(side=64, epochs=80, patience=12, max_iter=300, tol=0.1, lr=2e-3, out=WEIGHTS, seed_after=SEED_AFTER,
         log=print):
-    """Data (plain Monte Carlo on the training and validation clouds),
-    training with validation-based stopping, the envelope from the training
-    data, the shrink factor from the validation clouds, the weights saved to
-    `out`, and the comparison on the test clouds.  The network's input is T
-    after `seed_after` plain dust iterations."""
+    """Data (plain Monte Carlo on the training and validation clouds), then
+    for every candidate k in `seed_after` (the network's inputs come from T
+    after k - 1 and k plain dust iterations) training with validation-based
+    stopping (slow clouds oversampled), the envelope from the training data
+    and the shrink factor from the validation clouds; the k and shrink factor
+    with the fewest validation dust iterations are kept, saved to `out`, and
+    compared on the test clouds."""
     t0 = time.perf_counter()
-    T1, T, rho, info = make_dataset(TRAIN + VAL, side, seed_after, max_iter=max_iter, tol=tol, log=log)
+    snaps, T, rho, info = make_dataset(TRAIN + VAL, side, seed_after, max_iter=max_iter, tol=tol, log=log)
     t_data = time.perf_counter() - t0
     ntr = len(TRAIN)
-    norm = norm_stats(T1[:ntr], T[:ntr], rho[:ntr])
-    env = envelope(T1[:ntr], T[:ntr])
-    X = features(T1, rho, norm, side)
-    Y = targets(T1, T, norm, side)
-    del T1, T, rho
+    reps = repeats([r["iterations"] for r in info[:ntr]])
+    best = None
+    tried = {}
     t1 = time.perf_counter()
-    params, hist, vhist, best_ep = train(X[:ntr], Y[:ntr], X[ntr:], Y[ntr:], epochs=epochs, patience=patience,
-                                         lr=lr, log=log)
+    for k in sorted(set(int(k) for k in seed_after)):
+        Tk, Tp = snaps[k], snaps[k - 1]
+        norm = norm_stats(Tk[:ntr], Tp[:ntr], T[:ntr], rho[:ntr])
+        env = envelope(Tk[:ntr], T[:ntr])
+        X = features(Tk, Tp, rho, norm, side)
+        Y = targets(Tk, T, norm, side)
+        params, hist, vhist, best_ep = train(X[:ntr], Y[:ntr], X[ntr:], Y[ntr:], epochs=epochs, patience=patience,
+                                             lr=lr, reps=reps, log=log)
+        del X, Y
+        norm["env"] = [env[0], env[1], list(map(float, env[2])), list(map(float, env[3]))]
+        norm["seed_after"] = k
+        shrink, table = choose_shrink(params, norm, VAL, side, max_iter, tol, log=log)
+        norm["shrink"] = shrink
+        tried[k] = dict(validation_iterations=table, best_epoch=best_ep, epochs_run=len(hist), train_loss=hist,
+                        val_loss=vhist)
+        if best is None or table[str(shrink)] < best[0]:
+            best = (table[str(shrink)], k, params, norm, env, shrink)
     t_train = time.perf_counter() - t1
-    del X, Y
-    norm["env"] = [env[0], env[1], list(map(float, env[2])), list(map(float, env[3]))]
-    norm["seed_after"] = seed_after
-    shrink, table = choose_shrink(params, norm, VAL, side, max_iter, tol, log=log)
-    norm["shrink"] = shrink
-    meta = dict(train=[TRAIN[0], TRAIN[-1]], val=[VAL[0], VAL[-1]], side=side, epochs_run=len(hist),
-                best_epoch=best_ep, train_loss=hist, val_loss=vhist, lr=lr, tol_K=tol,
-                data_seconds=t_data, train_seconds=t_train, train_info=info, validation_iterations=table)
+    del snaps, T, rho
+    _, k, params, norm, env, shrink = best
+    meta = dict(train=[TRAIN[0], TRAIN[-1]], val=[VAL[0], VAL[-1]], side=side, seed_after=k, tried=tried,
+                best_epoch=tried[k]["best_epoch"], epochs_run=tried[k]["epochs_run"], lr=lr, tol_K=tol,
+                data_seconds=t_data, train_seconds=t_train, train_info=info, repeats=reps.tolist())
     if out:
         save_weights(out, params, {k_: v for k_, v in norm.items() if k_ not in ("env", "shrink")}, meta, shrink, env)
     cmp_ = compare(params, norm, TEST, side, max_iter, tol, log=log)
@@ -461,8 +509,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=300)
     ap.add_argument("--tol", type=float, default=0.1)
     ap.add_argument("--lr", type=float, default=2e-3)
-    ap.add_argument("--seed-after", type=int, default=SEED_AFTER,
-                    help="plain dust iterations before the network seeds the rest")
+    ap.add_argument("--seed-after", type=int, nargs="+", default=list(SEED_AFTER),
+                    help="candidate numbers of plain dust iterations before the network seeds the rest")
     ap.add_argument("--out", default=WEIGHTS, help="where the trained weights are written")
     ap.add_argument("--summary", default="", help="JSON summary file")
     ap.add_argument("--bound", action="store_true", help="only the seed bound on the test clouds")

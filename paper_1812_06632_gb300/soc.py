@@ -148,7 +148,7 @@ def _load():
         "soc_capture_end": ([P, P, C.POINTER(I)], I),
         "soc_graph_launch": ([P, I, P], I),
         "soc_graph_destroy": ([P, I], I),
-        "soc_unet_create": ([I, I, I, C.POINTER(I)], I),
+        "soc_unet_create": ([I, I, I, I, C.POINTER(I)], I),
         "soc_unet_destroy": ([I], I),
         "soc_unet_param_count": ([], C.c_int64),
         "soc_unet_set_params": ([I, P], I),
@@ -168,10 +168,10 @@ def _load():
         "soc_abort_status": ([P, C.POINTER(I), C.POINTER(I)], I),
         "soc_set_timeout": ([P, C.c_double], I),
         "soc_nn_adam": ([P, P, P, P, C.c_int64, C.c_float, C.c_int32, P, P], I),
-        "soc_seed_features": ([P, I, P, P, P, P], I),
+        "soc_seed_features": ([P, I, P, P, P, I, P, P], I),
         "soc_seed_transform": ([P, I, P, P, C.POINTER(SeedMap), P, P], I),
         "soc_iterate_batch": ([P, I, P, C.POINTER(IterateParams), P, P, P, P, P], I),
-        "soc_nn_seed_features": ([P, P, C.c_int64, P, P, P], I),
+        "soc_nn_seed_features": ([P, P, P, C.c_int64, P, I, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -453,11 +453,13 @@ class Context:
         self._check(lib.soc_map(self.h, cloud_id, _t_ptr(T), freq, _np_ptr(d), _np_ptr(u), npx, npy,
                                 float(pix_size), _np_ptr(c), float(I_bg), _t_ptr(out), _stream(stream)))
 
-    def seed_features(self, cloud_id, T1, norm, x, stream=None):
-        """soc_seed_features: x (float32 [n_cells, 2]) from T1 and the grid's
-        density; norm = (lt_mean, lt_std, lr_mean, lr_std)."""
+    def seed_features(self, cloud_id, T, norm, x, T_prev=None, stream=None):
+        """soc_seed_features: x (float32 [n_cells, n_features]) from T, the
+        grid's density and (3 features) T_prev; norm = {mean, width} of each
+        feature (4 or 6 values)."""
         nrm = np.ascontiguousarray(norm, np.float64)
-        self._check(lib.soc_seed_features(self.h, cloud_id, _t_ptr(T1), _np_ptr(nrm), _t_ptr(x), _stream(stream)))
+        self._check(lib.soc_seed_features(self.h, cloud_id, _t_ptr(T), _t_ptr(T_prev), _np_ptr(nrm), nrm.size // 2,
+                                          _t_ptr(x), _stream(stream)))
 
     def seed_transform(self, cloud_id, T1, pred, smap, T_seed, stream=None):
         """soc_seed_transform: T_seed = clamp(T1 exp(y)) with y the
@@ -533,14 +535,14 @@ def _nn_check(st, what):
 
 class UNet:
     """The learned temperature seed (soc_unet_*): 3D U-Net on cubes of side
-    `side` (multiple of 8), batch `batch`; input (N,S,S,S,2) FP32, output
-    (N,S,S,S) FP32, all torch CUDA tensors."""
+    `side` (multiple of 8), batch `batch`; input (N,S,S,S,n_inputs) FP32,
+    output (N,S,S,S) FP32, all torch CUDA tensors."""
 
-    def __init__(self, batch: int, side: int, device: int = 0):
+    def __init__(self, batch: int, side: int, device: int = 0, n_inputs: int = 2):
         nid = C.c_int(-1)
-        _nn_check(lib.soc_unet_create(device, batch, side, C.byref(nid)), "soc_unet_create")
+        _nn_check(lib.soc_unet_create(device, batch, side, n_inputs, C.byref(nid)), "soc_unet_create")
         self.id = nid.value
-        self.batch, self.side = batch, side
+        self.batch, self.side, self.n_inputs = batch, side, n_inputs
         self.n_params = int(lib.soc_unet_param_count())
 
     def close(self):
@@ -598,11 +600,12 @@ def conv3d_dgrad(gy, w, w_scratch, gx, stream=None):
                                       _t_ptr(gx), _stream(stream)), "soc_nn_conv3d_dgrad")
 
 
-def seed_features(T1, rho, norm, x, stream=None):
-    """soc_nn_seed_features: x (float32 [n, 2]) from device T1 and rho."""
+def seed_features(T, rho, norm, x, T_prev=None, stream=None):
+    """soc_nn_seed_features: x (float32 [n, n_features]) from device T, rho
+    and (3 features) T_prev; norm = {mean, width} of each feature."""
     nrm = np.ascontiguousarray(norm, np.float64)
-    _nn_check(lib.soc_nn_seed_features(_t_ptr(T1), _t_ptr(rho), T1.numel(), _np_ptr(nrm), _t_ptr(x), _stream(stream)),
-              "soc_nn_seed_features")
+    _nn_check(lib.soc_nn_seed_features(_t_ptr(T), _t_ptr(T_prev), _t_ptr(rho), T.numel(), _np_ptr(nrm),
+                                       nrm.size // 2, _t_ptr(x), _stream(stream)), "soc_nn_seed_features")
 
 
 def adam(w, m, v, g, lr, t, w_bf16=None, stream=None):

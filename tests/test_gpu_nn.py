@@ -98,17 +98,18 @@ def _bf_params(P):
 GRAD_BOUND_W, GRAD_BOUND_B, PRED_BOUND = 6e-2, 4e-2, 1.5e-2
 
 
-def test_unet_forward_and_gradients_match_oracle(libsoc):
+@pytest.mark.parametrize("n_in", [2, 3])
+def test_unet_forward_and_gradients_match_oracle(libsoc, n_in):
     B, S = 1, 32
     rng = np.random.default_rng(7)
     P = O.init_params(seed=1)
     for n, _, cout in O.LAYERS:
         P[n] = (P[n][0], rng.normal(0, 0.05, cout) * (np.arange(cout) < (1 if n == "head" else cout)))
     flat = _flat(P).astype(np.float32)
-    net = libsoc.UNet(B, S)
+    net = libsoc.UNet(B, S, n_inputs=n_in)
     assert net.n_params == flat.size
     net.set_params(flat)
-    x_np = rng.standard_normal((B, S, S, S, 2)).astype(np.float32)
+    x_np = rng.standard_normal((B, S, S, S, n_in)).astype(np.float32)
     t_np = rng.standard_normal((B, S, S, S)).astype(np.float32)
     x = torch.from_numpy(x_np).cuda()
     t = torch.from_numpy(t_np).cuda()
@@ -118,7 +119,7 @@ def test_unet_forward_and_gradients_match_oracle(libsoc):
     torch.cuda.synchronize()
     Pb = _bf_params(P)
     x16 = np.zeros((B, S, S, S, 16))
-    x16[..., :2] = torch.from_numpy(x_np).to(torch.bfloat16).float().numpy()
+    x16[..., :n_in] = torch.from_numpy(x_np).to(torch.bfloat16).float().numpy()
     p_ref, cache = O.unet_forward(x16, Pb, store_bf16=True)
     assert _rel(pred.cpu().numpy(), p_ref) < PRED_BOUND
     L_ref, g_ref = O.mse(p_ref, t_np)
@@ -252,6 +253,14 @@ def test_seed_features_and_transform_match_oracle(libsoc):
     torch.cuda.synchronize()
     xr = O.seed_features(T1, cl.rho.astype(np.float32), norm)
     np.testing.assert_allclose(x.cpu().numpy(), xr, rtol=2e-7, atol=2e-7)
+    # three features: the last iteration's change of ln T as well
+    Tp = (T1 * rng.uniform(0.5, 1.0, cl.n_cells)).astype(np.float32)
+    norm3 = dict(norm, ld_mean=0.2, ld_std=0.3)
+    x3 = torch.empty((cl.n_cells, 3), dtype=torch.float32, device="cuda")
+    ctx.seed_features(ids[0], T1d, [3.1, 0.7, -0.2, 1.4, 0.2, 0.3], x3, T_prev=torch.from_numpy(Tp).cuda())
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(x3.cpu().numpy(), O.seed_features(T1, cl.rho.astype(np.float32), norm3, T_prev=Tp),
+                               rtol=2e-7, atol=2e-7)
     Tr = O.seed_transform(T1, pred, 0.15, 0.6)
     np.testing.assert_allclose(Ts.cpu().numpy(), Tr, rtol=2e-7)
     # shrink and a 64-bin envelope; cells within 1e-9 of a bin edge are left

@@ -229,6 +229,12 @@ def test_seed_features_standardise_their_own_statistics():
     x = nn.seed_features(T1, rho, norm)
     np.testing.assert_allclose(x.mean(axis=0), 0.0, atol=1e-12)
     np.testing.assert_allclose(x.std(axis=0), 1.0, rtol=1e-12)
+    # the third feature is the standardised change of ln T
+    Tp = T1 * rng.uniform(0.5, 1.0, T1.size)
+    d = np.log(T1) - np.log(Tp)
+    x3 = nn.seed_features(T1, rho, dict(norm, ld_mean=d.mean(), ld_std=d.std()), T_prev=Tp)
+    np.testing.assert_allclose(x3[:, :2], x, rtol=1e-15)
+    np.testing.assert_allclose(x3[:, 2], (d - d.mean()) / d.std(), rtol=1e-12, atol=1e-12)
     # identity normalisation gives the logarithms; T1 below 2.7 K and rho = 0 are clamped
     x0 = nn.seed_features([1.0, 10.0], [0.0, 2.0], dict(lt_mean=0.0, lt_std=1.0, lr_mean=0.0, lr_std=1.0))
     np.testing.assert_allclose(x0, [[np.log(2.7), np.log(1e-30)], [np.log(10.0), np.log(2.0)]], rtol=1e-15)

@@ -13,9 +13,9 @@ SRC = os.path.join(ROOT, "oracle", "soc_oracle.c")
 MUTANTS = {
     "uniform_not_cosine_entry": ("float mu = sqrtf(u);                 /* cosine-weighted inward angle */",
                                  "float mu = u;"),
-    "exp_drops_ln2_lo": ("float r = (x - t * LN2_HI) - t * LN2_LO;", "float r = (x - t * LN2_HI);"),
+    "exp_drops_ln2_lo": ("    r = fmaf(-t, LN2_LO, r);\n", ""),
     "log_drops_ln2_lo": ("return (t * LN2_LO + lm) + t * LN2_HI;", "return lm + t * LN2_HI;"),
-    "series_one_term_short": ("for (int k = 8; k >= 2; --k)", "for (int k = 8; k >= 3; --k)"),
+    "series_one_term_short": ("    p = fmaf(p, r, 0x1.555556p-3f);             /* 1/3! */\n", ""),
     "hg_sign": ("mu = ((1.0f + g2) - tmp * tmp) / (g + g);", "mu = ((1.0f + g2) - tmp) / (g + g);"),
     "rotation_sign": ("ny = (sint * ((dy * dz) * c + dx * s)) / t + dy * mu;",
                       "ny = (sint * ((dy * dz) * c - dx * s)) / t + dy * mu;"),
