@@ -597,9 +597,10 @@ soc_status soc_nn_adam(float *d_w, float *d_m, float *d_v, const float *d_g, int
  *                       x[c][2] = (ln clamp(T[c]) - ln clamp(T_prev[c]) -
  *                                  norm[4]) / norm[5]   (n_features = 3:
  *                       the last iteration's change; d_T_prev required),
- *                       rho from the uploaded grid.  norm: host double
- *                       [2 n_features], {mean, width} of each feature over
- *                       the training set (widths > 0).  The grid must be a
+ *                       each feature clipped to [-6, 6] after the
+ *                       standardisation; rho from the uploaded grid.  norm:
+ *                       host double [2 n_features], {mean, width} of each
+ *                       feature over the training set (widths > 0).  The grid must be a
  *                       regular cube whose side is a multiple of 8
  *                       (SOC_ERR_ARG otherwise).
  *   soc_seed_transform  for every cell (the network predicts the normalised

@@ -231,6 +231,7 @@ def adam_step(theta, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 # Seeding transform (float64)
 # ---------------------------------------------------------------------------
 T_MIN, T_MAX = 2.7, 3000.0
+FEATURE_CLIP = 6.0
 
 
 def seed_features(T, rho, norm, T_prev=None):
@@ -238,14 +239,15 @@ def seed_features(T, rho, norm, T_prev=None):
     lr_mean) / lr_std) and, given T_prev, ((ln T - ln T_prev) - ld_mean) /
     ld_std, with temperatures clamped to [T_MIN, T_MAX] and rho to at least
     1e-30.  norm: dict with lt_mean, lt_std, lr_mean, lr_std (ld_mean,
-    ld_std).  Returns (n, 2) or (n, 3)."""
+    ld_std).  Each standardised feature is clipped to [-FEATURE_CLIP,
+    FEATURE_CLIP].  Returns (n, 2) or (n, 3)."""
     lT = np.log(np.clip(np.asarray(T, np.float64), T_MIN, T_MAX))
     cols = [(lT - norm["lt_mean"]) / norm["lt_std"],
             (np.log(np.maximum(np.asarray(rho, np.float64), 1e-30)) - norm["lr_mean"]) / norm["lr_std"]]
     if T_prev is not None:
         lP = np.log(np.clip(np.asarray(T_prev, np.float64), T_MIN, T_MAX))
         cols.append((lT - lP - norm["ld_mean"]) / norm["ld_std"])
-    return np.stack(cols, axis=-1)
+    return np.clip(np.stack(cols, axis=-1), -FEATURE_CLIP, FEATURE_CLIP)
 
 
 def seed_transform(T1, pred, y_mean, y_std, shrink=1.0, envelope=None):

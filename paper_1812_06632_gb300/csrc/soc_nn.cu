@@ -677,21 +677,30 @@ __global__ void to_bf16_kernel(const float *src, long long n, bf16 *dst)
 }
 
 // Seeding transform of the learned temperature seed, in FP64 per cell.
-// Features (nf = 2 or 3 per cell):
+// Features (nf = 2 or 3 per cell), each standardised and then clipped to
+// [-6, 6] (rare cells far outside the training distribution, e.g. next to
+// a source, would otherwise dominate the first layer):
 //   x[c][0] = (ln clamp(T, 2.7, 3000) - norm[0]) / norm[1],
 //   x[c][1] = (ln max(rho, 1e-30) - norm[2]) / norm[3],
 //   x[c][2] = (ln clamp(T) - ln clamp(T_prev) - norm[4]) / norm[5]  (nf = 3).
+constexpr double kFeatureClip = 6.0;
+
+__device__ __forceinline__ float clip_feature(double v)
+{
+    return (float)fmin(fmax(v, -kFeatureClip), kFeatureClip);
+}
+
 __global__ void seed_features_kernel(const float *T, const float *T_prev, const float *rho, long long n, int nf,
                                      const SeedNorm nm, float *x)
 {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const double lt = log(fmin(fmax((double)T[c], kTMin), kTMax));
         const double r = fmax((double)rho[c], 1e-30);
-        x[nf * c] = (float)((lt - nm.v[0]) / nm.v[1]);
-        x[nf * c + 1] = (float)((log(r) - nm.v[2]) / nm.v[3]);
+        x[nf * c] = clip_feature((lt - nm.v[0]) / nm.v[1]);
+        x[nf * c + 1] = clip_feature((log(r) - nm.v[2]) / nm.v[3]);
         if (nf == 3) {
             const double lp = log(fmin(fmax((double)T_prev[c], kTMin), kTMax));
-            x[nf * c + 2] = (float)((lt - lp - nm.v[4]) / nm.v[5]);
+            x[nf * c + 2] = clip_feature((lt - lp - nm.v[4]) / nm.v[5]);
         }
     }
 }

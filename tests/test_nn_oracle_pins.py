@@ -236,8 +236,12 @@ def test_seed_features_standardise_their_own_statistics():
     np.testing.assert_allclose(x3[:, :2], x, rtol=1e-15)
     np.testing.assert_allclose(x3[:, 2], (d - d.mean()) / d.std(), rtol=1e-12, atol=1e-12)
     # identity normalisation gives the logarithms; T1 below 2.7 K and rho = 0 are clamped
-    x0 = nn.seed_features([1.0, 10.0], [0.0, 2.0], dict(lt_mean=0.0, lt_std=1.0, lr_mean=0.0, lr_std=1.0))
-    np.testing.assert_allclose(x0, [[np.log(2.7), np.log(1e-30)], [np.log(10.0), np.log(2.0)]], rtol=1e-15)
+    x0 = nn.seed_features([1.0, 10.0], [0.0, 2.0], dict(lt_mean=0.0, lt_std=1.0, lr_mean=-60.0, lr_std=20.0))
+    np.testing.assert_allclose(x0, [[np.log(2.7), (np.log(1e-30) + 60) / 20], [np.log(10.0), (np.log(2.0) + 60) / 20]],
+                               rtol=1e-15)
+    # standardised values beyond 6 are clipped
+    xc = nn.seed_features([3000.0, 2.7, 90.0], [1.0] * 3, dict(lt_mean=4.5, lt_std=0.5, lr_mean=0.0, lr_std=1.0))
+    np.testing.assert_allclose(xc[:, 0], [6.0, -6.0, (np.log(90.0) - 4.5) / 0.5], rtol=1e-15)
 
 
 def test_bf16_storage_rounds_every_stored_tensor_and_nothing_else():
