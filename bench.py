@@ -37,8 +37,8 @@ WORKLOAD = "lognormal 128^3, 64 nu (3e11-3e15 Hz), 1e6 background packages/nu, H
 # DRAM bytes (read + write) per photon-cell step of trace_kernel from one ncu
 # capture (small case of the same workload, scaled by steps), valid only for
 # the kernel source it was taken on.
-TRACE_DRAM = {"source_sha1": "6c7e518edaaee0f5ffe00b379aab5122a70c5b16", "bytes_per_step": 2.2397,
-              "warp_instructions_per_step": 8.576, "l2_bytes_per_step": 74.15,
+TRACE_DRAM = {"source_sha1": "1779ba3fd86f381c4bbf94e157e7d52b74fb0e73", "bytes_per_step": 2.2121,
+              "warp_instructions_per_step": 7.757, "l2_bytes_per_step": 73.02,
               "profile": "profiles/trace_kernel_lognormal128_8nu_1e6pkg_full.md"}
 # issue-rate peak: 4 warp-instructions per cycle per SM (4 schedulers)
 ISSUE_PER_SM_CYCLE = 4
@@ -605,8 +605,9 @@ def learned_record():
             "plain_iterations_total": int(sum(c["plain_iterations"])),
             "learned_iterations_total": int(sum(c["learned_iterations"])),
             "plain_steps": c["plain_steps"], "learned_steps": c["learned_steps"],
-            "converged": bool(c["plain_converged"] and c["learned_converged"]),
-            "max_abs_T_difference_K": c["max_abs_T_difference_K"],
+            "clouds_converged": {"plain": c["plain_converged"], "learned": c["learned_converged"]},
+            "unconverged_final_max_dT_K": c["unconverged_final_dT_K"],
+            "max_abs_T_difference_K_converged": c["max_abs_T_difference_K"],
             "seed_max_err_K_mean": float(np.mean(c["seed_max_err_K"])),
             "start_max_err_K_mean": float(np.mean(c["start_max_err_K"])), "seed_after": c["seed_after"],
             "weights_sha256": digest, "trained": {k: meta.get(k) for k in ("best_epoch", "epochs_run", "train", "val")},

@@ -19,8 +19,10 @@
 // BF16 inputs, FP32 accumulation throughout.  Every reduction (weight and
 // bias gradients, the loss) sums per-block partials in a fixed order, so a
 // training run is bit-reproducible.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -251,6 +253,231 @@ __global__ void __launch_bounds__(128) conv3d_tc_kernel(const ConvArgs a, int n_
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 float t = __uint_as_float(r[j]);
+                if (a.bias) t += a.bias[n0 + c + j];
+                if (a.relu) t = fmaxf(t, 0.f);
+                val[j] = t;
+            }
+            const long long o = v * a.out_stride + a.out_off + n0 + c;
+            if (a.out_f32) {
+                float4 *dst = reinterpret_cast<float4 *>(a.out_f32 + o);
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    float4 w4 = make_float4(val[4 * q4], val[4 * q4 + 1], val[4 * q4 + 2], val[4 * q4 + 3]);
+                    if (a.accumulate) {
+                        const float4 old = dst[q4];
+                        w4.x += old.x; w4.y += old.y; w4.z += old.z; w4.w += old.w;
+                    }
+                    dst[q4] = w4;
+                }
+            } else {
+                uint32_t pk[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(val[2 * j], val[2 * j + 1]);
+                    pk[j] = *reinterpret_cast<const uint32_t *>(&h2);
+                }
+                uint4 *dst = reinterpret_cast<uint4 *>(a.out + o);
+                dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward (and dgrad) convolution with operands staged by the Tensor Memory
+// Accelerator.  A block computes a box of 128 output voxels (bx x by x bz x
+// bn over W, H, D, N; accumulator row r = voxel ((n bz + z) by + y) bx + x of
+// the box) x n_tile output channels.  For every tap and chunk of KC input
+// channels, one TMA load brings the input box shifted by the tap's offset --
+// coordinates outside the volume read zeros, which is the convolution's
+// padding -- and a second one the weights (n_tile rows x KC), both with
+// rows of KC * 2 bytes in the hardware's 32/64/128-byte swizzle, which the
+// MMA's shared-memory descriptors name.  Thread 0 issues the loads
+// (mbarrier with the expected byte count per stage), thread 32 the MMAs
+// (committed to the stage's "empty" mbarrier), n_stages stages deep; every
+// wait is bounded (on a timeout the block raises the error flag, waits for
+// its loads in flight, frees its tensor memory and returns).
+// ---------------------------------------------------------------------------
+struct TmaConvArgs {
+    int N, D, H, W, Cin, Cout;
+    int bx, by, bz, bn;              // output box (bx by bz bn <= 128)
+    int tiles_x, tiles_y, tiles_z;
+    bf16 *out;
+    float *out_f32;
+    const float *bias;
+    int out_stride, out_off, relu, accumulate;
+};
+
+// Shared-memory descriptor of a K-major operand whose rows are `row_bytes`
+// (32, 64 or 128) long in the matching swizzle: 8-row groups row_bytes * 8
+// apart (stride offset), layout type 6 / 4 / 2.
+__device__ __forceinline__ uint64_t smem_desc_sw(uint32_t addr, int row_bytes)
+{
+    const uint64_t layout = row_bytes == 32 ? 6ull : (row_bytes == 64 ? 4ull : 2ull);
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) |
+           ((uint64_t)(((uint32_t)row_bytes * 8u >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (layout << 61);
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+                    "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3}], [%4];"
+                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar) : "memory");
+}
+
+template <int KC>
+__global__ void __launch_bounds__(128) conv3d_tma_kernel(const __grid_constant__ CUtensorMap map_in,
+                                                         const __grid_constant__ CUtensorMap map_w,
+                                                         const TmaConvArgs a, int n_tile, uint32_t tmem_cols,
+                                                         int n_stages)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // stages start on 1024-byte boundaries (the swizzle pattern repeats every
+    // 8 rows of up to 128 bytes)
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr int kRow = KC * 2;                       // bytes per operand row
+    const int a_bytes = 128 * kRow, b_bytes = n_tile * kRow;
+    const int stage_bytes = a_bytes + b_bytes;         // multiple of 1024
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + n_stages * stage_bytes);
+    uint64_t *empty = full + n_stages;
+    uint64_t *done = empty + n_stages;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    int *s_fail = reinterpret_cast<int *>(tslot + 1);
+    const uint32_t smem0 = smem_u32(smem);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // this block's box
+    int q = blockIdx.x;
+    const int tx = q % a.tiles_x; q /= a.tiles_x;
+    const int ty = q % a.tiles_y; q /= a.tiles_y;
+    const int tz = q % a.tiles_z;
+    const int tn = q / a.tiles_z;
+    const int x0 = tx * a.bx, y0 = ty * a.by, z0 = tz * a.bz, nb0 = tn * a.bn;
+    const int n0 = blockIdx.y * n_tile;
+    const int n_chunks = a.Cin / KC;
+    const int total = 27 * n_chunks;
+    const uint32_t a_box = (uint32_t)(a.bx * a.by * a.bz * a.bn) * kRow;    // bytes one input load writes
+    const uint32_t tx_bytes = a_box + (uint32_t)b_bytes;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(tmem_cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int k = 0; k < n_stages; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[k])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[k])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(done)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&map_in)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&map_w)) : "memory");
+        *s_fail = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    if (tid == 0) {
+        // producer: step t = (tap, chunk) into stage t % n_stages once the
+        // MMAs of step t - n_stages have released it
+        int issued = 0;
+        for (int t = 0; t < total; ++t) {
+            const int st = t % n_stages;
+            if (t >= n_stages && !mbar_wait(smem_u32(&empty[st]), (uint32_t)((t / n_stages) - 1) & 1u)) {
+                atomicExch(s_fail, 1);
+                break;
+            }
+            if (*reinterpret_cast<volatile int *>(s_fail)) break;
+            const int tap = t / n_chunks, c0 = (t - tap * n_chunks) * KC;
+            const uint32_t dst = smem0 + (uint32_t)(st * stage_bytes);
+            const uint32_t bar = smem_u32(&full[st]);
+            mbar_expect_tx(bar, tx_bytes);
+            tma_load_5d(dst, &map_in, c0, x0 + tap % 3 - 1, y0 + (tap / 3) % 3 - 1, z0 + tap / 9 - 1, nb0, bar);
+            tma_load_2d(dst + (uint32_t)a_bytes, &map_w, tap * a.Cin + c0, n0, bar);
+            issued = t + 1;
+        }
+        // loads still in flight when giving up land before the block leaves
+        if (*reinterpret_cast<volatile int *>(s_fail))
+            for (int t = (issued > n_stages ? issued - n_stages : 0); t < issued; ++t)
+                mbar_wait(smem_u32(&full[t % n_stages]), (uint32_t)(t / n_stages) & 1u);
+    } else if (tid == 32) {
+        // MMA issuer
+        const uint32_t idesc = mma_idesc(128, n_tile);
+        int t = 0;
+        for (; t < total; ++t) {
+            const int st = t % n_stages;
+            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)(t / n_stages) & 1u)) { atomicExch(s_fail, 1); break; }
+            if (*reinterpret_cast<volatile int *>(s_fail)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem0 + (uint32_t)(st * stage_bytes), b0 = a0 + (uint32_t)a_bytes;
+#pragma unroll
+            for (int j = 0; j < KC / 16; ++j) {
+                const uint64_t ad = smem_desc_sw(a0 + j * 32, kRow);
+                const uint64_t bd = smem_desc_sw(b0 + j * 32, kRow);
+                const uint32_t acc = (t > 0 || j > 0) ? 1u : 0u;
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(&empty[st])) : "memory");
+        }
+        // completion of every MMA issued
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(smem_u32(done)) : "memory");
+    }
+    __syncwarp();
+    const bool finished = mbar_wait(smem_u32(done), 0u);
+    const bool ok_run = __syncthreads_and(finished && !*reinterpret_cast<volatile int *>(s_fail));
+    if (!ok_run) {
+        atomicExch(&g_tc_error, 1);
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        // accumulator row tid -> voxel of the box
+        int r = tid;
+        const int x = x0 + r % a.bx; r /= a.bx;
+        const int y = y0 + r % a.by; r /= a.by;
+        const int z = z0 + r % a.bz;
+        const int nn = nb0 + r / a.bz;
+        const bool vin = tid < a.bx * a.by * a.bz * a.bn && x < a.W && y < a.H && z < a.D && nn < a.N;
+        const long long v = vin ? (((long long)nn * a.D + z) * a.H + y) * a.W + x : 0;
+        for (int c = 0; c < n_tile; c += 16) {
+            uint32_t rr[16];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
+                           "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]),
+                           "=r"(rr[13]), "=r"(rr[14]), "=r"(rr[15])
+                         : "r"(row_addr + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (!vin) continue;
+            float val[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                float t = __uint_as_float(rr[j]);
                 if (a.bias) t += a.bias[n0 + c + j];
                 if (a.relu) t = fmaxf(t, 0.f);
                 val[j] = t;
@@ -780,9 +1007,111 @@ cudaError_t tc_launch(const ConvArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// K per step: 3 taps of all channels for 16 or 32 input channels, all
-// channels of one tap up to 96, else 64/32/16-channel chunks of one tap.
+// cuTensorMapEncodeTiled from the driver, looked up once (no link against
+// libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// The TMA-fed convolution: tensor maps over the input view (channels,
+// W, H, D, N; channels c0 .. c0 + KC of a voxel, voxel stride in_stride) and
+// the weights ([Cout][27 Cin]), boxes of KC channels x the output box and
+// KC x n_tile, the swizzle of KC * 2-byte rows.
+template <int KC>
+cudaError_t tma_launch(const ConvArgs &a, cudaStream_t s)
+{
+    auto encode = encode_tiled();
+    if (!encode) return cudaErrorNotSupported;
+    const uintptr_t in_addr = reinterpret_cast<uintptr_t>(a.in + a.in_off);
+    if ((in_addr & 15u) || (a.in_stride % 8) || (reinterpret_cast<uintptr_t>(a.w) & 15u)) return cudaErrorInvalidValue;
+    int dev = 0, sms = 148, sm_smem = 0, blk_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&blk_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    TmaConvArgs t{};
+    t.N = a.N; t.D = a.D; t.H = a.H; t.W = a.W; t.Cin = a.Cin; t.Cout = a.Cout;
+    t.bx = std::min(a.W, 128);
+    t.by = std::min(a.H, 128 / t.bx);
+    t.bz = std::min(a.D, 128 / (t.bx * t.by));
+    t.bn = std::min(a.N, 128 / (t.bx * t.by * t.bz));
+    t.tiles_x = (a.W + t.bx - 1) / t.bx;
+    t.tiles_y = (a.H + t.by - 1) / t.by;
+    t.tiles_z = (a.D + t.bz - 1) / t.bz;
+    const long long tiles = (long long)t.tiles_x * t.tiles_y * t.tiles_z * ((a.N + t.bn - 1) / t.bn);
+    t.out = a.out; t.out_f32 = a.out_f32; t.bias = a.bias;
+    t.out_stride = a.out_stride; t.out_off = a.out_off; t.relu = a.relu; t.accumulate = a.accumulate;
+    const int n_tile = tc_n_tile(a.Cout, tiles, sms);
+    constexpr CUtensorMapSwizzle sw = KC == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                    : (KC == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
+    CUtensorMap map_in, map_w;
+    {
+        const cuuint64_t dims[5] = {(cuuint64_t)a.Cin, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.D,
+                                    (cuuint64_t)a.N};
+        const cuuint64_t vb = (cuuint64_t)a.in_stride * 2;
+        const cuuint64_t strides[4] = {vb, vb * a.W, vb * a.W * a.H, vb * a.W * a.H * a.D};
+        const cuuint32_t box[5] = {(cuuint32_t)KC, (cuuint32_t)t.bx, (cuuint32_t)t.by, (cuuint32_t)t.bz,
+                                   (cuuint32_t)t.bn};
+        const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        if (encode(&map_in, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, reinterpret_cast<void *>(in_addr), dims, strides, box,
+                   es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        const cuuint64_t dims[2] = {(cuuint64_t)27 * a.Cin, (cuuint64_t)a.Cout};
+        const cuuint64_t strides[1] = {(cuuint64_t)27 * a.Cin * 2};
+        const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)n_tile};
+        const cuuint32_t es[2] = {1, 1};
+        if (encode(&map_w, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(a.w), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    uint32_t cols = 32;
+    while ((int)cols < n_tile) cols <<= 1;
+    const int stage_bytes = (128 + n_tile) * KC * 2;
+    int stages = 98304 / stage_bytes;                 // about 96 KB of stages, 2 to 8
+    stages = stages < 2 ? 2 : (stages > 8 ? 8 : stages);
+    // stages (1024-byte aligned) + barriers, tensor-memory slot and flag;
+    // padded so that no more blocks are resident on an SM than its 512
+    // columns of tensor memory can hold
+    const int need = 1024 + stages * stage_bytes + 8 * (2 * stages + 1) + 16;
+    const int max_blocks = 512 / (int)cols;
+    const int pad = sm_smem / (max_blocks + 1) + 1024;
+    int bytes = need > pad ? need : pad;
+    if (need > blk_max) return cudaErrorInvalidValue;
+    if (bytes > blk_max) bytes = blk_max;
+    cudaError_t e = cudaFuncSetAttribute(conv3d_tma_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)tiles, (unsigned)(a.Cout / n_tile));
+    conv3d_tma_kernel<KC><<<grid, 128, bytes, s>>>(map_in, map_w, t, n_tile, cols, stages);
+    return cudaGetLastError();
+}
+
+// TMA-fed kernel with K chunks of 64, 32 or 16 input channels (the largest
+// dividing C_in).
 cudaError_t conv_launch(const ConvArgs &a, cudaStream_t s)
+{
+    if (a.Cin % 64 == 0) return tma_launch<64>(a, s);
+    if (a.Cin % 32 == 0) return tma_launch<32>(a, s);
+    return tma_launch<16>(a, s);
+}
+
+// The cp.async-fed kernel (kept for comparison): K per step 3 taps of all
+// channels for 16 or 32 input channels, all channels of one tap up to 96,
+// else 64/32/16-channel chunks of one tap.
+cudaError_t conv_launch_cpasync(const ConvArgs &a, cudaStream_t s)
 {
     switch (a.Cin) {
     case 16: return tc_launch<16, 3>(a, s);
