@@ -10,7 +10,7 @@
 // Convolutions (3x3x3, stride 1, zero padding 1) are implicit GEMMs:
 //   forward:  M = voxels, N = C_out, K = 27 C_in (tap-major, channel-minor),
 //             on the tcgen05 tensor cores with the accumulator in tensor
-//             memory;
+//             memory, operands staged by the Tensor Memory Accelerator;
 //   dgrad:    the forward kernel with the weights flipped in space and
 //             transposed in channels;
 //   wgrad:    M = C_out, N = C_in per tap, K = voxels (split over blocks
@@ -50,23 +50,9 @@ struct ConvArgs {
 };
 
 // ---------------------------------------------------------------------------
-// Forward (and dgrad) convolution on the 5th-generation tensor cores (tcgen05).
-//
-// A block of 128 threads computes 128 output voxels (the 128 lanes of the
-// accumulator in tensor memory) x n_tile output channels (columns).  K runs
-// over the 27 taps and, per tap, chunks of KC input channels; each chunk of
-// A (128 voxels x KC) and B (n_tile channels x KC) is copied to shared
-// memory in the canonical K-major layout without swizzling (8-row x 16-byte
-// core matrices, 128 bytes each: core (g, c) of rows 8g..8g+7 and elements
-// 8c..8c+7 at ((g * KC/8) + c) * 128 bytes, so the leading-dimension offset
-// (next core along K) is 128 B and the stride offset (next 8 rows) KC * 16 B).
-// Two stages alternate: thread 0 issues KC/16 MMAs (M = 128, N = n_tile,
-// K = 16, BF16 x BF16 -> FP32) per chunk and commits them to the stage's
-// mbarrier, which the block waits on before it overwrites that stage.  The
-// epilogue reads the accumulator with tcgen05.ld (warp w reads lanes
-// 32w..32w+31, i.e. its own 32 voxels), adds the bias, applies the ReLU and
-// stores BF16 or (accumulating) FP32.
-// Every wait is bounded: on a timeout the block raises the error flag, frees
+// Helpers of the tensor-core kernels (tcgen05.mma with the accumulator in
+// tensor memory; shared-memory operand descriptors; bounded mbarrier waits).
+// Every wait is bounded: on a timeout a block raises the error flag, frees
 // its tensor memory and returns.
 // ---------------------------------------------------------------------------
 __device__ int g_tc_error;                    // set by a block whose wait timed out
@@ -108,186 +94,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-
-// A step covers TK consecutive taps x KC channels (TK > 1 only with KC = C_in,
-// so that the weights of consecutive taps are contiguous): K = TK * KC.
-template <int KC, int TK>
-__global__ void __launch_bounds__(128) conv3d_tc_kernel(const ConvArgs a, int n_tile, uint32_t tmem_cols,
-                                                        int n_stages)
-{
-    extern __shared__ __align__(1024) uint8_t smem[];
-    constexpr int kPpt = KC / 8;                      // 16-byte pieces per tap and row
-    constexpr int kPpr = TK * kPpt;                   // 16-byte pieces per row of a step
-    const int a_bytes = 128 * TK * KC * 2, b_bytes = n_tile * TK * KC * 2;
-    const int stage_bytes = a_bytes + b_bytes;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + n_stages * stage_bytes);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + n_stages * stage_bytes + 8 * n_stages);
-    const uint32_t smem0 = smem_u32(smem);
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const long long V = (long long)a.N * a.D * a.H * a.W;
-    const long long v = (long long)blockIdx.x * 128 + tid;
-    const int n0 = blockIdx.y * n_tile;
-
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(tslot)), "r"(tmem_cols) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (tid == 0) {
-        for (int k = 0; k < n_stages; ++k)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[k])) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tslot;
-
-    // this thread's voxel (row of A and of the accumulator)
-    const bool vin = v < V;
-    int n = 0, z = 0, y = 0, x = 0;
-    if (vin) {
-        long long q = v;
-        x = (int)(q % a.W); q /= a.W;
-        y = (int)(q % a.H); q /= a.H;
-        z = (int)(q % a.D); n = (int)(q / a.D);
-    }
-    const uint32_t idesc = mma_idesc(128, n_tile);
-    const int n_chunks = a.Cin / KC;
-    const int total = (27 / TK) * n_chunks;
-    const uint32_t r_off = (uint32_t)(((tid >> 3) * kPpr * 8 + (tid & 7)) * 16);   // row tid, core column 0
-
-    // copies of step t into its stage (t % n_stages); one commit group per step
-    auto issue = [&](int t) {
-        if (t < total) {
-            const uint32_t st = smem0 + (uint32_t)((t % n_stages) * stage_bytes);
-            const int tg = t / n_chunks, c0 = (t - tg * n_chunks) * KC;
-#pragma unroll
-            for (int i = 0; i < TK; ++i) {
-                const int tap = tg * TK + i;
-                const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
-                const bool ok = vin && zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-                const bf16 *src = a.in +
-                                  (ok ? ((((long long)n * a.D + zz) * a.H + yy) * a.W + xx) * a.in_stride : 0) +
-                                  a.in_off + c0;
-#pragma unroll
-                for (int c = 0; c < kPpt; ++c)
-                    cp_async16(st + r_off + (i * kPpt + c) * 128, src + c * 8, ok ? 16u : 0u);
-            }
-            // weights of taps tg*TK .. tg*TK + TK - 1 (contiguous when TK > 1)
-            for (int i = tid; i < n_tile * kPpr; i += 128) {
-                const int co = i / kPpr, c = i - co * kPpr;
-                cp_async16(st + a_bytes + ((co >> 3) * kPpr * 8 + (co & 7)) * 16 + c * 128,
-                           a.w + ((long long)(n0 + co) * 27 + tg * TK) * a.Cin + c0 + c * 8, 16u);
-            }
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-
-    // a timed-out wait is turned into a block-wide decision (so every thread
-    // passes the same barriers) and ends the main loop
-    // copies run n_stages - 2 steps ahead: at step t every thread waits (on
-    // the stage's mbarrier) for the multiplies of step t - 2, refills that
-    // stage with the copies of step t + n_stages - 2, waits for its own
-    // copies of step t, and one barrier per step hands the stage to the MMA
-    // thread; the multiplies of steps t - 1 and t keep the tensor core busy
-    bool ok_run = true;
-    int last = -1;                                    // last step whose MMAs were committed
-    const int ahead = n_stages - 2;
-    for (int t = 0; t < ahead; ++t) issue(t);
-    for (int step = 0; step < total; ++step) {
-        const int s = step % n_stages;
-        const int nxt = step + ahead;
-        bool waited = true;
-        if (step >= 2 && nxt < total) {
-            const int prev = step - 2;
-            waited = mbar_wait(smem_u32(&mbar[prev % n_stages]), (uint32_t)(prev / n_stages) & 1u);
-        }
-        if (waited) issue(nxt);
-        else asm volatile("cp.async.commit_group;" ::: "memory");
-        // this step's copies: all but the newest `ahead` groups are complete
-        if (ahead >= 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
-        else asm volatile("cp.async.wait_group 1;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        if (!__syncthreads_and(waited)) { ok_run = false; break; }
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem0 + (uint32_t)(s * stage_bytes), b0 = a0 + (uint32_t)a_bytes;
-#pragma unroll
-            for (int j = 0; j < TK * KC / 16; ++j) {
-                const uint64_t ad = smem_desc(a0 + j * 256, 128, kPpr * 128);
-                const uint64_t bd = smem_desc(b0 + j * 256, 128, kPpr * 128);
-                const uint32_t acc = (step > 0 || j > 0) ? 1u : 0u;
-                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                             :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(&mbar[s])) : "memory");
-        }
-        last = step;
-    }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    // the last commit covers every MMA issued before it
-    {
-        bool done = true;
-        if (last >= 0) done = mbar_wait(smem_u32(&mbar[last % n_stages]), (uint32_t)(last / n_stages) & 1u);
-        ok_run = __syncthreads_and(ok_run && done);
-    }
-    if (!ok_run) {
-        atomicExch(&g_tc_error, 1);
-    } else {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c = 0; c < n_tile; c += 16) {
-            uint32_t r[16];
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                           "=r"(r[14]), "=r"(r[15])
-                         : "r"(row_addr + (uint32_t)c));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (!vin) continue;
-            float val[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                float t = __uint_as_float(r[j]);
-                if (a.bias) t += a.bias[n0 + c + j];
-                if (a.relu) t = fmaxf(t, 0.f);
-                val[j] = t;
-            }
-            const long long o = v * a.out_stride + a.out_off + n0 + c;
-            if (a.out_f32) {
-                float4 *dst = reinterpret_cast<float4 *>(a.out_f32 + o);
-#pragma unroll
-                for (int q4 = 0; q4 < 4; ++q4) {
-                    float4 w4 = make_float4(val[4 * q4], val[4 * q4 + 1], val[4 * q4 + 2], val[4 * q4 + 3]);
-                    if (a.accumulate) {
-                        const float4 old = dst[q4];
-                        w4.x += old.x; w4.y += old.y; w4.z += old.z; w4.w += old.w;
-                    }
-                    dst[q4] = w4;
-                }
-            } else {
-                uint32_t pk[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(val[2 * j], val[2 * j + 1]);
-                    pk[j] = *reinterpret_cast<const uint32_t *>(&h2);
-                }
-                uint4 *dst = reinterpret_cast<uint4 *>(a.out + o);
-                dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols) : "memory");
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -974,39 +780,6 @@ inline int tc_n_tile(int Cout, long long v_tiles, int sms)
     return t;
 }
 
-template <int KC, int TK>
-cudaError_t tc_launch(const ConvArgs &a, cudaStream_t s)
-{
-    const long long V = (long long)a.N * a.D * a.H * a.W;
-    const long long v_tiles = (V + 127) / 128;
-    int dev = 0, sms = 148, sm_smem = 0, blk_max = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&blk_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int n_tile = tc_n_tile(a.Cout, v_tiles, sms);
-    uint32_t cols = 32;
-    while ((int)cols < n_tile) cols <<= 1;
-    // stages of A + B copies: 3 or 4 (copies 1 or 2 steps ahead), within
-    // 72 KB where possible (keeps 3 blocks per SM on the larger tiles)
-    const int stage_bytes = (128 + n_tile) * TK * KC * 2;
-    int stages = 73728 / stage_bytes;
-    stages = stages < 3 ? 3 : (stages > 4 ? 4 : stages);
-    // shared memory padded so that no more blocks are resident on an SM than
-    // its 512 columns of tensor memory can hold
-    const int need = stages * stage_bytes + 8 * stages + 16;
-    const int max_blocks = 512 / (int)cols;
-    const int pad = sm_smem / (max_blocks + 1) + 1024;
-    int bytes = need > pad ? need : pad;
-    if (bytes > blk_max) bytes = blk_max;
-    if (need > blk_max) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(conv3d_tc_kernel<KC, TK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)v_tiles, (unsigned)(a.Cout / n_tile));
-    conv3d_tc_kernel<KC, TK><<<grid, 128, bytes, s>>>(a, n_tile, cols, stages);
-    return cudaGetLastError();
-}
-
 // cuTensorMapEncodeTiled from the driver, looked up once (no link against
 // libcuda).
 PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
@@ -1106,25 +879,6 @@ cudaError_t conv_launch(const ConvArgs &a, cudaStream_t s)
     if (a.Cin % 64 == 0) return tma_launch<64>(a, s);
     if (a.Cin % 32 == 0) return tma_launch<32>(a, s);
     return tma_launch<16>(a, s);
-}
-
-// The cp.async-fed kernel (kept for comparison): K per step 3 taps of all
-// channels for 16 or 32 input channels, all channels of one tap up to 96,
-// else 64/32/16-channel chunks of one tap.
-cudaError_t conv_launch_cpasync(const ConvArgs &a, cudaStream_t s)
-{
-    switch (a.Cin) {
-    case 16: return tc_launch<16, 3>(a, s);
-    case 32: return tc_launch<32, 3>(a, s);
-    case 48: return tc_launch<48, 1>(a, s);
-    case 64: return tc_launch<64, 1>(a, s);
-    case 80: return tc_launch<80, 1>(a, s);
-    case 96: return tc_launch<96, 1>(a, s);
-    default: break;
-    }
-    if (a.Cin % 64 == 0) return tc_launch<64, 1>(a, s);
-    if (a.Cin % 32 == 0) return tc_launch<32, 1>(a, s);
-    return tc_launch<16, 1>(a, s);
 }
 
 // Launch plan of the weight gradient: tiles and the split of the voxels into
