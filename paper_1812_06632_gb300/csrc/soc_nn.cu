@@ -105,11 +105,11 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
 // coordinates outside the volume read zeros, which is the convolution's
 // padding -- and a second one the weights (n_tile rows x KC), both with
 // rows of KC * 2 bytes in the hardware's 32/64/128-byte swizzle, which the
-// MMA's shared-memory descriptors name.  Thread 0 issues the loads
-// (mbarrier with the expected byte count per stage), thread 32 the MMAs
+// MMA's shared-memory descriptors name.  One thread issues the loads
+// (mbarrier with the expected byte count per stage), another the MMAs
 // (committed to the stage's "empty" mbarrier), n_stages stages deep; every
 // wait is bounded (on a timeout the block raises the error flag, waits for
-// its loads in flight, frees its tensor memory and returns).
+// its loads and MMAs in flight, frees its tensor memory and returns).
 // ---------------------------------------------------------------------------
 struct TmaConvArgs {
     int N, D, H, W, Cin, Cout;
@@ -152,11 +152,21 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
                  :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar) : "memory");
 }
 
+// Persistent and warp-specialised: a block of 6 warps walks the output
+// boxes blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 4 (lane 0) issues the
+// TMA loads into n_stages shared-memory stages, warp 5 (lane 0) the MMAs into
+// one of two accumulators in tensor memory (2 x n_tile columns), and warps
+// 0-3 (tensor-memory lanes 32w .. 32w + 31) drain the other accumulator:
+// loads of the next box, MMAs and the epilogue of the previous one overlap.
+// Barriers: full/empty per stage (TMA bytes arrived / MMAs done with it),
+// acc_full/acc_empty per accumulator (MMAs of a box done / epilogue done).
+constexpr int kConvThreads = 192;
+
 template <int KC>
-__global__ void __launch_bounds__(128) conv3d_tma_kernel(const __grid_constant__ CUtensorMap map_in,
-                                                         const __grid_constant__ CUtensorMap map_w,
-                                                         const TmaConvArgs a, int n_tile, uint32_t tmem_cols,
-                                                         int n_stages)
+__global__ void __launch_bounds__(kConvThreads) conv3d_tma_kernel(const __grid_constant__ CUtensorMap map_in,
+                                                                  const __grid_constant__ CUtensorMap map_w,
+                                                                  const TmaConvArgs a, int n_tile, uint32_t tmem_cols,
+                                                                  int n_stages)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // stages start on 1024-byte boundaries (the swizzle pattern repeats every
@@ -167,25 +177,21 @@ __global__ void __launch_bounds__(128) conv3d_tma_kernel(const __grid_constant__
     const int stage_bytes = a_bytes + b_bytes;         // multiple of 1024
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + n_stages * stage_bytes);
     uint64_t *empty = full + n_stages;
-    uint64_t *done = empty + n_stages;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    uint64_t *acc_full = empty + n_stages;             // [2]
+    uint64_t *acc_empty = acc_full + 2;                // [2]
+    uint64_t *drain = acc_empty + 2;                   // MMAs done, after a failure
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(drain + 1);
     int *s_fail = reinterpret_cast<int *>(tslot + 1);
+    volatile int *fail = s_fail;
     const uint32_t smem0 = smem_u32(smem);
-    const int tid = threadIdx.x, warp = tid >> 5;
-    // this block's box
-    int q = blockIdx.x;
-    const int tx = q % a.tiles_x; q /= a.tiles_x;
-    const int ty = q % a.tiles_y; q /= a.tiles_y;
-    const int tz = q % a.tiles_z;
-    const int tn = q / a.tiles_z;
-    const int x0 = tx * a.bx, y0 = ty * a.by, z0 = tz * a.bz, nb0 = tn * a.bn;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n0 = blockIdx.y * n_tile;
     const int n_chunks = a.Cin / KC;
-    const int total = 27 * n_chunks;
-    const uint32_t a_box = (uint32_t)(a.bx * a.by * a.bz * a.bn) * kRow;    // bytes one input load writes
-    const uint32_t tx_bytes = a_box + (uint32_t)b_bytes;
+    const int steps = 27 * n_chunks;                   // per box
+    const int n_boxes = a.tiles_x * a.tiles_y * a.tiles_z * ((a.N + a.bn - 1) / a.bn);
+    const uint32_t tx_bytes = (uint32_t)(a.bx * a.by * a.bz * a.bn) * kRow + (uint32_t)b_bytes;
 
-    if (warp == 0) {
+    if (warp == 5) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(tslot)), "r"(tmem_cols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -195,10 +201,12 @@ __global__ void __launch_bounds__(128) conv3d_tma_kernel(const __grid_constant__
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[k])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[k])) : "memory");
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(done)) : "memory");
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&acc_full[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" :: "r"(smem_u32(&acc_empty[b])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(drain)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&map_in)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&map_w)) : "memory");
         *s_fail = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -206,116 +214,173 @@ __global__ void __launch_bounds__(128) conv3d_tma_kernel(const __grid_constant__
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
 
-    if (tid == 0) {
-        // producer: step t = (tap, chunk) into stage t % n_stages once the
-        // MMAs of step t - n_stages have released it
-        int issued = 0;
-        for (int t = 0; t < total; ++t) {
-            const int st = t % n_stages;
-            if (t >= n_stages && !mbar_wait(smem_u32(&empty[st]), (uint32_t)((t / n_stages) - 1) & 1u)) {
-                atomicExch(s_fail, 1);
-                break;
-            }
-            if (*reinterpret_cast<volatile int *>(s_fail)) break;
-            const int tap = t / n_chunks, c0 = (t - tap * n_chunks) * KC;
-            const uint32_t dst = smem0 + (uint32_t)(st * stage_bytes);
-            const uint32_t bar = smem_u32(&full[st]);
-            mbar_expect_tx(bar, tx_bytes);
-            tma_load_5d(dst, &map_in, c0, x0 + tap % 3 - 1, y0 + (tap / 3) % 3 - 1, z0 + tap / 9 - 1, nb0, bar);
-            tma_load_2d(dst + (uint32_t)a_bytes, &map_w, tap * a.Cin + c0, n0, bar);
-            issued = t + 1;
-        }
-        // loads still in flight when giving up land before the block leaves
-        if (*reinterpret_cast<volatile int *>(s_fail))
-            for (int t = (issued > n_stages ? issued - n_stages : 0); t < issued; ++t)
-                mbar_wait(smem_u32(&full[t % n_stages]), (uint32_t)(t / n_stages) & 1u);
-    } else if (tid == 32) {
-        // MMA issuer
-        const uint32_t idesc = mma_idesc(128, n_tile);
-        int t = 0;
-        for (; t < total; ++t) {
-            const int st = t % n_stages;
-            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)(t / n_stages) & 1u)) { atomicExch(s_fail, 1); break; }
-            if (*reinterpret_cast<volatile int *>(s_fail)) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem0 + (uint32_t)(st * stage_bytes), b0 = a0 + (uint32_t)a_bytes;
-#pragma unroll
-            for (int j = 0; j < KC / 16; ++j) {
-                const uint64_t ad = smem_desc_sw(a0 + j * 32, kRow);
-                const uint64_t bd = smem_desc_sw(b0 + j * 32, kRow);
-                const uint32_t acc = (t > 0 || j > 0) ? 1u : 0u;
-                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                             :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(&empty[st])) : "memory");
-        }
-        // completion of every MMA issued
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     :: "r"(smem_u32(done)) : "memory");
-    }
-    __syncwarp();
-    const bool finished = mbar_wait(smem_u32(done), 0u);
-    const bool ok_run = __syncthreads_and(finished && !*reinterpret_cast<volatile int *>(s_fail));
-    if (!ok_run) {
-        atomicExch(&g_tc_error, 1);
-    } else {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16);
-        // accumulator row tid -> voxel of the box
-        int r = tid;
-        const int x = x0 + r % a.bx; r /= a.bx;
-        const int y = y0 + r % a.by; r /= a.by;
-        const int z = z0 + r % a.bz;
-        const int nn = nb0 + r / a.bz;
-        const bool vin = tid < a.bx * a.by * a.bz * a.bn && x < a.W && y < a.H && z < a.D && nn < a.N;
-        const long long v = vin ? (((long long)nn * a.D + z) * a.H + y) * a.W + x : 0;
-        for (int c = 0; c < n_tile; c += 16) {
-            uint32_t rr[16];
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                         : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
-                           "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]),
-                           "=r"(rr[13]), "=r"(rr[14]), "=r"(rr[15])
-                         : "r"(row_addr + (uint32_t)c));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (!vin) continue;
-            float val[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                float t = __uint_as_float(rr[j]);
-                if (a.bias) t += a.bias[n0 + c + j];
-                if (a.relu) t = fmaxf(t, 0.f);
-                val[j] = t;
-            }
-            const long long o = v * a.out_stride + a.out_off + n0 + c;
-            if (a.out_f32) {
-                float4 *dst = reinterpret_cast<float4 *>(a.out_f32 + o);
-#pragma unroll
-                for (int q4 = 0; q4 < 4; ++q4) {
-                    float4 w4 = make_float4(val[4 * q4], val[4 * q4 + 1], val[4 * q4 + 2], val[4 * q4 + 3]);
-                    if (a.accumulate) {
-                        const float4 old = dst[q4];
-                        w4.x += old.x; w4.y += old.y; w4.z += old.z; w4.w += old.w;
+    if (warp == 4) {
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&map_in)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&map_w)) : "memory");
+            // producer: step g = (box, tap, chunk) into stage st = g mod
+            // n_stages, in round ph = floor(g / n_stages) mod 2, once the MMAs
+            // of step g - n_stages have released it
+            int st = 0, issued = 0;
+            uint32_t ph = 0;
+            for (int box = blockIdx.x; box < n_boxes && !*fail; box += gridDim.x) {
+                int q = box;
+                const int tx = q % a.tiles_x; q /= a.tiles_x;
+                const int ty = q % a.tiles_y; q /= a.tiles_y;
+                const int tz = q % a.tiles_z;
+                const int tn = q / a.tiles_z;
+                const int x0 = tx * a.bx - 1, y0 = ty * a.by - 1, z0 = tz * a.bz - 1, nb0 = tn * a.bn;
+                bool stop = false;
+                for (int tap = 0, dx = 0, dy = 0, dz = 0; tap < 27 && !stop; ++tap) {
+                    for (int c0 = 0; c0 < a.Cin; c0 += KC) {
+                        if (issued >= n_stages && !mbar_wait(smem_u32(&empty[st]), ph ^ 1u)) {
+                            atomicExch(s_fail, 1);
+                            stop = true;
+                            break;
+                        }
+                        if (*fail) { stop = true; break; }
+                        const uint32_t dst = smem0 + (uint32_t)(st * stage_bytes);
+                        const uint32_t bar = smem_u32(&full[st]);
+                        mbar_expect_tx(bar, tx_bytes);
+                        tma_load_5d(dst, &map_in, c0, x0 + dx, y0 + dy, z0 + dz, nb0, bar);
+                        tma_load_2d(dst + (uint32_t)a_bytes, &map_w, tap * a.Cin + c0, n0, bar);
+                        ++issued;
+                        if (++st == n_stages) { st = 0; ph ^= 1u; }
                     }
-                    dst[q4] = w4;
+                    // tap = 9 dz + 3 dy + dx
+                    if (++dx == 3) { dx = 0; if (++dy == 3) { dy = 0; ++dz; } }
                 }
-            } else {
-                uint32_t pk[8];
+                if (stop) break;
+            }
+            // the last stages: after a failure the loads in flight land, else
+            // the MMAs' releases of them arrive, before the block leaves
+            const bool failed = *fail;
+            for (int h = (issued > n_stages ? issued - n_stages : 0); h < issued; ++h)
+                mbar_wait(smem_u32(failed ? &full[h % n_stages] : &empty[h % n_stages]), (uint32_t)(h / n_stages) & 1u);
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // MMA issuer: box i into accumulator i % 2, once the epilogue has
+            // drained box i - 2 from it
+            const uint32_t idesc = mma_idesc(128, n_tile);
+            int st = 0, i = 0;
+            uint32_t ph = 0;
+            for (int box = blockIdx.x; box < n_boxes && !*fail; box += gridDim.x, ++i) {
+                const int b = i & 1;
+                if (i >= 2 && !mbar_wait(smem_u32(&acc_empty[b]), (uint32_t)((i >> 1) - 1) & 1u)) {
+                    atomicExch(s_fail, 1);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc_addr = tmem + (uint32_t)(b * n_tile);
+                for (int t = 0; t < steps; ++t) {
+                    if (!mbar_wait(smem_u32(&full[st]), ph)) {
+                        atomicExch(s_fail, 1);
+                        break;
+                    }
+                    if (*fail) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem0 + (uint32_t)(st * stage_bytes), b0 = a0 + (uint32_t)a_bytes;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(val[2 * j], val[2 * j + 1]);
-                    pk[j] = *reinterpret_cast<const uint32_t *>(&h2);
+                    for (int j = 0; j < KC / 16; ++j) {
+                        const uint64_t ad = smem_desc_sw(a0 + j * 32, kRow);
+                        const uint64_t bd = smem_desc_sw(b0 + j * 32, kRow);
+                        const uint32_t acc = (t > 0 || j > 0) ? 1u : 0u;
+                        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                     :: "r"(acc_addr), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(smem_u32(&empty[st])) : "memory");
+                    if (++st == n_stages) { st = 0; ph ^= 1u; }
                 }
-                uint4 *dst = reinterpret_cast<uint4 *>(a.out + o);
-                dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                // the box's accumulator is complete once its MMAs are
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(smem_u32(&acc_full[b])) : "memory");
             }
         }
+    } else {
+        // epilogue: warps 0-3, accumulator row tid = voxel of the box
+        int i = 0;
+        for (int box = blockIdx.x; box < n_boxes; box += gridDim.x, ++i) {
+            const int b = i & 1;
+            const bool ready = mbar_wait(smem_u32(&acc_full[b]), (uint32_t)(i >> 1) & 1u);
+            if (__any_sync(0xffffffffu, !ready || *fail)) { atomicExch(s_fail, 1); break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            int q = box;
+            const int tx = q % a.tiles_x; q /= a.tiles_x;
+            const int ty = q % a.tiles_y; q /= a.tiles_y;
+            const int tz = q % a.tiles_z;
+            const int tn = q / a.tiles_z;
+            int r = tid;
+            const int x = tx * a.bx + r % a.bx; r /= a.bx;
+            const int y = ty * a.by + r % a.by; r /= a.by;
+            const int z = tz * a.bz + r % a.bz;
+            const int nn = tn * a.bn + r / a.bz;
+            const bool vin = tid < a.bx * a.by * a.bz * a.bn && x < a.W && y < a.H && z < a.D && nn < a.N;
+            const long long v = vin ? (((long long)nn * a.D + z) * a.H + y) * a.W + x : 0;
+            const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * n_tile);
+            for (int c = 0; c < n_tile; c += 16) {
+                uint32_t rr[16];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]),
+                               "=r"(rr[6]), "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]),
+                               "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]), "=r"(rr[15])
+                             : "r"(row_addr + (uint32_t)c));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (!vin) continue;
+                float val[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float t = __uint_as_float(rr[j]);
+                    if (a.bias) t += a.bias[n0 + c + j];
+                    if (a.relu) t = fmaxf(t, 0.f);
+                    val[j] = t;
+                }
+                const long long o = v * a.out_stride + a.out_off + n0 + c;
+                if (a.out_f32) {
+                    float4 *dst = reinterpret_cast<float4 *>(a.out_f32 + o);
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        float4 w4 = make_float4(val[4 * q4], val[4 * q4 + 1], val[4 * q4 + 2], val[4 * q4 + 3]);
+                        if (a.accumulate) {
+                            const float4 old = dst[q4];
+                            w4.x += old.x; w4.y += old.y; w4.z += old.z; w4.w += old.w;
+                        }
+                        dst[q4] = w4;
+                    }
+                } else {
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(val[2 * j], val[2 * j + 1]);
+                        pk[j] = *reinterpret_cast<const uint32_t *>(&h2);
+                    }
+                    uint4 *dst = reinterpret_cast<uint4 *>(a.out + o);
+                    dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&acc_empty[b])) : "memory");
+        }
     }
+    // every MMA of the block has completed before its tensor memory is freed:
+    // the epilogue waited for the last box's accumulator, or, after a
+    // failure, the MMA thread waits (bounded) for all it issued
+    __syncwarp();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    const bool ok = __syncthreads_and(!*fail);
+    if (!ok) {
+        if (tid == 0) atomicExch(&g_tc_error, 1);
+        if (warp == 5 && lane == 0) {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(drain)) : "memory");
+            mbar_wait(smem_u32(drain), 0);
+        }
+    }
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 5) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols) : "memory");
     }
@@ -851,24 +916,43 @@ cudaError_t tma_launch(const ConvArgs &a, cudaStream_t s)
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
+    // two accumulators of n_tile columns
     uint32_t cols = 32;
-    while ((int)cols < n_tile) cols <<= 1;
+    while ((int)cols < 2 * n_tile) cols <<= 1;
+    if (cols > 512) return cudaErrorInvalidValue;
+    // blocks per SM: at most what 512 columns of tensor memory hold, and 8;
+    // the rest of the SM's shared memory split among them as stages, 2 to 8
+    const int per_sm = std::min(8, std::min(512 / (int)cols, 2048 / kConvThreads));
     const int stage_bytes = (128 + n_tile) * KC * 2;
-    int stages = 98304 / stage_bytes;                 // about 96 KB of stages, 2 to 8
+    const int fixed = 1024 + 8 * (2 * 8 + 5) + 8;     // alignment, barriers, slot and flag
+    int stages = (sm_smem / per_sm - 1024 - fixed) / stage_bytes;
     stages = stages < 2 ? 2 : (stages > 8 ? 8 : stages);
-    // stages (1024-byte aligned) + barriers, tensor-memory slot and flag;
-    // padded so that no more blocks are resident on an SM than its 512
-    // columns of tensor memory can hold
-    const int need = 1024 + stages * stage_bytes + 8 * (2 * stages + 1) + 16;
-    const int max_blocks = 512 / (int)cols;
-    const int pad = sm_smem / (max_blocks + 1) + 1024;
-    int bytes = need > pad ? need : pad;
+    const int need = 1024 + stages * stage_bytes + 8 * (2 * stages + 5) + 8;
     if (need > blk_max) return cudaErrorInvalidValue;
+    // padded so that no more than per_sm blocks are resident on an SM
+    const int pad = sm_smem / (per_sm + 1) + 1024;
+    int bytes = need > pad ? need : pad;
     if (bytes > blk_max) bytes = blk_max;
     cudaError_t e = cudaFuncSetAttribute(conv3d_tma_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)tiles, (unsigned)(a.Cout / n_tile));
-    conv3d_tma_kernel<KC><<<grid, 128, bytes, s>>>(map_in, map_w, t, n_tile, cols, stages);
+    // all of the SM's unified memory as shared memory, so that per_sm blocks fit
+    e = cudaFuncSetAttribute(conv3d_tma_kernel<KC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    // blocks an SM holds, from the kernel's registers (the runtime's occupancy
+    // query answers 1 for any kernel that allocates tensor memory); more
+    // blocks than the SMs hold only run later, each still walking its boxes
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, conv3d_tma_kernel<KC>);
+    if (e != cudaSuccess) return e;
+    const int warp_regs = ((fa.numRegs + 7) / 8) * 8 * 32;
+    const int reg_blocks = 65536 / (warp_regs * (kConvThreads / 32));
+    const int occ = std::max(1, std::min(per_sm, reg_blocks));
+    const int grid_y = a.Cout / n_tile;
+    // persistent: each block walks boxes gridDim.x apart
+    const long long slots = std::max(1LL, (long long)sms * occ / grid_y);
+    dim3 grid((unsigned)std::min(tiles, slots), (unsigned)grid_y);
+    conv3d_tma_kernel<KC><<<grid, kConvThreads, bytes, s>>>(map_in, map_w, t, n_tile, cols, stages);
     return cudaGetLastError();
 }
 
