@@ -111,15 +111,68 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
 // wait is bounded (on a timeout the block raises the error flag, waits for
 // its loads and MMAs in flight, frees its tensor memory and returns).
 // ---------------------------------------------------------------------------
-struct TmaConvArgs {
-    int N, D, H, W, Cin, Cout;
-    int bx, by, bz, bn;              // output box (bx by bz bn <= 128)
-    int tiles_x, tiles_y, tiles_z;
+// Output of a convolution: bias, ReLU, then BF16 or FP32 (optionally added
+// to what is there) at out[v * out_stride + out_off + co].
+struct ConvOut {
     bf16 *out;
     float *out_f32;
     const float *bias;
     int out_stride, out_off, relu, accumulate;
 };
+
+struct TmaConvArgs {
+    int N, D, H, W, Cin, Cout;
+    int bx, by, bz, bn;              // output box (bx by bz bn <= 128)
+    int tiles_x, tiles_y, tiles_z;
+    ConvOut o;
+};
+
+// 16 consecutive accumulator columns of the warp's 32 tensor-memory lanes
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&rr)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
+                   "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]),
+                   "=r"(rr[14]), "=r"(rr[15])
+                 : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Output channels co .. co + 15 of voxel v from their FP32 accumulators
+__device__ __forceinline__ void store_row16(const ConvOut &o, long long v, int co, const uint32_t (&rr)[16])
+{
+    float val[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        float t = __uint_as_float(rr[j]);
+        if (o.bias) t += o.bias[co + j];
+        if (o.relu) t = fmaxf(t, 0.f);
+        val[j] = t;
+    }
+    const long long off = v * o.out_stride + o.out_off + co;
+    if (o.out_f32) {
+        float4 *dst = reinterpret_cast<float4 *>(o.out_f32 + off);
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+            float4 w4 = make_float4(val[4 * q4], val[4 * q4 + 1], val[4 * q4 + 2], val[4 * q4 + 3]);
+            if (o.accumulate) {
+                const float4 old = dst[q4];
+                w4.x += old.x; w4.y += old.y; w4.z += old.z; w4.w += old.w;
+            }
+            dst[q4] = w4;
+        }
+    } else {
+        uint32_t pk[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(val[2 * j], val[2 * j + 1]);
+            pk[j] = *reinterpret_cast<const uint32_t *>(&h2);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(o.out + off);
+        dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    }
+}
 
 // Shared-memory descriptor of a K-major operand whose rows are `row_bytes`
 // (32, 64 or 128) long in the matching swizzle: 8-row groups row_bytes * 8
@@ -322,44 +375,8 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tma_kernel(const __grid_c
             const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * n_tile);
             for (int c = 0; c < n_tile; c += 16) {
                 uint32_t rr[16];
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                             : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]),
-                               "=r"(rr[6]), "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]),
-                               "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]), "=r"(rr[15])
-                             : "r"(row_addr + (uint32_t)c));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (!vin) continue;
-                float val[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    float t = __uint_as_float(rr[j]);
-                    if (a.bias) t += a.bias[n0 + c + j];
-                    if (a.relu) t = fmaxf(t, 0.f);
-                    val[j] = t;
-                }
-                const long long o = v * a.out_stride + a.out_off + n0 + c;
-                if (a.out_f32) {
-                    float4 *dst = reinterpret_cast<float4 *>(a.out_f32 + o);
-#pragma unroll
-                    for (int q4 = 0; q4 < 4; ++q4) {
-                        float4 w4 = make_float4(val[4 * q4], val[4 * q4 + 1], val[4 * q4 + 2], val[4 * q4 + 3]);
-                        if (a.accumulate) {
-                            const float4 old = dst[q4];
-                            w4.x += old.x; w4.y += old.y; w4.z += old.z; w4.w += old.w;
-                        }
-                        dst[q4] = w4;
-                    }
-                } else {
-                    uint32_t pk[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(val[2 * j], val[2 * j + 1]);
-                        pk[j] = *reinterpret_cast<const uint32_t *>(&h2);
-                    }
-                    uint4 *dst = reinterpret_cast<uint4 *>(a.out + o);
-                    dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                    dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                }
+                tmem_ld16(row_addr + (uint32_t)c, rr);
+                if (vin) store_row16(a.o, v, n0 + c, rr);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&acc_empty[b])) : "memory");
@@ -368,6 +385,207 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tma_kernel(const __grid_c
     // every MMA of the block has completed before its tensor memory is freed:
     // the epilogue waited for the last box's accumulator, or, after a
     // failure, the MMA thread waits (bounded) for all it issued
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    const bool ok = __syncthreads_and(!*fail);
+    if (!ok) {
+        if (tid == 0) atomicExch(&g_tc_error, 1);
+        if (warp == 5 && lane == 0) {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(drain)) : "memory");
+            mbar_wait(smem_u32(drain), 0);
+        }
+    }
+    __syncthreads();
+    if (warp == 5) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Slab-fed convolution, for volumes whose rows hold W = 8 .. 128 voxels with
+// W dividing 128.  An output box is bx = W by by x bz voxels of one sample,
+// n_acc groups of 128 voxels (g = 128 / W consecutive rows each, gyn groups
+// along y, bz along z).  For every chunk of KC input channels and x offset
+// dx, one TMA load brings the slab of voxels x + dx - 1 (x = 0 .. W - 1),
+// y0 - 1 .. y0 + by, z0 - 1 .. z0 + bz (out-of-volume voxels read zero),
+// and nine loads the weights of the taps (dx, dy, dz).  The A operand of tap
+// (dy, dz) and group (gy, gz) is the 128 consecutive slab rows from
+// ((gz + dz)(by + 2) + g gy + dy) W on: a multiple of 8 rows, so the swizzle
+// atoms stay aligned.  Every input voxel is then read from L2 3 (by + 2)
+// (bz + 2) / (by bz) times per chunk instead of 27.  Block organisation,
+// barriers and the bounded waits are those of conv3d_tma_kernel; the
+// accumulators of box i are the n_acc x n_tile columns of buffer i mod 2.
+// ---------------------------------------------------------------------------
+struct SlabArgs {
+    int N, D, H, W, Cin, Cout;
+    int by, bz, g, gyn, n_acc, tiles_y, tiles_z;
+    ConvOut o;
+};
+
+template <int KC>
+__global__ void __launch_bounds__(kConvThreads, 1) conv3d_slab_kernel(const __grid_constant__ CUtensorMap map_in,
+                                                                   const __grid_constant__ CUtensorMap map_w,
+                                                                   const SlabArgs a, int n_tile, uint32_t tmem_cols,
+                                                                   int n_stages, int slab_bytes, int stage_bytes)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr int kRow = KC * 2;
+    const int bx = a.W;
+    const int rows_s = bx * (a.by + 2) * (a.bz + 2);
+    const int tap_bytes = n_tile * kRow;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + n_stages * stage_bytes);
+    uint64_t *empty = full + n_stages;
+    uint64_t *acc_full = empty + n_stages;
+    uint64_t *acc_empty = acc_full + 2;
+    uint64_t *drain = acc_empty + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(drain + 1);
+    int *s_fail = reinterpret_cast<int *>(tslot + 1);
+    volatile int *fail = s_fail;
+    const uint32_t smem0 = smem_u32(smem);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n0 = blockIdx.y * n_tile;
+    const int n_boxes = a.tiles_y * a.tiles_z * a.N;
+    const uint32_t tx_bytes = (uint32_t)rows_s * kRow + 9u * (uint32_t)tap_bytes;
+
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(tmem_cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int k = 0; k < n_stages; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[k])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[k])) : "memory");
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&acc_full[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" :: "r"(smem_u32(&acc_empty[b])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(drain)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *s_fail = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&map_in)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&map_w)) : "memory");
+            int st = 0, issued = 0;
+            uint32_t ph = 0;
+            bool stop = false;
+            for (int box = blockIdx.x; box < n_boxes && !stop && !*fail; box += gridDim.x) {
+                const int ty = box % a.tiles_y, q = box / a.tiles_y;
+                const int tz = q % a.tiles_z, nn = q / a.tiles_z;
+                const int y0 = ty * a.by - 1, z0 = tz * a.bz - 1;
+                for (int c0 = 0; c0 < a.Cin && !stop; c0 += KC) {
+                    for (int dx = 0; dx < 3; ++dx) {
+                        if (issued >= n_stages && !mbar_wait(smem_u32(&empty[st]), ph ^ 1u)) {
+                            atomicExch(s_fail, 1);
+                            stop = true;
+                            break;
+                        }
+                        if (*fail) { stop = true; break; }
+                        const uint32_t dst = smem0 + (uint32_t)(st * stage_bytes);
+                        const uint32_t bar = smem_u32(&full[st]);
+                        mbar_expect_tx(bar, tx_bytes);
+                        tma_load_5d(dst, &map_in, c0, dx - 1, y0, z0, nn, bar);
+                        // weights of taps 9 dz + 3 dy + dx, block 3 dz + dy
+                        for (int t9 = 0; t9 < 9; ++t9)
+                            tma_load_2d(dst + (uint32_t)(slab_bytes + t9 * tap_bytes), &map_w,
+                                        (3 * t9 + dx) * a.Cin + c0, n0, bar);
+                        ++issued;
+                        if (++st == n_stages) { st = 0; ph ^= 1u; }
+                    }
+                }
+            }
+            const bool failed = *fail;
+            for (int h = (issued > n_stages ? issued - n_stages : 0); h < issued; ++h)
+                mbar_wait(smem_u32(failed ? &full[h % n_stages] : &empty[h % n_stages]), (uint32_t)(h / n_stages) & 1u);
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            const uint32_t idesc = mma_idesc(128, n_tile);
+            const int steps = 3 * (a.Cin / KC);
+            int st = 0, i = 0;
+            uint32_t ph = 0;
+            for (int box = blockIdx.x; box < n_boxes && !*fail; box += gridDim.x, ++i) {
+                const int b = i & 1;
+                if (i >= 2 && !mbar_wait(smem_u32(&acc_empty[b]), (uint32_t)((i >> 1) - 1) & 1u)) {
+                    atomicExch(s_fail, 1);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc0 = tmem + (uint32_t)(b * a.n_acc * n_tile);
+                for (int s = 0; s < steps; ++s) {
+                    if (!mbar_wait(smem_u32(&full[st]), ph)) {
+                        atomicExch(s_fail, 1);
+                        break;
+                    }
+                    if (*fail) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem0 + (uint32_t)(st * stage_bytes);
+                    for (int t9 = 0; t9 < 9; ++t9) {
+                        const int dz = t9 / 3, dy = t9 - 3 * dz;
+                        const uint32_t b0 = a0 + (uint32_t)(slab_bytes + t9 * tap_bytes);
+                        for (int q = 0; q < a.n_acc; ++q) {
+                            const int gz = q / a.gyn, gy = q - gz * a.gyn;
+                            const int row = ((gz + dz) * (a.by + 2) + gy * a.g + dy) * bx;
+                            const uint32_t ar = a0 + (uint32_t)(row * kRow);
+                            const uint32_t acc_addr = acc0 + (uint32_t)(q * n_tile);
+#pragma unroll
+                            for (int j = 0; j < KC / 16; ++j) {
+                                const uint64_t ad = smem_desc_sw(ar + j * 32, kRow);
+                                const uint64_t bd = smem_desc_sw(b0 + j * 32, kRow);
+                                const uint32_t acc = (s > 0 || t9 > 0 || j > 0) ? 1u : 0u;
+                                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                             :: "r"(acc_addr), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+                            }
+                        }
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(smem_u32(&empty[st])) : "memory");
+                    if (++st == n_stages) { st = 0; ph ^= 1u; }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(smem_u32(&acc_full[b])) : "memory");
+            }
+        }
+    } else {
+        // epilogue: warps 0-3; accumulator row tid of group q = voxel
+        // (x, y) = (tid mod W, y0 + g gy + tid / W), z = z0 + gz
+        int i = 0;
+        for (int box = blockIdx.x; box < n_boxes; box += gridDim.x, ++i) {
+            const int b = i & 1;
+            const bool ready = mbar_wait(smem_u32(&acc_full[b]), (uint32_t)(i >> 1) & 1u);
+            if (__any_sync(0xffffffffu, !ready || *fail)) { atomicExch(s_fail, 1); break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int ty = box % a.tiles_y, qq = box / a.tiles_y;
+            const int tz = qq % a.tiles_z, nn = qq / a.tiles_z;
+            const int x = tid % bx;
+            for (int q = 0; q < a.n_acc; ++q) {
+                const int gz = q / a.gyn, gy = q - gz * a.gyn;
+                const int y = ty * a.by + gy * a.g + tid / bx, z = tz * a.bz + gz;
+                const bool vin = y < a.H && z < a.D;
+                const long long v = vin ? (((long long)nn * a.D + z) * a.H + y) * a.W + x : 0;
+                const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((b * a.n_acc + q) * n_tile);
+                for (int c = 0; c < n_tile; c += 16) {
+                    uint32_t rr[16];
+                    tmem_ld16(row_addr + (uint32_t)c, rr);
+                    if (vin) store_row16(a.o, v, n0 + c, rr);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&acc_empty[b])) : "memory");
+        }
+    }
     __syncwarp();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     const bool ok = __syncthreads_and(!*fail);
@@ -589,8 +807,8 @@ __global__ void reduce_partials_kernel(const float *part, int n_parts, long long
 }
 
 // Bias gradient, per block: part[blockIdx.x][c] = sum over the block's voxels
-// of gy[v][c] (BF16 gradient, dense C channels); reduce_partials_kernel adds
-// the blocks' sums in order.
+// of gy[v][c] (BF16 gradient, dense C channels), 256 / C voxel lanes of C
+// channels each; bias_reduce_kernel adds the blocks' sums in a fixed order.
 __global__ void bias_grad_kernel(const bf16 *gy, int C, long long V, long long vox_per_block, float *part)
 {
     __shared__ float s_part[256];
@@ -609,112 +827,181 @@ __global__ void bias_grad_kernel(const bf16 *gy, int C, long long V, long long v
     }
 }
 
-// out_bf16[v][c] = (mask == null || mask[v][c] > 0) ? bf16(g[v][c]) : 0.
+// gb[c] += sum over k of part[k][c], block c: thread t takes k = t, t + 256,
+// ... in order, then a fixed tree over the 256 threads (the same order on
+// every run).
+__global__ void bias_reduce_kernel(const float *part, int n_parts, int C, float *gb)
+{
+    __shared__ float s_sum[256];
+    const int c = blockIdx.x;
+    float t = 0.f;
+    for (int k = threadIdx.x; k < n_parts; k += blockDim.x) t += part[(long long)k * C + c];
+    s_sum[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s_sum[threadIdx.x] += s_sum[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) gb[c] += s_sum[0];
+}
+
+// out_bf16[v][c] = (mask == null || mask[v][c] > 0) ? bf16(g[v][c]) : 0;
+// one voxel per thread, 8 channels at a time (C, the strides and offsets
+// multiples of 8, of 4 for g).
 __global__ void mask_to_bf16_kernel(const float *g, int g_stride, int g_off, const bf16 *mask, int m_stride, int m_off,
                                     int C, long long V, bf16 *out)
 {
-    const long long n = V * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const long long v = i / C;
-        const int c = (int)(i % C);
-        float val = g[v * g_stride + g_off + c];
-        if (mask && !(__bfloat162float(mask[v * m_stride + m_off + c]) > 0.f)) val = 0.f;
-        out[i] = __float2bfloat16_rn(val);
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const float *gv = g + v * g_stride + g_off;
+    for (int c = 0; c < C; c += 8) {
+        const float4 a = *reinterpret_cast<const float4 *>(gv + c);
+        const float4 b = *reinterpret_cast<const float4 *>(gv + c + 4);
+        float val[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        if (mask) {
+            const uint4 m = *reinterpret_cast<const uint4 *>(mask + v * m_stride + m_off + c);
+            const __nv_bfloat16 *mh = reinterpret_cast<const __nv_bfloat16 *>(&m);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (!(__bfloat162float(mh[j]) > 0.f)) val[j] = 0.f;
+        }
+        uint32_t pk[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(val[2 * j], val[2 * j + 1]);
+            pk[j] = *reinterpret_cast<const uint32_t *>(&h2);
+        }
+        *reinterpret_cast<uint4 *>(out + v * C + c) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     }
 }
 
+// Kernels over the voxels of a volume N x D x H x W: blockIdx.y (strided by
+// gridDim.y) walks the rows (n, z, y), threads the row's voxels x times
+// channel groups of 8 (BF16) or 4 (FP32).
+
 // 2x2x2 max pooling of a strided BF16 view into a dense output; arg = index
-// of the first maximum in octant order ox + 2 oy + 4 oz.
+// of the first maximum in octant order ox + 2 oy + 4 oz.  Coarse rows.
 __global__ void maxpool_kernel(const bf16 *in, int in_stride, int in_off, int N, int D, int H, int W, int C, bf16 *out,
                                uint8_t *arg)
 {
-    const int d2 = D / 2, h2 = H / 2, w2 = W / 2;
-    const long long n_out = (long long)N * d2 * h2 * w2 * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_out; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        long long q = i / C;
-        const int x = (int)(q % w2); q /= w2;
-        const int y = (int)(q % h2); q /= h2;
-        const int z = (int)(q % d2);
-        const long long n = q / d2;
-        float best = 0.f;
-        int bi = 0;
+    const int d2 = D / 2, h2 = H / 2, w2 = W / 2, ng = C / 8;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= w2 * ng) return;
+    const int x = t / ng, c = (t - x * ng) * 8;
+    const int rows = N * d2 * h2;
+    for (int row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int y = row % h2, q = row / h2, z = q % d2, n = q / d2;
+        float best[8];
+        uint32_t bi[8];
         for (int o = 0; o < 8; ++o) {
             const int zz = 2 * z + (o >> 2), yy = 2 * y + ((o >> 1) & 1), xx = 2 * x + (o & 1);
-            const float val = __bfloat162float(in[(((n * D + zz) * H + yy) * W + xx) * in_stride + in_off + c]);
-            if (o == 0 || val > best) { best = val; bi = o; }
+            const uint4 u = *reinterpret_cast<const uint4 *>(
+                in + ((((long long)n * D + zz) * H + yy) * W + xx) * in_stride + in_off + c);
+            const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&u);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float val = __bfloat162float(h[j]);
+                if (o == 0 || val > best[j]) { best[j] = val; bi[j] = (uint32_t)o; }
+            }
         }
-        out[i] = __float2bfloat16_rn(best);
-        arg[i] = (uint8_t)bi;
+        const long long ov = (long long)row * w2 + x;
+        uint32_t pk[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const __nv_bfloat162 h2v = __floats2bfloat162_rn(best[2 * j], best[2 * j + 1]);
+            pk[j] = *reinterpret_cast<const uint32_t *>(&h2v);
+        }
+        *reinterpret_cast<uint4 *>(out + ov * C + c) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        *reinterpret_cast<uint2 *>(arg + ov * C + c) =
+            make_uint2(bi[0] | bi[1] << 8 | bi[2] << 16 | bi[3] << 24, bi[4] | bi[5] << 8 | bi[6] << 16 | bi[7] << 24);
     }
 }
 
-// g_in[argmax] += g_out (FP32; g_in strided view of the fine grid).
+// g_in[argmax] += g_out (FP32; g_in strided view of the fine grid).  Coarse
+// rows; the 8 voxels of an octant belong to one coarse voxel, so no two
+// threads write one element.
 __global__ void maxpool_bwd_kernel(const float *g_out, const uint8_t *arg, int N, int D, int H, int W, int C, float *g_in,
                                    int in_stride, int in_off)
 {
-    const int d2 = D / 2, h2 = H / 2, w2 = W / 2;
-    const long long n_out = (long long)N * d2 * h2 * w2 * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_out; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        long long q = i / C;
-        const int x = (int)(q % w2); q /= w2;
-        const int y = (int)(q % h2); q /= h2;
-        const int z = (int)(q % d2);
-        const long long n = q / d2;
-        const int o = arg[i];
-        const int zz = 2 * z + (o >> 2), yy = 2 * y + ((o >> 1) & 1), xx = 2 * x + (o & 1);
-        g_in[(((n * D + zz) * H + yy) * W + xx) * in_stride + in_off + c] += g_out[i];
+    const int d2 = D / 2, h2 = H / 2, w2 = W / 2, ng = C / 8;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= w2 * ng) return;
+    const int x = t / ng, c = (t - x * ng) * 8;
+    const int rows = N * d2 * h2;
+    for (int row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int y = row % h2, q = row / h2, z = q % d2, n = q / d2;
+        const long long ov = (long long)row * w2 + x;
+        const uint2 a = *reinterpret_cast<const uint2 *>(arg + ov * C + c);
+        const float4 g0 = *reinterpret_cast<const float4 *>(g_out + ov * C + c);
+        const float4 g1 = *reinterpret_cast<const float4 *>(g_out + ov * C + c + 4);
+        const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int o = (int)(((j < 4 ? a.x : a.y) >> (8 * (j & 3))) & 0xFFu);
+            const int zz = 2 * z + (o >> 2), yy = 2 * y + ((o >> 1) & 1), xx = 2 * x + (o & 1);
+            g_in[((((long long)n * D + zz) * H + yy) * W + xx) * in_stride + in_off + c + j] += gv[j];
+        }
     }
 }
 
-// Nearest 2x upsampling of a dense coarse BF16 tensor into a strided fine view.
+// Nearest 2x upsampling of a dense coarse BF16 tensor into a strided fine
+// view.  Fine rows.
 __global__ void upsample_kernel(const bf16 *in, int N, int d2, int h2, int w2, int C, bf16 *out, int out_stride, int out_off)
 {
-    const int D = 2 * d2, H = 2 * h2, W = 2 * w2;
-    const long long n = (long long)N * D * H * W * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        long long q = i / C;
-        const int x = (int)(q % W); q /= W;
-        const int y = (int)(q % H); q /= H;
-        const int z = (int)(q % D);
-        const long long nn = q / D;
-        out[(q * H * W + (long long)y * W + x) * out_stride + out_off + c] =
-            in[(((nn * d2 + z / 2) * h2 + y / 2) * w2 + x / 2) * C + c];
+    const int D = 2 * d2, H = 2 * h2, W = 2 * w2, ng = C / 8;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= W * ng) return;
+    const int x = t / ng, c = (t - x * ng) * 8;
+    const int rows = N * D * H;
+    for (int row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int y = row % H, q = row / H, z = q % D, n = q / D;
+        const uint4 u = *reinterpret_cast<const uint4 *>(
+            in + ((((long long)n * d2 + z / 2) * h2 + y / 2) * w2 + x / 2) * C + c);
+        *reinterpret_cast<uint4 *>(out + ((long long)row * W + x) * out_stride + out_off + c) = u;
     }
 }
 
-// g_in[coarse] = sum over the 8 fine voxels of g_out (strided FP32 view).
+// g_in[coarse] = sum over the 8 fine voxels, in octant order, of g_out
+// (strided FP32 view).  Coarse rows, 4 channels per thread.
 __global__ void upsample_bwd_kernel(const float *g_out, int out_stride, int out_off, int N, int d2, int h2, int w2, int C,
                                     float *g_in)
 {
-    const int D = 2 * d2, H = 2 * h2, W = 2 * w2;
-    const long long n = (long long)N * d2 * h2 * w2 * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        long long q = i / C;
-        const int x = (int)(q % w2); q /= w2;
-        const int y = (int)(q % h2); q /= h2;
-        const int z = (int)(q % d2);
-        const long long nn = q / d2;
-        float s = 0.f;
+    const int D = 2 * d2, H = 2 * h2, W = 2 * w2, ng = C / 4;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= w2 * ng) return;
+    const int x = t / ng, c = (t - x * ng) * 4;
+    const int rows = N * d2 * h2;
+    for (int row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int y = row % h2, q = row / h2, z = q % d2, n = q / d2;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int o = 0; o < 8; ++o) {
             const int zz = 2 * z + (o >> 2), yy = 2 * y + ((o >> 1) & 1), xx = 2 * x + (o & 1);
-            s += g_out[(((nn * D + zz) * H + yy) * W + xx) * out_stride + out_off + c];
+            const float4 g = *reinterpret_cast<const float4 *>(
+                g_out + ((((long long)n * D + zz) * H + yy) * W + xx) * out_stride + out_off + c);
+            s.x += g.x; s.y += g.y; s.z += g.z; s.w += g.w;
         }
-        g_in[i] = s;
+        *reinterpret_cast<float4 *>(g_in + ((long long)row * w2 + x) * C + c) = s;
     }
 }
 
 // Network input: x16[v][0..n_in-1] = bf16(in[v][0..n_in-1]), the other
-// channels of the 16 zero.
+// channels of the 16 zero; one voxel per thread.
 __global__ void input_kernel(const float *in, long long V, int n_in, bf16 *x16)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V * 16; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % 16);
-        x16[i] = __float2bfloat16_rn(c < n_in ? in[(i / 16) * n_in + c] : 0.f);
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    float val[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) val[c] = c < n_in ? in[v * n_in + c] : 0.f;
+    uint32_t pk[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(val[2 * j], val[2 * j + 1]);
+        pk[j] = *reinterpret_cast<const uint32_t *>(&h2);
     }
+    uint4 *dst = reinterpret_cast<uint4 *>(x16 + v * 16);
+    dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
 }
 
 // Prediction = head channel 0; MSE loss and its gradient into head channel 0.
@@ -743,13 +1030,20 @@ __global__ void mse_kernel(const float *head, const float *target, long long V, 
     if (threadIdx.x == 0 && loss_part && target) loss_part[blockIdx.x] = part[0] / (double)V;
 }
 
+// loss = sum of the blocks' shares: thread t takes k = t, t + 256, ... in
+// order, then a fixed tree (one block of 256 threads).
 __global__ void sum_loss_kernel(const double *loss_part, int n, double *loss)
 {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < n; ++k) s += loss_part[k];
-        *loss = s;
+    __shared__ double s_sum[256];
+    double t = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) t += loss_part[k];
+    s_sum[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s_sum[threadIdx.x] += s_sum[threadIdx.x + o];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) *loss = s_sum[0];
 }
 
 // Adam on FP32 master weights; writes the BF16 copy used by the kernels.
@@ -828,6 +1122,16 @@ inline int grid_1d(long long n, int block = 256)
     return (int)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
 }
 
+// One thread per element (no grid-stride loop)
+inline unsigned grid_all(long long n, int block = 256) { return (unsigned)((n + block - 1) / block); }
+
+// Grid of the row kernels: threads over row_threads, blockIdx.y over at most
+// 65535 of the rows (the kernels stride by gridDim.y)
+inline dim3 grid_rows(int row_threads, long long rows)
+{
+    return dim3((unsigned)((row_threads + 127) / 128), (unsigned)(rows < 65535 ? (rows < 1 ? 1 : rows) : 65535));
+}
+
 
 // Output channels per block of the tensor-core convolution: a multiple of
 // 16 dividing C_out, at most 256, narrowed (down to 16) while the blocks
@@ -887,8 +1191,7 @@ cudaError_t tma_launch(const ConvArgs &a, cudaStream_t s)
     t.tiles_y = (a.H + t.by - 1) / t.by;
     t.tiles_z = (a.D + t.bz - 1) / t.bz;
     const long long tiles = (long long)t.tiles_x * t.tiles_y * t.tiles_z * ((a.N + t.bn - 1) / t.bn);
-    t.out = a.out; t.out_f32 = a.out_f32; t.bias = a.bias;
-    t.out_stride = a.out_stride; t.out_off = a.out_off; t.relu = a.relu; t.accumulate = a.accumulate;
+    t.o = ConvOut{a.out, a.out_f32, a.bias, a.out_stride, a.out_off, a.relu, a.accumulate};
     const int n_tile = tc_n_tile(a.Cout, tiles, sms);
     constexpr CUtensorMapSwizzle sw = KC == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
                                     : (KC == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
@@ -956,10 +1259,136 @@ cudaError_t tma_launch(const ConvArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// TMA-fed kernel with K chunks of 64, 32 or 16 input channels (the largest
-// dividing C_in).
+// Plan of the slab-fed kernel, or false where it does not apply (rows that
+// do not divide 128 voxels, a 128-voxel group taller than the volume,
+// channel counts not multiples of 16).  Output boxes are tried from the most
+// input reuse down (4, then 2, then 1 groups of 128 voxels) and taken with
+// the widest channel tile that still gives every SM a block; K chunks of 32
+// or 16 channels, 32 where two blocks still fit an SM.
+struct SlabPlan {
+    int kc, by, bz, gyn, n_acc, n_tile, stages, slab_bytes, stage_bytes, bytes, per_sm;
+};
+
+bool slab_plan(const ConvArgs &a, int sms, int sm_smem, int blk_max, SlabPlan &p)
+{
+    if (a.W < 8 || 128 % a.W || a.Cin % 16 || a.Cout % 16 || a.in_stride % 8) return false;
+    const int g = 128 / a.W;
+    if (g > a.H) return false;
+    static const int cand[6][2] = {{2, 2}, {4, 1}, {1, 4}, {1, 2}, {2, 1}, {1, 1}};
+    const int fixed = 1024 + 8 * (2 * 8 + 5) + 8;
+    for (const auto &c : cand) {
+        const int gyn = c[0], bz = c[1], by = gyn * g, n_acc = gyn * bz;
+        if ((gyn > 1 && by > a.H) || (bz > 1 && bz > a.D)) continue;
+        const long long boxes = (long long)((a.H + by - 1) / by) * ((a.D + bz - 1) / bz) * a.N;
+        int n_tile = 256 / n_acc;
+        while (n_tile > 16 && a.Cout % n_tile) n_tile -= 16;
+        while (n_tile > 16 && boxes * (a.Cout / n_tile) < sms) {
+            int u = n_tile - 16;
+            while (u > 16 && a.Cout % u) u -= 16;
+            n_tile = u;
+        }
+        if (a.Cout % n_tile || boxes * (a.Cout / n_tile) < sms) continue;
+        uint32_t cols = 32;
+        while ((int)cols < 2 * n_acc * n_tile) cols <<= 1;
+        if (cols > 512) continue;
+        bool found = false;
+        for (int kc = 32; kc >= 16; kc >>= 1) {
+            if (a.Cin % kc) continue;
+            const int rows_s = a.W * (by + 2) * (bz + 2);
+            const int slab = (rows_s * kc * 2 + 1023) / 1024 * 1024;
+            const int stage = (slab + 9 * n_tile * kc * 2 + 1023) / 1024 * 1024;
+            if (2 * stage + fixed > blk_max) continue;
+            const int per_sm = std::min(std::min(512 / (int)cols, 2048 / kConvThreads),
+                                        sm_smem / (2 * stage + fixed + 1024));
+            if (per_sm < 1) continue;
+            if (!found || (p.per_sm < 2 && per_sm >= 2)) {
+                p = SlabPlan{kc, by, bz, gyn, n_acc, n_tile, 0, slab, stage, 0, per_sm};
+                found = true;
+            }
+            if (per_sm >= 2) break;
+        }
+        if (!found) continue;
+        int stages = (sm_smem / p.per_sm - 1024 - fixed) / p.stage_bytes;
+        p.stages = stages < 2 ? 2 : (stages > 8 ? 8 : stages);
+        const int need = 1024 + p.stages * p.stage_bytes + 8 * (2 * p.stages + 5) + 8;
+        const int pad = sm_smem / (p.per_sm + 1) + 1024;
+        p.bytes = std::min(std::max(need, pad), blk_max);
+        return need <= blk_max;
+    }
+    return false;
+}
+
+template <int KC>
+cudaError_t slab_launch(const ConvArgs &a, const SlabPlan &p, int sms, cudaStream_t s)
+{
+    auto encode = encode_tiled();
+    if (!encode) return cudaErrorNotSupported;
+    const uintptr_t in_addr = reinterpret_cast<uintptr_t>(a.in + a.in_off);
+    if ((in_addr & 15u) || (reinterpret_cast<uintptr_t>(a.w) & 15u)) return cudaErrorInvalidValue;
+    SlabArgs t{};
+    t.N = a.N; t.D = a.D; t.H = a.H; t.W = a.W; t.Cin = a.Cin; t.Cout = a.Cout;
+    t.by = p.by; t.bz = p.bz; t.g = 128 / a.W; t.gyn = p.gyn; t.n_acc = p.n_acc;
+    t.tiles_y = (a.H + p.by - 1) / p.by;
+    t.tiles_z = (a.D + p.bz - 1) / p.bz;
+    t.o = ConvOut{a.out, a.out_f32, a.bias, a.out_stride, a.out_off, a.relu, a.accumulate};
+    constexpr CUtensorMapSwizzle sw = KC == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                    : (KC == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
+    CUtensorMap map_in, map_w;
+    {
+        const cuuint64_t dims[5] = {(cuuint64_t)a.Cin, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.D,
+                                    (cuuint64_t)a.N};
+        const cuuint64_t vb = (cuuint64_t)a.in_stride * 2;
+        const cuuint64_t strides[4] = {vb, vb * a.W, vb * a.W * a.H, vb * a.W * a.H * a.D};
+        const cuuint32_t box[5] = {(cuuint32_t)KC, (cuuint32_t)a.W, (cuuint32_t)(p.by + 2), (cuuint32_t)(p.bz + 2), 1};
+        const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        if (encode(&map_in, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, reinterpret_cast<void *>(in_addr), dims, strides, box,
+                   es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        const cuuint64_t dims[2] = {(cuuint64_t)27 * a.Cin, (cuuint64_t)a.Cout};
+        const cuuint64_t strides[1] = {(cuuint64_t)27 * a.Cin * 2};
+        const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)p.n_tile};
+        const cuuint32_t es[2] = {1, 1};
+        if (encode(&map_w, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(a.w), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    uint32_t cols = 32;
+    while ((int)cols < 2 * p.n_acc * p.n_tile) cols <<= 1;
+    cudaError_t e = cudaFuncSetAttribute(conv3d_slab_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(conv3d_slab_kernel<KC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, conv3d_slab_kernel<KC>);
+    if (e != cudaSuccess) return e;
+    const int warp_regs = ((fa.numRegs + 7) / 8) * 8 * 32;
+    const int occ = std::max(1, std::min(p.per_sm, 65536 / (warp_regs * (kConvThreads / 32))));
+    const int grid_y = a.Cout / p.n_tile;
+    const long long n_boxes = (long long)t.tiles_y * t.tiles_z * a.N;
+    const long long slots = std::max(1LL, (long long)sms * occ / grid_y);
+    dim3 grid((unsigned)std::min(n_boxes, slots), (unsigned)grid_y);
+    conv3d_slab_kernel<KC><<<grid, kConvThreads, p.bytes, s>>>(map_in, map_w, t, p.n_tile, cols, p.stages,
+                                                               p.slab_bytes, p.stage_bytes);
+    return cudaGetLastError();
+}
+
+// The slab-fed kernel where its plan applies, else the per-tap kernel with K
+// chunks of 64, 32 or 16 input channels (the largest dividing C_in).
 cudaError_t conv_launch(const ConvArgs &a, cudaStream_t s)
 {
+    int dev = 0, sms = 148, sm_smem = 0, blk_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&blk_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    SlabPlan p{};
+    if (slab_plan(a, sms, sm_smem, blk_max, p))
+        return p.kc == 32 ? slab_launch<32>(a, p, sms, s) : slab_launch<16>(a, p, sms, s);
     if (a.Cin % 64 == 0) return tma_launch<64>(a, s);
     if (a.Cin % 32 == 0) return tma_launch<32>(a, s);
     return tma_launch<16>(a, s);
@@ -1042,18 +1471,21 @@ cudaError_t wgrad_launch(const WgradArgs &a0, float *gw, long long part_floats, 
     return cudaGetLastError();
 }
 
-constexpr long long kBiasVox = 4096;      // voxels per block of the bias gradient
+// Voxels per block of the bias gradient: 16 per voxel lane of its 256 threads
+inline long long bias_vox(int C) { return 16LL * (256 / (C < 1 ? 1 : C)); }
 
-inline long long bias_part_floats(long long V, int C) { return (V + kBiasVox - 1) / kBiasVox * C; }
+inline long long bias_part_floats(long long V, int C) { return (V + bias_vox(C) - 1) / bias_vox(C) * C; }
 
-// gb[C] += sum_v gy[v]: per-block sums into part, then their ordered sum.
+// gb[C] += sum_v gy[v]: per-block sums into part, then their sum in a fixed
+// order.
 cudaError_t bias_grad_launch(const bf16 *gy, int C, long long V, float *gb, float *part, long long part_floats,
                              cudaStream_t s)
 {
-    const long long blocks = (V + kBiasVox - 1) / kBiasVox;
-    if (blocks * C > part_floats || C > 256) return cudaErrorInvalidValue;
-    bias_grad_kernel<<<(unsigned)blocks, 256, 0, s>>>(gy, C, V, kBiasVox, part);
-    reduce_partials_kernel<<<grid_1d(C), 256, 0, s>>>(part, (int)blocks, C, gb);
+    if (C < 1 || C > 256) return cudaErrorInvalidValue;
+    const long long blocks = (V + bias_vox(C) - 1) / bias_vox(C);
+    if (blocks * C > part_floats || blocks > 0x7FFFFFFF) return cudaErrorInvalidValue;
+    bias_grad_kernel<<<(unsigned)blocks, 256, 0, s>>>(gy, C, V, bias_vox(C), part);
+    bias_reduce_kernel<<<C, 256, 0, s>>>(part, (int)blocks, C, gb);
     return cudaGetLastError();
 }
 
@@ -1200,7 +1632,7 @@ soc_status bwd(Net &n, int l, const float *gy, int gy_stride, int gy_off, const 
 {
     const int Cin = kSpec[l].cin, Cout = kSpec[l].cout;
     const long long V = (long long)n.batch * S * S * S;
-    mask_to_bf16_kernel<<<grid_1d(V * Cout), 256, 0, s>>>(gy, gy_stride, gy_off, kSpec[l].relu ? y : nullptr, y_stride,
+    mask_to_bf16_kernel<<<grid_all(V), 256, 0, s>>>(gy, gy_stride, gy_off, kSpec[l].relu ? y : nullptr, y_stride,
                                                          y_off, Cout, V, n.gstage.p);
     NNCK(cudaGetLastError());
     WgradArgs wa;
@@ -1221,26 +1653,26 @@ soc_status forward(Net &n, const float *d_in, cudaStream_t s)
 {
     const int S0 = n.S, S1 = S0 / 2, S2 = S0 / 4, S3 = S0 / 8;
     soc_status st;
-    input_kernel<<<grid_1d(n.V0 * 16), 256, 0, s>>>(d_in, n.V0, n.n_in, n.x16.p);
+    input_kernel<<<grid_all(n.V0), 256, 0, s>>>(d_in, n.V0, n.n_in, n.x16.p);
     NNCK(cudaGetLastError());
     if ((st = fwd(n, 0, n.x16.p, 16, 0, S0, n.e0a.p, 16, 0, s))) return st;
     if ((st = fwd(n, 1, n.e0a.p, 16, 0, S0, n.cat0.p, 48, 32, s))) return st;
-    maxpool_kernel<<<grid_1d(n.V1 * 16), 256, 0, s>>>(n.cat0.p, 48, 32, n.batch, S0, S0, S0, 16, n.p0.p, n.arg0.p);
+    maxpool_kernel<<<grid_rows(S1 * 2, (long long)n.batch * S1 * S1), 128, 0, s>>>(n.cat0.p, 48, 32, n.batch, S0, S0, S0, 16, n.p0.p, n.arg0.p);
     if ((st = fwd(n, 2, n.p0.p, 16, 0, S1, n.e1a.p, 32, 0, s))) return st;
     if ((st = fwd(n, 3, n.e1a.p, 32, 0, S1, n.cat1.p, 96, 64, s))) return st;
-    maxpool_kernel<<<grid_1d(n.V2 * 32), 256, 0, s>>>(n.cat1.p, 96, 64, n.batch, S1, S1, S1, 32, n.p1.p, n.arg1.p);
+    maxpool_kernel<<<grid_rows(S2 * 4, (long long)n.batch * S2 * S2), 128, 0, s>>>(n.cat1.p, 96, 64, n.batch, S1, S1, S1, 32, n.p1.p, n.arg1.p);
     if ((st = fwd(n, 4, n.p1.p, 32, 0, S2, n.e2a.p, 64, 0, s))) return st;
     if ((st = fwd(n, 5, n.e2a.p, 64, 0, S2, n.cat2.p, 192, 128, s))) return st;
-    maxpool_kernel<<<grid_1d(n.V3 * 64), 256, 0, s>>>(n.cat2.p, 192, 128, n.batch, S2, S2, S2, 64, n.p2.p, n.arg2.p);
+    maxpool_kernel<<<grid_rows(S3 * 8, (long long)n.batch * S3 * S3), 128, 0, s>>>(n.cat2.p, 192, 128, n.batch, S2, S2, S2, 64, n.p2.p, n.arg2.p);
     if ((st = fwd(n, 6, n.p2.p, 64, 0, S3, n.b_a.p, 128, 0, s))) return st;
     if ((st = fwd(n, 7, n.b_a.p, 128, 0, S3, n.b_b.p, 128, 0, s))) return st;
-    upsample_kernel<<<grid_1d(n.V2 * 128), 256, 0, s>>>(n.b_b.p, n.batch, S3, S3, S3, 128, n.cat2.p, 192, 0);
+    upsample_kernel<<<grid_rows(S2 * 16, (long long)n.batch * S2 * S2), 128, 0, s>>>(n.b_b.p, n.batch, S3, S3, S3, 128, n.cat2.p, 192, 0);
     if ((st = fwd(n, 8, n.cat2.p, 192, 0, S2, n.d2a.p, 64, 0, s))) return st;
     if ((st = fwd(n, 9, n.d2a.p, 64, 0, S2, n.d2b.p, 64, 0, s))) return st;
-    upsample_kernel<<<grid_1d(n.V1 * 64), 256, 0, s>>>(n.d2b.p, n.batch, S2, S2, S2, 64, n.cat1.p, 96, 0);
+    upsample_kernel<<<grid_rows(S1 * 8, (long long)n.batch * S1 * S1), 128, 0, s>>>(n.d2b.p, n.batch, S2, S2, S2, 64, n.cat1.p, 96, 0);
     if ((st = fwd(n, 10, n.cat1.p, 96, 0, S1, n.d1a.p, 32, 0, s))) return st;
     if ((st = fwd(n, 11, n.d1a.p, 32, 0, S1, n.d1b.p, 32, 0, s))) return st;
-    upsample_kernel<<<grid_1d(n.V0 * 32), 256, 0, s>>>(n.d1b.p, n.batch, S1, S1, S1, 32, n.cat0.p, 48, 0);
+    upsample_kernel<<<grid_rows(S0 * 4, (long long)n.batch * S0 * S0), 128, 0, s>>>(n.d1b.p, n.batch, S1, S1, S1, 32, n.cat0.p, 48, 0);
     if ((st = fwd(n, 12, n.cat0.p, 48, 0, S0, n.d0a.p, 16, 0, s))) return st;
     if ((st = fwd(n, 13, n.d0a.p, 16, 0, S0, n.d0b.p, 16, 0, s))) return st;
     ConvArgs a = conv_args(n.d0b.p, 16, 0, n.w16[14].p, n.b32[14].p, n.batch, S0, 16, 16, 0);
@@ -1261,33 +1693,33 @@ soc_status backward(Net &n, const float *d_target, cudaStream_t s)
     }
     NNCK(cudaMemsetAsync(n.g_head.p, 0, n.g_head.n * 4, s));
     mse_kernel<<<grid_1d(n.V0), 256, 0, s>>>(n.head.p, d_target, n.V0, nullptr, n.g_head.p, n.loss_part.p);
-    sum_loss_kernel<<<1, 32, 0, s>>>(n.loss_part.p, grid_1d(n.V0), n.loss.p);
+    sum_loss_kernel<<<1, 256, 0, s>>>(n.loss_part.p, grid_1d(n.V0), n.loss.p);
     NNCK(cudaGetLastError());
     // decoder level 0
     if ((st = bwd(n, 14, n.g_head.p, 16, 0, nullptr, 0, 0, n.d0b.p, 16, 0, S0, n.g_d0b.p, 16, 0, 0, s))) return st;
     if ((st = bwd(n, 13, n.g_d0b.p, 16, 0, n.d0b.p, 16, 0, n.d0a.p, 16, 0, S0, n.g_d0a.p, 16, 0, 0, s))) return st;
     if ((st = bwd(n, 12, n.g_d0a.p, 16, 0, n.d0a.p, 16, 0, n.cat0.p, 48, 0, S0, n.g_cat0.p, 48, 0, 0, s))) return st;
-    upsample_bwd_kernel<<<grid_1d(n.V1 * 32), 256, 0, s>>>(n.g_cat0.p, 48, 0, n.batch, S1, S1, S1, 32, n.g_d1b.p);
+    upsample_bwd_kernel<<<grid_rows(S1 * 8, (long long)n.batch * S1 * S1), 128, 0, s>>>(n.g_cat0.p, 48, 0, n.batch, S1, S1, S1, 32, n.g_d1b.p);
     // decoder level 1
     if ((st = bwd(n, 11, n.g_d1b.p, 32, 0, n.d1b.p, 32, 0, n.d1a.p, 32, 0, S1, n.g_d1a.p, 32, 0, 0, s))) return st;
     if ((st = bwd(n, 10, n.g_d1a.p, 32, 0, n.d1a.p, 32, 0, n.cat1.p, 96, 0, S1, n.g_cat1.p, 96, 0, 0, s))) return st;
-    upsample_bwd_kernel<<<grid_1d(n.V2 * 64), 256, 0, s>>>(n.g_cat1.p, 96, 0, n.batch, S2, S2, S2, 64, n.g_d2b.p);
+    upsample_bwd_kernel<<<grid_rows(S2 * 16, (long long)n.batch * S2 * S2), 128, 0, s>>>(n.g_cat1.p, 96, 0, n.batch, S2, S2, S2, 64, n.g_d2b.p);
     // decoder level 2
     if ((st = bwd(n, 9, n.g_d2b.p, 64, 0, n.d2b.p, 64, 0, n.d2a.p, 64, 0, S2, n.g_d2a.p, 64, 0, 0, s))) return st;
     if ((st = bwd(n, 8, n.g_d2a.p, 64, 0, n.d2a.p, 64, 0, n.cat2.p, 192, 0, S2, n.g_cat2.p, 192, 0, 0, s))) return st;
-    upsample_bwd_kernel<<<grid_1d(n.V3 * 128), 256, 0, s>>>(n.g_cat2.p, 192, 0, n.batch, S3, S3, S3, 128, n.g_bb.p);
+    upsample_bwd_kernel<<<grid_rows(S3 * 32, (long long)n.batch * S3 * S3), 128, 0, s>>>(n.g_cat2.p, 192, 0, n.batch, S3, S3, S3, 128, n.g_bb.p);
     // bottleneck
     if ((st = bwd(n, 7, n.g_bb.p, 128, 0, n.b_b.p, 128, 0, n.b_a.p, 128, 0, S3, n.g_ba.p, 128, 0, 0, s))) return st;
     if ((st = bwd(n, 6, n.g_ba.p, 128, 0, n.b_a.p, 128, 0, n.p2.p, 64, 0, S3, n.g_p2.p, 64, 0, 0, s))) return st;
-    maxpool_bwd_kernel<<<grid_1d(n.V3 * 64), 256, 0, s>>>(n.g_p2.p, n.arg2.p, n.batch, S2, S2, S2, 64, n.g_cat2.p, 192,
+    maxpool_bwd_kernel<<<grid_rows(S3 * 8, (long long)n.batch * S3 * S3), 128, 0, s>>>(n.g_p2.p, n.arg2.p, n.batch, S2, S2, S2, 64, n.g_cat2.p, 192,
                                                           128);
     // encoder level 2 (its output is the skip slice of cat2)
     if ((st = bwd(n, 5, n.g_cat2.p, 192, 128, n.cat2.p, 192, 128, n.e2a.p, 64, 0, S2, n.g_e2a.p, 64, 0, 0, s))) return st;
     if ((st = bwd(n, 4, n.g_e2a.p, 64, 0, n.e2a.p, 64, 0, n.p1.p, 32, 0, S2, n.g_p1.p, 32, 0, 0, s))) return st;
-    maxpool_bwd_kernel<<<grid_1d(n.V2 * 32), 256, 0, s>>>(n.g_p1.p, n.arg1.p, n.batch, S1, S1, S1, 32, n.g_cat1.p, 96, 64);
+    maxpool_bwd_kernel<<<grid_rows(S2 * 4, (long long)n.batch * S2 * S2), 128, 0, s>>>(n.g_p1.p, n.arg1.p, n.batch, S1, S1, S1, 32, n.g_cat1.p, 96, 64);
     if ((st = bwd(n, 3, n.g_cat1.p, 96, 64, n.cat1.p, 96, 64, n.e1a.p, 32, 0, S1, n.g_e1a.p, 32, 0, 0, s))) return st;
     if ((st = bwd(n, 2, n.g_e1a.p, 32, 0, n.e1a.p, 32, 0, n.p0.p, 16, 0, S1, n.g_p0.p, 16, 0, 0, s))) return st;
-    maxpool_bwd_kernel<<<grid_1d(n.V1 * 16), 256, 0, s>>>(n.g_p0.p, n.arg0.p, n.batch, S0, S0, S0, 16, n.g_cat0.p, 48, 32);
+    maxpool_bwd_kernel<<<grid_rows(S1 * 2, (long long)n.batch * S1 * S1), 128, 0, s>>>(n.g_p0.p, n.arg0.p, n.batch, S0, S0, S0, 16, n.g_cat0.p, 48, 32);
     if ((st = bwd(n, 1, n.g_cat0.p, 48, 32, n.cat0.p, 48, 32, n.e0a.p, 16, 0, S0, n.g_e0a.p, 16, 0, 0, s))) return st;
     if ((st = bwd(n, 0, n.g_e0a.p, 16, 0, n.e0a.p, 16, 0, n.x16.p, 16, 0, S0, nullptr, 0, 0, 0, s))) return st;
     NNCK(cudaGetLastError());

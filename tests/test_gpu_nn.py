@@ -34,9 +34,14 @@ def _rel(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
 
 
+# The first seven shapes take the per-tap kernel; the last three the
+# slab-fed one (rows of 64, 32 and 16 voxels; y and z tails shorter than the
+# output box; 1 to 3 K chunks of 16 or 32 channels; up to 16 channel tiles),
+# and the input gradient of (2, 13, 10, 32) x 48 -> 160 as well.
 @pytest.mark.parametrize("shape,cin,cout", [((2, 5, 6, 7), 32, 48), ((1, 9, 4, 3), 16, 16), ((1, 8, 8, 8), 192, 64),
                                              ((1, 6, 5, 4), 48, 32), ((2, 4, 4, 4), 96, 16), ((1, 4, 5, 6), 80, 256),
-                                             ((1, 3, 3, 3), 320, 32)])
+                                             ((1, 3, 3, 3), 320, 32), ((1, 9, 7, 64), 16, 256),
+                                             ((2, 13, 10, 32), 48, 160), ((4, 16, 16, 16), 64, 64)])
 def test_conv3d_forward_dgrad_wgrad(libsoc, shape, cin, cout):
     rng = np.random.default_rng(cin + cout)
     x, x64 = _bf(rng.standard_normal(shape + (cin,)))
@@ -46,6 +51,9 @@ def test_conv3d_forward_dgrad_wgrad(libsoc, shape, cin, cout):
     libsoc.conv3d(x, w, b, relu=False, out_f32=y)
     ref = O.conv3d(x64, w64, b.cpu().numpy().astype(np.float64))
     assert _rel(y.cpu().numpy(), ref) < 1e-4
+    # every output (a voxel or channel mapped to the wrong accumulator row or
+    # column is off by the order of the outputs themselves)
+    assert np.abs(y.cpu().numpy() - ref).max() < 1e-3 * max(np.abs(ref).max(), 1.0)
     # BF16 output with ReLU
     y16 = torch.zeros(shape + (cout,), dtype=torch.bfloat16, device="cuda")
     libsoc.conv3d(x, w, b, relu=True, out=y16)
