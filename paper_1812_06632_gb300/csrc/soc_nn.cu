@@ -408,9 +408,9 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tma_kernel(const __grid_c
 // W dividing 128.  An output box is bx = W by by x bz voxels of one sample,
 // n_acc groups of 128 voxels (g = 128 / W consecutive rows each, gyn groups
 // along y, bz along z).  For every chunk of KC input channels and x offset
-// dx, one TMA load brings the slab of voxels x + dx - 1 (x = 0 .. W - 1),
-// y0 - 1 .. y0 + by, z0 - 1 .. z0 + bz (out-of-volume voxels read zero),
-// and nine loads the weights of the taps (dx, dy, dz).  The A operand of tap
+// dx, TMA loads (one per row) bring the slab of voxels x + dx - 1 (x = 0 ..
+// W - 1), y0 - 1 .. y0 + by, z0 - 1 .. z0 + bz (out-of-volume voxels read
+// zero), and nine loads the weights of the taps (dx, dy, dz).  The A operand of tap
 // (dy, dz) and group (gy, gz) is the 128 consecutive slab rows from
 // ((gz + dz)(by + 2) + g gy + dy) W on: a multiple of 8 rows, so the swizzle
 // atoms stay aligned.  Every input voxel is then read from L2 3 (by + 2)
@@ -424,7 +424,7 @@ struct SlabArgs {
     ConvOut o;
 };
 
-template <int KC>
+template <int KC, int NACC>
 __global__ void __launch_bounds__(kConvThreads, 1) conv3d_slab_kernel(const __grid_constant__ CUtensorMap map_in,
                                                                    const __grid_constant__ CUtensorMap map_w,
                                                                    const SlabArgs a, int n_tile, uint32_t tmem_cols,
@@ -477,6 +477,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3d_slab_kernel(const __gr
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&map_in)) : "memory");
             asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&map_w)) : "memory");
+            const int n_rows = (a.by + 2) * (a.bz + 2), row_bytes = bx * kRow;
             int st = 0, issued = 0;
             uint32_t ph = 0;
             bool stop = false;
@@ -495,7 +496,14 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3d_slab_kernel(const __gr
                         const uint32_t dst = smem0 + (uint32_t)(st * stage_bytes);
                         const uint32_t bar = smem_u32(&full[st]);
                         mbar_expect_tx(bar, tx_bytes);
-                        tma_load_5d(dst, &map_in, c0, dx - 1, y0, z0, nn, bar);
+                        // the slab one row (y, z) at a time: many short
+                        // copies in flight keep the copy engine busier
+                        // than one large box
+                        for (int r = 0, ry = 0, rz = 0; r < n_rows; ++r) {
+                            tma_load_5d(dst + (uint32_t)(r * row_bytes), &map_in, c0, dx - 1, y0 + ry, z0 + rz, nn,
+                                        bar);
+                            if (++ry == a.by + 2) { ry = 0; ++rz; }
+                        }
                         // weights of taps 9 dz + 3 dy + dx, block 3 dz + dy
                         for (int t9 = 0; t9 < 9; ++t9)
                             tma_load_2d(dst + (uint32_t)(slab_bytes + t9 * tap_bytes), &map_w,
@@ -513,6 +521,19 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3d_slab_kernel(const __gr
         if (lane == 0) {
             const uint32_t idesc = mma_idesc(128, n_tile);
             const int steps = 3 * (a.Cin / KC);
+            // descriptor start-address offsets (16-byte units): A rows of
+            // group q at dy = dz = 0, one row of the slab in y and in z, one
+            // tap's weights (a descriptor plus an offset names the shifted
+            // operand: smem addresses stay below 2^18, the 14-bit field
+            // does not overflow)
+            uint32_t q_off[NACC];
+#pragma unroll
+            for (int q = 0; q < NACC; ++q) {
+                const int gz = q / a.gyn, gy = q - gz * a.gyn;
+                q_off[q] = (uint32_t)((gz * (a.by + 2) + gy * a.g) * bx * kRow) >> 4;
+            }
+            const uint32_t dy_off = (uint32_t)(bx * kRow) >> 4, dz_off = (uint32_t)((a.by + 2) * bx * kRow) >> 4;
+            const uint32_t tap_off = (uint32_t)tap_bytes >> 4;
             int st = 0, i = 0;
             uint32_t ph = 0;
             for (int box = blockIdx.x; box < n_boxes && !*fail; box += gridDim.x, ++i) {
@@ -522,7 +543,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3d_slab_kernel(const __gr
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t acc0 = tmem + (uint32_t)(b * a.n_acc * n_tile);
+                const uint32_t acc0 = tmem + (uint32_t)(b * NACC * n_tile);
                 for (int s = 0; s < steps; ++s) {
                     if (!mbar_wait(smem_u32(&full[st]), ph)) {
                         atomicExch(s_fail, 1);
@@ -531,22 +552,21 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3d_slab_kernel(const __gr
                     if (*fail) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t a0 = smem0 + (uint32_t)(st * stage_bytes);
+                    const uint64_t da = smem_desc_sw(a0, kRow), db = smem_desc_sw(a0 + (uint32_t)slab_bytes, kRow);
+#pragma unroll
                     for (int t9 = 0; t9 < 9; ++t9) {
-                        const int dz = t9 / 3, dy = t9 - 3 * dz;
-                        const uint32_t b0 = a0 + (uint32_t)(slab_bytes + t9 * tap_bytes);
-                        for (int q = 0; q < a.n_acc; ++q) {
-                            const int gz = q / a.gyn, gy = q - gz * a.gyn;
-                            const int row = ((gz + dz) * (a.by + 2) + gy * a.g + dy) * bx;
-                            const uint32_t ar = a0 + (uint32_t)(row * kRow);
-                            const uint32_t acc_addr = acc0 + (uint32_t)(q * n_tile);
+                        const uint32_t rt = (uint32_t)(t9 / 3) * dz_off + (uint32_t)(t9 % 3) * dy_off;
+#pragma unroll
+                        for (int q = 0; q < NACC; ++q) {
 #pragma unroll
                             for (int j = 0; j < KC / 16; ++j) {
-                                const uint64_t ad = smem_desc_sw(ar + j * 32, kRow);
-                                const uint64_t bd = smem_desc_sw(b0 + j * 32, kRow);
+                                const uint64_t ad = da + (q_off[q] + rt + 2u * j);
+                                const uint64_t bd = db + ((uint32_t)t9 * tap_off + 2u * j);
                                 const uint32_t acc = (s > 0 || t9 > 0 || j > 0) ? 1u : 0u;
                                 asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                                              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                                             :: "r"(acc_addr), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+                                             :: "r"(acc0 + (uint32_t)(q * n_tile)), "l"(ad), "l"(bd), "r"(idesc),
+                                                "r"(acc) : "memory");
                             }
                         }
                     }
@@ -570,12 +590,13 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3d_slab_kernel(const __gr
             const int ty = box % a.tiles_y, qq = box / a.tiles_y;
             const int tz = qq % a.tiles_z, nn = qq / a.tiles_z;
             const int x = tid % bx;
-            for (int q = 0; q < a.n_acc; ++q) {
+#pragma unroll
+            for (int q = 0; q < NACC; ++q) {
                 const int gz = q / a.gyn, gy = q - gz * a.gyn;
                 const int y = ty * a.by + gy * a.g + tid / bx, z = tz * a.bz + gz;
                 const bool vin = y < a.H && z < a.D;
                 const long long v = vin ? (((long long)nn * a.D + z) * a.H + y) * a.W + x : 0;
-                const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((b * a.n_acc + q) * n_tile);
+                const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((b * NACC + q) * n_tile);
                 for (int c = 0; c < n_tile; c += 16) {
                     uint32_t rr[16];
                     tmem_ld16(row_addr + (uint32_t)c, rr);
@@ -1318,7 +1339,7 @@ bool slab_plan(const ConvArgs &a, int sms, int sm_smem, int blk_max, SlabPlan &p
     return false;
 }
 
-template <int KC>
+template <int KC, int NACC>
 cudaError_t slab_launch(const ConvArgs &a, const SlabPlan &p, int sms, cudaStream_t s)
 {
     auto encode = encode_tiled();
@@ -1339,7 +1360,7 @@ cudaError_t slab_launch(const ConvArgs &a, const SlabPlan &p, int sms, cudaStrea
                                     (cuuint64_t)a.N};
         const cuuint64_t vb = (cuuint64_t)a.in_stride * 2;
         const cuuint64_t strides[4] = {vb, vb * a.W, vb * a.W * a.H, vb * a.W * a.H * a.D};
-        const cuuint32_t box[5] = {(cuuint32_t)KC, (cuuint32_t)a.W, (cuuint32_t)(p.by + 2), (cuuint32_t)(p.bz + 2), 1};
+        const cuuint32_t box[5] = {(cuuint32_t)KC, (cuuint32_t)a.W, 1, 1, 1};       // one row of the slab
         const cuuint32_t es[5] = {1, 1, 1, 1, 1};
         if (encode(&map_in, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, reinterpret_cast<void *>(in_addr), dims, strides, box,
                    es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -1358,13 +1379,13 @@ cudaError_t slab_launch(const ConvArgs &a, const SlabPlan &p, int sms, cudaStrea
     }
     uint32_t cols = 32;
     while ((int)cols < 2 * p.n_acc * p.n_tile) cols <<= 1;
-    cudaError_t e = cudaFuncSetAttribute(conv3d_slab_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.bytes);
+    cudaError_t e = cudaFuncSetAttribute(conv3d_slab_kernel<KC, NACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.bytes);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(conv3d_slab_kernel<KC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(conv3d_slab_kernel<KC, NACC>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, conv3d_slab_kernel<KC>);
+    e = cudaFuncGetAttributes(&fa, conv3d_slab_kernel<KC, NACC>);
     if (e != cudaSuccess) return e;
     const int warp_regs = ((fa.numRegs + 7) / 8) * 8 * 32;
     const int occ = std::max(1, std::min(p.per_sm, 65536 / (warp_regs * (kConvThreads / 32))));
@@ -1372,7 +1393,7 @@ cudaError_t slab_launch(const ConvArgs &a, const SlabPlan &p, int sms, cudaStrea
     const long long n_boxes = (long long)t.tiles_y * t.tiles_z * a.N;
     const long long slots = std::max(1LL, (long long)sms * occ / grid_y);
     dim3 grid((unsigned)std::min(n_boxes, slots), (unsigned)grid_y);
-    conv3d_slab_kernel<KC><<<grid, kConvThreads, p.bytes, s>>>(map_in, map_w, t, p.n_tile, cols, p.stages,
+    conv3d_slab_kernel<KC, NACC><<<grid, kConvThreads, p.bytes, s>>>(map_in, map_w, t, p.n_tile, cols, p.stages,
                                                                p.slab_bytes, p.stage_bytes);
     return cudaGetLastError();
 }
@@ -1387,8 +1408,13 @@ cudaError_t conv_launch(const ConvArgs &a, cudaStream_t s)
     cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&blk_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     SlabPlan p{};
-    if (slab_plan(a, sms, sm_smem, blk_max, p))
-        return p.kc == 32 ? slab_launch<32>(a, p, sms, s) : slab_launch<16>(a, p, sms, s);
+    if (slab_plan(a, sms, sm_smem, blk_max, p)) {
+        if (p.kc == 32)
+            return p.n_acc == 4 ? slab_launch<32, 4>(a, p, sms, s)
+                                : (p.n_acc == 2 ? slab_launch<32, 2>(a, p, sms, s) : slab_launch<32, 1>(a, p, sms, s));
+        return p.n_acc == 4 ? slab_launch<16, 4>(a, p, sms, s)
+                            : (p.n_acc == 2 ? slab_launch<16, 2>(a, p, sms, s) : slab_launch<16, 1>(a, p, sms, s));
+    }
     if (a.Cin % 64 == 0) return tma_launch<64>(a, s);
     if (a.Cin % 32 == 0) return tma_launch<32>(a, s);
     return tma_launch<16>(a, s);
