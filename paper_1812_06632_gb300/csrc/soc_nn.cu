@@ -711,37 +711,60 @@ __global__ void __launch_bounds__(128) conv3d_wgrad_tc_kernel(const WgradArgs a,
     const uint32_t idesc = mma_idesc_mn(128, n_tile);
     const int kv = tid & (kWgKV - 1), half = tid >> 6;                 // this thread's voxel and half
 
+    // this thread's 8 pieces of A: piece pc = half * 8 + i is tap tap0 +
+    // pc / CP of the block (offsets tdx, tdy, tdz), channels tco
+    int tdx[8], tdy[8], tdz[8], tco[8];
+    bool tin[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int pc = half * 8 + i, tl = pc / CP, tap = tap0 + tl;
+        tin[i] = tap < 27;
+        tdz[i] = tap / 9 - 1;
+        tdy[i] = (tap / 3) % 3 - 1;
+        tdx[i] = tap % 3 - 1;
+        tco[i] = a.x_off + ci0 + (pc - tl * CP) * 8;
+    }
+    // the voxel of the next step, advanced by kWgKV per step
+    long long cv = vb + kv;
+    int cx = 0, cy = 0, cz = 0;
+    long long cn = 0;
+    {
+        long long q = cv < V ? cv : 0;
+        cx = (int)(q % a.W); q /= a.W;
+        cy = (int)(q % a.H); q /= a.H;
+        cz = (int)(q % a.D); cn = q / a.D;
+    }
+
     auto issue = [&](int t) {
         if (t < total) {
             const uint32_t st = smem0 + (uint32_t)((t % n_stages) * stage_bytes);
-            const long long v = vb + (long long)t * kWgKV + kv;
+            const long long v = cv;
             const bool vin = v < ve;
-            int xx0 = 0, yy0 = 0, zz0 = 0;
-            long long nn = 0;
-            if (vin) {
-                long long q = v;
-                xx0 = (int)(q % a.W); q /= a.W;
-                yy0 = (int)(q % a.H); q /= a.H;
-                zz0 = (int)(q % a.D); nn = q / a.D;
-            }
-            // A: the 16 pieces of this voxel's row of cores: piece p = tap
-            // (p / CP) of the block, channels ci0 + (p % CP) * 8
+            // A: the 16 pieces of this voxel's row of cores
             const uint32_t arow = st + (uint32_t)(((kv >> 3) * 16) * 128 + (kv & 7) * 16);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const int pc = half * 8 + i;
-                const int tl = pc / CP, c8 = pc - tl * CP;
-                const int tap = tap0 + tl;
-                const int zz = zz0 + tap / 9 - 1, yy = yy0 + (tap / 3) % 3 - 1, xx = xx0 + tap % 3 - 1;
-                const bool ok = vin && tap < 27 && zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-                const long long sv = ok ? ((nn * a.D + zz) * a.H + yy) * a.W + xx : 0;
-                cp_async16(arow + pc * 128, a.x + sv * a.x_stride + a.x_off + ci0 + c8 * 8, ok ? 16u : 0u);
+                const int zz = cz + tdz[i], yy = cy + tdy[i], xx = cx + tdx[i];
+                const bool ok = vin && tin[i] && (unsigned)zz < (unsigned)a.D && (unsigned)yy < (unsigned)a.H &&
+                                (unsigned)xx < (unsigned)a.W;
+                const long long sv = ok ? ((cn * a.D + zz) * a.H + yy) * a.W + xx : 0;
+                cp_async16(arow + (half * 8 + i) * 128, a.x + sv * a.x_stride + tco[i], ok ? 16u : 0u);
             }
             // B: gy[v][co0 .. co0 + n_tile - 1], half of the NC pieces
             const uint32_t brow = st + (uint32_t)a_bytes + (uint32_t)(((kv >> 3) * NC) * 128 + (kv & 7) * 16);
             for (int nc = half * (NC / 2); nc < (half + 1) * (NC / 2); ++nc)
                 cp_async16(brow + nc * 128, a.gy + (vin ? v * a.gy_stride : 0) + a.gy_off + co0 + nc * 8,
                            vin ? 16u : 0u);
+            // next step's voxel: kWgKV further along x, carried into y, z, n
+            cv += kWgKV;
+            cx += kWgKV;
+            while (cx >= a.W) {
+                cx -= a.W;
+                if (++cy == a.H) {
+                    cy = 0;
+                    if (++cz == a.D) { cz = 0; ++cn; }
+                }
+            }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
