@@ -43,9 +43,20 @@ import numpy as np
 from . import inputs as I
 
 T_MIN, T_MAX = 2.7, 3000.0
-TRAIN = list(range(1000, 1160))
+TRAIN = list(range(1000, 1160)) + list(range(1200, 1360))
 VAL = list(range(1160, 1180))
 TEST = list(range(1180, 1200))
+
+
+def seed_ranges(seeds):
+    """[[first, last], ...] of the consecutive runs in a list of seeds."""
+    out = []
+    for v in sorted(set(int(x) for x in seeds)):
+        if out and v == out[-1][1] + 1:
+            out[-1][1] = v
+        else:
+            out.append([v, v])
+    return out
 HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS = os.path.join(HERE, "data", "unet_c4_hotcore.npz")
 PACKAGES = dict(n_background=200_000, n_point=200_000)
@@ -107,6 +118,65 @@ def snapshots(ctx, ids, w, ks, tol=0.1):
         out[k] = [t.clone() for t in T]
         k_prev = k
     return out, done, conv
+
+
+def seeded_run(ctx, ids, seeder, starts, max_iter=300, tol=0.1, reseed=None):
+    """Dust iterations of every cloud from its start temperatures to
+    max |dT| < tol.  With reseed = R (>= 2), every R iterations the clouds
+    not yet converged are seeded again by the network from their last two
+    iterates, the same inputs as the first seeding (the Monte Carlo
+    iterations still judge every seed).  Returns per cloud the rows of
+    `dust_iterations` summed over the segments, and the final temperatures."""
+    import torch
+    n = len(ids)
+    rows = [dict(iterations=0, converged=False, steps=0, final_max_dT=None) for _ in range(n)]
+    final = [None] * n
+    cur = list(starts)
+    active = list(range(n))
+
+    def run(js, seeds, its):
+        outs = [torch.empty_like(seeds[i]) for i in range(len(js))]
+        got = dust_iterations(ctx, [ids[j] for j in js], outs, seeds=seeds, max_iter=its, tol=tol)
+        for i, j in enumerate(js):
+            rows[j]["iterations"] += got[i]["iterations"]
+            rows[j]["steps"] += got[i]["steps"]
+            rows[j]["converged"] = got[i]["converged"]
+            rows[j]["final_max_dT"] = got[i].get("final_max_dT")
+        return outs, got
+
+    while active:
+        left = max_iter - rows[active[0]]["iterations"]       # equal for every active cloud
+        if reseed is None or left <= reseed:
+            outs, _ = run(active, [cur[j] for j in active], left)
+            for i, j in enumerate(active):
+                final[j] = outs[i]
+            break
+        # R - 1 iterations, then one more: the pair (T_{m-1}, T_m) of the next seed
+        ta, got = run(active, [cur[j] for j in active], reseed - 1)
+        still = []
+        for i, j in enumerate(active):
+            if got[i]["converged"]:
+                final[j] = ta[i]
+            else:
+                still.append((j, ta[i]))
+        if not still:
+            break
+        js = [j for j, _ in still]
+        tb, got = run(js, [t for _, t in still], 1)
+        nxt, prev = [], []
+        for i, j in enumerate(js):
+            if got[i]["converged"]:
+                final[j] = tb[i]
+            else:
+                nxt.append(j)
+                prev.append((dict(still)[j], tb[i]))
+        if not nxt:
+            break
+        s = seeder.seeds(ctx, [ids[j] for j in nxt], [b for _, b in prev], [a for a, _ in prev])
+        for i, j in enumerate(nxt):
+            cur[j] = s[i]
+        active = nxt
+    return rows, final
 
 
 def make_dataset(seeds, side=64, seed_after=(3,), chunk=20, max_iter=300, tol=0.1, log=print):
@@ -210,9 +280,12 @@ def repeats(iterations, cap=8):
     return np.clip(np.rint(it / np.median(it)), 1, cap).astype(np.int64)
 
 
-def train(X, Y, Xv, Yv, epochs=80, patience=12, batch=4, lr=2e-3, seed=0, reps=None, log=print):
+def train(X, Y, Xv, Yv, epochs=80, patience=16, batch=4, lr=1e-3, seed=0, reps=None, warmup_epochs=2, log=print):
     """Adam on the MSE of the normalised target (a constant predictor scores
-    1), learning rate decaying linearly to 10 %; each epoch visits cloud c
+    1), learning rate rising linearly from 0 over the first warmup_epochs
+    (the first full-rate steps on the freshly initialised network blew the
+    loss up to ~100, and whether training recovered depended on rounding
+    order), then decaying linearly to 10 %; each epoch visits cloud c
     reps[c] times (default once); after every epoch the validation loss
     decides which weights are kept, and training stops after `patience`
     epochs without improvement.  Returns (best parameters, train loss
@@ -228,13 +301,17 @@ def train(X, Y, Xv, Yv, epochs=80, patience=12, batch=4, lr=2e-3, seed=0, reps=N
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
     hist, vhist = [], []
     best, best_ep = None, -1
+    per_epoch = order.size // batch
+    warm = max(1, warmup_epochs * per_epoch)
+    step = 0
     for ep in range(epochs):
         perm = torch.from_numpy(rng.permutation(order)).cuda()
         tot = 0.0
         for b0 in range(0, order.size - batch + 1, batch):
             idx = perm[b0:b0 + batch]
             net.backward(X.index_select(0, idx).contiguous(), Y.index_select(0, idx).contiguous(), loss=loss)
-            net.adam(lr * (1.0 - 0.9 * ep / max(1, epochs - 1)))
+            step += 1
+            net.adam(lr * (1.0 - 0.9 * ep / max(1, epochs - 1)) * min(1.0, step / warm))
             tot += loss.item()
         hist.append(tot / max(1, order.size // batch))
         vhist.append(_mse(net, Xv, Yv, batch))
@@ -333,13 +410,14 @@ class Seeder:
         self.net.close()
 
 
-def compare(params, norm, seeds=TEST, side=64, max_iter=300, tol=0.1, log=print):
+def compare(params, norm, seeds=TEST, side=64, max_iter=300, tol=0.1, reseed=None, log=print):
     """Wall time to max |dT| < tol of the batch of clouds `seeds`: iteration 0
     (shared), then the dust iterations plain and learned-seeded, each as one
     batched run (one tracer launch per iteration for every unconverged
     cloud).  The seeded run makes norm["seed_after"] plain dust iterations,
     then seeds every cloud from their result (features, network forward,
-    transform, all in its time) and iterates on."""
+    transform, all in its time) and iterates on; with reseed = R the clouds
+    still unconverged are seeded again every R iterations (seeded_run)."""
     import torch
     k = int(norm["seed_after"])
     w = I.config_c4(seeds, side=side)
@@ -380,9 +458,12 @@ def compare(params, norm, seeds=TEST, side=64, max_iter=300, tol=0.1, log=print)
     s = seeder.seeds(ctx, ids, Tk, Tp)
     done = [f["converged"] or l["converged"] for f, l in zip(first, last)]
     s = [Tk[j] if done[j] else s[j] for j in range(len(ids))]
-    learn = dust_iterations(ctx, ids, T_learn, seeds=s, max_iter=max_iter, tol=tol)
+    learn, fin = seeded_run(ctx, ids, seeder, s, max_iter=max_iter, tol=tol, reseed=reseed)
     torch.cuda.synchronize()
     t_learn = time.perf_counter() - t0
+    for j in range(len(ids)):
+        if fin[j] is not None:
+            T_learn[j].copy_(fin[j])
     learn_its = [f["iterations"] + l["iterations"] + r["iterations"] for f, l, r in zip(first, last, learn)]
 
     # seed quality: max |T_seed - T_converged| against the same for T_k (the start it replaces)
@@ -392,7 +473,8 @@ def compare(params, norm, seeds=TEST, side=64, max_iter=300, tol=0.1, log=print)
     dmax = max((float((T_plain[j] - T_learn[j]).abs().max().item()) for j in both), default=0.0)
     seeder.close()
     ctx.close()
-    out = dict(n_clouds=len(ids), side=side, tol_K=tol, seed_after=k, constant_s=t_const, plain_dust_s=t_plain,
+    out = dict(n_clouds=len(ids), side=side, tol_K=tol, seed_after=k, reseed_every=reseed, constant_s=t_const,
+               plain_dust_s=t_plain,
                learned_dust_s=t_learn, plain_s=t_const + t_plain, learned_s=t_const + t_learn,
                plain_iterations=[r["iterations"] for r in plain], learned_iterations=learn_its,
                plain_converged=sum(r["converged"] for r in plain), learned_converged=sum(r["converged"] for r in learn),
@@ -432,11 +514,43 @@ def choose_shrink(params, norm, seeds=VAL, side=64, max_iter=300, tol=0.1, shrin
     return best, table
 
 
-SEED_AFTER = (3, 5)
+RESEEDS = (None, 10, 20, 40)
 
 
-def run(side=64, epochs=80, patience=12, max_iter=300, tol=0.1, lr=2e-3, out=WEIGHTS, seed_after=SEED_AFTER,
-        log=print):
+def choose_reseed(params, norm, seeds=VAL, side=64, max_iter=300, tol=0.1, options=RESEEDS, log=print):
+    """Dust iterations and wall time of the validation clouds, seeded once
+    and re-seeded every R iterations for every R in options; returns (the R
+    with the shortest wall time, table)."""
+    import torch
+    k = int(norm["seed_after"])
+    w = I.config_c4(seeds, side=side)
+    ctx, ids = context(w)
+    seeder = Seeder(params, norm, len(ids), side)
+    sn, done, conv = snapshots(ctx, ids, w, (k - 1, k), tol)
+    s0 = seeder.seeds(ctx, ids, sn[k], sn[k - 1])
+    s0 = [sn[k][j] if conv[j] else s0[j] for j in range(len(ids))]
+    seeded_run(ctx, ids, seeder, s0, max_iter=2, tol=tol, reseed=None)           # warm-up
+    table = {}
+    for R in options:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rows, _ = seeded_run(ctx, ids, seeder, s0, max_iter=max_iter, tol=tol, reseed=R)
+        torch.cuda.synchronize()
+        table[str(R)] = dict(iterations=sum(done) + sum(0 if conv[j] else r["iterations"] for j, r in enumerate(rows)),
+                             converged=sum(r["converged"] for r in rows), wall_s=time.perf_counter() - t0)
+    seeder.close()
+    ctx.close()
+    best = min(options, key=lambda R: table[str(R)]["wall_s"])
+    log(json.dumps({"seed_after": k, "validation": table, "reseed_every": best}))
+    return best, table
+
+
+# k = 5 won the validation sweeps against 3 and against 10
+SEED_AFTER = (5,)
+
+
+def run(side=64, epochs=80, patience=16, max_iter=300, tol=0.1, lr=1e-3, out=WEIGHTS, seed_after=SEED_AFTER,
+        train_seeds=TRAIN, log=print):
     """Data (plain Monte Carlo on the training and validation clouds), then
     for every candidate k in `seed_after` (the network's inputs come from T
     after k - 1 and k plain dust iterations) training with validation-based
@@ -445,9 +559,9 @@ def run(side=64, epochs=80, patience=12, max_iter=300, tol=0.1, lr=2e-3, out=WEI
     with the fewest validation dust iterations are kept, saved to `out`, and
     compared on the test clouds."""
     t0 = time.perf_counter()
-    snaps, T, rho, info = make_dataset(TRAIN + VAL, side, seed_after, max_iter=max_iter, tol=tol, log=log)
+    snaps, T, rho, info = make_dataset(list(train_seeds) + VAL, side, seed_after, max_iter=max_iter, tol=tol, log=log)
     t_data = time.perf_counter() - t0
-    ntr = len(TRAIN)
+    ntr = len(train_seeds)
     reps = repeats([r["iterations"] for r in info[:ntr]])
     best = None
     tried = {}
@@ -472,7 +586,7 @@ def run(side=64, epochs=80, patience=12, max_iter=300, tol=0.1, lr=2e-3, out=WEI
     t_train = time.perf_counter() - t1
     del snaps, T, rho
     _, k, params, norm, env, shrink = best
-    meta = dict(train=[TRAIN[0], TRAIN[-1]], val=[VAL[0], VAL[-1]], side=side, seed_after=k, tried=tried,
+    meta = dict(train=seed_ranges(train_seeds), val=[VAL[0], VAL[-1]], side=side, seed_after=k, tried=tried,
                 best_epoch=tried[k]["best_epoch"], epochs_run=tried[k]["epochs_run"], lr=lr, tol_K=tol,
                 data_seconds=t_data, train_seconds=t_train, train_info=info, repeats=reps.tolist())
     if out:
@@ -510,10 +624,10 @@ def main():
     ap = argparse.ArgumentParser(description="learned temperature seed: data, training, comparison")
     ap.add_argument("--side", type=int, default=64)
     ap.add_argument("--epochs", type=int, default=80)
-    ap.add_argument("--patience", type=int, default=12)
+    ap.add_argument("--patience", type=int, default=16)
     ap.add_argument("--max-iter", type=int, default=300)
     ap.add_argument("--tol", type=float, default=0.1)
-    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed-after", type=int, nargs="+", default=list(SEED_AFTER),
                     help="candidate numbers of plain dust iterations before the network seeds the rest")
     ap.add_argument("--out", default=WEIGHTS, help="where the trained weights are written")
