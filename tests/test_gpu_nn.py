@@ -34,14 +34,19 @@ def _rel(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
 
 
-# The first seven shapes take the per-tap kernel; the last three the
-# slab-fed one (rows of 64, 32 and 16 voxels; y and z tails shorter than the
-# output box; 1 to 3 K chunks of 16 or 32 channels; up to 16 channel tiles),
-# and the input gradient of (2, 13, 10, 32) x 48 -> 160 as well.
+# The first seven shapes take the per-tap kernel; the others the slab-fed
+# one: rows of 64, 32 and 16 voxels; y and z tails shorter than the output
+# box; 1 to 3 K chunks of 16 or 32 channels; up to 16 channel tiles; 1, 2
+# or 4 accumulator groups; channel tiles of 16, 32 and 48 (the last with all
+# 512 tensor-memory columns, three stages and one block per SM), in the
+# forward direction and, for several, in the input gradient as well (the
+# plans the U-Net's 64^3 training takes).
 @pytest.mark.parametrize("shape,cin,cout", [((2, 5, 6, 7), 32, 48), ((1, 9, 4, 3), 16, 16), ((1, 8, 8, 8), 192, 64),
                                              ((1, 6, 5, 4), 48, 32), ((2, 4, 4, 4), 96, 16), ((1, 4, 5, 6), 80, 256),
                                              ((1, 3, 3, 3), 320, 32), ((1, 9, 7, 64), 16, 256),
-                                             ((2, 13, 10, 32), 48, 160), ((4, 16, 16, 16), 64, 64)])
+                                             ((2, 13, 10, 32), 48, 160), ((4, 16, 16, 16), 64, 64),
+                                             ((4, 32, 32, 32), 16, 32), ((4, 16, 16, 16), 64, 32),
+                                             ((1, 76, 16, 64), 16, 48), ((3, 32, 16, 32), 32, 96)])
 def test_conv3d_forward_dgrad_wgrad(libsoc, shape, cin, cout):
     rng = np.random.default_rng(cin + cout)
     x, x64 = _bf(rng.standard_normal(shape + (cin,)))
