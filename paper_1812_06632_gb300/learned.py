@@ -490,7 +490,9 @@ def compare(params, norm, seeds=TEST, side=64, max_iter=300, tol=0.1, reseed=Non
     return out
 
 
-SHRINKS = (0.5, 0.65, 0.8, 0.9, 1.0)
+# factors of the predicted correction tried on the validation clouds (above 1
+# over-relaxes it; 1.35 and 1.5 overshot)
+SHRINKS = (0.5, 0.65, 0.8, 0.9, 1.0, 1.1, 1.2)
 
 
 def choose_shrink(params, norm, seeds=VAL, side=64, max_iter=300, tol=0.1, shrinks=SHRINKS, log=print):

@@ -28,7 +28,7 @@ def test_committed_weights_are_well_formed():
     assert params.dtype == np.float32 and params.size == L.init_params(0).size
     assert np.all(np.isfinite(params))
     assert norm["seed_after"] in (3, 5, 10) and norm["seed_after"] == meta["seed_after"]
-    assert 0.0 < norm["shrink"] <= 1.0
+    assert norm["shrink"] in L.SHRINKS                      # a factor the validation sweep tried
     lo, hi, y_lo, y_hi = norm["env"]
     assert lo < hi and len(y_lo) == len(y_hi) == L.ENV_BINS
     assert all(0.0 <= a <= b for a, b in zip(y_lo, y_hi))   # the seed never lowers T (y >= 0)
