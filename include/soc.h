@@ -586,6 +586,13 @@ soc_status soc_nn_conv3d_wgrad(const void *gy, const void *x, int N, int D, int 
 soc_status soc_nn_adam(float *d_w, float *d_m, float *d_v, const float *d_g, int64_t n, float lr, int32_t t,
                        void *d_w_bf16, void *stream);
 
+/* soc_nn_scale_add: d_y[i] = fma(a, d_x[i], d_y[i]) for i < n (device FP32,
+ * d_y in/out, one rounding per element), in the order of the calls on the
+ * stream.  The learned seed averages the predictions of an ensemble of
+ * networks with it (a = 1/K per member, members in a fixed order, so the
+ * mean is bit-reproducible).  SOC_ERR_ARG for null pointers, n < 1 or a NaN. */
+soc_status soc_nn_scale_add(float *d_y, const float *d_x, int64_t n, float a, void *stream);
+
 /* ------------------------------------------------------------------------
  * Seeding transform of the learned temperature seed (not a step of the
  * paper's method), per cell of an uploaded regular grid, in FP64:

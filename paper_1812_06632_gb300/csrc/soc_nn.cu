@@ -1106,6 +1106,14 @@ __global__ void adam_kernel(float *w, float *m, float *v, const float *g, long l
     }
 }
 
+// y[i] = fma(a, x[i], y[i]): one rounding per element (the mean of an
+// ensemble's predictions, summed member by member in a fixed order).
+__global__ void scale_add_kernel(float *y, const float *x, long long n, float a)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = __fmaf_rn(a, x[i], y[i]);
+}
+
 __global__ void to_bf16_kernel(const float *src, long long n, bf16 *dst)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -2039,6 +2047,14 @@ soc_status soc_nn_adam(float *d_w, float *d_m, float *d_v, const float *d_g, int
     const float c2 = (float)(1.0 - std::pow((double)b2, (double)t));
     adam_kernel<<<grid_1d(n), 256, 0, (cudaStream_t)stream>>>(d_w, d_m, d_v, d_g, n, lr, b1, b2, eps, c1, c2,
                                                               (bf16 *)d_w_bf16);
+    NNCK(cudaGetLastError());
+    return SOC_OK;
+}
+
+soc_status soc_nn_scale_add(float *d_y, const float *d_x, int64_t n, float a, void *stream)
+{
+    if (!d_y || !d_x || n < 1 || !(a == a)) return SOC_ERR_ARG;
+    scale_add_kernel<<<grid_1d(n), 256, 0, (cudaStream_t)stream>>>(d_y, d_x, n, a);
     NNCK(cudaGetLastError());
     return SOC_OK;
 }

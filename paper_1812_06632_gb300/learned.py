@@ -376,18 +376,29 @@ def load_weights(path=WEIGHTS):
     return z["params"], norm, json.loads(str(z["meta"])), digest
 
 
+def members(params):
+    """The parameter vectors of an ensemble ([K, P]; one network is K = 1)."""
+    p = np.asarray(params, np.float32)
+    return p.reshape(1, -1) if p.ndim == 1 else p
+
+
 class Seeder:
-    """The trained network ready for a batch of n clouds of one side (its
-    buffers are allocated once, like loading a model)."""
+    """The trained network (or ensemble) ready for a batch of n clouds of one
+    side (its buffers are allocated once, like loading a model).  An
+    ensemble's prediction is the mean of its members', summed member by
+    member in the library (soc_nn_scale_add)."""
 
     def __init__(self, params, norm, n, side):
         import torch
         from . import soc
+        self.soc = soc
         self.norm, self.side = norm, side
+        self.members = members(params)
         self.net = soc.UNet(n, side, n_inputs=3)
-        self.net.set_params(params)
+        self.net.set_params(self.members[0])
         self.x = torch.empty((n, side, side, side, 3), dtype=torch.float32, device="cuda")
         self.pred = torch.empty((n, side, side, side), dtype=torch.float32, device="cuda")
+        self.mean = torch.empty_like(self.pred) if len(self.members) > 1 else None
 
     def seeds(self, ctx, ids, Tks, Tps, shrink=None):
         """T_seed of every cloud from T_k and T_{k-1}: features, one batched
@@ -398,11 +409,20 @@ class Seeder:
         out = []
         for k, cid in enumerate(ids):
             ctx.seed_features(cid, Tks[k], _norm6(self.norm), self.x[k], T_prev=Tps[k])
-        self.net.forward(self.x, self.pred)
+        pred = self.pred
+        if self.mean is None:
+            self.net.forward(self.x, self.pred)
+        else:
+            self.mean.zero_()
+            for p in self.members:
+                self.net.set_params(p)
+                self.net.forward(self.x, self.pred)
+                self.soc.scale_add(self.mean, self.pred, 1.0 / len(self.members))
+            pred = self.mean
         m = seed_map(self.norm, self.norm.get("shrink", 1.0) if shrink is None else shrink, self.norm.get("env"))
         for k, cid in enumerate(ids):
             t = torch.empty_like(Tks[k])
-            ctx.seed_transform(cid, Tks[k], self.pred[k].reshape(-1), m, t)
+            ctx.seed_transform(cid, Tks[k], pred[k].reshape(-1), m, t)
             out.append(t)
         return out
 
@@ -549,17 +569,22 @@ def choose_reseed(params, norm, seeds=VAL, side=64, max_iter=300, tol=0.1, optio
 
 # k = 5 won the validation sweeps against 3 and against 10
 SEED_AFTER = (5,)
+# networks averaged by the seed
+ENSEMBLE = 1
 
 
 def run(side=64, epochs=80, patience=16, max_iter=300, tol=0.1, lr=1e-3, out=WEIGHTS, seed_after=SEED_AFTER,
-        train_seeds=TRAIN, log=print):
+        train_seeds=TRAIN, ensemble=None, log=print):
     """Data (plain Monte Carlo on the training and validation clouds), then
     for every candidate k in `seed_after` (the network's inputs come from T
     after k - 1 and k plain dust iterations) training with validation-based
     stopping (slow clouds oversampled), the envelope from the training data
     and the shrink factor from the validation clouds; the k and shrink factor
     with the fewest validation dust iterations are kept, saved to `out`, and
-    compared on the test clouds."""
+    compared on the test clouds.  ensemble = K (default ENSEMBLE) trains K
+    networks that differ in their initial weights and sample order (seeds 0
+    .. K - 1) and seeds with their mean prediction."""
+    K = ENSEMBLE if ensemble is None else int(ensemble)
     t0 = time.perf_counter()
     snaps, T, rho, info = make_dataset(list(train_seeds) + VAL, side, seed_after, max_iter=max_iter, tol=tol, log=log)
     t_data = time.perf_counter() - t0
@@ -574,15 +599,17 @@ def run(side=64, epochs=80, patience=16, max_iter=300, tol=0.1, lr=1e-3, out=WEI
         env = envelope(Tk[:ntr], T[:ntr])
         X = features(Tk, Tp, rho, norm, side)
         Y = targets(Tk, T, norm, side)
-        params, hist, vhist, best_ep = train(X[:ntr], Y[:ntr], X[ntr:], Y[ntr:], epochs=epochs, patience=patience,
-                                             lr=lr, reps=reps, log=log)
+        runs = [train(X[:ntr], Y[:ntr], X[ntr:], Y[ntr:], epochs=epochs, patience=patience, lr=lr, seed=m,
+                      reps=reps, log=log) for m in range(K)]
+        params = runs[0][0] if K == 1 else np.stack([r[0] for r in runs])
+        _, hist, vhist, best_ep = runs[0]
         del X, Y
         norm["env"] = [env[0], env[1], list(map(float, env[2])), list(map(float, env[3]))]
         norm["seed_after"] = k
         shrink, table = choose_shrink(params, norm, VAL, side, max_iter, tol, log=log)
         norm["shrink"] = shrink
         tried[k] = dict(validation_iterations=table, best_epoch=best_ep, epochs_run=len(hist), train_loss=hist,
-                        val_loss=vhist)
+                        val_loss=vhist, members=[dict(best_epoch=r[3], epochs_run=len(r[1])) for r in runs])
         if best is None or table[str(shrink)] < best[0]:
             best = (table[str(shrink)], k, params, norm, env, shrink)
     t_train = time.perf_counter() - t1

@@ -52,7 +52,7 @@ EXPORTS = ["soc_create", "soc_destroy", "soc_last_error", "soc_grid_upload", "so
            "soc_nn_conv3d", "soc_nn_conv3d_dgrad", "soc_nn_conv3d_wgrad", "soc_nn_error_flag",
            "soc_simulate_frequency_batch_noalloc", "soc_abort", "soc_abort_clear", "soc_abort_status",
            "soc_set_timeout", "soc_nn_adam", "soc_seed_features", "soc_seed_transform",
-           "soc_iterate_batch", "soc_nn_seed_features"]
+           "soc_iterate_batch", "soc_nn_seed_features", "soc_nn_scale_add"]
 
 
 class GridDesc(C.Structure):
@@ -168,6 +168,7 @@ def _load():
         "soc_abort_status": ([P, C.POINTER(I), C.POINTER(I)], I),
         "soc_set_timeout": ([P, C.c_double], I),
         "soc_nn_adam": ([P, P, P, P, C.c_int64, C.c_float, C.c_int32, P, P], I),
+        "soc_nn_scale_add": ([P, P, C.c_int64, C.c_float, P], I),
         "soc_seed_features": ([P, I, P, P, P, I, P, P], I),
         "soc_seed_transform": ([P, I, P, P, C.POINTER(SeedMap), P, P], I),
         "soc_iterate_batch": ([P, I, P, C.POINTER(IterateParams), P, P, P, P, P], I),
@@ -606,6 +607,14 @@ def seed_features(T, rho, norm, x, T_prev=None, stream=None):
     nrm = np.ascontiguousarray(norm, np.float64)
     _nn_check(lib.soc_nn_seed_features(_t_ptr(T), _t_ptr(T_prev), _t_ptr(rho), T.numel(), _np_ptr(nrm),
                                        nrm.size // 2, _t_ptr(x), _stream(stream)), "soc_nn_seed_features")
+
+
+def scale_add(y, x, a, stream=None):
+    """soc_nn_scale_add: y <- fma(a, x, y) on FP32 device tensors of one size."""
+    if y.numel() != x.numel():
+        raise ValueError("y and x differ in size")
+    _nn_check(lib.soc_nn_scale_add(_t_ptr(y), _t_ptr(x), y.numel(), C.c_float(a), _stream(stream)),
+              "soc_nn_scale_add")
 
 
 def adam(w, m, v, g, lr, t, w_bf16=None, stream=None):

@@ -297,3 +297,24 @@ def test_seed_features_and_transform_match_oracle(libsoc):
     with pytest.raises(libsoc.SocError):
         ctx2.seed_features(ids2[0], torch.zeros(wo.clouds[0].n_cells, device="cuda"), [0, 1, 0, 1],
                            torch.empty((wo.clouds[0].n_cells, 2), device="cuda"))
+
+
+def test_scale_add_is_one_fused_multiply_add_per_element(libsoc):
+    """soc_nn_scale_add (the ensemble's mean): y <- fma(a, x, y), a ragged
+    length.  The FP64 sum of the exact product a x (48 bits) and y, rounded
+    to FP32, is the fused result except when the FP64 rounding of the sum
+    lands on an FP32 tie (double rounding): allow 1 ulp on at most a few
+    elements."""
+    rng = np.random.default_rng(11)
+    n = 1_000_003
+    x = rng.standard_normal(n).astype(np.float32)
+    y = rng.standard_normal(n).astype(np.float32)
+    a = np.float32(1.0 / 3.0)
+    yd = torch.from_numpy(y).cuda()
+    libsoc.scale_add(yd, torch.from_numpy(x).cuda(), float(a))
+    got = yd.cpu().numpy()
+    ref = (np.float64(a) * x.astype(np.float64) + y.astype(np.float64)).astype(np.float32)
+    ulp = np.abs(got.view(np.int32).astype(np.int64) - ref.view(np.int32).astype(np.int64))
+    assert ulp.max() <= 1 and int((ulp > 0).sum()) <= 10
+    with pytest.raises(ValueError):
+        libsoc.scale_add(yd, torch.zeros(3, device="cuda"), 1.0)

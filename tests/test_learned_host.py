@@ -23,9 +23,18 @@ def test_repeats_oversample_slow_clouds_up_to_the_cap():
     assert r.tolist() == [1, 1, 1, 2, 8]          # median 20: ratio rounded, at least 1, at most 8
 
 
+def test_members_of_one_network_and_of_an_ensemble():
+    p = L.init_params(0)
+    assert L.members(p).shape == (1, p.size)
+    e = np.stack([L.init_params(0), L.init_params(1)])
+    m = L.members(e)
+    assert m.shape == (2, p.size) and np.array_equal(m[0], p) and not np.array_equal(m[0], m[1])
+
+
 def test_committed_weights_are_well_formed():
     params, norm, meta, digest = L.load_weights()
-    assert params.dtype == np.float32 and params.size == L.init_params(0).size
+    P = L.members(params)                                   # [K, parameters], K networks averaged
+    assert params.dtype == np.float32 and P.shape == (L.ENSEMBLE, L.init_params(0).size)
     assert np.all(np.isfinite(params))
     assert norm["seed_after"] in (3, 5, 10) and norm["seed_after"] == meta["seed_after"]
     assert norm["shrink"] in L.SHRINKS                      # a factor the validation sweep tried
