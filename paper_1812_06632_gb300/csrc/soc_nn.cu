@@ -783,8 +783,16 @@ __global__ void __launch_bounds__(128) conv3d_wgrad_tc_kernel(const WgradArgs a,
         }
         if (waited) issue(nxt);
         else asm volatile("cp.async.commit_group;" ::: "memory");
-        if (ahead >= 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
-        else asm volatile("cp.async.wait_group 1;" ::: "memory");
+        // this step's copies have landed once at most `ahead` later groups
+        // are pending (the count is an immediate)
+        switch (ahead) {
+        case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+        case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+        case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+        case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+        case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
+        default: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (!__syncthreads_and(waited)) { ok_run = false; break; }
         if (tid == 0) {
@@ -1458,7 +1466,19 @@ struct WgradPlan {
     long long per = 0, chunks = 0;
 };
 
-inline WgradPlan wgrad_plan(long long V, int Cin, int Cout, int sms)
+// Stages of a weight-gradient block and blocks per SM: as many stages as
+// leave room for two blocks (3 to 8), so that every block of the grid is
+// resident at once.
+inline void wgrad_stages(int n_tile, int sm_smem, int *stages, int *per_sm)
+{
+    const int stage_bytes = (128 + n_tile) * kWgKV * 2;
+    int st = (sm_smem / 2 - 2048) / stage_bytes;
+    st = st < 3 ? 3 : (st > 8 ? 8 : st);
+    *stages = st;
+    *per_sm = std::max(1, sm_smem / (st * stage_bytes + 8 * st + 16 + 1024));
+}
+
+inline WgradPlan wgrad_plan(long long V, int Cin, int Cout, int sms, int sm_smem = 233472)
 {
     WgradPlan p;
     // input-channel tile: 16, 32, 64 or 128 (dividing C_in), 128 / tile taps
@@ -1470,7 +1490,11 @@ inline WgradPlan wgrad_plan(long long V, int Cin, int Cout, int sms)
     const int TT = 128 / p.ci_tile;
     p.tap_groups = (27 + TT - 1) / TT;
     const long long tiles = (long long)p.tap_groups * (Cin / p.ci_tile) * (Cout / p.n_tile);
-    long long chunks = (4LL * sms + tiles - 1) / tiles;
+    // one wave: the voxels split into as many chunks as the SMs hold blocks
+    // of every tile
+    int stages = 0, per_sm = 0;
+    wgrad_stages(p.n_tile, sm_smem, &stages, &per_sm);
+    long long chunks = std::max(1LL, (long long)per_sm * sms / tiles);
     long long per = (V + chunks - 1) / chunks;
     per = (per + kWgKV - 1) / kWgKV * kWgKV;
     if (per < kWgKV) per = kWgKV;
@@ -1490,7 +1514,10 @@ inline int device_sms()
 // Floats of partial sums a weight gradient of this shape needs.
 inline long long wgrad_part_floats(long long V, int Cin, int Cout, int sms)
 {
-    return wgrad_plan(V, Cin, Cout, sms).chunks * Cout * 27LL * Cin;
+    int dev = 0, sm_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    return wgrad_plan(V, Cin, Cout, sms, sm_smem).chunks * Cout * 27LL * Cin;
 }
 
 // gw[Cout][27][Cin] += sum_v gy[v] x[v + tap]: partial sums per voxel chunk
@@ -1504,7 +1531,7 @@ cudaError_t wgrad_launch(const WgradArgs &a0, float *gw, long long part_floats, 
     const int sms = device_sms();
     cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&blk_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const WgradPlan p = wgrad_plan(V, a.Cin, a.Cout, sms);
+    const WgradPlan p = wgrad_plan(V, a.Cin, a.Cout, sms, sm_smem);
     if (a.Cin % p.ci_tile) return cudaErrorInvalidValue;
     const long long n_w = (long long)a.Cout * 27 * a.Cin;
     if (p.chunks * n_w > part_floats) return cudaErrorInvalidValue;
@@ -1512,8 +1539,8 @@ cudaError_t wgrad_launch(const WgradArgs &a0, float *gw, long long part_floats, 
     uint32_t cols = 32;
     while ((int)cols < p.n_tile) cols <<= 1;
     const int stage_bytes = (128 + p.n_tile) * kWgKV * 2;
-    int stages = 73728 / stage_bytes;
-    stages = stages < 3 ? 3 : (stages > 4 ? 4 : stages);
+    int stages = 0, per_sm = 0;
+    wgrad_stages(p.n_tile, sm_smem, &stages, &per_sm);
     const int need = stages * stage_bytes + 8 * stages + 16;
     const int max_blocks = 512 / (int)cols;
     const int pad = sm_smem / (max_blocks + 1) + 1024;
