@@ -598,12 +598,16 @@ soc_status soc_nn_scale_add(float *d_y, const float *d_x, int64_t n, float a, vo
  * paper's method), per cell of an uploaded regular grid, in FP64:
  *   soc_seed_features   network input d_x (device float [n_cells][n_features],
  *                       the channels-last (side, side, side, n_features)
- *                       layout of one sample), n_features 2 or 3:
+ *                       layout of one sample), n_features 2, 3 or 4:
  *                       x[c][0] = (ln clamp(T[c], 2.7, 3000) - norm[0]) / norm[1],
  *                       x[c][1] = (ln max(rho_c, 1e-30) - norm[2]) / norm[3],
  *                       x[c][2] = (ln clamp(T[c]) - ln clamp(T_prev[c]) -
- *                                  norm[4]) / norm[5]   (n_features = 3:
+ *                                  norm[4]) / norm[5]   (n_features >= 3:
  *                       the last iteration's change; d_T_prev required),
+ *                       x[c][3] = (ln clamp(T_prev[c]) - ln clamp(T_prev2[c]) -
+ *                                  norm[6]) / norm[7]   (n_features = 4:
+ *                       the change one iteration earlier; d_T_prev2
+ *                       required; NULL otherwise),
  *                       each feature clipped to [-6, 6] after the
  *                       standardisation; rho from the uploaded grid.  norm:
  *                       host double [2 n_features], {mean, width} of each
@@ -620,14 +624,14 @@ soc_status soc_nn_scale_add(float *d_y, const float *d_x, int64_t n, float a, vo
  *                       map: host soc_seed_map (copied into the launch).
  *                       d_T1, d_pred, d_T_seed: device float [n_cells].
  *   soc_nn_seed_features  the features of soc_seed_features from caller
- *                       arrays (no context): d_T, d_T_prev, d_rho device
- *                       float [n], d_x device float [n][n_features] (e.g. a
+ *                       arrays (no context): d_T, d_T_prev, d_T_prev2, d_rho
+ *                       device float [n], d_x device float [n][n_features] (e.g. a
  *                       training set kept after its clouds were freed).
  * All asynchronous on `stream`; d_T_seed may be passed as the seed of
  * soc_iterate or soc_iterate_batch.
  * ------------------------------------------------------------------------ */
-soc_status soc_seed_features(soc_ctx *ctx, int cloud_id, const float *d_T, const float *d_T_prev, const double *norm,
-                             int n_features, float *d_x, void *stream);
+soc_status soc_seed_features(soc_ctx *ctx, int cloud_id, const float *d_T, const float *d_T_prev,
+                             const float *d_T_prev2, const double *norm, int n_features, float *d_x, void *stream);
 #define SOC_SEED_MAX_BINS 64
 typedef struct soc_seed_map {
     double y_mean, y_std;      /* de-normalisation of the prediction            */
@@ -639,8 +643,8 @@ typedef struct soc_seed_map {
 } soc_seed_map;
 soc_status soc_seed_transform(soc_ctx *ctx, int cloud_id, const float *d_T1, const float *d_pred,
                               const soc_seed_map *map, float *d_T_seed, void *stream);
-soc_status soc_nn_seed_features(const float *d_T, const float *d_T_prev, const float *d_rho, int64_t n,
-                                const double *norm, int n_features, float *d_x, void *stream);
+soc_status soc_nn_seed_features(const float *d_T, const float *d_T_prev, const float *d_T_prev2, const float *d_rho,
+                                int64_t n, const double *norm, int n_features, float *d_x, void *stream);
 
 /* ------------------------------------------------------------------------
  * Launch configuration of the tracer (autotuner hook).  threads_per_block in

@@ -234,19 +234,24 @@ T_MIN, T_MAX = 2.7, 3000.0
 FEATURE_CLIP = 6.0
 
 
-def seed_features(T, rho, norm, T_prev=None):
+def seed_features(T, rho, norm, T_prev=None, T_prev2=None):
     """Network input per cell: ((ln T - lt_mean) / lt_std, (ln rho -
-    lr_mean) / lr_std) and, given T_prev, ((ln T - ln T_prev) - ld_mean) /
-    ld_std, with temperatures clamped to [T_MIN, T_MAX] and rho to at least
-    1e-30.  norm: dict with lt_mean, lt_std, lr_mean, lr_std (ld_mean,
-    ld_std).  Each standardised feature is clipped to [-FEATURE_CLIP,
-    FEATURE_CLIP].  Returns (n, 2) or (n, 3)."""
+    lr_mean) / lr_std); given T_prev, ((ln T - ln T_prev) - ld_mean) /
+    ld_std (the last iteration's change); given T_prev2 as well, ((ln T_prev
+    - ln T_prev2) - pd_mean) / pd_std (the change one iteration earlier);
+    temperatures clamped to [T_MIN, T_MAX] and rho to at least 1e-30.  norm:
+    dict with lt_mean, lt_std, lr_mean, lr_std (ld_mean, ld_std; pd_mean,
+    pd_std).  Each standardised feature is clipped to [-FEATURE_CLIP,
+    FEATURE_CLIP].  Returns (n, 2), (n, 3) or (n, 4)."""
     lT = np.log(np.clip(np.asarray(T, np.float64), T_MIN, T_MAX))
     cols = [(lT - norm["lt_mean"]) / norm["lt_std"],
             (np.log(np.maximum(np.asarray(rho, np.float64), 1e-30)) - norm["lr_mean"]) / norm["lr_std"]]
     if T_prev is not None:
         lP = np.log(np.clip(np.asarray(T_prev, np.float64), T_MIN, T_MAX))
         cols.append((lT - lP - norm["ld_mean"]) / norm["ld_std"])
+        if T_prev2 is not None:
+            lPP = np.log(np.clip(np.asarray(T_prev2, np.float64), T_MIN, T_MAX))
+            cols.append((lP - lPP - norm["pd_mean"]) / norm["pd_std"])
     return np.clip(np.stack(cols, axis=-1), -FEATURE_CLIP, FEATURE_CLIP)
 
 

@@ -1284,22 +1284,24 @@ soc_status soc_update_temperature_ali(soc_ctx *ctx, int cloud_id, const double *
     });
 }
 
-soc_status soc_seed_features(soc_ctx *ctx, int cloud_id, const float *d_T, const float *d_T_prev, const double *norm,
-                             int n_features, float *d_x, void *stream)
+soc_status soc_seed_features(soc_ctx *ctx, int cloud_id, const float *d_T, const float *d_T_prev,
+                             const float *d_T_prev2, const double *norm, int n_features, float *d_x, void *stream)
 {
     return guarded(ctx, [&]() -> soc_status {
         soc_status st = check_cloud(ctx, cloud_id);
         if (st) return st;
         if (!d_T || !norm || !d_x) return fail(ctx, SOC_ERR_ARG, "null argument");
-        if (n_features != 2 && n_features != 3) return fail(ctx, SOC_ERR_ARG, "n_features must be 2 or 3");
-        if (n_features == 3 && !d_T_prev) return fail(ctx, SOC_ERR_ARG, "3 features need d_T_prev");
+        if (n_features < 2 || n_features > 4) return fail(ctx, SOC_ERR_ARG, "n_features must be 2, 3 or 4");
+        if (n_features >= 3 && !d_T_prev) return fail(ctx, SOC_ERR_ARG, "3 or 4 features need d_T_prev");
+        if (n_features == 4 && !d_T_prev2) return fail(ctx, SOC_ERR_ARG, "4 features need d_T_prev2");
         for (int k = 1; k < 2 * n_features; k += 2)
             if (!(norm[k] > 0.0)) return fail(ctx, SOC_ERR_ARG, "normalisation widths must be > 0");
         const CloudHost &cl = *ctx->clouds[cloud_id];
         if (cl.n_levels != 1 || cl.nx != cl.ny || cl.nx != cl.nz || cl.nx % 8)
             return fail(ctx, SOC_ERR_ARG, "the network takes regular cubic grids with a side that is a multiple of 8");
         CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-        CK(launch_seed_features(d_T, d_T_prev, cl.rho.p, cl.n_cells, n_features, norm, d_x, (cudaStream_t)stream),
+        CK(launch_seed_features(d_T, d_T_prev, d_T_prev2, cl.rho.p, cl.n_cells, n_features, norm, d_x,
+                                (cudaStream_t)stream),
            "seed features");
         return SOC_OK;
     });

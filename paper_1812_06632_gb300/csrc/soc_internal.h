@@ -135,10 +135,10 @@ cudaError_t launch_dust_emission(const DevCloud *dcl, int64_t n_leaf, const Temp
                                  double *e_unit, unsigned long long *scratch_max, cudaStream_t s);
 
 // Learned seed: network features of a cloud's cells and the seeding transform
-// (soc_nn.cu).  norm: {mean, width} of each feature (2 or 3 features).
-struct SeedNorm { double v[6]; };
-cudaError_t launch_seed_features(const float *T, const float *T_prev, const float *rho, int64_t n, int n_features,
-                                 const double *norm, float *x, cudaStream_t s);
+// (soc_nn.cu).  norm: {mean, width} of each feature (2, 3 or 4 features).
+struct SeedNorm { double v[8]; };
+cudaError_t launch_seed_features(const float *T, const float *T_prev, const float *T_prev2, const float *rho,
+                                 int64_t n, int n_features, const double *norm, float *x, cudaStream_t s);
 cudaError_t launch_seed_transform(const float *T1, const float *pred, int64_t n, const soc_seed_map &map,
                                   float *T_seed, cudaStream_t s);
 

@@ -1142,17 +1142,21 @@ __device__ __forceinline__ float clip_feature(double v)
     return (float)fmin(fmax(v, -kFeatureClip), kFeatureClip);
 }
 
-__global__ void seed_features_kernel(const float *T, const float *T_prev, const float *rho, long long n, int nf,
-                                     const SeedNorm nm, float *x)
+__global__ void seed_features_kernel(const float *T, const float *T_prev, const float *T_prev2, const float *rho,
+                                     long long n, int nf, const SeedNorm nm, float *x)
 {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const double lt = log(fmin(fmax((double)T[c], kTMin), kTMax));
         const double r = fmax((double)rho[c], 1e-30);
         x[nf * c] = clip_feature((lt - nm.v[0]) / nm.v[1]);
         x[nf * c + 1] = clip_feature((log(r) - nm.v[2]) / nm.v[3]);
-        if (nf == 3) {
+        if (nf >= 3) {
             const double lp = log(fmin(fmax((double)T_prev[c], kTMin), kTMax));
             x[nf * c + 2] = clip_feature((lt - lp - nm.v[4]) / nm.v[5]);
+            if (nf == 4) {
+                const double lpp = log(fmin(fmax((double)T_prev2[c], kTMin), kTMax));
+                x[nf * c + 3] = clip_feature((lp - lpp - nm.v[6]) / nm.v[7]);
+            }
         }
     }
 }
@@ -1639,12 +1643,12 @@ struct Net {
 
 }  // namespace nn
 
-cudaError_t launch_seed_features(const float *T, const float *T_prev, const float *rho, int64_t n, int n_features,
-                                 const double *norm, float *x, cudaStream_t s)
+cudaError_t launch_seed_features(const float *T, const float *T_prev, const float *T_prev2, const float *rho,
+                                 int64_t n, int n_features, const double *norm, float *x, cudaStream_t s)
 {
     SeedNorm nm{};
     for (int k = 0; k < 2 * n_features; ++k) nm.v[k] = norm[k];
-    nn::seed_features_kernel<<<nn::grid_1d(n), 256, 0, s>>>(T, T_prev, rho, n, n_features, nm, x);
+    nn::seed_features_kernel<<<nn::grid_1d(n), 256, 0, s>>>(T, T_prev, T_prev2, rho, n, n_features, nm, x);
     return cudaGetLastError();
 }
 
@@ -2053,15 +2057,15 @@ soc_status soc_nn_conv3d_wgrad(const void *gy, const void *x, int N, int D, int 
     return SOC_OK;
 }
 
-soc_status soc_nn_seed_features(const float *d_T, const float *d_T_prev, const float *d_rho, int64_t n,
-                                const double *norm, int n_features, float *d_x, void *stream)
+soc_status soc_nn_seed_features(const float *d_T, const float *d_T_prev, const float *d_T_prev2, const float *d_rho,
+                                int64_t n, const double *norm, int n_features, float *d_x, void *stream)
 {
-    if (!d_T || !d_rho || !norm || !d_x || n < 1 || (n_features != 2 && n_features != 3) ||
-        (n_features == 3 && !d_T_prev))
+    if (!d_T || !d_rho || !norm || !d_x || n < 1 || n_features < 2 || n_features > 4 ||
+        (n_features >= 3 && !d_T_prev) || (n_features == 4 && !d_T_prev2))
         return SOC_ERR_ARG;
     for (int k = 1; k < 2 * n_features; k += 2)
         if (!(norm[k] > 0.0)) return SOC_ERR_ARG;
-    NNCK(soc::launch_seed_features(d_T, d_T_prev, d_rho, n, n_features, norm, d_x, (cudaStream_t)stream));
+    NNCK(soc::launch_seed_features(d_T, d_T_prev, d_T_prev2, d_rho, n, n_features, norm, d_x, (cudaStream_t)stream));
     return SOC_OK;
 }
 

@@ -9,11 +9,12 @@ plain iteration needs tens of dust iterations.  For every cloud the Monte
 Carlo path gives T1 (temperatures after iteration 0: background and point
 sources only) and the converged T (dust re-emission iterated with frozen
 random numbers until max |dT| < tol).  The network maps the features
-(soc_seed_features: normalised ln T_k, ln rho and ln T_k - ln T_{k-1}, T_k
-the temperatures after k plain dust iterations) to the normalised
-y = ln T - ln T_k.  The last change carries the slow mode of the iteration
-(T - T_k ~ (T_k - T_{k-1}) r / (1 - r) for a mode that shrinks by r per
-iteration), which the network learns to extrapolate.  A seeded run makes k
+(soc_seed_features: normalised ln T_k, ln rho, ln T_k - ln T_{k-1} and
+ln T_{k-1} - ln T_{k-2}, T_k the temperatures after k plain dust iterations)
+to the normalised y = ln T - ln T_k.  The last change carries the slow mode
+of the iteration (T - T_k ~ (T_k - T_{k-1}) r / (1 - r) for a mode that
+shrinks by r per iteration), and the ratio of the last two changes gives r
+cell by cell, which the network learns to use.  A seeded run makes k
 plain dust iterations, then continues from T_k exp(y) (soc_seed_transform), y
 the de-normalised prediction; the iterations then continue to the same fixed
 point, so they are both the fallback and the measure of the seed's error.
@@ -24,11 +25,12 @@ absorbed power, so the converged T is never below T1), and y stays inside the
 envelope of the training data per bin of ln T1 (the hottest cells next to the
 sources are rare and far outside the network's typical inputs).  A shrink
 factor on y, chosen on the validation clouds by the dust iterations it
-needs, moves the seed towards T1, from below.
+needs, scales the correction (below 1 towards T_k, above 1 beyond).
 
-The 200 cloud seeds 1000..1199 split 160 / 20 / 20 into training,
-validation (early stopping: the weights of the epoch with the lowest
-validation loss are kept; the shrink factor) and test clouds.
+Cloud seeds 1000..1159 and 1200..1359 are the training clouds, 1160..1179
+the validation clouds (early stopping: the weights of the epoch with the
+lowest validation loss are kept; the shrink factor) and 1180..1199 the test
+clouds.
 """
 from __future__ import annotations
 
@@ -122,12 +124,16 @@ def snapshots(ctx, ids, w, ks, tol=0.1):
 
 def seeded_run(ctx, ids, seeder, starts, max_iter=300, tol=0.1, reseed=None):
     """Dust iterations of every cloud from its start temperatures to
-    max |dT| < tol.  With reseed = R (>= 2), every R iterations the clouds
-    not yet converged are seeded again by the network from their last two
-    iterates, the same inputs as the first seeding (the Monte Carlo
-    iterations still judge every seed).  Returns per cloud the rows of
-    `dust_iterations` summed over the segments, and the final temperatures."""
+    max |dT| < tol.  With reseed = R (at least the number of iterates the
+    network's features take), every R iterations the clouds not yet
+    converged are seeded again by the network from their last iterates, the
+    same inputs as the first seeding (the Monte Carlo iterations still judge
+    every seed).  Returns per cloud the rows of `dust_iterations` summed over
+    the segments, and the final temperatures."""
     import torch
+    h = seeder.history
+    if reseed is not None and reseed < h:
+        raise ValueError(f"reseed must be at least {h}")
     n = len(ids)
     rows = [dict(iterations=0, converged=False, steps=0, final_max_dT=None) for _ in range(n)]
     final = [None] * n
@@ -151,42 +157,47 @@ def seeded_run(ctx, ids, seeder, starts, max_iter=300, tol=0.1, reseed=None):
             for i, j in enumerate(active):
                 final[j] = outs[i]
             break
-        # R - 1 iterations, then one more: the pair (T_{m-1}, T_m) of the next seed
-        ta, got = run(active, [cur[j] for j in active], reseed - 1)
-        still = []
+        # R - h + 1 iterations, then h - 1 more one at a time: the last h
+        # iterates, the inputs of the next seed
+        ta, got = run(active, [cur[j] for j in active], reseed - h + 1)
+        hist, still = {}, []
         for i, j in enumerate(active):
             if got[i]["converged"]:
                 final[j] = ta[i]
             else:
-                still.append((j, ta[i]))
+                still.append(j)
+                hist[j] = [ta[i]]
+        for _ in range(h - 1):
+            if not still:
+                break
+            tb, got = run(still, [hist[j][-1] for j in still], 1)
+            nxt = []
+            for i, j in enumerate(still):
+                if got[i]["converged"]:
+                    final[j] = tb[i]
+                else:
+                    nxt.append(j)
+                    hist[j].append(tb[i])
+            still = nxt
         if not still:
             break
-        js = [j for j, _ in still]
-        tb, got = run(js, [t for _, t in still], 1)
-        nxt, prev = [], []
-        for i, j in enumerate(js):
-            if got[i]["converged"]:
-                final[j] = tb[i]
-            else:
-                nxt.append(j)
-                prev.append((dict(still)[j], tb[i]))
-        if not nxt:
-            break
-        s = seeder.seeds(ctx, [ids[j] for j in nxt], [b for _, b in prev], [a for a, _ in prev])
-        for i, j in enumerate(nxt):
+        s = seeder.seeds(ctx, [ids[j] for j in still], [hist[j][-1] for j in still], [hist[j][-2] for j in still],
+                         Tpps=[hist[j][-3] for j in still] if h == 3 else None)
+        for i, j in enumerate(still):
             cur[j] = s[i]
-        active = nxt
+        active = still
     return rows, final
 
 
 def make_dataset(seeds, side=64, seed_after=(3,), chunk=20, max_iter=300, tol=0.1, log=print):
     """Plain Monte Carlo of every cloud, `chunk` clouds per batched run: the
-    temperatures after k - 1 and k dust iterations for every k in
-    `seed_after` (the network's candidate inputs) and the converged T.
+    temperatures after k - 1 and k (and k - 2 for four network inputs) dust
+    iterations for every k in `seed_after` (the network's candidate inputs)
+    and the converged T.
     Returns ({k: T_k}, T, rho) as device tensors [n, side^3] and one info row
     per cloud (plain dust iterations in all)."""
     import torch
-    ks = sorted(set(int(k) for k in seed_after) | set(int(k) - 1 for k in seed_after))
+    ks = sorted({int(k) - h for k in seed_after for h in range(FEATURES - 1)})
     snaps, Ts, rhos, info = {k: [] for k in ks}, [], [], []
     for c0 in range(0, len(seeds), chunk):
         w = I.config_c4(seeds[c0:c0 + chunk], side=side)
@@ -209,30 +220,46 @@ def make_dataset(seeds, side=64, seed_after=(3,), chunk=20, max_iter=300, tol=0.
     return {k: torch.stack(v) for k, v in snaps.items()}, torch.stack(Ts), torch.stack(rhos), info
 
 
-def norm_stats(Tk, Tp, T, rho):
-    """Means and widths of the network's three inputs and of its target over
-    a data set (Tk: the input temperatures, Tp: one iteration earlier)."""
+def norm_stats(Tk, Tp, T, rho, Tpp=None):
+    """Means and widths of the network's inputs and of its target over a
+    data set (Tk: the input temperatures, Tp: one iteration earlier, Tpp:
+    two iterations earlier, for the fourth input)."""
     import torch
     lt = torch.log(Tk.double().clamp(T_MIN, T_MAX))
     lr = torch.log(rho.double().clamp_min(1e-30))
-    ld = lt - torch.log(Tp.double().clamp(T_MIN, T_MAX))
+    lp = torch.log(Tp.double().clamp(T_MIN, T_MAX))
+    ld = lt - lp
     y = torch.log(T.double().clamp(T_MIN, T_MAX)) - lt
-    return dict(lt_mean=lt.mean().item(), lt_std=lt.std().item() + 1e-12, lr_mean=lr.mean().item(),
-                lr_std=lr.std().item() + 1e-12, ld_mean=ld.mean().item(), ld_std=ld.std().item() + 1e-12,
-                y_mean=y.mean().item(), y_std=y.std().item() + 1e-12)
+    out = dict(lt_mean=lt.mean().item(), lt_std=lt.std().item() + 1e-12, lr_mean=lr.mean().item(),
+               lr_std=lr.std().item() + 1e-12, ld_mean=ld.mean().item(), ld_std=ld.std().item() + 1e-12,
+               y_mean=y.mean().item(), y_std=y.std().item() + 1e-12)
+    if Tpp is not None:
+        pd = lp - torch.log(Tpp.double().clamp(T_MIN, T_MAX))
+        out.update(pd_mean=pd.mean().item(), pd_std=pd.std().item() + 1e-12)
+    return out
 
 
-def _norm6(norm):
-    return [norm["lt_mean"], norm["lt_std"], norm["lr_mean"], norm["lr_std"], norm["ld_mean"], norm["ld_std"]]
+def n_features(norm):
+    """Inputs per cell of the network a normalisation belongs to: 3, or 4
+    with the change one iteration earlier."""
+    return 4 if "pd_mean" in norm else 3
 
 
-def features(Tk, Tp, rho, norm, side):
-    """Network inputs [n, side, side, side, 3] by the library's feature kernel."""
+def _norm_vec(norm):
+    v = [norm["lt_mean"], norm["lt_std"], norm["lr_mean"], norm["lr_std"], norm["ld_mean"], norm["ld_std"]]
+    return v + ([norm["pd_mean"], norm["pd_std"]] if n_features(norm) == 4 else [])
+
+
+def features(Tk, Tp, rho, norm, side, Tpp=None):
+    """Network inputs [n, side, side, side, 3 or 4] by the library's feature
+    kernel (Tpp: T two iterations before Tk, for four inputs)."""
     import torch
     from . import soc
-    x = torch.empty((Tk.shape[0], side, side, side, 3), dtype=torch.float32, device="cuda")
+    nf = n_features(norm)
+    x = torch.empty((Tk.shape[0], side, side, side, nf), dtype=torch.float32, device="cuda")
     for k in range(Tk.shape[0]):
-        soc.seed_features(Tk[k].contiguous(), rho[k].contiguous(), _norm6(norm), x[k], T_prev=Tp[k].contiguous())
+        soc.seed_features(Tk[k].contiguous(), rho[k].contiguous(), _norm_vec(norm), x[k], T_prev=Tp[k].contiguous(),
+                          T_prev2=Tpp[k].contiguous() if nf == 4 else None)
     return x
 
 
@@ -394,21 +421,25 @@ class Seeder:
         self.soc = soc
         self.norm, self.side = norm, side
         self.members = members(params)
-        self.net = soc.UNet(n, side, n_inputs=3)
+        self.n_in = n_features(norm)
+        self.history = self.n_in - 1              # iterates the features take: T_k and the ones before
+        self.net = soc.UNet(n, side, n_inputs=self.n_in)
         self.net.set_params(self.members[0])
-        self.x = torch.empty((n, side, side, side, 3), dtype=torch.float32, device="cuda")
+        self.x = torch.empty((n, side, side, side, self.n_in), dtype=torch.float32, device="cuda")
         self.pred = torch.empty((n, side, side, side), dtype=torch.float32, device="cuda")
         self.mean = torch.empty_like(self.pred) if len(self.members) > 1 else None
 
-    def seeds(self, ctx, ids, Tks, Tps, shrink=None):
-        """T_seed of every cloud from T_k and T_{k-1}: features, one batched
+    def seeds(self, ctx, ids, Tks, Tps, Tpps=None, shrink=None):
+        """T_seed of every cloud from T_k, T_{k-1} (and T_{k-2} for four
+        inputs): features, one batched
         network forward and the seeding transform (shrink and envelope of
         the map), all on the GPU.  shrink overrides the stored factor
         (validation sweeps)."""
         import torch
         out = []
         for k, cid in enumerate(ids):
-            ctx.seed_features(cid, Tks[k], _norm6(self.norm), self.x[k], T_prev=Tps[k])
+            ctx.seed_features(cid, Tks[k], _norm_vec(self.norm), self.x[k], T_prev=Tps[k],
+                              T_prev2=Tpps[k] if self.n_in == 4 else None)
         pred = self.pred
         if self.mean is None:
             self.net.forward(self.x, self.pred)
@@ -449,7 +480,7 @@ def compare(params, norm, seeds=TEST, side=64, max_iter=300, tol=0.1, reseed=Non
     T0 = empty_fields(w0)
     constant_iteration(c0, i0, T0)
     dust_iterations(c0, i0, empty_fields(w0), max_iter=1)
-    Seeder(params, norm, 1, side).seeds(c0, i0, T0, T0)
+    Seeder(params, norm, 1, side).seeds(c0, i0, T0, T0, Tpps=T0)
     c0.close()
     torch.cuda.synchronize()
 
@@ -467,16 +498,21 @@ def compare(params, norm, seeds=TEST, side=64, max_iter=300, tol=0.1, reseed=Non
 
     T_learn = empty_fields(w)
     t0 = time.perf_counter()
-    # k - 1 plain dust iterations, then one more (T_{k-1}, T_k), then the seed
-    Tp = T1
-    first = [dict(iterations=0, converged=False, steps=0) for _ in ids]
-    if k > 1:
-        Tp = empty_fields(w)
-        first = dust_iterations(ctx, ids, Tp, seeds=T1, max_iter=k - 1, tol=tol)
-    Tk = empty_fields(w)
-    last = dust_iterations(ctx, ids, Tk, seeds=Tp, max_iter=1, tol=tol)
-    s = seeder.seeds(ctx, ids, Tk, Tp)
-    done = [f["converged"] or l["converged"] for f, l in zip(first, last)]
+    # k - h plain dust iterations, then h more one at a time (the iterates
+    # the features take, T_{k-h+1} .. T_k), then the seed
+    h = seeder.history
+    hist, stages = [T1], []
+    if k > h:
+        Ta = empty_fields(w)
+        stages.append(dust_iterations(ctx, ids, Ta, seeds=T1, max_iter=k - h, tol=tol))
+        hist = [Ta]
+    for _ in range(h):
+        Tn = empty_fields(w)
+        stages.append(dust_iterations(ctx, ids, Tn, seeds=hist[-1], max_iter=1, tol=tol))
+        hist.append(Tn)
+    Tk, Tp = hist[-1], hist[-2]
+    s = seeder.seeds(ctx, ids, Tk, Tp, Tpps=hist[-3] if h == 3 else None)
+    done = [any(st[j]["converged"] for st in stages) for j in range(len(ids))]
     s = [Tk[j] if done[j] else s[j] for j in range(len(ids))]
     learn, fin = seeded_run(ctx, ids, seeder, s, max_iter=max_iter, tol=tol, reseed=reseed)
     torch.cuda.synchronize()
@@ -484,7 +520,7 @@ def compare(params, norm, seeds=TEST, side=64, max_iter=300, tol=0.1, reseed=Non
     for j in range(len(ids)):
         if fin[j] is not None:
             T_learn[j].copy_(fin[j])
-    learn_its = [f["iterations"] + l["iterations"] + r["iterations"] for f, l, r in zip(first, last, learn)]
+    learn_its = [sum(st[j]["iterations"] for st in stages) + learn[j]["iterations"] for j in range(len(ids))]
 
     # seed quality: max |T_seed - T_converged| against the same for T_k (the start it replaces)
     seed_err = [float((s[j] - T_plain[j]).abs().max().item()) for j in range(len(ids))]
@@ -501,8 +537,7 @@ def compare(params, norm, seeds=TEST, side=64, max_iter=300, tol=0.1, reseed=Non
                unconverged_final_dT_K={str(seeds[j]): [plain[j]["final_max_dT"], learn[j]["final_max_dT"]]
                                        for j in range(len(ids)) if j not in both},
                plain_steps=int(sum(r["steps"] for r in plain)),
-               learned_steps=int(sum(r["steps"] for r in learn) + sum(f["steps"] for f in first)
-                                 + sum(l["steps"] for l in last)),
+               learned_steps=int(sum(r["steps"] for r in learn) + sum(r["steps"] for st in stages for r in st)),
                max_abs_T_difference_K=dmax, seed_max_err_K=seed_err, start_max_err_K=tk_err)
     # (max_abs_T_difference_K: over the clouds both runs converged on; the
     # fixed point is the same, so it stays within about the tolerance)
@@ -522,10 +557,10 @@ def choose_shrink(params, norm, seeds=VAL, side=64, max_iter=300, tol=0.1, shrin
     w = I.config_c4(seeds, side=side)
     ctx, ids = context(w)
     seeder = Seeder(params, norm, len(ids), side)
-    sn, done, conv = snapshots(ctx, ids, w, (k - 1, k), tol)
+    sn, done, conv = snapshots(ctx, ids, w, range(k - seeder.history + 1, k + 1), tol)
     table = {"plain": sum(r["iterations"] for r in dust_iterations(ctx, ids, empty_fields(w), None, max_iter, tol))}
     for a in shrinks:
-        s = seeder.seeds(ctx, ids, sn[k], sn[k - 1], shrink=a)
+        s = seeder.seeds(ctx, ids, sn[k], sn[k - 1], Tpps=sn.get(k - 2), shrink=a)
         s = [sn[k][j] if conv[j] else s[j] for j in range(len(ids))]
         rows = dust_iterations(ctx, ids, empty_fields(w), s, max_iter, tol)
         table[str(a)] = sum(done) + sum(0 if conv[j] else r["iterations"] for j, r in enumerate(rows))
@@ -548,8 +583,8 @@ def choose_reseed(params, norm, seeds=VAL, side=64, max_iter=300, tol=0.1, optio
     w = I.config_c4(seeds, side=side)
     ctx, ids = context(w)
     seeder = Seeder(params, norm, len(ids), side)
-    sn, done, conv = snapshots(ctx, ids, w, (k - 1, k), tol)
-    s0 = seeder.seeds(ctx, ids, sn[k], sn[k - 1])
+    sn, done, conv = snapshots(ctx, ids, w, range(k - seeder.history + 1, k + 1), tol)
+    s0 = seeder.seeds(ctx, ids, sn[k], sn[k - 1], Tpps=sn.get(k - 2))
     s0 = [sn[k][j] if conv[j] else s0[j] for j in range(len(ids))]
     seeded_run(ctx, ids, seeder, s0, max_iter=2, tol=tol, reseed=None)           # warm-up
     table = {}
@@ -571,6 +606,8 @@ def choose_reseed(params, norm, seeds=VAL, side=64, max_iter=300, tol=0.1, optio
 SEED_AFTER = (5,)
 # networks averaged by the seed
 ENSEMBLE = 1
+# network inputs per cell: ln T_k, ln rho, ln T_k - ln T_{k-1} and (4) ln T_{k-1} - ln T_{k-2}
+FEATURES = 4
 
 
 def run(side=64, epochs=80, patience=16, max_iter=300, tol=0.1, lr=1e-3, out=WEIGHTS, seed_after=SEED_AFTER,
@@ -595,9 +632,10 @@ def run(side=64, epochs=80, patience=16, max_iter=300, tol=0.1, lr=1e-3, out=WEI
     t1 = time.perf_counter()
     for k in sorted(set(int(k) for k in seed_after)):
         Tk, Tp = snaps[k], snaps[k - 1]
-        norm = norm_stats(Tk[:ntr], Tp[:ntr], T[:ntr], rho[:ntr])
+        Tpp = snaps[k - 2] if FEATURES == 4 else None
+        norm = norm_stats(Tk[:ntr], Tp[:ntr], T[:ntr], rho[:ntr], None if Tpp is None else Tpp[:ntr])
         env = envelope(Tk[:ntr], T[:ntr])
-        X = features(Tk, Tp, rho, norm, side)
+        X = features(Tk, Tp, rho, norm, side, Tpp=Tpp)
         Y = targets(Tk, T, norm, side)
         runs = [train(X[:ntr], Y[:ntr], X[ntr:], Y[ntr:], epochs=epochs, patience=patience, lr=lr, seed=m,
                       reps=reps, log=log) for m in range(K)]

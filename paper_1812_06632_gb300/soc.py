@@ -169,10 +169,10 @@ def _load():
         "soc_set_timeout": ([P, C.c_double], I),
         "soc_nn_adam": ([P, P, P, P, C.c_int64, C.c_float, C.c_int32, P, P], I),
         "soc_nn_scale_add": ([P, P, C.c_int64, C.c_float, P], I),
-        "soc_seed_features": ([P, I, P, P, P, I, P, P], I),
+        "soc_seed_features": ([P, I, P, P, P, P, I, P, P], I),
         "soc_seed_transform": ([P, I, P, P, C.POINTER(SeedMap), P, P], I),
         "soc_iterate_batch": ([P, I, P, C.POINTER(IterateParams), P, P, P, P, P], I),
-        "soc_nn_seed_features": ([P, P, P, C.c_int64, P, I, P, P], I),
+        "soc_nn_seed_features": ([P, P, P, P, C.c_int64, P, I, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -454,13 +454,13 @@ class Context:
         self._check(lib.soc_map(self.h, cloud_id, _t_ptr(T), freq, _np_ptr(d), _np_ptr(u), npx, npy,
                                 float(pix_size), _np_ptr(c), float(I_bg), _t_ptr(out), _stream(stream)))
 
-    def seed_features(self, cloud_id, T, norm, x, T_prev=None, stream=None):
+    def seed_features(self, cloud_id, T, norm, x, T_prev=None, T_prev2=None, stream=None):
         """soc_seed_features: x (float32 [n_cells, n_features]) from T, the
-        grid's density and (3 features) T_prev; norm = {mean, width} of each
-        feature (4 or 6 values)."""
+        grid's density, (3 or 4 features) T_prev and (4 features) T_prev2;
+        norm = {mean, width} of each feature (4, 6 or 8 values)."""
         nrm = np.ascontiguousarray(norm, np.float64)
-        self._check(lib.soc_seed_features(self.h, cloud_id, _t_ptr(T), _t_ptr(T_prev), _np_ptr(nrm), nrm.size // 2,
-                                          _t_ptr(x), _stream(stream)))
+        self._check(lib.soc_seed_features(self.h, cloud_id, _t_ptr(T), _t_ptr(T_prev), _t_ptr(T_prev2), _np_ptr(nrm),
+                                          nrm.size // 2, _t_ptr(x), _stream(stream)))
 
     def seed_transform(self, cloud_id, T1, pred, smap, T_seed, stream=None):
         """soc_seed_transform: T_seed = clamp(T1 exp(y)) with y the
@@ -601,12 +601,13 @@ def conv3d_dgrad(gy, w, w_scratch, gx, stream=None):
                                       _t_ptr(gx), _stream(stream)), "soc_nn_conv3d_dgrad")
 
 
-def seed_features(T, rho, norm, x, T_prev=None, stream=None):
-    """soc_nn_seed_features: x (float32 [n, n_features]) from device T, rho
-    and (3 features) T_prev; norm = {mean, width} of each feature."""
+def seed_features(T, rho, norm, x, T_prev=None, T_prev2=None, stream=None):
+    """soc_nn_seed_features: x (float32 [n, n_features]) from device T, rho,
+    (3 or 4 features) T_prev and (4 features) T_prev2; norm = {mean, width}
+    of each feature."""
     nrm = np.ascontiguousarray(norm, np.float64)
-    _nn_check(lib.soc_nn_seed_features(_t_ptr(T), _t_ptr(T_prev), _t_ptr(rho), T.numel(), _np_ptr(nrm),
-                                       nrm.size // 2, _t_ptr(x), _stream(stream)), "soc_nn_seed_features")
+    _nn_check(lib.soc_nn_seed_features(_t_ptr(T), _t_ptr(T_prev), _t_ptr(T_prev2), _t_ptr(rho), T.numel(),
+                                       _np_ptr(nrm), nrm.size // 2, _t_ptr(x), _stream(stream)), "soc_nn_seed_features")
 
 
 def scale_add(y, x, a, stream=None):

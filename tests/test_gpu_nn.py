@@ -274,6 +274,19 @@ def test_seed_features_and_transform_match_oracle(libsoc):
     torch.cuda.synchronize()
     np.testing.assert_allclose(x3.cpu().numpy(), O.seed_features(T1, cl.rho.astype(np.float32), norm3, T_prev=Tp),
                                rtol=2e-7, atol=2e-7)
+    # four features: the change one iteration earlier too
+    Tpp = (Tp * rng.uniform(0.5, 1.0, cl.n_cells)).astype(np.float32)
+    norm4 = dict(norm3, pd_mean=0.25, pd_std=0.35)
+    x4 = torch.empty((cl.n_cells, 4), dtype=torch.float32, device="cuda")
+    ctx.seed_features(ids[0], T1d, [3.1, 0.7, -0.2, 1.4, 0.2, 0.3, 0.25, 0.35], x4, T_prev=torch.from_numpy(Tp).cuda(),
+                      T_prev2=torch.from_numpy(Tpp).cuda())
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(x4.cpu().numpy(),
+                               O.seed_features(T1, cl.rho.astype(np.float32), norm4, T_prev=Tp, T_prev2=Tpp),
+                               rtol=2e-7, atol=2e-7)
+    with pytest.raises(libsoc.SocError):                      # four features without T_prev2
+        ctx.seed_features(ids[0], T1d, [3.1, 0.7, -0.2, 1.4, 0.2, 0.3, 0.25, 0.35], x4,
+                          T_prev=torch.from_numpy(Tp).cuda())
     Tr = O.seed_transform(T1, pred, 0.15, 0.6)
     np.testing.assert_allclose(Ts.cpu().numpy(), Tr, rtol=2e-7)
     # shrink and a 64-bin envelope; cells within 1e-9 of a bin edge are left

@@ -41,7 +41,8 @@ def test_committed_weights_are_well_formed():
     lo, hi, y_lo, y_hi = norm["env"]
     assert lo < hi and len(y_lo) == len(y_hi) == L.ENV_BINS
     assert all(0.0 <= a <= b for a, b in zip(y_lo, y_hi))   # the seed never lowers T (y >= 0)
-    for k in ("lt_std", "lr_std", "ld_std", "y_std"):
+    assert L.n_features(norm) == L.FEATURES               # the inputs the seeding code feeds
+    for k in ("lt_std", "lr_std", "ld_std", "y_std") + (("pd_std",) if L.FEATURES == 4 else ()):
         assert norm[k] > 0.0
     assert meta["train"] == L.seed_ranges(L.TRAIN) and meta["val"] == [L.VAL[0], L.VAL[-1]]
     assert 0 <= meta["best_epoch"] < meta["epochs_run"]

@@ -235,6 +235,19 @@ def test_seed_features_standardise_their_own_statistics():
     x3 = nn.seed_features(T1, rho, dict(norm, ld_mean=d.mean(), ld_std=d.std()), T_prev=Tp)
     np.testing.assert_allclose(x3[:, :2], x, rtol=1e-15)
     np.testing.assert_allclose(x3[:, 2], (d - d.mean()) / d.std(), rtol=1e-12, atol=1e-12)
+    # the fourth is the standardised change one iteration earlier (T_prev to
+    # T_prev2), the first three as with three features (temperatures kept
+    # above the 2.7 K clamp)
+    Ta = rng.uniform(20.0, 300.0, 4096)
+    Tb = Ta * rng.uniform(0.5, 1.0, Ta.size)
+    Tc = Tb * rng.uniform(0.5, 1.0, Ta.size)
+    da, e = np.log(Ta) - np.log(Tb), np.log(Tb) - np.log(Tc)
+    n3 = dict(norm, ld_mean=da.mean(), ld_std=da.std())
+    x4 = nn.seed_features(Ta, rho, dict(n3, pd_mean=e.mean(), pd_std=e.std()), T_prev=Tb, T_prev2=Tc)
+    assert x4.shape == (Ta.size, 4)
+    np.testing.assert_allclose(x4[:, :3], nn.seed_features(Ta, rho, n3, T_prev=Tb), rtol=1e-15)
+    np.testing.assert_allclose(x4[:, 3], (e - e.mean()) / e.std(), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(x4[:, 3].std(), 1.0, rtol=1e-12)
     # identity normalisation gives the logarithms; T1 below 2.7 K and rho = 0 are clamped
     x0 = nn.seed_features([1.0, 10.0], [0.0, 2.0], dict(lt_mean=0.0, lt_std=1.0, lr_mean=-60.0, lr_std=20.0))
     np.testing.assert_allclose(x0, [[np.log(2.7), (np.log(1e-30) + 60) / 20], [np.log(10.0), (np.log(2.0) + 60) / 20]],
