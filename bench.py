@@ -37,8 +37,8 @@ WORKLOAD = "lognormal 128^3, 64 nu (3e11-3e15 Hz), 1e6 background packages/nu, H
 # DRAM bytes (read + write) per photon-cell step of trace_kernel from one ncu
 # capture (small case of the same workload, scaled by steps), valid only for
 # the kernel source it was taken on.
-TRACE_DRAM = {"source_sha1": "1779ba3fd86f381c4bbf94e157e7d52b74fb0e73", "bytes_per_step": 2.2121,
-              "warp_instructions_per_step": 7.757, "l2_bytes_per_step": 73.02,
+TRACE_DRAM = {"source_sha1": "0195c78cace870d5542a5cb2f8fcc31015d7c503", "bytes_per_step": 2.2797,
+              "warp_instructions_per_step": 7.758, "l2_bytes_per_step": 73.00,
               "profile": "profiles/trace_kernel_lognormal128_8nu_1e6pkg_full.md"}
 # issue-rate peak: 4 warp-instructions per cycle per SM (4 schedulers)
 ISSUE_PER_SM_CYCLE = 4
