@@ -170,3 +170,28 @@ def test_binding_refuses_host_and_strided_tensors(libsoc):
     with pytest.raises(ValueError):
         libsoc._t_ptr(torch.zeros(4))
     assert libsoc._t_ptr(None) is None
+
+
+def test_learned_seed_entry_points_reject_bad_arguments_on_the_host(libsoc):
+    """The network helpers check their arguments before any CUDA call, as
+    include/soc.h states (SOC_ERR_ARG = -1): null pointers, sizes, a NaN
+    factor, and four features without the iterate before the previous one.
+    The device pointers given are never dereferenced on these paths."""
+    import ctypes as C
+    ERR_ARG = -1
+    fake = C.c_void_p(0x1000)                      # a non-null device address, never touched here
+    f = libsoc.lib.soc_nn_scale_add
+    assert f(None, fake, 10, C.c_float(1.0), None) == ERR_ARG
+    assert f(fake, None, 10, C.c_float(1.0), None) == ERR_ARG
+    assert f(fake, fake, 0, C.c_float(1.0), None) == ERR_ARG
+    assert f(fake, fake, 10, C.c_float(float("nan")), None) == ERR_ARG
+    norm = np.ascontiguousarray([0.0, 1.0] * 4, np.float64)
+    nptr = norm.ctypes.data_as(C.c_void_p)
+    g = libsoc.lib.soc_nn_seed_features
+    # (T, T_prev, T_prev2, rho, n, norm, n_features, x, stream)
+    assert g(fake, fake, None, fake, 10, nptr, 4, fake, None) == ERR_ARG      # four features need T_prev2
+    assert g(fake, None, None, fake, 10, nptr, 3, fake, None) == ERR_ARG      # three need T_prev
+    assert g(fake, fake, fake, fake, 10, nptr, 5, fake, None) == ERR_ARG      # 2 to 4 features
+    assert g(fake, fake, fake, None, 10, nptr, 2, fake, None) == ERR_ARG      # rho
+    bad = np.ascontiguousarray([0.0, 1.0, 0.0, 1.0, 0.0, 0.0], np.float64)   # a zero width
+    assert g(fake, fake, None, fake, 10, bad.ctypes.data_as(C.c_void_p), 3, fake, None) == ERR_ARG
