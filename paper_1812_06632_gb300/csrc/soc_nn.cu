@@ -205,6 +205,91 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
                  :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar) : "memory");
 }
 
+// Bookkeeping of a persistent convolution block, in shared memory after its
+// n_stages operand stages: full/empty per stage (TMA bytes arrived / MMAs
+// done with it), acc_full/acc_empty per accumulator buffer (MMAs of a box
+// done / epilogue done), the drain barrier (all MMAs done, after a failure),
+// the tensor-memory slot and the failure flag.
+struct ConvBlock {
+    uint64_t *full, *empty, *acc_full, *acc_empty, *drain;
+    int *s_fail;
+    uint32_t tmem;
+};
+
+// Carve the bookkeeping after the stages, allocate tmem_cols columns of
+// tensor memory (warp 5) and initialise the barriers (thread 0).  Every
+// thread of the block calls it.
+__device__ __forceinline__ ConvBlock conv_block_begin(uint8_t *after_stages, int n_stages, uint32_t tmem_cols)
+{
+    ConvBlock c;
+    c.full = reinterpret_cast<uint64_t *>(after_stages);
+    c.empty = c.full + n_stages;
+    c.acc_full = c.empty + n_stages;
+    c.acc_empty = c.acc_full + 2;
+    c.drain = c.acc_empty + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(c.drain + 1);
+    c.s_fail = reinterpret_cast<int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(tmem_cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int k = 0; k < n_stages; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&c.full[k])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&c.empty[k])) : "memory");
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&c.acc_full[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" :: "r"(smem_u32(&c.acc_empty[b])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(c.drain)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *c.s_fail = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    c.tmem = *tslot;
+    return c;
+}
+
+// The producer's last stages (issued: its copies so far, into stages
+// h mod n_stages): after a failure the copies in flight land, else the MMAs'
+// releases of them arrive, before the block leaves.  Bounded waits.
+__device__ __forceinline__ void conv_producer_tail(const ConvBlock &c, int n_stages, int issued)
+{
+    const bool failed = *reinterpret_cast<volatile int *>(c.s_fail);
+    for (int h = (issued > n_stages ? issued - n_stages : 0); h < issued; ++h)
+        mbar_wait(smem_u32(failed ? &c.full[h % n_stages] : &c.empty[h % n_stages]), (uint32_t)(h / n_stages) & 1u);
+}
+
+// End of a block: every MMA has completed before the tensor memory is freed
+// (the epilogue waited for the last box's accumulator, or, after a failure,
+// the MMA thread waits, bounded, for all it issued); a failure raises the
+// error flag.  Every thread calls it.
+__device__ __forceinline__ void conv_block_end(const ConvBlock &c, uint32_t tmem_cols)
+{
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    const bool ok = __syncthreads_and(!*reinterpret_cast<volatile int *>(c.s_fail));
+    if (!ok) {
+        if (tid == 0) atomicExch(&g_tc_error, 1);
+        if (warp == 5 && lane == 0) {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(c.drain)) : "memory");
+            mbar_wait(smem_u32(c.drain), 0);
+        }
+    }
+    __syncthreads();
+    if (warp == 5) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(c.tmem), "r"(tmem_cols) : "memory");
+    }
+}
+
 // Persistent and warp-specialised: a block of 6 warps walks the output
 // boxes blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 4 (lane 0) issues the
 // TMA loads into n_stages shared-memory stages, warp 5 (lane 0) the MMAs into
@@ -228,14 +313,12 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tma_kernel(const __grid_c
     constexpr int kRow = KC * 2;                       // bytes per operand row
     const int a_bytes = 128 * kRow, b_bytes = n_tile * kRow;
     const int stage_bytes = a_bytes + b_bytes;         // multiple of 1024
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + n_stages * stage_bytes);
-    uint64_t *empty = full + n_stages;
-    uint64_t *acc_full = empty + n_stages;             // [2]
-    uint64_t *acc_empty = acc_full + 2;                // [2]
-    uint64_t *drain = acc_empty + 2;                   // MMAs done, after a failure
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(drain + 1);
-    int *s_fail = reinterpret_cast<int *>(tslot + 1);
+    const ConvBlock cb = conv_block_begin(smem + n_stages * stage_bytes, n_stages, tmem_cols);
+    uint64_t *const full = cb.full, *const empty = cb.empty, *const acc_full = cb.acc_full;
+    uint64_t *const acc_empty = cb.acc_empty;
+    int *const s_fail = cb.s_fail;
     volatile int *fail = s_fail;
+    const uint32_t tmem = cb.tmem;
     const uint32_t smem0 = smem_u32(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n0 = blockIdx.y * n_tile;
@@ -244,28 +327,6 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tma_kernel(const __grid_c
     const int n_boxes = a.tiles_x * a.tiles_y * a.tiles_z * ((a.N + a.bn - 1) / a.bn);
     const uint32_t tx_bytes = (uint32_t)(a.bx * a.by * a.bz * a.bn) * kRow + (uint32_t)b_bytes;
 
-    if (warp == 5) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(tslot)), "r"(tmem_cols) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (tid == 0) {
-        for (int k = 0; k < n_stages; ++k) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[k])) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[k])) : "memory");
-        }
-        for (int b = 0; b < 2; ++b) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&acc_full[b])) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" :: "r"(smem_u32(&acc_empty[b])) : "memory");
-        }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(drain)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        *s_fail = 0;
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tslot;
 
     if (warp == 4) {
         if (lane == 0) {
@@ -305,11 +366,7 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tma_kernel(const __grid_c
                 }
                 if (stop) break;
             }
-            // the last stages: after a failure the loads in flight land, else
-            // the MMAs' releases of them arrive, before the block leaves
-            const bool failed = *fail;
-            for (int h = (issued > n_stages ? issued - n_stages : 0); h < issued; ++h)
-                mbar_wait(smem_u32(failed ? &full[h % n_stages] : &empty[h % n_stages]), (uint32_t)(h / n_stages) & 1u);
+            conv_producer_tail(cb, n_stages, issued);
         }
     } else if (warp == 5) {
         if (lane == 0) {
@@ -382,25 +439,7 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tma_kernel(const __grid_c
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&acc_empty[b])) : "memory");
         }
     }
-    // every MMA of the block has completed before its tensor memory is freed:
-    // the epilogue waited for the last box's accumulator, or, after a
-    // failure, the MMA thread waits (bounded) for all it issued
-    __syncwarp();
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    const bool ok = __syncthreads_and(!*fail);
-    if (!ok) {
-        if (tid == 0) atomicExch(&g_tc_error, 1);
-        if (warp == 5 && lane == 0) {
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(drain)) : "memory");
-            mbar_wait(smem_u32(drain), 0);
-        }
-    }
-    __syncthreads();
-    if (warp == 5) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols) : "memory");
-    }
+    conv_block_end(cb, tmem_cols);
 }
 
 // ---------------------------------------------------------------------------
@@ -436,42 +475,18 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3d_slab_kernel(const __gr
     const int bx = a.W;
     const int rows_s = bx * (a.by + 2) * (a.bz + 2);
     const int tap_bytes = n_tile * kRow;
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + n_stages * stage_bytes);
-    uint64_t *empty = full + n_stages;
-    uint64_t *acc_full = empty + n_stages;
-    uint64_t *acc_empty = acc_full + 2;
-    uint64_t *drain = acc_empty + 2;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(drain + 1);
-    int *s_fail = reinterpret_cast<int *>(tslot + 1);
+    const ConvBlock cb = conv_block_begin(smem + n_stages * stage_bytes, n_stages, tmem_cols);
+    uint64_t *const full = cb.full, *const empty = cb.empty, *const acc_full = cb.acc_full;
+    uint64_t *const acc_empty = cb.acc_empty;
+    int *const s_fail = cb.s_fail;
     volatile int *fail = s_fail;
+    const uint32_t tmem = cb.tmem;
     const uint32_t smem0 = smem_u32(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n0 = blockIdx.y * n_tile;
     const int n_boxes = a.tiles_y * a.tiles_z * a.N;
     const uint32_t tx_bytes = (uint32_t)rows_s * kRow + 9u * (uint32_t)tap_bytes;
 
-    if (warp == 5) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(tslot)), "r"(tmem_cols) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (tid == 0) {
-        for (int k = 0; k < n_stages; ++k) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[k])) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[k])) : "memory");
-        }
-        for (int b = 0; b < 2; ++b) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&acc_full[b])) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" :: "r"(smem_u32(&acc_empty[b])) : "memory");
-        }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(drain)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        *s_fail = 0;
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tslot;
 
     if (warp == 4) {
         if (lane == 0) {
@@ -513,9 +528,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3d_slab_kernel(const __gr
                     }
                 }
             }
-            const bool failed = *fail;
-            for (int h = (issued > n_stages ? issued - n_stages : 0); h < issued; ++h)
-                mbar_wait(smem_u32(failed ? &full[h % n_stages] : &empty[h % n_stages]), (uint32_t)(h / n_stages) & 1u);
+            conv_producer_tail(cb, n_stages, issued);
         }
     } else if (warp == 5) {
         if (lane == 0) {
@@ -607,22 +620,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3d_slab_kernel(const __gr
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&acc_empty[b])) : "memory");
         }
     }
-    __syncwarp();
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    const bool ok = __syncthreads_and(!*fail);
-    if (!ok) {
-        if (tid == 0) atomicExch(&g_tc_error, 1);
-        if (warp == 5 && lane == 0) {
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(drain)) : "memory");
-            mbar_wait(smem_u32(drain), 0);
-        }
-    }
-    __syncthreads();
-    if (warp == 5) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols) : "memory");
-    }
+    conv_block_end(cb, tmem_cols);
 }
 
 // Wt[ci][t][co] = W[co][26 - t][ci]: weights of the transposed convolution.
