@@ -1187,11 +1187,15 @@ inline int grid_1d(long long n, int block = 256)
 // One thread per element (no grid-stride loop)
 inline unsigned grid_all(long long n, int block = 256) { return (unsigned)((n + block - 1) / block); }
 
-// Grid of the row kernels: threads over row_threads, blockIdx.y over at most
-// 65535 of the rows (the kernels stride by gridDim.y)
+// Grid of the row kernels: threads over row_threads, blockIdx.y over the
+// rows, at most about 8 blocks per SM's worth in all (the kernels stride by
+// gridDim.y, so each block takes several rows)
 inline dim3 grid_rows(int row_threads, long long rows)
 {
-    return dim3((unsigned)((row_threads + 127) / 128), (unsigned)(rows < 65535 ? (rows < 1 ? 1 : rows) : 65535));
+    const long long gx = (row_threads + 127) / 128;
+    long long gy = std::max(1LL, 1216 / gx);
+    gy = std::min(gy, std::max(1LL, rows));
+    return dim3((unsigned)gx, (unsigned)gy);
 }
 
 
