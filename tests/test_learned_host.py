@@ -1,6 +1,8 @@
 """Host side of the learned seed (no GPU): the cloud splits, the
-oversampling rule, and the committed trained weights as loaded."""
+oversampling rule, the committed trained weights as loaded, and the
+segmentation of a re-seeded run (with a fake iteration and seeder)."""
 import numpy as np
+import pytest
 
 from paper_1812_06632_gb300 import learned as L
 
@@ -47,3 +49,58 @@ def test_committed_weights_are_well_formed():
     assert meta["train"] == L.seed_ranges(L.TRAIN) and meta["val"] == [L.VAL[0], L.VAL[-1]]
     assert 0 <= meta["best_epoch"] < meta["epochs_run"]
     assert len(digest) == 64
+
+
+class _FakeSeeder:
+    """Seeds with a tenth of the latest iterate's error; records its inputs."""
+
+    def __init__(self, history):
+        self.history, self.calls = history, []
+
+    def seeds(self, ctx, ids, Tks, Tps, Tpps=None, shrink=None):
+        self.calls.append((len(ids), Tpps is not None))
+        assert len(Tks) == len(Tps) == len(ids)
+        assert (Tpps is not None) == (self.history == 3)
+        return [t * 0.1 for t in Tks]
+
+
+def _fake_iterations(monkeypatch):
+    """Each dust iteration halves a cloud's error T; it has converged once
+    the change, half the error, is below tol."""
+    torch = pytest.importorskip("torch")
+
+    def dust(ctx, ids, outs, seeds=None, max_iter=300, tol=0.1):
+        rows = []
+        for i in range(len(ids)):
+            t, its, conv = float(seeds[i].item()), 0, False
+            while its < max_iter and not conv:
+                change = t / 2
+                t -= change
+                its += 1
+                conv = change < tol
+            outs[i].fill_(t)
+            rows.append(dict(iterations=its, converged=conv, steps=its, final_max_dT=change))
+        return rows
+    monkeypatch.setattr(L, "dust_iterations", dust)
+    return torch
+
+
+@pytest.mark.parametrize("history", [2, 3])
+def test_seeded_run_counts_every_segment_and_feeds_the_iterates(monkeypatch, history):
+    torch = _fake_iterations(monkeypatch)
+    starts = [torch.tensor([v]) for v in (1000.0, 0.15, 40.0)]
+    # no re-seeding: one call, the plain count from each start
+    s = _FakeSeeder(history)
+    rows, fin = L.seeded_run(None, [0, 1, 2], s, starts, max_iter=300, tol=0.1)
+    assert [r["iterations"] for r in rows] == [14, 1, 9] and all(r["converged"] for r in rows)
+    assert s.calls == []
+    # re-seeding every 5: after 5 - (history - 1) iterations and history - 1
+    # single ones the unconverged clouds are seeded (error / 10) and go on
+    s = _FakeSeeder(history)
+    rows, fin = L.seeded_run(None, [0, 1, 2], s, starts, max_iter=300, tol=0.1, reseed=5)
+    assert all(r["converged"] for r in rows)
+    assert s.calls[0] == (2, history == 3)                     # clouds 0 and 2, with T_{k-2} for 3 iterates
+    assert rows[1]["iterations"] == 1 and rows[0]["iterations"] < 14
+    assert all(float(f.item()) < 0.2 for f in fin)
+    with pytest.raises(ValueError):
+        L.seeded_run(None, [0], _FakeSeeder(history), starts[:1], reseed=history - 1)
