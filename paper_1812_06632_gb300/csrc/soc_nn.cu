@@ -659,17 +659,19 @@ struct WgradArgs {
 // bytes).  Core (mn, k) of A sits at (k * 16 + mn) * 128 bytes, of B at
 // (k * n_tile / 8 + mn) * 128: the stride between cores along M/N (the
 // descriptor's stride offset) is 128 B, along K (its leading offset)
-// 16 * 128 or n_tile / 8 * 128 B.  A step covers kWgKV = 64 voxels (four
-// MMAs with K = 16); two threads share a voxel.
+// 16 * 128 or n_tile / 8 * 128 B.  A step covers kWgKV = 128 voxels (eight
+// MMAs with K = 16); two threads of the block's 256 share a voxel, and warps
+// 0-3 read the accumulator out.
 // ---------------------------------------------------------------------------
-constexpr int kWgKV = 64;
+constexpr int kWgKV = 128;
+constexpr int kWgThreads = 2 * kWgKV;         // two threads per voxel of a step
 
 __host__ __device__ constexpr uint32_t mma_idesc_mn(int m, int n)
 {
     return mma_idesc(m, n) | (1u << 15) | (1u << 16);       // A and B MN-major
 }
 
-__global__ void __launch_bounds__(128) conv3d_wgrad_tc_kernel(const WgradArgs a, int ci_tile, int n_tile,
+__global__ void __launch_bounds__(kWgThreads) conv3d_wgrad_tc_kernel(const WgradArgs a, int ci_tile, int n_tile,
                                                              uint32_t tmem_cols, int n_stages)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -707,7 +709,7 @@ __global__ void __launch_bounds__(128) conv3d_wgrad_tc_kernel(const WgradArgs a,
     const int NC = n_tile / 8, CP = ci_tile / 8;           // 16-byte pieces per voxel of B and per tap of A
     const uint32_t a_lbo = 16 * 128, b_lbo = (uint32_t)NC * 128;      // stride between cores along K
     const uint32_t idesc = mma_idesc_mn(128, n_tile);
-    const int kv = tid & (kWgKV - 1), half = tid >> 6;                 // this thread's voxel and half
+    const int kv = tid & (kWgKV - 1), half = tid / kWgKV;              // this thread's voxel and half
 
     // this thread's 8 pieces of A: piece pc = half * 8 + i is tap tap0 +
     // pc / CP of the block (offsets tdx, tdy, tdz), channels tco
@@ -817,8 +819,9 @@ __global__ void __launch_bounds__(128) conv3d_wgrad_tc_kernel(const WgradArgs a,
         ok_run = __syncthreads_and(ok_run && done);
     }
     if (!ok_run) {
-        atomicExch(&g_tc_error, 1);
-    } else {
+        if (tid == 0) atomicExch(&g_tc_error, 1);
+    } else if (warp < 4) {
+        // warps 0-3 read the 128 accumulator lanes (warp w: lanes 32w ..)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16);
         const int tap = tap0 + tid / ci_tile, ci = ci0 + tid % ci_tile;   // accumulator lane = (tap, ci)
@@ -1488,10 +1491,10 @@ inline WgradPlan wgrad_plan(long long V, int Cin, int Cout, int sms, int sm_smem
 {
     WgradPlan p;
     // input-channel tile: 16, 32, 64 or 128 (dividing C_in), 128 / tile taps
-    // per block; output-channel tile: a multiple of 16, at most 256
+    // per block; output-channel tile: a multiple of 16, at most 128
     p.ci_tile = 128;
     while (p.ci_tile > 16 && Cin % p.ci_tile) p.ci_tile >>= 1;
-    p.n_tile = 256;
+    p.n_tile = 128;          // at most 128: three stages of kWgKV voxels fit a block
     while (p.n_tile > 16 && (p.n_tile > Cout || Cout % p.n_tile)) p.n_tile -= 16;
     const int TT = 128 / p.ci_tile;
     p.tap_groups = (27 + TT - 1) / TT;
@@ -1556,7 +1559,7 @@ cudaError_t wgrad_launch(const WgradArgs &a0, float *gw, long long part_floats, 
     cudaError_t e = cudaFuncSetAttribute(conv3d_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)p.chunks, (unsigned)p.tap_groups, (unsigned)((a.Cin / p.ci_tile) * (a.Cout / p.n_tile)));
-    conv3d_wgrad_tc_kernel<<<grid, 128, bytes, s>>>(a, p.ci_tile, p.n_tile, cols, stages);
+    conv3d_wgrad_tc_kernel<<<grid, kWgThreads, bytes, s>>>(a, p.ci_tile, p.n_tile, cols, stages);
     reduce_partials_kernel<<<grid_1d(n_w), 256, 0, s>>>(a.part, (int)p.chunks, n_w, gw);
     return cudaGetLastError();
 }
